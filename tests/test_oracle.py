@@ -1,0 +1,229 @@
+"""Pins for the FP64 oracle, each tied to something other than the oracle itself:
+closed forms, library routines (scipy), brute force on tiny grids, a
+manufactured solution and the textbook Chebyshev error bound."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.linalg
+import scipy.sparse.linalg as spl
+
+import oracle as O
+from workloads import bumps_medium, manufactured_medium, Medium
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _random_medium(seed):
+    rng = np.random.default_rng(seed)
+    a, b, c = rng.uniform(0.5, 2.0, 3)
+
+    def kappa(r, z):
+        return 1.0 + a * np.sin(3 * r + b) ** 2 + c * z * z
+
+    def q(r, z):
+        return 0.3 + 0.2 * np.cos(2 * r * z) ** 2
+
+    return Medium("rand", kappa, q, [lambda r, z: np.exp(r - z)])
+
+
+def _op(nr, nz, seed=0):
+    g = O.Grid(nr, nz)
+    kr, kz, q, f = O.sample_medium(_random_medium(seed), g)
+    return O.Operator(kr, kz, q, g), f
+
+
+# --------------------------------------------------------------------------- A
+@pytest.mark.parametrize("nr,nz", [(1, 1), (1, 4), (3, 1), (3, 5), (6, 4), (9, 7)])
+def test_operator_symmetric_positive_definite(nr, nz):
+    op, _ = _op(nr, nz)
+    A = op.A.toarray()
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+def test_operator_tiny_by_hand():
+    line = [l for l in open(os.path.join(GOLDEN, "tiny_operator.txt")) if l.startswith("A ")][0]
+    vals = [float(x) for x in line.split()[1:]]
+    g = O.Grid(2, 1)
+    kr, kz, q, _ = O.sample_medium(Medium("one", lambda r, z: np.ones(np.broadcast(r, z).shape),
+                                          lambda r, z: np.zeros(np.broadcast(r, z).shape),
+                                          [lambda r, z: r * 0]), g)
+    A = O.assemble(*O.scheme_coefficients(kr, kz, q, g), g).toarray()
+    np.testing.assert_allclose(A.ravel(), vals, rtol=1e-14)
+
+
+def test_operator_row_sums_conservative():
+    """Flux form: away from Dirichlet neighbours a constant has zero flux
+    divergence, so (A 1) = W there, including the one-sided axis row."""
+    nr, nz = 7, 9
+    op, _ = _op(nr, nz, seed=3)
+    s = op.apply_A(np.ones((nr, nz)))
+    inner = (slice(0, nr - 1), slice(1, nz - 1))
+    np.testing.assert_allclose(s[inner], op.W[inner], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("variable_kappa", [False, True])
+def test_manufactured_solution_second_order(variable_kappa):
+    """Section 2.1 states second-order accuracy (Table 2 prints error ratios
+    4.09 and 5 per halving).  With u* = cos(pi r/2) sin(pi z) the max-norm
+    nodal error must fall about 4x per halving of h."""
+    med, u = manufactured_medium(q0=1.0, variable_kappa=variable_kappa)
+    errs = []
+    for n in (16, 32, 64, 128):
+        g = O.Grid(n, n)
+        kr, kz, q, f = O.sample_medium(med, g)
+        op = O.Operator(kr, kz, q, g)
+        y = spl.spsolve(op.A.tocsc(), op.phi(f[0]).ravel()).reshape(n, n)
+        errs.append(np.abs(y - u(g.r[:, None], g.z[None, :])).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.5 < x < 5.1 for x in ratios), ratios
+    assert errs[-1] < 1e-4
+
+
+# ------------------------------------------------------------- sine transform
+def test_dst1_golden_and_closed_forms():
+    lines = [l for l in open(os.path.join(GOLDEN, "dst1_n3.txt")) if not l.startswith("#")]
+    S3 = np.array([[float(x) for x in l.split()] for l in lines[:3]])
+    np.testing.assert_allclose(O.dst1_matrix(3), S3, atol=1e-15)
+    eig = [float(x) for x in lines[3].split()[1:]]
+    np.testing.assert_allclose(O.mode_eigenvalues(3, 0.25), eig, rtol=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 127])
+def test_dst1_orthogonal_and_matches_scipy(n):
+    S = O.dst1_matrix(n)
+    np.testing.assert_allclose(S @ S, np.eye(n), atol=1e-13)
+    ref = scipy.fft.dst(np.eye(n), type=1, norm="ortho", axis=0)
+    np.testing.assert_allclose(S, ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 5, 33])
+def test_dst1_diagonalises_dirichlet_second_difference(n):
+    h = 1.0 / (n + 1)
+    L = (2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)) / h ** 2
+    S = O.dst1_matrix(n)
+    np.testing.assert_allclose(S @ L @ S, np.diag(O.mode_eigenvalues(n, h)), atol=1e-9 * (n + 1) ** 2)
+
+
+# ------------------------------------------------------------------- Thomas
+@pytest.mark.parametrize("n,k", [(1, 1), (2, 3), (3, 1), (17, 4), (100, 2)])
+def test_thomas_matches_banded_solver(n, k):
+    rng = np.random.default_rng(n)
+    sub = rng.uniform(-1, 1, n - 1)
+    sup = rng.uniform(-1, 1, n - 1)
+    diag = 2.5 + rng.uniform(0, 1, n)
+    b = rng.normal(size=(n, k))
+    ab = np.zeros((3, n))
+    ab[0, 1:], ab[1], ab[2, :-1] = sup, diag, sub
+    ref = scipy.linalg.solve_banded((1, 1), ab, b)
+    np.testing.assert_allclose(O.thomas(sub, diag, sup, b), ref, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------ preconditioner
+@pytest.mark.parametrize("nr,nz", [(1, 1), (2, 3), (5, 2), (8, 8), (13, 6)])
+def test_precond_solve_matches_dense_solve_of_B(nr, nz):
+    g = O.Grid(nr, nz)
+    kt, qt = 1.7, 0.35
+    B = O.assemble_preconditioner(kt, qt, g).toarray()
+    v = np.random.default_rng(nr * 31 + nz).normal(size=(nr, nz))
+    ref = np.linalg.solve(B, v.ravel()).reshape(nr, nz)
+    np.testing.assert_allclose(O.precond_solve(v, kt, qt, g), ref, rtol=1e-11, atol=1e-13)
+
+
+def test_preconditioner_constants_mean_of_extremes():
+    kr = np.array([[1.0, 4.0]])
+    kz = np.array([[2.0, 3.0, 9.0]])
+    q = np.array([[0.5, 1.5]])
+    assert O.preconditioner_constants(kr, kz, q) == (5.0, 1.0)
+
+
+def test_pcg_one_iteration_when_coefficients_constant():
+    """kappa and q constant => B = A exactly (Eq. coeff2), so PCG converges in
+    one step."""
+    g = O.Grid(24, 20)
+    med = Medium("const", lambda r, z: np.full(np.broadcast(r, z).shape, 2.3),
+                 lambda r, z: np.full(np.broadcast(r, z).shape, 0.7),
+                 [lambda r, z: np.exp(-((r - .3) ** 2 + (z - .6) ** 2) * 20)])
+    kr, kz, q, f = O.sample_medium(med, g)
+    op = O.Operator(kr, kz, q, g)
+    assert (abs(op.A - O.assemble_preconditioner(op.kappa_t, op.q_t, g)).max()) < 1e-10
+    y, info = op.solve(f[0], tol=1e-13)
+    assert info.iters == 1 and info.rel_res <= 1e-13
+
+
+# ------------------------------------------------------------------------ PCG
+@pytest.mark.parametrize("nr,nz", [(3, 4), (16, 9), (33, 20)])
+def test_pcg_matches_direct_solve(nr, nz):
+    op, f = _op(nr, nz, seed=nr)
+    y, info = op.solve(f[0], tol=1e-13)
+    ref = spl.spsolve(op.A.tocsc(), op.phi(f[0]).ravel()).reshape(nr, nz)
+    assert info.converged
+    assert np.linalg.norm(y - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_pcg_bumps_64_matches_direct_solve():
+    g = O.Grid(64, 64)
+    kr, kz, q, f = O.sample_medium(bumps_medium(), g)
+    op = O.Operator(kr, kz, q, g)
+    y, info = op.solve(f[0], tol=1e-10)
+    assert info.converged and info.rel_res <= 1e-10
+    ref = spl.spsolve(op.A.tocsc(), op.phi(f[0]).ravel()).reshape(64, 64)
+    assert np.linalg.norm(y - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert 5 <= info.iters <= 60
+
+
+def test_pcg_iterations_independent_of_grid():
+    """The condition number of B^-1 A does not depend on h (Section 2.2), and
+    Table 2 prints nearly equal counts for three grids."""
+    its = []
+    for n in (32, 64, 128):
+        g = O.Grid(n, n)
+        kr, kz, q, f = O.sample_medium(bumps_medium(), g)
+        _, info = O.Operator(kr, kz, q, g).solve(f[0], tol=1e-10)
+        its.append(info.iters)
+    assert max(its) <= 1.15 * min(its) + 1, its
+
+
+# ------------------------------------------------------------------ Chebyshev
+def test_chebyshev_bounds_contain_generalised_spectrum():
+    op, _ = _op(6, 5, seed=7)
+    A = op.A.toarray()
+    B = O.assemble_preconditioner(op.kappa_t, op.q_t, op.grid).toarray()
+    ev = scipy.linalg.eigh(A, B, eigvals_only=True)
+    g1, g2 = op.gamma
+    assert g1 <= ev.min() * (1 + 1e-12) and ev.max() <= g2 * (1 + 1e-12)
+
+
+def test_chebyshev_error_bound_each_step():
+    """A-norm error after n steps <= 2 rho1^n / (1 + rho1^(2n)) ||e0||_A,
+    rho1 = (1 - sqrt(xi)) / (1 + sqrt(xi)): the Chebyshev-polynomial bound."""
+    op, f = _op(10, 12, seed=11)
+    phi = op.phi(f[0])
+    u = spl.spsolve(op.A.tocsc(), phi.ravel()).reshape(phi.shape)
+    A = op.A
+
+    def anorm(e):
+        return math.sqrt(float(e.ravel() @ (A @ e.ravel())))
+
+    g1, g2 = op.gamma
+    xi = g1 / g2
+    rho1 = (1 - math.sqrt(xi)) / (1 + math.sqrt(xi))
+    e0 = anorm(u)
+    for n in range(1, 12):
+        y, info = O.chebyshev(op.apply_A, op.apply_Binv, phi, g1, g2, tol=0.0, max_iter=n)
+        assert info.iters == n
+        bound = 2 * rho1 ** n / (1 + rho1 ** (2 * n))
+        assert anorm(u - y) <= bound * e0 * (1 + 1e-9) + 1e-14
+
+
+def test_chebyshev_agrees_with_pcg():
+    g = O.Grid(64, 64)
+    kr, kz, q, f = O.sample_medium(bumps_medium(), g)
+    op = O.Operator(kr, kz, q, g)
+    y1, i1 = op.solve(f[0], tol=1e-11)
+    y2, i2 = op.solve(f[0], tol=1e-11, method="cheb")
+    assert i1.converged and i2.converged
+    assert np.linalg.norm(y1 - y2) <= 1e-8 * np.linalg.norm(y1)
