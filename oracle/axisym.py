@@ -80,7 +80,8 @@ def sample_medium(medium, grid: Grid, rhs_index=None):
     kappa_z = medium.kappa(r[:, None], zbar[None, :])
     q = medium.q(r[:, None], z[None, :])
     idx = range(medium.n_rhs) if rhs_index is None else rhs_index
-    f = np.stack([medium.f(r[:, None], z[None, :], m) for m in idx])
+    fs = [np.broadcast_to(medium.f(r[:, None], z[None, :], m), (grid.nr, grid.nz)) for m in idx]
+    f = np.stack(fs) if fs else np.zeros((0, grid.nr, grid.nz))
     return (np.ascontiguousarray(kappa_r, dtype=np.float64),
             np.ascontiguousarray(kappa_z, dtype=np.float64),
             np.ascontiguousarray(q, dtype=np.float64),
@@ -167,7 +168,10 @@ def dst1_matrix(n: int) -> np.ndarray:
     k, l = 1..n.  The eigenvectors of the Dirichlet second difference along z
     (the sine counterpart of the cosine sums of Eq. fft_phi)."""
     k = np.arange(1, n + 1)
-    return math.sqrt(2.0 / (n + 1)) * np.sin(np.pi * np.outer(k, k) / (n + 1))
+    # sin(pi k l / (n+1)) has period 2 (n+1) in the integer k l: reduce it
+    # exactly before scaling, so large arguments lose no accuracy.
+    kl = np.outer(k, k) % (2 * (n + 1))
+    return math.sqrt(2.0 / (n + 1)) * np.sin(np.pi * kl / (n + 1))
 
 
 def mode_eigenvalues(nz: int, hz: float) -> np.ndarray:
