@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: unknowns solved per second at relative residual 1e-8.
+
+Workload (default ``layered_1024_m64``): the axisymmetric equation on a
+1024 x 1024 grid (r x z), 64 right-hand sides (Gaussian point sources), kappa in
+8 z-layers times an elliptical x5 inclusion, q proportional to kappa.  One
+"step" is one complete solve of all 64 right-hand sides to an FP64 true
+relative residual of 1e-8 with the chosen form (FP32 PCG inside FP64
+iterative refinement), inputs resident in HBM.  The plain FP64 PCG on the
+same GPU is timed beside it.  Under torchrun each rank solves its own replica
+(weak scaling, no data-path collective).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "unknowns solved/s at rel. residual 1e-8"
+UNIT = "unknowns/s"
+TOL = 1e-8
+
+# Algorithmic bytes per grid unknown of one launch (FP32 working precision),
+# M = right-hand sides sharing the coefficient tables.
+#   stencil (p = z + beta p, q = A p): read z, p_old; write p, q  -> 16 B, + CR, CZ, W (12 B / M)
+#   forward transform (x += a p, r -= a q, rhat = S r): read x, p, r, q; write x, r, rhat -> 28 B
+#   mode solves: read rhat, write yhat -> 8 B, + IP (4 B / M)
+#   inverse transform (z = S yhat, (r, z)): read yhat, r; write z -> 12 B
+#   FP64 outer residual (r = phi - A x): read x, phi (FP64); write r (FP32) -> 20 B, + 24 B / M
+ALG_BYTES = {"stencil": (16.0, 12.0), "dst_forward": (28.0, 0.0), "mode_solve": (8.0, 4.0),
+             "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0)}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="layered_1024_m64")
+    ap.add_argument("--method", default="pcg_mixed", choices=["pcg_mixed", "cheb_mixed", "pcg64", "cheb64"])
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed solves of the plain FP64 comparator")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(name: str, instance: int = 0):
+    from workloads import layered_inclusion_medium, large_medium, bumps_medium
+    if name == "layered_1024_m64":
+        return 1024, 1024, layered_inclusion_medium(64, 1024, instance=instance)
+    if name == "large_4096_m16":
+        return 4096, 4096, large_medium(16, 4096, instance=instance)
+    if name == "bumps_64":
+        return 64, 64, bumps_medium(instance)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, one right-hand side per process
+# ---------------------------------------------------------------------------
+def _oracle_one(args):
+    name, j = args
+    import oracle as O
+    nr, nz, med = workload(name)
+    g = O.Grid(nr, nz)
+    kr, kz, q, f = O.sample_medium(med, g, rhs_index=[j])
+    t0 = time.perf_counter()
+    op = O.Operator(kr, kz, q, g)
+    t1 = time.perf_counter()
+    _, info = op.solve(f[0], TOL)
+    t2 = time.perf_counter()
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": info.iters, "unknowns": nr * nz,
+            "converged": bool(info.converged)}
+
+
+def oracle_pool(cores: int):
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    for k in env_keys:
+        os.environ[k] = "1"  # inherited by the spawned workers before they import numpy
+    return mp.get_context("spawn").Pool(cores)
+
+
+def cpu_baseline(name: str, cores: int, pool=None):
+    """Solves `cores` right-hand sides of the workload, one per core, with the
+    oracle's PCG; returns unknowns solved per second of wall time."""
+    own = pool is None
+    pool = pool or oracle_pool(cores)
+    try:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_one, [(name, j % 64) for j in range(cores)])
+        wall = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    unknowns = sum(r["unknowns"] for r in res)
+    return {"value": unknowns / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} right-hand sides of {name}, one per host core, FP64 oracle PCG to {TOL:g} "
+                      f"(set-up included), wall {wall:.1f} s, iterations {[r['iters'] for r in res][:4]}...",
+            "wall_s": wall}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    pool = oracle_pool(cores)
+    try:
+        # warm-up steps: a 64 x 64 solve per core (pool start-up, imports)
+        for _ in range(args.warmup):
+            pool.map(_oracle_one, [("bumps_64", 0)] * cores)
+        times, units = [], 0
+        for _ in range(args.steps):
+            r = cpu_baseline(args.workload, cores, pool)
+            times.append(r["wall_s"])
+            units += cores * 1024 * 1024
+        total = sum(times)
+        value = units / total
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": args.workload, "rhs_per_step": cores, "tol": TOL},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"each step: {cores} right-hand sides of {args.workload}, one per core"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+    finally:
+        pool.close()
+        pool.join()
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    # The oracle pool must start before the first CUDA call (spawned workers).
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = os.cpu_count() or 1
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = oracle_pool(cores)
+
+    import numpy as np
+    import torch
+    import paper_1002_3094_gb300 as P
+    from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    P.build()
+    P.load_library()
+
+    nr, nz, med = workload(args.workload, instance=rank)
+    m = med.n_rhs
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz)
+    f_host = sample_rhs(med, nr, nz)
+    f = torch.from_numpy(f_host).to(dev)
+    u = torch.zeros_like(f)
+    method = P.METHODS[args.method]
+    stream = torch.cuda.current_stream()
+
+    def solve(meth=method, ff=f, uu=u, flags=0):
+        st, info = P.ax_solve(op, ff, uu, m, TOL, 20000, meth, flags, stream=stream)
+        if st != P.AX_OK:
+            raise RuntimeError(f"solve failed: {P.ax_status_string(st)} {info[:2]}")
+        return info
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        info = solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    launches0 = P.ax_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        info = solve()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = P.ax_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms)
+    unknowns_step = nr * nz * m
+    value = world * unknowns_step * args.steps / (ms_max / 1000.0)
+    iters = [i["iters"] for i in info]
+    outer = [i["outer"] for i in info]
+    rel = max(i["rel_res"] for i in info)
+
+    # ---- plain FP64 PCG on the same GPU (the comparator named by the metric) ----
+    plain = None
+    if args.plain_steps > 0 and method != P.AX_PCG_FP64:
+        u64 = torch.zeros_like(f)
+        solve(P.AX_PCG_FP64, f, u64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.plain_steps):
+            pinfo = solve(P.AX_PCG_FP64, f, u64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(e0.elapsed_time(e1)) / args.plain_steps
+        pval = world * unknowns_step / (pms / 1000.0)
+        diff = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+        plain = {"value": pval, "ms_per_step": pms, "iters_max": max(i["iters"] for i in pinfo),
+                 "rel_diff_to_chosen": diff}
+        del u64
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(f_host).pin_memory()
+        uh = torch.zeros_like(fh).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            P.ax_solve(op, fh, uh, m, TOL, 20000, method, P.AX_FLAG_HOST_BUFFERS, stream=stream)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        nbytes = f_host.nbytes
+        e2e = {"value": world * unknowns_step * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    # ---- per-kernel times with CUDA events (one profiled solve) ----
+    P.ax_set_option(op, "profile", 1)
+    solve()
+    torch.cuda.synchronize()
+    prof = {k: P.ax_profile_read(op, k) for k in P.PROFILE_KINDS}
+    P.ax_set_option(op, "profile", 0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = None
+    cand = {k: v for k, v in prof.items() if k in ALG_BYTES and v["launches"] > 0}
+    if cand:
+        top = max(cand, key=lambda k: cand[k]["ms"])
+        p = cand[top]
+        per_u, per_m = ALG_BYTES[top]
+        units_per_launch = p["units"] / p["launches"]
+        rhs_per_launch = units_per_launch / (nr * nz)
+        bytes_per_launch = units_per_launch * per_u + (nr * nz) * per_m
+        avg_s = p["ms"] / p["launches"] / 1000.0
+        achieved = bytes_per_launch / avg_s / 1e9
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            try:
+                tt = json.load(open(tpath)).get(f"{args.workload}:{args.method}:{top}")
+                traffic = tt
+            except (OSError, ValueError):
+                traffic = None
+        roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1e3,
+                "rhs_per_launch": rhs_per_launch}
+    kernel_ms = {k: {"ms": round(v["ms"], 3), "launches": int(v["launches"])} for k, v in prof.items()}
+
+    cpu = None
+    if pool is not None:
+        try:
+            cpu = cpu_baseline(args.workload, cores, pool)
+            cpu.pop("wall_s", None)
+        finally:
+            pool.close()
+            pool.join()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "nr": nr, "nz": nz, "rhs": m, "tol": TOL,
+                       "method": args.method, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (f is %d MB, working set > 2 GB)" % (f_host.nbytes >> 20)},
+            "iters": {"max": max(iters), "min": min(iters), "outer_max": max(outer)},
+            "max_rel_res": rel,
+            "plain_fp64": plain,
+            "vs_plain_fp64": (value / plain["value"]) if plain else None,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+            "kernel_ms_profiled_solve": kernel_ms, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    P.ax_destroy_operator(op)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

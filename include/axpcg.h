@@ -1,0 +1,184 @@
+/*
+ * axpcg.h — C ABI of the GB300 (sm_103a) solver for the axisymmetric elliptic
+ * equation of Terekhov, "High performance parallel algorithm for solving
+ * elliptic equations with non-separable variables" (arXiv 1002.3094):
+ *
+ *     (1/r) d_r(r kappa d_r u) + d_z(kappa d_z u) - q u = -f     on [0,lr] x [0,lz]
+ *
+ * (Section 2.1, Eq. main_eq), r kappa u_r = 0 on the axis r = 0, u = 0 on r = lr,
+ * and u = 0 on z = 0 and z = lz (the sine-transform variant of the paper's
+ * z-boundary; see the note on bc_z below).  Many right-hand sides share one
+ * operator (Section 1, Eq. main_problem).
+ *
+ * Discretisation (Section 2.1, Eqs. poisson_diff_2, scheme_op_r_z,
+ * diff_approx1): r_i = (i - 1/2) h_r, h_r = lr / (nr + 1/2), i = 1..nr, with
+ * u = 0 at r_{nr+1} = lr; faces rbar_i = i h_r.  z_k = k h_z, h_z = lz/(nz+1),
+ * k = 1..nz; faces zbar_k = (k + 1/2) h_z, k = 0..nz.  The discrete operator is
+ * the r-weighted conservative 5-point scheme, sign-reversed so that it is
+ * symmetric positive definite (Section 2.2, Eq. a-eq):
+ *   (A y)_{i,k} = [KR_i (y_{i,k}-y_{i+1,k}) + KR_{i-1} (y_{i,k}-y_{i-1,k})] / h_r^2
+ *               + [KZ_{i,k} (y_{i,k}-y_{i,k+1}) + KZ_{i,k-1} (y_{i,k}-y_{i,k-1})] / h_z^2
+ *               + W_{i,k} y_{i,k},
+ * KR_i = rbar_i kappa(rbar_i, z_k), KZ_{i,k} = r_i kappa(r_i, zbar_k),
+ * W = r_i q(r_i, z_k), right-hand side phi = r_i f(r_i, z_k), KR_0 = 0.
+ *
+ * Each iteration of the solver applies A once and the preconditioner
+ * B = kappa~ Delta - q~ (Eq. coeff2, with f~ = (min f + max f)/2 as in the
+ * footnote of Eq. diff_approx2) once, inverted by separation of variables
+ * (Section 4.2, Eqs. fft_phi, eq_trid): an orthonormal sine transform (DST-I)
+ * along z, one tridiagonal solve along r per z-mode l with the diagonal
+ * shifted by r_i (kappa~ lambda_l + q~), lambda_l = (4/h_z^2) sin^2(pi l /
+ * (2 (nz+1))), and the inverse transform.
+ *
+ * Conventions for every entry point:
+ *  - Grid functions are FP64, row-major [m][nr][nz] (z fastest), index
+ *    [m][i-1][k-1] for node (r_i, z_k), right-hand side m.
+ *  - Array pointers are CALLER-OWNED device memory unless a flag says host;
+ *    the library never frees them.  The operator owns its own workspace.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Work is queued on it; calls that must return host results
+ *    (ax_solve's info, ax_setup_operator) synchronise that stream.
+ *  - Every function returns an AX_* status; none aborts, traps or exits.
+ */
+#ifndef AXPCG_H
+#define AXPCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  AX_OK = 0,
+  AX_ERR_INVALID_ARG = 1,   /* null pointer, bad size, kappa <= 0, q < 0, non-finite input  */
+  AX_ERR_NO_CONVERGENCE = 2,/* max_iter reached; u holds the last iterate, info.rel_res set */
+  AX_ERR_BREAKDOWN = 3,     /* (p, Ap) <= 0 or a NaN scalar in the iteration                */
+  AX_ERR_TIMEOUT = 4,       /* a bounded device wait expired                                 */
+  AX_ERR_OOM = 5,           /* device allocation failed                                      */
+  AX_ERR_CUDA = 6,          /* any other CUDA runtime error                                  */
+  AX_ERR_UNSUPPORTED = 7    /* option not built (e.g. bc_z = 1)                              */
+};
+
+/* ---- methods and flags -------------------------------------------------- */
+enum {
+  AX_PCG_FP64 = 0,    /* plain method: PCG, every kernel in FP64 (Section 2.2, Section 4.2)      */
+  AX_CHEB_FP64 = 1,   /* three-layer Chebyshev iteration (Eq. main-scheme), FP64                  */
+  AX_PCG_MIXED = 2,   /* FP32 PCG inner solves inside FP64 iterative refinement                   */
+  AX_CHEB_MIXED = 3   /* FP32 Chebyshev inner solves inside FP64 iterative refinement             */
+};
+enum {
+  AX_FLAG_USE_GUESS = 1,    /* u holds an initial guess on entry (else the start is zero)   */
+  AX_FLAG_HOST_BUFFERS = 4  /* f and u are host pointers; copies are made inside the call   */
+};
+enum { AX_PREC_FP64 = 0, AX_PREC_FP32 = 1 };
+
+typedef struct {
+  int32_t nr, nz;   /* unknowns along r and z (>= 1)                                        */
+  double lr, lz;    /* domain [0, lr] x [0, lz]                                             */
+  int32_t bc_z;     /* 0: u = 0 at z = 0, lz (sine transform).  1 (the paper's Neumann z
+                       condition with the cosine transform of Eq. fft_phi) is not built:
+                       AX_ERR_UNSUPPORTED                                                   */
+} ax_grid;
+
+typedef struct ax_operator ax_operator; /* opaque, library-owned */
+
+typedef struct {
+  int32_t iters;          /* operator products A p (inner iterations for the mixed methods) */
+  int32_t outer;          /* FP64 refinement steps (mixed methods), else 0                  */
+  double rel_res;         /* final FP64 true residual ||phi - A u|| / ||phi||               */
+  int32_t guess_accepted; /* 1 if the initial guess was kept                                 */
+  int32_t status;         /* AX_* status of this right-hand side                              */
+} ax_solve_info;
+
+/* ---- operator set-up (Section 2.1, Eq. diff_approx1; Eq. coeff2) ---------
+ * kappa_r : [nr][nz]   kappa(rbar_i, z_k), i = 1..nr          device pointer
+ * kappa_z : [nr][nz+1] kappa(r_i, zbar_k), k = 0..nz          device pointer
+ * q       : [nr][nz]   q(r_i, z_k) >= 0                        device pointer
+ * Validates 0 < kappa, 0 <= q, all finite (Eq. elliptic_condition; q >= 0 as in
+ * Eq. main_problem) and the sizes; builds the scaled coefficients in FP64 and
+ * FP32, the per-mode tridiagonal factors (computed in FP64) and the transform
+ * tables.  Synchronises `stream`.  On success *out owns device memory that
+ * ax_destroy_operator frees.  Errors: AX_ERR_INVALID_ARG, AX_ERR_UNSUPPORTED,
+ * AX_ERR_OOM, AX_ERR_CUDA (nothing is leaked). */
+int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double *q,
+                      const ax_grid *g, void *stream, ax_operator **out);
+
+/* Frees everything the operator owns.  NULL is accepted. */
+int ax_destroy_operator(ax_operator *op);
+
+/* Preconditioner constants kappa~, q~ (Eq. coeff2) and the Chebyshev bounds
+ * gamma_1 <= (Ay,y)/(By,y) <= gamma_2 (Eq. energy_rel) of a set-up operator. */
+int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
+                     double *gamma1, double *gamma2);
+
+/* Tuning options of an operator (host-side settings, no device work):
+ *   "profile"        1: per-launch CUDA-event profiler on (see ax_profile_read)
+ *   "inner_tol"      relative residual reduction of each FP32 inner solve of the
+ *                    mixed methods (0 < v < 1, default 1e-4)
+ *   "inner_max_iter" cap on the iterations of one inner solve (default 400)
+ *   "graph_iters"    iterations captured per CUDA-graph replay (1..256, default 8)
+ *   "max_outer"      cap on FP64 refinement steps (default 30)
+ * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */
+int ax_set_option(ax_operator *op, const char *name, double value);
+
+/* ---- solve (Section 2.2, Eq. main-scheme and CG; stop rule of Section 4.2) --
+ * f : [m][nr][nz] physical f (the library forms phi = r_i f), device pointer
+ *     (host pointer with AX_FLAG_HOST_BUFFERS)
+ * u : [m][nr][nz] out: solution; in: guess if AX_FLAG_USE_GUESS
+ * Each right-hand side stops when its FP64 true residual satisfies
+ * ||phi - A u||_2 <= tol ||phi||_2, or fails after max_iter iterations.
+ * info : host array [m] (may be NULL).  Returns the worst per-RHS status. */
+int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
+             int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
+
+/* ---- single steps of the hot path, for testing each kernel -----------------
+ * All take FP64 device arrays [m][nr][nz]; precision selects the kernel
+ * (AX_PREC_FP64 or AX_PREC_FP32 — the FP32 kernels round the input to FP32
+ * first and widen the output).  in and out must not overlap. */
+
+/* out = A in (the 5-point stencil of Eqs. poisson_diff_2, scheme_op_r_z). */
+int ax_apply_operator(ax_operator *op, const double *in, double *out, int32_t m,
+                      int32_t precision, void *stream);
+
+/* out[row] = S in[row] for every one of `rows` rows of length nz, where
+ * S[l][k] = sqrt(2/(nz+1)) sin(pi k l/(nz+1)) (orthonormal DST-I, the sine
+ * counterpart of Eq. fft_phi; S = S^T = S^-1). */
+int ax_apply_dst(ax_operator *op, const double *in, double *out, int32_t rows,
+                 int32_t precision, void *stream);
+
+/* For each right-hand side and each mode column l, solve T_l y[:, l] = in[:, l]
+ * along r, T_l = Lr(kappa~) + diag(r_i (kappa~ lambda_l + q~)) (Eq. eq_trid). */
+int ax_apply_mode_solve(ax_operator *op, const double *in, double *out, int32_t m,
+                        int32_t precision, void *stream);
+
+/* out = B^-1 in (sine transform, mode solves, inverse transform). */
+int ax_apply_preconditioner(ax_operator *op, const double *in, double *out, int32_t m,
+                            int32_t precision, void *stream);
+
+/* ---- diagnostics ----------------------------------------------------------
+ * Number of CUDA kernels this library has issued in this process (direct
+ * launches plus the kernel nodes of replayed graphs). */
+int64_t ax_kernel_launches(void);
+
+/* Per-launch profiler.  ax_set_option(op, "profile", 1) turns it on (and
+ * clears it); while it is on, solves launch iterations one by one (no graph)
+ * and bracket each kernel with CUDA events on the solve's stream.  kind:
+ * 0 stencil (p update + A p), 1 forward sine transform (fused x, r update),
+ * 2 mode solves, 3 inverse sine transform (fused (r, z)), 4 scalar kernels,
+ * 5 FP64 outer residual, 6 other.  Returns the summed event time in ms, the
+ * number of launches and the grid unknowns they processed (right-hand sides
+ * active at launch x nr x nz). */
+int ax_profile_read(ax_operator *op, int32_t kind, double *ms, double *launches, double *units);
+
+/* Human-readable name of a status code (static storage). */
+const char *ax_status_string(int status);
+
+/* Library version string (static storage). */
+const char *ax_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AXPCG_H */

@@ -1,0 +1,202 @@
+"""GB300-native Laplace-preconditioned CG / Chebyshev solver for the
+axisymmetric elliptic equation of arXiv 1002.3094 (Terekhov).
+
+A thin ctypes binding of ``libaxpcg.so`` (``include/axpcg.h``): the functions
+below carry the C ABI's names and only marshal arguments; every step of the
+solve runs in the library's CUDA kernels.  There is no CPU fallback: loading
+fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB, build  # noqa: F401
+
+AX_OK = 0
+AX_ERR_INVALID_ARG = 1
+AX_ERR_NO_CONVERGENCE = 2
+AX_ERR_BREAKDOWN = 3
+AX_ERR_TIMEOUT = 4
+AX_ERR_OOM = 5
+AX_ERR_CUDA = 6
+AX_ERR_UNSUPPORTED = 7
+
+AX_PCG_FP64 = 0
+AX_CHEB_FP64 = 1
+AX_PCG_MIXED = 2
+AX_CHEB_MIXED = 3
+
+AX_FLAG_USE_GUESS = 1
+AX_FLAG_HOST_BUFFERS = 4
+
+AX_PREC_FP64 = 0
+AX_PREC_FP32 = 1
+
+METHODS = {"pcg64": AX_PCG_FP64, "cheb64": AX_CHEB_FP64, "pcg_mixed": AX_PCG_MIXED,
+           "cheb_mixed": AX_CHEB_MIXED}
+
+EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_set_option", "ax_solve",
+            "ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
+            "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read")
+
+PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
+                 "outer_residual": 5, "other": 6}
+
+
+class AxGrid(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("lz", ctypes.c_double), ("bc_z", ctypes.c_int32)]
+
+
+class AxSolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("guess_accepted", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {ax_status_string(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Loads libaxpcg.so (built in-tree by ``build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libaxpcg is not built ({path}); run paper_1002_3094_gb300.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.ax_setup_operator.argtypes = [vp, vp, vp, ctypes.POINTER(AxGrid), vp, ctypes.POINTER(vp)]
+    lib.ax_destroy_operator.argtypes = [vp]
+    lib.ax_operator_info.argtypes = [vp] + [ctypes.POINTER(dbl)] * 4
+    lib.ax_set_option.argtypes = [vp, ctypes.c_char_p, dbl]
+    lib.ax_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
+    for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner"):
+        getattr(lib, name).argtypes = [vp, vp, vp, i32, i32, vp]
+    lib.ax_status_string.argtypes = [ctypes.c_int]
+    lib.ax_status_string.restype = ctypes.c_char_p
+    lib.ax_version.restype = ctypes.c_char_p
+    lib.ax_kernel_launches.argtypes = []
+    lib.ax_kernel_launches.restype = ctypes.c_int64
+    lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
+    for name in EXPORTED:
+        if name not in ("ax_status_string", "ax_version", "ax_kernel_launches"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int:
+    """Device (or host) address of a torch tensor, numpy array or int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, what: str) -> int:
+    if status != AX_OK:
+        raise AxError(status, what)
+    return status
+
+
+def ax_status_string(status: int) -> str:
+    return load_library().ax_status_string(status).decode()
+
+
+def ax_version() -> str:
+    return load_library().ax_version().decode()
+
+
+def ax_setup_operator(kappa_r, kappa_z, q, nr: int, nz: int, lr: float = 1.0, lz: float = 1.0,
+                      bc_z: int = 0, stream=None) -> int:
+    """Returns an opaque operator handle (int).  kappa_r, kappa_z, q: FP64
+    device tensors [nr][nz], [nr][nz+1], [nr][nz]."""
+    lib = load_library()
+    g = AxGrid(nr, nz, lr, lz, bc_z)
+    out = ctypes.c_void_p()
+    _check(lib.ax_setup_operator(_ptr(kappa_r), _ptr(kappa_z), _ptr(q), ctypes.byref(g), _stream(stream),
+                                 ctypes.byref(out)), "ax_setup_operator")
+    return out.value
+
+
+def ax_destroy_operator(op: int) -> None:
+    load_library().ax_destroy_operator(op)
+
+
+def ax_operator_info(op: int):
+    vals = [ctypes.c_double() for _ in range(4)]
+    _check(load_library().ax_operator_info(op, *[ctypes.byref(v) for v in vals]), "ax_operator_info")
+    return tuple(v.value for v in vals)
+
+
+def ax_set_option(op: int, name: str, value: float) -> None:
+    _check(load_library().ax_set_option(op, name.encode(), float(value)), f"ax_set_option({name})")
+
+
+def ax_solve(op: int, f, u, m: int, tol: float, max_iter: int = 10000, method: int = AX_PCG_FP64,
+             flags: int = 0, stream=None, raise_on_error: bool = True):
+    """Solves for m right-hand sides; returns (status, [info dicts])."""
+    infos = (AxSolveInfo * m)()
+    st = load_library().ax_solve(op, _ptr(f), _ptr(u), m, tol, max_iter, method, flags, infos,
+                                 _stream(stream) if not (flags & AX_FLAG_HOST_BUFFERS) or stream else
+                                 _stream(None))
+    if raise_on_error and st not in (AX_OK, AX_ERR_NO_CONVERGENCE):
+        raise AxError(st, "ax_solve")
+    return st, [i.as_dict() for i in infos]
+
+
+def _apply(name: str, op: int, x, y, count: int, precision: int, stream=None) -> None:
+    _check(getattr(load_library(), name)(op, _ptr(x), _ptr(y), count, precision, _stream(stream)), name)
+
+
+def ax_apply_operator(op, x, y, m, precision=AX_PREC_FP64, stream=None):
+    _apply("ax_apply_operator", op, x, y, m, precision, stream)
+
+
+def ax_apply_dst(op, x, y, rows, precision=AX_PREC_FP64, stream=None):
+    _apply("ax_apply_dst", op, x, y, rows, precision, stream)
+
+
+def ax_apply_mode_solve(op, x, y, m, precision=AX_PREC_FP64, stream=None):
+    _apply("ax_apply_mode_solve", op, x, y, m, precision, stream)
+
+
+def ax_apply_preconditioner(op, x, y, m, precision=AX_PREC_FP64, stream=None):
+    _apply("ax_apply_preconditioner", op, x, y, m, precision, stream)
+
+
+def ax_kernel_launches() -> int:
+    return int(load_library().ax_kernel_launches())
+
+
+def ax_profile_read(op: int, kind) -> dict:
+    """{'ms', 'launches', 'units'} of one kernel class (name or number)."""
+    k = PROFILE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    vals = [ctypes.c_double() for _ in range(3)]
+    _check(load_library().ax_profile_read(op, k, *[ctypes.byref(v) for v in vals]), "ax_profile_read")
+    return {"ms": vals[0].value, "launches": vals[1].value, "units": vals[2].value}

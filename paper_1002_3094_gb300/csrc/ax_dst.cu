@@ -1,0 +1,372 @@
+// Orthonormal sine transform (DST-I) along z of every r-row, the
+// Dirichlet-z counterpart of the paper's separation of variables (Section 4.2,
+// Eq. fft_phi, computed there with a sequential FFT):
+//
+//     out[l] = sqrt(2/L) * sum_{k=1}^{L-1} in[k] sin(pi k l / L),   L = nz + 1.
+//
+// Method: the odd extension x of a row (x_0 = x_L = 0, x_k = in[k],
+// x_{2L-k} = -in[k]) has the DFT X_l = -2i sum_k in[k] sin(pi k l / L).  The
+// length-2L real sequence is packed into L complex numbers z_j = x_{2j} +
+// i x_{2j+1}, transformed by a mixed-radix Stockham FFT of length L in shared
+// memory, and split into X_l with the standard real-FFT post-processing; only
+// Im X_l is kept.  Radices 2, 3, 4, 5, 8 run as unrolled register butterflies;
+// any other odd prime radix R runs as a paired direct DFT (outputs o and R - o
+// share the sums and differences of inputs r and R - r), eight output pairs
+// per thread.
+//
+// One CTA transforms `rpb` rows of one right-hand side (blockIdx.x = RHS).
+// The fused variants update the CG iterate and residual while loading the
+// rows (forward) or form the (r, z) partial while storing (inverse).
+#include <cmath>
+#include "ax_common.cuh"
+
+namespace ax {
+
+namespace {
+
+template <typename T> struct CplxT;
+template <> struct CplxT<float> { using type = float2; };
+template <> struct CplxT<double> { using type = double2; };
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// a * exp(-i theta) with (c, s) = (cos theta, sin theta)
+template <typename C, typename T>
+__device__ __forceinline__ C crot(C a, T c, T s) {
+  C r;
+  r.x = fma(a.x, c, a.y * s);
+  r.y = fma(a.y, c, -a.x * s);
+  return r;
+}
+// -i * a
+template <typename C>
+__device__ __forceinline__ C cmi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+
+template <typename T, int R> struct Butterfly;
+
+template <typename T> struct Butterfly<T, 2> {
+  template <typename C> __device__ __forceinline__ static void run(C *v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <typename T> struct Butterfly<T, 4> {
+  template <typename C> __device__ __forceinline__ static void run(C *v) {
+    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    C t2 = cadd(v[1], v[3]), t3 = cmi(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <typename T> struct Butterfly<T, 8> {
+  template <typename C> __device__ __forceinline__ static void run(C *v) {
+    const T h = T(0.70710678118654752440);
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    Butterfly<T, 4>::run(e);
+    Butterfly<T, 4>::run(o);
+    C w1, w2, w3;
+    w1.x = (o[1].x + o[1].y) * h; w1.y = (o[1].y - o[1].x) * h;
+    w2 = cmi(o[2]);
+    w3.x = (o[3].y - o[3].x) * h; w3.y = -(o[3].x + o[3].y) * h;
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], w1);   v[5] = csub(e[1], w1);
+    v[2] = cadd(e[2], w2);   v[6] = csub(e[2], w2);
+    v[3] = cadd(e[3], w3);   v[7] = csub(e[3], w3);
+  }
+};
+
+template <typename T> struct Butterfly<T, 3> {
+  template <typename C> __device__ __forceinline__ static void run(C *v) {
+    const T h = T(0.86602540378443864676);  // sin(2 pi / 3)
+    C s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    C m0;
+    m0.x = v[0].x - T(0.5) * s.x;
+    m0.y = v[0].y - T(0.5) * s.y;
+    v[0] = cadd(v[0], s);
+    v[1].x = m0.x + h * d.y; v[1].y = m0.y - h * d.x;
+    v[2].x = m0.x - h * d.y; v[2].y = m0.y + h * d.x;
+  }
+};
+
+template <typename T> struct Butterfly<T, 5> {
+  template <typename C> __device__ __forceinline__ static void run(C *v) {
+    const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);  // cos 2pi/5, cos 4pi/5
+    const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);   // sin 2pi/5, sin 4pi/5
+    C s_1 = cadd(v[1], v[4]), d_1 = csub(v[1], v[4]);
+    C s_2 = cadd(v[2], v[3]), d_2 = csub(v[2], v[3]);
+    C x0 = v[0];
+    C a1, b1, a2, b2;
+    a1.x = x0.x + c1 * s_1.x + c2 * s_2.x;  a1.y = x0.y + c1 * s_1.y + c2 * s_2.y;
+    b1.x = s1 * d_1.x + s2 * d_2.x;         b1.y = s1 * d_1.y + s2 * d_2.y;
+    a2.x = x0.x + c2 * s_1.x + c1 * s_2.x;  a2.y = x0.y + c2 * s_1.y + c1 * s_2.y;
+    b2.x = s2 * d_1.x - s1 * d_2.x;         b2.y = s2 * d_1.y - s1 * d_2.y;
+    v[0] = cadd(x0, cadd(s_1, s_2));
+    v[1].x = a1.x + b1.y; v[1].y = a1.y - b1.x;
+    v[4].x = a1.x - b1.y; v[4].y = a1.y + b1.x;
+    v[2].x = a2.x + b2.y; v[2].y = a2.y - b2.x;
+    v[3].x = a2.x - b2.y; v[3].y = a2.y + b2.x;
+  }
+};
+
+// One Stockham stage with a small radix: butterfly j of row rr reads
+// src[j + r T] (T = L / R), applies the twiddles exp(-2 pi i k r / (Ns R)),
+// k = j mod Ns, and writes dst[(j / Ns) Ns R + k + o Ns].
+template <typename T, int R, typename C>
+__device__ __forceinline__ void small_stage(const C *__restrict__ src, C *__restrict__ dst, int nrows,
+                                            int L, int Ns, const T *__restrict__ TW) {
+  const int Tn = L / R;
+  const int tstep = L / (Ns * R);
+  for (int it = threadIdx.x; it < nrows * Tn; it += blockDim.x) {
+    const int rr = it / Tn;
+    const int j = it - rr * Tn;
+    const int k = j % Ns;
+    const C *s = src + rr * L + j;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[r * Tn];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const int idx = (int)(((long long)k * r * tstep) % L);
+        v[r] = crot(v[r], __ldg(TW + 2 * idx), __ldg(TW + 2 * idx + 1));
+      }
+    }
+    Butterfly<T, R>::run(v);
+    C *d = dst + rr * L + (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int o = 0; o < R; ++o) d[o * Ns] = v[o];
+  }
+}
+
+// Generic odd radix R (prime > 5): paired direct DFT.  Twiddles are applied in
+// place first (skipped on the first stage, where Ns = 1).
+template <typename T, typename C>
+__device__ __forceinline__ void generic_stage(C *__restrict__ src, C *__restrict__ dst, int nrows, int L,
+                                              int Ns, int R, const T *__restrict__ TW) {
+  constexpr int G = 8;
+  const int Tn = L / R;
+  if (Ns > 1) {
+    const int tstep = L / (Ns * R);
+    for (int e = threadIdx.x; e < nrows * L; e += blockDim.x) {
+      const int rr = e / L;
+      const int idx = e - rr * L;
+      const int r = idx / Tn;
+      const int j = idx - r * Tn;
+      if (r > 0) {
+        const int k = j % Ns;
+        const int ti = (int)(((long long)k * r * tstep) % L);
+        src[e] = crot(src[e], __ldg(TW + 2 * ti), __ldg(TW + 2 * ti + 1));
+      }
+    }
+    __syncthreads();
+  }
+  const int H = (R - 1) / 2;
+  const int NB = (H + G - 1) / G;
+  const int cstep = L / R;
+  for (int it = threadIdx.x; it < nrows * NB * Tn; it += blockDim.x) {
+    const int rr = it / (NB * Tn);
+    const int rem = it - rr * NB * Tn;
+    const int b = rem / Tn;
+    const int j = rem - b * Tn;
+    const C *col = src + rr * L + j;
+    const C t0 = col[0];
+    C A[G], B[G];
+    int idx[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      A[g].x = A[g].y = B[g].x = B[g].y = T(0);
+      idx[g] = 0;
+    }
+    C dc;
+    dc.x = dc.y = T(0);
+    const int o0 = 1 + b * G;
+    for (int r = 1; r <= H; ++r) {
+      const C tr = col[r * Tn], tm = col[(R - r) * Tn];
+      const C s = cadd(tr, tm), d = csub(tr, tm);
+      dc = cadd(dc, s);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int o = o0 + g;
+        int v = idx[g] + o;
+        v = (v >= R) ? v - R : v;
+        idx[g] = v;
+        const T c = __ldg(TW + 2 * v * cstep), sn = __ldg(TW + 2 * v * cstep + 1);
+        A[g].x = fma(s.x, c, A[g].x);
+        A[g].y = fma(s.y, c, A[g].y);
+        B[g].x = fma(d.x, sn, B[g].x);
+        B[g].y = fma(d.y, sn, B[g].y);
+      }
+    }
+    C *out = dst + rr * L + (j / Ns) * Ns * R + (j % Ns);
+    if (b == 0) out[0] = cadd(t0, dc);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int o = o0 + g;
+      if (o <= H) {
+        C xo, xm;
+        xo.x = t0.x + A[g].x + B[g].y; xo.y = t0.y + A[g].y - B[g].x;
+        xm.x = t0.x + A[g].x - B[g].y; xm.y = t0.y + A[g].y + B[g].x;
+        out[o * Ns] = xo;
+        out[(R - o) * Ns] = xm;
+      }
+    }
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
+  using C = typename CplxT<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[8];
+  const int m = blockIdx.x;
+  if (!rhs_selected(a.st, a.mask, m)) return;
+  const int L = a.plan.L, n = a.n;
+  const int row0 = blockIdx.y * a.rpb;
+  const int nrows = min(a.rpb, a.rows - row0);
+  C *buf0 = reinterpret_cast<C *>(smem_raw);
+  C *buf1 = buf0 + a.rpb * L;
+  T *pk = reinterpret_cast<T *>(buf0);  // packed real view: pk[rr * 2L + idx] = x_idx
+  const size_t base = (size_t)m * (size_t)a.field + (size_t)row0 * a.pitch;
+  T alpha = T(0);
+  const T *p = nullptr;
+  if (MODE == kDstPcgForward) {
+    alpha = (T)a.st[m].alpha;
+    p = (a.st[m].iters & 1) ? a.pa : a.pb;
+  }
+  T acc = T(0);
+
+  // ---- load rows into the packed odd extension ----
+  for (int rr = 0; rr < nrows; ++rr) {
+    const size_t rb = base + (size_t)rr * a.pitch;
+    T *px = pk + rr * 2 * L;
+    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
+      const size_t e = rb + kk;
+      T v;
+      if (MODE == kDstPcgForward) {
+        const T xv = fma(alpha, p[e], a.x[e]);
+        const T rv = fma(-alpha, a.in[e], a.r[e]);
+        a.x[e] = xv;
+        a.r[e] = rv;
+        acc = fma(rv, rv, acc);
+        v = rv;
+      } else {
+        v = a.in[e];
+      }
+      px[kk + 1] = v;
+      px[2 * L - kk - 1] = -v;
+    }
+    if (threadIdx.x == 0) {
+      px[0] = T(0);
+      px[L] = T(0);
+    }
+  }
+
+  // ---- complex FFT of length L (Stockham, ping-pong) ----
+  C *src = buf0, *dst = buf1;
+  int Ns = 1;
+  for (int s = 0; s < a.plan.nstages; ++s) {
+    const int R = a.plan.radix[s];
+    __syncthreads();
+    switch (R) {
+      case 2: small_stage<T, 2>(src, dst, nrows, L, Ns, a.TW); break;
+      case 3: small_stage<T, 3>(src, dst, nrows, L, Ns, a.TW); break;
+      case 4: small_stage<T, 4>(src, dst, nrows, L, Ns, a.TW); break;
+      case 5: small_stage<T, 5>(src, dst, nrows, L, Ns, a.TW); break;
+      case 8: small_stage<T, 8>(src, dst, nrows, L, Ns, a.TW); break;
+      default: generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+    }
+    C *t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+  __syncthreads();
+
+  // ---- split into the sine coefficients and store ----
+  const T sc = (T)a.scale;
+  T cheb_a = T(0), tau = T(0);
+  if (MODE == kDstChebInverse) {
+    cheb_a = (T)a.st[m].cheb_a;
+    tau = (T)a.tau;
+  }
+  for (int rr = 0; rr < nrows; ++rr) {
+    const size_t rb = base + (size_t)rr * a.pitch;
+    const C *Z = src + rr * L;
+    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
+      const int k = kk + 1;
+      const C zk = Z[k], zm = Z[L - k];
+      const T c = __ldg(a.HW + 2 * k), s = __ldg(a.HW + 2 * k + 1);
+      T v = (zm.y - zk.y) + c * (zk.x - zm.x) + s * (zk.y + zm.y);
+      v *= sc;
+      const size_t e = rb + kk;
+      if (MODE == kDstPlain || MODE == kDstPcgForward) {
+        a.out[e] = v;
+      } else if (MODE == kDstPcgInverse) {
+        a.out[e] = v;
+        acc = fma(a.r[e], v, acc);
+      } else {  // Chebyshev: y_{k+1} = a (y_k - tau B^-1 res) + (1 - a) y_{k-1}
+        const T yb = fma(-tau, v, a.y[e]);
+        a.yprev[e] = fma(cheb_a, yb - a.yprev[e], a.yprev[e]);
+      }
+    }
+  }
+  if (MODE == kDstPcgForward || MODE == kDstPcgInverse) {
+    const double s = block_sum((double)acc, red);
+    if (threadIdx.x == 0) a.partial[(size_t)m * kPartialStride + blockIdx.y] = s;
+  }
+}
+
+constexpr size_t kDstSmemBudget = 67584;
+
+}  // namespace
+
+int dst_rows_per_block(int L, int elem_bytes) {
+  const size_t per_row = 2ull * L * 2 * elem_bytes;
+  size_t r = kDstSmemBudget / per_row;
+  if (r < 1) r = 1;
+  if (r > 16) r = 16;
+  return (int)r;
+}
+
+size_t dst_smem_bytes(int L, int elem_bytes) {
+  return (size_t)dst_rows_per_block(L, elem_bytes) * 2ull * L * 2 * elem_bytes;
+}
+
+template <typename T>
+void launch_dst(int mode, const DstArgs<T> &a_in, cudaStream_t s) {
+  DstArgs<T> a = a_in;
+  a.rpb = dst_rows_per_block(a.plan.L, (int)sizeof(T));
+  const size_t smem = dst_smem_bytes(a.plan.L, (int)sizeof(T));
+  dim3 grid(a.m, (a.rows + a.rpb - 1) / a.rpb);
+  dim3 block(256);
+  note_launch();
+  switch (mode) {
+    case kDstPlain:
+      cudaFuncSetAttribute(dst_kernel<T, kDstPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      dst_kernel<T, kDstPlain><<<grid, block, smem, s>>>(a);
+      break;
+    case kDstPcgForward:
+      cudaFuncSetAttribute(dst_kernel<T, kDstPcgForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      dst_kernel<T, kDstPcgForward><<<grid, block, smem, s>>>(a);
+      break;
+    case kDstPcgInverse:
+      cudaFuncSetAttribute(dst_kernel<T, kDstPcgInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      dst_kernel<T, kDstPcgInverse><<<grid, block, smem, s>>>(a);
+      break;
+    default:
+      cudaFuncSetAttribute(dst_kernel<T, kDstChebInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      dst_kernel<T, kDstChebInverse><<<grid, block, smem, s>>>(a);
+      break;
+  }
+}
+
+template void launch_dst<float>(int, const DstArgs<float> &, cudaStream_t);
+template void launch_dst<double>(int, const DstArgs<double> &, cudaStream_t);
+
+}  // namespace ax

@@ -1,0 +1,164 @@
+// Internal declarations shared by the CUDA translation units of libaxpcg.
+//
+// Device data layout (all grid functions): [m][nr][pitch], z fastest, pitch =
+// nz rounded up to a multiple of 32 elements, so every row starts on a
+// 128-byte (FP32) or 256-byte (FP64) boundary.  Padding columns are kept zero
+// and never read as data.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <cstddef>
+
+#include "../../include/axpcg.h"
+
+namespace ax {
+
+constexpr int kMaxStages = 24;
+
+// Radix plan of the complex FFT of length L = nz + 1 used by the sine
+// transform.  Odd radices larger than 8 use the generic paired kernel.
+struct FftPlan {
+  int L = 0;
+  int nstages = 0;
+  int radix[kMaxStages] = {0};
+};
+
+// Per-precision device tables of one operator.
+template <typename T>
+struct Coef {
+  T *CR = nullptr;   // [nr][pitch]   KR_i / h_r^2   (face rbar_i, between r-nodes i and i+1)
+  T *CZ = nullptr;   // [nr][pitchz]  KZ_{i,c} / h_z^2, c = 0..nz (face zbar_c)
+  T *W = nullptr;    // [nr][pitch]   r_i q
+  T *IP = nullptr;   // [nr][pitch]   1 / delta_i(l): inverse Thomas pivots of T_l (column l)
+  T *E = nullptr;    // [nr]          off-diagonal of T_l between rows i and i+1 (0 at i = nr)
+  T *R = nullptr;    // [nr]          r_i
+  T *TW = nullptr;   // [2 L]         (cos, sin)(2 pi j / L), j < L
+  T *HW = nullptr;   // [2 L]         (cos, sin)(pi j / L),   j < L
+};
+
+// Scalar state of one right-hand side during an iteration.  Lives in device
+// memory; written only by the scalar kernels.
+struct RhsState {
+  double rho;      // (r, z)
+  double alpha;    // step length
+  double beta;     // direction update
+  double rr;       // ||r||^2 of the recursive residual
+  double bb;       // reference norm^2 (||phi||^2, or ||r_outer||^2 for inner solves)
+  double thresh2;  // stop when rr <= thresh2
+  double cheb_a;   // Chebyshev alpha_k
+  double tmp;
+  int state;       // kActive / kCheck / kDone / kFailed
+  int iters;
+  int status;      // AX_* status
+  int max_iter;
+};
+
+enum { kActive = 0, kCheck = 1, kDone = 2, kFailed = 3, kIdle = 4 };
+
+// Launch geometry shared by producers and consumers of per-CTA partial sums.
+constexpr int kStencilRows = 16;     // rows per stencil CTA
+constexpr int kStencilWarps = 8;     // warps per stencil CTA (along z)
+constexpr int kPartialStride = 8192; // max partials per RHS per kind
+constexpr int kMaxNr = 8192, kMaxNz = 7000;
+
+struct Workspace;
+
+// Host-side count of kernels issued (direct launches, plus the kernel nodes of
+// every replayed CUDA graph).  Launchers call note_launch(); while a graph is
+// being captured nothing is counted (the replay counts the nodes).
+void note_launch();
+
+// Kernel classes of the per-launch profiler (ax_profile_read).
+enum { kProfStencil = 0, kProfDstFwd = 1, kProfTridiag = 2, kProfDstInv = 3, kProfScalar = 4,
+       kProfOuter = 5, kProfOther = 6, kProfKinds = 7 };
+
+}  // namespace ax
+
+struct ax_operator {
+  int nr = 0, nz = 0, pitch = 0, pitchz = 0;
+  double lr = 1, lz = 1, hr = 0, hz = 0;
+  double kappa_t = 0, q_t = 0, gamma1 = 0, gamma2 = 0;
+  int device = 0;
+  ax::FftPlan plan;
+  ax::Coef<double> c64;
+  ax::Coef<float> c32;
+  ax::Workspace *ws = nullptr;
+};
+
+namespace ax {
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (implemented in the .cu files).  `mask` selects the right-
+// hand sides whose RhsState.state equals it; mask < 0 runs every RHS.
+// ---------------------------------------------------------------------------
+
+// Stencil modes
+enum { kStencilApply = 0, kStencilPcg = 1, kStencilResidual = 2, kStencilCheb = 3 };
+
+template <typename T>
+struct StencilArgs {
+  const T *CR, *CZ, *W;
+  int nr, nz, pitch, pitchz;
+  long long field;       // elements per RHS (nr * pitch)
+  int m;
+  const T *in;           // Apply: y.  Pcg: z.  Residual: x.  Cheb: y
+  T *pa, *pb;            // Pcg: the two search-direction buffers; an RHS with an even
+                         // iteration count reads pa and writes pb, an odd one the reverse
+  T *out;                // Apply: A y.  Pcg: q = A p_new.  Cheb: res = A y - phi
+  const T *phi;          // Residual, Cheb: phi
+  float *out32;          // Residual: phi - A x rounded to FP32 (may be null)
+  T *out_res;            // Residual: phi - A x (may be null)
+  const RhsState *st;    // per RHS state (Pcg reads beta)
+  int mask;
+  double *partial;       // [m][kPartialStride] per-CTA sums: Pcg (p,q); Residual, Cheb ||res||^2
+};
+
+template <typename T>
+void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s);
+int stencil_blocks_per_rhs(int nr, int nz, int vec);
+
+// Sine-transform modes
+enum { kDstPlain = 0, kDstPcgForward = 1, kDstPcgInverse = 2, kDstChebInverse = 3 };
+
+template <typename T>
+struct DstArgs {
+  const T *TW, *HW;
+  FftPlan plan;
+  int n, rows, pitch;      // n = nz; rows per RHS
+  long long field;         // elements per RHS
+  int m;
+  const T *in;             // Plain: input rows.  PcgForward: q.  PcgInverse/Cheb: yhat rows
+  T *out;                  // Plain: output rows.  PcgForward: rhat.  PcgInverse: z (in place ok)
+  T *x, *r;                // PcgForward: x += alpha p, r -= alpha q.  PcgInverse: r for (r,z)
+  T *pa, *pb;              // PcgForward: p is pb for an even iteration count, pa for odd
+  T *y, *yprev;            // Cheb: y_{k+1} = a (y - tau res^) + (1 - a) y_{k-1}, written to yprev
+  double tau;             // Cheb: constant step tau_0
+  double scale;           // 0.5 / sqrt(2 L): orthonormal scaling folded with the real-FFT split
+  int rpb;                // rows per CTA (set by the launcher)
+  const RhsState *st;
+  int mask;
+  double *partial;        // [m][kPartialStride]: PcgForward ||r||^2, PcgInverse (r, z)
+};
+
+template <typename T>
+void launch_dst(int mode, const DstArgs<T> &a, cudaStream_t s);
+int dst_rows_per_block(int L, int elem_bytes);
+size_t dst_smem_bytes(int L, int elem_bytes);
+
+template <typename T>
+struct TriArgs {
+  const T *IP, *E;
+  int nr, nz, pitch;
+  long long field;
+  int m;
+  const T *in;
+  T *out;                  // may alias in
+  const RhsState *st;
+  int mask;
+};
+
+template <typename T>
+void launch_tridiag(const TriArgs<T> &a, cudaStream_t s);
+
+}  // namespace ax

@@ -1,0 +1,1311 @@
+// Operator set-up, iteration drivers and the C ABI of libaxpcg.
+//
+// Iterations (Section 2.2): preconditioned conjugate gradients with the
+// Laplace preconditioner B of Eq. coeff2 (A B^-1 A is self-adjoint, so CG
+// applies), and the implicit three-layer Chebyshev scheme of Eq. main-scheme.
+// The stop rule is the paper's (Section 4.2): the true residual
+// ||A y - phi|| / ||phi|| <= tol.
+//
+// GPU organisation.  Scalars (alpha, beta, rho, norms) live on the device in
+// one RhsState per right-hand side and are produced by tiny "scalar" kernels
+// that reduce per-CTA FP64 partial sums in a fixed order (deterministic, no
+// atomics).  Every iteration kernel reads its RHS's state and returns at once
+// unless the state matches the kernel's mask, so converged right-hand sides
+// stop costing bandwidth while the others continue.  A block of iterations is
+// captured once into a CUDA graph and replayed; the host reads the states
+// between replays.
+//
+// Mixed precision (AX_PCG_MIXED / AX_CHEB_MIXED): iterative refinement.  The
+// outer loop forms the true residual r = phi - A x in FP64 (FP64 stencil,
+// FP64 coefficients), the inner loop solves A d = r in FP32 to a relative
+// tolerance eta_in (or a fixed number of steps), and x += d in FP64.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "ax_common.cuh"
+
+namespace ax {
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  int key = -1;
+  size_t nodes = 0;
+};
+
+struct ProfEvent {
+  int kind;
+  cudaEvent_t a, b;
+  double units;
+};
+
+struct Workspace {
+  int m64 = 0, m32 = 0, mbase = 0;
+  // FP64 vectors [m][nr][pitch]
+  double *phi64 = nullptr, *x64 = nullptr;
+  double *r64 = nullptr, *pa64 = nullptr, *pb64 = nullptr, *q64 = nullptr, *z64 = nullptr, *y64prev = nullptr;
+  // FP32 vectors
+  float *x32 = nullptr, *r32 = nullptr, *pa32 = nullptr, *pb32 = nullptr, *q32 = nullptr, *z32 = nullptr,
+        *y32prev = nullptr;
+  // partial sums [4][m][kPartialStride]
+  double *part = nullptr;
+  RhsState *st = nullptr, *st_outer = nullptr;
+  RhsState *h_st = nullptr;   // pinned host mirror [2 m]
+  // dense FP64 staging for host buffers and single-step entry points
+  double *stage_a = nullptr, *stage_b = nullptr;
+  size_t stage_elems = 0;
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaStream_t cap = nullptr;
+  GraphCache g64, g32, gc64, gc32;
+  // options
+  double inner_tol = 1e-4;
+  int inner_max = 400;
+  int graph_iters = 8;
+  int max_outer = 30;
+  // per-launch profiler (off by default; graphs are not used while it is on)
+  bool profile = false;
+  std::vector<ProfEvent> prof_events;
+  double prof_ms[kProfKinds] = {0}, prof_launches[kProfKinds] = {0}, prof_units[kProfKinds] = {0};
+};
+
+static long long g_launches = 0;
+static thread_local bool g_capturing = false;
+void note_launch() {
+  if (!g_capturing) __atomic_add_fetch(&g_launches, 1, __ATOMIC_RELAXED);
+}
+
+namespace {
+
+int status_from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return AX_OK;
+  if (e == cudaErrorMemoryAllocation) return AX_ERR_OOM;
+  return AX_ERR_CUDA;
+}
+
+#define AX_TRY(expr)                                  \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return status_from_cuda(_e); \
+  } while (0)
+
+#define AX_CHECK_LAUNCH() AX_TRY(cudaGetLastError())
+
+template <typename P>
+cudaError_t dalloc(P **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(P));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  return cudaMemset(*p, 0, count * sizeof(P));
+}
+
+template <typename P>
+void dfree(P *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+void free_graph(GraphCache &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.key = -1;
+}
+
+void free_vectors64(Workspace *w) {
+  dfree(w->r64); dfree(w->pa64); dfree(w->pb64); dfree(w->q64); dfree(w->z64); dfree(w->y64prev);
+  w->m64 = 0;
+  free_graph(w->g64);
+  free_graph(w->gc64);
+}
+void free_vectors32(Workspace *w) {
+  dfree(w->x32); dfree(w->r32); dfree(w->pa32); dfree(w->pb32); dfree(w->q32); dfree(w->z32); dfree(w->y32prev);
+  w->m32 = 0;
+  free_graph(w->g32);
+  free_graph(w->gc32);
+}
+void free_base(Workspace *w) {
+  dfree(w->phi64); dfree(w->x64); dfree(w->part); dfree(w->st); dfree(w->st_outer);
+  if (w->h_st) cudaFreeHost(w->h_st);
+  w->h_st = nullptr;
+  w->mbase = 0;
+  free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+}
+
+size_t field_elems(const ax_operator *op) { return (size_t)op->nr * op->pitch; }
+
+int ensure_base(ax_operator *op, int m) {
+  Workspace *w = op->ws;
+  if (w->mbase >= m) return AX_OK;
+  free_base(w);
+  const size_t f = field_elems(op) * m;
+  AX_TRY(dalloc(&w->phi64, f));
+  AX_TRY(dalloc(&w->x64, f));
+  AX_TRY(dalloc(&w->part, (size_t)4 * m * kPartialStride));
+  AX_TRY(dalloc(&w->st, (size_t)m));
+  AX_TRY(dalloc(&w->st_outer, (size_t)m));
+  AX_TRY(cudaMallocHost((void **)&w->h_st, sizeof(RhsState) * 2 * m));
+  w->mbase = m;
+  return AX_OK;
+}
+
+int ensure_vec64(ax_operator *op, int m, bool cheb) {
+  Workspace *w = op->ws;
+  if (w->m64 >= m && (!cheb || w->y64prev)) return AX_OK;
+  free_vectors64(w);
+  const size_t f = field_elems(op) * m;
+  AX_TRY(dalloc(&w->r64, f));
+  AX_TRY(dalloc(&w->pa64, f));
+  AX_TRY(dalloc(&w->pb64, f));
+  AX_TRY(dalloc(&w->q64, f));
+  AX_TRY(dalloc(&w->z64, f));
+  if (cheb) AX_TRY(dalloc(&w->y64prev, f));
+  w->m64 = m;
+  return AX_OK;
+}
+
+int ensure_vec32(ax_operator *op, int m, bool cheb) {
+  Workspace *w = op->ws;
+  if (w->m32 >= m && (!cheb || w->y32prev)) return AX_OK;
+  free_vectors32(w);
+  const size_t f = field_elems(op) * m;
+  AX_TRY(dalloc(&w->x32, f));
+  AX_TRY(dalloc(&w->r32, f));
+  AX_TRY(dalloc(&w->pa32, f));
+  AX_TRY(dalloc(&w->pb32, f));
+  AX_TRY(dalloc(&w->q32, f));
+  AX_TRY(dalloc(&w->z32, f));
+  if (cheb) AX_TRY(dalloc(&w->y32prev, f));
+  w->m32 = m;
+  return AX_OK;
+}
+
+int ensure_stage(ax_operator *op, size_t elems) {
+  Workspace *w = op->ws;
+  if (w->stage_elems >= elems) return AX_OK;
+  dfree(w->stage_a);
+  dfree(w->stage_b);
+  w->stage_elems = 0;
+  AX_TRY(dalloc(&w->stage_a, elems));
+  AX_TRY(dalloc(&w->stage_b, elems));
+  w->stage_elems = elems;
+  return AX_OK;
+}
+
+int ensure_scratch(ax_operator *op, size_t bytes) {
+  Workspace *w = op->ws;
+  if (w->scratch_bytes >= bytes) return AX_OK;
+  if (w->scratch) cudaFree(w->scratch);
+  w->scratch = nullptr;
+  w->scratch_bytes = 0;
+  unsigned char *p = nullptr;
+  AX_TRY(dalloc(&p, bytes));
+  w->scratch = p;
+  w->scratch_bytes = bytes;
+  return AX_OK;
+}
+
+// Records a pair of events around the launches in its lifetime when the
+// operator's profiler is on.
+struct ProfScope {
+  Workspace *w;
+  int kind;
+  double units;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(Workspace *w_, int kind_, double units_, cudaStream_t s_) : w(w_), kind(kind_), units(units_), s(s_) {
+    if (w && w->profile && !g_capturing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(b, s);
+    w->prof_events.push_back({kind, a, b, units});
+  }
+};
+
+void prof_collect(Workspace *w) {
+  for (auto &e : w->prof_events) {
+    float ms = 0.f;
+    cudaEventSynchronize(e.b);
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    w->prof_ms[e.kind] += ms;
+    w->prof_launches[e.kind] += 1;
+    w->prof_units[e.kind] += e.units;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  w->prof_events.clear();
+}
+
+double *part_ptr(Workspace *w, int kind) { return w->part + (size_t)kind * w->mbase * kPartialStride; }
+enum { kPartA = 0, kPartB = 1, kPartC = 2, kPartD = 3 };
+
+// ---------------------------------------------------------------------------
+// Conversion kernels (dense caller layout <-> padded device layout)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void dense_to_padded(const double *__restrict__ src, T *__restrict__ dst, long long rows, int nz,
+                                int pitch) {
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) dst[row * pitch + k] = (T)src[row * nz + k];
+}
+
+template <typename T>
+__global__ void padded_to_dense(const T *__restrict__ src, double *__restrict__ dst, long long rows, int nz,
+                                int pitch) {
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) dst[row * nz + k] = (double)src[row * pitch + k];
+}
+
+// phi = r_i f (Eq. diff_approx1), FP64, plus per-CTA partials of ||phi||^2.
+// grid (m, ceil(nr / 16)), 256 threads.
+__global__ void prep_rhs(const double *__restrict__ f, double *__restrict__ phi, const double *__restrict__ R,
+                         int nr, int nz, int pitch, double *__restrict__ part) {
+  __shared__ double red[8];
+  const int m = blockIdx.x;
+  const int i0 = blockIdx.y * 16, i1 = min(i0 + 16, nr);
+  double acc = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double ri = R[i];
+    const double *fr = f + ((size_t)m * nr + i) * nz;
+    double *pr = phi + ((size_t)m * nr + i) * pitch;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+      const double v = ri * fr[k];
+      pr[k] = v;
+      acc = fma(v, v, acc);
+    }
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(size_t)m * kPartialStride + blockIdx.y] = s;
+}
+
+template <typename T>
+__global__ void to_precision(const double *__restrict__ src, T *__restrict__ dst, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+
+// x64 += d32 for right-hand sides whose outer state matches `mask`.
+__global__ void add_correction(double *__restrict__ x, const float *__restrict__ d, size_t field,
+                               const RhsState *st, int mask) {
+  const int m = blockIdx.y;
+  if (!rhs_selected(st, mask, m)) return;
+  const size_t b = (size_t)m * field;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < field; e += (size_t)gridDim.x * blockDim.x)
+    x[b + e] += (double)d[b + e];
+}
+
+// ---------------------------------------------------------------------------
+// Scalar kernels: one warp per right-hand side, fixed-order reductions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double reduce_part(const double *p, int nb) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s += p[i];
+  return warp_sum(s);
+}
+
+// rr = ||phi - A x||^2, bb = ||phi||^2 (or given), start the iteration.
+__global__ void sc_start(RhsState *st, const double *prr, int nbr, const double *pbb, int nbb, double tol2,
+                         int max_iter, int mask, int use_rr_as_bb) {
+  const int m = blockIdx.x;
+  if (!rhs_selected(st, mask, m)) return;
+  const double rr = reduce_part(prr + (size_t)m * kPartialStride, nbr);
+  const double bb = use_rr_as_bb ? rr : reduce_part(pbb + (size_t)m * kPartialStride, nbb);
+  if (threadIdx.x == 0) {
+    RhsState s = st[m];
+    s.rr = rr;
+    s.bb = bb;
+    s.thresh2 = tol2 * bb;
+    s.iters = 0;
+    s.max_iter = max_iter;
+    s.beta = 0.0;
+    s.cheb_a = 2.0;
+    s.status = AX_OK;
+    if (!isfinite(rr) || !isfinite(bb)) {
+      s.state = kFailed;
+      s.status = AX_ERR_BREAKDOWN;
+    } else {
+      s.state = (rr <= s.thresh2 || bb == 0.0) ? kDone : kActive;
+    }
+    st[m] = s;
+  }
+}
+
+__global__ void sc_rho_init(RhsState *st, const double *p, int nb, int mask) {
+  const int m = blockIdx.x;
+  if (!rhs_selected(st, mask, m)) return;
+  const double rz = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    st[m].rho = rz;
+    st[m].beta = 0.0;
+    if (!isfinite(rz)) {
+      st[m].state = kFailed;
+      st[m].status = AX_ERR_BREAKDOWN;
+    }
+  }
+}
+
+__global__ void sc_alpha(RhsState *st, const double *p, int nb) {
+  const int m = blockIdx.x;
+  if (st[m].state != kActive) return;
+  const double pq = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(st[m].rho)) {
+      st[m].state = kFailed;
+      st[m].status = AX_ERR_BREAKDOWN;
+    } else {
+      st[m].alpha = st[m].rho / pq;
+    }
+  }
+}
+
+// After x, r update: count the iteration and test the recursive residual.
+__global__ void sc_after_update(RhsState *st, const double *p, int nb, int on_converge) {
+  const int m = blockIdx.x;
+  if (st[m].state != kActive) return;
+  const double rr = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    RhsState s = st[m];
+    s.rr = rr;
+    s.iters += 1;
+    if (!isfinite(rr)) {
+      s.state = kFailed;
+      s.status = AX_ERR_BREAKDOWN;
+    } else if (rr <= s.thresh2) {
+      s.state = on_converge;
+    } else if (s.iters >= s.max_iter) {
+      s.state = (on_converge == kDone) ? kDone : kFailed;
+      if (on_converge != kDone) s.status = AX_ERR_NO_CONVERGENCE;
+    }
+    st[m] = s;
+  }
+}
+
+__global__ void sc_beta(RhsState *st, const double *p, int nb, int mask, int next_state) {
+  const int m = blockIdx.x;
+  if (st[m].state != mask) return;
+  const double rz = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    const double rho = st[m].rho;
+    if (!isfinite(rz) || rho == 0.0) {
+      st[m].state = kFailed;
+      st[m].status = AX_ERR_BREAKDOWN;
+    } else {
+      st[m].beta = rz / rho;
+      st[m].rho = rz;
+      st[m].state = next_state;
+    }
+  }
+}
+
+// True-residual test of right-hand sides in kCheck.
+__global__ void sc_true_check(RhsState *st, const double *p, int nb) {
+  const int m = blockIdx.x;
+  if (st[m].state != kCheck) return;
+  const double rr = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    st[m].rr = rr;
+    if (rr <= st[m].thresh2) st[m].state = kDone;
+    else if (st[m].iters >= st[m].max_iter) {
+      st[m].state = kFailed;
+      st[m].status = AX_ERR_NO_CONVERGENCE;
+    }
+  }
+}
+
+// Chebyshev: rr = ||A y - phi||^2 of the current iterate; stop or continue and
+// advance alpha_{k+1} = 4 / (4 - rho0^2 alpha_k) (alpha for the first step is 1).
+__global__ void sc_cheb(RhsState *st, const double *p, int nb, double rho0sq, int on_converge) {
+  const int m = blockIdx.x;
+  if (st[m].state != kActive) return;
+  const double rr = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    RhsState s = st[m];
+    s.rr = rr;
+    if (!isfinite(rr)) {
+      s.state = kFailed;
+      s.status = AX_ERR_BREAKDOWN;
+    } else if (rr <= s.thresh2) {
+      s.state = on_converge;
+    } else if (s.iters >= s.max_iter) {
+      s.state = (on_converge == kDone) ? kDone : kFailed;
+      if (on_converge != kDone) s.status = AX_ERR_NO_CONVERGENCE;
+    } else {
+      if (s.iters == 0) {
+        s.cheb_a = 1.0;  // y_1 = y_0 - tau B^-1 (A y_0 - phi) (the y_{-1} term drops out)
+      } else {
+        const double prev = (s.iters == 1) ? 2.0 : s.cheb_a;
+        s.cheb_a = 4.0 / (4.0 - rho0sq * prev);
+      }
+      s.iters += 1;
+    }
+    st[m] = s;
+  }
+}
+
+// Outer refinement step: rr = ||phi - A x||^2 (FP64).  Converged RHS -> done;
+// the others get an inner solve with reference ||r||^2.
+__global__ void sc_outer(RhsState *so, RhsState *si, const double *prr, int nbr, const double *pbb, int nbb,
+                         double tol2, double eta2, int inner_max, int first) {
+  const int m = blockIdx.x;
+  if (so[m].state != kActive) {
+    if (threadIdx.x == 0) si[m].state = kIdle;
+    return;
+  }
+  const double rr = reduce_part(prr + (size_t)m * kPartialStride, nbr);
+  double bb = 0.0;
+  if (first) bb = reduce_part(pbb + (size_t)m * kPartialStride, nbb);
+  if (threadIdx.x == 0) {
+    RhsState s = so[m];
+    if (first) {
+      s.bb = bb;
+      s.thresh2 = tol2 * bb;
+      s.iters = 0;
+      s.status = AX_OK;
+      s.tmp = 0.0;  // outer steps
+    } else {
+      s.iters += si[m].iters;  // inner iterations of the step just finished
+      if (si[m].state == kFailed) {
+        s.state = kFailed;
+        s.status = si[m].status;
+      }
+    }
+    s.rr = rr;
+    RhsState in = si[m];
+    in.state = kIdle;
+    if (s.state == kActive) {
+      if (!isfinite(rr)) {
+        s.state = kFailed;
+        s.status = AX_ERR_BREAKDOWN;
+      } else if (rr <= s.thresh2 || s.bb == 0.0) {
+        s.state = kDone;
+      } else if (s.iters >= s.max_iter) {
+        s.state = kFailed;
+        s.status = AX_ERR_NO_CONVERGENCE;
+      } else {
+        s.tmp += 1.0;
+        in.state = kActive;
+        in.bb = rr;
+        in.rr = rr;
+        in.thresh2 = eta2 * rr;
+        in.iters = 0;
+        in.max_iter = inner_max;
+        in.beta = 0.0;
+        in.cheb_a = 2.0;
+        in.status = AX_OK;
+      }
+    }
+    so[m] = s;
+    si[m] = in;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side plan and coefficient construction
+// ---------------------------------------------------------------------------
+FftPlan make_plan(int L) {
+  FftPlan p;
+  p.L = L;
+  std::vector<int> odd_big, fives, threes;
+  int twos = 0, m = L;
+  while (m % 2 == 0) { m /= 2; ++twos; }
+  for (int d = 3; (long long)d * d <= m; d += 2) {
+    while (m % d == 0) {
+      if (d == 3) threes.push_back(3);
+      else if (d == 5) fives.push_back(5);
+      else odd_big.push_back(d);
+      m /= d;
+    }
+  }
+  if (m > 1) {
+    if (m == 3) threes.push_back(3);
+    else if (m == 5) fives.push_back(5);
+    else odd_big.push_back(m);
+  }
+  std::sort(odd_big.rbegin(), odd_big.rend());
+  std::vector<int> r;
+  for (int x : odd_big) r.push_back(x);
+  for (int x : fives) r.push_back(x);
+  for (int x : threes) r.push_back(x);
+  while (twos >= 3) { r.push_back(8); twos -= 3; }
+  if (twos == 2) r.push_back(4);
+  if (twos == 1) r.push_back(2);
+  p.nstages = (int)r.size();
+  for (int i = 0; i < p.nstages && i < kMaxStages; ++i) p.radix[i] = r[i];
+  return p;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<double> &src) {
+  std::vector<T> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+  cudaError_t e = dalloc(dst, src.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+void free_coef(Coef<T> &c) {
+  dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW);
+}
+
+// ---------------------------------------------------------------------------
+// One preconditioner application on the rows of `v` (already in rhat layout):
+// forward transform, mode solves, inverse transform.
+// ---------------------------------------------------------------------------
+template <typename T>
+const Coef<T> &coef(const ax_operator *op);
+template <>
+const Coef<double> &coef<double>(const ax_operator *op) { return op->c64; }
+template <>
+const Coef<float> &coef<float>(const ax_operator *op) { return op->c32; }
+
+template <typename T>
+DstArgs<T> dst_args(const ax_operator *op, int m, int rows, const RhsState *st, int mask) {
+  DstArgs<T> a{};
+  const Coef<T> &c = coef<T>(op);
+  a.TW = c.TW;
+  a.HW = c.HW;
+  a.plan = op->plan;
+  a.n = op->nz;
+  a.rows = rows;
+  a.pitch = op->pitch;
+  a.field = (long long)rows * op->pitch;
+  a.m = m;
+  a.scale = 0.5 / std::sqrt(2.0 * op->plan.L);
+  a.st = st;
+  a.mask = mask;
+  return a;
+}
+
+template <typename T>
+StencilArgs<T> stencil_args(const ax_operator *op, int m, const RhsState *st, int mask) {
+  StencilArgs<T> a{};
+  const Coef<T> &c = coef<T>(op);
+  a.CR = c.CR;
+  a.CZ = c.CZ;
+  a.W = c.W;
+  a.nr = op->nr;
+  a.nz = op->nz;
+  a.pitch = op->pitch;
+  a.pitchz = op->pitchz;
+  a.field = (long long)field_elems(op);
+  a.m = m;
+  a.st = st;
+  a.mask = mask;
+  return a;
+}
+
+template <typename T>
+TriArgs<T> tri_args(const ax_operator *op, int m, const T *in, T *out, const RhsState *st, int mask) {
+  TriArgs<T> a{};
+  const Coef<T> &c = coef<T>(op);
+  a.IP = c.IP;
+  a.E = c.E;
+  a.nr = op->nr;
+  a.nz = op->nz;
+  a.pitch = op->pitch;
+  a.field = (long long)field_elems(op);
+  a.m = m;
+  a.in = in;
+  a.out = out;
+  a.st = st;
+  a.mask = mask;
+  return a;
+}
+
+int dst_blocks(const ax_operator *op, int rows, int bytes) {
+  const int rpb = dst_rows_per_block(op->plan.L, bytes);
+  return (rows + rpb - 1) / rpb;
+}
+
+// z = B^-1 r for selected RHS, with (r, z) partials into `prz`.
+template <typename T>
+void precond_apply(const ax_operator *op, int m, const T *r, T *z, const RhsState *st, int mask, double *prz,
+                   cudaStream_t s) {
+  DstArgs<T> f = dst_args<T>(op, m, op->nr, st, mask);
+  f.in = r;
+  f.out = z;
+  launch_dst<T>(kDstPlain, f, s);
+  launch_tridiag<T>(tri_args<T>(op, m, z, z, st, mask), s);
+  DstArgs<T> b = dst_args<T>(op, m, op->nr, st, mask);
+  b.in = z;
+  b.out = z;
+  b.r = const_cast<T *>(r);
+  b.partial = prz;
+  launch_dst<T>(kDstPcgInverse, b, s);
+}
+
+// ---------------------------------------------------------------------------
+// PCG (generic over the working precision T)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PcgVecs {
+  T *x, *r, *pa, *pb, *q, *z;
+};
+
+template <typename T>
+void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *st, Workspace *w,
+                   int on_converge, cudaStream_t s, double units = 0.0) {
+  const int V = VecT<T>::n;
+  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
+  const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
+  double *pq = part_ptr(w, kPartA), *prr = part_ptr(w, kPartB), *prz = part_ptr(w, kPartC);
+  StencilArgs<T> sa = stencil_args<T>(op, m, st, kActive);
+  sa.in = v.z;
+  sa.pa = v.pa;
+  sa.pb = v.pb;
+  sa.out = v.q;
+  sa.partial = pq;
+  { ProfScope ps(w, kProfStencil, units, s); launch_stencil<T>(kStencilPcg, sa, s); }
+  {
+    ProfScope ps(w, kProfScalar, 0.0, s);
+    note_launch();
+    sc_alpha<<<m, 32, 0, s>>>(st, pq, nbs);
+  }
+  DstArgs<T> f = dst_args<T>(op, m, op->nr, st, kActive);
+  f.in = v.q;
+  f.out = v.z;
+  f.x = v.x;
+  f.r = v.r;
+  f.pa = v.pa;
+  f.pb = v.pb;
+  f.partial = prr;
+  { ProfScope ps(w, kProfDstFwd, units, s); launch_dst<T>(kDstPcgForward, f, s); }
+  {
+    ProfScope ps(w, kProfScalar, 0.0, s);
+    note_launch();
+    sc_after_update<<<m, 32, 0, s>>>(st, prr, nbd, on_converge);
+  }
+  { ProfScope ps(w, kProfTridiag, units, s); launch_tridiag<T>(tri_args<T>(op, m, v.z, v.z, st, kActive), s); }
+  DstArgs<T> b = dst_args<T>(op, m, op->nr, st, kActive);
+  b.in = v.z;
+  b.out = v.z;
+  b.r = v.r;
+  b.partial = prz;
+  { ProfScope ps(w, kProfDstInv, units, s); launch_dst<T>(kDstPcgInverse, b, s); }
+  {
+    ProfScope ps(w, kProfScalar, 0.0, s);
+    note_launch();
+    sc_beta<<<m, 32, 0, s>>>(st, prz, nbd, kActive, kActive);
+  }
+}
+
+// Chebyshev step for RHS in kActive: res = A y - phi, test, ybar = y - tau
+// B^-1 res, y_{k+1} = a ybar + (1 - a) y_{k-1} (written over y_{k-1}; the
+// caller swaps the two buffers by parity).
+template <typename T>
+struct ChebVecs {
+  T *ya, *yb, *res, *phi;
+};
+
+template <typename T>
+__global__ void cheb_swap_dummy() {}
+
+template <typename T>
+void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, Workspace *w,
+                    double tau, double rho0sq, int on_converge, int parity, cudaStream_t s) {
+  const int V = VecT<T>::n;
+  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
+  double *prr = part_ptr(w, kPartB);
+  T *y = parity ? v.yb : v.ya;
+  T *yprev = parity ? v.ya : v.yb;
+  StencilArgs<T> sa = stencil_args<T>(op, m, st, kActive);
+  sa.in = y;
+  sa.out = v.res;
+  sa.phi = v.phi;
+  sa.partial = prr;
+  launch_stencil<T>(kStencilCheb, sa, s);
+  note_launch();
+  sc_cheb<<<m, 32, 0, s>>>(st, prr, nbs, rho0sq, on_converge);
+  DstArgs<T> f = dst_args<T>(op, m, op->nr, st, kActive);
+  f.in = v.res;
+  f.out = v.res;
+  launch_dst<T>(kDstPlain, f, s);
+  launch_tridiag<T>(tri_args<T>(op, m, v.res, v.res, st, kActive), s);
+  DstArgs<T> b = dst_args<T>(op, m, op->nr, st, kActive);
+  b.in = v.res;
+  b.y = y;
+  b.yprev = yprev;
+  b.tau = tau;
+  launch_dst<T>(kDstChebInverse, b, s);
+}
+
+int read_states(Workspace *w, const RhsState *dev, int m, cudaStream_t s, RhsState *host) {
+  AX_TRY(cudaMemcpyAsync(host, dev, sizeof(RhsState) * m, cudaMemcpyDeviceToHost, s));
+  AX_TRY(cudaStreamSynchronize(s));
+  return AX_OK;
+}
+
+// Runs `iters` captured iterations of `body` on stream s (graph cached by key).
+template <typename F>
+int run_graph(Workspace *w, GraphCache &g, int key, cudaStream_t s, F body) {
+  if (g.exec == nullptr || g.key != key) {
+    free_graph(g);
+    cudaGraph_t graph = nullptr;
+    AX_TRY(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeRelaxed));
+    g_capturing = true;
+    body(w->cap);
+    g_capturing = false;
+    cudaError_t e = cudaStreamEndCapture(w->cap, &graph);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    g.nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &g.nodes);
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return status_from_cuda(e);
+    }
+    g.key = key;
+  }
+  AX_TRY(cudaGraphLaunch(g.exec, s));
+  __atomic_add_fetch(&g_launches, (long long)g.nodes, __ATOMIC_RELAXED);
+  return AX_OK;
+}
+
+int count_state(const RhsState *h, int m, int state) {
+  int c = 0;
+  for (int i = 0; i < m; ++i) c += (h[i].state == state);
+  return c;
+}
+
+bool any_state(const RhsState *h, int m, int state) {
+  for (int i = 0; i < m; ++i)
+    if (h[i].state == state) return true;
+  return false;
+}
+
+// PCG for the vectors v with right-hand side phi (in v.r on entry as the
+// residual).  Assumes st has been started (sc_start) and x holds the start.
+// If `true_check`, right-hand sides whose recursive residual passes get an
+// FP64-exact test with the true residual phi - A x (plain method); otherwise
+// they finish at once (inner solves).
+template <typename T>
+int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState *st, GraphCache &g, bool true_check,
+             cudaStream_t s) {
+  Workspace *w = op->ws;
+  const int V = VecT<T>::n;
+  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
+  const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
+  // z = B^-1 r, rho = (r, z), p = 0 so that p_1 = z
+  precond_apply<T>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s);
+  note_launch();
+  sc_rho_init<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kActive);
+  AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(T) * field_elems(op) * m, s));
+  AX_CHECK_LAUNCH();
+  const int on_conv = true_check ? kCheck : kDone;
+  const int K = w->graph_iters;
+  const int key = m * 4 + (true_check ? 1 : 0);
+  const double per_rhs = (double)op->nr * op->nz;
+  for (int guard = 0; guard < 1000000; ++guard) {
+    int rc = AX_OK;
+    RhsState *h = w->h_st;
+    if (w->profile) {
+      // one iteration at a time, so every launch is timed with the true
+      // number of right-hand sides it works on
+      if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+      pcg_iteration<T>(op, m, v, st, w, on_conv, s, per_rhs * count_state(h, m, kActive));
+      AX_CHECK_LAUNCH();
+    } else {
+      rc = run_graph(w, g, key, s, [&](cudaStream_t cs) {
+        for (int k = 0; k < K; ++k) pcg_iteration<T>(op, m, v, st, w, on_conv, cs);
+      });
+    }
+    if (rc != AX_OK) return rc;
+    if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    if (true_check && any_state(h, m, kCheck)) {
+      StencilArgs<T> ra = stencil_args<T>(op, m, st, kCheck);
+      ra.in = v.x;
+      ra.phi = phi;
+      ra.out_res = v.r;
+      ra.partial = part_ptr(w, kPartB);
+      launch_stencil<T>(kStencilResidual, ra, s);
+      note_launch();
+      sc_true_check<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs);
+      precond_apply<T>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), s);
+      note_launch();
+      sc_beta<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
+      AX_CHECK_LAUNCH();
+      if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    }
+    if (!any_state(h, m, kActive)) break;
+  }
+  return AX_OK;
+}
+
+template <typename T>
+int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphCache &g, int on_conv, int *parity,
+              cudaStream_t s) {
+  Workspace *w = op->ws;
+  const double tau = 2.0 / (op->gamma1 + op->gamma2);
+  const double xi = op->gamma1 / op->gamma2;
+  const double rho0 = (1.0 - xi) / (1.0 + xi);
+  const int K = 2 * std::max(1, w->graph_iters / 2);  // even: the buffer roles repeat
+  const int key = m * 4 + 2 + (on_conv == kDone ? 1 : 0) + (*parity << 20);
+  for (int guard = 0; guard < 1000000; ++guard) {
+    int rc = run_graph(w, g, key, s, [&](cudaStream_t cs) {
+      for (int k = 0; k < K; ++k) cheb_iteration<T>(op, m, v, st, w, tau, rho0 * rho0, on_conv, (*parity + k) & 1, cs);
+    });
+    if (rc != AX_OK) return rc;
+    RhsState *h = w->h_st;
+    if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    if (!any_state(h, m, kActive)) break;
+  }
+  return AX_OK;
+}
+
+}  // namespace
+}  // namespace ax
+
+using namespace ax;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *ax_status_string(int status) {
+  switch (status) {
+    case AX_OK: return "ok";
+    case AX_ERR_INVALID_ARG: return "invalid argument";
+    case AX_ERR_NO_CONVERGENCE: return "no convergence within max_iter";
+    case AX_ERR_BREAKDOWN: return "breakdown (non-positive curvature or non-finite scalar)";
+    case AX_ERR_TIMEOUT: return "bounded device wait expired";
+    case AX_ERR_OOM: return "device out of memory";
+    case AX_ERR_CUDA: return "CUDA runtime error";
+    case AX_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+const char *ax_version(void) { return "axpcg 0.1 sm_103a"; }
+
+int64_t ax_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int ax_profile_read(ax_operator *op, int32_t kind, double *ms, double *launches, double *units) {
+  if (!op || kind < 0 || kind >= kProfKinds) return AX_ERR_INVALID_ARG;
+  prof_collect(op->ws);
+  if (ms) *ms = op->ws->prof_ms[kind];
+  if (launches) *launches = op->ws->prof_launches[kind];
+  if (units) *units = op->ws->prof_units[kind];
+  return AX_OK;
+}
+
+int ax_destroy_operator(ax_operator *op) {
+  if (!op) return AX_OK;
+  free_coef(op->c64);
+  free_coef(op->c32);
+  if (op->ws) {
+    Workspace *w = op->ws;
+    free_vectors64(w);
+    free_vectors32(w);
+    free_base(w);
+    dfree(w->stage_a);
+    dfree(w->stage_b);
+    if (w->scratch) cudaFree(w->scratch);
+    if (w->cap) cudaStreamDestroy(w->cap);
+    delete w;
+  }
+  delete op;
+  return AX_OK;
+}
+
+int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t, double *gamma1, double *gamma2) {
+  if (!op) return AX_ERR_INVALID_ARG;
+  if (kappa_t) *kappa_t = op->kappa_t;
+  if (q_t) *q_t = op->q_t;
+  if (gamma1) *gamma1 = op->gamma1;
+  if (gamma2) *gamma2 = op->gamma2;
+  return AX_OK;
+}
+
+int ax_set_option(ax_operator *op, const char *name, double value) {
+  if (!op || !name) return AX_ERR_INVALID_ARG;
+  Workspace *w = op->ws;
+  if (!strcmp(name, "inner_tol")) {
+    if (!(value > 0.0 && value < 1.0)) return AX_ERR_INVALID_ARG;
+    w->inner_tol = value;
+  } else if (!strcmp(name, "inner_max_iter")) {
+    if (!(value >= 1)) return AX_ERR_INVALID_ARG;
+    w->inner_max = (int)value;
+  } else if (!strcmp(name, "graph_iters")) {
+    if (!(value >= 1 && value <= 256)) return AX_ERR_INVALID_ARG;
+    w->graph_iters = (int)value;
+    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+  } else if (!strcmp(name, "profile")) {
+    prof_collect(w);
+    w->profile = value != 0.0;
+    for (int k = 0; k < kProfKinds; ++k) w->prof_ms[k] = w->prof_launches[k] = w->prof_units[k] = 0.0;
+  } else if (!strcmp(name, "max_outer")) {
+    if (!(value >= 1)) return AX_ERR_INVALID_ARG;
+    w->max_outer = (int)value;
+  } else {
+    return AX_ERR_INVALID_ARG;
+  }
+  return AX_OK;
+}
+
+int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double *q, const ax_grid *g, void *stream,
+                      ax_operator **out) {
+  if (!out) return AX_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!kappa_r || !kappa_z || !q || !g) return AX_ERR_INVALID_ARG;
+  if (g->bc_z != 0) return g->bc_z == 1 ? AX_ERR_UNSUPPORTED : AX_ERR_INVALID_ARG;
+  const int nr = g->nr, nz = g->nz;
+  if (nr < 1 || nz < 1 || nr > kMaxNr || nz > kMaxNz) return AX_ERR_INVALID_ARG;
+  if (!(g->lr > 0.0) || !(g->lz > 0.0) || !std::isfinite(g->lr) || !std::isfinite(g->lz)) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nrz = (size_t)nr * nz, nrz1 = (size_t)nr * (nz + 1);
+  std::vector<double> kr(nrz), kz(nrz1), qq(nrz);
+  AX_TRY(cudaMemcpyAsync(kr.data(), kappa_r, nrz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AX_TRY(cudaMemcpyAsync(kz.data(), kappa_z, nrz1 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AX_TRY(cudaMemcpyAsync(qq.data(), q, nrz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AX_TRY(cudaStreamSynchronize(s));
+  double kmin = INFINITY, kmax = -INFINITY, qmin = INFINITY, qmax = -INFINITY;
+  for (double v : kr) {
+    if (!std::isfinite(v) || !(v > 0.0)) return AX_ERR_INVALID_ARG;
+    kmin = std::min(kmin, v); kmax = std::max(kmax, v);
+  }
+  for (double v : kz) {
+    if (!std::isfinite(v) || !(v > 0.0)) return AX_ERR_INVALID_ARG;
+    kmin = std::min(kmin, v); kmax = std::max(kmax, v);
+  }
+  for (double v : qq) {
+    if (!std::isfinite(v) || v < 0.0) return AX_ERR_INVALID_ARG;
+    qmin = std::min(qmin, v); qmax = std::max(qmax, v);
+  }
+
+  ax_operator *op = new ax_operator();
+  op->ws = new Workspace();
+  op->nr = nr;
+  op->nz = nz;
+  op->pitch = (nz + 31) / 32 * 32;
+  op->pitchz = (nz + 1 + 31) / 32 * 32;
+  op->lr = g->lr;
+  op->lz = g->lz;
+  op->hr = g->lr / (nr + 0.5);
+  op->hz = g->lz / (nz + 1.0);
+  cudaGetDevice(&op->device);
+  // Eq. coeff2 with the footnote of Eq. diff_approx2: mean of the extremes.
+  op->kappa_t = 0.5 * (kmin + kmax);
+  op->q_t = 0.5 * (qmin + qmax);
+  // gamma_1, gamma_2 (Eq. energy_rel): face-wise ratios bound the Rayleigh quotient.
+  op->gamma1 = kmin / op->kappa_t;
+  op->gamma2 = kmax / op->kappa_t;
+  if (op->q_t > 0.0) {
+    op->gamma1 = std::min(op->gamma1, qmin / op->q_t);
+    op->gamma2 = std::max(op->gamma2, qmax / op->q_t);
+  }
+  const int L = nz + 1;
+  op->plan = make_plan(L);
+  if (op->plan.nstages > kMaxStages) {
+    ax_destroy_operator(op);
+    return AX_ERR_UNSUPPORTED;
+  }
+
+  const double hr = op->hr, hz = op->hz, hr2 = hr * hr, hz2 = hz * hz;
+  const int P = op->pitch, PZ = op->pitchz;
+  std::vector<double> ri(nr), CR((size_t)nr * P, 0.0), CZ((size_t)nr * PZ, 0.0), W((size_t)nr * P, 0.0);
+  for (int a = 0; a < nr; ++a) ri[a] = (a + 0.5) * hr;
+  for (int a = 0; a < nr; ++a) {
+    const double rbar = (a + 1) * hr;  // face between r-nodes a+1 and a+2 (1-based)
+    for (int b = 0; b < nz; ++b) {
+      CR[(size_t)a * P + b] = rbar * kr[(size_t)a * nz + b] / hr2;
+      W[(size_t)a * P + b] = ri[a] * qq[(size_t)a * nz + b];
+    }
+    for (int c = 0; c <= nz; ++c) CZ[(size_t)a * PZ + c] = ri[a] * kz[(size_t)a * (nz + 1) + c] / hz2;
+  }
+  // Per-mode Thomas factors of T_l (Eq. eq_trid), computed in FP64.
+  std::vector<double> E(nr, 0.0), IP((size_t)nr * P, 0.0);
+  const double kt = op->kappa_t, qt = op->q_t;
+  for (int a = 0; a + 1 < nr; ++a) E[a] = -kt * (a + 1) * hr / hr2;
+  for (int l = 1; l <= nz; ++l) {
+    const double sn = std::sin(M_PI * l / (2.0 * (nz + 1)));
+    const double lam = 4.0 / hz2 * sn * sn;
+    double delta = 0.0;
+    for (int a = 0; a < nr; ++a) {
+      const double rbar_hi = (a + 1) * hr, rbar_lo = a * hr;
+      const double d = kt * (rbar_hi + rbar_lo) / hr2 + ri[a] * (kt * lam + qt);
+      delta = (a == 0) ? d : d - E[a - 1] * E[a - 1] / delta;
+      IP[(size_t)a * P + (l - 1)] = 1.0 / delta;
+    }
+  }
+  std::vector<double> TW(2 * (size_t)L), HW(2 * (size_t)L);
+  for (int j = 0; j < L; ++j) {
+    TW[2 * j] = std::cos(2.0 * M_PI * j / L);
+    TW[2 * j + 1] = std::sin(2.0 * M_PI * j / L);
+    HW[2 * j] = std::cos(M_PI * j / L);
+    HW[2 * j + 1] = std::sin(M_PI * j / L);
+  }
+  cudaError_t e = cudaSuccess;
+#define AX_UP(T, field, vec) \
+  if (e == cudaSuccess) e = upload<T>(&op->field, vec);
+  AX_UP(double, c64.CR, CR) AX_UP(double, c64.CZ, CZ) AX_UP(double, c64.W, W) AX_UP(double, c64.IP, IP)
+  AX_UP(double, c64.E, E) AX_UP(double, c64.R, ri) AX_UP(double, c64.TW, TW) AX_UP(double, c64.HW, HW)
+  AX_UP(float, c32.CR, CR) AX_UP(float, c32.CZ, CZ) AX_UP(float, c32.W, W) AX_UP(float, c32.IP, IP)
+  AX_UP(float, c32.E, E) AX_UP(float, c32.R, ri) AX_UP(float, c32.TW, TW) AX_UP(float, c32.HW, HW)
+#undef AX_UP
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&op->ws->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    ax_destroy_operator(op);
+    return status_from_cuda(e);
+  }
+  *out = op;
+  return AX_OK;
+}
+
+}  // extern "C"
+
+// ---- single-step entry points --------------------------------------------
+template <typename T>
+static int apply_step(ax_operator *op, const double *in, double *out, int m, int rows_per, int which,
+                      cudaStream_t s) {
+  Workspace *w = op->ws;
+  const size_t field = (size_t)rows_per * op->pitch;
+  int rc = ensure_scratch(op, 2 * field * m * sizeof(T));
+  if (rc != AX_OK) return rc;
+  T *a = reinterpret_cast<T *>(w->scratch);
+  T *b = a + field * m;
+  AX_TRY(cudaMemsetAsync(w->scratch, 0, 2 * field * m * sizeof(T), s));
+  const long long rows = (long long)rows_per * m;
+  const int blocks = (int)std::min<long long>(rows, 65535);
+  note_launch();
+  dense_to_padded<T><<<blocks, 256, 0, s>>>(in, a, rows, op->nz, op->pitch);
+  if (which == 0) {
+    StencilArgs<T> sa = stencil_args<T>(op, m, nullptr, -1);
+    sa.in = a;
+    sa.out = b;
+    launch_stencil<T>(kStencilApply, sa, s);
+  } else if (which == 1) {
+    DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
+    d.in = a;
+    d.out = b;
+    launch_dst<T>(kDstPlain, d, s);
+  } else if (which == 2) {
+    launch_tridiag<T>(tri_args<T>(op, m, a, b, nullptr, -1), s);
+  } else {
+    DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
+    d.in = a;
+    d.out = b;
+    launch_dst<T>(kDstPlain, d, s);
+    launch_tridiag<T>(tri_args<T>(op, m, b, b, nullptr, -1), s);
+    DstArgs<T> d2 = dst_args<T>(op, m, rows_per, nullptr, -1);
+    d2.in = b;
+    d2.out = b;
+    launch_dst<T>(kDstPlain, d2, s);
+  }
+  note_launch();
+  padded_to_dense<T><<<blocks, 256, 0, s>>>(b, out, rows, op->nz, op->pitch);
+  AX_CHECK_LAUNCH();
+  return AX_OK;
+}
+
+static int apply_dispatch(ax_operator *op, const double *in, double *out, int m, int rows_per, int precision,
+                          int which, void *stream) {
+  if (!op || !in || !out || m < 1 || rows_per < 1) return AX_ERR_INVALID_ARG;
+  if (precision != AX_PREC_FP64 && precision != AX_PREC_FP32) return AX_ERR_INVALID_ARG;
+  if ((long long)rows_per * m > 2147483647LL / 2) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return precision == AX_PREC_FP64 ? apply_step<double>(op, in, out, m, rows_per, which, s)
+                                   : apply_step<float>(op, in, out, m, rows_per, which, s);
+}
+
+extern "C" {
+
+int ax_apply_operator(ax_operator *op, const double *in, double *out, int32_t m, int32_t precision, void *stream) {
+  return apply_dispatch(op, in, out, m, op ? op->nr : 0, precision, 0, stream);
+}
+int ax_apply_dst(ax_operator *op, const double *in, double *out, int32_t rows, int32_t precision, void *stream) {
+  if (op && rows > 65535 * 16) return AX_ERR_INVALID_ARG;
+  return apply_dispatch(op, in, out, 1, rows, precision, 1, stream);
+}
+int ax_apply_mode_solve(ax_operator *op, const double *in, double *out, int32_t m, int32_t precision,
+                        void *stream) {
+  return apply_dispatch(op, in, out, m, op ? op->nr : 0, precision, 2, stream);
+}
+int ax_apply_preconditioner(ax_operator *op, const double *in, double *out, int32_t m, int32_t precision,
+                            void *stream) {
+  return apply_dispatch(op, in, out, m, op ? op->nr : 0, precision, 3, stream);
+}
+
+// ---- solve ------------------------------------------------------------------
+static int finish_info(ax_operator *op, int m, const RhsState *dev, ax_solve_info *info, int outer_kind,
+                       int guess, cudaStream_t s) {
+  Workspace *w = op->ws;
+  int rc = read_states(w, dev, m, s, w->h_st);
+  if (rc != AX_OK) return rc;
+  int worst = AX_OK;
+  for (int i = 0; i < m; ++i) {
+    const RhsState &h = w->h_st[i];
+    int st = h.status;
+    if (st == AX_OK && h.state != kDone) st = AX_ERR_NO_CONVERGENCE;
+    if (info) {
+      info[i].iters = h.iters;
+      info[i].outer = outer_kind ? (int)h.tmp : 0;
+      info[i].rel_res = h.bb > 0.0 ? std::sqrt(h.rr / h.bb) : 0.0;
+      info[i].guess_accepted = guess;
+      info[i].status = st;
+    }
+    if (st != AX_OK && (worst == AX_OK || st > worst)) worst = st;
+  }
+  return worst;
+}
+
+int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol, int32_t max_iter, int32_t method,
+             int32_t flags, ax_solve_info *info, void *stream) {
+  if (!op || !f || !u || m < 1) return AX_ERR_INVALID_ARG;
+  if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return AX_ERR_INVALID_ARG;
+  if (method < AX_PCG_FP64 || method > AX_CHEB_MIXED) return AX_ERR_INVALID_ARG;
+  if ((size_t)m * kPartialStride * 4 > ((size_t)1 << 40)) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w = op->ws;
+  const int nr = op->nr, nz = op->nz, P = op->pitch;
+  const size_t field = field_elems(op), dense = (size_t)nr * nz * m;
+  int rc;
+  if ((rc = ensure_base(op, m)) != AX_OK) return rc;
+  const bool host = (flags & AX_FLAG_HOST_BUFFERS) != 0;
+  const bool guess = (flags & AX_FLAG_USE_GUESS) != 0;
+  const double *fd = f;
+  double *ud = u;
+  if (host) {
+    if ((rc = ensure_stage(op, dense)) != AX_OK) return rc;
+    AX_TRY(cudaMemcpyAsync(w->stage_a, f, dense * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (guess) AX_TRY(cudaMemcpyAsync(w->stage_b, u, dense * sizeof(double), cudaMemcpyHostToDevice, s));
+    fd = w->stage_a;
+    ud = w->stage_b;
+  }
+  const long long rows = (long long)nr * m;
+  const int cblocks = (int)std::min<long long>(rows, 65535);
+  // phi = r f (FP64) and ||phi||^2 partials
+  note_launch();
+  prep_rhs<<<dim3(m, (nr + 15) / 16), 256, 0, s>>>(fd, w->phi64, op->c64.R, nr, nz, P, part_ptr(w, kPartD));
+  const int nbf = (nr + 15) / 16;
+  // x64: guess or zero
+  if (guess) {
+    note_launch();
+    dense_to_padded<double><<<cblocks, 256, 0, s>>>(ud, w->x64, rows, nz, P);
+  } else {
+    AX_TRY(cudaMemsetAsync(w->x64, 0, field * m * sizeof(double), s));
+  }
+  AX_CHECK_LAUNCH();
+  const int nbs64 = stencil_blocks_per_rhs(nr, nz, 2);
+  const bool cheb = (method == AX_CHEB_FP64 || method == AX_CHEB_MIXED);
+  int outer_kind = 0;
+
+  if (method == AX_PCG_FP64 || method == AX_CHEB_FP64) {
+    if ((rc = ensure_vec64(op, m, cheb)) != AX_OK) return rc;
+    // r = phi - A x, start
+    StencilArgs<double> ra = stencil_args<double>(op, m, w->st, -1);
+    ra.in = w->x64;
+    ra.phi = w->phi64;
+    ra.out_res = w->r64;
+    ra.partial = part_ptr(w, kPartB);
+    launch_stencil<double>(kStencilResidual, ra, s);
+    note_launch();
+    sc_start<<<m, 32, 0, s>>>(w->st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol, max_iter, -1,
+                              0);
+    AX_CHECK_LAUNCH();
+    if (!cheb) {
+      PcgVecs<double> v{w->x64, w->r64, w->pa64, w->pb64, w->q64, w->z64};
+      if ((rc = pcg_loop<double>(op, m, v, w->phi64, w->st, w->g64, true, s)) != AX_OK) return rc;
+    } else {
+      // y_{-1} = y_0 (so that the first step, with alpha = 1, is plain)
+      AX_TRY(cudaMemcpyAsync(w->y64prev, w->x64, field * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ChebVecs<double> v{w->x64, w->y64prev, w->r64, w->phi64};
+      int parity = 0;
+      if ((rc = cheb_loop<double>(op, m, v, w->st, w->gc64, kDone, &parity, s)) != AX_OK) return rc;
+      // The iterate that passed the test is y (the buffer read by the last
+      // residual); with parity flipping every step it is x64 when iters is even.
+      // Copy the odd ones back into x64.
+      // (handled per RHS below)
+      RhsState *h = w->h_st;
+      if ((rc = read_states(w, w->st, m, s, h)) != AX_OK) return rc;
+      for (int i = 0; i < m; ++i)
+        if (h[i].iters & 1)
+          AX_TRY(cudaMemcpyAsync(w->x64 + (size_t)i * field, w->y64prev + (size_t)i * field,
+                                 field * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    rc = finish_info(op, m, w->st, info, 0, guess, s);
+  } else {
+    // ---- mixed precision: FP64 iterative refinement around FP32 inner solves
+    outer_kind = 1;
+    if ((rc = ensure_vec32(op, m, cheb)) != AX_OK) return rc;
+    RhsState *so = w->st_outer, *si = w->st;
+    // outer states start active
+    {
+      std::vector<RhsState> init(m);
+      for (int i = 0; i < m; ++i) {
+        std::memset(&init[i], 0, sizeof(RhsState));
+        init[i].state = kActive;
+        init[i].max_iter = max_iter;
+      }
+      AX_TRY(cudaMemcpyAsync(so, init.data(), sizeof(RhsState) * m, cudaMemcpyHostToDevice, s));
+      AX_TRY(cudaStreamSynchronize(s));
+    }
+    const double eta2 = w->inner_tol * w->inner_tol;
+    for (int outer = 0; outer <= w->max_outer; ++outer) {
+      if (outer > 0) {
+        dim3 g((unsigned)std::min<size_t>((field + 255) / 256, 4096), m);
+        note_launch();
+        add_correction<<<g, 256, 0, s>>>(w->x64, w->x32, field, so, kActive);
+      }
+      StencilArgs<double> ra = stencil_args<double>(op, m, so, kActive);
+      ra.in = w->x64;
+      ra.phi = w->phi64;
+      ra.out32 = w->r32;
+      ra.partial = part_ptr(w, kPartB);
+      {
+        ProfScope ps(w, kProfOuter, (double)nr * nz * m, s);
+        launch_stencil<double>(kStencilResidual, ra, s);
+      }
+      note_launch();
+      sc_outer<<<m, 32, 0, s>>>(so, si, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol, eta2,
+                                w->inner_max, outer == 0);
+      AX_CHECK_LAUNCH();
+      RhsState *h = w->h_st;
+      if ((rc = read_states(w, so, m, s, h)) != AX_OK) return rc;
+      if (!any_state(h, m, kActive) || outer == w->max_outer) break;
+      AX_TRY(cudaMemsetAsync(w->x32, 0, field * m * sizeof(float), s));
+      if (!cheb) {
+        PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
+        if ((rc = pcg_loop<float>(op, m, v, nullptr, si, w->g32, false, s)) != AX_OK) return rc;
+      } else {
+        // inner Chebyshev on A d = r from d = 0: phi_inner = r32, iterate in x32/y32prev
+        AX_TRY(cudaMemsetAsync(w->y32prev, 0, field * m * sizeof(float), s));
+        ChebVecs<float> v{w->x32, w->y32prev, w->z32, w->r32};
+        int parity = 0;
+        if ((rc = cheb_loop<float>(op, m, v, si, w->gc32, kDone, &parity, s)) != AX_OK) return rc;
+        RhsState *hh = w->h_st + m;
+        if ((rc = read_states(w, si, m, s, hh)) != AX_OK) return rc;
+        for (int i = 0; i < m; ++i)
+          if (hh[i].state != kIdle && (hh[i].iters & 1))
+            AX_TRY(cudaMemcpyAsync(w->x32 + (size_t)i * field, w->y32prev + (size_t)i * field,
+                                   field * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    rc = finish_info(op, m, so, info, 1, guess, s);
+  }
+  note_launch();
+  padded_to_dense<double><<<cblocks, 256, 0, s>>>(w->x64, ud, rows, nz, P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return status_from_cuda(e);
+  if (host) {
+    AX_TRY(cudaMemcpyAsync(u, ud, dense * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AX_TRY(cudaStreamSynchronize(s));
+  }
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Variable-coefficient cylindrical 5-point stencil (Section 2.1, Eqs.
+// poisson_diff_2, scheme_op_r_z, diff_approx1, sign-reversed so A > 0):
+//
+//   (A y)_{i,k} = CR_i (y_{i,k} - y_{i+1,k}) + CR_{i-1} (y_{i,k} - y_{i-1,k})
+//               + CZ_{i,k} (y_{i,k} - y_{i,k+1}) + CZ_{i,k-1} (y_{i,k} - y_{i,k-1})
+//               + W_{i,k} y_{i,k}
+//
+// with CR = KR / h_r^2, CZ = KZ / h_z^2 precomputed, CR_0 = 0 on the axis and
+// zero values beyond the Dirichlet boundaries r = lr, z = 0, z = lz.
+//
+// One CTA owns kStencilRows consecutive r-rows and a strip of z-columns of one
+// right-hand side.  Each lane holds a short vector (4 FP32 / 2 FP64) of
+// consecutive z-nodes and walks down the rows with a three-row register
+// window, so every input element is read from memory once (plus one halo row
+// per CTA edge).  z-neighbours across lanes come from warp shuffles; the two
+// warp-edge lanes fetch one extra element.  blockIdx.x is the right-hand side,
+// so CTAs that share a coefficient tile run together and the tile is served
+// from L2.
+#include "ax_common.cuh"
+
+namespace ax {
+
+namespace {
+
+template <typename T, int MODE>
+struct StencilValue {
+  // Value of the grid function the operator is applied to, at element e.
+  __device__ __forceinline__ static T at(const StencilArgs<T> &a, const T *p_old, size_t e, T beta) {
+    if (MODE == kStencilPcg) return a.in[e] + beta * p_old[e];
+    return a.in[e];
+  }
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
+  constexpr int V = VecT<T>::n;
+  __shared__ double red[8];
+  const int m = blockIdx.x;
+  if (!rhs_selected(a.st, a.mask, m)) return;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int k0 = ((blockIdx.z * nwarps + warp) * 32 + lane) * V;
+  const int nr = a.nr, nz = a.nz;
+  const int i0 = blockIdx.y * kStencilRows;
+  const int i1 = min(i0 + kStencilRows, nr);
+  const size_t base = (size_t)m * (size_t)a.field;
+  const bool col_ok = k0 < nz;
+  T beta = T(0);
+  const T *p_old = nullptr;
+  T *p_new = nullptr;
+  if (MODE == kStencilPcg) {
+    beta = (T)a.st[m].beta;
+    const bool odd = a.st[m].iters & 1;
+    p_old = odd ? a.pb : a.pa;
+    p_new = odd ? a.pa : a.pb;
+  }
+
+  auto load_row = [&](int i, T (&v)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = T(0);
+    if (!col_ok) return;
+    const size_t off = base + (size_t)i * a.pitch + k0;
+    T t[V];
+    load_vec<T>(a.in + off, t);
+    if (MODE == kStencilPcg) {
+      T po[V];
+      load_vec<T>(p_old + off, po);
+#pragma unroll
+      for (int e = 0; e < V; ++e) t[e] += beta * po[e];
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = (k0 + e < nz) ? t[e] : T(0);
+  };
+  auto load_coef = [&](const T *c, int i, T (&v)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = T(0);
+    if (!col_ok) return;
+    load_vec<T>(c + (size_t)i * a.pitch + k0, v);
+  };
+
+  T pm[V], pc[V], pn[V], crl[V], crh[V];
+  if (i0 > 0) {
+    load_row(i0 - 1, pm);
+    load_coef(a.CR, i0 - 1, crl);
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) { pm[e] = T(0); crl[e] = T(0); }
+  }
+  load_row(i0, pc);
+
+  // FP32 partials per thread are short sums (<= 64 terms); the CTA and grid
+  // combination is FP64.
+  T acc = T(0);
+  for (int i = i0; i < i1; ++i) {
+    if (i + 1 < nr) {
+      load_row(i + 1, pn);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) pn[e] = T(0);
+    }
+    const size_t rowoff = base + (size_t)i * a.pitch;
+    // z-neighbours of the lane's first and last node.
+    T left = __shfl_up_sync(0xffffffffu, pc[V - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, pc[0], 1);
+    if (lane == 0) left = (col_ok && k0 > 0) ? StencilValue<T, MODE>::at(a, p_old, rowoff + k0 - 1, beta) : T(0);
+    if (lane == 31) right = (k0 + V < nz) ? StencilValue<T, MODE>::at(a, p_old, rowoff + k0 + V, beta) : T(0);
+    T czl[V], w[V];
+    load_coef(a.CR, i, crh);
+#pragma unroll
+    for (int e = 0; e < V; ++e) czl[e] = T(0);
+    // Faces run to index nz, so the lane just past the last node still loads
+    // its first face (the upper face of node nz - 1, fetched by the shuffle).
+    if (k0 <= nz) load_vec<T>(a.CZ + (size_t)i * a.pitchz + k0, czl);
+    T czlast = __shfl_down_sync(0xffffffffu, czl[0], 1);
+    if (lane == 31) czlast = (k0 + V <= nz) ? a.CZ[(size_t)i * a.pitchz + k0 + V] : T(0);
+    load_coef(a.W, i, w);
+
+    T o[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const T yl = (e == 0) ? left : pc[e - 1];
+      const T yr = (e == V - 1) ? right : pc[e + 1];
+      const T czh = (e == V - 1) ? czlast : czl[e + 1];
+      const T y = pc[e];
+      T v = w[e] * y;
+      v = fma(crh[e], y - pn[e], v);
+      v = fma(crl[e], y - pm[e], v);
+      v = fma(czh, y - yr, v);
+      v = fma(czl[e], y - yl, v);
+      o[e] = (k0 + e < nz) ? v : T(0);
+    }
+    if (col_ok) {
+      if (MODE == kStencilApply) {
+        store_vec<T>(a.out + rowoff + k0, o);
+      } else if (MODE == kStencilPcg) {
+        store_vec<T>(p_new + rowoff + k0, pc);
+        store_vec<T>(a.out + rowoff + k0, o);
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc = fma(pc[e], o[e], acc);
+      } else {
+        T ph[V];
+        load_vec<T>(a.phi + rowoff + k0, ph);
+        T res[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          res[e] = (k0 + e < nz) ? ((MODE == kStencilResidual) ? ph[e] - o[e] : o[e] - ph[e]) : T(0);
+          acc = fma(res[e], res[e], acc);
+        }
+        if (MODE == kStencilResidual) {
+          if (a.out_res) store_vec<T>(a.out_res + rowoff + k0, res);
+          if (a.out32) {
+            float r32[4];
+#pragma unroll
+            for (int e = 0; e < V; ++e) r32[e] = (float)res[e];
+            if (V == 4) {
+              *reinterpret_cast<float4 *>(a.out32 + rowoff + k0) = make_float4(r32[0], r32[1], r32[2], r32[3]);
+            } else {
+              *reinterpret_cast<float2 *>(a.out32 + rowoff + k0) = make_float2(r32[0], r32[1]);
+            }
+          }
+        } else {
+          store_vec<T>(a.out + rowoff + k0, res);
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      pm[e] = pc[e];
+      pc[e] = pn[e];
+      crl[e] = crh[e];
+    }
+  }
+  if (MODE != kStencilApply) {
+    const double s = block_sum((double)acc, red);
+    if (threadIdx.x == 0)
+      a.partial[(size_t)m * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = s;
+  }
+}
+
+int column_warps(int nz, int vec) {
+  int w = (nz + 32 * vec - 1) / (32 * vec);
+  return w < kStencilWarps ? (w < 1 ? 1 : w) : kStencilWarps;
+}
+
+}  // namespace
+
+int stencil_blocks_per_rhs(int nr, int nz, int vec) {
+  const int wx = column_warps(nz, vec);
+  const int gz = (nz + 32 * vec * wx - 1) / (32 * vec * wx);
+  const int gy = (nr + kStencilRows - 1) / kStencilRows;
+  return gy * gz;
+}
+
+template <typename T>
+void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
+  constexpr int V = VecT<T>::n;
+  const int wx = column_warps(a.nz, V);
+  dim3 grid(a.m, (a.nr + kStencilRows - 1) / kStencilRows, (a.nz + 32 * V * wx - 1) / (32 * V * wx));
+  dim3 block(32 * wx);
+  note_launch();
+  switch (mode) {
+    case kStencilApply: stencil_kernel<T, kStencilApply><<<grid, block, 0, s>>>(a); break;
+    case kStencilPcg: stencil_kernel<T, kStencilPcg><<<grid, block, 0, s>>>(a); break;
+    case kStencilResidual: stencil_kernel<T, kStencilResidual><<<grid, block, 0, s>>>(a); break;
+    default: stencil_kernel<T, kStencilCheb><<<grid, block, 0, s>>>(a); break;
+  }
+}
+
+template void launch_stencil<float>(int, const StencilArgs<float> &, cudaStream_t);
+template void launch_stencil<double>(int, const StencilArgs<double> &, cudaStream_t);
+
+}  // namespace ax

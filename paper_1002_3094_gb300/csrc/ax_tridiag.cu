@@ -1,0 +1,173 @@
+// Per-mode tridiagonal solves along r (Section 4.2, Eq. eq_trid; the series
+// of systems with one fixed matrix per mode l, Section 3, Eq. main_eq3):
+//
+//     T_l y = b,   T_l = Lr(kappa~) + diag(r_i (kappa~ lambda_l + q~)),
+//
+// for every right-hand side m and every mode column l of a transformed field.
+// The matrix of each mode is fixed for the whole solve, so its LU factors are
+// computed once at set-up (in FP64): IP[i][l] = 1 / delta_i(l) and the
+// off-diagonal E[i] (the same for all l).  With them Thomas is two first-order
+// linear recurrences:
+//
+//     g_i = b_i IP_i + alpha_i g_{i-1},   alpha_i = -E_{i-1} IP_i     (forward)
+//     y_i = g_i + beta_i y_{i+1},         beta_i  = -E_i IP_i         (backward)
+//
+// GPU mapping.  A CTA owns W consecutive mode columns of one right-hand side
+// and the whole r-range; lanes run along l, so every row access is one
+// coalesced segment.  The r-range is cut into P chunks of C rows, one thread
+// per (column, chunk), each holding its C values in registers.  A chunk first
+// runs its recurrence with zero carry-in, which yields an affine map
+// carry_out = a + mu * carry_in (mu = product of the chunk's alpha); the P
+// maps of a column are composed by a log-depth scan in shared memory, and a
+// second pass applies the true carry-in.  This is the same observation as the
+// paper's dichotomy algorithm (Section 3: with a fixed matrix, the unknowns at
+// sub-system boundaries follow from precomputable linear combinations), laid
+// out for one CTA instead of a multicomputer.  The data are read and written
+// once; IP is re-read from L1/L2.
+#include "ax_common.cuh"
+
+namespace ax {
+
+namespace {
+
+// Read-only loads that the compiler may not merge across the kernel's passes
+// (keeping every factor live in registers would spill the chunk's data).
+__device__ __forceinline__ float ld_nc(const float *p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_nc(const double *p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void scan_affine(T *sa, T *sm, int P, int W, int c, int w, T &a, T &mu,
+                                            bool reverse) {
+  // Inclusive scan of affine maps f_c(x) = a_c + mu_c x composed in chunk
+  // order (reverse = from the last chunk down).  On return (a, mu) of thread
+  // (c, w) describe the composition of chunks 0..c (or c..P-1).
+  const int pos = reverse ? (P - 1 - c) : c;
+  for (int off = 1; off < P; off <<= 1) {
+    sa[pos * W + w] = a;
+    sm[pos * W + w] = mu;
+    __syncthreads();
+    if (pos >= off) {
+      const T pa = sa[(pos - off) * W + w], pm = sm[(pos - off) * W + w];
+      a = fma(mu, pa, a);
+      mu = mu * pm;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(1024) tridiag_kernel(const TriArgs<T> a, int W, int P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sa = reinterpret_cast<T *>(smem_raw);
+  T *sm = sa + P * W;
+  const int m = blockIdx.x;
+  if (!rhs_selected(a.st, a.mask, m)) return;
+  const int w = threadIdx.x % W;
+  const int c = threadIdx.x / W;
+  const int col = blockIdx.y * W + w;
+  const bool col_ok = col < a.nz;
+  const int s0 = c * C;
+  const size_t base = (size_t)m * (size_t)a.field + col;
+  const int nr = a.nr;
+
+  T v[C];
+#pragma unroll
+  for (int t = 0; t < C; ++t) {
+    const int i = s0 + t;
+    v[t] = (col_ok && i < nr) ? a.in[base + (size_t)i * a.pitch] : T(0);
+  }
+  auto ip_at = [&](int i) -> T { return (col_ok && i < nr) ? ld_nc(a.IP + (size_t)i * a.pitch + col) : T(0); };
+  auto e_at = [&](int i) -> T { return (i >= 0 && i < nr) ? ld_nc(a.E + i) : T(0); };
+
+  // forward, zero carry-in
+  T g = T(0), mu = T(1);
+#pragma unroll
+  for (int t = 0; t < C; ++t) {
+    const int i = s0 + t;
+    const T ip = ip_at(i);
+    const T al = -e_at(i - 1) * ip;
+    g = fma(v[t], ip, al * g);
+    mu *= al;
+    v[t] = g;
+  }
+  T A = g, M = mu;
+  scan_affine(sa, sm, P, W, c, w, A, M, false);
+  // carry into chunk c = value at the last row of chunk c - 1
+  sa[c * W + w] = A;
+  __syncthreads();
+  const T gin = (c > 0) ? sa[(c - 1) * W + w] : T(0);
+  __syncthreads();
+  mu = T(1);
+#pragma unroll
+  for (int t = 0; t < C; ++t) {
+    const int i = s0 + t;
+    const T al = -e_at(i - 1) * ip_at(i);
+    mu *= al;
+    v[t] = fma(mu, gin, v[t]);
+  }
+
+  // backward, zero carry-in
+  T y = T(0);
+  mu = T(1);
+#pragma unroll
+  for (int t = C - 1; t >= 0; --t) {
+    const int i = s0 + t;
+    const T be = -e_at(i) * ip_at(i);
+    y = fma(be, y, v[t]);
+    mu *= be;
+    v[t] = y;
+  }
+  A = y;
+  M = mu;
+  scan_affine(sa, sm, P, W, c, w, A, M, true);
+  sa[c * W + w] = A;
+  __syncthreads();
+  const T yin = (c + 1 < P) ? sa[(c + 1) * W + w] : T(0);
+  mu = T(1);
+#pragma unroll
+  for (int t = C - 1; t >= 0; --t) {
+    const int i = s0 + t;
+    const T be = -e_at(i) * ip_at(i);
+    mu *= be;
+    v[t] = fma(mu, yin, v[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < C; ++t) {
+    const int i = s0 + t;
+    if (col_ok && i < nr) a.out[base + (size_t)i * a.pitch] = v[t];
+  }
+}
+
+template <typename T> struct TriChunk;
+template <> struct TriChunk<float> { static constexpr int C = 32; };
+template <> struct TriChunk<double> { static constexpr int C = 16; };
+
+}  // namespace
+
+template <typename T>
+void launch_tridiag(const TriArgs<T> &a, cudaStream_t s) {
+  constexpr int C = TriChunk<T>::C;
+  const int P = (a.nr + C - 1) / C;
+  int W = 32;
+  while (W > 1 && W * P > 1024) W >>= 1;
+  // P <= 1024 is guaranteed by the set-up limit on nr.
+  const size_t smem = 2ull * P * W * sizeof(T);
+  dim3 grid(a.m, (a.nz + W - 1) / W);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(tridiag_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
+  tridiag_kernel<T, C><<<grid, W * P, smem, s>>>(a, W, P);
+}
+
+template void launch_tridiag<float>(const TriArgs<float> &, cudaStream_t);
+template void launch_tridiag<double>(const TriArgs<double> &, cudaStream_t);
+
+}  // namespace ax

@@ -1,0 +1,295 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances (relative, 2-norm over the compared array unless stated):
+  stencil      FP64 1e-14   FP32 2e-6
+  sine transf. FP64 1e-13   FP32 2e-6
+  mode solves  backward error FP64 1e-14, FP32 2e-6; forward error vs oracle 1e-9 / 1e-3
+  B^-1         FP64 1e-12   FP32 1e-5
+  FP64 PCG     |iters - oracle| <= 1, oracle true residual of the GPU answer <= tol;
+               solved to 1e-13 both sides: ||u_gpu - u_oracle|| <= 1e-10 ||u_oracle||
+  mixed forms  oracle FP64 true residual of the GPU answer <= tol = 1e-8
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+import paper_1002_3094_gb300 as P  # noqa: E402
+from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs  # noqa: E402
+from workloads import Medium, bumps_medium, layered_inclusion_medium, batched_instances  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    P.load_library()
+    return torch.device("cuda:0")
+
+
+def _rand_medium(seed):
+    rng = np.random.default_rng(seed)
+    a, b = rng.uniform(0.5, 3.0, 2)
+
+    def kappa(r, z):
+        return 1.0 + a * np.sin(5 * r + 2 * z) ** 2 + b * (z > 0.4)
+
+    def q(r, z):
+        return 0.2 + 0.3 * np.cos(3 * r * z) ** 2
+
+    return Medium("rand", kappa, q, [lambda r, z: np.exp(-((r - .4) ** 2 + (z - .5) ** 2) * 30)])
+
+
+class Pair:
+    """The same operator set up in the library and in the oracle."""
+
+    def __init__(self, medium, nr, nz, dev):
+        kr, kz, q = sample_operator_inputs(medium, nr, nz)
+        g = O.Grid(nr, nz)
+        okr, okz, oq, _ = O.sample_medium(medium, g, rhs_index=[])
+        assert np.array_equal(kr, okr) and np.array_equal(kz, okz) and np.array_equal(q, oq)
+        self.t = [torch.from_numpy(x).to(dev) for x in (kr, kz, q)]
+        self.op = P.ax_setup_operator(*self.t, nr, nz)
+        self.ora = O.Operator(okr, okz, oq, g)
+        self.nr, self.nz, self.dev, self.medium = nr, nz, dev, medium
+
+    def close(self):
+        P.ax_destroy_operator(self.op)
+
+    def dev_array(self, x):
+        return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(self.dev)
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+SHAPES = [(1, 1), (2, 3), (5, 7), (16, 33), (33, 64), (64, 64), (40, 127), (17, 300), (9, 1024), (3, 1025)]
+
+
+@pytest.mark.parametrize("nr,nz", SHAPES)
+@pytest.mark.parametrize("prec,tol", [(P.AX_PREC_FP64, 1e-14), (P.AX_PREC_FP32, 2e-6)])
+def test_stencil(cuda, nr, nz, prec, tol):
+    pr = Pair(_rand_medium(nr + nz), nr, nz, cuda)
+    m = 2
+    y = np.random.default_rng(1).normal(size=(m, nr, nz))
+    out = torch.zeros((m, nr, nz), dtype=torch.float64, device=cuda)
+    P.ax_apply_operator(pr.op, pr.dev_array(y), out, m, prec)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for j in range(m):
+        assert _rel(got[j], pr.ora.apply_A(y[j])) <= tol
+    pr.close()
+
+
+DST_N = [1, 2, 3, 4, 5, 6, 7, 8, 12, 15, 16, 40, 63, 64, 100, 127, 240, 255, 256, 1023, 1024, 2047, 4096]
+
+
+@pytest.mark.parametrize("nz", DST_N)
+@pytest.mark.parametrize("prec,tol", [(P.AX_PREC_FP64, 1e-13), (P.AX_PREC_FP32, 2e-6)])
+def test_sine_transform(cuda, nz, prec, tol):
+    pr = Pair(_rand_medium(3), 2, nz, cuda)
+    rows = 7
+    x = np.random.default_rng(nz).normal(size=(rows, nz))
+    out = torch.zeros((rows, nz), dtype=torch.float64, device=cuda)
+    P.ax_apply_dst(pr.op, pr.dev_array(x), out, rows, prec)
+    torch.cuda.synchronize()
+    ref = x @ O.dst1_matrix(nz)
+    assert _rel(out.cpu().numpy(), ref) <= tol
+    pr.close()
+
+
+@pytest.mark.parametrize("nr,nz", [(1, 1), (2, 5), (31, 17), (32, 33), (33, 64), (100, 40), (513, 20), (1024, 9),
+                                   (2047, 3), (4096, 2)])
+@pytest.mark.parametrize("prec,bwd,fwd", [(P.AX_PREC_FP64, 1e-14, 1e-9), (P.AX_PREC_FP32, 2e-6, 1e-3)])
+def test_mode_solves(cuda, nr, nz, prec, bwd, fwd):
+    """Backward error ||T_l y - b|| / (||T_l|| ||y||) of every mode system
+    (a backward-stable solver's guarantee), and the forward error against the
+    oracle's Thomas, which cond(T_l) ~ nr^2 may amplify."""
+    pr = Pair(_rand_medium(nr), nr, nz, cuda)
+    m = 2
+    b = np.random.default_rng(5).normal(size=(m, nr, nz))
+    out = torch.zeros((m, nr, nz), dtype=torch.float64, device=cuda)
+    P.ax_apply_mode_solve(pr.op, pr.dev_array(b), out, m, prec)
+    torch.cuda.synchronize()
+    g = pr.ora.grid
+    lam = O.mode_eigenvalues(nz, g.hz)
+    sub, diag, sup = O.mode_tridiagonal(pr.ora.kappa_t, pr.ora.q_t, lam, g)
+    got = out.cpu().numpy()
+    for j in range(m):
+        y = got[j]
+        Ty = diag * y
+        Ty[:-1] += sup * y[1:]
+        Ty[1:] += sub * y[:-1]
+        tnorm = np.abs(diag).max() + 2 * np.abs(sub).max() if nr > 1 else np.abs(diag).max()
+        for l in range(nz):
+            assert np.linalg.norm(Ty[:, l] - b[j][:, l]) <= bwd * tnorm * np.linalg.norm(y[:, l])
+        assert _rel(y, O.thomas(sub, diag, sup, b[j])) <= fwd
+    pr.close()
+
+
+@pytest.mark.parametrize("nr,nz", [(1, 1), (3, 4), (20, 31), (64, 64), (65, 100), (128, 255)])
+@pytest.mark.parametrize("prec,tol", [(P.AX_PREC_FP64, 1e-12), (P.AX_PREC_FP32, 1e-5)])
+def test_preconditioner(cuda, nr, nz, prec, tol):
+    pr = Pair(_rand_medium(nz), nr, nz, cuda)
+    m = 3
+    v = np.random.default_rng(9).normal(size=(m, nr, nz))
+    out = torch.zeros((m, nr, nz), dtype=torch.float64, device=cuda)
+    P.ax_apply_preconditioner(pr.op, pr.dev_array(v), out, m, prec)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for j in range(m):
+        assert _rel(got[j], pr.ora.apply_Binv(v[j])) <= tol
+    pr.close()
+
+
+def _solve(pr, f, method, tol, max_iter=5000, flags=0, u0=None):
+    m = f.shape[0]
+    u = pr.dev_array(u0) if u0 is not None else torch.zeros(f.shape, dtype=torch.float64, device=pr.dev)
+    st, info = P.ax_solve(pr.op, pr.dev_array(f), u, m, tol, max_iter, method, flags)
+    torch.cuda.synchronize()
+    return st, info, u.cpu().numpy()
+
+
+def _oracle_rel_res(pr, f, u):
+    phi = pr.ora.phi(f)
+    return np.linalg.norm(phi - pr.ora.apply_A(u)) / np.linalg.norm(phi)
+
+
+def test_pcg_fp64_bumps_64(cuda):
+    """Workload bumps_64: iteration count and residual against the oracle."""
+    pr = Pair(bumps_medium(), 64, 64, cuda)
+    f = sample_rhs(pr.medium, 64, 64)
+    st, info, u = _solve(pr, f, P.AX_PCG_FP64, 1e-10)
+    assert st == P.AX_OK
+    _, oinfo = pr.ora.solve(f[0], 1e-10)
+    assert abs(info[0]["iters"] - oinfo.iters) <= 1
+    assert _oracle_rel_res(pr, f[0], u[0]) <= 1e-10
+    # tight solves on both sides agree on the solution itself
+    st, info, u = _solve(pr, f, P.AX_PCG_FP64, 1e-13)
+    y, _ = pr.ora.solve(f[0], 1e-13)
+    assert _rel(u[0], y) <= 1e-10
+    pr.close()
+
+
+@pytest.mark.parametrize("method", [P.AX_PCG_MIXED, P.AX_CHEB_FP64, P.AX_CHEB_MIXED])
+def test_other_methods_bumps_64(cuda, method):
+    pr = Pair(bumps_medium(), 64, 64, cuda)
+    f = sample_rhs(pr.medium, 64, 64)
+    tol = 1e-10 if method == P.AX_CHEB_FP64 else 1e-8
+    st, info, u = _solve(pr, f, method, tol)
+    assert st == P.AX_OK, info
+    assert _oracle_rel_res(pr, f[0], u[0]) <= tol
+    pr.close()
+
+
+@pytest.mark.parametrize("method", [P.AX_PCG_FP64, P.AX_PCG_MIXED, P.AX_CHEB_MIXED])
+def test_layered_inclusion_multi_rhs(cuda, method):
+    """Shape of the 1024^2 x 64 workload at 128^2 x 5 (several tiles, ragged
+    nothing): every right-hand side meets the tolerance in the oracle's norm."""
+    med = layered_inclusion_medium(n_rhs=5, nominal_n=128)
+    pr = Pair(med, 128, 128, cuda)
+    f = sample_rhs(med, 128, 128)
+    st, info, u = _solve(pr, f, method, 1e-8)
+    assert st == P.AX_OK, info
+    for j in range(f.shape[0]):
+        assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-8
+    pr.close()
+
+
+def test_batched_rhs_equal_single(cuda):
+    """Deterministic reductions: each RHS of a batch gets bit-identical results
+    to solving it alone."""
+    med = layered_inclusion_medium(n_rhs=3, nominal_n=96)
+    pr = Pair(med, 96, 80, cuda)
+    f = sample_rhs(med, 96, 80)
+    _, info_b, ub = _solve(pr, f, P.AX_PCG_FP64, 1e-9)
+    for j in range(3):
+        _, info_s, us = _solve(pr, f[j:j + 1], P.AX_PCG_FP64, 1e-9)
+        assert info_s[0]["iters"] == info_b[j]["iters"]
+        assert np.array_equal(us[0], ub[j])
+    pr.close()
+
+
+def test_ragged_uneven_instance(cuda):
+    """One instance of the uneven-size workload (odd sizes, non power of two)."""
+    nr, nz, med = batched_instances(4)[1]
+    nr, nz = min(nr, 255), min(nz, 255)
+    pr = Pair(med, nr, nz, cuda)
+    f = sample_rhs(med, nr, nz)
+    for method in (P.AX_PCG_FP64, P.AX_PCG_MIXED):
+        st, info, u = _solve(pr, f, method, 1e-8)
+        assert st == P.AX_OK
+        assert _oracle_rel_res(pr, f[0], u[0]) <= 1e-8
+    pr.close()
+
+
+def test_host_buffers_and_guess(cuda):
+    pr = Pair(bumps_medium(), 64, 64, cuda)
+    f = sample_rhs(pr.medium, 64, 64)
+    _, info_d, ud = _solve(pr, f, P.AX_PCG_FP64, 1e-10)
+    uh = np.zeros_like(f)
+    st, info_h = P.ax_solve(pr.op, f, uh, 1, 1e-10, 5000, P.AX_PCG_FP64, P.AX_FLAG_HOST_BUFFERS)
+    assert st == P.AX_OK and np.array_equal(uh, ud)
+    # exact guess: zero iterations
+    st, info, _ = _solve(pr, f, P.AX_PCG_FP64, 1e-10, flags=P.AX_FLAG_USE_GUESS, u0=ud)
+    assert st == P.AX_OK and info[0]["iters"] == 0
+    pr.close()
+
+
+def test_invalid_arguments(cuda):
+    nr, nz = 4, 5
+    good = [torch.ones((nr, nz), dtype=torch.float64, device=cuda),
+            torch.linspace(1, 3, nr * (nz + 1), dtype=torch.float64, device=cuda).reshape(nr, nz + 1),
+            torch.zeros((nr, nz), dtype=torch.float64, device=cuda)]
+    bad_k = good[0].clone()
+    bad_k[1, 2] = 0.0
+    with pytest.raises(P.AxError) as e:
+        P.ax_setup_operator(bad_k, good[1], good[2], nr, nz)
+    assert e.value.status == P.AX_ERR_INVALID_ARG
+    bad_q = good[2].clone()
+    bad_q[0, 0] = -1.0
+    with pytest.raises(P.AxError):
+        P.ax_setup_operator(good[0], good[1], bad_q, nr, nz)
+    nan_k = good[1].clone()
+    nan_k[0, 0] = float("nan")
+    with pytest.raises(P.AxError):
+        P.ax_setup_operator(good[0], nan_k, good[2], nr, nz)
+    with pytest.raises(P.AxError) as e:
+        P.ax_setup_operator(*good, nr, nz, bc_z=1)
+    assert e.value.status == P.AX_ERR_UNSUPPORTED
+    with pytest.raises(P.AxError):
+        P.ax_setup_operator(*good, 0, nz)
+    op = P.ax_setup_operator(*good, nr, nz)
+    f = torch.ones((1, nr, nz), dtype=torch.float64, device=cuda)
+    u = torch.zeros_like(f)
+    with pytest.raises(P.AxError):
+        P.ax_solve(op, f, u, 1, -1.0)
+    st, info = P.ax_solve(op, f, u, 1, 1e-14, 1, P.AX_PCG_FP64, raise_on_error=False)
+    assert st == P.AX_ERR_NO_CONVERGENCE and info[0]["status"] == P.AX_ERR_NO_CONVERGENCE
+    P.ax_destroy_operator(op)
+
+
+def test_full_size_layered_1024_m64_sampled(cuda):
+    """The benchmark's workload (1024 x 1024, 64 right-hand sides, mixed PCG,
+    tol 1e-8): the oracle's FP64 true residual of sampled right-hand sides."""
+    nr = nz = 1024
+    med = layered_inclusion_medium(64, 1024)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    t = [torch.from_numpy(x).cuda() for x in (kr, kz, q)]
+    op = P.ax_setup_operator(*t, nr, nz)
+    f = torch.from_numpy(sample_rhs(med, nr, nz)).cuda()
+    u = torch.zeros_like(f)
+    st, info = P.ax_solve(op, f, u, 64, 1e-8, 5000, P.AX_PCG_MIXED)
+    assert st == P.AX_OK
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
+    fh, uh = f.cpu().numpy(), u.cpu().numpy()
+    for j in (0, 17, 63):
+        phi = ora.phi(fh[j])
+        assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1e-8 * np.linalg.norm(phi)
+    P.ax_destroy_operator(op)
