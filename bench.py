@@ -53,16 +53,16 @@ def parse_args():
     ap.add_argument("--plain-steps", type=int, default=1, help="timed solves of the plain FP64 comparator")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--rhs", type=int, default=0, help="override the number of right-hand sides (profiling)")
     return ap.parse_args()
 
 
-def workload(name: str, instance: int = 0):
+def workload(name: str, instance: int = 0, rhs: int = 0):
     from workloads import layered_inclusion_medium, large_medium, bumps_medium
     if name == "layered_1024_m64":
-        return 1024, 1024, layered_inclusion_medium(64, 1024, instance=instance)
+        return 1024, 1024, layered_inclusion_medium(rhs or 64, 1024, instance=instance)
     if name == "large_4096_m16":
-        return 4096, 4096, large_medium(16, 4096, instance=instance)
+        return 4096, 4096, large_medium(rhs or 16, 4096, instance=instance)
     if name == "bumps_64":
         return 64, 64, bumps_medium(instance)
     raise SystemExit(f"unknown workload {name}")
@@ -222,7 +222,7 @@ def main():
     P.build()
     P.load_library()
 
-    nr, nz, med = workload(args.workload, instance=rank)
+    nr, nz, med = workload(args.workload, instance=rank, rhs=args.rhs)
     m = med.n_rhs
     kr, kz, q = sample_operator_inputs(med, nr, nz)
     op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz)

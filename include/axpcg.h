@@ -65,7 +65,7 @@ enum {
 enum {
   AX_PCG_FP64 = 0,    /* plain method: PCG, every kernel in FP64 (Section 2.2, Section 4.2)      */
   AX_CHEB_FP64 = 1,   /* three-layer Chebyshev iteration (Eq. main-scheme), FP64                  */
-  AX_PCG_MIXED = 2,   /* FP32 PCG inner solves inside FP64 iterative refinement                   */
+  AX_PCG_MIXED = 2,   /* FP32 PCG with FP64 residual replacement (x accumulated in FP64)          */
   AX_CHEB_MIXED = 3   /* FP32 Chebyshev inner solves inside FP64 iterative refinement             */
 };
 enum {
@@ -120,6 +120,11 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *   "inner_max_iter" cap on the iterations of one inner solve (default 400)
  *   "graph_iters"    iterations captured per CUDA-graph replay (1..256, default 8)
  *   "max_outer"      cap on FP64 refinement steps (default 30)
+ *   "replace_delta"  AX_PCG_MIXED: recursive-residual reduction (relative to the
+ *                    last FP64 true residual) that triggers the next FP64
+ *                    residual replacement (0 < v < 1, default 1e-3)
+ *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
+ *                    inner PCG to "inner_tol", x += d in FP64) instead
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */
 int ax_set_option(ax_operator *op, const char *name, double value);
 

@@ -17,6 +17,7 @@
 // One CTA transforms `rpb` rows of one right-hand side (blockIdx.x = RHS).
 // The fused variants update the CG iterate and residual while loading the
 // rows (forward) or form the (r, z) partial while storing (inverse).
+#pragma once
 #include <cmath>
 #include "ax_common.cuh"
 
@@ -116,6 +117,119 @@ template <typename T> struct Butterfly<T, 5> {
   }
 };
 
+// cos / sin(2 pi j / R), j < R, for the prime radices whose paired DFT is
+// fully unrolled (every coefficient then becomes a constant-bank operand).
+// Filled once per device by dst_prepare_device().
+constexpr int kUnrolledPrimes[] = {7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47};
+constexpr int kNumUnrolled = 12;
+constexpr int prime_offset(int R) {
+  int off = 0;
+  for (int i = 0; i < kNumUnrolled; ++i) {
+    if (kUnrolledPrimes[i] == R) return off;
+    off += 2 * kUnrolledPrimes[i];
+  }
+  return -1;
+}
+constexpr int kPrimeTable = prime_offset(47) + 2 * 47;
+__constant__ float c_prime_f[kPrimeTable];
+__constant__ double c_prime_d[kPrimeTable];
+
+template <typename T> __device__ __forceinline__ T prime_coef(int i);
+template <> __device__ __forceinline__ float prime_coef<float>(int i) { return c_prime_f[i]; }
+template <> __device__ __forceinline__ double prime_coef<double>(int i) { return c_prime_d[i]; }
+
+// One block of G output pairs (o = 1 + B G ...) of the paired radix-R DFT of
+// the R inputs col[r Tn]; B = 0 also produces the DC output.
+template <typename T, int R, int G, int B, typename C>
+__device__ __forceinline__ void prime_item(const C *__restrict__ col, int Tn, C *__restrict__ out, int Ns) {
+  constexpr int H = (R - 1) / 2;
+  constexpr int OFF = prime_offset(R);
+  constexpr int O0 = 1 + B * G;
+  constexpr int GN = (O0 + G - 1 <= H) ? G : (H - O0 + 1);
+  const C t0 = col[0];
+  C A[G], Bq[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) A[g].x = A[g].y = Bq[g].x = Bq[g].y = T(0);
+  C dc;
+  dc.x = dc.y = T(0);
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    // Keeps the compiler from hoisting all R loads ahead of the sums (which
+    // would hold every input in registers at once).
+    asm volatile("" ::: "memory");
+    const C tr = col[r * Tn], tm = col[(R - r) * Tn];
+    const C s = cadd(tr, tm), d = csub(tr, tm);
+    if (B == 0) dc = cadd(dc, s);
+#pragma unroll
+    for (int g = 0; g < GN; ++g) {
+      const int idx = (r * (O0 + g)) % R;
+      const T c = prime_coef<T>(OFF + 2 * idx), sn = prime_coef<T>(OFF + 2 * idx + 1);
+      A[g].x = fma(s.x, c, A[g].x);
+      A[g].y = fma(s.y, c, A[g].y);
+      Bq[g].x = fma(d.x, sn, Bq[g].x);
+      Bq[g].y = fma(d.y, sn, Bq[g].y);
+    }
+  }
+  if (B == 0) out[0] = cadd(t0, dc);
+#pragma unroll
+  for (int g = 0; g < GN; ++g) {
+    const int o = O0 + g;
+    C xo, xm;
+    xo.x = t0.x + A[g].x + Bq[g].y; xo.y = t0.y + A[g].y - Bq[g].x;
+    xm.x = t0.x + A[g].x - Bq[g].y; xm.y = t0.y + A[g].y + Bq[g].x;
+    out[o * Ns] = xo;
+    out[(R - o) * Ns] = xm;
+  }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void twiddle_in_place(C *__restrict__ src, int nrows, int L, int Ns, int R,
+                                                 const T *__restrict__ TW) {
+  const int Tn = L / R;
+  const int tstep = L / (Ns * R);
+  for (int e = threadIdx.x; e < nrows * L; e += blockDim.x) {
+    const int rr = e / L;
+    const int idx = e - rr * L;
+    const int r = idx / Tn;
+    const int j = idx - r * Tn;
+    if (r > 0) {
+      const int k = j % Ns;
+      const int ti = (int)(((long long)k * r * tstep) % L);
+      src[e] = crot(src[e], __ldg(TW + 2 * ti), __ldg(TW + 2 * ti + 1));
+    }
+  }
+  __syncthreads();
+}
+
+// Stage with an unrolled prime radix R.
+template <typename T, int R, typename C>
+__device__ __forceinline__ void prime_stage(C *__restrict__ src, C *__restrict__ dst, int nrows, int L, int Ns,
+                                            const T *__restrict__ TW) {
+  constexpr int H = (R - 1) / 2;
+  constexpr int GMAX = sizeof(T) == 4 ? 10 : 4;  // output pairs per thread (register budget)
+  constexpr int G = H < GMAX ? H : GMAX;
+  constexpr int NB = (H + G - 1) / G;
+  static_assert(NB <= 6, "prime radix too large for the unrolled stage");
+  const int Tn = L / R;
+  if (Ns > 1) twiddle_in_place<T>(src, nrows, L, Ns, R, TW);
+  for (int it = threadIdx.x; it < nrows * NB * Tn; it += blockDim.x) {
+    const int rr = it / (NB * Tn);
+    const int rem = it - rr * NB * Tn;
+    const int b = rem / Tn;
+    const int j = rem - b * Tn;
+    const C *col = src + rr * L + j;
+    C *out = dst + rr * L + (j / Ns) * Ns * R + (j % Ns);
+    switch (b) {
+      case 0: prime_item<T, R, G, 0>(col, Tn, out, Ns); break;
+      case 1: if (NB > 1) prime_item<T, R, G, (NB > 1 ? 1 : 0)>(col, Tn, out, Ns); break;
+      case 2: if (NB > 2) prime_item<T, R, G, (NB > 2 ? 2 : 0)>(col, Tn, out, Ns); break;
+      case 3: if (NB > 3) prime_item<T, R, G, (NB > 3 ? 3 : 0)>(col, Tn, out, Ns); break;
+      case 4: if (NB > 4) prime_item<T, R, G, (NB > 4 ? 4 : 0)>(col, Tn, out, Ns); break;
+      default: if (NB > 5) prime_item<T, R, G, (NB > 5 ? 5 : 0)>(col, Tn, out, Ns); break;
+    }
+  }
+}
+
 // One Stockham stage with a small radix: butterfly j of row rr reads
 // src[j + r T] (T = L / R), applies the twiddles exp(-2 pi i k r / (Ns R)),
 // k = j mod Ns, and writes dst[(j / Ns) Ns R + k + o Ns].
@@ -133,10 +247,17 @@ __device__ __forceinline__ void small_stage(const C *__restrict__ src, C *__rest
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[r * Tn];
     if (Ns > 1) {
+      // w = exp(-2 pi i k / (Ns R)); the r-th twiddle is w^r, formed by
+      // repeated complex multiplication (a few roundings, no further lookups).
+      const int idx = k * tstep;  // < L
+      const T c1 = __ldg(TW + 2 * idx), s1 = __ldg(TW + 2 * idx + 1);
+      T cr = c1, sr = s1;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const int idx = (int)(((long long)k * r * tstep) % L);
-        v[r] = crot(v[r], __ldg(TW + 2 * idx), __ldg(TW + 2 * idx + 1));
+        v[r] = crot(v[r], cr, sr);
+        const T cn = cr * c1 - sr * s1;
+        sr = fma(sr, c1, cr * s1);
+        cr = cn;
       }
     }
     Butterfly<T, R>::run(v);
@@ -281,6 +402,18 @@ __global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
       case 4: small_stage<T, 4>(src, dst, nrows, L, Ns, a.TW); break;
       case 5: small_stage<T, 5>(src, dst, nrows, L, Ns, a.TW); break;
       case 8: small_stage<T, 8>(src, dst, nrows, L, Ns, a.TW); break;
+      case 7: prime_stage<T, 7>(src, dst, nrows, L, Ns, a.TW); break;
+      case 11: prime_stage<T, 11>(src, dst, nrows, L, Ns, a.TW); break;
+      case 13: prime_stage<T, 13>(src, dst, nrows, L, Ns, a.TW); break;
+      case 17: prime_stage<T, 17>(src, dst, nrows, L, Ns, a.TW); break;
+      case 19: prime_stage<T, 19>(src, dst, nrows, L, Ns, a.TW); break;
+      case 23: prime_stage<T, 23>(src, dst, nrows, L, Ns, a.TW); break;
+      case 29: prime_stage<T, 29>(src, dst, nrows, L, Ns, a.TW); break;
+      case 31: prime_stage<T, 31>(src, dst, nrows, L, Ns, a.TW); break;
+      case 37: prime_stage<T, 37>(src, dst, nrows, L, Ns, a.TW); break;
+      case 41: prime_stage<T, 41>(src, dst, nrows, L, Ns, a.TW); break;
+      case 43: prime_stage<T, 43>(src, dst, nrows, L, Ns, a.TW); break;
+      case 47: prime_stage<T, 47>(src, dst, nrows, L, Ns, a.TW); break;
       default: generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
     }
     C *t = src; src = dst; dst = t;
@@ -325,48 +458,5 @@ __global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
 constexpr size_t kDstSmemBudget = 67584;
 
 }  // namespace
-
-int dst_rows_per_block(int L, int elem_bytes) {
-  const size_t per_row = 2ull * L * 2 * elem_bytes;
-  size_t r = kDstSmemBudget / per_row;
-  if (r < 1) r = 1;
-  if (r > 16) r = 16;
-  return (int)r;
-}
-
-size_t dst_smem_bytes(int L, int elem_bytes) {
-  return (size_t)dst_rows_per_block(L, elem_bytes) * 2ull * L * 2 * elem_bytes;
-}
-
-template <typename T>
-void launch_dst(int mode, const DstArgs<T> &a_in, cudaStream_t s) {
-  DstArgs<T> a = a_in;
-  a.rpb = dst_rows_per_block(a.plan.L, (int)sizeof(T));
-  const size_t smem = dst_smem_bytes(a.plan.L, (int)sizeof(T));
-  dim3 grid(a.m, (a.rows + a.rpb - 1) / a.rpb);
-  dim3 block(256);
-  note_launch();
-  switch (mode) {
-    case kDstPlain:
-      cudaFuncSetAttribute(dst_kernel<T, kDstPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      dst_kernel<T, kDstPlain><<<grid, block, smem, s>>>(a);
-      break;
-    case kDstPcgForward:
-      cudaFuncSetAttribute(dst_kernel<T, kDstPcgForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      dst_kernel<T, kDstPcgForward><<<grid, block, smem, s>>>(a);
-      break;
-    case kDstPcgInverse:
-      cudaFuncSetAttribute(dst_kernel<T, kDstPcgInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      dst_kernel<T, kDstPcgInverse><<<grid, block, smem, s>>>(a);
-      break;
-    default:
-      cudaFuncSetAttribute(dst_kernel<T, kDstChebInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      dst_kernel<T, kDstChebInverse><<<grid, block, smem, s>>>(a);
-      break;
-  }
-}
-
-template void launch_dst<float>(int, const DstArgs<float> &, cudaStream_t);
-template void launch_dst<double>(int, const DstArgs<double> &, cudaStream_t);
 
 }  // namespace ax

@@ -77,6 +77,9 @@ enum { kProfStencil = 0, kProfDstFwd = 1, kProfTridiag = 2, kProfDstInv = 3, kPr
 
 struct ax_operator {
   int nr = 0, nz = 0, pitch = 0, pitchz = 0;
+  // A group operator stacks the coefficient tables of several operators of one
+  // grid shape; right-hand side m then uses table m (strides in elements).
+  long long cstride = 0, czstride = 0, estride = 0;
   double lr = 1, lz = 1, hr = 0, hz = 0;
   double kappa_t = 0, q_t = 0, gamma1 = 0, gamma2 = 0;
   int device = 0;
@@ -99,6 +102,7 @@ enum { kStencilApply = 0, kStencilPcg = 1, kStencilResidual = 2, kStencilCheb = 
 template <typename T>
 struct StencilArgs {
   const T *CR, *CZ, *W;
+  long long cstride, czstride;  // coefficient elements per RHS (0: one operator for all RHS)
   int nr, nz, pitch, pitchz;
   long long field;       // elements per RHS (nr * pitch)
   int m;
@@ -143,12 +147,19 @@ struct DstArgs {
 
 template <typename T>
 void launch_dst(int mode, const DstArgs<T> &a, cudaStream_t s);
+template <>
+void launch_dst<float>(int mode, const DstArgs<float> &a, cudaStream_t s);
+template <>
+void launch_dst<double>(int mode, const DstArgs<double> &a, cudaStream_t s);
 int dst_rows_per_block(int L, int elem_bytes);
+int dst_prepare_device();  // constant tables of the unrolled prime radices (once per device)
+int dst_prepare_f64();
 size_t dst_smem_bytes(int L, int elem_bytes);
 
 template <typename T>
 struct TriArgs {
   const T *IP, *E;
+  long long cstride, estride;   // factor elements per RHS (0: one operator for all RHS)
   int nr, nz, pitch;
   long long field;
   int m;

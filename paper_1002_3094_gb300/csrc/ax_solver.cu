@@ -69,6 +69,8 @@ struct Workspace {
   int inner_max = 400;
   int graph_iters = 8;
   int max_outer = 30;
+  int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
+  double replace_delta = 1e-3;  // residual reduction between FP64 replacements
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
   std::vector<ProfEvent> prof_events;
@@ -454,6 +456,70 @@ __global__ void sc_cheb(RhsState *st, const double *p, int nb, double rho0sq, in
   }
 }
 
+// Mixed PCG with residual replacement: start.  rr = ||phi - A x||^2 (FP64),
+// bb = ||phi||^2; the FP32 iteration runs until its recursive residual falls
+// below thresh2 = max(delta^2 rr_true, (tol/2)^2 bb), then the true residual
+// replaces it.
+__global__ void sc_mixed_start(RhsState *st, const double *prr, int nbr, const double *pbb, int nbb, double tol2,
+                               double delta2, int max_iter) {
+  const int m = blockIdx.x;
+  const double rr = reduce_part(prr + (size_t)m * kPartialStride, nbr);
+  const double bb = reduce_part(pbb + (size_t)m * kPartialStride, nbb);
+  if (threadIdx.x == 0) {
+    RhsState s;
+    memset(&s, 0, sizeof(s));
+    s.rr = rr;
+    s.bb = bb;
+    s.max_iter = max_iter;
+    s.status = AX_OK;
+    if (!isfinite(rr) || !isfinite(bb)) {
+      s.state = kFailed;
+      s.status = AX_ERR_BREAKDOWN;
+    } else if (rr <= tol2 * bb || bb == 0.0) {
+      s.state = kDone;
+    } else {
+      s.state = kActive;
+      s.thresh2 = fmax(delta2 * rr, 0.25 * tol2 * bb);
+    }
+    st[m] = s;
+  }
+}
+
+// Residual replacement: rr = ||phi - A x64||^2 just computed in FP64 for the
+// right-hand sides in kCheck.  Done, failed, or a new threshold (the caller
+// then recomputes z = B^-1 r and resumes with sc_beta).
+__global__ void sc_mixed_replace(RhsState *st, const double *prr, int nbr, double tol2, double delta2) {
+  const int m = blockIdx.x;
+  if (st[m].state != kCheck) return;
+  const double rr = reduce_part(prr + (size_t)m * kPartialStride, nbr);
+  if (threadIdx.x == 0) {
+    RhsState s = st[m];
+    s.rr = rr;
+    s.tmp += 1.0;  // replacements
+    if (!isfinite(rr)) {
+      s.state = kFailed;
+      s.status = AX_ERR_BREAKDOWN;
+    } else if (rr <= tol2 * s.bb) {
+      s.state = kDone;
+    } else if (s.iters >= s.max_iter) {
+      s.state = kFailed;
+      s.status = AX_ERR_NO_CONVERGENCE;
+    } else {
+      s.thresh2 = fmax(delta2 * rr, 0.25 * tol2 * s.bb);
+    }
+    st[m] = s;
+  }
+}
+
+template <typename T>
+__global__ void zero_masked(T *x, size_t field, const RhsState *st, int mask) {
+  const int m = blockIdx.y;
+  if (!rhs_selected(st, mask, m)) return;
+  const size_t b = (size_t)m * field;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < field; e += (size_t)gridDim.x * blockDim.x)
+    x[b + e] = T(0);
+}
+
 // Outer refinement step: rr = ||phi - A x||^2 (FP64).  Converged RHS -> done;
 // the others get an inner solve with reference ||r||^2.
 __global__ void sc_outer(RhsState *so, RhsState *si, const double *prr, int nbr, const double *pbb, int nbb,
@@ -596,6 +662,8 @@ StencilArgs<T> stencil_args(const ax_operator *op, int m, const RhsState *st, in
   a.CR = c.CR;
   a.CZ = c.CZ;
   a.W = c.W;
+  a.cstride = op->cstride;
+  a.czstride = op->czstride;
   a.nr = op->nr;
   a.nz = op->nz;
   a.pitch = op->pitch;
@@ -613,6 +681,8 @@ TriArgs<T> tri_args(const ax_operator *op, int m, const T *in, T *out, const Rhs
   const Coef<T> &c = coef<T>(op);
   a.IP = c.IP;
   a.E = c.E;
+  a.cstride = op->cstride;
+  a.estride = op->estride;
   a.nr = op->nr;
   a.nz = op->nz;
   a.pitch = op->pitch;
@@ -866,6 +936,77 @@ int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphC
   return AX_OK;
 }
 
+// Mixed precision PCG with FP64 residual replacement.  The iteration runs in
+// FP32 (x32 holds the correction accumulated since the last replacement); when
+// a right-hand side's recursive residual passes its threshold it goes to
+// kCheck, x64 += x32, the FP64 true residual phi - A x64 replaces r (rounded
+// to FP32), and the iteration resumes with the same search direction (beta
+// from the new (r, z)).  It stops when the FP64 true residual meets tol.
+int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_iter, cudaStream_t s) {
+  Workspace *w = op->ws;
+  RhsState *st = w->st;
+  const size_t field = field_elems(op);
+  const int nbs64 = stencil_blocks_per_rhs(op->nr, op->nz, 2);
+  const int nbf = (op->nr + 15) / 16;
+  const int nbd = dst_blocks(op, op->nr, (int)sizeof(float));
+  PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
+  dim3 zg((unsigned)std::min<size_t>((field + 255) / 256, 4096), m);
+  auto residual64 = [&](int mask) {
+    StencilArgs<double> ra = stencil_args<double>(op, m, st, mask);
+    ra.in = w->x64;
+    ra.phi = w->phi64;
+    ra.out32 = w->r32;
+    ra.partial = part_ptr(w, kPartB);
+    ProfScope ps(w, kProfOuter, (double)op->nr * op->nz * m, s);
+    launch_stencil<double>(kStencilResidual, ra, s);
+  };
+  residual64(-1);
+  note_launch();
+  sc_mixed_start<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol,
+                                  delta * delta, max_iter);
+  AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * field * m, s));
+  AX_CHECK_LAUNCH();
+  precond_apply<float>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s);
+  note_launch();
+  sc_rho_init<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kActive);
+  AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(float) * field * m, s));
+  AX_CHECK_LAUNCH();
+  const int K = w->graph_iters;
+  const int key = m * 4 + 3;
+  const double per_rhs = (double)op->nr * op->nz;
+  for (int guard = 0; guard < 1000000; ++guard) {
+    int rc = AX_OK;
+    RhsState *h = w->h_st;
+    if (w->profile) {
+      if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+      pcg_iteration<float>(op, m, v, st, w, kCheck, s, per_rhs * count_state(h, m, kActive));
+      AX_CHECK_LAUNCH();
+    } else {
+      rc = run_graph(w, w->g32, key, s, [&](cudaStream_t cs) {
+        for (int k = 0; k < K; ++k) pcg_iteration<float>(op, m, v, st, w, kCheck, cs);
+      });
+    }
+    if (rc != AX_OK) return rc;
+    if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    if (any_state(h, m, kCheck)) {
+      note_launch();
+      add_correction<<<zg, 256, 0, s>>>(w->x64, w->x32, field, st, kCheck);
+      note_launch();
+      zero_masked<float><<<zg, 256, 0, s>>>(w->x32, field, st, kCheck);
+      residual64(kCheck);
+      note_launch();
+      sc_mixed_replace<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, tol * tol, delta * delta);
+      precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), s);
+      note_launch();
+      sc_beta<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
+      AX_CHECK_LAUNCH();
+      if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    }
+    if (!any_state(h, m, kActive)) break;
+  }
+  return AX_OK;
+}
+
 }  // namespace
 }  // namespace ax
 
@@ -948,6 +1089,11 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     prof_collect(w);
     w->profile = value != 0.0;
     for (int k = 0; k < kProfKinds; ++k) w->prof_ms[k] = w->prof_launches[k] = w->prof_units[k] = 0.0;
+  } else if (!strcmp(name, "mixed_restart")) {
+    w->mixed_restart = value != 0.0;
+  } else if (!strcmp(name, "replace_delta")) {
+    if (!(value > 0.0 && value < 1.0)) return AX_ERR_INVALID_ARG;
+    w->replace_delta = value;
   } else if (!strcmp(name, "max_outer")) {
     if (!(value >= 1)) return AX_ERR_INVALID_ARG;
     w->max_outer = (int)value;
@@ -967,6 +1113,10 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   if (nr < 1 || nz < 1 || nr > kMaxNr || nz > kMaxNz) return AX_ERR_INVALID_ARG;
   if (!(g->lr > 0.0) || !(g->lz > 0.0) || !std::isfinite(g->lr) || !std::isfinite(g->lz)) return AX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    const int prc = dst_prepare_device();
+    if (prc != AX_OK) return prc;
+  }
   const size_t nrz = (size_t)nr * nz, nrz1 = (size_t)nr * (nz + 1);
   std::vector<double> kr(nrz), kz(nrz1), qq(nrz);
   AX_TRY(cudaMemcpyAsync(kr.data(), kappa_r, nrz * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1239,9 +1389,15 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     }
     rc = finish_info(op, m, w->st, info, 0, guess, s);
   } else {
-    // ---- mixed precision: FP64 iterative refinement around FP32 inner solves
+    // ---- mixed precision
     outer_kind = 1;
     if ((rc = ensure_vec32(op, m, cheb)) != AX_OK) return rc;
+    if (!cheb && !w->mixed_restart) {
+      // FP32 PCG with FP64 residual replacement
+      if ((rc = pcg_mixed_loop(op, m, tol, w->replace_delta, max_iter, s)) != AX_OK) return rc;
+      rc = finish_info(op, m, w->st, info, 1, guess, s);
+    } else {
+    // FP64 iterative refinement around restarted FP32 inner solves
     RhsState *so = w->st_outer, *si = w->st;
     // outer states start active
     {
@@ -1296,6 +1452,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
       }
     }
     rc = finish_info(op, m, so, info, 1, guess, s);
+    }
   }
   note_launch();
   padded_to_dense<double><<<cblocks, 256, 0, s>>>(w->x64, ud, rows, nz, P);

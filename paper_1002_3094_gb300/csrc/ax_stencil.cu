@@ -46,6 +46,9 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   const int i1 = min(i0 + kStencilRows, nr);
   const size_t base = (size_t)m * (size_t)a.field;
   const bool col_ok = k0 < nz;
+  const T *__restrict__ CR = a.CR + (size_t)m * a.cstride;
+  const T *__restrict__ CZ = a.CZ + (size_t)m * a.czstride;
+  const T *__restrict__ Wc = a.W + (size_t)m * a.cstride;
   T beta = T(0);
   const T *p_old = nullptr;
   T *p_new = nullptr;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   T pm[V], pc[V], pn[V], crl[V], crh[V];
   if (i0 > 0) {
     load_row(i0 - 1, pm);
-    load_coef(a.CR, i0 - 1, crl);
+    load_coef(CR, i0 - 1, crl);
   } else {
 #pragma unroll
     for (int e = 0; e < V; ++e) { pm[e] = T(0); crl[e] = T(0); }
@@ -106,15 +109,15 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     if (lane == 0) left = (col_ok && k0 > 0) ? StencilValue<T, MODE>::at(a, p_old, rowoff + k0 - 1, beta) : T(0);
     if (lane == 31) right = (k0 + V < nz) ? StencilValue<T, MODE>::at(a, p_old, rowoff + k0 + V, beta) : T(0);
     T czl[V], w[V];
-    load_coef(a.CR, i, crh);
+    load_coef(CR, i, crh);
 #pragma unroll
     for (int e = 0; e < V; ++e) czl[e] = T(0);
     // Faces run to index nz, so the lane just past the last node still loads
     // its first face (the upper face of node nz - 1, fetched by the shuffle).
-    if (k0 <= nz) load_vec<T>(a.CZ + (size_t)i * a.pitchz + k0, czl);
+    if (k0 <= nz) load_vec<T>(CZ + (size_t)i * a.pitchz + k0, czl);
     T czlast = __shfl_down_sync(0xffffffffu, czl[0], 1);
-    if (lane == 31) czlast = (k0 + V <= nz) ? a.CZ[(size_t)i * a.pitchz + k0 + V] : T(0);
-    load_coef(a.W, i, w);
+    if (lane == 31) czlast = (k0 + V <= nz) ? CZ[(size_t)i * a.pitchz + k0 + V] : T(0);
+    load_coef(Wc, i, w);
 
     T o[V];
 #pragma unroll

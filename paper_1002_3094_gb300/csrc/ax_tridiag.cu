@@ -43,6 +43,19 @@ __device__ __forceinline__ double ld_nc(const double *p) {
   return v;
 }
 
+// Returns x unchanged, but hides its value from the optimiser, so addresses
+// built from it are recomputed per pass instead of being kept live in
+// registers across passes (which would spill the chunk's data).
+template <typename X>
+__device__ __forceinline__ X launder(X x) {
+  asm volatile("" : "+l"(x));
+  return x;
+}
+__device__ __forceinline__ int launder_i(int x) {
+  asm volatile("" : "+r"(x));
+  return x;
+}
+
 template <typename T>
 __device__ __forceinline__ void scan_affine(T *sa, T *sm, int P, int W, int c, int w, T &a, T &mu,
                                             bool reverse) {
@@ -73,57 +86,74 @@ __global__ void __launch_bounds__(1024) tridiag_kernel(const TriArgs<T> a, int W
   const int w = threadIdx.x % W;
   const int c = threadIdx.x / W;
   const int col = blockIdx.y * W + w;
-  const bool col_ok = col < a.nz;
-  const int s0 = c * C;
-  const size_t base = (size_t)m * (size_t)a.field + col;
   const int nr = a.nr;
+  const int s0 = c * C;
+  // rows of this chunk that exist (0 for padding columns)
+  const int cnt = (col < a.nz) ? max(0, min(C, nr - s0)) : 0;
+  const int pitch = a.pitch;
+  const T *__restrict__ in = a.in + (size_t)m * (size_t)a.field + (size_t)s0 * pitch + col;
+  T *__restrict__ out = a.out + (size_t)m * (size_t)a.field + (size_t)s0 * pitch + col;
+  const T *__restrict__ ipc = a.IP + (size_t)m * a.cstride + (size_t)s0 * pitch + col;
+  const T *__restrict__ E0 = a.E + (size_t)m * a.estride;
+  const T *__restrict__ E = E0 + s0;   // E[t] couples rows s0 + t and s0 + t + 1
+  const T e_before = (s0 > 0 && cnt > 0) ? ld_nc(E0 + s0 - 1) : T(0);
 
   T v[C];
+  {
+  const T *ip_in = launder(in);
+  const int pt = launder_i(pitch);
 #pragma unroll
-  for (int t = 0; t < C; ++t) {
-    const int i = s0 + t;
-    v[t] = (col_ok && i < nr) ? a.in[base + (size_t)i * a.pitch] : T(0);
+  for (int t = 0; t < C; ++t) v[t] = (t < cnt) ? ip_in[t * pt] : T(0);
   }
-  auto ip_at = [&](int i) -> T { return (col_ok && i < nr) ? ld_nc(a.IP + (size_t)i * a.pitch + col) : T(0); };
-  auto e_at = [&](int i) -> T { return (i >= 0 && i < nr) ? ld_nc(a.E + i) : T(0); };
 
-  // forward, zero carry-in
-  T g = T(0), mu = T(1);
+  // forward, zero carry-in: g_t = v_t ip_t + alpha_t g_{t-1}
+  T g = T(0), mu = T(1), eprev = e_before;
+  {
+  const T *ipp = launder(ipc);
+  const int pt = launder_i(pitch);
 #pragma unroll
   for (int t = 0; t < C; ++t) {
-    const int i = s0 + t;
-    const T ip = ip_at(i);
-    const T al = -e_at(i - 1) * ip;
+    const T ip = (t < cnt) ? ld_nc(ipp + t * pt) : T(0);
+    const T al = -eprev * ip;
     g = fma(v[t], ip, al * g);
     mu *= al;
     v[t] = g;
+    eprev = (t < cnt) ? ld_nc(E + t) : T(0);
+  }
   }
   T A = g, M = mu;
   scan_affine(sa, sm, P, W, c, w, A, M, false);
-  // carry into chunk c = value at the last row of chunk c - 1
   sa[c * W + w] = A;
   __syncthreads();
   const T gin = (c > 0) ? sa[(c - 1) * W + w] : T(0);
   __syncthreads();
   mu = T(1);
+  eprev = e_before;
+  {
+  const T *ipp = launder(ipc);
+  const int pt = launder_i(pitch);
 #pragma unroll
   for (int t = 0; t < C; ++t) {
-    const int i = s0 + t;
-    const T al = -e_at(i - 1) * ip_at(i);
-    mu *= al;
+    const T ip = (t < cnt) ? ld_nc(ipp + t * pt) : T(0);
+    mu *= -eprev * ip;
     v[t] = fma(mu, gin, v[t]);
+    eprev = (t < cnt) ? ld_nc(E + t) : T(0);
+  }
   }
 
-  // backward, zero carry-in
+  // backward, zero carry-in: y_t = g_t + beta_t y_{t+1}, beta_t = -E_t ip_t
   T y = T(0);
   mu = T(1);
+  {
+  const T *ipp = launder(ipc);
+  const int pt = launder_i(pitch);
 #pragma unroll
   for (int t = C - 1; t >= 0; --t) {
-    const int i = s0 + t;
-    const T be = -e_at(i) * ip_at(i);
+    const T be = (t < cnt) ? -ld_nc(E + t) * ld_nc(ipp + t * pt) : T(0);
     y = fma(be, y, v[t]);
     mu *= be;
     v[t] = y;
+  }
   }
   A = y;
   M = mu;
@@ -132,39 +162,52 @@ __global__ void __launch_bounds__(1024) tridiag_kernel(const TriArgs<T> a, int W
   __syncthreads();
   const T yin = (c + 1 < P) ? sa[(c + 1) * W + w] : T(0);
   mu = T(1);
+  {
+  const T *ipp = launder(ipc);
+  const int pt = launder_i(pitch);
 #pragma unroll
   for (int t = C - 1; t >= 0; --t) {
-    const int i = s0 + t;
-    const T be = -e_at(i) * ip_at(i);
+    const T be = (t < cnt) ? -ld_nc(E + t) * ld_nc(ipp + t * pt) : T(0);
     mu *= be;
     v[t] = fma(mu, yin, v[t]);
   }
+  }
+  {
+  T *op = launder(out);
+  const int pt = launder_i(pitch);
 #pragma unroll
-  for (int t = 0; t < C; ++t) {
-    const int i = s0 + t;
-    if (col_ok && i < nr) a.out[base + (size_t)i * a.pitch] = v[t];
+  for (int t = 0; t < C; ++t)
+    if (t < cnt) op[t * pt] = v[t];
   }
 }
 
-template <typename T> struct TriChunk;
-template <> struct TriChunk<float> { static constexpr int C = 32; };
-template <> struct TriChunk<double> { static constexpr int C = 16; };
-
 }  // namespace
 
-template <typename T>
-void launch_tridiag(const TriArgs<T> &a, cudaStream_t s) {
-  constexpr int C = TriChunk<T>::C;
+// Chunk length C: short enough that the chunk stays in registers without
+// spilling (16 FP32 / 8 FP64 values); very tall systems use twice that so
+// that a CTA still spans >= 8 mode columns (32-byte row segments).
+template <typename T> struct TriChunk;
+template <> struct TriChunk<float> { static constexpr int small = 16, large = 32, switch_nr = 2048; };
+template <> struct TriChunk<double> { static constexpr int small = 8, large = 16, switch_nr = 1024; };
+
+template <typename T, int C>
+void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
   const int P = (a.nr + C - 1) / C;
   int W = 32;
   while (W > 1 && W * P > 1024) W >>= 1;
-  // P <= 1024 is guaranteed by the set-up limit on nr.
+  // P <= 1024 holds for nr <= 8192 (the set-up limit).
   const size_t smem = 2ull * P * W * sizeof(T);
   dim3 grid(a.m, (a.nz + W - 1) / W);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(tridiag_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  note_launch();
   tridiag_kernel<T, C><<<grid, W * P, smem, s>>>(a, W, P);
+}
+
+template <typename T>
+void launch_tridiag(const TriArgs<T> &a, cudaStream_t s) {
+  note_launch();
+  if (a.nr > TriChunk<T>::switch_nr) launch_tridiag_c<T, TriChunk<T>::large>(a, s);
+  else launch_tridiag_c<T, TriChunk<T>::small>(a, s);
 }
 
 template void launch_tridiag<float>(const TriArgs<float> &, cudaStream_t);

@@ -293,3 +293,26 @@ def test_full_size_layered_1024_m64_sampled(cuda):
         phi = ora.phi(fh[j])
         assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1e-8 * np.linalg.norm(phi)
     P.ax_destroy_operator(op)
+
+
+def test_mixed_replacement_keeps_fp64_iteration_count(cuda):
+    """FP32 PCG with FP64 residual replacement keeps the search direction, so
+    its iteration count stays close to the FP64 method's; the restarted
+    refinement (option mixed_restart) also meets the tolerance."""
+    med = layered_inclusion_medium(n_rhs=4, nominal_n=160)
+    pr = Pair(med, 160, 144, cuda)
+    f = sample_rhs(med, 160, 144)
+    _, i64, _ = _solve(pr, f, P.AX_PCG_FP64, 1e-8)
+    st, imx, u = _solve(pr, f, P.AX_PCG_MIXED, 1e-8)
+    assert st == P.AX_OK
+    for j in range(4):
+        assert imx[j]["iters"] <= 1.2 * i64[j]["iters"] + 4, (imx[j], i64[j])
+        assert imx[j]["outer"] >= 1
+        assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-8
+    P.ax_set_option(pr.op, "mixed_restart", 1)
+    st, irs, u = _solve(pr, f, P.AX_PCG_MIXED, 1e-8)
+    assert st == P.AX_OK
+    for j in range(4):
+        assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-8
+    P.ax_set_option(pr.op, "mixed_restart", 0)
+    pr.close()
