@@ -162,6 +162,21 @@ int ax_apply_mode_solve(ax_operator *op, const double *in, double *out, int32_t 
 int ax_apply_preconditioner(ax_operator *op, const double *in, double *out, int32_t m,
                             int32_t precision, void *stream);
 
+/* out = B^-1 in like ax_apply_preconditioner, but without allocating device
+ * memory.  The paper has no counterpart; this exists for callers that cannot
+ * call cudaMalloc (code running under CUDA-graph stream capture, pools that
+ * own all device memory, loops that must not enter the memory manager).
+ * Staging goes through one 32 MiB array compiled into the library, held on
+ * every GPU that loads it until the process exits.  Needs
+ * 2 * m * nr * pitch * sizeof(T) bytes of it (pitch = nz rounded up to 32,
+ * T = double for AX_PREC_FP64, float for AX_PREC_FP32); larger requests return
+ * AX_ERR_INVALID_ARG and queue nothing.  The first call on a device looks up
+ * the array's device address, so make it before any stream capture.  All calls
+ * share the array: calls whose GPU work may overlap (unordered streams) race
+ * and must be serialised by the caller.  Calls no cudaMalloc or cudaFree. */
+int ax_apply_preconditioner_noalloc(ax_operator *op, const double *in, double *out, int32_t m,
+                                    int32_t precision, void *stream);
+
 /* ---- diagnostics ----------------------------------------------------------
  * Number of CUDA kernels this library has issued in this process (direct
  * launches plus the kernel nodes of replayed graphs). */

@@ -38,7 +38,8 @@ METHODS = {"pcg64": AX_PCG_FP64, "cheb64": AX_CHEB_FP64, "pcg_mixed": AX_PCG_MIX
 
 EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_set_option", "ax_solve",
             "ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
-            "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read")
+            "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read",
+            "ax_apply_preconditioner_noalloc")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "other": 6}
@@ -81,7 +82,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_operator_info.argtypes = [vp] + [ctypes.POINTER(dbl)] * 4
     lib.ax_set_option.argtypes = [vp, ctypes.c_char_p, dbl]
     lib.ax_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
-    for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner"):
+    for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
+                 "ax_apply_preconditioner_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, i32, i32, vp]
     lib.ax_status_string.argtypes = [ctypes.c_int]
     lib.ax_status_string.restype = ctypes.c_char_p
@@ -188,6 +190,12 @@ def ax_apply_mode_solve(op, x, y, m, precision=AX_PREC_FP64, stream=None):
 
 def ax_apply_preconditioner(op, x, y, m, precision=AX_PREC_FP64, stream=None):
     _apply("ax_apply_preconditioner", op, x, y, m, precision, stream)
+
+
+def ax_apply_preconditioner_noalloc(op, x, y, m, precision=AX_PREC_FP64, stream=None):
+    """B^-1 without device allocation: stages through the library's fixed
+    32 MiB array (see include/axpcg.h)."""
+    _apply("ax_apply_preconditioner_noalloc", op, x, y, m, precision, stream)
 
 
 def ax_kernel_launches() -> int:
