@@ -194,10 +194,72 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_batched(args):
+    """Workload batched_256: 256 independent instances, nr and nz drawn from
+    {127, 255, 511, 1023, 2047}, one right-hand side each, solved together by
+    the batched entry point (instances of one grid shape share each launch;
+    shapes run concurrently).  value = all unknowns / wall time of one batched
+    solve; latency = per-instance time to its group's completion."""
+    import numpy as np
+    import torch
+    import paper_1002_3094_gb300 as P
+    from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs
+    from workloads import batched_instances
+    count = args.rhs or 256
+    dev = torch.device("cuda", 0)
+    P.build()
+    P.load_library()
+    ops, fs, us, unknowns = [], [], [], 0
+    for nr, nz, med in batched_instances(count):
+        kr, kz, q = sample_operator_inputs(med, nr, nz)
+        ops.append(P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz))
+        fs.append(torch.from_numpy(sample_rhs(med, nr, nz)[0]).to(dev))
+        us.append(torch.zeros((nr, nz), dtype=torch.float64, device=dev))
+        unknowns += nr * nz
+    batch = P.ax_batch_create(ops)
+    method = P.METHODS[args.method]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        P.ax_batch_solve(batch, fs, us, TOL, 20000, method, stream=stream)
+    torch.cuda.synchronize()
+    launches0 = P.ax_kernel_launches()
+    clocks = ClockSampler(0)
+    lats = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st, info = P.ax_batch_solve(batch, fs, us, TOL, 20000, method, stream=stream)
+        lat, groups = P.ax_batch_latency(batch, len(ops))
+        lats += lat
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    value = unknowns * args.steps / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched_256", "instances": len(ops), "unknowns": unknowns, "groups": groups,
+                       "method": args.method, "tol": TOL},
+            "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
+                           "max": float(max(lats))},
+            "iters": {"max": max(i["iters"] for i in info), "min": min(i["iters"] for i in info)},
+            "max_rel_res": max(i["rel_res"] for i in info),
+            "gpu_launches": P.ax_kernel_launches() - launches0, "clocks": clk}
+    print(json.dumps(line))
+    P.ax_batch_destroy(batch)
+    for op in ops:
+        P.ax_destroy_operator(op)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched_256":
+        run_batched(args)
         return
     # The oracle pool must start before the first CUDA call (spawned workers).
     world = int(os.environ.get("WORLD_SIZE", "1"))

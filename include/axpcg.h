@@ -138,6 +138,29 @@ int ax_set_option(ax_operator *op, const char *name, double value);
 int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
              int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
 
+/* ---- many independent operators (uneven grids) in one batched solve ---------
+ * Operators with the same (nr, nz, lr, lz) form a group whose coefficient
+ * tables are stacked, so each kernel launch serves the whole group with
+ * per-instance convergence masks; groups run concurrently on their own
+ * streams.  The paper has no batched form; it solves one series of right-hand
+ * sides per operator (Eq. main_problem).
+ * ax_batch_create copies the tables of `ops` (the operators stay owned by the
+ * caller and may be destroyed afterwards).  Synchronises `stream`.
+ * ax_batch_solve: f[i], u[i] are device arrays [nr_i][nz_i] of instance i;
+ * methods AX_PCG_FP64 and AX_PCG_MIXED (others: AX_ERR_UNSUPPORTED); info is a
+ * host array [n] (may be NULL).  Blocks until all groups are done.
+ * ax_batch_latency: per-instance wall time (ms) from the start of the last
+ * ax_batch_solve to the completion of the instance's group; *groups = count.
+ * ax_solve_batched = create + solve + destroy. */
+typedef struct ax_batch ax_batch;
+int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch **out);
+int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double tol, int32_t max_iter,
+                   int32_t method, int32_t flags, ax_solve_info *info, void *stream);
+int ax_batch_latency(const ax_batch *b, double *ms, int32_t *groups);
+int ax_batch_destroy(ax_batch *b);
+int ax_solve_batched(ax_operator *const *ops, const double *const *f, double *const *u, int32_t n, double tol,
+                     int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
+
 /* ---- single steps of the hot path, for testing each kernel -----------------
  * All take FP64 device arrays [m][nr][nz]; precision selects the kernel
  * (AX_PREC_FP64 or AX_PREC_FP32 — the FP32 kernels round the input to FP32

@@ -39,7 +39,8 @@ METHODS = {"pcg64": AX_PCG_FP64, "cheb64": AX_CHEB_FP64, "pcg_mixed": AX_PCG_MIX
 EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_set_option", "ax_solve",
             "ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
             "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read",
-            "ax_apply_preconditioner_noalloc")
+            "ax_apply_preconditioner_noalloc", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
+            "ax_batch_destroy", "ax_solve_batched")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "other": 6}
@@ -83,11 +84,18 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_set_option.argtypes = [vp, ctypes.c_char_p, dbl]
     lib.ax_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
     for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
-                 "ax_apply_preconditioner_noalloc"):
+                 "ax_apply_preconditioner_noalloc", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
+            "ax_batch_destroy", "ax_solve_batched"):
         getattr(lib, name).argtypes = [vp, vp, vp, i32, i32, vp]
     lib.ax_status_string.argtypes = [ctypes.c_int]
     lib.ax_status_string.restype = ctypes.c_char_p
     lib.ax_version.restype = ctypes.c_char_p
+    pp = ctypes.POINTER(vp)
+    lib.ax_batch_create.argtypes = [pp, i32, vp, ctypes.POINTER(vp)]
+    lib.ax_batch_solve.argtypes = [vp, pp, pp, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
+    lib.ax_batch_latency.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    lib.ax_batch_destroy.argtypes = [vp]
+    lib.ax_solve_batched.argtypes = [pp, pp, pp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
     lib.ax_kernel_launches.argtypes = []
     lib.ax_kernel_launches.restype = ctypes.c_int64
     lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
@@ -208,3 +216,50 @@ def ax_profile_read(op: int, kind) -> dict:
     vals = [ctypes.c_double() for _ in range(3)]
     _check(load_library().ax_profile_read(op, k, *[ctypes.byref(v) for v in vals]), "ax_profile_read")
     return {"ms": vals[0].value, "launches": vals[1].value, "units": vals[2].value}
+
+
+def _ptr_array(xs):
+    arr = (ctypes.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def ax_batch_create(ops, stream=None) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().ax_batch_create(_ptr_array(ops), len(ops), _stream(stream), ctypes.byref(out)),
+           "ax_batch_create")
+    return out.value
+
+
+def ax_batch_solve(batch: int, fs, us, tol: float, max_iter: int = 10000, method: int = AX_PCG_MIXED,
+                   flags: int = 0, stream=None, raise_on_error: bool = True):
+    n = len(fs)
+    infos = (AxSolveInfo * n)()
+    st = load_library().ax_batch_solve(batch, _ptr_array(fs), _ptr_array(us), tol, max_iter, method, flags, infos,
+                                       _stream(stream))
+    if raise_on_error and st not in (AX_OK, AX_ERR_NO_CONVERGENCE):
+        raise AxError(st, "ax_batch_solve")
+    return st, [i.as_dict() for i in infos]
+
+
+def ax_batch_latency(batch: int, n: int):
+    ms = (ctypes.c_double * n)()
+    g = ctypes.c_int32()
+    _check(load_library().ax_batch_latency(batch, ms, ctypes.byref(g)), "ax_batch_latency")
+    return list(ms), g.value
+
+
+def ax_batch_destroy(batch: int) -> None:
+    load_library().ax_batch_destroy(batch)
+
+
+def ax_solve_batched(ops, fs, us, tol: float, max_iter: int = 10000, method: int = AX_PCG_MIXED, flags: int = 0,
+                     stream=None, raise_on_error: bool = True):
+    n = len(ops)
+    infos = (AxSolveInfo * n)()
+    st = load_library().ax_solve_batched(_ptr_array(ops), _ptr_array(fs), _ptr_array(us), n, tol, max_iter, method,
+                                         flags, infos, _stream(stream))
+    if raise_on_error and st not in (AX_OK, AX_ERR_NO_CONVERGENCE):
+        raise AxError(st, "ax_solve_batched")
+    return st, [i.as_dict() for i in infos]

@@ -201,7 +201,8 @@ __device__ __forceinline__ void twiddle_in_place(C *__restrict__ src, int nrows,
   __syncthreads();
 }
 
-// Stage with an unrolled prime radix R.
+// Stage with an unrolled prime radix R (FP32 only: in FP64 the DFMA rate, not
+// the coefficient loads, bounds the stage, and the unrolled form spills).
 template <typename T, int R, typename C>
 __device__ __forceinline__ void prime_stage(C *__restrict__ src, C *__restrict__ dst, int nrows, int L, int Ns,
                                             const T *__restrict__ TW) {
@@ -272,7 +273,7 @@ __device__ __forceinline__ void small_stage(const C *__restrict__ src, C *__rest
 template <typename T, typename C>
 __device__ __forceinline__ void generic_stage(C *__restrict__ src, C *__restrict__ dst, int nrows, int L,
                                               int Ns, int R, const T *__restrict__ TW) {
-  constexpr int G = 8;
+  constexpr int G = 8;  // output pairs per thread
   const int Tn = L / R;
   if (Ns > 1) {
     const int tstep = L / (Ns * R);
@@ -342,9 +343,14 @@ __device__ __forceinline__ void generic_stage(C *__restrict__ src, C *__restrict
   }
 }
 
+template <typename T> struct DstOcc;
+template <> struct DstOcc<float> { static constexpr int min_blocks = 3; };
+template <> struct DstOcc<double> { static constexpr int min_blocks = 2; };
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
+__global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const DstArgs<T> a) {
   using C = typename CplxT<T>::type;
+  constexpr int V = VecT<T>::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
   const int m = blockIdx.x;
@@ -357,32 +363,46 @@ __global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
   T *pk = reinterpret_cast<T *>(buf0);  // packed real view: pk[rr * 2L + idx] = x_idx
   const size_t base = (size_t)m * (size_t)a.field + (size_t)row0 * a.pitch;
   T alpha = T(0);
-  const T *p = nullptr;
+  const T *__restrict__ p = nullptr;
   if (MODE == kDstPcgForward) {
     alpha = (T)a.st[m].alpha;
     p = (a.st[m].iters & 1) ? a.pa : a.pb;
   }
   T acc = T(0);
 
-  // ---- load rows into the packed odd extension ----
+  // ---- load rows into the packed odd extension (short vectors; padding
+  // columns beyond n hold zeros in every field and stay zero) ----
   for (int rr = 0; rr < nrows; ++rr) {
     const size_t rb = base + (size_t)rr * a.pitch;
     T *px = pk + rr * 2 * L;
-    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
-      const size_t e = rb + kk;
-      T v;
+    for (int k0 = threadIdx.x * V; k0 < n; k0 += blockDim.x * V) {
+      const size_t e = rb + k0;
+      T v[V];
       if (MODE == kDstPcgForward) {
-        const T xv = fma(alpha, p[e], a.x[e]);
-        const T rv = fma(-alpha, a.in[e], a.r[e]);
-        a.x[e] = xv;
-        a.r[e] = rv;
-        acc = fma(rv, rv, acc);
-        v = rv;
+        T xv[V], pv[V], rv[V], qv[V];
+        load_vec<T>(a.x + e, xv);
+        load_vec<T>(p + e, pv);
+        load_vec<T>(a.r + e, rv);
+        load_vec<T>(a.in + e, qv);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          xv[t] = fma(alpha, pv[t], xv[t]);
+          rv[t] = fma(-alpha, qv[t], rv[t]);
+          acc = fma(rv[t], rv[t], acc);
+          v[t] = rv[t];
+        }
+        store_vec<T>(a.x + e, xv);
+        store_vec<T>(a.r + e, rv);
       } else {
-        v = a.in[e];
+        load_vec<T>(a.in + e, v);
       }
-      px[kk + 1] = v;
-      px[2 * L - kk - 1] = -v;
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        if (k0 + t < n) {
+          px[k0 + t + 1] = v[t];
+          px[2 * L - k0 - t - 1] = -v[t];
+        }
+      }
     }
     if (threadIdx.x == 0) {
       px[0] = T(0);
@@ -402,18 +422,18 @@ __global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
       case 4: small_stage<T, 4>(src, dst, nrows, L, Ns, a.TW); break;
       case 5: small_stage<T, 5>(src, dst, nrows, L, Ns, a.TW); break;
       case 8: small_stage<T, 8>(src, dst, nrows, L, Ns, a.TW); break;
-      case 7: prime_stage<T, 7>(src, dst, nrows, L, Ns, a.TW); break;
-      case 11: prime_stage<T, 11>(src, dst, nrows, L, Ns, a.TW); break;
-      case 13: prime_stage<T, 13>(src, dst, nrows, L, Ns, a.TW); break;
-      case 17: prime_stage<T, 17>(src, dst, nrows, L, Ns, a.TW); break;
-      case 19: prime_stage<T, 19>(src, dst, nrows, L, Ns, a.TW); break;
-      case 23: prime_stage<T, 23>(src, dst, nrows, L, Ns, a.TW); break;
-      case 29: prime_stage<T, 29>(src, dst, nrows, L, Ns, a.TW); break;
-      case 31: prime_stage<T, 31>(src, dst, nrows, L, Ns, a.TW); break;
-      case 37: prime_stage<T, 37>(src, dst, nrows, L, Ns, a.TW); break;
-      case 41: prime_stage<T, 41>(src, dst, nrows, L, Ns, a.TW); break;
-      case 43: prime_stage<T, 43>(src, dst, nrows, L, Ns, a.TW); break;
-      case 47: prime_stage<T, 47>(src, dst, nrows, L, Ns, a.TW); break;
+      case 7: if (sizeof(T) == 4) prime_stage<T, 7>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 11: if (sizeof(T) == 4) prime_stage<T, 11>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 13: if (sizeof(T) == 4) prime_stage<T, 13>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 17: if (sizeof(T) == 4) prime_stage<T, 17>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 19: if (sizeof(T) == 4) prime_stage<T, 19>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 23: if (sizeof(T) == 4) prime_stage<T, 23>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 29: if (sizeof(T) == 4) prime_stage<T, 29>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 31: if (sizeof(T) == 4) prime_stage<T, 31>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 37: if (sizeof(T) == 4) prime_stage<T, 37>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 41: if (sizeof(T) == 4) prime_stage<T, 41>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 43: if (sizeof(T) == 4) prime_stage<T, 43>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 47: if (sizeof(T) == 4) prime_stage<T, 47>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
       default: generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
     }
     C *t = src; src = dst; dst = t;
@@ -421,31 +441,54 @@ __global__ void __launch_bounds__(256) dst_kernel(const DstArgs<T> a) {
   }
   __syncthreads();
 
-  // ---- split into the sine coefficients and store ----
+  // ---- split into the sine coefficients and store (columns outer, so the
+  // half-angle table is read once per column for all rows) ----
   const T sc = (T)a.scale;
   T cheb_a = T(0), tau = T(0);
   if (MODE == kDstChebInverse) {
     cheb_a = (T)a.st[m].cheb_a;
     tau = (T)a.tau;
   }
-  for (int rr = 0; rr < nrows; ++rr) {
-    const size_t rb = base + (size_t)rr * a.pitch;
-    const C *Z = src + rr * L;
-    for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
-      const int k = kk + 1;
-      const C zk = Z[k], zm = Z[L - k];
-      const T c = __ldg(a.HW + 2 * k), s = __ldg(a.HW + 2 * k + 1);
-      T v = (zm.y - zk.y) + c * (zk.x - zm.x) + s * (zk.y + zm.y);
-      v *= sc;
-      const size_t e = rb + kk;
+  for (int k0 = threadIdx.x * V; k0 < n; k0 += blockDim.x * V) {
+    T c[V], s[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int k = min(k0 + t + 1, L - 1);
+      c[t] = __ldg(a.HW + 2 * k);
+      s[t] = __ldg(a.HW + 2 * k + 1);
+    }
+    for (int rr = 0; rr < nrows; ++rr) {
+      const C *Z = src + rr * L;
+      T v[V];
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int k = k0 + t + 1;
+        if (k < L) {
+          const C zk = Z[k], zm = Z[L - k];
+          v[t] = ((zm.y - zk.y) + c[t] * (zk.x - zm.x) + s[t] * (zk.y + zm.y)) * sc;
+        } else {
+          v[t] = T(0);
+        }
+      }
+      const size_t e = base + (size_t)rr * a.pitch + k0;
       if (MODE == kDstPlain || MODE == kDstPcgForward) {
-        a.out[e] = v;
+        store_vec<T>(a.out + e, v);
       } else if (MODE == kDstPcgInverse) {
-        a.out[e] = v;
-        acc = fma(a.r[e], v, acc);
+        T rv[V];
+        load_vec<T>(a.r + e, rv);
+        store_vec<T>(a.out + e, v);
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc = fma(rv[t], v[t], acc);
       } else {  // Chebyshev: y_{k+1} = a (y_k - tau B^-1 res) + (1 - a) y_{k-1}
-        const T yb = fma(-tau, v, a.y[e]);
-        a.yprev[e] = fma(cheb_a, yb - a.yprev[e], a.yprev[e]);
+        T yv[V], pv[V];
+        load_vec<T>(a.y + e, yv);
+        load_vec<T>(a.yprev + e, pv);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          const T yb = fma(-tau, v[t], yv[t]);
+          pv[t] = (k0 + t < n) ? fma(cheb_a, yb - pv[t], pv[t]) : T(0);
+        }
+        store_vec<T>(a.yprev + e, pv);
       }
     }
   }

@@ -1466,3 +1466,235 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Batched solve of many independent operators (uneven grids)
+// ===========================================================================
+// Operators with the same grid shape form a group: their coefficient tables
+// and mode-solve factors are stacked into one group operator whose right-hand
+// side m uses table m (per-RHS strides in the kernel arguments), so a single
+// launch of every kernel serves the whole group, with per-instance
+// convergence masks, graph-replayed iterations and deterministic reductions
+// exactly as for one operator with many right-hand sides.  Each group runs
+// its own iteration loop on its own stream and host thread, so groups
+// execute concurrently on the GPU.
+#include <chrono>
+#include <thread>
+
+namespace ax {
+namespace {
+
+struct BatchGroup {
+  ax_operator *gop = nullptr;
+  std::vector<int> members;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  double *f_stack = nullptr, *u_stack = nullptr;  // dense [m][nr][nz]
+};
+
+template <typename T>
+cudaError_t stack_table(T **dst, size_t per, const std::vector<const T *> &src, cudaStream_t s) {
+  cudaError_t e = dalloc(dst, per * src.size());
+  for (size_t i = 0; e == cudaSuccess && i < src.size(); ++i)
+    e = cudaMemcpyAsync(*dst + i * per, src[i], per * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
+template <typename T>
+cudaError_t copy_table(T **dst, const T *src, size_t n, cudaStream_t s) {
+  cudaError_t e = dalloc(dst, n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
+template <typename T>
+cudaError_t build_group_coef(Coef<T> &g, const std::vector<const ax_operator *> &ops, const Coef<T> &(*pick)(const ax_operator *),
+                             cudaStream_t s) {
+  const ax_operator *o = ops[0];
+  const size_t f = (size_t)o->nr * o->pitch, fz = (size_t)o->nr * o->pitchz;
+  std::vector<const T *> cr, cz, w, ip, e;
+  for (auto *op : ops) {
+    const Coef<T> &c = pick(op);
+    cr.push_back(c.CR); cz.push_back(c.CZ); w.push_back(c.W); ip.push_back(c.IP); e.push_back(c.E);
+  }
+  cudaError_t err = stack_table(&g.CR, f, cr, s);
+  if (err == cudaSuccess) err = stack_table(&g.CZ, fz, cz, s);
+  if (err == cudaSuccess) err = stack_table(&g.W, f, w, s);
+  if (err == cudaSuccess) err = stack_table(&g.IP, f, ip, s);
+  if (err == cudaSuccess) err = stack_table(&g.E, (size_t)o->nr, e, s);
+  const Coef<T> &c0 = pick(o);
+  if (err == cudaSuccess) err = copy_table(&g.R, c0.R, (size_t)o->nr, s);
+  if (err == cudaSuccess) err = copy_table(&g.TW, c0.TW, 2 * (size_t)o->plan.L, s);
+  if (err == cudaSuccess) err = copy_table(&g.HW, c0.HW, 2 * (size_t)o->plan.L, s);
+  return err;
+}
+
+const Coef<double> &pick64(const ax_operator *op) { return op->c64; }
+const Coef<float> &pick32(const ax_operator *op) { return op->c32; }
+
+}  // namespace
+}  // namespace ax
+
+struct ax_batch {
+  std::vector<ax::BatchGroup> groups;
+  int n = 0;
+  std::vector<int> nr, nz;
+  std::vector<double> latency_ms;  // per instance, from the last solve
+};
+
+extern "C" {
+
+int ax_batch_destroy(ax_batch *b) {
+  if (!b) return AX_OK;
+  for (auto &g : b->groups) {
+    if (g.gop) ax_destroy_operator(g.gop);
+    dfree(g.f_stack);
+    dfree(g.u_stack);
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.stream) cudaStreamDestroy(g.stream);
+  }
+  delete b;
+  return AX_OK;
+}
+
+int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch **out) {
+  if (!out) return AX_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ops || n < 1) return AX_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ops[i] || ops[i]->cstride != 0) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  ax_batch *b = new ax_batch();
+  b->n = n;
+  for (int i = 0; i < n; ++i) {
+    b->nr.push_back(ops[i]->nr);
+    b->nz.push_back(ops[i]->nz);
+  }
+  // group by grid shape (and domain), in order of first appearance
+  std::vector<int> key_of(n, -1);
+  for (int i = 0; i < n; ++i) {
+    if (key_of[i] >= 0) continue;
+    BatchGroup g;
+    for (int j = i; j < n; ++j) {
+      if (key_of[j] >= 0) continue;
+      const ax_operator *a = ops[i], *c = ops[j];
+      if (a->nr == c->nr && a->nz == c->nz && a->lr == c->lr && a->lz == c->lz) {
+        key_of[j] = (int)b->groups.size();
+        g.members.push_back(j);
+      }
+    }
+    b->groups.push_back(g);
+  }
+  int rc = AX_OK;
+  for (auto &g : b->groups) {
+    std::vector<const ax_operator *> mops;
+    for (int j : g.members) mops.push_back(ops[j]);
+    const ax_operator *o = mops[0];
+    ax_operator *gop = new ax_operator();
+    gop->ws = new Workspace();
+    gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz;
+    gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;
+    gop->kappa_t = o->kappa_t; gop->q_t = o->q_t; gop->gamma1 = o->gamma1; gop->gamma2 = o->gamma2;
+    gop->device = o->device;
+    gop->plan = o->plan;
+    gop->cstride = (long long)o->nr * o->pitch;
+    gop->czstride = (long long)o->nr * o->pitchz;
+    gop->estride = o->nr;
+    g.gop = gop;
+    cudaError_t e = build_group_coef<double>(gop->c64, mops, pick64, s);
+    if (e == cudaSuccess) e = build_group_coef<float>(gop->c32, mops, pick32, s);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&gop->ws->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    const size_t dense = (size_t)o->nr * o->nz * g.members.size();
+    if (e == cudaSuccess) e = dalloc(&g.f_stack, dense);
+    if (e == cudaSuccess) e = dalloc(&g.u_stack, dense);
+    if (e != cudaSuccess) {
+      rc = status_from_cuda(e);
+      break;
+    }
+  }
+  if (rc == AX_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = AX_ERR_CUDA;
+  if (rc != AX_OK) {
+    ax_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return AX_OK;
+}
+
+int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double tol, int32_t max_iter,
+                   int32_t method, int32_t flags, ax_solve_info *info, void *stream) {
+  if (!b || !f || !u) return AX_ERR_INVALID_ARG;
+  if (method != AX_PCG_FP64 && method != AX_PCG_MIXED) return AX_ERR_UNSUPPORTED;
+  if (flags & AX_FLAG_HOST_BUFFERS) return AX_ERR_UNSUPPORTED;
+  for (int i = 0; i < b->n; ++i)
+    if (!f[i] || !u[i]) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t start;
+  if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return AX_ERR_CUDA;
+  cudaEventRecord(start, s);
+  b->latency_ms.assign(b->n, 0.0);
+  std::vector<int> status(b->groups.size(), AX_OK);
+  std::vector<std::vector<ax_solve_info>> ginfo(b->groups.size());
+  const auto t0 = std::chrono::steady_clock::now();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto run = [&](size_t gi) {
+    cudaSetDevice(dev);
+    BatchGroup &g = b->groups[gi];
+    const ax_operator *o = g.gop;
+    const size_t per = (size_t)o->nr * o->nz;
+    const int m = (int)g.members.size();
+    cudaStreamWaitEvent(g.stream, start, 0);
+    for (int k = 0; k < m; ++k) {
+      cudaMemcpyAsync(g.f_stack + k * per, f[g.members[k]], per * sizeof(double), cudaMemcpyDeviceToDevice, g.stream);
+      if (flags & AX_FLAG_USE_GUESS)
+        cudaMemcpyAsync(g.u_stack + k * per, u[g.members[k]], per * sizeof(double), cudaMemcpyDeviceToDevice,
+                        g.stream);
+    }
+    ginfo[gi].resize(m);
+    status[gi] = ax_solve(g.gop, g.f_stack, g.u_stack, m, tol, max_iter, method, flags, ginfo[gi].data(), g.stream);
+    for (int k = 0; k < m; ++k)
+      cudaMemcpyAsync(u[g.members[k]], g.u_stack + k * per, per * sizeof(double), cudaMemcpyDeviceToDevice, g.stream);
+    cudaEventRecord(g.done, g.stream);
+    cudaStreamSynchronize(g.stream);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < m; ++k) b->latency_ms[g.members[k]] = ms;
+  };
+  std::vector<std::thread> th;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) th.emplace_back(run, gi);
+  for (auto &t : th) t.join();
+  for (auto &g : b->groups) cudaStreamWaitEvent(s, g.done, 0);
+  cudaEventDestroy(start);
+  int worst = AX_OK;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const int st = status[gi];
+    if (st != AX_OK && (worst == AX_OK || st > worst)) worst = st;
+    if (info)
+      for (size_t k = 0; k < b->groups[gi].members.size(); ++k) info[b->groups[gi].members[k]] = ginfo[gi][k];
+  }
+  if (cudaGetLastError() != cudaSuccess) return AX_ERR_CUDA;
+  return worst;
+}
+
+int ax_batch_latency(const ax_batch *b, double *ms, int32_t *groups) {
+  if (!b) return AX_ERR_INVALID_ARG;
+  if (groups) *groups = (int32_t)b->groups.size();
+  if (ms)
+    for (int i = 0; i < b->n; ++i) ms[i] = i < (int)b->latency_ms.size() ? b->latency_ms[i] : 0.0;
+  return AX_OK;
+}
+
+int ax_solve_batched(ax_operator *const *ops, const double *const *f, double *const *u, int32_t n, double tol,
+                     int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream) {
+  ax_batch *b = nullptr;
+  int rc = ax_batch_create(ops, n, stream, &b);
+  if (rc != AX_OK) return rc;
+  rc = ax_batch_solve(b, f, u, tol, max_iter, method, flags, info, stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  ax_batch_destroy(b);
+  return rc;
+}
+
+}  // extern "C"

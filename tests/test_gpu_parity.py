@@ -316,3 +316,33 @@ def test_mixed_replacement_keeps_fp64_iteration_count(cuda):
         assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-8
     P.ax_set_option(pr.op, "mixed_restart", 0)
     pr.close()
+
+
+@pytest.mark.parametrize("method", [P.AX_PCG_FP64, P.AX_PCG_MIXED])
+def test_batched_uneven_instances_equal_single_solves(cuda, method):
+    """Instances of the uneven-size workload (sizes reduced to keep the test
+    short; shapes repeat so groups hold several instances): the batched solve
+    gives each instance bit-identical results to solving it alone, and the
+    oracle's true residual meets the tolerance."""
+    insts = batched_instances(7, sizes=(31, 64, 97))
+    pairs, fs, us = [], [], []
+    for nr, nz, med in insts:
+        pr = Pair(med, nr, nz, cuda)
+        pairs.append(pr)
+        fs.append(pr.dev_array(sample_rhs(med, nr, nz)[0]))
+        us.append(torch.zeros((nr, nz), dtype=torch.float64, device=cuda))
+    batch = P.ax_batch_create([p.op for p in pairs])
+    st, info = P.ax_batch_solve(batch, fs, us, 1e-8, 5000, method)
+    torch.cuda.synchronize()
+    assert st == P.AX_OK
+    lat, groups = P.ax_batch_latency(batch, len(pairs))
+    assert groups < len(pairs) and all(x > 0 for x in lat)
+    for j, pr in enumerate(pairs):
+        f = fs[j].cpu().numpy()[None]
+        st1, info1, u1 = _solve(pr, f, method, 1e-8)
+        assert info1[0]["iters"] == info[j]["iters"]
+        assert np.array_equal(u1[0], us[j].cpu().numpy())
+        assert _oracle_rel_res(pr, f[0], u1[0]) <= 1e-8
+    P.ax_batch_destroy(batch)
+    for pr in pairs:
+        pr.close()
