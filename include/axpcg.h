@@ -70,7 +70,11 @@ enum {
 };
 enum {
   AX_FLAG_USE_GUESS = 1,    /* u holds an initial guess on entry (else the start is zero)   */
-  AX_FLAG_HOST_BUFFERS = 4  /* f and u are host pointers; copies are made inside the call   */
+  AX_FLAG_HOST_BUFFERS = 4, /* f and u are host pointers; copies are made inside the call   */
+  AX_FLAG_CHECK_GUESS = 8   /* with AX_FLAG_USE_GUESS: keep a right-hand side's guess only if
+                               its true residual ||phi - A u0|| is below ||phi||, else start
+                               that right-hand side from zero (AX_PCG_FP64, AX_PCG_MIXED;
+                               info.guess_accepted tells which)                              */
 };
 enum { AX_PREC_FP64 = 0, AX_PREC_FP32 = 1 };
 
@@ -118,11 +122,11 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *   "inner_tol"      relative residual reduction of each FP32 inner solve of the
  *                    mixed methods (0 < v < 1, default 1e-4)
  *   "inner_max_iter" cap on the iterations of one inner solve (default 400)
- *   "graph_iters"    iterations captured per CUDA-graph replay (1..256, default 8)
+ *   "graph_iters"    iterations captured per CUDA-graph replay (1..256, default 16)
  *   "max_outer"      cap on FP64 refinement steps (default 30)
  *   "replace_delta"  AX_PCG_MIXED: recursive-residual reduction (relative to the
  *                    last FP64 true residual) that triggers the next FP64
- *                    residual replacement (0 < v < 1, default 1e-3)
+ *                    residual replacement (0 < v < 1, default 1e-2)
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */
@@ -160,6 +164,46 @@ int ax_batch_latency(const ax_batch *b, double *ms, int32_t *groups);
 int ax_batch_destroy(ax_batch *b);
 int ax_solve_batched(ax_operator *const *ops, const double *const *f, double *const *u, int32_t n, double tol,
                      int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
+
+/* ---- learned initial guess --------------------------------------------------
+ * A convolutional encoder-decoder (4 levels, channels c1..c4, default 24, 48,
+ * 96, 192: about 1.0 M parameters) mapping the features (log kappa, q, f / s)
+ * on an hw x hw lattice to u0 / s; BF16 weights and activations, FP32
+ * accumulation, FP32 master weights, Adam.  The paper has no counterpart; the
+ * solver only keeps a proposed u0 if it lowers the initial residual
+ * (AX_FLAG_CHECK_GUESS) and always iterates to the requested tolerance.
+ * Arrays are device pointers: features x [B][3][hw][hw] FP32, outputs and
+ * targets [B][hw][hw] FP32.  Flat parameter order: for each layer (e1a e1b e2a
+ * e2b e3a e3b b1 b2 d3a d3b d2a d2b d1a d1b) weights [3][3][cin][cout] then
+ * biases [cout]; the 1x1 head's weights [c1] then its bias.
+ *   create: hw a multiple of 8; channels NULL for the default; batch_capacity
+ *           the largest B; He-normal initialisation from `seed`.
+ *   forward: y = net(x).
+ *   gradients: loss = mean (net(x) - target)^2 and its gradient (host copy in
+ *           grad_host if not NULL, [num_params]).
+ *   train_step: gradients + one Adam step (beta 0.9 / 0.999, eps 1e-8).
+ *   save / load: header (magic "AXGN", version, hw, channels, count), FP32
+ *           little-endian parameters, FNV-1a 64-bit checksum.
+ *   features: per RHS m, s[m] = max |f_m| and the lattice features (cell
+ *           averages when nr, nz are multiples of hw, else nearest samples) from
+ *           kappa [nr][nz] (e.g. the kappa_r samples), q [nr][nz], f [m][nr][nz].
+ *   lift:   u[m] = s[m] * bilinear interpolation of y[m] onto the grid nodes. */
+int ax_guessnet_create(int32_t hw, const int32_t *channels, int32_t batch_capacity, uint64_t seed, void **net);
+int ax_guessnet_destroy(void *net);
+int64_t ax_guessnet_num_params(void *net);
+int ax_guessnet_get_params(void *net, float *host, int64_t n);
+int ax_guessnet_set_params(void *net, const float *host, int64_t n);
+int ax_guessnet_forward(void *net, const float *x, float *y, int32_t batch, void *stream);
+int ax_guessnet_gradients(void *net, const float *x, const float *target, int32_t batch, float *grad_host,
+                          double *loss, void *stream);
+int ax_guessnet_train_step(void *net, const float *x, const float *target, int32_t batch, float lr,
+                           double *loss, void *stream);
+int ax_guessnet_save(void *net, const char *path);
+int ax_guessnet_load(void *net, const char *path);
+int ax_guessnet_features(const double *kappa, const double *q, const double *f, int32_t m, int32_t nr,
+                         int32_t nz, int32_t hw, float *x, double *scale, void *stream);
+int ax_guessnet_lift(const float *y, int32_t m, int32_t hw, const double *scale, int32_t nr, int32_t nz,
+                     double *u, void *stream);
 
 /* ---- single steps of the hot path, for testing each kernel -----------------
  * All take FP64 device arrays [m][nr][nz]; precision selects the kernel
@@ -217,6 +261,10 @@ int ax_profile_read(ax_operator *op, int32_t kind, double *ms, double *launches,
 
 /* Human-readable name of a status code (static storage). */
 const char *ax_status_string(int status);
+
+/* Name and description of the last CUDA runtime error the library turned into
+ * AX_ERR_CUDA / AX_ERR_OOM (static storage, overwritten by later errors). */
+const char *ax_last_error(void);
 
 /* Library version string (static storage). */
 const char *ax_version(void);

@@ -1,0 +1,151 @@
+"""FP64 reference of the initial-guess network (forward and backward).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The network proposes the starting iterate u0 of the CG solve from (kappa, q,
+f).  The paper has no such network; this module is the plain reference that
+the CUDA training and inference kernels are compared against.  Everything is
+written out with NumPy in FP64: 3x3 "same" convolutions as sums of shifted
+arrays, ReLU, 2x2 average pooling, nearest 2x upsampling, additive skips, a
+1x1 head and a mean-squared-error loss, each with its hand-derived gradient.
+
+Tensor layout: activations (C, H, W); conv weights (3, 3, Cin, Cout) indexed
+[dy + 1, dx + 1, ci, co] with out[co, y, x] = b[co] +
+sum_{dy, dx, ci} w[dy+1, dx+1, ci, co] * in[ci, y+dy, x+dx] (zero padding).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# (name, cin, cout, kind): kind "c" = conv3x3 + ReLU, "s" = conv3x3 + ReLU then
+# add the saved skip of the same level, "h" = 1x1 head without activation.
+def architecture(ch=(24, 48, 96, 192), cin=3):
+    c1, c2, c3, c4 = ch
+    return [
+        ("e1a", cin, c1, "c"), ("e1b", c1, c1, "c"), ("pool", 0, 0, "p"),
+        ("e2a", c1, c2, "c"), ("e2b", c2, c2, "c"), ("pool", 0, 0, "p"),
+        ("e3a", c2, c3, "c"), ("e3b", c3, c3, "c"), ("pool", 0, 0, "p"),
+        ("b1", c3, c4, "c"), ("b2", c4, c4, "c"), ("up", 0, 0, "u"),
+        ("d3a", c4, c3, "s"), ("d3b", c3, c3, "c"), ("up", 0, 0, "u"),
+        ("d2a", c3, c2, "s"), ("d2b", c2, c2, "c"), ("up", 0, 0, "u"),
+        ("d1a", c2, c1, "s"), ("d1b", c1, c1, "c"), ("head", c1, 1, "h"),
+    ]
+
+
+def conv3x3(x, w, b):
+    """Zero-padded 3x3 cross-correlation: out[co] = b[co] + sum w * shifted x."""
+    cin, h, wd = x.shape
+    xp = np.zeros((cin, h + 2, wd + 2))
+    xp[:, 1:-1, 1:-1] = x
+    out = np.zeros((w.shape[3], h, wd)) + b[:, None, None]
+    for dy in range(3):
+        for dx in range(3):
+            patch = xp[:, dy:dy + h, dx:dx + wd]          # in[ci, y + dy - 1, x + dx - 1]
+            out += np.einsum("ihw,io->ohw", patch, w[dy, dx])
+    return out
+
+
+def conv3x3_backward(x, w, gout):
+    """Gradients of conv3x3 with respect to x, w and b."""
+    cin, h, wd = x.shape
+    xp = np.zeros((cin, h + 2, wd + 2))
+    xp[:, 1:-1, 1:-1] = x
+    gw = np.zeros_like(w)
+    gxp = np.zeros_like(xp)
+    for dy in range(3):
+        for dx in range(3):
+            patch = xp[:, dy:dy + h, dx:dx + wd]
+            gw[dy, dx] = np.einsum("ihw,ohw->io", patch, gout)
+            gxp[:, dy:dy + h, dx:dx + wd] += np.einsum("io,ohw->ihw", w[dy, dx], gout)
+    return gxp[:, 1:-1, 1:-1], gw, gout.sum(axis=(1, 2))
+
+
+def pool2(x):
+    c, h, w = x.shape
+    return x.reshape(c, h // 2, 2, w // 2, 2).mean(axis=(2, 4))
+
+
+def pool2_backward(g):
+    return np.repeat(np.repeat(g, 2, axis=1), 2, axis=2) * 0.25
+
+
+def up2(x):
+    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def up2_backward(g):
+    c, h, w = g.shape
+    return g.reshape(c, h // 2, 2, w // 2, 2).sum(axis=(2, 4))
+
+
+def init_params(arch, seed=0):
+    """He-normal weights, zero biases (FP64)."""
+    rng = np.random.default_rng(seed)
+    params = {}
+    for name, cin, cout, kind in arch:
+        if kind in "csh":
+            k = 1 if kind == "h" else 3
+            fan_in = cin * k * k
+            std = np.sqrt(2.0 / fan_in) if kind != "h" else np.sqrt(1.0 / fan_in)
+            w = rng.normal(0.0, std, size=(k, k, cin, cout))
+            params[name] = (w, np.zeros(cout))
+    return params
+
+
+def forward(params, arch, x):
+    """Returns (output (1, H, W), cache for backward)."""
+    cache = []
+    skips = []
+    h = x
+    for name, cin, cout, kind in arch:
+        if kind == "p":
+            skips.append(h)
+            cache.append(("p", None))
+            h = pool2(h)
+        elif kind == "u":
+            cache.append(("u", None))
+            h = up2(h)
+        elif kind in "cs":
+            w, b = params[name]
+            z = conv3x3(h, w, b)
+            a = np.maximum(z, 0.0)
+            cache.append((name, (h, z)))
+            if kind == "s":
+                a = a + skips.pop()
+            h = a
+        else:  # head: 1x1
+            w, b = params[name]
+            cache.append((name, (h, None)))
+            h = np.einsum("ihw,io->ohw", h, w[0, 0]) + b[:, None, None]
+    return h, cache
+
+
+def backward(params, arch, cache, gout):
+    """Gradients of every parameter given d(loss)/d(output)."""
+    grads = {}
+    g = gout
+    skip_grads = []
+    for (name, cin, cout, kind), (cname, saved) in zip(reversed(arch), reversed(cache)):
+        if kind == "h":
+            hin, _ = saved
+            w, _ = params[name]
+            grads[name] = (np.einsum("ihw,ohw->io", hin, g)[None, None], g.sum(axis=(1, 2)))
+            g = np.einsum("io,ohw->ihw", w[0, 0], g)
+        elif kind in "cs":
+            hin, z = saved
+            if kind == "s":
+                skip_grads.append(g)       # the skip input receives the same gradient
+            gz = g * (z > 0.0)
+            gx, gw, gb = conv3x3_backward(hin, params[name][0], gz)
+            grads[name] = (gw, gb)
+            g = gx
+        elif kind == "u":
+            g = up2_backward(g)
+        else:  # pool: the saved activation was also a skip source
+            g = pool2_backward(g) + skip_grads.pop()
+    return grads, g
+
+
+def mse_loss(out, target):
+    d = out - target
+    return float(np.mean(d * d)), 2.0 * d / d.size

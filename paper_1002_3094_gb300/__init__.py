@@ -29,6 +29,7 @@ AX_CHEB_MIXED = 3
 
 AX_FLAG_USE_GUESS = 1
 AX_FLAG_HOST_BUFFERS = 4
+AX_FLAG_CHECK_GUESS = 8
 
 AX_PREC_FP64 = 0
 AX_PREC_FP32 = 1
@@ -40,7 +41,10 @@ EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_
             "ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
             "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read",
             "ax_apply_preconditioner_noalloc", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
-            "ax_batch_destroy", "ax_solve_batched")
+            "ax_batch_destroy", "ax_solve_batched", "ax_last_error",
+            "ax_guessnet_create", "ax_guessnet_destroy", "ax_guessnet_num_params", "ax_guessnet_get_params",
+            "ax_guessnet_set_params", "ax_guessnet_forward", "ax_guessnet_gradients", "ax_guessnet_train_step",
+            "ax_guessnet_save", "ax_guessnet_load", "ax_guessnet_features", "ax_guessnet_lift")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "other": 6}
@@ -61,7 +65,8 @@ class AxSolveInfo(ctypes.Structure):
 
 class AxError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {ax_status_string(status)} (status {status})")
+        extra = f" [{ax_last_error()}]" if status in (AX_ERR_CUDA, AX_ERR_OOM) else ""
+        super().__init__(f"{what}: {ax_status_string(status)} (status {status}){extra}")
         self.status = status
 
 
@@ -84,23 +89,39 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_set_option.argtypes = [vp, ctypes.c_char_p, dbl]
     lib.ax_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
     for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
-                 "ax_apply_preconditioner_noalloc", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
-            "ax_batch_destroy", "ax_solve_batched"):
+                 "ax_apply_preconditioner_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, i32, i32, vp]
+    lib.ax_last_error.argtypes = []
     lib.ax_status_string.argtypes = [ctypes.c_int]
     lib.ax_status_string.restype = ctypes.c_char_p
     lib.ax_version.restype = ctypes.c_char_p
+    lib.ax_last_error.restype = ctypes.c_char_p
     pp = ctypes.POINTER(vp)
     lib.ax_batch_create.argtypes = [pp, i32, vp, ctypes.POINTER(vp)]
     lib.ax_batch_solve.argtypes = [vp, pp, pp, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
     lib.ax_batch_latency.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     lib.ax_batch_destroy.argtypes = [vp]
     lib.ax_solve_batched.argtypes = [pp, pp, pp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.ax_guessnet_create.argtypes = [i32, ctypes.POINTER(i32), i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+    lib.ax_guessnet_destroy.argtypes = [vp]
+    lib.ax_guessnet_num_params.argtypes = [vp]
+    lib.ax_guessnet_num_params.restype = ctypes.c_int64
+    lib.ax_guessnet_get_params.argtypes = [vp, vp, ctypes.c_int64]
+    lib.ax_guessnet_set_params.argtypes = [vp, vp, ctypes.c_int64]
+    lib.ax_guessnet_forward.argtypes = [vp, vp, vp, i32, vp]
+    lib.ax_guessnet_gradients.argtypes = [vp, vp, vp, i32, vp, ctypes.POINTER(dbl), vp]
+    lib.ax_guessnet_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, ctypes.POINTER(dbl), vp]
+    lib.ax_guessnet_save.argtypes = [vp, ctypes.c_char_p]
+    lib.ax_guessnet_load.argtypes = [vp, ctypes.c_char_p]
+    lib.ax_guessnet_features.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp, vp]
+    lib.ax_guessnet_lift.argtypes = [vp, i32, i32, vp, i32, i32, vp, vp]
     lib.ax_kernel_launches.argtypes = []
     lib.ax_kernel_launches.restype = ctypes.c_int64
     lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
     for name in EXPORTED:
-        if name not in ("ax_status_string", "ax_version", "ax_kernel_launches"):
+        if name not in ("ax_status_string", "ax_version", "ax_kernel_launches", "ax_last_error",
+                        "ax_guessnet_num_params"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -136,6 +157,10 @@ def _check(status: int, what: str) -> int:
 
 def ax_status_string(status: int) -> str:
     return load_library().ax_status_string(status).decode()
+
+
+def ax_last_error() -> str:
+    return load_library().ax_last_error().decode()
 
 
 def ax_version() -> str:
@@ -263,3 +288,72 @@ def ax_solve_batched(ops, fs, us, tol: float, max_iter: int = 10000, method: int
     if raise_on_error and st not in (AX_OK, AX_ERR_NO_CONVERGENCE):
         raise AxError(st, "ax_solve_batched")
     return st, [i.as_dict() for i in infos]
+
+
+# ---- learned initial guess ---------------------------------------------------
+def ax_guessnet_create(hw: int, channels=None, batch_capacity: int = 16, seed: int = 0) -> int:
+    out = ctypes.c_void_p()
+    ch = (ctypes.c_int32 * 4)(*channels) if channels is not None else None
+    _check(load_library().ax_guessnet_create(hw, ch, batch_capacity, seed, ctypes.byref(out)), "ax_guessnet_create")
+    return out.value
+
+
+def ax_guessnet_destroy(net: int) -> None:
+    load_library().ax_guessnet_destroy(net)
+
+
+def ax_guessnet_num_params(net: int) -> int:
+    return int(load_library().ax_guessnet_num_params(net))
+
+
+def ax_guessnet_get_params(net: int):
+    import numpy as np
+    n = ax_guessnet_num_params(net)
+    h = np.zeros(n, dtype=np.float32)
+    _check(load_library().ax_guessnet_get_params(net, h.ctypes.data, n), "ax_guessnet_get_params")
+    return h
+
+
+def ax_guessnet_set_params(net: int, flat) -> None:
+    import numpy as np
+    h = np.ascontiguousarray(flat, dtype=np.float32)
+    _check(load_library().ax_guessnet_set_params(net, h.ctypes.data, h.size), "ax_guessnet_set_params")
+
+
+def ax_guessnet_forward(net: int, x, y, batch: int, stream=None) -> None:
+    _check(load_library().ax_guessnet_forward(net, _ptr(x), _ptr(y), batch, _stream(stream)), "ax_guessnet_forward")
+
+
+def ax_guessnet_gradients(net: int, x, target, batch: int, stream=None):
+    """(loss, flat FP32 gradient as numpy)."""
+    import numpy as np
+    g = np.zeros(ax_guessnet_num_params(net), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(load_library().ax_guessnet_gradients(net, _ptr(x), _ptr(target), batch, g.ctypes.data, ctypes.byref(loss),
+                                                _stream(stream)), "ax_guessnet_gradients")
+    return loss.value, g
+
+
+def ax_guessnet_train_step(net: int, x, target, batch: int, lr: float, stream=None) -> float:
+    loss = ctypes.c_double()
+    _check(load_library().ax_guessnet_train_step(net, _ptr(x), _ptr(target), batch, lr, ctypes.byref(loss),
+                                                 _stream(stream)), "ax_guessnet_train_step")
+    return loss.value
+
+
+def ax_guessnet_save(net: int, path: str) -> None:
+    _check(load_library().ax_guessnet_save(net, path.encode()), "ax_guessnet_save")
+
+
+def ax_guessnet_load(net: int, path: str) -> None:
+    _check(load_library().ax_guessnet_load(net, path.encode()), "ax_guessnet_load")
+
+
+def ax_guessnet_features(kappa, q, f, m: int, nr: int, nz: int, hw: int, x, scale, stream=None) -> None:
+    _check(load_library().ax_guessnet_features(_ptr(kappa), _ptr(q), _ptr(f), m, nr, nz, hw, _ptr(x), _ptr(scale),
+                                               _stream(stream)), "ax_guessnet_features")
+
+
+def ax_guessnet_lift(y, m: int, hw: int, scale, nr: int, nz: int, u, stream=None) -> None:
+    _check(load_library().ax_guessnet_lift(_ptr(y), m, hw, _ptr(scale), nr, nz, _ptr(u), _stream(stream)),
+           "ax_guessnet_lift")

@@ -49,14 +49,16 @@ int fill_prime_table(const T (&sym)[N]) {
 
 int dst_rows_per_block(int L, int elem_bytes) {
   const size_t per_row = 2ull * L * 2 * elem_bytes;
-  size_t r = kDstSmemBudget / per_row;
+  size_t r = (kDstSmemBudget - 4 * elem_bytes) / per_row;
   if (r < 1) r = 1;
   if (r > 16) r = 16;
   return (int)r;
 }
 
 size_t dst_smem_bytes(int L, int elem_bytes) {
-  return (size_t)dst_rows_per_block(L, elem_bytes) * 2ull * L * 2 * elem_bytes;
+  // two buffers of rpb rows of L complex values; the second starts on a
+  // 16-byte boundary (one complex of slack)
+  return ((size_t)dst_rows_per_block(L, elem_bytes) * L + 1) * 2ull * 2 * elem_bytes;
 }
 
 int dst_prepare_f32() { return fill_prime_table<float>(c_prime_f); }

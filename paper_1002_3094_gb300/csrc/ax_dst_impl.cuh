@@ -184,18 +184,18 @@ __device__ __forceinline__ void prime_item(const C *__restrict__ col, int Tn, C 
 
 template <typename T, typename C>
 __device__ __forceinline__ void twiddle_in_place(C *__restrict__ src, int nrows, int L, int Ns, int R,
-                                                 const T *__restrict__ TW) {
-  const int Tn = L / R;
+                                                 const FastDiv &tn, const FastDiv &nsd, const T *__restrict__ TW) {
   const int tstep = L / (Ns * R);
-  for (int e = threadIdx.x; e < nrows * L; e += blockDim.x) {
-    const int rr = e / L;
-    const int idx = e - rr * L;
-    const int r = idx / Tn;
-    const int j = idx - r * Tn;
-    if (r > 0) {
-      const int k = j % Ns;
-      const int ti = (int)(((long long)k * r * tstep) % L);
-      src[e] = crot(src[e], __ldg(TW + 2 * ti), __ldg(TW + 2 * ti + 1));
+  for (int rr = 0; rr < nrows; ++rr) {
+    C *row = src + rr * L;
+    for (int idx = threadIdx.x; idx < L; idx += blockDim.x) {
+      const int r = fdiv(idx, tn);
+      const int j = idx - r * tn.d;
+      if (r > 0) {
+        const int k = j - fdiv(j, nsd) * Ns;
+        const int ti = (int)(((long long)k * r * tstep) % L);
+        row[idx] = crot(row[idx], __ldg(TW + 2 * ti), __ldg(TW + 2 * ti + 1));
+      }
     }
   }
   __syncthreads();
@@ -205,28 +205,31 @@ __device__ __forceinline__ void twiddle_in_place(C *__restrict__ src, int nrows,
 // the coefficient loads, bounds the stage, and the unrolled form spills).
 template <typename T, int R, typename C>
 __device__ __forceinline__ void prime_stage(C *__restrict__ src, C *__restrict__ dst, int nrows, int L, int Ns,
-                                            const T *__restrict__ TW) {
+                                            const FastDiv &tn, const FastDiv &nsd, const T *__restrict__ TW) {
   constexpr int H = (R - 1) / 2;
-  constexpr int GMAX = sizeof(T) == 4 ? 10 : 4;  // output pairs per thread (register budget)
-  constexpr int G = H < GMAX ? H : GMAX;
+  constexpr int G = H < 10 ? H : 10;
   constexpr int NB = (H + G - 1) / G;
   static_assert(NB <= 6, "prime radix too large for the unrolled stage");
-  const int Tn = L / R;
-  if (Ns > 1) twiddle_in_place<T>(src, nrows, L, Ns, R, TW);
-  for (int it = threadIdx.x; it < nrows * NB * Tn; it += blockDim.x) {
-    const int rr = it / (NB * Tn);
-    const int rem = it - rr * NB * Tn;
-    const int b = rem / Tn;
-    const int j = rem - b * Tn;
-    const C *col = src + rr * L + j;
-    C *out = dst + rr * L + (j / Ns) * Ns * R + (j % Ns);
-    switch (b) {
-      case 0: prime_item<T, R, G, 0>(col, Tn, out, Ns); break;
-      case 1: if (NB > 1) prime_item<T, R, G, (NB > 1 ? 1 : 0)>(col, Tn, out, Ns); break;
-      case 2: if (NB > 2) prime_item<T, R, G, (NB > 2 ? 2 : 0)>(col, Tn, out, Ns); break;
-      case 3: if (NB > 3) prime_item<T, R, G, (NB > 3 ? 3 : 0)>(col, Tn, out, Ns); break;
-      case 4: if (NB > 4) prime_item<T, R, G, (NB > 4 ? 4 : 0)>(col, Tn, out, Ns); break;
-      default: if (NB > 5) prime_item<T, R, G, (NB > 5 ? 5 : 0)>(col, Tn, out, Ns); break;
+  const int Tn = tn.d;
+  if (Ns > 1) twiddle_in_place<T>(src, nrows, L, Ns, R, tn, nsd, TW);
+  const FastDiv nid = make_fastdiv_dev(NB * Tn);  // items per row
+  {
+    for (int item = threadIdx.x; item < nrows * NB * Tn; item += blockDim.x) {
+      const int rr = fdiv(item, nid);
+      const int it = item - rr * NB * Tn;
+      const int b = fdiv(it, tn);
+      const int j = it - b * Tn;
+      const int q = fdiv(j, nsd);
+      const C *col = src + rr * L + j;
+      C *out = dst + rr * L + q * Ns * R + (j - q * Ns);
+      switch (b) {
+        case 0: prime_item<T, R, G, 0>(col, Tn, out, Ns); break;
+        case 1: if (NB > 1) prime_item<T, R, G, (NB > 1 ? 1 : 0)>(col, Tn, out, Ns); break;
+        case 2: if (NB > 2) prime_item<T, R, G, (NB > 2 ? 2 : 0)>(col, Tn, out, Ns); break;
+        case 3: if (NB > 3) prime_item<T, R, G, (NB > 3 ? 3 : 0)>(col, Tn, out, Ns); break;
+        case 4: if (NB > 4) prime_item<T, R, G, (NB > 4 ? 4 : 0)>(col, Tn, out, Ns); break;
+        default: if (NB > 5) prime_item<T, R, G, (NB > 5 ? 5 : 0)>(col, Tn, out, Ns); break;
+      }
     }
   }
 }
@@ -235,36 +238,40 @@ __device__ __forceinline__ void prime_stage(C *__restrict__ src, C *__restrict__
 // src[j + r T] (T = L / R), applies the twiddles exp(-2 pi i k r / (Ns R)),
 // k = j mod Ns, and writes dst[(j / Ns) Ns R + k + o Ns].
 template <typename T, int R, typename C>
-__device__ __forceinline__ void small_stage(const C *__restrict__ src, C *__restrict__ dst, int nrows,
-                                            int L, int Ns, const T *__restrict__ TW) {
-  const int Tn = L / R;
+__device__ __forceinline__ void small_stage(const C *__restrict__ src, C *__restrict__ dst, int nrows, int L,
+                                            int Ns, const FastDiv &tn, const FastDiv &nsd,
+                                            const T *__restrict__ TW) {
+  const int Tn = tn.d;
   const int tstep = L / (Ns * R);
-  for (int it = threadIdx.x; it < nrows * Tn; it += blockDim.x) {
-    const int rr = it / Tn;
-    const int j = it - rr * Tn;
-    const int k = j % Ns;
-    const C *s = src + rr * L + j;
-    C v[R];
+  {
+    for (int item = threadIdx.x; item < nrows * Tn; item += blockDim.x) {
+      const int rr = fdiv(item, tn);
+      const int j = item - rr * Tn;
+      const int q = fdiv(j, nsd);
+      const int k = j - q * Ns;
+      const C *s = src + rr * L + j;
+      C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[r * Tn];
-    if (Ns > 1) {
-      // w = exp(-2 pi i k / (Ns R)); the r-th twiddle is w^r, formed by
-      // repeated complex multiplication (a few roundings, no further lookups).
-      const int idx = k * tstep;  // < L
-      const T c1 = __ldg(TW + 2 * idx), s1 = __ldg(TW + 2 * idx + 1);
-      T cr = c1, sr = s1;
+      for (int r = 0; r < R; ++r) v[r] = s[r * Tn];
+      if (Ns > 1) {
+        // w = exp(-2 pi i k / (Ns R)); the r-th twiddle is w^r, formed by
+        // repeated complex multiplication (a few roundings, no further lookups).
+        const int idx = k * tstep;  // < L
+        const T c1 = __ldg(TW + 2 * idx), s1 = __ldg(TW + 2 * idx + 1);
+        T cr = c1, sr = s1;
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        v[r] = crot(v[r], cr, sr);
-        const T cn = cr * c1 - sr * s1;
-        sr = fma(sr, c1, cr * s1);
-        cr = cn;
+        for (int r = 1; r < R; ++r) {
+          v[r] = crot(v[r], cr, sr);
+          const T cn = cr * c1 - sr * s1;
+          sr = fma(sr, c1, cr * s1);
+          cr = cn;
+        }
       }
-    }
-    Butterfly<T, R>::run(v);
-    C *d = dst + rr * L + (j / Ns) * Ns * R + k;
+      Butterfly<T, R>::run(v);
+      C *d = dst + rr * L + q * Ns * R + k;
 #pragma unroll
-    for (int o = 0; o < R; ++o) d[o * Ns] = v[o];
+      for (int o = 0; o < R; ++o) d[o * Ns] = v[o];
+    }
   }
 }
 
@@ -272,72 +279,63 @@ __device__ __forceinline__ void small_stage(const C *__restrict__ src, C *__rest
 // place first (skipped on the first stage, where Ns = 1).
 template <typename T, typename C>
 __device__ __forceinline__ void generic_stage(C *__restrict__ src, C *__restrict__ dst, int nrows, int L,
-                                              int Ns, int R, const T *__restrict__ TW) {
+                                              int Ns, int R, const FastDiv &tn, const FastDiv &nsd,
+                                              const T *__restrict__ TW) {
   constexpr int G = 8;  // output pairs per thread
-  const int Tn = L / R;
-  if (Ns > 1) {
-    const int tstep = L / (Ns * R);
-    for (int e = threadIdx.x; e < nrows * L; e += blockDim.x) {
-      const int rr = e / L;
-      const int idx = e - rr * L;
-      const int r = idx / Tn;
-      const int j = idx - r * Tn;
-      if (r > 0) {
-        const int k = j % Ns;
-        const int ti = (int)(((long long)k * r * tstep) % L);
-        src[e] = crot(src[e], __ldg(TW + 2 * ti), __ldg(TW + 2 * ti + 1));
-      }
-    }
-    __syncthreads();
-  }
+  const int Tn = tn.d;
+  if (Ns > 1) twiddle_in_place<T>(src, nrows, L, Ns, R, tn, nsd, TW);
   const int H = (R - 1) / 2;
   const int NB = (H + G - 1) / G;
   const int cstep = L / R;
-  for (int it = threadIdx.x; it < nrows * NB * Tn; it += blockDim.x) {
-    const int rr = it / (NB * Tn);
-    const int rem = it - rr * NB * Tn;
-    const int b = rem / Tn;
-    const int j = rem - b * Tn;
-    const C *col = src + rr * L + j;
-    const C t0 = col[0];
-    C A[G], B[G];
-    int idx[G];
+  const FastDiv nid = make_fastdiv_dev(NB * Tn);  // items per row
+  {
+    for (int item = threadIdx.x; item < nrows * NB * Tn; item += blockDim.x) {
+      const int rr = fdiv(item, nid);
+      const int it = item - rr * NB * Tn;
+      const int b = fdiv(it, tn);
+      const int j = it - b * Tn;
+      const int q = fdiv(j, nsd);
+      const C *col = src + rr * L + j;
+      const C t0 = col[0];
+      C A[G], B[G];
+      int idx[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      A[g].x = A[g].y = B[g].x = B[g].y = T(0);
-      idx[g] = 0;
-    }
-    C dc;
-    dc.x = dc.y = T(0);
-    const int o0 = 1 + b * G;
-    for (int r = 1; r <= H; ++r) {
-      const C tr = col[r * Tn], tm = col[(R - r) * Tn];
-      const C s = cadd(tr, tm), d = csub(tr, tm);
-      dc = cadd(dc, s);
+      for (int g = 0; g < G; ++g) {
+        A[g].x = A[g].y = B[g].x = B[g].y = T(0);
+        idx[g] = 0;
+      }
+      C dc;
+      dc.x = dc.y = T(0);
+      const int o0 = 1 + b * G;
+      for (int r = 1; r <= H; ++r) {
+        const C tr = col[r * Tn], tm = col[(R - r) * Tn];
+        const C s = cadd(tr, tm), d = csub(tr, tm);
+        dc = cadd(dc, s);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int o = o0 + g;
+          int v = idx[g] + o;
+          v = (v >= R) ? v - R : v;
+          idx[g] = v;
+          const T c = __ldg(TW + 2 * v * cstep), sn = __ldg(TW + 2 * v * cstep + 1);
+          A[g].x = fma(s.x, c, A[g].x);
+          A[g].y = fma(s.y, c, A[g].y);
+          B[g].x = fma(d.x, sn, B[g].x);
+          B[g].y = fma(d.y, sn, B[g].y);
+        }
+      }
+      C *out = dst + rr * L + q * Ns * R + (j - q * Ns);
+      if (b == 0) out[0] = cadd(t0, dc);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int o = o0 + g;
-        int v = idx[g] + o;
-        v = (v >= R) ? v - R : v;
-        idx[g] = v;
-        const T c = __ldg(TW + 2 * v * cstep), sn = __ldg(TW + 2 * v * cstep + 1);
-        A[g].x = fma(s.x, c, A[g].x);
-        A[g].y = fma(s.y, c, A[g].y);
-        B[g].x = fma(d.x, sn, B[g].x);
-        B[g].y = fma(d.y, sn, B[g].y);
-      }
-    }
-    C *out = dst + rr * L + (j / Ns) * Ns * R + (j % Ns);
-    if (b == 0) out[0] = cadd(t0, dc);
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int o = o0 + g;
-      if (o <= H) {
-        C xo, xm;
-        xo.x = t0.x + A[g].x + B[g].y; xo.y = t0.y + A[g].y - B[g].x;
-        xm.x = t0.x + A[g].x - B[g].y; xm.y = t0.y + A[g].y + B[g].x;
-        out[o * Ns] = xo;
-        out[(R - o) * Ns] = xm;
+        if (o <= H) {
+          C xo, xm;
+          xo.x = t0.x + A[g].x + B[g].y; xo.y = t0.y + A[g].y - B[g].x;
+          xm.x = t0.x + A[g].x - B[g].y; xm.y = t0.y + A[g].y + B[g].x;
+          out[o * Ns] = xo;
+          out[(R - o) * Ns] = xm;
+        }
       }
     }
   }
@@ -359,7 +357,7 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   const int row0 = blockIdx.y * a.rpb;
   const int nrows = min(a.rpb, a.rows - row0);
   C *buf0 = reinterpret_cast<C *>(smem_raw);
-  C *buf1 = buf0 + a.rpb * L;
+  C *buf1 = buf0 + ((a.rpb * L + 1) & ~1);  // 16-byte aligned (vector staging stores)
   T *pk = reinterpret_cast<T *>(buf0);  // packed real view: pk[rr * 2L + idx] = x_idx
   const size_t base = (size_t)m * (size_t)a.field + (size_t)row0 * a.pitch;
   T alpha = T(0);
@@ -370,20 +368,26 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   }
   T acc = T(0);
 
-  // ---- load rows into the packed odd extension (short vectors; padding
-  // columns beyond n hold zeros in every field and stay zero) ----
+  // ---- load rows: short vectors from global memory into a plain staging
+  // copy of the rows (aligned vector stores into the second buffer), then the
+  // packed odd extension is built from it with unit-stride accesses.
+  // Padding columns beyond n hold zeros in every field and stay zero. ----
+  T *__restrict__ xg = a.x;
+  T *__restrict__ rg = a.r;
+  const T *__restrict__ ing = a.in;
+  const int spitch = (n + 3) & ~3;  // staging row length (16-byte aligned rows)
+  T *stg = reinterpret_cast<T *>(buf1);
   for (int rr = 0; rr < nrows; ++rr) {
     const size_t rb = base + (size_t)rr * a.pitch;
-    T *px = pk + rr * 2 * L;
     for (int k0 = threadIdx.x * V; k0 < n; k0 += blockDim.x * V) {
       const size_t e = rb + k0;
       T v[V];
       if (MODE == kDstPcgForward) {
         T xv[V], pv[V], rv[V], qv[V];
-        load_vec<T>(a.x + e, xv);
+        load_vec<T>(xg + e, xv);
         load_vec<T>(p + e, pv);
-        load_vec<T>(a.r + e, rv);
-        load_vec<T>(a.in + e, qv);
+        load_vec<T>(rg + e, rv);
+        load_vec<T>(ing + e, qv);
 #pragma unroll
         for (int t = 0; t < V; ++t) {
           xv[t] = fma(alpha, pv[t], xv[t]);
@@ -391,18 +395,22 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
           acc = fma(rv[t], rv[t], acc);
           v[t] = rv[t];
         }
-        store_vec<T>(a.x + e, xv);
-        store_vec<T>(a.r + e, rv);
+        store_vec<T>(xg + e, xv);
+        store_vec<T>(rg + e, rv);
       } else {
-        load_vec<T>(a.in + e, v);
+        load_vec<T>(ing + e, v);
       }
-#pragma unroll
-      for (int t = 0; t < V; ++t) {
-        if (k0 + t < n) {
-          px[k0 + t + 1] = v[t];
-          px[2 * L - k0 - t - 1] = -v[t];
-        }
-      }
+      store_vec<T>(stg + rr * spitch + k0, v);
+    }
+  }
+  __syncthreads();
+  for (int rr = 0; rr < nrows; ++rr) {
+    T *px = pk + rr * 2 * L;
+    const T *sr = stg + rr * spitch;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const T v = sr[k];
+      px[k + 1] = v;
+      px[2 * L - k - 1] = -v;
     }
     if (threadIdx.x == 0) {
       px[0] = T(0);
@@ -415,26 +423,27 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   int Ns = 1;
   for (int s = 0; s < a.plan.nstages; ++s) {
     const int R = a.plan.radix[s];
+    const FastDiv tn = a.plan.tn_div[s], nsd = a.plan.ns_div[s];
     __syncthreads();
     switch (R) {
-      case 2: small_stage<T, 2>(src, dst, nrows, L, Ns, a.TW); break;
-      case 3: small_stage<T, 3>(src, dst, nrows, L, Ns, a.TW); break;
-      case 4: small_stage<T, 4>(src, dst, nrows, L, Ns, a.TW); break;
-      case 5: small_stage<T, 5>(src, dst, nrows, L, Ns, a.TW); break;
-      case 8: small_stage<T, 8>(src, dst, nrows, L, Ns, a.TW); break;
-      case 7: if (sizeof(T) == 4) prime_stage<T, 7>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 11: if (sizeof(T) == 4) prime_stage<T, 11>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 13: if (sizeof(T) == 4) prime_stage<T, 13>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 17: if (sizeof(T) == 4) prime_stage<T, 17>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 19: if (sizeof(T) == 4) prime_stage<T, 19>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 23: if (sizeof(T) == 4) prime_stage<T, 23>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 29: if (sizeof(T) == 4) prime_stage<T, 29>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 31: if (sizeof(T) == 4) prime_stage<T, 31>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 37: if (sizeof(T) == 4) prime_stage<T, 37>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 41: if (sizeof(T) == 4) prime_stage<T, 41>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 43: if (sizeof(T) == 4) prime_stage<T, 43>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      case 47: if (sizeof(T) == 4) prime_stage<T, 47>(src, dst, nrows, L, Ns, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
-      default: generic_stage<T>(src, dst, nrows, L, Ns, R, a.TW); break;
+      case 2: small_stage<T, 2>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;
+      case 3: small_stage<T, 3>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;
+      case 4: small_stage<T, 4>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;
+      case 5: small_stage<T, 5>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;
+      case 8: small_stage<T, 8>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;
+      case 7: if (sizeof(T) == 4) prime_stage<T, 7>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 11: if (sizeof(T) == 4) prime_stage<T, 11>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 13: if (sizeof(T) == 4) prime_stage<T, 13>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 17: if (sizeof(T) == 4) prime_stage<T, 17>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 19: if (sizeof(T) == 4) prime_stage<T, 19>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 23: if (sizeof(T) == 4) prime_stage<T, 23>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 29: if (sizeof(T) == 4) prime_stage<T, 29>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 31: if (sizeof(T) == 4) prime_stage<T, 31>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 37: if (sizeof(T) == 4) prime_stage<T, 37>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 41: if (sizeof(T) == 4) prime_stage<T, 41>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 43: if (sizeof(T) == 4) prime_stage<T, 43>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      case 47: if (sizeof(T) == 4) prime_stage<T, 47>(src, dst, nrows, L, Ns, tn, nsd, a.TW); else generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
+      default: generic_stage<T>(src, dst, nrows, L, Ns, R, tn, nsd, a.TW); break;
     }
     C *t = src; src = dst; dst = t;
     Ns *= R;
@@ -444,6 +453,7 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   // ---- split into the sine coefficients and store (columns outer, so the
   // half-angle table is read once per column for all rows) ----
   const T sc = (T)a.scale;
+  T *__restrict__ outg = a.out;
   T cheb_a = T(0), tau = T(0);
   if (MODE == kDstChebInverse) {
     cheb_a = (T)a.st[m].cheb_a;
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
       }
       const size_t e = base + (size_t)rr * a.pitch + k0;
       if (MODE == kDstPlain || MODE == kDstPcgForward) {
-        store_vec<T>(a.out + e, v);
+        store_vec<T>(outg + e, v);
       } else if (MODE == kDstPcgInverse) {
         T rv[V];
         load_vec<T>(a.r + e, rv);

@@ -18,10 +18,46 @@ constexpr int kMaxStages = 24;
 
 // Radix plan of the complex FFT of length L = nz + 1 used by the sine
 // transform.  Odd radices larger than 8 use the generic paired kernel.
+// Division by a runtime constant d (1 <= d < 2^31) for 0 <= n < 2^31:
+// q = (umulhi(n, mul) + n) >> shift, with mul = floor(2^32 (2^shift - d) / d) + 1
+// and shift = ceil(log2 d) (the round-up multiplier method of Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994).
+struct FastDiv {
+  unsigned mul = 0;
+  int shift = 0;
+  int d = 1;
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  f.d = d;
+  if (d <= 1) return f;
+  int l = 0;
+  while ((1ll << l) < d) ++l;
+  f.shift = l;
+  f.mul = (unsigned)((((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d) + 1);
+  return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ FastDiv make_fastdiv_dev(int d) {
+  FastDiv f;
+  f.d = d;
+  if (d <= 1) return f;
+  const int l = 32 - __clz(d - 1);  // ceil(log2 d)
+  f.shift = l;
+  f.mul = (unsigned)((((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d) + 1);
+  return f;
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv &f) {
+  return (int)((__umulhi((unsigned)n, f.mul) + (unsigned)n) >> f.shift);
+}
+#endif
+
 struct FftPlan {
   int L = 0;
   int nstages = 0;
   int radix[kMaxStages] = {0};
+  FastDiv ns_div[kMaxStages];  // Ns of stage s (product of the earlier radices)
+  FastDiv tn_div[kMaxStages];  // L / radix[s]
 };
 
 // Per-precision device tables of one operator.

@@ -24,6 +24,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ax_common.cuh"
@@ -67,10 +68,10 @@ struct Workspace {
   // options
   double inner_tol = 1e-4;
   int inner_max = 400;
-  int graph_iters = 8;
+  int graph_iters = 16;
   int max_outer = 30;
   int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
-  double replace_delta = 1e-3;  // residual reduction between FP64 replacements
+  double replace_delta = 1e-2;  // residual reduction between FP64 replacements
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
   std::vector<ProfEvent> prof_events;
@@ -78,6 +79,11 @@ struct Workspace {
 };
 
 static long long g_launches = 0;
+// Serialises workspace allocation and graph capture across host threads (the
+// batched solve runs one thread per group): an allocation, which may
+// synchronise the device, must never overlap another thread's capture.
+static std::recursive_mutex g_alloc_capture_mutex;
+static char g_last_error[256] = "no error";
 static thread_local bool g_capturing = false;
 void note_launch() {
   if (!g_capturing) __atomic_add_fetch(&g_launches, 1, __ATOMIC_RELAXED);
@@ -87,6 +93,7 @@ namespace {
 
 int status_from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return AX_OK;
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return AX_ERR_OOM;
   return AX_ERR_CUDA;
 }
@@ -146,6 +153,7 @@ void free_base(Workspace *w) {
 size_t field_elems(const ax_operator *op) { return (size_t)op->nr * op->pitch; }
 
 int ensure_base(ax_operator *op, int m) {
+  std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
   Workspace *w = op->ws;
   if (w->mbase >= m) return AX_OK;
   free_base(w);
@@ -161,6 +169,7 @@ int ensure_base(ax_operator *op, int m) {
 }
 
 int ensure_vec64(ax_operator *op, int m, bool cheb) {
+  std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
   Workspace *w = op->ws;
   if (w->m64 >= m && (!cheb || w->y64prev)) return AX_OK;
   free_vectors64(w);
@@ -176,6 +185,7 @@ int ensure_vec64(ax_operator *op, int m, bool cheb) {
 }
 
 int ensure_vec32(ax_operator *op, int m, bool cheb) {
+  std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
   Workspace *w = op->ws;
   if (w->m32 >= m && (!cheb || w->y32prev)) return AX_OK;
   free_vectors32(w);
@@ -192,6 +202,7 @@ int ensure_vec32(ax_operator *op, int m, bool cheb) {
 }
 
 int ensure_stage(ax_operator *op, size_t elems) {
+  std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
   Workspace *w = op->ws;
   if (w->stage_elems >= elems) return AX_OK;
   dfree(w->stage_a);
@@ -204,6 +215,7 @@ int ensure_stage(ax_operator *op, size_t elems) {
 }
 
 int ensure_scratch(ax_operator *op, size_t bytes) {
+  std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
   Workspace *w = op->ws;
   if (w->scratch_bytes >= bytes) return AX_OK;
   if (w->scratch) cudaFree(w->scratch);
@@ -608,7 +620,13 @@ FftPlan make_plan(int L) {
   if (twos == 2) r.push_back(4);
   if (twos == 1) r.push_back(2);
   p.nstages = (int)r.size();
-  for (int i = 0; i < p.nstages && i < kMaxStages; ++i) p.radix[i] = r[i];
+  int ns = 1;
+  for (int i = 0; i < p.nstages && i < kMaxStages; ++i) {
+    p.radix[i] = r[i];
+    p.ns_div[i] = make_fastdiv(ns);
+    p.tn_div[i] = make_fastdiv(L / r[i]);
+    ns *= r[i];
+  }
   return p;
 }
 
@@ -822,6 +840,7 @@ int read_states(Workspace *w, const RhsState *dev, int m, cudaStream_t s, RhsSta
 template <typename F>
 int run_graph(Workspace *w, GraphCache &g, int key, cudaStream_t s, F body) {
   if (g.exec == nullptr || g.key != key) {
+    std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
     free_graph(g);
     cudaGraph_t graph = nullptr;
     AX_TRY(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeRelaxed));
@@ -936,13 +955,39 @@ int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphC
   return AX_OK;
 }
 
+// Initial-guess gate: right-hand sides whose starting iterate does not lower
+// the residual below ||phi|| (rr >= bb after the start kernel) restart from
+// zero.  `restart` re-runs the residual and start kernels for all RHS (the
+// accepted ones recompute the same values).  accepted[i] = 1 if kept.
+template <typename F>
+int gate_guess(ax_operator *op, int m, const RhsState *st, std::vector<int> &accepted, cudaStream_t s, F restart) {
+  Workspace *w = op->ws;
+  int rc = read_states(w, st, m, s, w->h_st);
+  if (rc != AX_OK) return rc;
+  const size_t field = field_elems(op);
+  bool any = false;
+  for (int i = 0; i < m; ++i) {
+    const RhsState &h = w->h_st[i];
+    const bool ok = std::isfinite(h.rr) && h.rr < h.bb;
+    accepted[i] = ok ? 1 : 0;
+    if (!ok) {
+      any = true;
+      AX_TRY(cudaMemsetAsync(w->x64 + (size_t)i * field, 0, field * sizeof(double), s));
+    }
+  }
+  if (any) restart();
+  AX_CHECK_LAUNCH();
+  return AX_OK;
+}
+
 // Mixed precision PCG with FP64 residual replacement.  The iteration runs in
 // FP32 (x32 holds the correction accumulated since the last replacement); when
 // a right-hand side's recursive residual passes its threshold it goes to
 // kCheck, x64 += x32, the FP64 true residual phi - A x64 replaces r (rounded
 // to FP32), and the iteration resumes with the same search direction (beta
 // from the new (r, z)).  It stops when the FP64 true residual meets tol.
-int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_iter, cudaStream_t s) {
+int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_iter, bool check_guess,
+                   std::vector<int> &accepted, cudaStream_t s) {
   Workspace *w = op->ws;
   RhsState *st = w->st;
   const size_t field = field_elems(op);
@@ -960,10 +1005,17 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     ProfScope ps(w, kProfOuter, (double)op->nr * op->nz * m, s);
     launch_stencil<double>(kStencilResidual, ra, s);
   };
-  residual64(-1);
-  note_launch();
-  sc_mixed_start<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol,
-                                  delta * delta, max_iter);
+  auto start = [&]() {
+    residual64(-1);
+    note_launch();
+    sc_mixed_start<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol,
+                                    delta * delta, max_iter);
+  };
+  start();
+  if (check_guess) {
+    int grc = gate_guess(op, m, st, accepted, s, start);
+    if (grc != AX_OK) return grc;
+  }
   AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * field * m, s));
   AX_CHECK_LAUNCH();
   precond_apply<float>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s);
@@ -1032,6 +1084,8 @@ const char *ax_status_string(int status) {
 }
 
 const char *ax_version(void) { return "axpcg 0.1 sm_103a"; }
+
+const char *ax_last_error(void) { return g_last_error; }
 
 int64_t ax_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
@@ -1292,7 +1346,7 @@ int ax_apply_preconditioner(ax_operator *op, const double *in, double *out, int3
 
 // ---- solve ------------------------------------------------------------------
 static int finish_info(ax_operator *op, int m, const RhsState *dev, ax_solve_info *info, int outer_kind,
-                       int guess, cudaStream_t s) {
+                       const std::vector<int> &accepted, cudaStream_t s) {
   Workspace *w = op->ws;
   int rc = read_states(w, dev, m, s, w->h_st);
   if (rc != AX_OK) return rc;
@@ -1305,7 +1359,7 @@ static int finish_info(ax_operator *op, int m, const RhsState *dev, ax_solve_inf
       info[i].iters = h.iters;
       info[i].outer = outer_kind ? (int)h.tmp : 0;
       info[i].rel_res = h.bb > 0.0 ? std::sqrt(h.rr / h.bb) : 0.0;
-      info[i].guess_accepted = guess;
+      info[i].guess_accepted = accepted[i];
       info[i].status = st;
     }
     if (st != AX_OK && (worst == AX_OK || st > worst)) worst = st;
@@ -1327,6 +1381,8 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   if ((rc = ensure_base(op, m)) != AX_OK) return rc;
   const bool host = (flags & AX_FLAG_HOST_BUFFERS) != 0;
   const bool guess = (flags & AX_FLAG_USE_GUESS) != 0;
+  const bool check_guess = guess && (flags & AX_FLAG_CHECK_GUESS) != 0;
+  std::vector<int> accepted(m, guess ? 1 : 0);
   const double *fd = f;
   double *ud = u;
   if (host) {
@@ -1362,11 +1418,15 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     ra.phi = w->phi64;
     ra.out_res = w->r64;
     ra.partial = part_ptr(w, kPartB);
-    launch_stencil<double>(kStencilResidual, ra, s);
-    note_launch();
-    sc_start<<<m, 32, 0, s>>>(w->st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol, max_iter, -1,
-                              0);
+    auto start = [&]() {
+      launch_stencil<double>(kStencilResidual, ra, s);
+      note_launch();
+      sc_start<<<m, 32, 0, s>>>(w->st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol, max_iter,
+                                -1, 0);
+    };
+    start();
     AX_CHECK_LAUNCH();
+    if (check_guess && (rc = gate_guess(op, m, w->st, accepted, s, start)) != AX_OK) return rc;
     if (!cheb) {
       PcgVecs<double> v{w->x64, w->r64, w->pa64, w->pb64, w->q64, w->z64};
       if ((rc = pcg_loop<double>(op, m, v, w->phi64, w->st, w->g64, true, s)) != AX_OK) return rc;
@@ -1387,15 +1447,16 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
           AX_TRY(cudaMemcpyAsync(w->x64 + (size_t)i * field, w->y64prev + (size_t)i * field,
                                  field * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    rc = finish_info(op, m, w->st, info, 0, guess, s);
+    rc = finish_info(op, m, w->st, info, 0, accepted, s);
   } else {
     // ---- mixed precision
     outer_kind = 1;
     if ((rc = ensure_vec32(op, m, cheb)) != AX_OK) return rc;
     if (!cheb && !w->mixed_restart) {
       // FP32 PCG with FP64 residual replacement
-      if ((rc = pcg_mixed_loop(op, m, tol, w->replace_delta, max_iter, s)) != AX_OK) return rc;
-      rc = finish_info(op, m, w->st, info, 1, guess, s);
+      if ((rc = pcg_mixed_loop(op, m, tol, w->replace_delta, max_iter, check_guess, accepted, s)) != AX_OK)
+        return rc;
+      rc = finish_info(op, m, w->st, info, 1, accepted, s);
     } else {
     // FP64 iterative refinement around restarted FP32 inner solves
     RhsState *so = w->st_outer, *si = w->st;
@@ -1451,7 +1512,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
                                    field * sizeof(float), cudaMemcpyDeviceToDevice, s));
       }
     }
-    rc = finish_info(op, m, so, info, 1, guess, s);
+    rc = finish_info(op, m, so, info, 1, accepted, s);
     }
   }
   note_launch();

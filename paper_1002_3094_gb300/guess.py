@@ -1,0 +1,145 @@
+"""Learned initial guess: data generation with the solver, training and
+evaluation of the guess network (calls into libaxpcg only; PyTorch holds the
+device arrays).
+
+The network maps (log kappa, q, f / s) on an hw x hw lattice to u / s; the
+solver keeps its output as the starting iterate only when that lowers the
+initial residual (AX_FLAG_CHECK_GUESS), and always iterates to the requested
+tolerance.  Training pairs come from solves of random-field media
+(workload 4); held-out seeds come from a disjoint seed stream.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import (AX_FLAG_CHECK_GUESS, AX_FLAG_USE_GUESS, AX_PCG_MIXED, ax_batch_create, ax_batch_destroy,
+               ax_batch_solve, ax_destroy_operator, ax_guessnet_features, ax_guessnet_forward,
+               ax_guessnet_lift, ax_guessnet_train_step, ax_setup_operator, ax_solve)
+from .inputs import sample_points
+
+
+def grf_fields(specs, nr: int, nz: int, device):
+    """kappa_r [n][nr][nz], kappa_z [n][nr][nz+1], q [n][nr][nz] and f [n][nr][nz]
+    (FP64 torch tensors on `device`) of random-field media given by their
+    specs (workloads.grf_spec), evaluated at the grid's sample points in bulk
+    on the GPU."""
+    import torch
+    rn, rf, zn, zf = sample_points(nr, nz)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device)  # noqa: E731
+    rn, rf, zn, zf = t(rn), t(rf), t(zn), t(zf)
+
+    def field(spec, r, z):
+        om, ph = t(spec["omega"]), t(spec["phase"])
+        g = torch.zeros((r.numel(), z.numel()), dtype=torch.float64, device=device)
+        for j0 in range(0, om.shape[0], 64):
+            arg = (r[:, None, None] * om[None, None, j0:j0 + 64, 0] + z[None, :, None] * om[None, None, j0:j0 + 64, 1]
+                   + ph[None, None, j0:j0 + 64])
+            g += torch.cos(arg).sum(dim=2)
+        g = spec["amp"] * g
+        tt = ((g - spec["gmin"]) / (spec["gmax"] - spec["gmin"])).clamp(0.0, 1.0)
+        return torch.exp(np.log(spec["contrast"]) * tt)
+
+    kr, kz, qq, ff = [], [], [], []
+    for sp in specs:
+        kr.append(field(sp, rf, zn))
+        kz.append(field(sp, rn, zf))
+        qq.append(torch.full((nr, nz), sp["q"], dtype=torch.float64, device=device))
+        f = torch.zeros((nr, nz), dtype=torch.float64, device=device)
+        for rc, zc, sg, am in sp["sources"]:
+            f += am * torch.exp(-((rn[:, None] - rc) ** 2 + (zn[None, :] - zc) ** 2) / (2 * sg * sg))
+        ff.append(f)
+    return torch.stack(kr), torch.stack(kz), torch.stack(qq), torch.stack(ff)
+
+
+def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=None):
+    """Solves every medium with the batched solver and returns features x
+    [n][3][hw][hw], targets u / s [n][hw][hw] (FP32 torch tensors), the
+    operators' inputs and the solutions (FP64)."""
+    import torch
+    kr, kz, q, f = grf_fields(specs, nr, nz, device)
+    n = len(specs)
+    ops = [ax_setup_operator(kr[i], kz[i], q[i], nr, nz) for i in range(n)]
+    u = torch.zeros_like(f)
+    batch = ax_batch_create(ops)
+    _, info = ax_batch_solve(batch, [f[i] for i in range(n)], [u[i] for i in range(n)], tol, 20000, AX_PCG_MIXED)
+    ax_batch_destroy(batch)
+    x = torch.zeros((n, 3, hw, hw), dtype=torch.float32, device=device)
+    s = torch.zeros(n, dtype=torch.float64, device=device)
+    for i in range(n):
+        ax_guessnet_features(kr[i], q[i], f[i], 1, nr, nz, hw, x[i], s[i:i + 1])
+    # targets on the lattice: cell averages of u / s (the lattice equals the grid
+    # here when nr = nz = hw)
+    if nr == hw and nz == hw:
+        y = (u / s[:, None, None]).float()
+    else:
+        y = torch.nn.functional.avg_pool2d((u / s[:, None, None]).float()[:, None], (nr // hw, nz // hw))[:, 0]
+    return {"x": x, "y": y.contiguous(), "kr": kr, "kz": kz, "q": q, "f": f, "u": u, "s": s, "ops": ops,
+            "iters": [i["iters"] for i in info]}
+
+
+def train(net: int, data, epochs: int, batch: int, lr: float, seed: int = 0, log=None):
+    import torch
+    n = data["x"].shape[0]
+    rng = np.random.default_rng(seed)
+    losses = []
+    for ep in range(epochs):
+        order = rng.permutation(n)
+        ep_loss = 0.0
+        steps = 0
+        for k in range(0, n - batch + 1, batch):
+            idx = torch.as_tensor(order[k:k + batch], device=data["x"].device)
+            xb = data["x"].index_select(0, idx).contiguous()
+            yb = data["y"].index_select(0, idx).contiguous()
+            ep_loss += ax_guessnet_train_step(net, xb, yb, batch, lr * (0.5 ** (ep // max(1, epochs // 3))))
+            steps += 1
+        losses.append(ep_loss / max(1, steps))
+        if log:
+            log(f"epoch {ep} loss {losses[-1]:.4e}")
+    return losses
+
+
+def guess_for(net: int, data, i: int, hw: int, nr: int, nz: int):
+    """u0 for sample i: features -> network -> bilinear lift -> scale."""
+    import torch
+    dev = data["f"].device
+    x = torch.zeros((1, 3, hw, hw), dtype=torch.float32, device=dev)
+    s = torch.zeros(1, dtype=torch.float64, device=dev)
+    ax_guessnet_features(data["kr"][i], data["q"][i], data["f"][i], 1, nr, nz, hw, x, s)
+    y = torch.zeros((1, hw, hw), dtype=torch.float32, device=dev)
+    ax_guessnet_forward(net, x, y, 1)
+    u0 = torch.zeros((1, nr, nz), dtype=torch.float64, device=dev)
+    ax_guessnet_lift(y, 1, hw, s, nr, nz, u0)
+    return u0
+
+
+def evaluate(net: int, data, hw: int, nr: int, nz: int, tol: float = 1e-8, method: int = AX_PCG_MIXED):
+    """Per held-out sample: iterations and wall time from zero and from the
+    network's guess (guess time included), with the residual gate on."""
+    import torch
+    rows = []
+    for i, op in enumerate(data["ops"]):
+        f = data["f"][i:i + 1]
+        u = torch.zeros_like(f)
+        ax_solve(op, f, u, 1, tol, 20000, method)          # warm the graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u.zero_()
+        _, i0 = ax_solve(op, f, u, 1, tol, 20000, method)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u0 = guess_for(net, data, i, hw, nr, nz)
+        _, ig = ax_solve(op, f, u0, 1, tol, 20000, method, AX_FLAG_USE_GUESS | AX_FLAG_CHECK_GUESS)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        rows.append({"iters_zero": i0[0]["iters"], "iters_guess": ig[0]["iters"], "ms_zero": 1e3 * (t1 - t0),
+                     "ms_guess": 1e3 * (t2 - t1), "accepted": ig[0]["guess_accepted"],
+                     "res_zero": i0[0]["rel_res"], "res_guess": ig[0]["rel_res"]})
+    return rows
+
+
+def release(data):
+    for op in data["ops"]:
+        ax_destroy_operator(op)
+    data["ops"] = []

@@ -346,3 +346,26 @@ def test_batched_uneven_instances_equal_single_solves(cuda, method):
     P.ax_batch_destroy(batch)
     for pr in pairs:
         pr.close()
+
+
+@pytest.mark.parametrize("method", [P.AX_PCG_FP64, P.AX_PCG_MIXED])
+def test_guess_gate_rejects_bad_and_keeps_good_guesses(cuda, method):
+    """AX_FLAG_CHECK_GUESS: a garbage starting iterate (residual above ||phi||)
+    is replaced by zero, a good one is kept and saves iterations; both reach
+    the tolerance in the oracle's norm."""
+    med = layered_inclusion_medium(n_rhs=2, nominal_n=96)
+    pr = Pair(med, 96, 80, cuda)
+    f = sample_rhs(med, 96, 80)
+    _, i0, u_ref = _solve(pr, f, method, 1e-9)
+    rng = np.random.default_rng(0)
+    u0 = np.stack([1e3 * rng.normal(size=u_ref[0].shape),             # garbage
+                   u_ref[1] * (1 + 1e-4 * rng.normal(size=u_ref[1].shape))])  # near solution
+    flags = P.AX_FLAG_USE_GUESS | P.AX_FLAG_CHECK_GUESS
+    st, info, u = _solve(pr, f, method, 1e-9, flags=flags, u0=u0)
+    assert st == P.AX_OK
+    assert info[0]["guess_accepted"] == 0 and info[1]["guess_accepted"] == 1
+    assert info[0]["iters"] == i0[0]["iters"]
+    assert info[1]["iters"] < i0[1]["iters"]
+    for j in range(2):
+        assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-9
+    pr.close()

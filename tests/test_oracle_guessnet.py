@@ -1,0 +1,73 @@
+"""Pins for the FP64 reference of the initial-guess network: convolution
+against scipy.signal.correlate, adjoint identities, and every gradient
+against central finite differences."""
+import numpy as np
+import pytest
+import scipy.signal
+
+from oracle import guessnet as G
+
+
+def test_conv3x3_matches_scipy_correlate():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(3, 9, 7))
+    w = rng.normal(size=(3, 3, 3, 4))
+    b = rng.normal(size=4)
+    out = G.conv3x3(x, w, b)
+    for co in range(4):
+        ref = b[co] + sum(scipy.signal.correlate(x[ci], w[:, :, ci, co], mode="same") for ci in range(3))
+        np.testing.assert_allclose(out[co], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_pool_and_upsample_adjoints():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 8, 6))
+    y = rng.normal(size=(2, 4, 3))
+    assert np.isclose(np.sum(G.pool2(x) * y), np.sum(x * G.pool2_backward(y)))
+    assert np.isclose(np.sum(G.up2(y) * x), np.sum(y * G.up2_backward(x)))
+
+
+def test_gradients_match_finite_differences():
+    arch = G.architecture(ch=(2, 3, 4, 5), cin=3)
+    params = G.init_params(arch, seed=3)
+    rng = np.random.default_rng(4)
+    # non-zero biases so that ReLU kinks are away from the probe points
+    params = {k: (w, rng.normal(0, 0.1, size=b.shape)) for k, (w, b) in params.items()}
+    x = rng.normal(size=(3, 16, 16))
+    t = rng.normal(size=(1, 16, 16))
+
+    def loss(p, xx):
+        out, _ = G.forward(p, arch, xx)
+        return G.mse_loss(out, t)[0]
+
+    out, cache = G.forward(params, arch, x)
+    _, gout = G.mse_loss(out, t)
+    grads, gx = G.backward(params, arch, cache, gout)
+    eps = 1e-6
+    for name in ("e1a", "e2b", "b1", "d3a", "d1a", "d1b", "head"):
+        w, b = params[name]
+        gw, gb = grads[name]
+        for idx in [tuple(rng.integers(0, s) for s in w.shape) for _ in range(4)]:
+            wp, wm = w.copy(), w.copy()
+            wp[idx] += eps
+            wm[idx] -= eps
+            fd = (loss({**params, name: (wp, b)}, x) - loss({**params, name: (wm, b)}, x)) / (2 * eps)
+            assert abs(fd - gw[idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx, fd, gw[idx])
+        j = int(rng.integers(0, b.shape[0]))
+        bp, bm = b.copy(), b.copy()
+        bp[j] += eps
+        bm[j] -= eps
+        fd = (loss({**params, name: (w, bp)}, x) - loss({**params, name: (w, bm)}, x)) / (2 * eps)
+        assert abs(fd - gb[j]) <= 1e-6 * max(1.0, abs(fd)), (name, j)
+    for idx in [(0, 3, 4), (2, 15, 0), (1, 8, 8)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        fd = (loss(params, xp) - loss(params, xm)) / (2 * eps)
+        assert abs(fd - gx[idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_default_network_has_about_a_million_parameters():
+    arch = G.architecture()
+    n = sum(w.size + b.size for w, b in G.init_params(arch).values())
+    assert 0.9e6 < n < 1.1e6

@@ -13,6 +13,7 @@ from .media import (  # noqa: F401
     layered_inclusion_medium,
     batched_instances,
     grf_medium,
+    grf_spec,
     large_medium,
     manufactured_medium,
     WORKLOADS,

@@ -185,26 +185,55 @@ def _random_fourier_field(rng: np.random.Generator, corr_len: float, n_feat: int
             arg = np.outer(rf, omega[j0:j0 + 32, 0]) + np.outer(zf, omega[j0:j0 + 32, 1]) + phase[j0:j0 + 32]
             out += np.cos(arg).sum(axis=1)
         return (amp * out).reshape(shape)
+    g.omega, g.phase, g.amp = omega, phase, amp
     return g
 
 
-def grf_medium(instance: int, split: str = "train") -> Medium:
-    """split 'train' uses instances 0..; 'eval' uses a disjoint seed stream."""
+def grf_spec(instance: int, split: str = "train") -> dict:
+    """All random draws of one random-field instance: Fourier features
+    (omega, phase, amp), the extremes (gmin, gmax) of the field on a fixed 128^2
+    reference lattice, the contrast, q and the Gaussian sources
+    (r, z, sigma, amplitude).  grf_medium builds its functions from this, and
+    bulk evaluators can reproduce the same field from it."""
     rng = _rng(4 if split == "train" else 40, instance)
     g = _random_fourier_field(rng, 0.1)
     rr, zz = _reference_lattice(128)
     gv = g(rr, zz)
-    gmin, gmax = float(gv.min()), float(gv.max())
-    contrast = rng.uniform(1.0, 10.0)
+    spec = {"omega": g.omega, "phase": g.phase, "amp": g.amp, "gmin": float(gv.min()), "gmax": float(gv.max())}
+    spec["contrast"] = float(rng.uniform(1.0, 10.0))
+    spec["q"] = float(rng.uniform(0.0, 0.5))
+    k = int(rng.integers(1, 5))
+    spec["sources"] = [(*rng.uniform(0.1, 0.9, size=2), rng.uniform(0.02, 0.1), rng.uniform(-1.0, 1.0))
+                       for _ in range(k)]
+    return spec
+
+
+def grf_medium(instance: int, split: str = "train") -> Medium:
+    """kappa = exp(ln(C) * clip((g - gmin) / (gmax - gmin), 0, 1)) for a Gaussian
+    random field g (correlation length 0.1), contrast C ~ U[1, 10]; q ~ U[0, 0.5];
+    f = 1-4 Gaussians with amplitude U[-1, 1], sigma U[0.02, 0.1].  split
+    'train' and 'eval' use disjoint seed streams."""
+    spec = grf_spec(instance, split)
+    omega, phase, amp = spec["omega"], spec["phase"], spec["amp"]
+    gmin, gmax, contrast = spec["gmin"], spec["gmax"], spec["contrast"]
+
+    def g(r, z):
+        r = np.asarray(r, dtype=np.float64)
+        z = np.asarray(z, dtype=np.float64)
+        shape = np.broadcast(r, z).shape
+        rf = np.broadcast_to(r, shape).reshape(-1)
+        zf = np.broadcast_to(z, shape).reshape(-1)
+        out = np.zeros(rf.shape)
+        for j0 in range(0, omega.shape[0], 32):
+            arg = np.outer(rf, omega[j0:j0 + 32, 0]) + np.outer(zf, omega[j0:j0 + 32, 1]) + phase[j0:j0 + 32]
+            out += np.cos(arg).sum(axis=1)
+        return (amp * out).reshape(shape)
 
     def kappa(r, z):
         t = (g(r, z) - gmin) / (gmax - gmin)
         return np.exp(np.log(contrast) * np.clip(t, 0.0, 1.0))
 
-    qv = rng.uniform(0.0, 0.5)
-    k = int(rng.integers(1, 5))
-    srcs = [_gaussian(*rng.uniform(0.1, 0.9, size=2), rng.uniform(0.02, 0.1), rng.uniform(-1.0, 1.0))
-            for _ in range(k)]
+    srcs = [_gaussian(rc, zc, sg, am) for rc, zc, sg, am in spec["sources"]]
 
     def f(r, z):
         out = np.zeros(np.broadcast(r, z).shape)
@@ -212,7 +241,7 @@ def grf_medium(instance: int, split: str = "train") -> Medium:
             out = out + s(r, z)
         return out
 
-    return Medium(f"grf_{split}{instance}", kappa, _const(qv), [f],
+    return Medium(f"grf_{split}{instance}", kappa, _const(spec["q"]), [f],
                   "kappa = exp(GRF, corr 0.1) scaled to contrast U[1,10]; q~U[0,0.5]; 1-4 Gaussians")
 
 
