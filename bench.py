@@ -54,6 +54,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rhs", type=int, default=0, help="override the number of right-hand sides (profiling)")
+    ap.add_argument("--train", type=int, default=4096, help="guess_256: training seeds")
+    ap.add_argument("--eval", type=int, default=512, help="guess_256: held-out seeds")
+    ap.add_argument("--epochs", type=int, default=8, help="guess_256: training epochs")
+    ap.add_argument("--batch", type=int, default=16, help="guess_256: batch size")
+    ap.add_argument("--lr", type=float, default=1e-3, help="guess_256: Adam learning rate")
+    ap.add_argument("--save", default="", help="guess_256: write the trained weights here")
     return ap.parse_args()
 
 
@@ -253,10 +259,77 @@ def run_batched(args):
         P.ax_destroy_operator(op)
 
 
+def run_guess(args):
+    """Workload guess_256 (random-field media on 256 x 256): solve
+    `--train` seeds with the batched solver, train the guess network on the
+    (features, u / s) pairs on the GPU, then solve `--eval` held-out seeds from
+    zero and from the network's guess (inference time included, residual gate
+    on) at 1e-8."""
+    import numpy as np
+    import torch
+    import paper_1002_3094_gb300 as P
+    from paper_1002_3094_gb300 import guess as GS
+    from workloads import grf_spec
+    dev = torch.device("cuda", 0)
+    P.build()
+    P.load_library()
+    n = hw = 256
+    t0 = time.perf_counter()
+    train = GS.make_dataset([grf_spec(i, "train") for i in range(args.train)], n, n, hw, TOL, dev)
+    t_data = time.perf_counter() - t0
+    GS.release(train)
+    net = P.ax_guessnet_create(hw, None, batch_capacity=args.batch, seed=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = GS.train(net, train, args.epochs, args.batch, args.lr, log=lambda m: print(m, file=sys.stderr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    ev = GS.make_dataset([grf_spec(i, "eval") for i in range(args.eval)], n, n, hw, TOL, dev)
+    rows = GS.evaluate(net, ev, hw, n, n, TOL)
+    GS.release(ev)
+    # inference time alone (batch 1), CUDA events
+    x = torch.zeros((1, 3, hw, hw), dtype=torch.float32, device=dev)
+    y = torch.zeros((1, hw, hw), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        P.ax_guessnet_forward(net, x, y, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        P.ax_guessnet_forward(net, x, y, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / 10
+    gflop = 2.0 * sum(9 * a * b for a, b in [(3, 24), (24, 24), (48, 24), (24, 24)]) * hw * hw / 1e9
+    gflop += 2.0 * sum(9 * a * b for a, b in [(24, 48), (48, 48), (96, 48), (48, 48)]) * (hw // 2) ** 2 / 1e9
+    gflop += 2.0 * sum(9 * a * b for a, b in [(48, 96), (96, 96), (192, 96), (96, 96)]) * (hw // 4) ** 2 / 1e9
+    gflop += 2.0 * sum(9 * a * b for a, b in [(96, 192), (192, 192)]) * (hw // 8) ** 2 / 1e9
+    it0 = np.array([r["iters_zero"] for r in rows])
+    itg = np.array([r["iters_guess"] for r in rows])
+    line = {"metric": "PCG iterations and wall time at rel. residual 1e-8, from the learned guess vs from zero",
+            "workload": "guess_256", "train_samples": args.train, "eval_samples": args.eval,
+            "epochs": args.epochs, "batch": args.batch, "params": P.ax_guessnet_num_params(net),
+            "data_s": t_data, "train_s": t_train, "train_samples_per_s": args.train * args.epochs / t_train,
+            "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+            "iters_zero_mean": float(it0.mean()), "iters_guess_mean": float(itg.mean()),
+            "iters_saved_frac": float(1 - itg.mean() / it0.mean()),
+            "ms_zero_mean": float(np.mean([r["ms_zero"] for r in rows])),
+            "ms_guess_mean": float(np.mean([r["ms_guess"] for r in rows])),
+            "accepted_frac": float(np.mean([r["accepted"] for r in rows])),
+            "max_rel_res_guess": float(max(r["res_guess"] for r in rows)),
+            "inference_ms": infer_ms, "inference_gflop": gflop, "inference_tflops": gflop / infer_ms}
+    print(json.dumps(line))
+    if args.save:
+        P.ax_guessnet_save(net, args.save)
+    P.ax_guessnet_destroy(net)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "guess_256":
+        run_guess(args)
         return
     if args.workload == "batched_256":
         run_batched(args)

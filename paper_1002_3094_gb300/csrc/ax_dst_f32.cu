@@ -7,25 +7,26 @@ template <typename T>
 void launch_dst_any(int mode, const DstArgs<T> &a_in, cudaStream_t s) {
   DstArgs<T> a = a_in;
   a.rpb = dst_rows_per_block(a.plan.L, (int)sizeof(T));
-  const size_t smem = dst_smem_bytes(a.plan.L, (int)sizeof(T));
+  size_t smem = dst_smem_bytes(a.plan.L, (int)sizeof(T));
+  if (a.plan.rader) smem += 2ull * a.rpb * a.plan.tn_div[0].d * 2 * sizeof(T);
   dim3 grid(a.m, (a.rows + a.rpb - 1) / a.rpb);
   dim3 block(256);
   note_launch();
   switch (mode) {
     case kDstPlain:
-      cudaFuncSetAttribute(dst_kernel<T, kDstPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem_attr((const void *)dst_kernel<T, kDstPlain>, smem);
       dst_kernel<T, kDstPlain><<<grid, block, smem, s>>>(a);
       break;
     case kDstPcgForward:
-      cudaFuncSetAttribute(dst_kernel<T, kDstPcgForward>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem_attr((const void *)dst_kernel<T, kDstPcgForward>, smem);
       dst_kernel<T, kDstPcgForward><<<grid, block, smem, s>>>(a);
       break;
     case kDstPcgInverse:
-      cudaFuncSetAttribute(dst_kernel<T, kDstPcgInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem_attr((const void *)dst_kernel<T, kDstPcgInverse>, smem);
       dst_kernel<T, kDstPcgInverse><<<grid, block, smem, s>>>(a);
       break;
     default:
-      cudaFuncSetAttribute(dst_kernel<T, kDstChebInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem_attr((const void *)dst_kernel<T, kDstChebInverse>, smem);
       dst_kernel<T, kDstChebInverse><<<grid, block, smem, s>>>(a);
       break;
   }

@@ -341,6 +341,91 @@ __device__ __forceinline__ void generic_stage(C *__restrict__ src, C *__restrict
   }
 }
 
+// First stage by Rader's algorithm (prime R, Ns = 1): for every butterfly j
+// the inputs a_p = x_{g^p} (p < P = R - 1) are transformed, multiplied by the
+// spectrum of the permuted kernel c'_m = W^(g^-m), and transformed again
+// (inverse via conjugation), which gives X_{g^-q} = x_0 + (a * c')_q; X_0 =
+// x_0 + sum a.  The P-point transforms reuse the small-radix Stockham stages
+// on sub-rows of length P laid out in the two shared buffers.  x0s holds 2
+// values per butterfly (x_0 and X_0).
+template <typename T, typename C>
+__device__ __forceinline__ void rader_stage(C *__restrict__ src, C *__restrict__ dst, C *__restrict__ x0s, int nrows,
+                                            int L, int R, const FftPlan &pl, const T *__restrict__ RK,
+                                            const T *__restrict__ RT, const int *__restrict__ RP) {
+  const int P = R - 1;
+  const FastDiv &tn = pl.tn_div[0];
+  const int Tn = tn.d;
+  const int nsub = nrows * Tn;
+  for (int item = threadIdx.x; item < nsub * P; item += blockDim.x) {
+    const int sub = fdiv(item, pl.p_div);
+    const int p = item - sub * P;
+    const int rr = fdiv(sub, tn);
+    const int j = sub - rr * Tn;
+    dst[item] = src[rr * L + j + __ldg(RP + p) * Tn];
+  }
+  for (int sub = threadIdx.x; sub < nsub; sub += blockDim.x) {
+    const int rr = fdiv(sub, tn);
+    x0s[sub] = src[rr * L + (sub - rr * Tn)];
+  }
+  __syncthreads();
+  C *a = dst, *b = src;
+  for (int pass = 0; pass < 2; ++pass) {
+    int ns = 1;
+    for (int k = 0; k < pl.sub_n; ++k) {
+      const int Rk = pl.sub_radix[k];
+      switch (Rk) {
+        case 2: small_stage<T, 2>(a, b, nsub, P, ns, pl.sub_tn[k], pl.sub_ns[k], RT); break;
+        case 3: small_stage<T, 3>(a, b, nsub, P, ns, pl.sub_tn[k], pl.sub_ns[k], RT); break;
+        case 4: small_stage<T, 4>(a, b, nsub, P, ns, pl.sub_tn[k], pl.sub_ns[k], RT); break;
+        case 5: small_stage<T, 5>(a, b, nsub, P, ns, pl.sub_tn[k], pl.sub_ns[k], RT); break;
+        default: small_stage<T, 8>(a, b, nsub, P, ns, pl.sub_tn[k], pl.sub_ns[k], RT); break;
+      }
+      C *t = a; a = b; b = t;
+      ns *= Rk;
+      __syncthreads();
+    }
+    if (pass == 0) {
+      // Z = conj(A * C'); X_0 = x_0 + A_0
+      for (int item = threadIdx.x; item < nsub * P; item += blockDim.x) {
+        const int sub = fdiv(item, pl.p_div);
+        const int k = item - sub * P;
+        const C v = a[item];
+        const T cr = __ldg(RK + 2 * k), ci = __ldg(RK + 2 * k + 1);
+        C z;
+        z.x = v.x * cr - v.y * ci;
+        z.y = -(v.x * ci + v.y * cr);
+        b[item] = z;
+        if (k == 0) {
+          C x0 = x0s[sub];
+          x0.x += v.x;
+          x0.y += v.y;
+          x0s[nsub + sub] = x0;
+        }
+      }
+      C *t = a; a = b; b = t;
+      __syncthreads();
+    }
+  }
+  // a == src here (an odd number of buffer moves): scatter into the stage output
+  const T inv = T(1) / T(P);
+  for (int item = threadIdx.x; item < nsub * P; item += blockDim.x) {
+    const int sub = fdiv(item, pl.p_div);
+    const int q = item - sub * P;
+    const int rr = fdiv(sub, tn);
+    const int j = sub - rr * Tn;
+    const C v = a[item];
+    const C x0 = x0s[sub];
+    C o;
+    o.x = x0.x + v.x * inv;
+    o.y = x0.y - v.y * inv;
+    dst[rr * L + j * R + __ldg(RP + P + q)] = o;
+  }
+  for (int sub = threadIdx.x; sub < nsub; sub += blockDim.x) {
+    const int rr = fdiv(sub, tn);
+    dst[rr * L + (sub - rr * Tn) * R] = x0s[nsub + sub];
+  }
+}
+
 template <typename T> struct DstOcc;
 template <> struct DstOcc<float> { static constexpr int min_blocks = 3; };
 template <> struct DstOcc<double> { static constexpr int min_blocks = 2; };
@@ -358,6 +443,7 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   const int nrows = min(a.rpb, a.rows - row0);
   C *buf0 = reinterpret_cast<C *>(smem_raw);
   C *buf1 = buf0 + ((a.rpb * L + 1) & ~1);  // 16-byte aligned (vector staging stores)
+  C *x0s = buf1 + a.rpb * L;                 // Rader: 2 values per first-stage butterfly
   T *pk = reinterpret_cast<T *>(buf0);  // packed real view: pk[rr * 2L + idx] = x_idx
   const size_t base = (size_t)m * (size_t)a.field + (size_t)row0 * a.pitch;
   T alpha = T(0);
@@ -425,6 +511,12 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
     const int R = a.plan.radix[s];
     const FastDiv tn = a.plan.tn_div[s], nsd = a.plan.ns_div[s];
     __syncthreads();
+    if (s == 0 && a.plan.rader) {
+      rader_stage<T>(src, dst, x0s, nrows, L, R, a.plan, a.RK, a.RT, a.RP);
+      C *t = src; src = dst; dst = t;
+      Ns *= R;
+      continue;
+    }
     switch (R) {
       case 2: small_stage<T, 2>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;
       case 3: small_stage<T, 3>(src, dst, nrows, L, Ns, tn, nsd, a.TW); break;

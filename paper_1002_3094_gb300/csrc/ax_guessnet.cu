@@ -583,7 +583,7 @@ void launch_wgrad(GuessNet *n, const TIn *in, const float *gz, float *gw, int B,
   const int tiles = ((res + kTile - 1) / kTile) * ((res + kTile - 1) / kTile);
   const int nco = (Cout + kCob - 1) / kCob;
   const size_t smem = sizeof(float) * (kCib * (kTile + 2) * (kTile + 2) + kTile * kTile * kCob);
-  cudaFuncSetAttribute(conv3x3_wgrad_kernel<TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ensure_smem_attr((const void *)conv3x3_wgrad_kernel<TIn>, smem);
   dim3 grid(tiles, (Cin + kCib - 1) / kCib, nco * B);
   note_launch();
   conv3x3_wgrad_kernel<TIn><<<grid, 144, smem, s>>>(in, gz, n->partial, Cin, Cout, res, res);

@@ -58,6 +58,13 @@ struct FftPlan {
   int radix[kMaxStages] = {0};
   FastDiv ns_div[kMaxStages];  // Ns of stage s (product of the earlier radices)
   FastDiv tn_div[kMaxStages];  // L / radix[s]
+  // Rader's algorithm for a large prime first radix R: the length-R DFT becomes
+  // a cyclic convolution of length P = R - 1 done with these sub-stages.
+  int rader = 0;
+  int sub_n = 0;
+  int sub_radix[8] = {0};
+  FastDiv sub_ns[8], sub_tn[8];
+  FastDiv p_div;               // P
 };
 
 // Per-precision device tables of one operator.
@@ -71,6 +78,8 @@ struct Coef {
   T *R = nullptr;    // [nr]          r_i
   T *TW = nullptr;   // [2 L]         (cos, sin)(2 pi j / L), j < L
   T *HW = nullptr;   // [2 L]         (cos, sin)(pi j / L),   j < L
+  T *RK = nullptr;   // [2 P]         Rader: DFT of the permuted kernel W^(g^-m)
+  T *RT = nullptr;   // [2 P]         Rader: (cos, sin)(2 pi j / P)
 };
 
 // Scalar state of one right-hand side during an iteration.  Lives in device
@@ -105,6 +114,11 @@ struct Workspace;
 // being captured nothing is counted (the replay counts the nodes).
 void note_launch();
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit to `bytes`.
+// Thread-safe: host threads of a batched solve launch the same kernels with
+// different shared-memory sizes concurrently.
+cudaError_t ensure_smem_attr(const void *func, size_t bytes);
+
 // Kernel classes of the per-launch profiler (ax_profile_read).
 enum { kProfStencil = 0, kProfDstFwd = 1, kProfTridiag = 2, kProfDstInv = 3, kProfScalar = 4,
        kProfOuter = 5, kProfOther = 6, kProfKinds = 7 };
@@ -120,6 +134,7 @@ struct ax_operator {
   double kappa_t = 0, q_t = 0, gamma1 = 0, gamma2 = 0;
   int device = 0;
   ax::FftPlan plan;
+  int *rader_perm = nullptr;  // [2 P] device
   ax::Coef<double> c64;
   ax::Coef<float> c32;
   ax::Workspace *ws = nullptr;
@@ -164,6 +179,8 @@ enum { kDstPlain = 0, kDstPcgForward = 1, kDstPcgInverse = 2, kDstChebInverse = 
 template <typename T>
 struct DstArgs {
   const T *TW, *HW;
+  const T *RK, *RT;        // Rader tables (plan.rader)
+  const int *RP;           // Rader permutations: g^p mod R (p < P), then g^-q mod R
   FftPlan plan;
   int n, rows, pitch;      // n = nz; rows per RHS
   long long field;         // elements per RHS

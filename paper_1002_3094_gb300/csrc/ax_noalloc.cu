@@ -94,6 +94,9 @@ int precond_noalloc(ax_operator *op, const double *in, double *out, int m, cudaS
   DstArgs<T> d{};
   d.TW = c.TW;
   d.HW = c.HW;
+  d.RK = c.RK;
+  d.RT = c.RT;
+  d.RP = op->rader_perm;
   d.plan = op->plan;
   d.n = op->nz;
   d.rows = op->nr;

@@ -89,6 +89,22 @@ void note_launch() {
   if (!g_capturing) __atomic_add_fetch(&g_launches, 1, __ATOMIC_RELAXED);
 }
 
+cudaError_t ensure_smem_attr(const void *func, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void *, size_t>> limits;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto &e : limits)
+    if (e.first == func) {
+      if (e.second >= bytes) return cudaSuccess;
+      cudaError_t r = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (r == cudaSuccess) e.second = bytes;
+      return r;
+    }
+  cudaError_t r = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (r == cudaSuccess) limits.push_back({func, bytes});
+  return r;
+}
+
 namespace {
 
 int status_from_cuda(cudaError_t e) {
@@ -627,7 +643,91 @@ FftPlan make_plan(int L) {
     p.tn_div[i] = make_fastdiv(L / r[i]);
     ns *= r[i];
   }
+  // Rader's algorithm for a first radix that is a prime above the unrolled
+  // set, when R - 1 has only the factors 2, 3, 5.
+  if (p.nstages > 0 && p.radix[0] > 47) {
+    const int P = p.radix[0] - 1;
+    int m = P, t2 = 0;
+    std::vector<int> sub;
+    while (m % 2 == 0) { m /= 2; ++t2; }
+    while (m % 5 == 0) { m /= 5; sub.push_back(5); }
+    while (m % 3 == 0) { m /= 3; sub.push_back(3); }
+    while (t2 >= 3) { sub.push_back(8); t2 -= 3; }
+    if (t2 == 2) sub.push_back(4);
+    if (t2 == 1) sub.push_back(2);
+    if (m == 1 && sub.size() <= 8) {
+      p.rader = 1;
+      p.sub_n = (int)sub.size();
+      int sns = 1;
+      for (int i = 0; i < p.sub_n; ++i) {
+        p.sub_radix[i] = sub[i];
+        p.sub_ns[i] = make_fastdiv(sns);
+        p.sub_tn[i] = make_fastdiv(P / sub[i]);
+        sns *= sub[i];
+      }
+      p.p_div = make_fastdiv(P);
+    }
+  }
   return p;
+}
+
+// Tables of Rader's algorithm for prime R (P = R - 1): permutations by a
+// primitive root g, the DFT of the permuted kernel c'_m = exp(-2 pi i g^-m / R)
+// (FP64, direct sum) and the twiddles of length P.
+void rader_tables(int R, std::vector<int> &perm, std::vector<double> &rk, std::vector<double> &rt) {
+  const int P = R - 1;
+  auto powmod = [R](long long b, long long e) {
+    long long x = 1;
+    b %= R;
+    while (e > 0) {
+      if (e & 1) x = x * b % R;
+      b = b * b % R;
+      e >>= 1;
+    }
+    return (int)x;
+  };
+  std::vector<int> fs;
+  for (int m = P, d = 2; m > 1; ++d) {
+    if (m % d == 0) {
+      fs.push_back(d);
+      while (m % d == 0) m /= d;
+    }
+  }
+  int g = 2;
+  for (;; ++g) {
+    bool ok = true;
+    for (int f : fs) ok = ok && powmod(g, P / f) != 1;
+    if (ok) break;
+  }
+  const int ginv = powmod(g, R - 2);
+  perm.assign(2 * P, 0);
+  for (int q = 0; q < P; ++q) {
+    perm[q] = powmod(g, q);
+    perm[P + q] = powmod(ginv, q);
+  }
+  std::vector<double> cr(P), ci(P);
+  for (int mm = 0; mm < P; ++mm) {
+    const double ang = -2.0 * M_PI * perm[P + mm] / R;
+    cr[mm] = std::cos(ang);
+    ci[mm] = std::sin(ang);
+  }
+  rk.assign(2 * P, 0.0);
+  for (int k = 0; k < P; ++k) {
+    double sr = 0.0, si = 0.0;
+    for (int mm = 0; mm < P; ++mm) {
+      const long long e = ((long long)mm * k) % P;
+      const double c = std::cos(2.0 * M_PI * e / P), sn = -std::sin(2.0 * M_PI * e / P);
+      sr += cr[mm] * c - ci[mm] * sn;
+      si += cr[mm] * sn + ci[mm] * c;
+    }
+    rk[2 * k] = sr;
+    rk[2 * k + 1] = si;
+  }
+  rt.assign(2 * P, 0.0);
+  for (int j = 0; j < P; ++j) {
+    rt[2 * j] = std::cos(2.0 * M_PI * j / P);
+    rt[2 * j + 1] = std::sin(2.0 * M_PI * j / P);
+  }
 }
 
 template <typename T>
@@ -642,6 +742,7 @@ cudaError_t upload(T **dst, const std::vector<double> &src) {
 template <typename T>
 void free_coef(Coef<T> &c) {
   dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW);
+  dfree(c.RK); dfree(c.RT);
 }
 
 // ---------------------------------------------------------------------------
@@ -661,6 +762,9 @@ DstArgs<T> dst_args(const ax_operator *op, int m, int rows, const RhsState *st, 
   const Coef<T> &c = coef<T>(op);
   a.TW = c.TW;
   a.HW = c.HW;
+  a.RK = c.RK;
+  a.RT = c.RT;
+  a.RP = op->rader_perm;
   a.plan = op->plan;
   a.n = op->nz;
   a.rows = rows;
@@ -1102,6 +1206,7 @@ int ax_destroy_operator(ax_operator *op) {
   if (!op) return AX_OK;
   free_coef(op->c64);
   free_coef(op->c32);
+  dfree(op->rader_perm);
   if (op->ws) {
     Workspace *w = op->ws;
     free_vectors64(w);
@@ -1261,6 +1366,18 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   AX_UP(float, c32.CR, CR) AX_UP(float, c32.CZ, CZ) AX_UP(float, c32.W, W) AX_UP(float, c32.IP, IP)
   AX_UP(float, c32.E, E) AX_UP(float, c32.R, ri) AX_UP(float, c32.TW, TW) AX_UP(float, c32.HW, HW)
 #undef AX_UP
+  if (e == cudaSuccess && op->plan.rader) {
+    std::vector<int> perm;
+    std::vector<double> rk, rt;
+    rader_tables(op->plan.radix[0], perm, rk, rt);
+    e = upload<double>(&op->c64.RK, rk);
+    if (e == cudaSuccess) e = upload<double>(&op->c64.RT, rt);
+    if (e == cudaSuccess) e = upload<float>(&op->c32.RK, rk);
+    if (e == cudaSuccess) e = upload<float>(&op->c32.RT, rt);
+    if (e == cudaSuccess) e = dalloc(&op->rader_perm, perm.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(op->rader_perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&op->ws->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     ax_destroy_operator(op);
@@ -1587,6 +1704,11 @@ cudaError_t build_group_coef(Coef<T> &g, const std::vector<const ax_operator *> 
   if (err == cudaSuccess) err = copy_table(&g.R, c0.R, (size_t)o->nr, s);
   if (err == cudaSuccess) err = copy_table(&g.TW, c0.TW, 2 * (size_t)o->plan.L, s);
   if (err == cudaSuccess) err = copy_table(&g.HW, c0.HW, 2 * (size_t)o->plan.L, s);
+  if (err == cudaSuccess && o->plan.rader) {
+    const size_t P = (size_t)o->plan.radix[0] - 1;
+    err = copy_table(&g.RK, c0.RK, 2 * P, s);
+    if (err == cudaSuccess) err = copy_table(&g.RT, c0.RT, 2 * P, s);
+  }
   return err;
 }
 
@@ -1664,6 +1786,8 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     g.gop = gop;
     cudaError_t e = build_group_coef<double>(gop->c64, mops, pick64, s);
     if (e == cudaSuccess) e = build_group_coef<float>(gop->c32, mops, pick32, s);
+    if (e == cudaSuccess && o->plan.rader)
+      e = copy_table(&gop->rader_perm, o->rader_perm, 2 * (size_t)(o->plan.radix[0] - 1), s);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&gop->ws->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);

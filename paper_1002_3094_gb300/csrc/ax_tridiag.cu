@@ -198,8 +198,7 @@ void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
   // P <= 1024 holds for nr <= 8192 (the set-up limit).
   const size_t smem = 2ull * P * W * sizeof(T);
   dim3 grid(a.m, (a.nz + W - 1) / W);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(tridiag_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) ensure_smem_attr((const void *)tridiag_kernel<T, C>, smem);
   tridiag_kernel<T, C><<<grid, W * P, smem, s>>>(a, W, P);
 }
 
