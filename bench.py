@@ -42,6 +42,34 @@ ALG_BYTES = {"stencil": (16.0, 12.0), "dst_forward": (28.0, 0.0), "mode_solve": 
              "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0)}
 
 
+# Source files whose change invalidates an ncu traffic figure of a kernel class.
+KERNEL_SOURCES = {"stencil": ["ax_stencil.cu"], "dst_forward": ["ax_dst_impl.cuh", "ax_dst_f32.cu"],
+                  "dst_inverse": ["ax_dst_impl.cuh", "ax_dst_f32.cu"], "mode_solve": ["ax_tridiag.cu"],
+                  "outer_residual": ["ax_stencil.cu"]}
+
+
+def source_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_1002_3094_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, units_per_launch: float):
+    """DRAM bytes (read + write) per launch of `kernel`, scaled from the ncu
+    capture recorded in profiles/traffic.json (bytes per grid unknown of the
+    captured launch), or None when no capture matches the current source."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha") != source_hash(kernel):
+        return None
+    return rec["dram_bytes_per_unknown"] * units_per_launch
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,8 +243,9 @@ def run_batched(args):
     dev = torch.device("cuda", 0)
     P.build()
     P.load_library()
-    ops, fs, us, unknowns = [], [], [], 0
+    ops, fs, us, unknowns, nr_nz = [], [], [], 0, []
     for nr, nz, med in batched_instances(count):
+        nr_nz.append((nr, nz))
         kr, kz, q = sample_operator_inputs(med, nr, nz)
         ops.append(P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz))
         fs.append(torch.from_numpy(sample_rhs(med, nr, nz)[0]).to(dev))
@@ -226,7 +255,16 @@ def run_batched(args):
     method = P.METHODS[args.method]
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        P.ax_batch_solve(batch, fs, us, TOL, 20000, method, stream=stream)
+        st, info = P.ax_batch_solve(batch, fs, us, TOL, 20000, method, stream=stream, raise_on_error=False)
+        if st != P.AX_OK:
+            bad = [(j, nr_nz[j], i) for j, i in enumerate(info) if i["status"] != P.AX_OK]
+            print(json.dumps({"error": P.ax_status_string(st), "failed": bad[:10], "n_failed": len(bad)}))
+            for j, (nr, nz), _ in bad[:3]:  # the same instance alone
+                u1 = torch.zeros_like(us[j])
+                st1, i1 = P.ax_solve(ops[j], fs[j], u1, 1, TOL, 20000, method, raise_on_error=False)
+                st2, i2 = P.ax_solve(ops[j], fs[j], u1, 1, TOL, 20000, P.AX_PCG_FP64, raise_on_error=False)
+                print(json.dumps({"instance": j, "shape": [nr, nz], "alone": i1[0], "alone_fp64": i2[0]}))
+            return
     torch.cuda.synchronize()
     launches0 = P.ax_kernel_launches()
     clocks = ClockSampler(0)
@@ -468,14 +506,7 @@ def main():
         bytes_per_launch = units_per_launch * per_u + (nr * nz) * per_m
         avg_s = p["ms"] / p["launches"] / 1000.0
         achieved = bytes_per_launch / avg_s / 1e9
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tpath):
-            try:
-                tt = json.load(open(tpath)).get(f"{args.workload}:{args.method}:{top}")
-                traffic = tt
-            except (OSError, ValueError):
-                traffic = None
+        traffic = measured_traffic(top, units_per_launch)
         roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",

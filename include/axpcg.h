@@ -72,9 +72,11 @@ enum {
   AX_FLAG_USE_GUESS = 1,    /* u holds an initial guess on entry (else the start is zero)   */
   AX_FLAG_HOST_BUFFERS = 4, /* f and u are host pointers; copies are made inside the call   */
   AX_FLAG_CHECK_GUESS = 8   /* with AX_FLAG_USE_GUESS: keep a right-hand side's guess only if
-                               its true residual ||phi - A u0|| is below ||phi||, else start
-                               that right-hand side from zero (AX_PCG_FP64, AX_PCG_MIXED;
-                               info.guess_accepted tells which)                              */
+                               its preconditioned residual norm (r0, B^-1 r0), r0 = phi - A u0,
+                               is below (phi, B^-1 phi), the zero start's (both measure the
+                               start error in the energy norm that CG reduces); else start that
+                               right-hand side from zero (AX_PCG_FP64, AX_PCG_MIXED;
+                               info.guess_accepted tells which; costs two B^-1 applications)  */
 };
 enum { AX_PREC_FP64 = 0, AX_PREC_FP32 = 1 };
 

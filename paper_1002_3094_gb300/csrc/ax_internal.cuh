@@ -93,6 +93,8 @@ struct RhsState {
   double thresh2;  // stop when rr <= thresh2
   double cheb_a;   // Chebyshev alpha_k
   double tmp;
+  double gate_phi; // (phi, B^-1 phi): preconditioned norm^2 of the zero-start residual
+  double gate_res; // (r0, B^-1 r0) of the residual of a supplied initial guess
   int state;       // kActive / kCheck / kDone / kFailed
   int iters;
   int status;      // AX_* status

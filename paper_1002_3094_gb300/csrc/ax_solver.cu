@@ -1059,20 +1059,45 @@ int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphC
   return AX_OK;
 }
 
-// Initial-guess gate: right-hand sides whose starting iterate does not lower
-// the residual below ||phi|| (rr >= bb after the start kernel) restart from
-// zero.  `restart` re-runs the residual and start kernels for all RHS (the
-// accepted ones recompute the same values).  accepted[i] = 1 if kept.
-template <typename F>
-int gate_guess(ax_operator *op, int m, const RhsState *st, std::vector<int> &accepted, cudaStream_t s, F restart) {
+// Stores sum(partials) of each right-hand side into gate_phi (which = 0) or
+// gate_res (which = 1).
+__global__ void sc_store_gate(RhsState *st, const double *p, int nb, int which) {
+  const int m = blockIdx.x;
+  const double v = reduce_part(p + (size_t)m * kPartialStride, nb);
+  if (threadIdx.x == 0) {
+    if (which == 0) st[m].gate_phi = v;
+    else st[m].gate_res = v;
+  }
+}
+
+// Initial-guess gate.  CG reduces the error in the energy norm, and a learned
+// guess is typically close to the solution in that norm while its small
+// high-frequency errors make the plain residual norm large; so the guess of a
+// right-hand side is kept only if its preconditioned residual norm
+// (r0, B^-1 r0) is below that of the zero start, (phi, B^-1 phi) (both the
+// energy norm of the start error in the metric of B^-1 A).  Rejected ones
+// restart from zero; `restart` re-runs the residual and start kernels for all
+// right-hand sides.  phiT and r0T hold phi and the guess residual in the
+// working precision; zbuf is scratch.  accepted[i] = 1 if kept.
+template <typename T, typename F>
+int gate_guess(ax_operator *op, int m, RhsState *st, const T *phiT, const T *r0T, T *zbuf,
+               std::vector<int> &accepted, cudaStream_t s, F restart) {
   Workspace *w = op->ws;
+  const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
+  precond_apply<T>(op, m, phiT, zbuf, st, -1, part_ptr(w, kPartC), s);
+  note_launch();
+  sc_store_gate<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, 0);
+  precond_apply<T>(op, m, r0T, zbuf, st, -1, part_ptr(w, kPartC), s);
+  note_launch();
+  sc_store_gate<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, 1);
+  AX_CHECK_LAUNCH();
   int rc = read_states(w, st, m, s, w->h_st);
   if (rc != AX_OK) return rc;
   const size_t field = field_elems(op);
   bool any = false;
   for (int i = 0; i < m; ++i) {
     const RhsState &h = w->h_st[i];
-    const bool ok = std::isfinite(h.rr) && h.rr < h.bb;
+    const bool ok = std::isfinite(h.gate_res) && std::isfinite(h.rr) && h.gate_res < h.gate_phi;
     accepted[i] = ok ? 1 : 0;
     if (!ok) {
       any = true;
@@ -1117,7 +1142,10 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   };
   start();
   if (check_guess) {
-    int grc = gate_guess(op, m, st, accepted, s, start);
+    const size_t n = field * m;
+    note_launch();
+    to_precision<float><<<(unsigned)std::min<size_t>((n + 255) / 256, 65535), 256, 0, s>>>(w->phi64, w->pa32, n);
+    int grc = gate_guess<float>(op, m, st, w->pa32, w->r32, w->z32, accepted, s, start);
     if (grc != AX_OK) return grc;
   }
   AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * field * m, s));
@@ -1543,7 +1571,9 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     };
     start();
     AX_CHECK_LAUNCH();
-    if (check_guess && (rc = gate_guess(op, m, w->st, accepted, s, start)) != AX_OK) return rc;
+    if (check_guess &&
+        (rc = gate_guess<double>(op, m, w->st, w->phi64, w->r64, w->z64, accepted, s, start)) != AX_OK)
+      return rc;
     if (!cheb) {
       PcgVecs<double> v{w->x64, w->r64, w->pa64, w->pb64, w->q64, w->z64};
       if ((rc = pcg_loop<double>(op, m, v, w->phi64, w->st, w->g64, true, s)) != AX_OK) return rc;

@@ -191,13 +191,13 @@ def _random_fourier_field(rng: np.random.Generator, corr_len: float, n_feat: int
 
 def grf_spec(instance: int, split: str = "train") -> dict:
     """All random draws of one random-field instance: Fourier features
-    (omega, phase, amp), the extremes (gmin, gmax) of the field on a fixed 128^2
+    (omega, phase, amp), the extremes (gmin, gmax) of the field on a fixed 64^2
     reference lattice, the contrast, q and the Gaussian sources
     (r, z, sigma, amplitude).  grf_medium builds its functions from this, and
     bulk evaluators can reproduce the same field from it."""
     rng = _rng(4 if split == "train" else 40, instance)
     g = _random_fourier_field(rng, 0.1)
-    rr, zz = _reference_lattice(128)
+    rr, zz = _reference_lattice(64)
     gv = g(rr, zz)
     spec = {"omega": g.omega, "phase": g.phase, "amp": g.amp, "gmin": float(gv.min()), "gmax": float(gv.max())}
     spec["contrast"] = float(rng.uniform(1.0, 10.0))
