@@ -259,6 +259,13 @@ def run_batched(args):
         if st != P.AX_OK:
             bad = [(j, nr_nz[j], i) for j, i in enumerate(info) if i["status"] != P.AX_OK]
             print(json.dumps({"error": P.ax_status_string(st), "failed": bad[:10], "n_failed": len(bad)}))
+            for u_ in us:
+                u_.zero_()
+            st2, info2 = P.ax_batch_solve(batch, fs, us, TOL, 20000, method, P.AX_FLAG_SERIAL_GROUPS, stream=stream,
+                                          raise_on_error=False)
+            bad2 = [(j, nr_nz[j], i) for j, i in enumerate(info2) if i["status"] != P.AX_OK]
+            print(json.dumps({"serial_groups_status": P.ax_status_string(st2), "n_failed": len(bad2),
+                              "failed": bad2[:5]}))
             for j, (nr, nz), _ in bad[:3]:  # the same instance alone
                 u1 = torch.zeros_like(us[j])
                 st1, i1 = P.ax_solve(ops[j], fs[j], u1, 1, TOL, 20000, method, raise_on_error=False)
@@ -322,7 +329,8 @@ def run_guess(args):
     losses = GS.train(net, train, args.epochs, args.batch, args.lr, log=lambda m: print(m, file=sys.stderr))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    ev = GS.make_dataset([grf_spec(i, "eval") for i in range(args.eval)], n, n, hw, TOL, dev)
+    ev = GS.make_dataset([grf_spec(i, "eval") for i in range(args.eval)], n, n, hw, TOL, dev,
+                         target_scale=train["tscale"])
     rows = GS.evaluate(net, ev, hw, n, n, TOL)
     GS.release(ev)
     # inference time alone (batch 1), CUDA events

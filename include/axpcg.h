@@ -71,6 +71,8 @@ enum {
 enum {
   AX_FLAG_USE_GUESS = 1,    /* u holds an initial guess on entry (else the start is zero)   */
   AX_FLAG_HOST_BUFFERS = 4, /* f and u are host pointers; copies are made inside the call   */
+  AX_FLAG_SERIAL_GROUPS = 16, /* ax_batch_solve: run the shape groups one after another on the
+                                 calling thread instead of concurrently                     */
   AX_FLAG_CHECK_GUESS = 8   /* with AX_FLAG_USE_GUESS: keep a right-hand side's guess only if
                                its preconditioned residual norm (r0, B^-1 r0), r0 = phi - A u0,
                                is below (phi, B^-1 phi), the zero start's (both measure the

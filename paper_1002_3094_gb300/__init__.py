@@ -30,6 +30,7 @@ AX_CHEB_MIXED = 3
 AX_FLAG_USE_GUESS = 1
 AX_FLAG_HOST_BUFFERS = 4
 AX_FLAG_CHECK_GUESS = 8
+AX_FLAG_SERIAL_GROUPS = 16
 
 AX_PREC_FP64 = 0
 AX_PREC_FP32 = 1

@@ -126,6 +126,106 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const TIn *__restrict__ in
 }
 
 // ---------------------------------------------------------------------------
+// 3x3 convolution, forward, on the tensor cores: implicit GEMM with
+// mma.sync m16n8k16 (BF16 inputs, FP32 accumulation).  A CTA computes a
+// 16 x 8 pixel patch (8 warps, one patch row of 16 pixels each) for 32 output
+// channels; K runs over the 9 taps x input channels in chunks of 16.
+// Shared memory holds the haloed input patch as [pixel][16 channels] and the
+// weights as [tap][32 out][16 in], so each (k, k+1) pair of a fragment is one
+// 32-bit word.
+// ---------------------------------------------------------------------------
+constexpr int kPx = 16, kPy = 8, kCo = 32;
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(256) conv3x3_mma_kernel(const TIn *__restrict__ in, const bf16 *__restrict__ w,
+                                                          const float *__restrict__ bias, bf16 *__restrict__ out,
+                                                          const bf16 *__restrict__ skip, bf16 *__restrict__ out2,
+                                                          int Cin, int Cout, int H, int W, int relu) {
+  __shared__ __align__(16) bf16 s_in[(kPy + 2) * (kPx + 2)][16];
+  __shared__ __align__(16) bf16 s_w[9][kCo][16];
+  const int tiles_x = (W + kPx - 1) / kPx;
+  const int x0 = (blockIdx.x % tiles_x) * kPx, y0 = (blockIdx.x / tiles_x) * kPy;
+  const int co0 = blockIdx.y * kCo;
+  const int b = blockIdx.z;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const size_t plane = (size_t)H * W;
+  const TIn *inb = in + (size_t)b * Cin * plane;
+  float acc[4][4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[n][c] = 0.f;
+  const unsigned *sin32 = reinterpret_cast<const unsigned *>(&s_in[0][0]);
+  const unsigned *sw32 = reinterpret_cast<const unsigned *>(&s_w[0][0][0]);
+  for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
+    __syncthreads();
+    for (int e = t; e < (kPy + 2) * (kPx + 2) * 16; e += 256) {
+      const int ci = e / ((kPy + 2) * (kPx + 2));
+      const int pix = e - ci * (kPy + 2) * (kPx + 2);
+      const int yy = pix / (kPx + 2), xx = pix - yy * (kPx + 2);
+      const int gy = y0 + yy - 1, gx = x0 + xx - 1;
+      float v = 0.f;
+      if (ci0 + ci < Cin && gy >= 0 && gy < H && gx >= 0 && gx < W)
+        v = ld_as_float(inb + (size_t)(ci0 + ci) * plane + (size_t)gy * W + gx);
+      s_in[pix][ci] = __float2bfloat16(v);
+    }
+    for (int e = t; e < 9 * kCo * 16; e += 256) {
+      const int tap = e / (kCo * 16);
+      const int rem = e - tap * kCo * 16;
+      const int c = rem / 16, ci = rem - c * 16;
+      bf16 v = __float2bfloat16(0.f);
+      if (ci0 + ci < Cin && co0 + c < Cout) v = w[((size_t)tap * Cin + ci0 + ci) * Cout + co0 + c];
+      s_w[tap][c][ci] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3;
+      // A rows: pixels x = g and x = g + 8 of patch row `warp`, shifted by the tap
+      const int p0 = (warp + dy) * (kPx + 2) + g + dx;
+      const int p1 = p0 + 8;
+      unsigned a[4];
+      a[0] = sin32[p0 * 8 + tq];
+      a[1] = sin32[p1 * 8 + tq];
+      a[2] = sin32[p0 * 8 + tq + 4];
+      a[3] = sin32[p1 * 8 + tq + 4];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const int c = n * 8 + g;
+        unsigned bb[2];
+        bb[0] = sw32[(tap * kCo + c) * 8 + tq];
+        bb[1] = sw32[(tap * kCo + c) * 8 + tq + 4];
+        mma_bf16_16816(acc[n], a, bb);
+      }
+    }
+  }
+  // epilogue: acc[n][0..1] pixel x = g, channels n*8 + 2tq + {0,1}; acc[n][2..3] pixel x = g + 8
+  const int y = y0 + warp;
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int x = x0 + g + ((c >> 1) ? 8 : 0);
+      const int co = co0 + n * 8 + 2 * tq + (c & 1);
+      if (y >= H || x >= W || co >= Cout) continue;
+      float v = acc[n][c] + bias[co];
+      if (relu) v = fmaxf(v, 0.f);
+      const size_t o = ((size_t)b * Cout + co) * plane + (size_t)y * W + x;
+      out[o] = __float2bfloat16(v);
+      if (skip) out2[o] = __float2bfloat16(v + __bfloat162float(skip[o]));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient of a 3x3 conv over one 32x32 tile of one sample:
 //   partial[tile][tap][ci][co] = sum_{pixels} in[ci][y+dy-1][x+dx-1] gz[co][y][x]
 // 144 threads: (tap, ci) x 2 halves of the 16 output channels.
@@ -578,6 +678,15 @@ void launch_conv(const TIn *in, const bf16 *w, const float *bias, TOut *out, con
 }
 
 template <typename TIn>
+void launch_conv_mma(const TIn *in, const bf16 *w, const float *bias, bf16 *out, const bf16 *skip, bf16 *out2, int B,
+                     int Cin, int Cout, int res, cudaStream_t s) {
+  const int tiles = ((res + kPx - 1) / kPx) * ((res + kPy - 1) / kPy);
+  dim3 grid(tiles, (Cout + kCo - 1) / kCo, B);
+  note_launch();
+  conv3x3_mma_kernel<TIn><<<grid, 256, 0, s>>>(in, w, bias, out, skip, out2, Cin, Cout, res, res, 1);
+}
+
+template <typename TIn>
 void launch_wgrad(GuessNet *n, const TIn *in, const float *gz, float *gw, int B, int Cin, int Cout, int res,
                   cudaStream_t s) {
   const int tiles = ((res + kTile - 1) / kTile) * ((res + kTile - 1) / kTile);
@@ -610,9 +719,9 @@ void forward_pass(GuessNet *n, const float *x, int B, cudaStream_t s) {
       const bf16 *skip = (L.kind == 's') ? n->act[L.skip] : nullptr;
       bf16 *out2 = (L.kind == 's') ? n->act[L.out2] : nullptr;
       if (cur < 0)
-        launch_conv<float, bf16>(x, w, bias, out, skip, out2, B, L.cin, L.cout, L.res, true, s);
+        launch_conv_mma<float>(x, w, bias, out, skip, out2, B, L.cin, L.cout, L.res, s);
       else
-        launch_conv<bf16, bf16>(n->act[cur], w, bias, out, skip, out2, B, L.cin, L.cout, L.res, true, s);
+        launch_conv_mma<bf16>(n->act[cur], w, bias, out, skip, out2, B, L.cin, L.cout, L.res, s);
       cur = (L.kind == 's') ? L.out2 : L.out;
     } else if (L.kind == 'p') {
       note_launch();

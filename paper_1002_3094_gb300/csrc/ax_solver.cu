@@ -1001,6 +1001,22 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
   const int on_conv = true_check ? kCheck : kDone;
   const int K = w->graph_iters;
   const int key = m * 4 + (true_check ? 1 : 0);
+  // True-residual test of the right-hand sides in kCheck, inside the graph
+  // after every iteration (the kernels return at once for the others).
+  auto check_step = [&](cudaStream_t ss) {
+    if (!true_check) return;
+    StencilArgs<T> ra = stencil_args<T>(op, m, st, kCheck);
+    ra.in = v.x;
+    ra.phi = phi;
+    ra.out_res = v.r;
+    ra.partial = part_ptr(w, kPartB);
+    launch_stencil<T>(kStencilResidual, ra, ss);
+    note_launch();
+    sc_true_check<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbs);
+    precond_apply<T>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss);
+    note_launch();
+    sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
+  };
   const double per_rhs = (double)op->nr * op->nz;
   for (int guard = 0; guard < 1000000; ++guard) {
     int rc = AX_OK;
@@ -1010,30 +1026,19 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
       // number of right-hand sides it works on
       if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
       pcg_iteration<T>(op, m, v, st, w, on_conv, s, per_rhs * count_state(h, m, kActive));
+      check_step(s);
       AX_CHECK_LAUNCH();
     } else {
       rc = run_graph(w, g, key, s, [&](cudaStream_t cs) {
-        for (int k = 0; k < K; ++k) pcg_iteration<T>(op, m, v, st, w, on_conv, cs);
+        for (int k = 0; k < K; ++k) {
+          pcg_iteration<T>(op, m, v, st, w, on_conv, cs);
+          check_step(cs);
+        }
       });
     }
     if (rc != AX_OK) return rc;
     if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
-    if (true_check && any_state(h, m, kCheck)) {
-      StencilArgs<T> ra = stencil_args<T>(op, m, st, kCheck);
-      ra.in = v.x;
-      ra.phi = phi;
-      ra.out_res = v.r;
-      ra.partial = part_ptr(w, kPartB);
-      launch_stencil<T>(kStencilResidual, ra, s);
-      note_launch();
-      sc_true_check<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs);
-      precond_apply<T>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), s);
-      note_launch();
-      sc_beta<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
-      AX_CHECK_LAUNCH();
-      if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
-    }
-    if (!any_state(h, m, kActive)) break;
+    if (!any_state(h, m, kActive) && !any_state(h, m, kCheck)) break;
   }
   return AX_OK;
 }
@@ -1125,20 +1130,35 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   const int nbd = dst_blocks(op, op->nr, (int)sizeof(float));
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
   dim3 zg((unsigned)std::min<size_t>((field + 255) / 256, 4096), m);
-  auto residual64 = [&](int mask) {
+  auto residual64 = [&](int mask, cudaStream_t ss) {
     StencilArgs<double> ra = stencil_args<double>(op, m, st, mask);
     ra.in = w->x64;
     ra.phi = w->phi64;
     ra.out32 = w->r32;
     ra.partial = part_ptr(w, kPartB);
-    ProfScope ps(w, kProfOuter, (double)op->nr * op->nz * m, s);
-    launch_stencil<double>(kStencilResidual, ra, s);
+    ProfScope ps(w, kProfOuter, (double)op->nr * op->nz * m, ss);
+    launch_stencil<double>(kStencilResidual, ra, ss);
   };
   auto start = [&]() {
-    residual64(-1);
+    residual64(-1, s);
     note_launch();
     sc_mixed_start<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol,
                                     delta * delta, max_iter);
+  };
+  // Residual replacement of the right-hand sides in kCheck (every kernel
+  // returns at once for the others, so this runs after every iteration inside
+  // the captured graph and no right-hand side waits for the host).
+  auto replace_step = [&](cudaStream_t ss) {
+    note_launch();
+    add_correction<<<zg, 256, 0, ss>>>(w->x64, w->x32, field, st, kCheck);
+    note_launch();
+    zero_masked<float><<<zg, 256, 0, ss>>>(w->x32, field, st, kCheck);
+    residual64(kCheck, ss);
+    note_launch();
+    sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbs64, tol * tol, delta * delta);
+    precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss);
+    note_launch();
+    sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
   };
   start();
   if (check_guess) {
@@ -1164,29 +1184,19 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     if (w->profile) {
       if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
       pcg_iteration<float>(op, m, v, st, w, kCheck, s, per_rhs * count_state(h, m, kActive));
+      replace_step(s);
       AX_CHECK_LAUNCH();
     } else {
       rc = run_graph(w, w->g32, key, s, [&](cudaStream_t cs) {
-        for (int k = 0; k < K; ++k) pcg_iteration<float>(op, m, v, st, w, kCheck, cs);
+        for (int k = 0; k < K; ++k) {
+          pcg_iteration<float>(op, m, v, st, w, kCheck, cs);
+          replace_step(cs);
+        }
       });
     }
     if (rc != AX_OK) return rc;
     if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
-    if (any_state(h, m, kCheck)) {
-      note_launch();
-      add_correction<<<zg, 256, 0, s>>>(w->x64, w->x32, field, st, kCheck);
-      note_launch();
-      zero_masked<float><<<zg, 256, 0, s>>>(w->x32, field, st, kCheck);
-      residual64(kCheck);
-      note_launch();
-      sc_mixed_replace<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, tol * tol, delta * delta);
-      precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), s);
-      note_launch();
-      sc_beta<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
-      AX_CHECK_LAUNCH();
-      if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
-    }
-    if (!any_state(h, m, kActive)) break;
+    if (!any_state(h, m, kActive) && !any_state(h, m, kCheck)) break;
   }
   return AX_OK;
 }
@@ -1869,7 +1879,8 @@ int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double
                         g.stream);
     }
     ginfo[gi].resize(m);
-    status[gi] = ax_solve(g.gop, g.f_stack, g.u_stack, m, tol, max_iter, method, flags, ginfo[gi].data(), g.stream);
+    status[gi] = ax_solve(g.gop, g.f_stack, g.u_stack, m, tol, max_iter, method, flags & ~AX_FLAG_SERIAL_GROUPS,
+                          ginfo[gi].data(), g.stream);
     for (int k = 0; k < m; ++k)
       cudaMemcpyAsync(u[g.members[k]], g.u_stack + k * per, per * sizeof(double), cudaMemcpyDeviceToDevice, g.stream);
     cudaEventRecord(g.done, g.stream);
@@ -1877,9 +1888,13 @@ int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     for (int k = 0; k < m; ++k) b->latency_ms[g.members[k]] = ms;
   };
-  std::vector<std::thread> th;
-  for (size_t gi = 0; gi < b->groups.size(); ++gi) th.emplace_back(run, gi);
-  for (auto &t : th) t.join();
+  if (flags & AX_FLAG_SERIAL_GROUPS) {
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) run(gi);
+  } else {
+    std::vector<std::thread> th;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) th.emplace_back(run, gi);
+    for (auto &t : th) t.join();
+  }
   for (auto &g : b->groups) cudaStreamWaitEvent(s, g.done, 0);
   cudaEventDestroy(start);
   int worst = AX_OK;

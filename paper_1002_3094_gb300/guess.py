@@ -53,7 +53,7 @@ def grf_fields(specs, nr: int, nz: int, device):
     return torch.stack(kr), torch.stack(kz), torch.stack(qq), torch.stack(ff)
 
 
-def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=None):
+def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=None, target_scale: float = 0.0):
     """Solves every medium with the batched solver and returns features x
     [n][3][hw][hw], targets u / s [n][hw][hw] (FP32 torch tensors), the
     operators' inputs and the solutions (FP64)."""
@@ -75,8 +75,11 @@ def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=Non
         y = (u / s[:, None, None]).float()
     else:
         y = torch.nn.functional.avg_pool2d((u / s[:, None, None]).float()[:, None], (nr // hw, nz // hw))[:, 0]
-    return {"x": x, "y": y.contiguous(), "kr": kr, "kz": kz, "q": q, "f": f, "u": u, "s": s, "ops": ops,
-            "iters": [i["iters"] for i in info]}
+    # u / s is small (~1e-3); the network learns the target scaled to unit
+    # spread, and its output is divided by the same factor at solve time
+    tscale = target_scale if target_scale else float(1.0 / y.std().item())
+    return {"x": x, "y": (y * tscale).contiguous(), "kr": kr, "kz": kz, "q": q, "f": f, "u": u, "s": s,
+            "ops": ops, "iters": [i["iters"] for i in info], "tscale": tscale}
 
 
 def train(net: int, data, epochs: int, batch: int, lr: float, seed: int = 0, log=None):
@@ -110,7 +113,7 @@ def guess_for(net: int, data, i: int, hw: int, nr: int, nz: int):
     y = torch.zeros((1, hw, hw), dtype=torch.float32, device=dev)
     ax_guessnet_forward(net, x, y, 1)
     u0 = torch.zeros((1, nr, nz), dtype=torch.float64, device=dev)
-    ax_guessnet_lift(y, 1, hw, s, nr, nz, u0)
+    ax_guessnet_lift(y, 1, hw, s / data["tscale"], nr, nz, u0)
     return u0
 
 
