@@ -9,6 +9,12 @@ written out with NumPy in FP64: 3x3 "same" convolutions as sums of shifted
 arrays, ReLU, 2x2 average pooling, nearest 2x upsampling, additive skips, a
 1x1 head and a mean-squared-error loss, each with its hand-derived gradient.
 
+The CUDA network stores weights and activations in BF16 and accumulates in
+FP32.  forward() takes an optional `store` rounding (round_bf16 here) applied
+wherever that network writes an activation to memory: the input, each conv
+output after ReLU (after the skip add for "s" layers) and each pooled map.
+With store=None it is the plain FP64 network.
+
 Tensor layout: activations (C, H, W); conv weights (3, 3, Cin, Cout) indexed
 [dy + 1, dx + 1, ci, co] with out[co, y, x] = b[co] +
 sum_{dy, dx, ci} w[dy+1, dx+1, ci, co] * in[ci, y+dy, x+dx] (zero padding).
@@ -92,16 +98,28 @@ def init_params(arch, seed=0):
     return params
 
 
-def forward(params, arch, x):
-    """Returns (output (1, H, W), cache for backward)."""
+def round_bf16(a):
+    """Rounds to the nearest BF16 value (8 significant bits, ties to even),
+    by way of FP32: the upper 16 bits of the FP32 pattern after adding half
+    an ulp of the kept part (plus one if the kept part is odd)."""
+    a32 = np.ascontiguousarray(a, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(a))
+
+
+def forward(params, arch, x, store=None):
+    """Returns (output (1, H, W), cache for backward).  `store`, if given,
+    rounds every activation the network keeps in memory (see the header)."""
+    st = store if store is not None else (lambda v: v)
     cache = []
     skips = []
-    h = x
+    h = st(x)
     for name, cin, cout, kind in arch:
         if kind == "p":
             skips.append(h)
             cache.append(("p", None))
-            h = pool2(h)
+            h = st(pool2(h))
         elif kind == "u":
             cache.append(("u", None))
             h = up2(h)
@@ -112,7 +130,7 @@ def forward(params, arch, x):
             cache.append((name, (h, z)))
             if kind == "s":
                 a = a + skips.pop()
-            h = a
+            h = st(a)
         else:  # head: 1x1
             w, b = params[name]
             cache.append((name, (h, None)))

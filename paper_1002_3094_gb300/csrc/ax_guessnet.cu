@@ -653,7 +653,10 @@ cudaError_t zalloc(P **p, size_t count) {
   *p = nullptr;
   if (count == 0) return cudaSuccess;
   cudaError_t e = cudaMalloc((void **)p, count * sizeof(P));
+  // the fill runs on the legacy stream: finish it before any launch on a
+  // non-blocking stream can touch the buffer
   if (e == cudaSuccess) e = cudaMemset(*p, 0, count * sizeof(P));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   return e;
 }
 

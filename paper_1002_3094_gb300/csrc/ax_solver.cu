@@ -131,7 +131,12 @@ cudaError_t dalloc(P **p, size_t count) {
     *p = nullptr;
     return e;
   }
-  return cudaMemset(*p, 0, count * sizeof(P));
+  // cudaMemset is queued on the legacy stream, which does not order itself
+  // with the non-blocking streams the batched groups run on: wait for the
+  // fill here so that no later launch on any stream can see it in flight.
+  e = cudaMemset(*p, 0, count * sizeof(P));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
+  return e;
 }
 
 template <typename P>
@@ -334,6 +339,30 @@ __global__ void add_correction(double *__restrict__ x, const float *__restrict__
   const size_t b = (size_t)m * field;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < field; e += (size_t)gridDim.x * blockDim.x)
     x[b + e] += (double)d[b + e];
+}
+
+// Residual replacement of the selected right-hand sides: x64 += x32 and
+// x32 = 0 in one pass (field is a multiple of 4: the pitch is).  Launched
+// with a few CTAs per right-hand side, since in most launches no right-hand
+// side is selected and every CTA returns at once.
+__global__ void fold_correction(double *__restrict__ x, float *__restrict__ d, size_t field, const RhsState *st,
+                                int mask) {
+  const int m = blockIdx.y;
+  if (!rhs_selected(st, mask, m)) return;
+  double2 *x2 = reinterpret_cast<double2 *>(x + (size_t)m * field);
+  float4 *d4 = reinterpret_cast<float4 *>(d + (size_t)m * field);
+  const size_t n4 = field / 4;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 c = d4[e];
+    double2 a = x2[2 * e], b = x2[2 * e + 1];
+    a.x += (double)c.x;
+    a.y += (double)c.y;
+    b.x += (double)c.z;
+    b.y += (double)c.w;
+    x2[2 * e] = a;
+    x2[2 * e + 1] = b;
+    d4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1129,7 +1158,10 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   const int nbf = (op->nr + 15) / 16;
   const int nbd = dst_blocks(op, op->nr, (int)sizeof(float));
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
-  dim3 zg((unsigned)std::min<size_t>((field + 255) / 256, 4096), m);
+  // a few thousand CTAs in all for the replacement fold (see fold_correction)
+  const unsigned fold_x = (unsigned)std::max<size_t>(
+      1, std::min<size_t>((field / 4 + 255) / 256, (size_t)std::max(8, 4096 / std::max(1, m))));
+  const dim3 zg(fold_x, m);
   auto residual64 = [&](int mask, cudaStream_t ss) {
     StencilArgs<double> ra = stencil_args<double>(op, m, st, mask);
     ra.in = w->x64;
@@ -1150,9 +1182,7 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   // the captured graph and no right-hand side waits for the host).
   auto replace_step = [&](cudaStream_t ss) {
     note_launch();
-    add_correction<<<zg, 256, 0, ss>>>(w->x64, w->x32, field, st, kCheck);
-    note_launch();
-    zero_masked<float><<<zg, 256, 0, ss>>>(w->x32, field, st, kCheck);
+    fold_correction<<<zg, 256, 0, ss>>>(w->x64, w->x32, field, st, kCheck);
     residual64(kCheck, ss);
     note_launch();
     sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbs64, tol * tol, delta * delta);

@@ -193,8 +193,11 @@ template <> struct TriChunk<double> { static constexpr int small = 8, large = 16
 template <typename T, int C>
 void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
   const int P = (a.nr + C - 1) / C;
+  // CTAs of at most 512 threads while that still spans >= 8 mode columns, so
+  // two CTAs share an SM (one loads while the other scans); else up to 1024.
+  const int max_threads = (P <= 64) ? 512 : 1024;
   int W = 32;
-  while (W > 1 && W * P > 1024) W >>= 1;
+  while (W > 1 && W * P > max_threads) W >>= 1;
   // P <= 1024 holds for nr <= 8192 (the set-up limit).
   const size_t smem = 2ull * P * W * sizeof(T);
   dim3 grid(a.m, (a.nz + W - 1) / W);

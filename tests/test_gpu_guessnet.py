@@ -1,9 +1,18 @@
 """The initial-guess network's CUDA kernels against its FP64 reference.
 
-Tolerances (relative, 2-norm): forward output 2e-2 (BF16 weights and
-activations between layers, FP32 accumulation); every layer's weight and bias
-gradient 5e-2 against the FP64 reference backward (which is itself pinned to
-finite differences in test_oracle_guessnet.py)."""
+The kernels keep conv weights and activations in BF16 and accumulate in
+FP32, so they are compared with the FP64 reference run on the same BF16
+values: conv weights rounded to BF16 and every kept activation rounded by
+round_bf16 (the reference's `store`).  What remains is FP32 against FP64
+accumulation, a BF16 rounding that falls the other way when the two
+accumulations straddle a rounding boundary, and the first layer's weight
+gradient, which reads the FP32 input rather than its BF16 copy.
+Tolerances (relative, 2-norm): forward output 5e-3, every layer's weight and
+bias gradient 2e-2.  Against the unrounded FP64 network the gradients of the
+4x4 bottleneck layers differ by up to ~25% (ReLU decisions that BF16 storage
+flips), which is why the rounding is matched instead of the tolerance
+widened.  The reference backward is itself pinned to finite differences in
+test_oracle_guessnet.py."""
 import os
 import tempfile
 
@@ -50,6 +59,16 @@ def _to_oracle(flat, arch):
     return params
 
 
+def _bf16_weights(params, arch):
+    """Conv weights as the kernels hold them (BF16); the 1x1 head reads FP32."""
+    out = dict(params)
+    for name, cin, cout, kind in arch:
+        if kind in "cs":
+            w, b = params[name]
+            out[name] = (G.round_bf16(w), b)
+    return out
+
+
 def _flat_grads(grads, arch):
     out = []
     for name, cin, cout, kind in arch:
@@ -70,15 +89,15 @@ def test_forward_matches_reference(cuda):
     arch = G.architecture(ch=CH)
     net = P.ax_guessnet_create(HW, CH, batch_capacity=4, seed=7)
     flat = P.ax_guessnet_get_params(net)
-    params = _to_oracle(flat, arch)
+    params = _bf16_weights(_to_oracle(flat, arch), arch)
     x, _ = _inputs(3, 1)
     y = torch.zeros((3, HW, HW), dtype=torch.float32, device=cuda)
     P.ax_guessnet_forward(net, torch.from_numpy(x).to(cuda), y, 3)
     torch.cuda.synchronize()
     got = y.cpu().numpy()
     for b in range(3):
-        ref, _ = G.forward(params, arch, x[b].astype(np.float64))
-        assert np.linalg.norm(got[b] - ref[0]) <= 2e-2 * np.linalg.norm(ref[0])
+        ref, _ = G.forward(params, arch, x[b].astype(np.float64), store=G.round_bf16)
+        assert np.linalg.norm(got[b] - ref[0]) <= 5e-3 * np.linalg.norm(ref[0])
     P.ax_guessnet_destroy(net)
 
 
@@ -89,7 +108,7 @@ def test_gradients_match_reference(cuda):
     flat = P.ax_guessnet_get_params(net)
     flat = flat + rng.normal(0, 0.05, size=flat.size).astype(np.float32) * (np.abs(flat) == 0)  # non-zero biases
     P.ax_guessnet_set_params(net, flat)
-    params = _to_oracle(flat, arch)
+    params = _bf16_weights(_to_oracle(flat, arch), arch)
     B = 2
     x, t = _inputs(B, 5)
     loss, g = P.ax_guessnet_gradients(net, torch.from_numpy(x).to(cuda), torch.from_numpy(t).to(cuda), B)
@@ -97,13 +116,13 @@ def test_gradients_match_reference(cuda):
     gsum, lsum = None, 0.0
     N = B * HW * HW
     for b in range(B):
-        out, cache = G.forward(params, arch, x[b].astype(np.float64))
+        out, cache = G.forward(params, arch, x[b].astype(np.float64), store=G.round_bf16)
         d = out - t[b]
         lsum += float(np.sum(d * d))
         grads, _ = G.backward(params, arch, cache, 2.0 * d / N)
         fg = _flat_grads(grads, arch)
         gsum = fg if gsum is None else gsum + fg
-    assert abs(loss - lsum / N) <= 2e-2 * (lsum / N)
+    assert abs(loss - lsum / N) <= 5e-3 * (lsum / N)
     off = 0
     for name, cin, cout, kind in arch:
         if kind not in "csh":
@@ -112,7 +131,7 @@ def test_gradients_match_reference(cuda):
         for part, n in (("w", nw), ("b", cout)):
             a, r = g[off:off + n], gsum[off:off + n]
             off += n
-            assert np.linalg.norm(a - r) <= 5e-2 * np.linalg.norm(r) + 1e-7, (name, part)
+            assert np.linalg.norm(a - r) <= 2e-2 * np.linalg.norm(r) + 1e-7, (name, part)
     P.ax_guessnet_destroy(net)
 
 

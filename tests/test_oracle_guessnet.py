@@ -71,3 +71,36 @@ def test_default_network_has_about_a_million_parameters():
     arch = G.architecture()
     n = sum(w.size + b.size for w, b in G.init_params(arch).values())
     assert 0.9e6 < n < 1.1e6
+
+
+def test_round_bf16_ties_to_even_and_matches_torch():
+    u = 2.0 ** -7  # BF16 spacing on [1, 2)
+    cases = {1.0: 1.0, 1 + u / 2: 1.0, 1 + 1.5 * u: 1 + 2 * u, 1 + u / 2 + 2.0 ** -20: 1 + u,
+             -(1 + 1.5 * u): -(1 + 2 * u), 3.0: 3.0, 0.0: 0.0}
+    for a, want in cases.items():
+        assert G.round_bf16(np.array([a]))[0] == want, a
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    x = (rng.normal(size=4096) * np.exp(rng.normal(size=4096) * 5)).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(G.round_bf16(x), ref)
+
+
+def test_store_rounding_applies_to_every_kept_activation():
+    arch = G.architecture(ch=(4, 4, 4, 4))
+    params = G.init_params(arch, seed=1)
+    calls = []
+
+    def store(v):
+        calls.append(v.shape)
+        return G.round_bf16(v)
+
+    x = np.random.default_rng(2).normal(size=(3, 16, 16))
+    out, _ = G.forward(params, arch, x, store=store)
+    n_conv = sum(k in "cs" for _, _, _, k in arch)
+    n_pool = sum(k == "p" for _, _, _, k in arch)
+    assert len(calls) == 1 + n_conv + n_pool
+    ref, _ = G.forward(params, arch, x)
+    # rounding kept activations to 8 significant bits moves the output by
+    # about the BF16 unit roundoff times the depth, not more
+    assert 0 < np.linalg.norm(out - ref) <= 5e-2 * np.linalg.norm(ref)
