@@ -212,13 +212,20 @@ __device__ __forceinline__ void prime_stage(C *__restrict__ src, C *__restrict__
   static_assert(NB <= 6, "prime radix too large for the unrolled stage");
   const int Tn = tn.d;
   if (Ns > 1) twiddle_in_place<T>(src, nrows, L, Ns, R, tn, nsd, TW);
-  const FastDiv nid = make_fastdiv_dev(NB * Tn);  // items per row
+  // Items are grouped by output block b, each group padded to whole warps,
+  // so that b (the unrolled code path) is the same across a warp.
+  const int per_b = nrows * Tn;
+  const int per_b_pad = (per_b + 31) & ~31;
   {
-    for (int item = threadIdx.x; item < nrows * NB * Tn; item += blockDim.x) {
-      const int rr = fdiv(item, nid);
-      const int it = item - rr * NB * Tn;
-      const int b = fdiv(it, tn);
-      const int j = it - b * Tn;
+    for (int item = threadIdx.x; item < NB * per_b_pad; item += blockDim.x) {
+      int b = 0, w = item;
+      while (w >= per_b_pad) {
+        w -= per_b_pad;
+        ++b;
+      }
+      if (w >= per_b) continue;
+      const int rr = fdiv(w, tn);
+      const int j = w - rr * Tn;
       const int q = fdiv(j, nsd);
       const C *col = src + rr * L + j;
       C *out = dst + rr * L + q * Ns * R + (j - q * Ns);
@@ -287,13 +294,32 @@ __device__ __forceinline__ void generic_stage(C *__restrict__ src, C *__restrict
   const int H = (R - 1) / 2;
   const int NB = (H + G - 1) / G;
   const int cstep = L / R;
-  const FastDiv nid = make_fastdiv_dev(NB * Tn);  // items per row
+  // FP32: output blocks b grouped and warp-aligned, as in prime_stage.  FP64
+  // keeps the row-major item order, which needs fewer registers there (the
+  // warp-aligned form spills in the FP64 kernels).
+  constexpr bool kAligned = sizeof(T) == 4;
+  const int per_b = nrows * Tn;
+  const int per_b_pad = kAligned ? ((per_b + 31) & ~31) : per_b;
+  const FastDiv nid = make_fastdiv_dev(NB * Tn);  // items per row (row-major order)
   {
-    for (int item = threadIdx.x; item < nrows * NB * Tn; item += blockDim.x) {
-      const int rr = fdiv(item, nid);
-      const int it = item - rr * NB * Tn;
-      const int b = fdiv(it, tn);
-      const int j = it - b * Tn;
+    for (int item = threadIdx.x; item < NB * per_b_pad; item += blockDim.x) {
+      int b, rr, j;
+      if (kAligned) {
+        int w = item;
+        b = 0;
+        while (w >= per_b_pad) {
+          w -= per_b_pad;
+          ++b;
+        }
+        if (w >= per_b) continue;
+        rr = fdiv(w, tn);
+        j = w - rr * Tn;
+      } else {
+        rr = fdiv(item, nid);
+        const int it = item - rr * NB * Tn;
+        b = fdiv(it, tn);
+        j = it - b * Tn;
+      }
       const int q = fdiv(j, nsd);
       const C *col = src + rr * L + j;
       const C t0 = col[0];
@@ -542,8 +568,11 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   }
   __syncthreads();
 
-  // ---- split into the sine coefficients and store (columns outer, so the
-  // half-angle table is read once per column for all rows) ----
+  // ---- split into the sine coefficients and store.  Consecutive threads take
+  // consecutive k, so the reads of Z[k] and Z[L - k] are free of bank
+  // conflicts and every global access of a warp is one contiguous segment;
+  // the half-angle pair is read once per column for all rows.  Padding
+  // columns are not written (they hold zeros and stay zero). ----
   const T sc = (T)a.scale;
   T *__restrict__ outg = a.out;
   T cheb_a = T(0), tau = T(0);
@@ -551,46 +580,23 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
     cheb_a = (T)a.st[m].cheb_a;
     tau = (T)a.tau;
   }
-  for (int k0 = threadIdx.x * V; k0 < n; k0 += blockDim.x * V) {
-    T c[V], s[V];
-#pragma unroll
-    for (int t = 0; t < V; ++t) {
-      const int k = min(k0 + t + 1, L - 1);
-      c[t] = __ldg(a.HW + 2 * k);
-      s[t] = __ldg(a.HW + 2 * k + 1);
-    }
+  for (int k = threadIdx.x + 1; k <= n; k += blockDim.x) {
+    const T c = __ldg(a.HW + 2 * k), sn = __ldg(a.HW + 2 * k + 1);
     for (int rr = 0; rr < nrows; ++rr) {
       const C *Z = src + rr * L;
-      T v[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) {
-        const int k = k0 + t + 1;
-        if (k < L) {
-          const C zk = Z[k], zm = Z[L - k];
-          v[t] = ((zm.y - zk.y) + c[t] * (zk.x - zm.x) + s[t] * (zk.y + zm.y)) * sc;
-        } else {
-          v[t] = T(0);
-        }
-      }
-      const size_t e = base + (size_t)rr * a.pitch + k0;
+      const C zk = Z[k], zm = Z[L - k];
+      const T v = ((zm.y - zk.y) + c * (zk.x - zm.x) + sn * (zk.y + zm.y)) * sc;
+      const size_t e = base + (size_t)rr * a.pitch + (k - 1);
       if (MODE == kDstPlain || MODE == kDstPcgForward) {
-        store_vec<T>(outg + e, v);
+        outg[e] = v;
       } else if (MODE == kDstPcgInverse) {
-        T rv[V];
-        load_vec<T>(a.r + e, rv);
-        store_vec<T>(a.out + e, v);
-#pragma unroll
-        for (int t = 0; t < V; ++t) acc = fma(rv[t], v[t], acc);
+        const T rv = a.r[e];
+        outg[e] = v;
+        acc = fma(rv, v, acc);
       } else {  // Chebyshev: y_{k+1} = a (y_k - tau B^-1 res) + (1 - a) y_{k-1}
-        T yv[V], pv[V];
-        load_vec<T>(a.y + e, yv);
-        load_vec<T>(a.yprev + e, pv);
-#pragma unroll
-        for (int t = 0; t < V; ++t) {
-          const T yb = fma(-tau, v[t], yv[t]);
-          pv[t] = (k0 + t < n) ? fma(cheb_a, yb - pv[t], pv[t]) : T(0);
-        }
-        store_vec<T>(a.yprev + e, pv);
+        const T yb = fma(-tau, v, a.y[e]);
+        const T pv = a.yprev[e];
+        a.yprev[e] = fma(cheb_a, yb - pv, pv);
       }
     }
   }
