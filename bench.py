@@ -88,6 +88,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=16, help="guess_256: batch size")
     ap.add_argument("--lr", type=float, default=1e-3, help="guess_256: Adam learning rate")
     ap.add_argument("--save", default="", help="guess_256: write the trained weights here")
+    ap.add_argument("--h1", type=float, default=10.0, help="guess_256: weight of the loss's lattice-edge term")
+    ap.add_argument("--no-pre", action="store_true", help="guess_256: raw f / s feature instead of B^-1 (r f)")
     return ap.parse_args()
 
 
@@ -320,17 +322,19 @@ def run_guess(args):
     P.load_library()
     n = hw = 256
     t0 = time.perf_counter()
-    train = GS.make_dataset([grf_spec(i, "train") for i in range(args.train)], n, n, hw, TOL, dev)
+    pre = not args.no_pre
+    train = GS.make_dataset([grf_spec(i, "train") for i in range(args.train)], n, n, hw, TOL, dev, pre=pre)
     t_data = time.perf_counter() - t0
     GS.release(train)
     net = P.ax_guessnet_create(hw, None, batch_capacity=args.batch, seed=1)
+    P.ax_guessnet_set_loss(net, args.h1)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     losses = GS.train(net, train, args.epochs, args.batch, args.lr, log=lambda m: print(m, file=sys.stderr))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     ev = GS.make_dataset([grf_spec(i, "eval") for i in range(args.eval)], n, n, hw, TOL, dev,
-                         target_scale=train["tscale"])
+                         target_scale=train["tscale"], pre=pre)
     rows = GS.evaluate(net, ev, hw, n, n, TOL)
     GS.release(ev)
     # inference time alone (batch 1), CUDA events
@@ -354,6 +358,7 @@ def run_guess(args):
     line = {"metric": "PCG iterations and wall time at rel. residual 1e-8, from the learned guess vs from zero",
             "workload": "guess_256", "train_samples": args.train, "eval_samples": args.eval,
             "epochs": args.epochs, "batch": args.batch, "params": P.ax_guessnet_num_params(net),
+            "h1_weight": args.h1, "feature": "B^-1 (r f) / s" if pre else "f / s",
             "data_s": t_data, "train_s": t_train, "train_samples_per_s": args.train * args.epochs / t_train,
             "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
             "iters_zero_mean": float(it0.mean()), "iters_guess_mean": float(itg.mean()),
@@ -361,6 +366,7 @@ def run_guess(args):
             "ms_zero_mean": float(np.mean([r["ms_zero"] for r in rows])),
             "ms_guess_mean": float(np.mean([r["ms_guess"] for r in rows])),
             "accepted_frac": float(np.mean([r["accepted"] for r in rows])),
+            "energy_ratio_median": float(np.median([r["energy_ratio"] for r in rows])),
             "max_rel_res_guess": float(max(r["res_guess"] for r in rows)),
             "inference_ms": infer_ms, "inference_gflop": gflop, "inference_tflops": gflop / infer_ms}
     print(json.dumps(line))

@@ -183,14 +183,24 @@ int ax_solve_batched(ax_operator *const *ops, const double *const *f, double *co
  *   create: hw a multiple of 8; channels NULL for the default; batch_capacity
  *           the largest B; He-normal initialisation from `seed`.
  *   forward: y = net(x).
- *   gradients: loss = mean (net(x) - target)^2 and its gradient (host copy in
- *           grad_host if not NULL, [num_params]).
+ *   gradients: loss = (1/n) [sum d^2 + h1 sum over lattice edges (d_p - d_q)^2],
+ *           d = net(x) - target, n = B hw hw (h1 = 0 by default: the mean
+ *           squared error), and its gradient (host copy in grad_host if not
+ *           NULL, [num_params]).
+ *   set_loss: the edge weight h1 >= 0 (a discrete H1 seminorm term, which
+ *           penalises errors the way the operator's energy norm does).
  *   train_step: gradients + one Adam step (beta 0.9 / 0.999, eps 1e-8).
  *   save / load: header (magic "AXGN", version, hw, channels, count), FP32
  *           little-endian parameters, FNV-1a 64-bit checksum.
  *   features: per RHS m, s[m] = max |f_m| and the lattice features (cell
  *           averages when nr, nz are multiples of hw, else nearest samples) from
  *           kappa [nr][nz] (e.g. the kappa_r samples), q [nr][nz], f [m][nr][nz].
+ *   features_pre: as features, with f_m replaced by g_m = B^-1 (r f_m), the
+ *           right-hand side after one application of the operator's Laplace
+ *           preconditioner (FP32 kernels; Section 4.2): the solution of the
+ *           averaged-coefficient problem, which the network then corrects for
+ *           the variable kappa.  s[m] = max |g_m|.  Uses the operator's
+ *           staging buffers (not concurrently with a host-buffer solve on it).
  *   lift:   u[m] = s[m] * bilinear interpolation of y[m] onto the grid nodes. */
 int ax_guessnet_create(int32_t hw, const int32_t *channels, int32_t batch_capacity, uint64_t seed, void **net);
 int ax_guessnet_destroy(void *net);
@@ -206,6 +216,9 @@ int ax_guessnet_save(void *net, const char *path);
 int ax_guessnet_load(void *net, const char *path);
 int ax_guessnet_features(const double *kappa, const double *q, const double *f, int32_t m, int32_t nr,
                          int32_t nz, int32_t hw, float *x, double *scale, void *stream);
+int ax_guessnet_set_loss(void *net, double h1_weight);
+int ax_guessnet_features_pre(ax_operator *op, const double *kappa, const double *q, const double *f, int32_t m,
+                             int32_t hw, float *x, double *scale, void *stream);
 int ax_guessnet_lift(const float *y, int32_t m, int32_t hw, const double *scale, int32_t nr, int32_t nz,
                      double *u, void *stream);
 

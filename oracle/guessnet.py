@@ -164,6 +164,25 @@ def backward(params, arch, cache, gout):
     return grads, g
 
 
+def h1_loss(out, target, lam):
+    """Mean squared error plus lam times the squared differences of the error
+    across every edge of the lattice (the last two axes), both over the
+    number of values n: (sum d^2 + lam sum_edges (d_p - d_q)^2) / n, with its
+    gradient 2 (d + lam L d) / n, L the lattice graph Laplacian
+    (L d)_p = sum_{q next to p} (d_p - d_q)."""
+    d = np.asarray(out, dtype=np.float64) - target
+    n = d.size
+    dx = d[..., :, 1:] - d[..., :, :-1]
+    dy = d[..., 1:, :] - d[..., :-1, :]
+    loss = (np.sum(d * d) + lam * (np.sum(dx * dx) + np.sum(dy * dy))) / n
+    ld = np.zeros_like(d)
+    ld[..., :, 1:] += dx
+    ld[..., :, :-1] -= dx
+    ld[..., 1:, :] += dy
+    ld[..., :-1, :] -= dy
+    return float(loss), 2.0 * (d + lam * ld) / n
+
+
 def mse_loss(out, target):
     d = out - target
     return float(np.mean(d * d)), 2.0 * d / d.size

@@ -45,7 +45,8 @@ EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_
             "ax_batch_destroy", "ax_solve_batched", "ax_last_error",
             "ax_guessnet_create", "ax_guessnet_destroy", "ax_guessnet_num_params", "ax_guessnet_get_params",
             "ax_guessnet_set_params", "ax_guessnet_forward", "ax_guessnet_gradients", "ax_guessnet_train_step",
-            "ax_guessnet_save", "ax_guessnet_load", "ax_guessnet_features", "ax_guessnet_lift")
+            "ax_guessnet_save", "ax_guessnet_load", "ax_guessnet_features", "ax_guessnet_lift",
+            "ax_guessnet_set_loss", "ax_guessnet_features_pre")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "other": 6}
@@ -117,6 +118,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_guessnet_load.argtypes = [vp, ctypes.c_char_p]
     lib.ax_guessnet_features.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp, vp]
     lib.ax_guessnet_lift.argtypes = [vp, i32, i32, vp, i32, i32, vp, vp]
+    lib.ax_guessnet_set_loss.argtypes = [vp, dbl]
+    lib.ax_guessnet_features_pre.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp]
     lib.ax_kernel_launches.argtypes = []
     lib.ax_kernel_launches.restype = ctypes.c_int64
     lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
@@ -353,6 +356,15 @@ def ax_guessnet_load(net: int, path: str) -> None:
 def ax_guessnet_features(kappa, q, f, m: int, nr: int, nz: int, hw: int, x, scale, stream=None) -> None:
     _check(load_library().ax_guessnet_features(_ptr(kappa), _ptr(q), _ptr(f), m, nr, nz, hw, _ptr(x), _ptr(scale),
                                                _stream(stream)), "ax_guessnet_features")
+
+
+def ax_guessnet_set_loss(net: int, h1_weight: float) -> None:
+    _check(load_library().ax_guessnet_set_loss(net, float(h1_weight)), "ax_guessnet_set_loss")
+
+
+def ax_guessnet_features_pre(op, kappa, q, f, m: int, hw: int, x, scale, stream=None) -> None:
+    _check(load_library().ax_guessnet_features_pre(op, _ptr(kappa), _ptr(q), _ptr(f), m, hw, _ptr(x), _ptr(scale),
+                                                   _stream(stream)), "ax_guessnet_features_pre")
 
 
 def ax_guessnet_lift(y, m: int, hw: int, scale, nr: int, nz: int, u, stream=None) -> None:

@@ -397,16 +397,41 @@ __global__ void head_bwd_weight(const bf16 *__restrict__ a, const float *__restr
   if (threadIdx.x == 0) partial[(size_t)b * C + c] = (float)s;
 }
 
-// MSE loss: gy = 2 (y - t) / n; per-block partial sums of (y - t)^2.
-__global__ void mse_kernel(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ gy, size_t n,
-                           double *__restrict__ partial) {
+// Loss over n = B H W lattice values, d = y - t:
+//   loss = (1/n) [ sum d^2 + lam sum_{lattice edges (p, q)} (d_p - d_q)^2 ]
+// (lam = 0: mean squared error; the edge term is a discrete H1 seminorm, which
+// weighs an error the way the operator's energy norm does: smooth errors
+// little, pixel-scale noise much).  gy_p = (2/n) [d_p + lam sum_q (d_p - d_q)]
+// over the lattice neighbours q of p.  Per-block partial sums of the loss.
+__global__ void loss_kernel(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ gy,
+                            int B, int H, int W, float lam, double *__restrict__ partial) {
   __shared__ double red[8];
   double s = 0.0;
+  const size_t n = (size_t)B * H * W;
   const float sc = 2.0f / (float)n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float d = y[i] - t[i];
-    gy[i] = sc * d;
-    s += (double)d * d;
+    float g = d;
+    double e = (double)d * d;
+    if (lam != 0.f) {
+      const int x = (int)(i % W), yy = (int)((i / W) % H);
+      float lap = 0.f;
+      if (x > 0) lap += d - (y[i - 1] - t[i - 1]);
+      if (yy > 0) lap += d - (y[i - W] - t[i - W]);
+      if (x + 1 < W) {
+        const float dr = d - (y[i + 1] - t[i + 1]);
+        lap += dr;
+        e += (double)lam * dr * dr;
+      }
+      if (yy + 1 < H) {
+        const float dd = d - (y[i + W] - t[i + W]);
+        lap += dd;
+        e += (double)lam * dd * dd;
+      }
+      g = fmaf(lam, lap, d);
+    }
+    gy[i] = sc * g;
+    s += e;
   }
   s = block_sum(s, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -539,6 +564,7 @@ struct GuessNet {
   float *partial = nullptr;                                      // weight-gradient partials
   size_t partial_n = 0;
   double *lpart = nullptr;                                       // loss partials
+  float h1 = 0.f;                                                // weight of the loss's edge term
   int step = 0;
 };
 
@@ -817,7 +843,7 @@ int loss_and_grad(GuessNet *n, const float *target, int B, cudaStream_t s, doubl
   const size_t N = (size_t)B * n->hw * n->hw;
   const int blocks = std::min<int>(grid1d(N), 1024);
   note_launch();
-  mse_kernel<<<blocks, 256, 0, s>>>(n->y, target, n->gZ, N, n->lpart);
+  loss_kernel<<<blocks, 256, 0, s>>>(n->y, target, n->gZ, B, n->hw, n->hw, n->h1, n->lpart);
   std::vector<double> h(blocks);
   if (cudaMemcpyAsync(h.data(), n->lpart, blocks * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return AX_ERR_CUDA;
@@ -932,6 +958,13 @@ int ax_guessnet_forward(void *net, const float *x, float *y, int32_t batch, void
   forward_pass(n, x, batch, s);
   cudaMemcpyAsync(y, n->y, (size_t)batch * n->hw * n->hw * sizeof(float), cudaMemcpyDeviceToDevice, s);
   return cudaGetLastError() == cudaSuccess ? AX_OK : AX_ERR_CUDA;
+}
+
+int ax_guessnet_set_loss(void *net, double h1_weight) {
+  GuessNet *g = (GuessNet *)net;
+  if (!g || !(h1_weight >= 0.0) || h1_weight > 1e6) return AX_ERR_INVALID_ARG;
+  g->h1 = (float)h1_weight;
+  return AX_OK;
 }
 
 int ax_guessnet_gradients(void *net, const float *x, const float *target, int32_t batch, float *grad_host,

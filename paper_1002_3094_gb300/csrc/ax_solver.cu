@@ -1457,6 +1457,16 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
 
 }  // extern "C"
 
+// out[m][i][k] = r_i f[m][i][k], r_i = (i + 1/2) h_r (dense rows): the
+// right-hand side phi = r f of the r-weighted form.
+__global__ void scale_rows_by_r(const double *__restrict__ f, double *__restrict__ out, long long rows, int nr, int nz,
+                                double hr) {
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const double r = ((double)(row % nr) + 0.5) * hr;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) out[row * nz + k] = r * f[row * nz + k];
+  }
+}
+
 // ---- single-step entry points --------------------------------------------
 template <typename T>
 static int apply_step(ax_operator *op, const double *in, double *out, int m, int rows_per, int which,
@@ -1527,6 +1537,24 @@ int ax_apply_mode_solve(ax_operator *op, const double *in, double *out, int32_t 
 int ax_apply_preconditioner(ax_operator *op, const double *in, double *out, int32_t m, int32_t precision,
                             void *stream) {
   return apply_dispatch(op, in, out, m, op ? op->nr : 0, precision, 3, stream);
+}
+
+int ax_guessnet_features_pre(ax_operator *op, const double *kappa, const double *q, const double *f, int32_t m,
+                             int32_t hw, float *x, double *scale, void *stream) {
+  if (!op || !kappa || !q || !f || !x || !scale || m < 1 || hw < 1) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long rows = (long long)op->nr * m;
+  const size_t dense = (size_t)rows * op->nz;
+  int rc = ensure_stage(op, dense);
+  if (rc != AX_OK) return rc;
+  Workspace *w = op->ws;
+  note_launch();
+  scale_rows_by_r<<<(unsigned)std::min<long long>(rows, 65535), 256, 0, s>>>(f, w->stage_a, rows, op->nr, op->nz,
+                                                                           op->hr);
+  AX_CHECK_LAUNCH();
+  rc = apply_dispatch(op, w->stage_a, w->stage_b, m, op->nr, AX_PREC_FP32, 3, stream);
+  if (rc != AX_OK) return rc;
+  return ax_guessnet_features(kappa, q, w->stage_b, m, op->nr, op->nz, hw, x, scale, stream);
 }
 
 // ---- solve ------------------------------------------------------------------

@@ -2,11 +2,15 @@
 evaluation of the guess network (calls into libaxpcg only; PyTorch holds the
 device arrays).
 
-The network maps (log kappa, q, f / s) on an hw x hw lattice to u / s; the
-solver keeps its output as the starting iterate only when that lowers the
-initial residual (AX_FLAG_CHECK_GUESS), and always iterates to the requested
-tolerance.  Training pairs come from solves of random-field media
-(workload 4); held-out seeds come from a disjoint seed stream.
+The network maps (log kappa, q, g / s) on an hw x hw lattice to u / s, where
+g = B^-1 (r f) is the right-hand side after one application of the Laplace
+preconditioner (the averaged-coefficient solution; `pre=False` uses f
+itself) and s = max |g|; the network then only has to correct g for the
+variable kappa.  The solver keeps the network's output as the starting
+iterate only when that lowers the initial preconditioned residual
+(AX_FLAG_CHECK_GUESS), and always iterates to the requested tolerance.
+Training pairs come from solves of random-field media (workload 4); held-out
+seeds come from a disjoint seed stream.
 """
 from __future__ import annotations
 
@@ -14,9 +18,10 @@ import time
 
 import numpy as np
 
-from . import (AX_FLAG_CHECK_GUESS, AX_FLAG_USE_GUESS, AX_PCG_MIXED, ax_batch_create, ax_batch_destroy,
-               ax_batch_solve, ax_destroy_operator, ax_guessnet_features, ax_guessnet_forward,
-               ax_guessnet_lift, ax_guessnet_train_step, ax_setup_operator, ax_solve)
+from . import (AX_FLAG_CHECK_GUESS, AX_FLAG_USE_GUESS, AX_PCG_MIXED, AX_PREC_FP64, ax_apply_operator,
+               ax_apply_preconditioner, ax_batch_create, ax_batch_destroy, ax_batch_solve, ax_destroy_operator,
+               ax_guessnet_features, ax_guessnet_features_pre, ax_guessnet_forward, ax_guessnet_lift,
+               ax_guessnet_train_step, ax_setup_operator, ax_solve)
 from .inputs import sample_points
 
 
@@ -53,7 +58,18 @@ def grf_fields(specs, nr: int, nz: int, device):
     return torch.stack(kr), torch.stack(kz), torch.stack(qq), torch.stack(ff)
 
 
-def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=None, target_scale: float = 0.0):
+def _features(data, i, x, s):
+    """Features of sample i into x [1][3][hw][hw] and its scale into s [1]."""
+    hw = x.shape[-1]
+    if data["pre"]:
+        ax_guessnet_features_pre(data["ops"][i], data["kr"][i], data["q"][i], data["f"][i], 1, hw, x, s)
+    else:
+        nr, nz = data["f"].shape[1:]
+        ax_guessnet_features(data["kr"][i], data["q"][i], data["f"][i], 1, nr, nz, hw, x, s)
+
+
+def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=None, target_scale: float = 0.0,
+                 pre: bool = True):
     """Solves every medium with the batched solver and returns features x
     [n][3][hw][hw], targets u / s [n][hw][hw] (FP32 torch tensors), the
     operators' inputs and the solutions (FP64)."""
@@ -67,8 +83,9 @@ def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=Non
     ax_batch_destroy(batch)
     x = torch.zeros((n, 3, hw, hw), dtype=torch.float32, device=device)
     s = torch.zeros(n, dtype=torch.float64, device=device)
+    data = {"kr": kr, "q": q, "f": f, "ops": ops, "pre": pre}
     for i in range(n):
-        ax_guessnet_features(kr[i], q[i], f[i], 1, nr, nz, hw, x[i], s[i:i + 1])
+        _features(data, i, x[i:i + 1], s[i:i + 1])
     # targets on the lattice: cell averages of u / s (the lattice equals the grid
     # here when nr = nz = hw)
     if nr == hw and nz == hw:
@@ -78,8 +95,9 @@ def make_dataset(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=Non
     # u / s is small (~1e-3); the network learns the target scaled to unit
     # spread, and its output is divided by the same factor at solve time
     tscale = target_scale if target_scale else float(1.0 / y.std().item())
-    return {"x": x, "y": (y * tscale).contiguous(), "kr": kr, "kz": kz, "q": q, "f": f, "u": u, "s": s,
-            "ops": ops, "iters": [i["iters"] for i in info], "tscale": tscale}
+    data.update({"x": x, "y": (y * tscale).contiguous(), "kz": kz, "u": u, "s": s,
+                 "iters": [i["iters"] for i in info], "tscale": tscale})
+    return data
 
 
 def train(net: int, data, epochs: int, batch: int, lr: float, seed: int = 0, log=None):
@@ -109,7 +127,7 @@ def guess_for(net: int, data, i: int, hw: int, nr: int, nz: int):
     dev = data["f"].device
     x = torch.zeros((1, 3, hw, hw), dtype=torch.float32, device=dev)
     s = torch.zeros(1, dtype=torch.float64, device=dev)
-    ax_guessnet_features(data["kr"][i], data["q"][i], data["f"][i], 1, nr, nz, hw, x, s)
+    _features(data, i, x, s)
     y = torch.zeros((1, hw, hw), dtype=torch.float32, device=dev)
     ax_guessnet_forward(net, x, y, 1)
     u0 = torch.zeros((1, nr, nz), dtype=torch.float64, device=dev)
@@ -117,9 +135,27 @@ def guess_for(net: int, data, i: int, hw: int, nr: int, nz: int):
     return u0
 
 
+def energy_ratio(op, f, u0):
+    """sqrt((r0, B^-1 r0) / (phi, B^-1 phi)) for r0 = phi - A u0, phi = r f: the
+    quantity the solver's guess gate compares with 1 (diagnostic, FP64)."""
+    import torch
+    from .inputs import sample_points
+    nr, nz = f.shape[-2:]
+    rn = torch.as_tensor(sample_points(nr, nz)[0], dtype=torch.float64, device=f.device)
+    phi = (rn[:, None] * f.reshape(nr, nz)).reshape(1, nr, nz).contiguous()
+    au = torch.zeros_like(phi)
+    ax_apply_operator(op, u0.reshape(1, nr, nz).contiguous(), au, 1, AX_PREC_FP64)
+    r0 = phi - au
+    br, bp = torch.zeros_like(phi), torch.zeros_like(phi)
+    ax_apply_preconditioner(op, r0, br, 1, AX_PREC_FP64)
+    ax_apply_preconditioner(op, phi, bp, 1, AX_PREC_FP64)
+    return float(torch.sqrt((r0 * br).sum() / (phi * bp).sum()))
+
+
 def evaluate(net: int, data, hw: int, nr: int, nz: int, tol: float = 1e-8, method: int = AX_PCG_MIXED):
     """Per held-out sample: iterations and wall time from zero and from the
-    network's guess (guess time included), with the residual gate on."""
+    network's guess (guess time included), with the residual gate on, and
+    the guess's gate ratio (energy_ratio)."""
     import torch
     rows = []
     for i, op in enumerate(data["ops"]):
@@ -138,7 +174,8 @@ def evaluate(net: int, data, hw: int, nr: int, nz: int, tol: float = 1e-8, metho
         t2 = time.perf_counter()
         rows.append({"iters_zero": i0[0]["iters"], "iters_guess": ig[0]["iters"], "ms_zero": 1e3 * (t1 - t0),
                      "ms_guess": 1e3 * (t2 - t1), "accepted": ig[0]["guess_accepted"],
-                     "res_zero": i0[0]["rel_res"], "res_guess": ig[0]["rel_res"]})
+                     "res_zero": i0[0]["rel_res"], "res_guess": ig[0]["rel_res"],
+                     "energy_ratio": energy_ratio(op, f, guess_for(net, data, i, hw, nr, nz))})
     return rows
 
 

@@ -8,7 +8,8 @@ accumulation, a BF16 rounding that falls the other way when the two
 accumulations straddle a rounding boundary, and the first layer's weight
 gradient, which reads the FP32 input rather than its BF16 copy.
 Tolerances (relative, 2-norm): forward output 5e-3, every layer's weight and
-bias gradient 2e-2.  Against the unrounded FP64 network the gradients of the
+bias gradient 2e-2, for the plain squared error and for the loss with the
+lattice-edge (H1) term.  Against the unrounded FP64 network the gradients of the
 4x4 bottleneck layers differ by up to ~25% (ReLU decisions that BF16 storage
 flips), which is why the rounding is matched instead of the tolerance
 widened.  The reference backward is itself pinned to finite differences in
@@ -101,9 +102,11 @@ def test_forward_matches_reference(cuda):
     P.ax_guessnet_destroy(net)
 
 
-def test_gradients_match_reference(cuda):
+def _check_gradients(cuda, h1):
     arch = G.architecture(ch=CH)
     net = P.ax_guessnet_create(HW, CH, batch_capacity=4, seed=9)
+    if h1:
+        P.ax_guessnet_set_loss(net, h1)
     rng = np.random.default_rng(3)
     flat = P.ax_guessnet_get_params(net)
     flat = flat + rng.normal(0, 0.05, size=flat.size).astype(np.float32) * (np.abs(flat) == 0)  # non-zero biases
@@ -112,17 +115,16 @@ def test_gradients_match_reference(cuda):
     B = 2
     x, t = _inputs(B, 5)
     loss, g = P.ax_guessnet_gradients(net, torch.from_numpy(x).to(cuda), torch.from_numpy(t).to(cuda), B)
-    # reference: loss = mean over the whole batch
+    # reference: the loss is the mean over the batch of the per-sample loss
     gsum, lsum = None, 0.0
-    N = B * HW * HW
     for b in range(B):
         out, cache = G.forward(params, arch, x[b].astype(np.float64), store=G.round_bf16)
-        d = out - t[b]
-        lsum += float(np.sum(d * d))
-        grads, _ = G.backward(params, arch, cache, 2.0 * d / N)
+        lb, gout = G.h1_loss(out, t[b], h1)
+        lsum += lb / B
+        grads, _ = G.backward(params, arch, cache, gout / B)
         fg = _flat_grads(grads, arch)
         gsum = fg if gsum is None else gsum + fg
-    assert abs(loss - lsum / N) <= 5e-3 * (lsum / N)
+    assert abs(loss - lsum) <= 5e-3 * lsum
     off = 0
     for name, cin, cout, kind in arch:
         if kind not in "csh":
@@ -133,6 +135,14 @@ def test_gradients_match_reference(cuda):
             off += n
             assert np.linalg.norm(a - r) <= 2e-2 * np.linalg.norm(r) + 1e-7, (name, part)
     P.ax_guessnet_destroy(net)
+
+
+def test_gradients_match_reference(cuda):
+    _check_gradients(cuda, 0.0)
+
+
+def test_h1_loss_gradients_match_reference(cuda):
+    _check_gradients(cuda, 3.0)
 
 
 def test_training_lowers_loss_and_checkpoint_round_trip(cuda):

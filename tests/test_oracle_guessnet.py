@@ -104,3 +104,31 @@ def test_store_rounding_applies_to_every_kept_activation():
     # rounding kept activations to 8 significant bits moves the output by
     # about the BF16 unit roundoff times the depth, not more
     assert 0 < np.linalg.norm(out - ref) <= 5e-2 * np.linalg.norm(ref)
+
+
+def test_h1_loss_closed_forms_and_finite_differences():
+    rng = np.random.default_rng(6)
+    H, W = 5, 7
+    t = rng.normal(size=(1, H, W))
+    # lam = 0 is the mean squared error
+    out = rng.normal(size=(1, H, W))
+    l0, g0 = G.h1_loss(out, t, 0.0)
+    lm, gm = G.mse_loss(out, t)
+    assert np.isclose(l0, lm) and np.allclose(g0, gm)
+    # a constant error has no edge term
+    l, g = G.h1_loss(t + 0.3, t, 5.0)
+    assert np.isclose(l, 0.09) and np.allclose(g, 2 * 0.3 / (H * W))
+    # a ramp a*x along the last axis: H (W - 1) edges of squared difference a^2
+    a = 0.2
+    ramp = a * np.arange(W)[None, None, :] * np.ones((1, H, 1))
+    l, _ = G.h1_loss(t + ramp, t, 3.0)
+    assert np.isclose(l, (np.sum(ramp ** 2) + 3.0 * H * (W - 1) * a * a) / (H * W))
+    # gradient against central differences
+    lam, eps = 2.5, 1e-6
+    _, g = G.h1_loss(out, t, lam)
+    for idx in [(0, 0, 0), (0, 2, 3), (0, H - 1, W - 1), (0, 4, 0)]:
+        op, om = out.copy(), out.copy()
+        op[idx] += eps
+        om[idx] -= eps
+        fd = (G.h1_loss(op, t, lam)[0] - G.h1_loss(om, t, lam)[0]) / (2 * eps)
+        assert abs(fd - g[idx]) <= 1e-7 * max(1.0, abs(fd))
