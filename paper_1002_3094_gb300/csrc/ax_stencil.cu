@@ -82,7 +82,27 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     load_vec<T>(c + (size_t)i * a.pitch + k0, v);
   };
 
-  T pm[V], pc[V], pn[V], crl[V], crh[V];
+  // Everything row i + 1 needs (values, its CR / CZ / W rows and the two
+  // warp-edge halo values) is loaded one row ahead, while row i is computed.
+  auto load_halo = [&](int i, T &left, T &right, T &czlast) {
+    const size_t rowoff = base + (size_t)i * a.pitch;
+    left = right = czlast = T(0);
+    if (lane == 0 && col_ok && k0 > 0) left = StencilValue<T, MODE>::at(a, p_old, rowoff + k0 - 1, beta);
+    if (lane == 31) {
+      if (k0 + V < nz) right = StencilValue<T, MODE>::at(a, p_old, rowoff + k0 + V, beta);
+      if (k0 + V <= nz) czlast = CZ[(size_t)i * a.pitchz + k0 + V];
+    }
+  };
+  auto load_cz = [&](int i, T (&v)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) v[e] = T(0);
+    // Faces run to index nz, so the lane just past the last node still loads
+    // its first face (the upper face of node nz - 1, fetched by the shuffle).
+    if (k0 <= nz) load_vec<T>(CZ + (size_t)i * a.pitchz + k0, v);
+  };
+
+  T pm[V], pc[V], pn[V], crl[V], crh[V], czl[V], w[V];
+  T left, right, czlast;
   if (i0 > 0) {
     load_row(i0 - 1, pm);
     load_coef(CR, i0 - 1, crl);
@@ -91,40 +111,48 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     for (int e = 0; e < V; ++e) { pm[e] = T(0); crl[e] = T(0); }
   }
   load_row(i0, pc);
+  load_coef(CR, i0, crh);
+  load_cz(i0, czl);
+  load_coef(Wc, i0, w);
+  load_halo(i0, left, right, czlast);
 
   // FP32 partials per thread are short sums (<= 64 terms); the CTA and grid
   // combination is FP64.
   T acc = T(0);
   for (int i = i0; i < i1; ++i) {
+    T crn[V], czn[V], wn[V], leftn = T(0), rightn = T(0), czlastn = T(0);
     if (i + 1 < nr) {
       load_row(i + 1, pn);
     } else {
 #pragma unroll
       for (int e = 0; e < V; ++e) pn[e] = T(0);
     }
+    if (i + 1 < i1) {
+      load_coef(CR, i + 1, crn);
+      load_cz(i + 1, czn);
+      load_coef(Wc, i + 1, wn);
+      load_halo(i + 1, leftn, rightn, czlastn);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) crn[e] = czn[e] = wn[e] = T(0);
+    }
     const size_t rowoff = base + (size_t)i * a.pitch;
     // z-neighbours of the lane's first and last node.
-    T left = __shfl_up_sync(0xffffffffu, pc[V - 1], 1);
-    T right = __shfl_down_sync(0xffffffffu, pc[0], 1);
-    if (lane == 0) left = (col_ok && k0 > 0) ? StencilValue<T, MODE>::at(a, p_old, rowoff + k0 - 1, beta) : T(0);
-    if (lane == 31) right = (k0 + V < nz) ? StencilValue<T, MODE>::at(a, p_old, rowoff + k0 + V, beta) : T(0);
-    T czl[V], w[V];
-    load_coef(CR, i, crh);
-#pragma unroll
-    for (int e = 0; e < V; ++e) czl[e] = T(0);
-    // Faces run to index nz, so the lane just past the last node still loads
-    // its first face (the upper face of node nz - 1, fetched by the shuffle).
-    if (k0 <= nz) load_vec<T>(CZ + (size_t)i * a.pitchz + k0, czl);
-    T czlast = __shfl_down_sync(0xffffffffu, czl[0], 1);
-    if (lane == 31) czlast = (k0 + V <= nz) ? CZ[(size_t)i * a.pitchz + k0 + V] : T(0);
-    load_coef(Wc, i, w);
+    T l = __shfl_up_sync(0xffffffffu, pc[V - 1], 1);
+    T r = __shfl_down_sync(0xffffffffu, pc[0], 1);
+    T czh_last = __shfl_down_sync(0xffffffffu, czl[0], 1);
+    if (lane == 0) l = left;
+    if (lane == 31) {
+      r = right;
+      czh_last = czlast;
+    }
 
     T o[V];
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-      const T yl = (e == 0) ? left : pc[e - 1];
-      const T yr = (e == V - 1) ? right : pc[e + 1];
-      const T czh = (e == V - 1) ? czlast : czl[e + 1];
+      const T yl = (e == 0) ? l : pc[e - 1];
+      const T yr = (e == V - 1) ? r : pc[e + 1];
+      const T czh = (e == V - 1) ? czh_last : czl[e + 1];
       const T y = pc[e];
       T v = w[e] * y;
       v = fma(crh[e], y - pn[e], v);
@@ -172,7 +200,13 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
       pm[e] = pc[e];
       pc[e] = pn[e];
       crl[e] = crh[e];
+      crh[e] = crn[e];
+      czl[e] = czn[e];
+      w[e] = wn[e];
     }
+    left = leftn;
+    right = rightn;
+    czlast = czlastn;
   }
   if (MODE != kStencilApply) {
     const double s = block_sum((double)acc, red);
