@@ -80,7 +80,13 @@ enum {
                                right-hand side from zero (AX_PCG_FP64, AX_PCG_MIXED;
                                info.guess_accepted tells which; costs two B^-1 applications)  */
 };
-enum { AX_PREC_FP64 = 0, AX_PREC_FP32 = 1 };
+/* AX_PREC_FP32_TC, AX_PREC_FP32_TC3 (single-step entry points, transform and
+ * preconditioner only): FP32 data through the tensor-core sine transform.  The
+ * input is split into BF16 halves, hi = bf16(x), lo = bf16(x - hi), and
+ * multiplied in FP32 accumulation by S_hi = bf16(S) (TC: the products hi S_hi
+ * + lo S_hi) or by S_hi + S_lo, S_lo = bf16(S - S_hi) (TC3: + hi S_lo, S to
+ * about 2^-16).  See the option "dst_tensor". */
+enum { AX_PREC_FP64 = 0, AX_PREC_FP32 = 1, AX_PREC_FP32_TC = 2, AX_PREC_FP32_TC3 = 3 };
 
 typedef struct {
   int32_t nr, nz;   /* unknowns along r and z (>= 1)                                        */
@@ -131,6 +137,13 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *   "replace_delta"  AX_PCG_MIXED: recursive-residual reduction (relative to the
  *                    last FP64 true residual) that triggers the next FP64
  *                    residual replacement (0 < v < 1, default 1e-2)
+ *   "dst_tensor"     AX_PCG_MIXED's FP32 kernels transform along z with the
+ *                    tcgen05 tensor-core GEMM: 1 by S_hi + S_lo (three BF16
+ *                    products, S to about 2^-16), 2 by S_hi = bf16(S) alone
+ *                    (two products; a fixed symmetric matrix within ~3e-3 of
+ *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
+ *                    close to B^-1); 0: the FFT transform (default).  nz <=
+ *                    2048, else AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */

@@ -34,6 +34,8 @@ AX_FLAG_SERIAL_GROUPS = 16
 
 AX_PREC_FP64 = 0
 AX_PREC_FP32 = 1
+AX_PREC_FP32_TC = 2
+AX_PREC_FP32_TC3 = 3
 
 METHODS = {"pcg64": AX_PCG_FP64, "cheb64": AX_CHEB_FP64, "pcg_mixed": AX_PCG_MIXED,
            "cheb_mixed": AX_CHEB_MIXED}

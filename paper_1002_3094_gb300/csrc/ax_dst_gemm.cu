@@ -1,0 +1,355 @@
+// Sine transform along z as a dense GEMM on the tcgen05 tensor cores, for the
+// FP32 working precision of the mixed method (the z-transform of the
+// preconditioner of Section 4.2, Eq. fft_phi, written as a matrix product):
+//
+//     out[row][l] = sum_k in[row][k] S^[k][l],   S^ = S_hi (+ S_lo),
+//     S[k][l] = sqrt(2/L) sin(pi (k+1) (l+1) / L),   L = nz + 1,
+//     S_hi = bf16(S),  S_lo = bf16(S - S_hi).
+//
+// The input arrives split, in = hi + lo with hi = bf16(in), lo = bf16(in - hi)
+// (|in - hi - lo| <= 2^-17 |in|), in the tile layout of ax_common.cuh, written
+// by the kernel that produced it.  The products hi S_hi + lo S_hi (and, with
+// `three`, + hi S_lo) accumulate in FP32 in the tensor memory.  Without the
+// third product the transform multiplies by S_hi: a fixed symmetric matrix
+// within ~3e-3 (spectral norm) of S, so the preconditioner S_hi T^-1 S_hi is
+// still symmetric positive definite and close to B^-1; with it the transform
+// is S to about 2^-16.  Either way the FP64 residual replacement keeps the
+// solution accuracy.
+//
+// Tiles: 128 rows x 256 output columns per CTA, K in blocks of 64 through a
+// ring of shared-memory stages (3 of 64 KB, or 2 of 96 KB with S_lo), each
+// filled by bulk copies (cp.async.bulk) of one 32 KB input tile and one or
+// two 32 KB tiles of S (stored in the same layout, symmetric: row l, column k).
+// Warp roles: warp 0 lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16,
+// BF16 x BF16 -> FP32 in 256 TMEM columns); warp 1 lane 0 issues the copies;
+// warps 4..7 run the epilogue (tcgen05.ld -> global, optional (r, out)
+// partial).  Every mbarrier wait is bounded; on expiry the CTA records the
+// failure in *err, stops issuing work, waits (bounded) for its MMAs and frees
+// its TMEM.
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include <vector>
+#include "ax_common.cuh"
+
+namespace ax {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64;
+constexpr int kATileBytes = kSplitTileBytes;                // hi and lo halves, 32 KB
+constexpr int kBTileBytes = kBN * kBK * 2;                  // 32 KB
+constexpr int kGemmThreads = 256;
+constexpr unsigned kWaitPolls = 1u << 22;
+
+template <int THREE> struct GemmStages {
+  static constexpr int stage_bytes = kATileBytes + (1 + THREE) * kBTileBytes;
+  static constexpr int stages = THREE ? 2 : 3;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false when it expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  for (unsigned i = 0; i < kWaitPolls; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
+// Core matrices of 8 rows x 16 bytes (128 contiguous bytes); the two core
+// matrices of one K = 16 step are 128 bytes apart (leading byte offset), and
+// consecutive 8-row groups 1024 bytes apart (stride byte offset; a tile row
+// group holds the 8 core matrices of K = 64).  Bits 46-47: descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+  const unsigned a = smem_u32(p);
+  return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+constexpr unsigned kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kBN >> 3) << 17) |
+                            ((unsigned)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void umma(unsigned d_tmem, uint64_t a, uint64_t b, unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns: thread i of the warp gets
+// lane (base + i), columns col .. col + 31.
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tiles in shared memory: byte offset of element (row, k) of a K = 64 block is
+// (row / 8) 1024 + (k / 8) 128 + (row % 8) 16 + (k % 8) 2.
+
+template <int THREE>
+__global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDstArgs a) {
+  constexpr int kStageBytes = GemmStages<THREE>::stage_bytes;
+  constexpr int kStages = GemmStages<THREE>::stages;
+  extern __shared__ __align__(1024) unsigned char gsm_raw[];
+  unsigned char *gsm =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ unsigned tmem_base;
+  __shared__ int abort_flag;
+  __shared__ double red[4];
+
+  const int nt = blockIdx.x;
+  const int m = blockIdx.y / a.mtiles;
+  const int mt = blockIdx.y - m * a.mtiles;
+  if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = mt * kBM;
+  const int KB = a.ktiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"((unsigned)kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      bool ok = true;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % kStages;
+        if (!mbar_wait(&full_bar[s], (unsigned)(kb / kStages) & 1u)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        unsigned char *st = gsm + s * kStageBytes;
+#pragma unroll
+        for (int j = 0; j < kBK / 16; ++j) {
+          const uint64_t ahi = smem_desc(st + j * 256), alo = smem_desc(st + kATileBytes / 2 + j * 256);
+          const uint64_t bhi = smem_desc(st + kATileBytes + j * 256);
+          umma(tmem, ahi, bhi, (kb | j) != 0);
+          umma(tmem, alo, bhi, 1u);
+          if (THREE) umma(tmem, ahi, smem_desc(st + kATileBytes + kBTileBytes + j * 256), 1u);
+        }
+        umma_commit(&empty_bar[s]);
+      }
+      if (!ok) {
+        atomicExch(&abort_flag, 1);
+        if (a.err) atomicExch(a.err, 1);
+      }
+      umma_commit(&done_bar);  // arrives once every MMA issued above has completed
+    }
+  } else if (warp == 1) {
+    // ---- bulk copies: input tile (m, mt, kb) and the S tiles (nt, kb) ----
+    if (lane == 0) {
+      const unsigned char *ga = a.A + ((size_t)m * a.mtiles + mt) * KB * (size_t)kATileBytes;
+      const unsigned char *gb = reinterpret_cast<const unsigned char *>(a.SB) + (size_t)nt * KB * 2 * kBTileBytes;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(kb / kStages - 1) & 1u)) {
+          atomicExch(&abort_flag, 1);
+          if (a.err) atomicExch(a.err, 1);
+          break;
+        }
+        unsigned char *st = gsm + s * kStageBytes;
+        mbar_arrive_tx(&full_bar[s], (unsigned)(kATileBytes + (1 + THREE) * kBTileBytes));
+        bulk_g2s(st, ga + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
+        bulk_g2s(st + kATileBytes, gb + (size_t)kb * 2 * kBTileBytes, kBTileBytes, &full_bar[s]);
+        if (THREE)
+          bulk_g2s(st + kATileBytes + kBTileBytes, gb + ((size_t)kb * 2 + 1) * kBTileBytes, kBTileBytes,
+                   &full_bar[s]);
+      }
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue: TMEM -> registers -> global (and the (r, out) partial) ----
+    const int tid = threadIdx.x - 128;
+    const int q = warp - 4;  // TMEM lane quarter of this warp
+    const bool ok = mbar_wait(&done_bar, 0u);
+    if (!ok) {
+      atomicExch(&abort_flag, 1);
+      if (a.err) atomicExch(a.err, 1);
+    }
+    tc_fence_after();
+    const int grow = row0 + q * 32 + lane;
+    float acc = 0.f;
+    // warp-uniform decision (tcgen05.ld is a warp-collective instruction)
+    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
+      float *outr = a.out + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
+      const float *rr = (a.r != nullptr) ? a.r + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch : nullptr;
+#pragma unroll 1
+      for (int c = 0; c < kBN / 32; ++c) {
+        const int l0 = nt * kBN + c * 32;
+        if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= a.pitch) break;  // nothing left for this warp
+        float v[32];
+        tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(c * 32), v);
+        if (grow < a.nr) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            // columns up to the pitch: S is zero beyond nz, so the padding
+            // columns receive the zeros they must hold
+            if (l0 + i < a.pitch) {
+              *reinterpret_cast<float4 *>(outr + l0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+              if (rr) {
+                const float4 r4 = *reinterpret_cast<const float4 *>(rr + l0 + i);
+                acc = fmaf(r4.x, v[i], acc);
+                acc = fmaf(r4.y, v[i + 1], acc);
+                acc = fmaf(r4.z, v[i + 2], acc);
+                acc = fmaf(r4.w, v[i + 3], acc);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (a.partial) {
+      double s = warp_sum((double)acc);
+      if (lane == 0) red[q] = s;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (tid == 0) a.partial[(size_t)m * kPartialStride + mt * gridDim.x + nt] = red[0] + red[1] + red[2] + red[3];
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    // the MMAs are complete once done_bar fired; if a wait expired, wait once
+    // more (bounded) before the columns are released
+    if (abort_flag) mbar_wait(&done_bar, 0u);
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)kBN) : "memory");
+  }
+}
+
+}  // namespace
+
+size_t dst_gemm_smem_bytes(int three) {
+  return three ? (size_t)GemmStages<1>::stages * GemmStages<1>::stage_bytes + 1024
+               : (size_t)GemmStages<0>::stages * GemmStages<0>::stage_bytes + 1024;
+}
+
+int dst_gemm_ktiles(int n) { return (n + kBK - 1) / kBK; }
+int dst_gemm_ntiles(int n) { return (n + kBN - 1) / kBN; }
+int dst_gemm_mtiles(int rows) { return (rows + kBM - 1) / kBM; }
+
+// S tiles: for every N tile (256 output columns) and K block (64 inputs) a
+// 32 KB tile of S_hi and one of S_lo, each in the shared-memory layout above
+// holding S[k][l] at (row l, column k) (S is symmetric).  Values in FP64,
+// rounded to BF16 (nearest, ties to even, by way of FP32).
+std::vector<uint16_t> dst_gemm_table(int n) {
+  const int KB = dst_gemm_ktiles(n), NT = dst_gemm_ntiles(n);
+  const int L = n + 1;
+  const double sc = std::sqrt(2.0 / L);
+  auto to_bf16 = [](double x) -> uint16_t {
+    const float v = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+  };
+  auto from_bf16 = [](uint16_t h) -> double {
+    const uint32_t u = (uint32_t)h << 16;
+    float v;
+    std::memcpy(&v, &u, 4);
+    return v;
+  };
+  const size_t tile = (size_t)kBN * kBK;  // elements of one 32 KB tile
+  std::vector<uint16_t> t((size_t)NT * KB * 2 * tile, 0);
+  for (int nt = 0; nt < NT; ++nt)
+    for (int kb = 0; kb < KB; ++kb) {
+      uint16_t *hi = t.data() + ((size_t)nt * KB + kb) * 2 * tile;
+      uint16_t *lo = hi + tile;
+      for (int nl = 0; nl < kBN; ++nl) {
+        const int l = nt * kBN + nl;
+        if (l >= n) continue;
+        for (int kl = 0; kl < kBK; ++kl) {
+          const int k = kb * kBK + kl;
+          if (k >= n) continue;
+          const long long e = ((long long)(k + 1) * (l + 1)) % (2LL * L);  // sin(pi e / L), e reduced
+          const double v = sc * std::sin(M_PI * (double)e / L);
+          const uint16_t h = to_bf16(v);
+          const int off = ((nl >> 3) * 1024 + (kl >> 3) * 128 + (nl & 7) * 16 + (kl & 7) * 2) / 2;
+          hi[off] = h;
+          lo[off] = to_bf16(v - from_bf16(h));
+        }
+      }
+    }
+  return t;
+}
+
+void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s) {
+  const size_t smem = dst_gemm_smem_bytes(a.three);
+  dim3 grid(a.ntiles, a.m * a.mtiles);
+  note_launch();
+  if (a.three) {
+    ensure_smem_attr((const void *)dst_gemm_kernel<1>, smem);
+    dst_gemm_kernel<1><<<grid, kGemmThreads, smem, s>>>(a);
+  } else {
+    ensure_smem_attr((const void *)dst_gemm_kernel<0>, smem);
+    dst_gemm_kernel<0><<<grid, kGemmThreads, smem, s>>>(a);
+  }
+}
+
+}  // namespace ax

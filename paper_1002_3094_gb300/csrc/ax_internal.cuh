@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <cstddef>
+#include <vector>
 
 #include "../../include/axpcg.h"
 
@@ -80,6 +81,7 @@ struct Coef {
   T *HW = nullptr;   // [2 L]         (cos, sin)(pi j / L),   j < L
   T *RK = nullptr;   // [2 P]         Rader: DFT of the permuted kernel W^(g^-m)
   T *RT = nullptr;   // [2 P]         Rader: (cos, sin)(2 pi j / P)
+  uint16_t *SB = nullptr;  // FP32 only: BF16 DST matrix tiles of the tensor-core transform
 };
 
 // Scalar state of one right-hand side during an iteration.  Lives in device
@@ -137,6 +139,8 @@ struct ax_operator {
   int device = 0;
   ax::FftPlan plan;
   int *rader_perm = nullptr;  // [2 P] device
+  int dst_tc = 0;             // 1: the FP32 PCG path transforms with the tensor-core GEMM
+  int *tc_err = nullptr;      // device flag: a bounded wait of the GEMM expired
   ax::Coef<double> c64;
   ax::Coef<float> c32;
   ax::Workspace *ws = nullptr;
@@ -211,6 +215,29 @@ int dst_prepare_device();  // constant tables of the unrolled prime radices (onc
 int dst_prepare_f64();
 size_t dst_smem_bytes(int L, int elem_bytes);
 
+// Tensor-core sine transform (input split into BF16 halves in the tile layout
+// of ax_common.cuh, BF16 DST matrix, FP32 accumulation).
+struct GemmDstArgs {
+  const unsigned char *A;  // split input, tiles (m, mtiles, ktiles)
+  float *out;              // rows of the output field (columns up to pitch written)
+  const uint16_t *SB;      // S_hi / S_lo tiles (dst_gemm_table)
+  int n, nr, pitch;        // n = nz; rows per RHS
+  long long field;         // elements per RHS of out
+  int m, mtiles, ntiles, ktiles;
+  int three;               // 1: add hi S_lo (the transform is S to ~2^-16)
+  const float *r;          // non-null: per-CTA partials of (r, out) into partial
+  double *partial;         // [m][kPartialStride], slot mt * ntiles + nt
+  const RhsState *st;
+  int mask;
+  int *err;                // set to 1 when a bounded wait expired
+};
+void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
+size_t dst_gemm_smem_bytes(int three);
+int dst_gemm_ktiles(int n);
+int dst_gemm_ntiles(int n);
+int dst_gemm_mtiles(int rows);
+std::vector<uint16_t> dst_gemm_table(int n);
+
 template <typename T>
 struct TriArgs {
   const T *IP, *E;
@@ -222,9 +249,15 @@ struct TriArgs {
   T *out;                  // may alias in
   const RhsState *st;
   int mask;
+  // FP32 tile kernel only: if set, the solution is written split into BF16
+  // halves (layout of ax_common.cuh, tiles mtiles x ktiles) instead of to out
+  unsigned char *split;
+  int split_mtiles, split_ktiles;
 };
 
 template <typename T>
 void launch_tridiag(const TriArgs<T> &a, cudaStream_t s);
+// whether launch_tridiag<float> can write the split layout for these sizes
+bool tridiag_split_ok(int nr);
 
 }  // namespace ax

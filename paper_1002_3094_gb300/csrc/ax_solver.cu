@@ -63,6 +63,8 @@ struct Workspace {
   size_t stage_elems = 0;
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+  unsigned char *split = nullptr;  // BF16 split operand of the tensor-core transform
+  size_t split_bytes = 0;
   cudaStream_t cap = nullptr;
   GraphCache g64, g32, gc64, gc32;
   // options
@@ -235,6 +237,17 @@ int ensure_stage(ax_operator *op, size_t elems) {
   return AX_OK;
 }
 
+int ensure_split(ax_operator *op, size_t bytes) {
+  std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
+  Workspace *w = op->ws;
+  if (w->split_bytes >= bytes) return AX_OK;
+  dfree(w->split);
+  w->split_bytes = 0;
+  AX_TRY(dalloc(&w->split, bytes));  // zero: padding rows and columns stay zero
+  w->split_bytes = bytes;
+  return AX_OK;
+}
+
 int ensure_scratch(ax_operator *op, size_t bytes) {
   std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
   Workspace *w = op->ws;
@@ -362,6 +375,84 @@ __global__ void fold_correction(double *__restrict__ x, float *__restrict__ d, s
     x2[2 * e] = a;
     x2[2 * e + 1] = b;
     d4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Task t of a right-hand side: 8 consecutive columns of one row, ordered like
+// the split layout (8 rows of one column chunk, then 8 chunks, then row groups
+// of a 128 x 64 tile, then tiles), so that a warp reads 8 rows x 128 bytes
+// and writes 512 contiguous bytes of each split half.
+__device__ __forceinline__ void split_task(int t, int ktiles, int &row, int &col) {
+  const int tile = t >> 10, w = t & 1023;
+  const int mt = tile / ktiles, kb = tile - mt * ktiles;
+  row = mt * 128 + (w >> 6) * 8 + (w & 7);
+  col = kb * 64 + ((w >> 3) & 7) * 8;
+}
+
+// x += alpha p, r -= alpha q for the selected right-hand sides, with per-block
+// partials of ||r||^2 and the new r written split into BF16 halves for the
+// tensor-core transform: the update that the FFT forward transform fuses into
+// its load phase.  p is pb for an even iteration count, pa for an odd one (as
+// in the stencil).
+constexpr int kUpdateBlocks = 64;  // CTAs per right-hand side
+__global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *__restrict__ r,
+                                                  const float *__restrict__ q, const float *__restrict__ pa,
+                                                  const float *__restrict__ pb, int nr, int pitch, size_t field,
+                                                  int mtiles, int ktiles, unsigned char *__restrict__ split,
+                                                  const RhsState *st, int mask, double *__restrict__ partial) {
+  __shared__ double red[8];
+  const int m = blockIdx.y;
+  if (!rhs_selected(st, mask, m)) return;
+  const float alpha = (float)st[m].alpha;
+  const float *p = (st[m].iters & 1) ? pa : pb;
+  const int tasks = mtiles * ktiles * 1024;
+  float acc = 0.f;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
+    int row, col;
+    split_task(t, ktiles, row, col);
+    if (row >= nr || col >= pitch) continue;  // col + 8 <= pitch (pitch is a multiple of 32)
+    const size_t e = (size_t)m * field + (size_t)row * pitch + col;
+    float xv[8], pv[8], rv[8], qv[8];
+    *reinterpret_cast<float4 *>(xv) = *reinterpret_cast<const float4 *>(x + e);
+    *reinterpret_cast<float4 *>(xv + 4) = *reinterpret_cast<const float4 *>(x + e + 4);
+    *reinterpret_cast<float4 *>(pv) = *reinterpret_cast<const float4 *>(p + e);
+    *reinterpret_cast<float4 *>(pv + 4) = *reinterpret_cast<const float4 *>(p + e + 4);
+    *reinterpret_cast<float4 *>(rv) = *reinterpret_cast<const float4 *>(r + e);
+    *reinterpret_cast<float4 *>(rv + 4) = *reinterpret_cast<const float4 *>(r + e + 4);
+    *reinterpret_cast<float4 *>(qv) = *reinterpret_cast<const float4 *>(q + e);
+    *reinterpret_cast<float4 *>(qv + 4) = *reinterpret_cast<const float4 *>(q + e + 4);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      xv[i] = fmaf(alpha, pv[i], xv[i]);
+      rv[i] = fmaf(-alpha, qv[i], rv[i]);
+      acc = fmaf(rv[i], rv[i], acc);
+    }
+    *reinterpret_cast<float4 *>(x + e) = *reinterpret_cast<const float4 *>(xv);
+    *reinterpret_cast<float4 *>(x + e + 4) = *reinterpret_cast<const float4 *>(xv + 4);
+    *reinterpret_cast<float4 *>(r + e) = *reinterpret_cast<const float4 *>(rv);
+    *reinterpret_cast<float4 *>(r + e + 4) = *reinterpret_cast<const float4 *>(rv + 4);
+    split_store8(split, m, row, col, mtiles, ktiles, rv);
+  }
+  const double sum = block_sum((double)acc, red);
+  if (threadIdx.x == 0) partial[(size_t)m * kPartialStride + blockIdx.x] = sum;
+}
+
+// The rows of a field written split into BF16 halves (tensor-core transform input).
+__global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int pitch, size_t field,
+                                                   int mtiles, int ktiles, unsigned char *__restrict__ split,
+                                                   const RhsState *st, int mask) {
+  const int m = blockIdx.y;
+  if (!rhs_selected(st, mask, m)) return;
+  const int tasks = mtiles * ktiles * 1024;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
+    int row, col;
+    split_task(t, ktiles, row, col);
+    if (row >= nr || col >= pitch) continue;
+    const size_t e = (size_t)m * field + (size_t)row * pitch + col;
+    float v[8];
+    *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(in + e);
+    *reinterpret_cast<float4 *>(v + 4) = *reinterpret_cast<const float4 *>(in + e + 4);
+    split_store8(split, m, row, col, mtiles, ktiles, v);
   }
 }
 
@@ -851,10 +942,143 @@ int dst_blocks(const ax_operator *op, int rows, int bytes) {
   return (rows + rpb - 1) / rpb;
 }
 
-// z = B^-1 r for selected RHS, with (r, z) partials into `prz`.
+// ---- tensor-core transform (FP32 path, nz <= kMaxTcN) ----------------------
+constexpr int kMaxTcN = 2048;
+
+// BF16 DST-matrix tiles per (device, nz), built on first use and kept for the
+// life of the process (shared by every operator with that nz); and one device
+// flag per device for expired waits of the GEMM kernel.
+struct TcCache {
+  std::mutex mu;
+  std::vector<std::pair<long long, uint16_t *>> tables;
+  std::vector<std::pair<int, int *>> flags;
+};
+TcCache &tc_cache() {
+  static TcCache c;
+  return c;
+}
+const uint16_t *tc_table(int device, int n) {
+  TcCache &c = tc_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  const long long key = (long long)device << 32 | (unsigned)n;
+  for (auto &e : c.tables)
+    if (e.first == key) return e.second;
+  std::vector<uint16_t> t = dst_gemm_table(n);
+  uint16_t *d = nullptr;
+  std::lock_guard<std::recursive_mutex> lock2(g_alloc_capture_mutex);
+  if (dalloc(&d, t.size()) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, t.data(), t.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  c.tables.push_back({key, d});
+  return d;
+}
+int *tc_flag(int device) {
+  TcCache &c = tc_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  for (auto &e : c.flags)
+    if (e.first == device) return e.second;
+  int *d = nullptr;
+  std::lock_guard<std::recursive_mutex> lock2(g_alloc_capture_mutex);
+  if (dalloc(&d, 1) != cudaSuccess) return nullptr;
+  c.flags.push_back({device, d});
+  return d;
+}
+
+template <typename T>
+bool use_tc(const ax_operator *op) {
+  return sizeof(T) == 4 && op->dst_tc != 0;
+}
+
+// Geometry of the split operand for `rows` rows per RHS.
+struct SplitGeom {
+  int mtiles, ktiles;
+  size_t bytes_per_rhs;
+};
+SplitGeom split_geom(const ax_operator *op, int rows) {
+  SplitGeom g;
+  g.mtiles = dst_gemm_mtiles(rows);
+  g.ktiles = dst_gemm_ktiles(op->nz);
+  g.bytes_per_rhs = (size_t)g.mtiles * g.ktiles * kSplitTileBytes;
+  return g;
+}
+
+// Tensor-core transform of `rows` rows per RHS: out = A S for the selected
+// right-hand sides (A in the split layout); with r, the (r, out) partials
+// into `partial`.
+void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, float *out, const RhsState *st,
+                  int mask, const float *r, double *partial, cudaStream_t s, int three = -1) {
+  GemmDstArgs g{};
+  g.A = A;
+  g.out = out;
+  g.SB = tc_table(op->device, op->nz);
+  g.n = op->nz;
+  g.nr = rows;
+  g.pitch = op->pitch;
+  g.field = (long long)rows * op->pitch;
+  g.m = m;
+  g.mtiles = dst_gemm_mtiles(rows);
+  g.ntiles = dst_gemm_ntiles(op->nz);
+  g.ktiles = dst_gemm_ktiles(op->nz);
+  g.three = three >= 0 ? three : (op->dst_tc == 1 ? 1 : 0);
+  g.r = r;
+  g.partial = partial;
+  g.st = st;
+  g.mask = mask;
+  g.err = tc_flag(op->device);
+  launch_dst_gemm(g, s);
+}
+
+// FP32 field -> split operand (rows per RHS `rows`).
+void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned char *split, const RhsState *st,
+              int mask, cudaStream_t s) {
+  const SplitGeom g = split_geom(op, rows);
+  note_launch();
+  split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->pitch, (size_t)rows * op->pitch, g.mtiles,
+                                                      g.ktiles, split, st, mask);
+}
+
+// Mode solves z -> split operand (the tile kernel writes it directly; otherwise
+// through the FP32 buffer tmp).
+void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, unsigned char *split,
+                   const RhsState *st, int mask, cudaStream_t s) {
+  const SplitGeom g = split_geom(op, op->nr);
+  TriArgs<float> t = tri_args<float>(op, m, z, tmp, st, mask);
+  if (tridiag_split_ok(op->nr)) {
+    t.split = split;
+    t.split_mtiles = g.mtiles;
+    t.split_ktiles = g.ktiles;
+    launch_tridiag<float>(t, s);
+  } else {
+    launch_tridiag<float>(t, s);
+    tc_split(op, m, op->nr, tmp, split, st, mask, s);
+  }
+}
+
+// Number of (r, z) partial slots per RHS that precond_apply writes.
+template <typename T>
+int precond_partials(const ax_operator *op) {
+  if (use_tc<T>(op)) return dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
+  return dst_blocks(op, op->nr, (int)sizeof(T));
+}
+
+// z = B^-1 r for selected RHS, with (r, z) partials into `prz`.  The
+// tensor-core path goes through the workspace's split operand (and tmp when
+// the mode solves cannot write it directly); the FFT path works in place in z.
 template <typename T>
 void precond_apply(const ax_operator *op, int m, const T *r, T *z, const RhsState *st, int mask, double *prz,
-                   cudaStream_t s) {
+                   cudaStream_t s, T *tmp = nullptr) {
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc<T>(op) && tmp != nullptr) {
+      unsigned char *sp = op->ws->split;
+      tc_split(op, m, op->nr, r, sp, st, mask, s);
+      tc_transform(op, m, op->nr, sp, z, st, mask, nullptr, nullptr, s);
+      tc_mode_solve(op, m, z, tmp, sp, st, mask, s);
+      tc_transform(op, m, op->nr, sp, z, st, mask, r, prz, s);
+      return;
+    }
+  }
   DstArgs<T> f = dst_args<T>(op, m, op->nr, st, mask);
   f.in = r;
   f.out = z;
@@ -894,6 +1118,34 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
     ProfScope ps(w, kProfScalar, 0.0, s);
     note_launch();
     sc_alpha<<<m, 32, 0, s>>>(st, pq, nbs);
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (use_tc<T>(op)) {
+      // update pass (r written split too), transform r -> z, mode solves
+      // z -> split, inverse transform split -> z with the (r, z) partials
+      const SplitGeom g = split_geom(op, op->nr);
+      unsigned char *sp = w->split;
+      {
+        ProfScope ps(w, kProfDstFwd, units, s);
+        note_launch();
+        pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(v.x, v.r, v.q, v.pa, v.pb, op->nr, op->pitch,
+                                                          field_elems(op), g.mtiles, g.ktiles, sp, st, kActive, prr);
+        tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s);
+      }
+      {
+        ProfScope ps(w, kProfScalar, 0.0, s);
+        note_launch();
+        sc_after_update<<<m, 32, 0, s>>>(st, prr, kUpdateBlocks, on_converge);
+      }
+      { ProfScope ps(w, kProfTridiag, units, s); tc_mode_solve(op, m, v.z, v.q, sp, st, kActive, s); }
+      { ProfScope ps(w, kProfDstInv, units, s); tc_transform(op, m, op->nr, sp, v.z, st, kActive, v.r, prz, s); }
+      {
+        ProfScope ps(w, kProfScalar, 0.0, s);
+        note_launch();
+        sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op), kActive, kActive);
+      }
+      return;
+    }
   }
   DstArgs<T> f = dst_args<T>(op, m, op->nr, st, kActive);
   f.in = v.q;
@@ -1020,9 +1272,9 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
   Workspace *w = op->ws;
   const int V = VecT<T>::n;
   const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
-  const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
+  const int nbd = precond_partials<T>(op);
   // z = B^-1 r, rho = (r, z), p = 0 so that p_1 = z
-  precond_apply<T>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s);
+  precond_apply<T>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s, v.q);
   note_launch();
   sc_rho_init<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kActive);
   AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(T) * field_elems(op) * m, s));
@@ -1042,7 +1294,7 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
     launch_stencil<T>(kStencilResidual, ra, ss);
     note_launch();
     sc_true_check<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbs);
-    precond_apply<T>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss);
+    precond_apply<T>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss, v.q);
     note_launch();
     sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
   };
@@ -1112,16 +1364,16 @@ __global__ void sc_store_gate(RhsState *st, const double *p, int nb, int which) 
 // energy norm of the start error in the metric of B^-1 A).  Rejected ones
 // restart from zero; `restart` re-runs the residual and start kernels for all
 // right-hand sides.  phiT and r0T hold phi and the guess residual in the
-// working precision; zbuf is scratch.  accepted[i] = 1 if kept.
+// working precision; zbuf and tmp are scratch.  accepted[i] = 1 if kept.
 template <typename T, typename F>
-int gate_guess(ax_operator *op, int m, RhsState *st, const T *phiT, const T *r0T, T *zbuf,
+int gate_guess(ax_operator *op, int m, RhsState *st, const T *phiT, const T *r0T, T *zbuf, T *tmp,
                std::vector<int> &accepted, cudaStream_t s, F restart) {
   Workspace *w = op->ws;
-  const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
-  precond_apply<T>(op, m, phiT, zbuf, st, -1, part_ptr(w, kPartC), s);
+  const int nbd = precond_partials<T>(op);
+  precond_apply<T>(op, m, phiT, zbuf, st, -1, part_ptr(w, kPartC), s, tmp);
   note_launch();
   sc_store_gate<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, 0);
-  precond_apply<T>(op, m, r0T, zbuf, st, -1, part_ptr(w, kPartC), s);
+  precond_apply<T>(op, m, r0T, zbuf, st, -1, part_ptr(w, kPartC), s, tmp);
   note_launch();
   sc_store_gate<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, 1);
   AX_CHECK_LAUNCH();
@@ -1156,7 +1408,7 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   const size_t field = field_elems(op);
   const int nbs64 = stencil_blocks_per_rhs(op->nr, op->nz, 2);
   const int nbf = (op->nr + 15) / 16;
-  const int nbd = dst_blocks(op, op->nr, (int)sizeof(float));
+  const int nbd = precond_partials<float>(op);
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
   // a few thousand CTAs in all for the replacement fold (see fold_correction)
   const unsigned fold_x = (unsigned)std::max<size_t>(
@@ -1186,7 +1438,7 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     residual64(kCheck, ss);
     note_launch();
     sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbs64, tol * tol, delta * delta);
-    precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss);
+    precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss, v.q);
     note_launch();
     sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
   };
@@ -1195,12 +1447,12 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     const size_t n = field * m;
     note_launch();
     to_precision<float><<<(unsigned)std::min<size_t>((n + 255) / 256, 65535), 256, 0, s>>>(w->phi64, w->pa32, n);
-    int grc = gate_guess<float>(op, m, st, w->pa32, w->r32, w->z32, accepted, s, start);
+    int grc = gate_guess<float>(op, m, st, w->pa32, w->r32, w->z32, w->q32, accepted, s, start);
     if (grc != AX_OK) return grc;
   }
   AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * field * m, s));
   AX_CHECK_LAUNCH();
-  precond_apply<float>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s);
+  precond_apply<float>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s, v.q);
   note_launch();
   sc_rho_init<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kActive);
   AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(float) * field * m, s));
@@ -1282,6 +1534,7 @@ int ax_destroy_operator(ax_operator *op) {
     free_base(w);
     dfree(w->stage_a);
     dfree(w->stage_b);
+    dfree(w->split);
     if (w->scratch) cudaFree(w->scratch);
     if (w->cap) cudaStreamDestroy(w->cap);
     delete w;
@@ -1321,6 +1574,11 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
   } else if (!strcmp(name, "replace_delta")) {
     if (!(value > 0.0 && value < 1.0)) return AX_ERR_INVALID_ARG;
     w->replace_delta = value;
+  } else if (!strcmp(name, "dst_tensor")) {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return AX_ERR_INVALID_ARG;
+    if (value != 0.0 && op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
+    op->dst_tc = (int)value;
+    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "max_outer")) {
     if (!(value >= 1)) return AX_ERR_INVALID_ARG;
     w->max_outer = (int)value;
@@ -1470,11 +1728,12 @@ __global__ void scale_rows_by_r(const double *__restrict__ f, double *__restrict
 // ---- single-step entry points --------------------------------------------
 template <typename T>
 static int apply_step(ax_operator *op, const double *in, double *out, int m, int rows_per, int which,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool tc = false, int tc_three = 0) {
   Workspace *w = op->ws;
   const size_t field = (size_t)rows_per * op->pitch;
   int rc = ensure_scratch(op, 2 * field * m * sizeof(T));
   if (rc != AX_OK) return rc;
+  if (tc && (rc = ensure_split(op, (size_t)m * split_geom(op, rows_per).bytes_per_rhs)) != AX_OK) return rc;
   T *a = reinterpret_cast<T *>(w->scratch);
   T *b = a + field * m;
   AX_TRY(cudaMemsetAsync(w->scratch, 0, 2 * field * m * sizeof(T), s));
@@ -1488,12 +1747,29 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
     sa.out = b;
     launch_stencil<T>(kStencilApply, sa, s);
   } else if (which == 1) {
-    DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
-    d.in = a;
-    d.out = b;
-    launch_dst<T>(kDstPlain, d, s);
+    if constexpr (sizeof(T) == 4) {
+      if (tc) {
+        unsigned char *sp = w->split;
+        tc_split(op, m, rows_per, a, sp, nullptr, -1, s);
+        tc_transform(op, m, rows_per, sp, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+      }
+    }
+    if (!tc) {
+      DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
+      d.in = a;
+      d.out = b;
+      launch_dst<T>(kDstPlain, d, s);
+    }
   } else if (which == 2) {
     launch_tridiag<T>(tri_args<T>(op, m, a, b, nullptr, -1), s);
+  } else if (tc) {
+    if constexpr (sizeof(T) == 4) {
+      unsigned char *sp = w->split;
+      tc_split(op, m, rows_per, a, sp, nullptr, -1, s);
+      tc_transform(op, m, rows_per, sp, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+      tc_mode_solve(op, m, b, a, sp, nullptr, -1, s);
+      tc_transform(op, m, rows_per, sp, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+    }
   } else {
     DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
     d.in = a;
@@ -1514,11 +1790,17 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
 static int apply_dispatch(ax_operator *op, const double *in, double *out, int m, int rows_per, int precision,
                           int which, void *stream) {
   if (!op || !in || !out || m < 1 || rows_per < 1) return AX_ERR_INVALID_ARG;
-  if (precision != AX_PREC_FP64 && precision != AX_PREC_FP32) return AX_ERR_INVALID_ARG;
+  const bool tc = precision == AX_PREC_FP32_TC || precision == AX_PREC_FP32_TC3;
+  if (precision != AX_PREC_FP64 && precision != AX_PREC_FP32 && !tc) return AX_ERR_INVALID_ARG;
   if ((long long)rows_per * m > 2147483647LL / 2) return AX_ERR_INVALID_ARG;
+  if (tc) {
+    if (which != 1 && which != 3) return AX_ERR_INVALID_ARG;
+    if (op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   return precision == AX_PREC_FP64 ? apply_step<double>(op, in, out, m, rows_per, which, s)
-                                   : apply_step<float>(op, in, out, m, rows_per, which, s);
+                                   : apply_step<float>(op, in, out, m, rows_per, which, s, tc,
+                                                       precision == AX_PREC_FP32_TC3 ? 1 : 0);
 }
 
 extern "C" {
@@ -1640,7 +1922,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     start();
     AX_CHECK_LAUNCH();
     if (check_guess &&
-        (rc = gate_guess<double>(op, m, w->st, w->phi64, w->r64, w->z64, accepted, s, start)) != AX_OK)
+        (rc = gate_guess<double>(op, m, w->st, w->phi64, w->r64, w->z64, w->q64, accepted, s, start)) != AX_OK)
       return rc;
     if (!cheb) {
       PcgVecs<double> v{w->x64, w->r64, w->pa64, w->pb64, w->q64, w->z64};
@@ -1667,6 +1949,11 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     // ---- mixed precision
     outer_kind = 1;
     if ((rc = ensure_vec32(op, m, cheb)) != AX_OK) return rc;
+    if (op->dst_tc) {
+      // buffers and tables before any graph capture
+      if ((rc = ensure_split(op, (size_t)m * split_geom(op, nr).bytes_per_rhs)) != AX_OK) return rc;
+      if (!tc_table(op->device, nz) || !tc_flag(op->device)) return AX_ERR_OOM;
+    }
     if (!cheb && !w->mixed_restart) {
       // FP32 PCG with FP64 residual replacement
       if ((rc = pcg_mixed_loop(op, m, tol, w->replace_delta, max_iter, check_guess, accepted, s)) != AX_OK)
@@ -1737,6 +2024,19 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   if (host) {
     AX_TRY(cudaMemcpyAsync(u, ud, dense * sizeof(double), cudaMemcpyDeviceToHost, s));
     AX_TRY(cudaStreamSynchronize(s));
+  }
+  if (op->dst_tc) {
+    // a bounded wait of the tensor-core transform expired: report and re-arm
+    int *flag = tc_flag(op->device), hf = 0;
+    if (flag) {
+      AX_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      AX_TRY(cudaStreamSynchronize(s));
+      if (hf) {
+        AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+        snprintf(g_last_error, sizeof(g_last_error), "tensor-core transform: a bounded wait expired");
+        return AX_ERR_TIMEOUT;
+      }
+    }
   }
   return rc;
 }

@@ -345,7 +345,23 @@ __global__ void __launch_bounds__(32 * kTileCW * MR, 4 / MR) tridiag_tile_kernel
   }
   __syncthreads();
   // ---- write back (coalesced) ----
-  if (cw < ncol) {
+  if (a.split != nullptr) {
+    // the 8 columns of a row (8 consecutive lanes) become one 16-byte chunk
+    // of BF16 high parts and one of low parts
+    const int lane8 = (threadIdx.x & 31) & ~7;
+    for (int base = 0; base < nr; base += blockDim.x / kTileCW) {
+      const int row = base + threadIdx.x / kTileCW;
+#pragma unroll
+      for (int j = 0; j < MR; ++j) {
+        if (!sel[j]) continue;
+        const float v = (row < nr) ? ds[j * kTileWords + tidx(row, cw, C)] : 0.f;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = __shfl_sync(0xffffffffu, v, lane8 + e);
+        if (cw == 0 && row < nr) split_store8(a.split, m0 + j, row, col0, a.split_mtiles, a.split_ktiles, x);
+      }
+    }
+  } else if (cw < ncol) {
     for (int row = threadIdx.x / kTileCW; row < nr; row += blockDim.x / kTileCW) {
       const int si = tidx(row, cw, C);
 #pragma unroll
@@ -405,6 +421,8 @@ bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
   else return false;
   return true;
 }
+
+bool tridiag_split_ok(int nr) { return nr <= 32 * 32; }
 
 template <typename T>
 void launch_tridiag(const TriArgs<T> &a, cudaStream_t s) {

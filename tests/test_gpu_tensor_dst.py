@@ -1,0 +1,133 @@
+"""The tensor-core sine transform (tcgen05 GEMM by the BF16-split DST-I
+matrix) against the oracle, through the C ABI.
+
+What it computes is fixed by its definition, with x32 = fp32(in),
+hi = bf16(x32), lo = bf16(x32 - hi), S the oracle's orthonormal DST-I matrix,
+S_hi = bf16(S), S_lo = bf16(S - S_hi):
+  AX_PREC_FP32_TC   out = (hi + lo) S_hi
+  AX_PREC_FP32_TC3  out = (hi + lo) S_hi + hi S_lo
+The reference evaluates these products in FP64 (the kernel accumulates up to
+3 nz products in FP32: tolerance 1e-5 relative per row).  Against the exact
+transform S x, TC differs by the BF16 rounding of S (about 3e-3 in the
+spectral norm: tolerance 1e-2) and TC3 by the dropped lo S_lo and the
+rounding of S_lo (tolerance 1e-4).  The preconditioner built from the TC
+transform, S_hi T^-1 S_hi, must stay symmetric (tolerance 1e-5 on
+(u, B^ v) - (B^ u, v), the input splitting being the only asymmetry) and close
+to B^-1 (2e-2), and the mixed PCG that uses either form must meet 1e-8 in the
+oracle's FP64 true residual.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from oracle import guessnet as G  # noqa: E402
+import paper_1002_3094_gb300 as P  # noqa: E402
+from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs  # noqa: E402
+from workloads import layered_inclusion_medium  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    P.load_library()
+    return torch.device("cuda:0")
+
+
+def _op(nr, nz, dev, seed=3):
+    med = layered_inclusion_medium(n_rhs=2, nominal_n=max(nr, nz), instance=seed)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    t = [torch.from_numpy(x).to(dev) for x in (kr, kz, q)]
+    return P.ax_setup_operator(*t, nr, nz), med, t
+
+
+def _split_reference(x, n, three):
+    x32 = x.astype(np.float32).astype(np.float64)
+    hi = G.round_bf16(x32)
+    lo = G.round_bf16(x32 - hi)
+    S = O.dst1_matrix(n)
+    Sh = G.round_bf16(S)
+    out = (hi + lo) @ Sh
+    if three:
+        out = out + hi @ G.round_bf16(S - Sh)
+    return out
+
+
+@pytest.mark.parametrize("rows,nz", [(300, 1024), (129, 200), (7, 31), (128, 256), (1, 1), (260, 2048)])
+@pytest.mark.parametrize("prec", [P.AX_PREC_FP32_TC, P.AX_PREC_FP32_TC3])
+def test_tensor_transform_matches_split_products(cuda, rows, nz, prec):
+    op, _, _ = _op(max(rows, 2), nz, cuda)
+    x = np.random.default_rng(rows + nz).normal(size=(rows, nz))
+    y = torch.zeros((rows, nz), dtype=torch.float64, device=cuda)
+    P.ax_apply_dst(op, torch.from_numpy(x).to(cuda), y, rows, prec)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    three = prec == P.AX_PREC_FP32_TC3
+    ref = _split_reference(x, nz, three)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 1e-5, err.max()
+    exact = x @ O.dst1_matrix(nz)
+    assert np.linalg.norm(got - exact) <= (1e-4 if three else 1e-2) * np.linalg.norm(exact)
+    P.ax_destroy_operator(op)
+
+
+def test_tensor_preconditioner_symmetric_and_close(cuda):
+    nr, nz = 160, 300
+    op, _, _ = _op(nr, nz, cuda)
+    rng = np.random.default_rng(5)
+    u, v = rng.normal(size=(1, nr, nz)), rng.normal(size=(1, nr, nz))
+
+    def apply(x, prec):
+        out = torch.zeros((1, nr, nz), dtype=torch.float64, device=cuda)
+        P.ax_apply_preconditioner(op, torch.from_numpy(x).to(cuda), out, 1, prec)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    bu, bv = apply(u, P.AX_PREC_FP32_TC), apply(v, P.AX_PREC_FP32_TC)
+    a, b = np.sum(u * bv), np.sum(bu * v)
+    assert abs(a - b) <= 1e-5 * np.sqrt(np.sum(u * bu) * np.sum(v * bv))
+    ex = apply(v, P.AX_PREC_FP64)
+    assert np.linalg.norm(bv - ex) <= 2e-2 * np.linalg.norm(ex)
+    P.ax_destroy_operator(op)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_mixed_pcg_with_tensor_transform_meets_tolerance(cuda, form):
+    nr, nz = 160, 144
+    med = layered_inclusion_medium(n_rhs=4, nominal_n=160)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(cuda) for x in (kr, kz, q)], nr, nz)
+    g = O.Grid(nr, nz)
+    ora = O.Operator(kr, kz, q, g)
+    f = sample_rhs(med, nr, nz)
+    fd = torch.from_numpy(f).to(cuda)
+    u64 = torch.zeros_like(fd)
+    _, i64 = P.ax_solve(op, fd, u64, 4, 1e-8, 5000, P.AX_PCG_FP64)
+    P.ax_set_option(op, "dst_tensor", form)
+    u = torch.zeros_like(fd)
+    st, imx = P.ax_solve(op, fd, u, 4, 1e-8, 5000, P.AX_PCG_MIXED)
+    torch.cuda.synchronize()
+    assert st == P.AX_OK
+    un = u.cpu().numpy()
+    for j in range(4):
+        phi = ora.phi(f[j])
+        assert np.linalg.norm(phi - ora.apply_A(un[j])) <= 1e-8 * np.linalg.norm(phi)
+        assert imx[j]["iters"] <= 1.2 * i64[j]["iters"] + 4, (imx[j], i64[j])
+    # back to the FFT transform: same answer to the tolerance
+    P.ax_set_option(op, "dst_tensor", 0)
+    u2 = torch.zeros_like(fd)
+    st, _ = P.ax_solve(op, fd, u2, 4, 1e-8, 5000, P.AX_PCG_MIXED)
+    assert st == P.AX_OK
+    P.ax_destroy_operator(op)
+
+
+def test_tensor_option_rejects_long_columns(cuda):
+    op, _, _ = _op(4, 2100, cuda)
+    with pytest.raises(P.AxError):
+        P.ax_set_option(op, "dst_tensor", 1)
+    P.ax_destroy_operator(op)
