@@ -62,20 +62,22 @@ __device__ __forceinline__ bool rhs_selected(const RhsState *st, int mask, int m
 // ---------------------------------------------------------------------------
 // BF16 operand of the tensor-core transform ("split" layout).  A field x is
 // stored as x = hi + lo, hi = bf16(x), lo = bf16(x - hi), in tiles of 128 rows
-// x 64 columns per right-hand side: tile (m, row / 128, col / 64) is 32 KB, the
-// 16 KB of high parts and then the 16 KB of low parts, each as 8 x 8 core
-// matrices of 16-byte rows, element (row, col) at byte
-//   (row % 128 / 8) 1024 + (col % 64 / 8) 128 + (row % 8) 16 + (col % 8) 2.
-// A tile is copied to shared memory as it is.  Padding rows and columns hold
-// zeros (the buffer is zeroed when allocated and never written there).
+// x 64 positions per right-hand side: tile (m, row / 128, pos / 64) is 32 KB,
+// the 16 KB of high parts and then the 16 KB of low parts, each as 8 x 8 core
+// matrices of 16-byte rows, element (row, pos) at byte
+//   (row % 128 / 8) 1024 + (pos % 64 / 8) 128 + (row % 8) 16 + (pos % 8) 2.
+// Columns are stored even ones first (the operand order of the transform's
+// even / odd split): column c at position c / 2 if c is even, else at
+// kbe 64 + c / 2, with kbe = ceil(ceil(n / 2) / 64) tiles of even columns.
+// A tile is copied to shared memory as it is.  Padding rows and positions
+// hold zeros (the buffer is zeroed when allocated and never written there).
 // ---------------------------------------------------------------------------
 constexpr int kSplitTileBytes = 32768;
 
-__device__ __forceinline__ size_t split_tile_off(int m, int row, int col, int mtiles, int ktiles) {
-  return (((size_t)m * mtiles + (row >> 7)) * ktiles + (col >> 6)) * (size_t)kSplitTileBytes;
-}
-__device__ __forceinline__ int split_in_tile(int row, int col) {
-  return ((row & 127) >> 3) * 1024 + ((col & 63) >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2;
+__device__ __forceinline__ int split_pos(int c, int kbe) { return (c & 1) ? kbe * 64 + (c >> 1) : (c >> 1); }
+__device__ __forceinline__ size_t split_byte(int m, int row, int pos, int mtiles, int ktiles) {
+  return (((size_t)m * mtiles + (row >> 7)) * ktiles + (pos >> 6)) * (size_t)kSplitTileBytes +
+         ((row & 127) >> 3) * 1024 + ((pos & 63) >> 3) * 128 + (row & 7) * 16 + (pos & 7) * 2;
 }
 __device__ __forceinline__ unsigned bf16_pack2(float a, float b) {
   // round-to-nearest-even BF16 of a (low half, lower address) and b
@@ -89,20 +91,22 @@ __device__ __forceinline__ float bf16_round(float a) {
   u += 0x7FFFu + ((u >> 16) & 1u);
   return __uint_as_float(u & 0xFFFF0000u);
 }
-// Writes the 8 consecutive columns col .. col + 7 (col % 8 == 0) of one row.
+// Writes the 8 consecutive columns col .. col + 7 (col % 8 == 0) of one row:
+// the 4 even ones and the 4 odd ones each as 8 bytes of high and of low parts.
 __device__ __forceinline__ void split_store8(unsigned char *split, int m, int row, int col, int mtiles, int ktiles,
-                                             const float (&x)[8]) {
+                                             int kbe, const float (&x)[8]) {
   float hi[8], lo[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     hi[e] = bf16_round(x[e]);
     lo[e] = x[e] - hi[e];
   }
-  unsigned char *t = split + split_tile_off(m, row, col, mtiles, ktiles) + split_in_tile(row, col);
-  *reinterpret_cast<uint4 *>(t) =
-      make_uint4(bf16_pack2(hi[0], hi[1]), bf16_pack2(hi[2], hi[3]), bf16_pack2(hi[4], hi[5]), bf16_pack2(hi[6], hi[7]));
-  *reinterpret_cast<uint4 *>(t + kSplitTileBytes / 2) =
-      make_uint4(bf16_pack2(lo[0], lo[1]), bf16_pack2(lo[2], lo[3]), bf16_pack2(lo[4], lo[5]), bf16_pack2(lo[6], lo[7]));
+  unsigned char *te = split + split_byte(m, row, split_pos(col, kbe), mtiles, ktiles);
+  unsigned char *to = split + split_byte(m, row, split_pos(col + 1, kbe), mtiles, ktiles);
+  *reinterpret_cast<uint2 *>(te) = make_uint2(bf16_pack2(hi[0], hi[2]), bf16_pack2(hi[4], hi[6]));
+  *reinterpret_cast<uint2 *>(te + kSplitTileBytes / 2) = make_uint2(bf16_pack2(lo[0], lo[2]), bf16_pack2(lo[4], lo[6]));
+  *reinterpret_cast<uint2 *>(to) = make_uint2(bf16_pack2(hi[1], hi[3]), bf16_pack2(hi[5], hi[7]));
+  *reinterpret_cast<uint2 *>(to + kSplitTileBytes / 2) = make_uint2(bf16_pack2(lo[1], lo[3]), bf16_pack2(lo[5], lo[7]));
 }
 
 }  // namespace ax

@@ -2,30 +2,36 @@
 // FP32 working precision of the mixed method (the z-transform of the
 // preconditioner of Section 4.2, Eq. fft_phi, written as a matrix product):
 //
-//     out[row][l] = sum_k in[row][k] S^[k][l],   S^ = S_hi (+ S_lo),
-//     S[k][l] = sqrt(2/L) sin(pi (k+1) (l+1) / L),   L = nz + 1,
-//     S_hi = bf16(S),  S_lo = bf16(S - S_hi).
+//     out[l] = sum_k in[k] S[k][l],   S[k][l] = sqrt(2/L) sin(pi (k+1) (l+1) / L),
+//     L = nz + 1 (0-based k, l < nz).
 //
-// The input arrives split, in = hi + lo with hi = bf16(in), lo = bf16(in - hi)
-// (|in - hi - lo| <= 2^-17 |in|), in the tile layout of ax_common.cuh, written
-// by the kernel that produced it.  The products hi S_hi + lo S_hi (and, with
-// `three`, + hi S_lo) accumulate in FP32 in the tensor memory.  Without the
-// third product the transform multiplies by S_hi: a fixed symmetric matrix
-// within ~3e-3 (spectral norm) of S, so the preconditioner S_hi T^-1 S_hi is
-// still symmetric positive definite and close to B^-1; with it the transform
-// is S to about 2^-16.  Either way the FP64 residual replacement keeps the
+// Even / odd split.  S[k][n-1-l] = (-1)^k S[k][l], so with
+//     P[l] = sum_{k even} in[k] S[k][l],   Q[l] = sum_{k odd} in[k] S[k][l]
+// for l < ceil(n/2):  out[l] = P[l] + Q[l],  out[n-1-l] = P[l] - Q[l]
+// (once for the middle column of odd n).  Two GEMMs of half the width and half
+// the depth replace one full one: half the multiply-adds.  The input arrives
+// with its even columns stored first (the split layout of ax_common.cuh).
+//
+// Precision.  The input arrives split, in = hi + lo, hi = bf16(in),
+// lo = bf16(in - hi) (|in - hi - lo| <= 2^-17 |in|), and S as S_hi = bf16(S),
+// S_lo = bf16(S - S_hi).  The products hi S_hi + lo S_hi (and, with `three`,
+// + hi S_lo) accumulate in FP32 in the tensor memory.  Without the third
+// product the transform multiplies by S_hi: a fixed symmetric matrix within
+// ~3e-3 (spectral norm) of S, so the preconditioner S_hi T^-1 S_hi is still
+// symmetric positive definite and close to B^-1; with it the transform is S
+// to about 2^-16.  Either way the FP64 residual replacement keeps the
 // solution accuracy.
 //
-// Tiles: 128 rows x 256 output columns per CTA, K in blocks of 64 through a
-// ring of shared-memory stages (3 of 64 KB, or 2 of 96 KB with S_lo), each
-// filled by bulk copies (cp.async.bulk) of one 32 KB input tile and one or
-// two 32 KB tiles of S (stored in the same layout, symmetric: row l, column k).
-// Warp roles: warp 0 lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16,
-// BF16 x BF16 -> FP32 in 256 TMEM columns); warp 1 lane 0 issues the copies;
-// warps 4..7 run the epilogue (tcgen05.ld -> global, optional (r, out)
-// partial).  Every mbarrier wait is bounded; on expiry the CTA records the
-// failure in *err, stops issuing work, waits (bounded) for its MMAs and frees
-// its TMEM.
+// Tiles: 128 rows x 256 columns l of both P and Q per CTA (512 TMEM columns),
+// K in blocks of 64 (the even blocks feed P, the odd ones Q) through a ring of
+// shared-memory stages (3 of 64 KB, or 2 of 96 KB with S_lo), each filled by
+// bulk copies (cp.async.bulk) of one 32 KB input tile and one or two 32 KB
+// tiles of S (stored in the same layout: row l, column k).  Warp roles: warp
+// 0 lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32);
+// warp 1 lane 0 issues the copies; warps 4..7 run the epilogue (tcgen05.ld,
+// the even / odd combination, global stores, optional (r, out) partial).
+// Every mbarrier wait is bounded; on expiry the CTA records the failure in
+// *err, stops issuing work, waits (bounded) for its MMAs and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstring>
@@ -38,6 +44,7 @@ namespace ax {
 namespace {
 
 constexpr int kBM = 128, kBN = 256, kBK = 64;
+constexpr unsigned kTmemCols = 2 * kBN;  // P and Q accumulators
 constexpr int kATileBytes = kSplitTileBytes;                // hi and lo halves, 32 KB
 constexpr int kBTileBytes = kBN * kBK * 2;                  // 32 KB
 constexpr int kGemmThreads = 256;
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"((unsigned)kBN)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -186,13 +193,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
         }
         tc_fence_after();
         unsigned char *st = gsm + s * kStageBytes;
+        const bool odd = kb >= a.kbe;                       // Q block
+        const unsigned acc_t = tmem + (odd ? (unsigned)kBN : 0u);
+        const int first = odd ? a.kbe : 0;                  // first block of this accumulator
 #pragma unroll
         for (int j = 0; j < kBK / 16; ++j) {
           const uint64_t ahi = smem_desc(st + j * 256), alo = smem_desc(st + kATileBytes / 2 + j * 256);
           const uint64_t bhi = smem_desc(st + kATileBytes + j * 256);
-          umma(tmem, ahi, bhi, (kb | j) != 0);
-          umma(tmem, alo, bhi, 1u);
-          if (THREE) umma(tmem, ahi, smem_desc(st + kATileBytes + kBTileBytes + j * 256), 1u);
+          umma(acc_t, ahi, bhi, (kb != first || j != 0) ? 1u : 0u);
+          umma(acc_t, alo, bhi, 1u);
+          if (THREE) umma(acc_t, ahi, smem_desc(st + kATileBytes + kBTileBytes + j * 256), 1u);
         }
         umma_commit(&empty_bar[s]);
       }
@@ -239,25 +249,55 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
     if (__all_sync(0xffffffffu, ok && !abort_flag)) {
       float *outr = a.out + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
       const float *rr = (a.r != nullptr) ? a.r + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch : nullptr;
+      const int n = a.n, ne = (n + 1) >> 1;
 #pragma unroll 1
       for (int c = 0; c < kBN / 32; ++c) {
         const int l0 = nt * kBN + c * 32;
-        if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= a.pitch) break;  // nothing left for this warp
-        float v[32];
-        tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(c * 32), v);
+        if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= ne) break;  // nothing left for this warp
+        float P[32], Q[32];
+        tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(c * 32), P);
+        if (a.ktiles > a.kbe) {
+          tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(kBN + c * 32), Q);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
+        }
         if (grow < a.nr) {
 #pragma unroll
           for (int i = 0; i < 32; i += 4) {
-            // columns up to the pitch: S is zero beyond nz, so the padding
-            // columns receive the zeros they must hold
-            if (l0 + i < a.pitch) {
-              *reinterpret_cast<float4 *>(outr + l0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            const int l = l0 + i;
+            float s0[4], d0[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              s0[e] = P[i + e] + Q[i + e];  // out[l + e]
+              d0[e] = P[i + e] - Q[i + e];  // out[n - 1 - l - e]
+            }
+            if (l + 3 < ne && (n & 3) == 0) {
+              // n % 4 == 0: both runs are whole aligned float4 groups, and the
+              // mirrored one (columns n - 4 - l .. n - 1 - l) lies above ne
+              const int lm = n - 4 - l;
+              *reinterpret_cast<float4 *>(outr + l) = make_float4(s0[0], s0[1], s0[2], s0[3]);
+              *reinterpret_cast<float4 *>(outr + lm) = make_float4(d0[3], d0[2], d0[1], d0[0]);
               if (rr) {
-                const float4 r4 = *reinterpret_cast<const float4 *>(rr + l0 + i);
-                acc = fmaf(r4.x, v[i], acc);
-                acc = fmaf(r4.y, v[i + 1], acc);
-                acc = fmaf(r4.z, v[i + 2], acc);
-                acc = fmaf(r4.w, v[i + 3], acc);
+                const float4 ra = *reinterpret_cast<const float4 *>(rr + l);
+                const float4 rb = *reinterpret_cast<const float4 *>(rr + lm);
+                acc = fmaf(ra.x, s0[0], acc); acc = fmaf(ra.y, s0[1], acc);
+                acc = fmaf(ra.z, s0[2], acc); acc = fmaf(ra.w, s0[3], acc);
+                acc = fmaf(rb.x, d0[3], acc); acc = fmaf(rb.y, d0[2], acc);
+                acc = fmaf(rb.z, d0[1], acc); acc = fmaf(rb.w, d0[0], acc);
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int le = l + e, lm = n - 1 - le;
+                if (le < ne) {
+                  outr[le] = s0[e];
+                  if (rr) acc = fmaf(rr[le], s0[e], acc);
+                  if (lm != le) {  // the middle column of odd n is written once
+                    outr[lm] = d0[e];
+                    if (rr) acc = fmaf(rr[lm], d0[e], acc);
+                  }
+                }
               }
             }
           }
@@ -279,7 +319,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
     // more (bounded) before the columns are released
     if (abort_flag) mbar_wait(&done_bar, 0u);
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)kBN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
@@ -290,17 +330,19 @@ size_t dst_gemm_smem_bytes(int three) {
                : (size_t)GemmStages<0>::stages * GemmStages<0>::stage_bytes + 1024;
 }
 
-int dst_gemm_ktiles(int n) { return (n + kBK - 1) / kBK; }
-int dst_gemm_ntiles(int n) { return (n + kBN - 1) / kBN; }
+int dst_gemm_kbe(int n) { return ((n + 1) / 2 + kBK - 1) / kBK; }
+int dst_gemm_ktiles(int n) { return dst_gemm_kbe(n) + (n / 2 + kBK - 1) / kBK; }
+int dst_gemm_ntiles(int n) { return ((n + 1) / 2 + kBN - 1) / kBN; }
 int dst_gemm_mtiles(int rows) { return (rows + kBM - 1) / kBM; }
 
-// S tiles: for every N tile (256 output columns) and K block (64 inputs) a
-// 32 KB tile of S_hi and one of S_lo, each in the shared-memory layout above
-// holding S[k][l] at (row l, column k) (S is symmetric).  Values in FP64,
-// rounded to BF16 (nearest, ties to even, by way of FP32).
+// S tiles: for every N tile (256 output columns l < ceil(n/2)) and K block (64
+// input columns: the even columns 0, 2, ... in the first kbe blocks, the odd
+// ones after) a 32 KB tile of S_hi and one of S_lo, each in the shared-memory
+// layout above holding S[k][l] at (row l, column k).  Values in FP64, rounded
+// to BF16 (nearest, ties to even, by way of FP32).
 std::vector<uint16_t> dst_gemm_table(int n) {
-  const int KB = dst_gemm_ktiles(n), NT = dst_gemm_ntiles(n);
-  const int L = n + 1;
+  const int KB = dst_gemm_ktiles(n), KBE = dst_gemm_kbe(n), NT = dst_gemm_ntiles(n);
+  const int L = n + 1, ne = (n + 1) / 2;
   const double sc = std::sqrt(2.0 / L);
   auto to_bf16 = [](double x) -> uint16_t {
     const float v = (float)x;
@@ -323,9 +365,9 @@ std::vector<uint16_t> dst_gemm_table(int n) {
       uint16_t *lo = hi + tile;
       for (int nl = 0; nl < kBN; ++nl) {
         const int l = nt * kBN + nl;
-        if (l >= n) continue;
+        if (l >= ne) continue;
         for (int kl = 0; kl < kBK; ++kl) {
-          const int k = kb * kBK + kl;
+          const int k = (kb < KBE) ? 2 * (kb * kBK + kl) : 2 * ((kb - KBE) * kBK + kl) + 1;
           if (k >= n) continue;
           const long long e = ((long long)(k + 1) * (l + 1)) % (2LL * L);  // sin(pi e / L), e reduced
           const double v = sc * std::sin(M_PI * (double)e / L);

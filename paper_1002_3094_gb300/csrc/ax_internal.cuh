@@ -218,12 +218,12 @@ size_t dst_smem_bytes(int L, int elem_bytes);
 // Tensor-core sine transform (input split into BF16 halves in the tile layout
 // of ax_common.cuh, BF16 DST matrix, FP32 accumulation).
 struct GemmDstArgs {
-  const unsigned char *A;  // split input, tiles (m, mtiles, ktiles)
-  float *out;              // rows of the output field (columns up to pitch written)
+  const unsigned char *A;  // split input, tiles (m, mtiles, ktiles), even columns first
+  float *out;              // rows of the output field (columns < n written)
   const uint16_t *SB;      // S_hi / S_lo tiles (dst_gemm_table)
   int n, nr, pitch;        // n = nz; rows per RHS
   long long field;         // elements per RHS of out
-  int m, mtiles, ntiles, ktiles;
+  int m, mtiles, ntiles, ktiles, kbe;  // kbe: K tiles of even input columns
   int three;               // 1: add hi S_lo (the transform is S to ~2^-16)
   const float *r;          // non-null: per-CTA partials of (r, out) into partial
   double *partial;         // [m][kPartialStride], slot mt * ntiles + nt
@@ -234,6 +234,7 @@ struct GemmDstArgs {
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);
 int dst_gemm_ktiles(int n);
+int dst_gemm_kbe(int n);
 int dst_gemm_ntiles(int n);
 int dst_gemm_mtiles(int rows);
 std::vector<uint16_t> dst_gemm_table(int n);
@@ -252,7 +253,7 @@ struct TriArgs {
   // FP32 tile kernel only: if set, the solution is written split into BF16
   // halves (layout of ax_common.cuh, tiles mtiles x ktiles) instead of to out
   unsigned char *split;
-  int split_mtiles, split_ktiles;
+  int split_mtiles, split_ktiles, split_kbe;
 };
 
 template <typename T>

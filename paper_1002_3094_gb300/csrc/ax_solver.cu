@@ -378,13 +378,13 @@ __global__ void fold_correction(double *__restrict__ x, float *__restrict__ d, s
   }
 }
 
-// Task t of a right-hand side: 8 consecutive columns of one row, ordered like
-// the split layout (8 rows of one column chunk, then 8 chunks, then row groups
-// of a 128 x 64 tile, then tiles), so that a warp reads 8 rows x 128 bytes
-// and writes 512 contiguous bytes of each split half.
-__device__ __forceinline__ void split_task(int t, int ktiles, int &row, int &col) {
+// Task t of a right-hand side: 8 consecutive columns of one row, in blocks of
+// 128 rows x 64 natural columns (8 rows of one column chunk, then 8 chunks,
+// then row groups, then blocks), so that a warp reads 8 rows x 128 bytes and
+// writes compact runs of each split half.
+__device__ __forceinline__ void split_task(int t, int ctiles, int &row, int &col) {
   const int tile = t >> 10, w = t & 1023;
-  const int mt = tile / ktiles, kb = tile - mt * ktiles;
+  const int mt = tile / ctiles, kb = tile - mt * ctiles;
   row = mt * 128 + (w >> 6) * 8 + (w & 7);
   col = kb * 64 + ((w >> 3) & 7) * 8;
 }
@@ -398,18 +398,19 @@ constexpr int kUpdateBlocks = 64;  // CTAs per right-hand side
 __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *__restrict__ r,
                                                   const float *__restrict__ q, const float *__restrict__ pa,
                                                   const float *__restrict__ pb, int nr, int pitch, size_t field,
-                                                  int mtiles, int ktiles, unsigned char *__restrict__ split,
+                                                  int mtiles, int ctiles, int ktiles, int kbe,
+                                                  unsigned char *__restrict__ split,
                                                   const RhsState *st, int mask, double *__restrict__ partial) {
   __shared__ double red[8];
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
   const float alpha = (float)st[m].alpha;
   const float *p = (st[m].iters & 1) ? pa : pb;
-  const int tasks = mtiles * ktiles * 1024;
+  const int tasks = mtiles * ctiles * 1024;
   float acc = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
     int row, col;
-    split_task(t, ktiles, row, col);
+    split_task(t, ctiles, row, col);
     if (row >= nr || col >= pitch) continue;  // col + 8 <= pitch (pitch is a multiple of 32)
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
     float xv[8], pv[8], rv[8], qv[8];
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
     *reinterpret_cast<float4 *>(x + e + 4) = *reinterpret_cast<const float4 *>(xv + 4);
     *reinterpret_cast<float4 *>(r + e) = *reinterpret_cast<const float4 *>(rv);
     *reinterpret_cast<float4 *>(r + e + 4) = *reinterpret_cast<const float4 *>(rv + 4);
-    split_store8(split, m, row, col, mtiles, ktiles, rv);
+    split_store8(split, m, row, col, mtiles, ktiles, kbe, rv);
   }
   const double sum = block_sum((double)acc, red);
   if (threadIdx.x == 0) partial[(size_t)m * kPartialStride + blockIdx.x] = sum;
@@ -439,20 +440,21 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
 
 // The rows of a field written split into BF16 halves (tensor-core transform input).
 __global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int pitch, size_t field,
-                                                   int mtiles, int ktiles, unsigned char *__restrict__ split,
+                                                   int mtiles, int ctiles, int ktiles, int kbe,
+                                                   unsigned char *__restrict__ split,
                                                    const RhsState *st, int mask) {
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
-  const int tasks = mtiles * ktiles * 1024;
+  const int tasks = mtiles * ctiles * 1024;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
     int row, col;
-    split_task(t, ktiles, row, col);
+    split_task(t, ctiles, row, col);
     if (row >= nr || col >= pitch) continue;
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
     float v[8];
     *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(in + e);
     *reinterpret_cast<float4 *>(v + 4) = *reinterpret_cast<const float4 *>(in + e + 4);
-    split_store8(split, m, row, col, mtiles, ktiles, v);
+    split_store8(split, m, row, col, mtiles, ktiles, kbe, v);
   }
 }
 
@@ -993,13 +995,16 @@ bool use_tc(const ax_operator *op) {
 
 // Geometry of the split operand for `rows` rows per RHS.
 struct SplitGeom {
-  int mtiles, ktiles;
+  int mtiles, ktiles, kbe;
+  int ctiles;  // tiles of 64 natural columns (the writers' task range)
   size_t bytes_per_rhs;
 };
 SplitGeom split_geom(const ax_operator *op, int rows) {
   SplitGeom g;
   g.mtiles = dst_gemm_mtiles(rows);
   g.ktiles = dst_gemm_ktiles(op->nz);
+  g.kbe = dst_gemm_kbe(op->nz);
+  g.ctiles = (op->nz + 63) / 64;
   g.bytes_per_rhs = (size_t)g.mtiles * g.ktiles * kSplitTileBytes;
   return g;
 }
@@ -1021,6 +1026,7 @@ void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A
   g.mtiles = dst_gemm_mtiles(rows);
   g.ntiles = dst_gemm_ntiles(op->nz);
   g.ktiles = dst_gemm_ktiles(op->nz);
+  g.kbe = dst_gemm_kbe(op->nz);
   g.three = three >= 0 ? three : (op->dst_tc == 1 ? 1 : 0);
   g.r = r;
   g.partial = partial;
@@ -1036,7 +1042,7 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
   const SplitGeom g = split_geom(op, rows);
   note_launch();
   split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->pitch, (size_t)rows * op->pitch, g.mtiles,
-                                                      g.ktiles, split, st, mask);
+                                                      g.ctiles, g.ktiles, g.kbe, split, st, mask);
 }
 
 // Mode solves z -> split operand (the tile kernel writes it directly; otherwise
@@ -1049,6 +1055,7 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
     t.split = split;
     t.split_mtiles = g.mtiles;
     t.split_ktiles = g.ktiles;
+    t.split_kbe = g.kbe;
     launch_tridiag<float>(t, s);
   } else {
     launch_tridiag<float>(t, s);
@@ -1129,7 +1136,8 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
         ProfScope ps(w, kProfDstFwd, units, s);
         note_launch();
         pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(v.x, v.r, v.q, v.pa, v.pb, op->nr, op->pitch,
-                                                          field_elems(op), g.mtiles, g.ktiles, sp, st, kActive, prr);
+                                                          field_elems(op), g.mtiles, g.ctiles, g.ktiles, g.kbe, sp,
+                                                          st, kActive, prr);
         tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s);
       }
       {

@@ -346,19 +346,24 @@ __global__ void __launch_bounds__(32 * kTileCW * MR, 4 / MR) tridiag_tile_kernel
   __syncthreads();
   // ---- write back (coalesced) ----
   if (a.split != nullptr) {
-    // the 8 columns of a row (8 consecutive lanes) become one 16-byte chunk
-    // of BF16 high parts and one of low parts
-    const int lane8 = (threadIdx.x & 31) & ~7;
+    // the 8 columns of a row (8 consecutive lanes) become, for the even and
+    // for the odd columns, 8 bytes of BF16 high parts and 8 of low parts:
+    // every lane splits its value, lanes 0, 1, 4, 5 pair theirs with lane + 2
+    // (the next column of the same parity) and store 4 bytes of each
     for (int base = 0; base < nr; base += blockDim.x / kTileCW) {
       const int row = base + threadIdx.x / kTileCW;
 #pragma unroll
       for (int j = 0; j < MR; ++j) {
         if (!sel[j]) continue;
         const float v = (row < nr) ? ds[j * kTileWords + tidx(row, cw, C)] : 0.f;
-        float x[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = __shfl_sync(0xffffffffu, v, lane8 + e);
-        if (cw == 0 && row < nr) split_store8(a.split, m0 + j, row, col0, a.split_mtiles, a.split_ktiles, x);
+        const float hi = bf16_round(v), lo = v - hi;
+        const float hi2 = __shfl_down_sync(0xffffffffu, hi, 2), lo2 = __shfl_down_sync(0xffffffffu, lo, 2);
+        if ((cw & 2) == 0 && row < nr) {
+          unsigned char *t = a.split + split_byte(m0 + j, row, split_pos(col0 + cw, a.split_kbe), a.split_mtiles,
+                                                  a.split_ktiles);
+          *reinterpret_cast<unsigned *>(t) = bf16_pack2(hi, hi2);
+          *reinterpret_cast<unsigned *>(t + kSplitTileBytes / 2) = bf16_pack2(lo, lo2);
+        }
       }
     }
   } else if (cw < ncol) {
