@@ -90,9 +90,9 @@ def parse_args():
     ap.add_argument("--save", default="", help="guess_256: write the trained weights here")
     ap.add_argument("--h1", type=float, default=10.0, help="guess_256: weight of the loss's lattice-edge term")
     ap.add_argument("--no-pre", action="store_true", help="guess_256: raw f / s feature instead of B^-1 (r f)")
-    ap.add_argument("--dst-tensor", type=int, default=0, choices=[0, 1, 2],
-                    help="FP32 path transform along z: 0 FFT, 1 tensor-core GEMM by S_hi + S_lo, "
-                         "2 tensor-core GEMM by S_hi (option dst_tensor)")
+    ap.add_argument("--dst-tensor", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="FP32 path transform along z: -1 the library's choice, 0 FFT, 1 tensor-core GEMM "
+                         "by S_hi + S_lo, 2 tensor-core GEMM by S_hi (option dst_tensor)")
     return ap.parse_args()
 
 
@@ -416,7 +416,7 @@ def main():
     m = med.n_rhs
     kr, kz, q = sample_operator_inputs(med, nr, nz)
     op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz)
-    if args.dst_tensor:
+    if args.dst_tensor >= 0:
         P.ax_set_option(op, "dst_tensor", args.dst_tensor)
     f_host = sample_rhs(med, nr, nz)
     f = torch.from_numpy(f_host).to(dev)

@@ -142,8 +142,10 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    products, S to about 2^-16), 2 by S_hi = bf16(S) alone
  *                    (two products; a fixed symmetric matrix within ~3e-3 of
  *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
- *                    close to B^-1); 0: the FFT transform (default).  nz <=
- *                    2048, else AX_ERR_UNSUPPORTED
+ *                    close to B^-1); 0: the FFT transform.  Default: 1 when
+ *                    nz <= 2048 and the FFT length nz + 1 has a prime factor
+ *                    above 7 (e.g. 1025 = 5^2 41), else 0.  nz <= 2048, else
+ *                    AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */

@@ -68,7 +68,9 @@ __device__ __forceinline__ bool rhs_selected(const RhsState *st, int mask, int m
 //   (row % 128 / 8) 1024 + (pos % 64 / 8) 128 + (row % 8) 16 + (pos % 8) 2.
 // Columns are stored even ones first (the operand order of the transform's
 // even / odd split): column c at position c / 2 if c is even, else at
-// kbe 64 + c / 2, with kbe = ceil(ceil(n / 2) / 64) tiles of even columns.
+// kbe 64 + c / 2, with kbe = ceil(n8 / 2 / 64) tiles of even columns and as
+// many of odd ones, n8 = n rounded up to 8.  Writers store whole chunks of 8
+// columns c < n8 only (chunk starts c < n), which keeps every position inside.
 // A tile is copied to shared memory as it is.  Padding rows and positions
 // hold zeros (the buffer is zeroed when allocated and never written there).
 // ---------------------------------------------------------------------------

@@ -36,6 +36,7 @@
 #include <cstdint>
 #include <cstring>
 #include <cmath>
+#include <algorithm>
 #include <vector>
 #include "ax_common.cuh"
 
@@ -43,22 +44,28 @@ namespace ax {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 64;
-constexpr unsigned kTmemCols = 2 * kBN;  // P and Q accumulators
+constexpr int kBM = 128, kBN = 128, kBK = 64;
+// one tile: P and Q, kBN columns each; two tiles in flight (MMA / epilogue)
+constexpr unsigned kTileCols = 2 * kBN;
+constexpr unsigned kTmemCols = 2 * kTileCols;
 constexpr int kATileBytes = kSplitTileBytes;                // hi and lo halves, 32 KB
-constexpr int kBTileBytes = kBN * kBK * 2;                  // 32 KB
-constexpr int kGemmThreads = 256;
+constexpr int kBTileBytes = kBN * kBK * 2;                  // 16 KB
+constexpr int kEpiWarps = 8;                                // warps 4 .. 11
+constexpr int kGemmThreads = 128 + 32 * kEpiWarps;
 constexpr unsigned kWaitPolls = 1u << 22;
 
 template <int THREE> struct GemmStages {
   static constexpr int stage_bytes = kATileBytes + (1 + THREE) * kBTileBytes;
-  static constexpr int stages = THREE ? 2 : 3;
+  static constexpr int stages = THREE ? 3 : 4;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -141,6 +148,16 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
 // Tiles in shared memory: byte offset of element (row, k) of a K = 64 block is
 // (row / 8) 1024 + (k / 8) 128 + (row % 8) 16 + (k % 8) 2.
 
+// Tile t (persistent CTAs take t = blockIdx.x, + gridDim.x, ...): N tile
+// fastest, so the CTAs working on one M tile at a time share its input tiles
+// in L2.
+__device__ __forceinline__ void gemm_tile(const GemmDstArgs &a, int t, int &m, int &mt, int &nt) {
+  nt = t % a.ntiles;
+  const int mm = t / a.ntiles;
+  m = mm / a.mtiles;
+  mt = mm - m * a.mtiles;
+}
+
 template <int THREE>
 __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDstArgs a) {
   constexpr int kStageBytes = GemmStages<THREE>::stage_bytes;
@@ -148,25 +165,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
   extern __shared__ __align__(1024) unsigned char gsm_raw[];
   unsigned char *gsm =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull_bar[2], tempty_bar[2];
   __shared__ unsigned tmem_base;
   __shared__ int abort_flag;
-  __shared__ double red[4];
+  __shared__ double red[kEpiWarps];
 
-  const int nt = blockIdx.x;
-  const int m = blockIdx.y / a.mtiles;
-  const int mt = blockIdx.y - m * a.mtiles;
-  if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = mt * kBM;
   const int KB = a.ktiles;
+  const int ntile_all = a.m * a.mtiles * a.ntiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], kEpiWarps);
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -185,117 +201,158 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
     // ---- MMA issuer ----
     if (lane == 0) {
       bool ok = true;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % kStages;
-        if (!mbar_wait(&full_bar[s], (unsigned)(kb / kStages) & 1u)) {
+      int kk = 0;  // k blocks consumed so far (ring position)
+      int it = 0;  // tiles processed so far (TMEM buffer = it & 1)
+      for (int t = blockIdx.x; t < ntile_all && ok; t += gridDim.x) {
+        int m, mt, nt;
+        gemm_tile(a, t, m, mt, nt);
+        if (!rhs_selected(a.st, a.mask, m)) continue;  // skipped alike by every role
+        const int b = it & 1;
+        // the epilogue must have drained this buffer (its previous tile)
+        if (it >= 2 && !mbar_wait(&tempty_bar[b], (unsigned)((it >> 1) - 1) & 1u)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        unsigned char *st = gsm + s * kStageBytes;
-        const bool odd = kb >= a.kbe;                       // Q block
-        const unsigned acc_t = tmem + (odd ? (unsigned)kBN : 0u);
-        const int first = odd ? a.kbe : 0;                  // first block of this accumulator
+        const unsigned accP = tmem + (unsigned)b * kTileCols, accQ = accP + kBN;
+        for (int kb = 0; kb < KB; ++kb, ++kk) {
+          const int s = kk % kStages;
+          if (!mbar_wait(&full_bar[s], (unsigned)(kk / kStages) & 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          unsigned char *st = gsm + s * kStageBytes;
+          const bool odd = kb >= a.kbe;  // Q block
+          const unsigned acc_t = odd ? accQ : accP;
+          const int first = odd ? a.kbe : 0;
 #pragma unroll
-        for (int j = 0; j < kBK / 16; ++j) {
-          const uint64_t ahi = smem_desc(st + j * 256), alo = smem_desc(st + kATileBytes / 2 + j * 256);
-          const uint64_t bhi = smem_desc(st + kATileBytes + j * 256);
-          umma(acc_t, ahi, bhi, (kb != first || j != 0) ? 1u : 0u);
-          umma(acc_t, alo, bhi, 1u);
-          if (THREE) umma(acc_t, ahi, smem_desc(st + kATileBytes + kBTileBytes + j * 256), 1u);
+          for (int j = 0; j < kBK / 16; ++j) {
+            const uint64_t ahi = smem_desc(st + j * 256), alo = smem_desc(st + kATileBytes / 2 + j * 256);
+            const uint64_t bhi = smem_desc(st + kATileBytes + j * 256);
+            umma(acc_t, ahi, bhi, (kb != first || j != 0) ? 1u : 0u);
+            umma(acc_t, alo, bhi, 1u);
+            if (THREE) umma(acc_t, ahi, smem_desc(st + kATileBytes + kBTileBytes + j * 256), 1u);
+          }
+          umma_commit(&empty_bar[s]);
         }
-        umma_commit(&empty_bar[s]);
+        if (ok) umma_commit(&tfull_bar[b]);  // accumulators of this tile complete
+        ++it;
       }
       if (!ok) {
         atomicExch(&abort_flag, 1);
         if (a.err) atomicExch(a.err, 1);
       }
-      umma_commit(&done_bar);  // arrives once every MMA issued above has completed
     }
   } else if (warp == 1) {
     // ---- bulk copies: input tile (m, mt, kb) and the S tiles (nt, kb) ----
     if (lane == 0) {
-      const unsigned char *ga = a.A + ((size_t)m * a.mtiles + mt) * KB * (size_t)kATileBytes;
-      const unsigned char *gb = reinterpret_cast<const unsigned char *>(a.SB) + (size_t)nt * KB * 2 * kBTileBytes;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % kStages;
-        if (kb >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(kb / kStages - 1) & 1u)) {
-          atomicExch(&abort_flag, 1);
-          if (a.err) atomicExch(a.err, 1);
-          break;
+      int kk = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntile_all && ok; t += gridDim.x) {
+        int m, mt, nt;
+        gemm_tile(a, t, m, mt, nt);
+        if (!rhs_selected(a.st, a.mask, m)) continue;
+        const unsigned char *ga = a.A + ((size_t)m * a.mtiles + mt) * KB * (size_t)kATileBytes;
+        const unsigned char *gb =
+            reinterpret_cast<const unsigned char *>(a.SB) + (size_t)nt * KB * 2 * kBTileBytes;
+        for (int kb = 0; kb < KB; ++kb, ++kk) {
+          const int s = kk % kStages;
+          if (kk >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(kk / kStages - 1) & 1u)) {
+            ok = false;
+            break;
+          }
+          if (abort_flag) {
+            ok = false;
+            break;
+          }
+          unsigned char *st = gsm + s * kStageBytes;
+          mbar_arrive_tx(&full_bar[s], (unsigned)(kATileBytes + (1 + THREE) * kBTileBytes));
+          bulk_g2s(st, ga + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
+          bulk_g2s(st + kATileBytes, gb + (size_t)kb * 2 * kBTileBytes, kBTileBytes, &full_bar[s]);
+          if (THREE)
+            bulk_g2s(st + kATileBytes + kBTileBytes, gb + ((size_t)kb * 2 + 1) * kBTileBytes, kBTileBytes,
+                     &full_bar[s]);
         }
-        unsigned char *st = gsm + s * kStageBytes;
-        mbar_arrive_tx(&full_bar[s], (unsigned)(kATileBytes + (1 + THREE) * kBTileBytes));
-        bulk_g2s(st, ga + (size_t)kb * kATileBytes, kATileBytes, &full_bar[s]);
-        bulk_g2s(st + kATileBytes, gb + (size_t)kb * 2 * kBTileBytes, kBTileBytes, &full_bar[s]);
-        if (THREE)
-          bulk_g2s(st + kATileBytes + kBTileBytes, gb + ((size_t)kb * 2 + 1) * kBTileBytes, kBTileBytes,
-                   &full_bar[s]);
+      }
+      if (!ok) {
+        atomicExch(&abort_flag, 1);
+        if (a.err) atomicExch(a.err, 1);
       }
     }
   } else if (warp >= 4) {
     // ---- epilogue: TMEM -> registers -> global (and the (r, out) partial) ----
-    const int tid = threadIdx.x - 128;
-    const int q = warp - 4;  // TMEM lane quarter of this warp
-    const bool ok = mbar_wait(&done_bar, 0u);
-    if (!ok) {
-      atomicExch(&abort_flag, 1);
-      if (a.err) atomicExch(a.err, 1);
-    }
-    tc_fence_after();
-    const int grow = row0 + q * 32 + lane;
-    float acc = 0.f;
-    // warp-uniform decision (tcgen05.ld is a warp-collective instruction)
-    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
-      float *outr = a.out + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
-      const float *rr = (a.r != nullptr) ? a.r + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch : nullptr;
-      const int n = a.n, ne = (n + 1) >> 1;
+    // warp w drains TMEM lane quarter w % 4, columns half (w - 4) / 4 of P and Q
+    const int ew = warp - 4;
+    const int q = warp & 3, half = ew >> 2;
+    const int n = a.n, ne = (n + 1) >> 1;
+    int it = 0;  // tiles processed so far, as counted by the MMA issuer
+    for (int t = blockIdx.x; t < ntile_all; t += gridDim.x) {
+      int m, mt, nt;
+      gemm_tile(a, t, m, mt, nt);
+      if (!rhs_selected(a.st, a.mask, m)) continue;
+      const int b = it & 1;
+      ++it;
+      const bool ok = !abort_flag && mbar_wait(&tfull_bar[b], (unsigned)((it - 1) >> 1) & 1u);
+      if (!ok) {
+        atomicExch(&abort_flag, 1);
+        if (a.err) atomicExch(a.err, 1);
+      }
+      tc_fence_after();
+      const int grow = mt * kBM + q * 32 + lane;
+      float acc = 0.f;
+      if (__all_sync(0xffffffffu, ok)) {
+        float *outr = a.out + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
+        const float *rr =
+            (a.r != nullptr) ? a.r + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch : nullptr;
+        const unsigned tP = tmem + ((unsigned)(q * 32) << 16) + (unsigned)b * kTileCols;
 #pragma unroll 1
-      for (int c = 0; c < kBN / 32; ++c) {
-        const int l0 = nt * kBN + c * 32;
-        if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= ne) break;  // nothing left for this warp
-        float P[32], Q[32];
-        tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(c * 32), P);
-        if (a.ktiles > a.kbe) {
-          tmem_ld32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(kBN + c * 32), Q);
-        } else {
+        for (int c = half * 2; c < half * 2 + 2; ++c) {
+          const int l0 = nt * kBN + c * 32;
+          if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= ne) break;  // nothing left for this warp
+          float P[32], Q[32];
+          tmem_ld32(tP + (unsigned)(c * 32), P);
+          if (a.ktiles > a.kbe) {
+            tmem_ld32(tP + (unsigned)(kBN + c * 32), Q);
+          } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
-        }
-        if (grow < a.nr) {
+            for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
+          }
+          if (grow < a.nr) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            const int l = l0 + i;
-            float s0[4], d0[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              s0[e] = P[i + e] + Q[i + e];  // out[l + e]
-              d0[e] = P[i + e] - Q[i + e];  // out[n - 1 - l - e]
-            }
-            if (l + 3 < ne && (n & 3) == 0) {
-              // n % 4 == 0: both runs are whole aligned float4 groups, and the
-              // mirrored one (columns n - 4 - l .. n - 1 - l) lies above ne
-              const int lm = n - 4 - l;
-              *reinterpret_cast<float4 *>(outr + l) = make_float4(s0[0], s0[1], s0[2], s0[3]);
-              *reinterpret_cast<float4 *>(outr + lm) = make_float4(d0[3], d0[2], d0[1], d0[0]);
-              if (rr) {
-                const float4 ra = *reinterpret_cast<const float4 *>(rr + l);
-                const float4 rb = *reinterpret_cast<const float4 *>(rr + lm);
-                acc = fmaf(ra.x, s0[0], acc); acc = fmaf(ra.y, s0[1], acc);
-                acc = fmaf(ra.z, s0[2], acc); acc = fmaf(ra.w, s0[3], acc);
-                acc = fmaf(rb.x, d0[3], acc); acc = fmaf(rb.y, d0[2], acc);
-                acc = fmaf(rb.z, d0[1], acc); acc = fmaf(rb.w, d0[0], acc);
-              }
-            } else {
+            for (int i = 0; i < 32; i += 4) {
+              const int l = l0 + i;
+              float s0[4], d0[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const int le = l + e, lm = n - 1 - le;
-                if (le < ne) {
-                  outr[le] = s0[e];
-                  if (rr) acc = fmaf(rr[le], s0[e], acc);
-                  if (lm != le) {  // the middle column of odd n is written once
-                    outr[lm] = d0[e];
-                    if (rr) acc = fmaf(rr[lm], d0[e], acc);
+                s0[e] = P[i + e] + Q[i + e];  // out[l + e]
+                d0[e] = P[i + e] - Q[i + e];  // out[n - 1 - l - e]
+              }
+              if (l + 3 < ne && (n & 3) == 0) {
+                // n % 4 == 0: both runs are whole aligned float4 groups, and the
+                // mirrored one (columns n - 4 - l .. n - 1 - l) lies above ne
+                const int lm = n - 4 - l;
+                *reinterpret_cast<float4 *>(outr + l) = make_float4(s0[0], s0[1], s0[2], s0[3]);
+                *reinterpret_cast<float4 *>(outr + lm) = make_float4(d0[3], d0[2], d0[1], d0[0]);
+                if (rr) {
+                  const float4 ra = *reinterpret_cast<const float4 *>(rr + l);
+                  const float4 rb = *reinterpret_cast<const float4 *>(rr + lm);
+                  acc = fmaf(ra.x, s0[0], acc); acc = fmaf(ra.y, s0[1], acc);
+                  acc = fmaf(ra.z, s0[2], acc); acc = fmaf(ra.w, s0[3], acc);
+                  acc = fmaf(rb.x, d0[3], acc); acc = fmaf(rb.y, d0[2], acc);
+                  acc = fmaf(rb.z, d0[1], acc); acc = fmaf(rb.w, d0[0], acc);
+                }
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const int le = l + e, lm = n - 1 - le;
+                  if (le < ne) {
+                    outr[le] = s0[e];
+                    if (rr) acc = fmaf(rr[le], s0[e], acc);
+                    if (lm != le) {  // the middle column of odd n is written once
+                      outr[lm] = d0[e];
+                      if (rr) acc = fmaf(rr[lm], d0[e], acc);
+                    }
                   }
                 }
               }
@@ -303,21 +360,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
           }
         }
       }
-    }
-    if (a.partial) {
-      double s = warp_sum((double)acc);
-      if (lane == 0) red[q] = s;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (tid == 0) a.partial[(size_t)m * kPartialStride + mt * gridDim.x + nt] = red[0] + red[1] + red[2] + red[3];
+      // buffer b drained: the MMA issuer may reuse it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[b]);
+      if (a.partial) {
+        const double sw = warp_sum((double)acc);
+        if (lane == 0) red[ew] = sw;
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        if (ew == 0 && lane == 0) {
+          double tot = 0.0;
+#pragma unroll
+          for (int i = 0; i < kEpiWarps; ++i) tot += red[i];
+          a.partial[(size_t)m * kPartialStride + mt * a.ntiles + nt] = tot;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+      }
     }
   }
 
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    // the MMAs are complete once done_bar fired; if a wait expired, wait once
-    // more (bounded) before the columns are released
-    if (abort_flag) mbar_wait(&done_bar, 0u);
+    // every MMA this CTA issued has completed once its tile's tfull fired; after
+    // an expired wait, give the tensor core a bounded moment before freeing
+    if (abort_flag) {
+      for (int b = 0; b < 2; ++b) mbar_wait(&tfull_bar[b], 0u);
+    }
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
@@ -330,8 +399,11 @@ size_t dst_gemm_smem_bytes(int three) {
                : (size_t)GemmStages<0>::stages * GemmStages<0>::stage_bytes + 1024;
 }
 
-int dst_gemm_kbe(int n) { return ((n + 1) / 2 + kBK - 1) / kBK; }
-int dst_gemm_ktiles(int n) { return dst_gemm_kbe(n) + (n / 2 + kBK - 1) / kBK; }
+// K tiles of even and of odd input columns.  The writers of the split operand
+// store whole 8-column chunks, so the ranges cover n rounded up to 8 columns
+// (positions past n hold zeros; S has zero rows there).
+int dst_gemm_kbe(int n) { return (((n + 7) & ~7) / 2 + kBK - 1) / kBK; }
+int dst_gemm_ktiles(int n) { return 2 * dst_gemm_kbe(n); }
 int dst_gemm_ntiles(int n) { return ((n + 1) / 2 + kBN - 1) / kBN; }
 int dst_gemm_mtiles(int rows) { return (rows + kBM - 1) / kBM; }
 
@@ -383,7 +455,15 @@ std::vector<uint16_t> dst_gemm_table(int n) {
 
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s) {
   const size_t smem = dst_gemm_smem_bytes(a.three);
-  dim3 grid(a.ntiles, a.m * a.mtiles);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  const int tiles = a.m * a.mtiles * a.ntiles;
+  dim3 grid(std::min(tiles, sms));
   note_launch();
   if (a.three) {
     ensure_smem_attr((const void *)dst_gemm_kernel<1>, smem);

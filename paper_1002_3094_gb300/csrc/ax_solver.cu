@@ -397,8 +397,8 @@ __device__ __forceinline__ void split_task(int t, int ctiles, int &row, int &col
 constexpr int kUpdateBlocks = 64;  // CTAs per right-hand side
 __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *__restrict__ r,
                                                   const float *__restrict__ q, const float *__restrict__ pa,
-                                                  const float *__restrict__ pb, int nr, int pitch, size_t field,
-                                                  int mtiles, int ctiles, int ktiles, int kbe,
+                                                  const float *__restrict__ pb, int nr, int n, int pitch,
+                                                  size_t field, int mtiles, int ctiles, int ktiles, int kbe,
                                                   unsigned char *__restrict__ split,
                                                   const RhsState *st, int mask, double *__restrict__ partial) {
   __shared__ double red[8];
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
     int row, col;
     split_task(t, ctiles, row, col);
-    if (row >= nr || col >= pitch) continue;  // col + 8 <= pitch (pitch is a multiple of 32)
+    if (row >= nr || col >= n) continue;  // col + 8 <= n rounded up to 8 <= pitch
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
     float xv[8], pv[8], rv[8], qv[8];
     *reinterpret_cast<float4 *>(xv) = *reinterpret_cast<const float4 *>(x + e);
@@ -439,8 +439,8 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
 }
 
 // The rows of a field written split into BF16 halves (tensor-core transform input).
-__global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int pitch, size_t field,
-                                                   int mtiles, int ctiles, int ktiles, int kbe,
+__global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int n, int pitch,
+                                                   size_t field, int mtiles, int ctiles, int ktiles, int kbe,
                                                    unsigned char *__restrict__ split,
                                                    const RhsState *st, int mask) {
   const int m = blockIdx.y;
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(256) split_field(const float *__restrict__ in,
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
     int row, col;
     split_task(t, ctiles, row, col);
-    if (row >= nr || col >= pitch) continue;
+    if (row >= nr || col >= n) continue;  // col + 8 <= n rounded up to 8 <= pitch
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
     float v[8];
     *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(in + e);
@@ -1041,8 +1041,8 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
               int mask, cudaStream_t s) {
   const SplitGeom g = split_geom(op, rows);
   note_launch();
-  split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->pitch, (size_t)rows * op->pitch, g.mtiles,
-                                                      g.ctiles, g.ktiles, g.kbe, split, st, mask);
+  split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->nz, op->pitch, (size_t)rows * op->pitch,
+                                                      g.mtiles, g.ctiles, g.ktiles, g.kbe, split, st, mask);
 }
 
 // Mode solves z -> split operand (the tile kernel writes it directly; otherwise
@@ -1135,7 +1135,7 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       {
         ProfScope ps(w, kProfDstFwd, units, s);
         note_launch();
-        pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(v.x, v.r, v.q, v.pa, v.pb, op->nr, op->pitch,
+        pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(v.x, v.r, v.q, v.pa, v.pb, op->nr, op->nz, op->pitch,
                                                           field_elems(op), g.mtiles, g.ctiles, g.ktiles, g.kbe, sp,
                                                           st, kActive, prr);
         tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s);
@@ -1657,6 +1657,13 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
     ax_destroy_operator(op);
     return AX_ERR_UNSUPPORTED;
   }
+  // Transform of the FP32 path: the tensor-core GEMM when the FFT of length L
+  // needs a prime radix above 8 (paired direct DFT or Rader stages, several
+  // times the work of the small radices) and nz is within the GEMM's range.
+  op->dst_tc = 0;
+  if (nz <= kMaxTcN)
+    for (int i = 0; i < op->plan.nstages; ++i)
+      if (op->plan.radix[i] > 8) op->dst_tc = 1;
 
   const double hr = op->hr, hz = op->hz, hr2 = hr * hr, hz2 = hz * hz;
   const int P = op->pitch, PZ = op->pitchz;
@@ -1792,6 +1799,18 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
   note_launch();
   padded_to_dense<T><<<blocks, 256, 0, s>>>(b, out, rows, op->nz, op->pitch);
   AX_CHECK_LAUNCH();
+  if (tc) {
+    int *flag = tc_flag(op->device), hf = 0;
+    if (flag) {
+      AX_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      AX_TRY(cudaStreamSynchronize(s));
+      if (hf) {
+        AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+        snprintf(g_last_error, sizeof(g_last_error), "tensor-core transform: a bounded wait expired");
+        return AX_ERR_TIMEOUT;
+      }
+    }
+  }
   return AX_OK;
 }
 
@@ -2186,6 +2205,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     gop->kappa_t = o->kappa_t; gop->q_t = o->q_t; gop->gamma1 = o->gamma1; gop->gamma2 = o->gamma2;
     gop->device = o->device;
     gop->plan = o->plan;
+    gop->dst_tc = o->dst_tc;
     gop->cstride = (long long)o->nr * o->pitch;
     gop->czstride = (long long)o->nr * o->pitchz;
     gop->estride = o->nr;

@@ -58,7 +58,8 @@ def _split_reference(x, n, three):
     return out
 
 
-@pytest.mark.parametrize("rows,nz", [(300, 1024), (129, 200), (7, 31), (128, 256), (1, 1), (260, 2048)])
+@pytest.mark.parametrize("rows,nz", [(300, 1024), (129, 200), (7, 31), (128, 256), (1, 1), (5, 2), (3, 9),
+                                     (130, 65), (64, 127), (260, 2048)])
 @pytest.mark.parametrize("prec", [P.AX_PREC_FP32_TC, P.AX_PREC_FP32_TC3])
 def test_tensor_transform_matches_split_products(cuda, rows, nz, prec):
     op, _, _ = _op(max(rows, 2), nz, cuda)
