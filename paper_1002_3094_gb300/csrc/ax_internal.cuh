@@ -81,7 +81,9 @@ struct Coef {
   T *HW = nullptr;   // [2 L]         (cos, sin)(pi j / L),   j < L
   T *RK = nullptr;   // [2 P]         Rader: DFT of the permuted kernel W^(g^-m)
   T *RT = nullptr;   // [2 P]         Rader: (cos, sin)(2 pi j / P)
-  uint16_t *SB = nullptr;  // FP32 only: BF16 DST matrix tiles of the tensor-core transform
+  // FP32 only: low parts of the FP64 stencil coefficients, CR64 = CR + CRl (CR the
+  // FP32 rounding), for the double-float residual of the mixed method
+  T *CRl = nullptr, *CZl = nullptr, *Wl = nullptr;
 };
 
 // Scalar state of one right-hand side during an iteration.  Lives in device
@@ -178,6 +180,25 @@ struct StencilArgs {
 template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s);
 int stencil_blocks_per_rhs(int nr, int nz, int vec);
+
+// Double-float true residual r = phi - A x of the mixed method: x, phi and the
+// coefficients as pairs of FP32 numbers (hi + lo), all arithmetic in FP32 with
+// error-free transformations; r is returned rounded to FP32 with per-CTA
+// partials of ||r||^2.
+struct DfResidualArgs {
+  const float *CRh, *CRl, *CZh, *CZl, *Wh, *Wl;
+  long long cstride, czstride;  // coefficient elements per RHS (0: one operator for all RHS)
+  int nr, nz, pitch, pitchz;
+  long long field;
+  int m;
+  const float *xh, *xl, *ph, *pl;
+  float *r32;
+  const RhsState *st;
+  int mask;
+  double *partial;  // [m][kPartialStride], slot blockIdx.y * gridDim.x + blockIdx.x
+};
+void launch_residual_df(const DfResidualArgs &a, cudaStream_t s);
+int residual_df_blocks(int nr, int nz);
 
 // Sine-transform modes
 enum { kDstPlain = 0, kDstPcgForward = 1, kDstPcgInverse = 2, kDstChebInverse = 3 };

@@ -52,6 +52,7 @@ struct Workspace {
   double *phi64 = nullptr, *x64 = nullptr;
   double *r64 = nullptr, *pa64 = nullptr, *pb64 = nullptr, *q64 = nullptr, *z64 = nullptr, *y64prev = nullptr;
   // FP32 vectors
+  float *xh = nullptr, *xl = nullptr, *phh = nullptr, *phl = nullptr;  // double-float x and phi (mixed PCG)
   float *x32 = nullptr, *r32 = nullptr, *pa32 = nullptr, *pb32 = nullptr, *q32 = nullptr, *z32 = nullptr,
         *y32prev = nullptr;
   // partial sums [4][m][kPartialStride]
@@ -161,6 +162,7 @@ void free_vectors64(Workspace *w) {
 }
 void free_vectors32(Workspace *w) {
   dfree(w->x32); dfree(w->r32); dfree(w->pa32); dfree(w->pb32); dfree(w->q32); dfree(w->z32); dfree(w->y32prev);
+  dfree(w->xh); dfree(w->xl); dfree(w->phh); dfree(w->phl);
   w->m32 = 0;
   free_graph(w->g32);
   free_graph(w->gc32);
@@ -219,6 +221,10 @@ int ensure_vec32(ax_operator *op, int m, bool cheb) {
   AX_TRY(dalloc(&w->pb32, f));
   AX_TRY(dalloc(&w->q32, f));
   AX_TRY(dalloc(&w->z32, f));
+  AX_TRY(dalloc(&w->xh, f));
+  AX_TRY(dalloc(&w->xl, f));
+  AX_TRY(dalloc(&w->phh, f));
+  AX_TRY(dalloc(&w->phl, f));
   if (cheb) AX_TRY(dalloc(&w->y32prev, f));
   w->m32 = m;
   return AX_OK;
@@ -354,30 +360,6 @@ __global__ void add_correction(double *__restrict__ x, const float *__restrict__
     x[b + e] += (double)d[b + e];
 }
 
-// Residual replacement of the selected right-hand sides: x64 += x32 and
-// x32 = 0 in one pass (field is a multiple of 4: the pitch is).  Launched
-// with a few CTAs per right-hand side, since in most launches no right-hand
-// side is selected and every CTA returns at once.
-__global__ void fold_correction(double *__restrict__ x, float *__restrict__ d, size_t field, const RhsState *st,
-                                int mask) {
-  const int m = blockIdx.y;
-  if (!rhs_selected(st, mask, m)) return;
-  double2 *x2 = reinterpret_cast<double2 *>(x + (size_t)m * field);
-  float4 *d4 = reinterpret_cast<float4 *>(d + (size_t)m * field);
-  const size_t n4 = field / 4;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
-    const float4 c = d4[e];
-    double2 a = x2[2 * e], b = x2[2 * e + 1];
-    a.x += (double)c.x;
-    a.y += (double)c.y;
-    b.x += (double)c.z;
-    b.y += (double)c.w;
-    x2[2 * e] = a;
-    x2[2 * e + 1] = b;
-    d4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
 // Task t of a right-hand side: 8 consecutive columns of one row, in blocks of
 // 128 rows x 64 natural columns (8 rows of one column chunk, then 8 chunks,
 // then row groups, then blocks), so that a warp reads 8 rows x 128 bytes and
@@ -387,6 +369,40 @@ __device__ __forceinline__ void split_task(int t, int ctiles, int &row, int &col
   const int mt = tile / ctiles, kb = tile - mt * ctiles;
   row = mt * 128 + (w >> 6) * 8 + (w & 7);
   col = kb * 64 + ((w >> 3) & 7) * 8;
+}
+
+// FP64 field -> double-float pair (hi = fl(x), lo = fl(x - hi)) and back.
+__global__ void to_df(const double *__restrict__ x, float *__restrict__ h, float *__restrict__ l, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float hv = (float)v;
+    h[i] = hv;
+    l[i] = (float)(v - (double)hv);
+  }
+}
+__global__ void from_df(const float *__restrict__ h, const float *__restrict__ l, double *__restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] = (double)h[i] + (double)l[i];
+}
+// Replacement of the selected right-hand sides in double-float: (xh, xl) +=
+// x32 (two-sum, then renormalised) and x32 = 0 in one pass.  Launched with a
+// few CTAs per right-hand side, since in most launches no right-hand side is
+// selected and every CTA returns at once.
+__global__ void fold_df(float *__restrict__ xh, float *__restrict__ xl, float *__restrict__ d, size_t field,
+                        const RhsState *st, int mask) {
+  const int m = blockIdx.y;
+  if (!rhs_selected(st, mask, m)) return;
+  const size_t b = (size_t)m * field;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < field; e += (size_t)gridDim.x * blockDim.x) {
+    const float a = xh[b + e], c = d[b + e];
+    const float s = a + c, bb = s - a;
+    float err = (a - (s - bb)) + (c - bb);
+    err += xl[b + e];
+    const float hs = s + err;
+    xh[b + e] = hs;
+    xl[b + e] = err - (hs - s);
+    d[b + e] = 0.f;
+  }
 }
 
 // x += alpha p, r -= alpha q for the selected right-hand sides, with per-block
@@ -865,6 +881,7 @@ template <typename T>
 void free_coef(Coef<T> &c) {
   dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW);
   dfree(c.RK); dfree(c.RT);
+  dfree(c.CRl); dfree(c.CZl); dfree(c.Wl);
 }
 
 // ---------------------------------------------------------------------------
@@ -1414,38 +1431,55 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   Workspace *w = op->ws;
   RhsState *st = w->st;
   const size_t field = field_elems(op);
-  const int nbs64 = stencil_blocks_per_rhs(op->nr, op->nz, 2);
+  const int nbdf = residual_df_blocks(op->nr, op->nz);
   const int nbf = (op->nr + 15) / 16;
   const int nbd = precond_partials<float>(op);
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
-  // a few thousand CTAs in all for the replacement fold (see fold_correction)
+  const size_t nall = field * m;
+  const unsigned cblocks = (unsigned)std::min<size_t>((nall + 255) / 256, 65535);
+  // a few thousand CTAs in all for the replacement fold (see fold_df)
   const unsigned fold_x = (unsigned)std::max<size_t>(
       1, std::min<size_t>((field / 4 + 255) / 256, (size_t)std::max(8, 4096 / std::max(1, m))));
   const dim3 zg(fold_x, m);
+  // The true residual phi - A x in double-float (x and phi as FP32 pairs, the
+  // FP64 coefficients as FP32 + low part): FP32 arithmetic throughout.
   auto residual64 = [&](int mask, cudaStream_t ss) {
-    StencilArgs<double> ra = stencil_args<double>(op, m, st, mask);
-    ra.in = w->x64;
-    ra.phi = w->phi64;
-    ra.out32 = w->r32;
+    DfResidualArgs ra{};
+    ra.CRh = op->c32.CR; ra.CRl = op->c32.CRl;
+    ra.CZh = op->c32.CZ; ra.CZl = op->c32.CZl;
+    ra.Wh = op->c32.W; ra.Wl = op->c32.Wl;
+    ra.cstride = op->cstride;
+    ra.czstride = op->czstride;
+    ra.nr = op->nr; ra.nz = op->nz; ra.pitch = op->pitch; ra.pitchz = op->pitchz;
+    ra.field = (long long)field;
+    ra.m = m;
+    ra.xh = w->xh; ra.xl = w->xl; ra.ph = w->phh; ra.pl = w->phl;
+    ra.r32 = w->r32;
+    ra.st = st;
+    ra.mask = mask;
     ra.partial = part_ptr(w, kPartB);
     ProfScope ps(w, kProfOuter, (double)op->nr * op->nz * m, ss);
-    launch_stencil<double>(kStencilResidual, ra, ss);
+    launch_residual_df(ra, ss);
   };
   auto start = [&]() {
+    note_launch();
+    to_df<<<cblocks, 256, 0, s>>>(w->x64, w->xh, w->xl, nall);
     residual64(-1, s);
     note_launch();
-    sc_mixed_start<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbs64, part_ptr(w, kPartD), nbf, tol * tol,
+    sc_mixed_start<<<m, 32, 0, s>>>(st, part_ptr(w, kPartB), nbdf, part_ptr(w, kPartD), nbf, tol * tol,
                                     delta * delta, max_iter);
   };
+  note_launch();
+  to_df<<<cblocks, 256, 0, s>>>(w->phi64, w->phh, w->phl, nall);
   // Residual replacement of the right-hand sides in kCheck (every kernel
   // returns at once for the others, so this runs after every iteration inside
   // the captured graph and no right-hand side waits for the host).
   auto replace_step = [&](cudaStream_t ss) {
     note_launch();
-    fold_correction<<<zg, 256, 0, ss>>>(w->x64, w->x32, field, st, kCheck);
+    fold_df<<<zg, 256, 0, ss>>>(w->xh, w->xl, w->x32, field, st, kCheck);
     residual64(kCheck, ss);
     note_launch();
-    sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbs64, tol * tol, delta * delta);
+    sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbdf, tol * tol, delta * delta);
     precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss, v.q);
     note_launch();
     sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
@@ -1488,6 +1522,10 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
     if (!any_state(h, m, kActive) && !any_state(h, m, kCheck)) break;
   }
+  // the iterate back in FP64
+  note_launch();
+  from_df<<<cblocks, 256, 0, s>>>(w->xh, w->xl, w->x64, nall);
+  AX_CHECK_LAUNCH();
   return AX_OK;
 }
 
@@ -1707,6 +1745,17 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   AX_UP(float, c32.CR, CR) AX_UP(float, c32.CZ, CZ) AX_UP(float, c32.W, W) AX_UP(float, c32.IP, IP)
   AX_UP(float, c32.E, E) AX_UP(float, c32.R, ri) AX_UP(float, c32.TW, TW) AX_UP(float, c32.HW, HW)
 #undef AX_UP
+  {
+    // low parts for the double-float residual: v64 = (float)v64 + lo
+    auto lo_of = [](const std::vector<double> &v) {
+      std::vector<double> lo(v.size());
+      for (size_t i = 0; i < v.size(); ++i) lo[i] = v[i] - (double)(float)v[i];
+      return lo;
+    };
+    if (e == cudaSuccess) e = upload<float>(&op->c32.CRl, lo_of(CR));
+    if (e == cudaSuccess) e = upload<float>(&op->c32.CZl, lo_of(CZ));
+    if (e == cudaSuccess) e = upload<float>(&op->c32.Wl, lo_of(W));
+  }
   if (e == cudaSuccess && op->plan.rader) {
     std::vector<int> perm;
     std::vector<double> rk, rt;
@@ -2125,6 +2174,16 @@ cudaError_t build_group_coef(Coef<T> &g, const std::vector<const ax_operator *> 
   if (err == cudaSuccess) err = stack_table(&g.W, f, w, s);
   if (err == cudaSuccess) err = stack_table(&g.IP, f, ip, s);
   if (err == cudaSuccess) err = stack_table(&g.E, (size_t)o->nr, e, s);
+  if (pick(o).CRl != nullptr) {
+    std::vector<const T *> crl, czl, wl;
+    for (auto *op : ops) {
+      const Coef<T> &c = pick(op);
+      crl.push_back(c.CRl); czl.push_back(c.CZl); wl.push_back(c.Wl);
+    }
+    if (err == cudaSuccess) err = stack_table(&g.CRl, f, crl, s);
+    if (err == cudaSuccess) err = stack_table(&g.CZl, fz, czl, s);
+    if (err == cudaSuccess) err = stack_table(&g.Wl, f, wl, s);
+  }
   const Coef<T> &c0 = pick(o);
   if (err == cudaSuccess) err = copy_table(&g.R, c0.R, (size_t)o->nr, s);
   if (err == cudaSuccess) err = copy_table(&g.TW, c0.TW, 2 * (size_t)o->plan.L, s);

@@ -215,6 +215,119 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   }
 }
 
+// ---- double-float residual -------------------------------------------------
+// Pairs (h, l) of FP32 numbers carry about 48 significant bits: sums by Knuth's
+// two-sum and Dekker's fast two-sum, products by the FMA two-product (the exact
+// error of a*b is fma(a, b, -a*b)).  GB300 runs FP32 about 58 times faster
+// than FP64, so the true residual of the mixed method costs a few FP32
+// operations per flop instead of FP64 ones.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.h, b.h);
+  return df_fast(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast(p, e);
+}
+
+constexpr int kDfRows = 16;      // rows per CTA
+constexpr int kDfThreads = 256;  // 4 z-nodes per thread
+
+__global__ void __launch_bounds__(kDfThreads) residual_df_kernel(const DfResidualArgs a) {
+  __shared__ double red[8];
+  const int m = blockIdx.z;
+  if (!rhs_selected(a.st, a.mask, m)) return;
+  const int nr = a.nr, nz = a.nz, P = a.pitch, PZ = a.pitchz;
+  const int k0 = (blockIdx.x * kDfThreads + threadIdx.x) * 4;
+  const int i0 = blockIdx.y * kDfRows, i1 = min(i0 + kDfRows, nr);
+  const bool col_ok = k0 < nz;
+  const size_t base = (size_t)m * (size_t)a.field;
+  const float *crh = a.CRh + (size_t)m * a.cstride, *crl = a.CRl + (size_t)m * a.cstride;
+  const float *czh = a.CZh + (size_t)m * a.czstride, *czl = a.CZl + (size_t)m * a.czstride;
+  const float *wh = a.Wh + (size_t)m * a.cstride, *wl = a.Wl + (size_t)m * a.cstride;
+  // 4 consecutive values of a field row (zero outside the grid; padding
+  // columns hold zeros)
+  auto ld4 = [&](const float *p, size_t off, bool ok, float (&v)[4]) {
+    if (ok) {
+      const float4 t = *reinterpret_cast<const float4 *>(p + off);
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+      v[0] = v[1] = v[2] = v[3] = 0.f;
+    }
+  };
+  float ymh[4], yml[4], ych[4], ycl[4], ynh[4], ynl[4], cph[4], cpl[4];
+  ld4(a.xh, base + (size_t)(i0 - 1) * P + k0, col_ok && i0 > 0, ymh);
+  ld4(a.xl, base + (size_t)(i0 - 1) * P + k0, col_ok && i0 > 0, yml);
+  ld4(crh, (size_t)(i0 - 1) * P + k0, col_ok && i0 > 0, cph);  // CR_{i-1}: 0 on the axis
+  ld4(crl, (size_t)(i0 - 1) * P + k0, col_ok && i0 > 0, cpl);
+  ld4(a.xh, base + (size_t)i0 * P + k0, col_ok, ych);
+  ld4(a.xl, base + (size_t)i0 * P + k0, col_ok, ycl);
+  float acc = 0.f;
+  for (int i = i0; i < i1; ++i) {
+    const size_t ro = (size_t)i * P + k0;
+    ld4(a.xh, base + ro + P, col_ok && i + 1 < nr, ynh);
+    ld4(a.xl, base + ro + P, col_ok && i + 1 < nr, ynl);
+    float cch[4], ccl[4], w4h[4], w4l[4], fh[4], fl[4], zh[4], zl[4];
+    ld4(crh, ro, col_ok, cch);
+    ld4(crl, ro, col_ok, ccl);
+    ld4(wh, ro, col_ok, w4h);
+    ld4(wl, ro, col_ok, w4l);
+    ld4(a.ph, base + ro, col_ok, fh);
+    ld4(a.pl, base + ro, col_ok, fl);
+    ld4(czh, (size_t)i * PZ + k0, col_ok, zh);  // faces k0 .. k0 + 3
+    ld4(czl, (size_t)i * PZ + k0, col_ok, zl);
+    // face k0 + 4 and the z-neighbours outside the 4 nodes
+    const bool up_ok = col_ok && k0 + 4 <= nz;
+    const DF z4 = {up_ok ? czh[(size_t)i * PZ + k0 + 4] : 0.f, up_ok ? czl[(size_t)i * PZ + k0 + 4] : 0.f};
+    const bool left_ok = col_ok && k0 > 0, right_ok = col_ok && k0 + 4 < nz;
+    const DF yleft = {left_ok ? a.xh[base + ro - 1] : 0.f, left_ok ? a.xl[base + ro - 1] : 0.f};
+    const DF yright = {right_ok ? a.xh[base + ro + 4] : 0.f, right_ok ? a.xl[base + ro + 4] : 0.f};
+    float res[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const DF y = {ych[e], ycl[e]};
+      const DF yl = (e == 0) ? yleft : DF{ych[e - 1], ycl[e - 1]};
+      const DF yr = (e == 3) ? yright : DF{ych[e + 1], ycl[e + 1]};
+      const DF czlo = {zh[e], zl[e]};
+      const DF czhi = (e == 3) ? z4 : DF{zh[e + 1], zl[e + 1]};
+      // A y = W y + CR_i (y - y_{i+1}) + CR_{i-1} (y - y_{i-1})
+      //           + CZ_{k+1} (y - y_{k+1}) + CZ_k (y - y_{k-1})
+      DF v = df_mul({w4h[e], w4l[e]}, y);
+      v = df_add(v, df_mul({cch[e], ccl[e]}, df_add(y, df_neg({ynh[e], ynl[e]}))));
+      v = df_add(v, df_mul({cph[e], cpl[e]}, df_add(y, df_neg({ymh[e], yml[e]}))));
+      v = df_add(v, df_mul(czhi, df_add(y, df_neg(yr))));
+      v = df_add(v, df_mul(czlo, df_add(y, df_neg(yl))));
+      const DF r = df_add({fh[e], fl[e]}, df_neg(v));
+      res[e] = (k0 + e < nz) ? r.h + r.l : 0.f;
+      acc = fmaf(res[e], res[e], acc);
+    }
+    if (col_ok) *reinterpret_cast<float4 *>(a.r32 + base + ro) = make_float4(res[0], res[1], res[2], res[3]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ymh[e] = ych[e]; yml[e] = ycl[e];
+      ych[e] = ynh[e]; ycl[e] = ynl[e];
+      cph[e] = cch[e]; cpl[e] = ccl[e];
+    }
+  }
+  const double sum = block_sum((double)acc, red);
+  if (threadIdx.x == 0) a.partial[(size_t)m * kPartialStride + blockIdx.y * gridDim.x + blockIdx.x] = sum;
+}
+
 int column_warps(int nz, int vec) {
   int w = (nz + 32 * vec - 1) / (32 * vec);
   return w < kStencilWarps ? (w < 1 ? 1 : w) : kStencilWarps;
@@ -242,6 +355,16 @@ void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
     case kStencilResidual: stencil_kernel<T, kStencilResidual><<<grid, block, 0, s>>>(a); break;
     default: stencil_kernel<T, kStencilCheb><<<grid, block, 0, s>>>(a); break;
   }
+}
+
+int residual_df_blocks(int nr, int nz) {
+  return ((nz + 4 * kDfThreads - 1) / (4 * kDfThreads)) * ((nr + kDfRows - 1) / kDfRows);
+}
+
+void launch_residual_df(const DfResidualArgs &a, cudaStream_t s) {
+  dim3 grid((a.nz + 4 * kDfThreads - 1) / (4 * kDfThreads), (a.nr + kDfRows - 1) / kDfRows, a.m);
+  note_launch();
+  residual_df_kernel<<<grid, kDfThreads, 0, s>>>(a);
 }
 
 template void launch_stencil<float>(int, const StencilArgs<float> &, cudaStream_t);
