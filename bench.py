@@ -34,18 +34,27 @@ TOL = 1e-8
 # Algorithmic bytes per grid unknown of one launch (FP32 working precision),
 # M = right-hand sides sharing the coefficient tables.
 #   stencil (p = z + beta p, q = A p): read z, p_old; write p, q  -> 16 B, + CR, CZ, W (12 B / M)
-#   forward transform (x += a p, r -= a q, rhat = S r): read x, p, r, q; write x, r, rhat -> 28 B
+#   FFT forward transform (x += a p, r -= a q, rhat = S r): read x, p, r, q; write x, r, rhat -> 28 B
+#   update pass (x += a p, r -= a q) ahead of the tensor-core transform: read x, p, r, q; write x, r -> 24 B
+#   tensor-core forward transform (rhat = S r): read r, write rhat -> 8 B
 #   mode solves: read rhat, write yhat -> 8 B, + IP (4 B / M)
 #   inverse transform (z = S yhat, (r, z)): read yhat, r; write z -> 12 B
-#   FP64 outer residual (r = phi - A x): read x, phi (FP64); write r (FP32) -> 20 B, + 24 B / M
+#   true residual (r = phi - A x, x and phi as FP32 pairs): read x, phi (16 B); write r (4 B) -> 20 B,
+#     + coefficients and their low parts 24 B / M
 ALG_BYTES = {"stencil": (16.0, 12.0), "dst_forward": (28.0, 0.0), "mode_solve": (8.0, 4.0),
-             "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0)}
+             "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0), "pcg_update": (24.0, 0.0)}
+ALG_BYTES_TC = dict(ALG_BYTES, dst_forward=(8.0, 0.0))
+# Tensor-core transform: multiply-adds per row = products x n^2 / 2 (even / odd
+# halves), 2 flops each.
+TC_CLASSES = ("dst_forward", "dst_inverse")
 
 
 # Source files whose change invalidates an ncu traffic figure of a kernel class.
-KERNEL_SOURCES = {"stencil": ["ax_stencil.cu"], "dst_forward": ["ax_dst_impl.cuh", "ax_dst_f32.cu"],
-                  "dst_inverse": ["ax_dst_impl.cuh", "ax_dst_f32.cu"], "mode_solve": ["ax_tridiag.cu"],
-                  "outer_residual": ["ax_stencil.cu"]}
+KERNEL_SOURCES = {"stencil": ["ax_stencil.cu"],
+                  "dst_forward": ["ax_dst_impl.cuh", "ax_dst_f32.cu", "ax_dst_gemm.cu"],
+                  "dst_inverse": ["ax_dst_impl.cuh", "ax_dst_f32.cu", "ax_dst_gemm.cu"],
+                  "mode_solve": ["ax_tridiag.cu"], "outer_residual": ["ax_stencil.cu"],
+                  "pcg_update": ["ax_solver.cu"]}
 
 
 def source_hash(kernel: str) -> str:
@@ -514,12 +523,17 @@ def main():
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # the transform runs inside a seconds-long solve: the sustained tensor figure
+    tc_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    tc_path = prof.get("pcg_update", {}).get("launches", 0) > 0  # the tensor-core transform is in use
+    products = 2 if args.dst_tensor == 2 else 3
+    alg = ALG_BYTES_TC if tc_path else ALG_BYTES
     roof = None
-    cand = {k: v for k, v in prof.items() if k in ALG_BYTES and v["launches"] > 0}
+    cand = {k: v for k, v in prof.items() if k in alg and v["launches"] > 0}
     if cand:
         top = max(cand, key=lambda k: cand[k]["ms"])
         p = cand[top]
-        per_u, per_m = ALG_BYTES[top]
+        per_u, per_m = alg[top]
         units_per_launch = p["units"] / p["launches"]
         rhs_per_launch = units_per_launch / (nr * nz)
         bytes_per_launch = units_per_launch * per_u + (nr * nz) * per_m
@@ -531,6 +545,14 @@ def main():
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1e3,
                 "rhs_per_launch": rhs_per_launch}
+        if tc_path and top in TC_CLASSES:
+            # the GEMM's binding resource is whichever of the two limits is longer
+            flops = (units_per_launch / nz) * products * float(nz) * nz
+            if flops / (tc_peak * 1e12) > bytes_per_launch / (hbm_peak * 1e9):
+                tflops = flops / avg_s / 1e12
+                roof.update({"bound": "tensor", "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s",
+                             "frac": tflops / tc_peak, "flops_per_launch": flops,
+                             "peak_source": "measured" if "bf16_tflops_sustained" in peaks else "fallback"})
     kernel_ms = {k: {"ms": round(v["ms"], 3), "launches": int(v["launches"])} for k, v in prof.items()}
 
     cpu = None

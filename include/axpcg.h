@@ -284,11 +284,13 @@ int64_t ax_kernel_launches(void);
 /* Per-launch profiler.  ax_set_option(op, "profile", 1) turns it on (and
  * clears it); while it is on, solves launch iterations one by one (no graph)
  * and bracket each kernel with CUDA events on the solve's stream.  kind:
- * 0 stencil (p update + A p), 1 forward sine transform (fused x, r update),
- * 2 mode solves, 3 inverse sine transform (fused (r, z)), 4 scalar kernels,
- * 5 FP64 outer residual, 6 other.  Returns the summed event time in ms, the
- * number of launches and the grid unknowns they processed (right-hand sides
- * active at launch x nr x nz). */
+ * 0 stencil (p update + A p), 1 forward sine transform (the FFT form fuses
+ * the x, r update), 2 mode solves, 3 inverse sine transform (fused (r, z)),
+ * 4 scalar kernels, 5 true residual of the mixed method (double-float) or FP64
+ * outer residual, 6 x, r update pass ahead of the tensor-core transform,
+ * 7 other.  Returns the summed event time in ms, the number of launches and
+ * the grid unknowns they processed (right-hand sides active at launch x nr x
+ * nz). */
 int ax_profile_read(ax_operator *op, int32_t kind, double *ms, double *launches, double *units);
 
 /* Human-readable name of a status code (static storage). */

@@ -51,7 +51,7 @@ EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_
             "ax_guessnet_set_loss", "ax_guessnet_features_pre")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
-                 "outer_residual": 5, "other": 6}
+                 "outer_residual": 5, "pcg_update": 6, "other": 7}
 
 
 class AxGrid(ctypes.Structure):

@@ -127,7 +127,7 @@ cudaError_t ensure_smem_attr(const void *func, size_t bytes);
 
 // Kernel classes of the per-launch profiler (ax_profile_read).
 enum { kProfStencil = 0, kProfDstFwd = 1, kProfTridiag = 2, kProfDstInv = 3, kProfScalar = 4,
-       kProfOuter = 5, kProfOther = 6, kProfKinds = 7 };
+       kProfOuter = 5, kProfUpdate = 6, kProfOther = 7, kProfKinds = 8 };
 
 }  // namespace ax
 

@@ -360,15 +360,12 @@ __global__ void add_correction(double *__restrict__ x, const float *__restrict__
     x[b + e] += (double)d[b + e];
 }
 
-// Task t of a right-hand side: 8 consecutive columns of one row, in blocks of
-// 128 rows x 64 natural columns (8 rows of one column chunk, then 8 chunks,
-// then row groups, then blocks), so that a warp reads 8 rows x 128 bytes and
-// writes compact runs of each split half.
-__device__ __forceinline__ void split_task(int t, int ctiles, int &row, int &col) {
-  const int tile = t >> 10, w = t & 1023;
-  const int mt = tile / ctiles, kb = tile - mt * ctiles;
-  row = mt * 128 + (w >> 6) * 8 + (w & 7);
-  col = kb * 64 + ((w >> 3) & 7) * 8;
+// Task t of a right-hand side: the 8 consecutive columns 8 (t % nch) ..
+// of row t / nch (nch = chunks of 8 columns per row): consecutive threads walk
+// along a row, so every warp reads 1 KB of contiguous row data per field.
+__device__ __forceinline__ void split_task(int t, int nch, int &row, int &col) {
+  row = t / nch;
+  col = (t - row * nch) * 8;
 }
 
 // FP64 field -> double-float pair (hi = fl(x), lo = fl(x - hi)) and back.
@@ -414,7 +411,7 @@ constexpr int kUpdateBlocks = 64;  // CTAs per right-hand side
 __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *__restrict__ r,
                                                   const float *__restrict__ q, const float *__restrict__ pa,
                                                   const float *__restrict__ pb, int nr, int n, int pitch,
-                                                  size_t field, int mtiles, int ctiles, int ktiles, int kbe,
+                                                  size_t field, int mtiles, int ktiles, int kbe,
                                                   unsigned char *__restrict__ split,
                                                   const RhsState *st, int mask, double *__restrict__ partial) {
   __shared__ double red[8];
@@ -422,12 +419,12 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
   if (!rhs_selected(st, mask, m)) return;
   const float alpha = (float)st[m].alpha;
   const float *p = (st[m].iters & 1) ? pa : pb;
-  const int tasks = mtiles * ctiles * 1024;
+  const int nch = (n + 7) >> 3;
+  const int tasks = nr * nch;
   float acc = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
     int row, col;
-    split_task(t, ctiles, row, col);
-    if (row >= nr || col >= n) continue;  // col + 8 <= n rounded up to 8 <= pitch
+    split_task(t, nch, row, col);  // row < nr, col < n, col + 8 <= n rounded up to 8 <= pitch
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
     float xv[8], pv[8], rv[8], qv[8];
     *reinterpret_cast<float4 *>(xv) = *reinterpret_cast<const float4 *>(x + e);
@@ -456,16 +453,16 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
 
 // The rows of a field written split into BF16 halves (tensor-core transform input).
 __global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int n, int pitch,
-                                                   size_t field, int mtiles, int ctiles, int ktiles, int kbe,
+                                                   size_t field, int mtiles, int ktiles, int kbe,
                                                    unsigned char *__restrict__ split,
                                                    const RhsState *st, int mask) {
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
-  const int tasks = mtiles * ctiles * 1024;
+  const int nch = (n + 7) >> 3;
+  const int tasks = nr * nch;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tasks; t += gridDim.x * blockDim.x) {
     int row, col;
-    split_task(t, ctiles, row, col);
-    if (row >= nr || col >= n) continue;  // col + 8 <= n rounded up to 8 <= pitch
+    split_task(t, nch, row, col);  // row < nr, col < n, col + 8 <= n rounded up to 8 <= pitch
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
     float v[8];
     *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(in + e);
@@ -1013,7 +1010,6 @@ bool use_tc(const ax_operator *op) {
 // Geometry of the split operand for `rows` rows per RHS.
 struct SplitGeom {
   int mtiles, ktiles, kbe;
-  int ctiles;  // tiles of 64 natural columns (the writers' task range)
   size_t bytes_per_rhs;
 };
 SplitGeom split_geom(const ax_operator *op, int rows) {
@@ -1021,7 +1017,6 @@ SplitGeom split_geom(const ax_operator *op, int rows) {
   g.mtiles = dst_gemm_mtiles(rows);
   g.ktiles = dst_gemm_ktiles(op->nz);
   g.kbe = dst_gemm_kbe(op->nz);
-  g.ctiles = (op->nz + 63) / 64;
   g.bytes_per_rhs = (size_t)g.mtiles * g.ktiles * kSplitTileBytes;
   return g;
 }
@@ -1059,7 +1054,7 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
   const SplitGeom g = split_geom(op, rows);
   note_launch();
   split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->nz, op->pitch, (size_t)rows * op->pitch,
-                                                      g.mtiles, g.ctiles, g.ktiles, g.kbe, split, st, mask);
+                                                      g.mtiles, g.ktiles, g.kbe, split, st, mask);
 }
 
 // Mode solves z -> split operand (the tile kernel writes it directly; otherwise
@@ -1150,13 +1145,13 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       const SplitGeom g = split_geom(op, op->nr);
       unsigned char *sp = w->split;
       {
-        ProfScope ps(w, kProfDstFwd, units, s);
+        ProfScope ps(w, kProfUpdate, units, s);
         note_launch();
         pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(v.x, v.r, v.q, v.pa, v.pb, op->nr, op->nz, op->pitch,
-                                                          field_elems(op), g.mtiles, g.ctiles, g.ktiles, g.kbe, sp,
+                                                          field_elems(op), g.mtiles, g.ktiles, g.kbe, sp,
                                                           st, kActive, prr);
-        tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s);
       }
+      { ProfScope ps(w, kProfDstFwd, units, s); tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s); }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
         note_launch();

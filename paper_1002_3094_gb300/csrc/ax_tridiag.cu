@@ -181,15 +181,11 @@ __global__ void __launch_bounds__(1024) tridiag_kernel(const TriArgs<T> a, int W
   }
 }
 
-// Tiled variant (FP32, nr <= 32 C): a CTA stages an nr x CW column tile of
-// IP, of the couplings E and of the data of MR right-hand sides in shared
-// memory with coalesced row loads.  Each warp then owns one (column,
-// right-hand side) system: lane c holds rows c C .. c C + C - 1 in registers,
-// and the affine carry maps of the 32 chunks are composed with warp shuffles
-// (no CTA-wide barrier inside the solve).  The shared layouts are padded by
-// one word per chunk, idx(row, col) = row CW + col + row / C, so that the 32
-// lanes of a warp (rows c C + t, one column) fall in 32 distinct banks: the
-// bank is ((8 C + 1) c + 8 t + col) mod 32 for CW = 8, and 8 C + 1 is odd.
+// Tiles of the register kernel below: a CTA stages an nr x kTileCW column tile
+// in shared memory; idx(row, col) = row kTileCW + col + row / C is padded by
+// one word per chunk of C rows, so the lanes of a warp (rows c C + t of one
+// column, c = lane) fall in distinct banks: the bank is ((8 C + 1) c + 8 t +
+// col) mod 32 for kTileCW = 8, and 8 C + 1 is odd.
 constexpr int kTileCW = 8;   // columns per CTA (one 32-byte sector per row)
 
 __device__ __forceinline__ int tidx(int row, int col, int C) { return row * kTileCW + col + row / C; }
@@ -202,177 +198,156 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// MR right-hand sides per CTA: 2 when they share one operator (the IP tile is
-// staged once for both), 1 when each has its own factors (batched groups).
-// The tile is padded to NP = 32 C rows with IP = E = 0 (and zero data): a
-// padding row then has alpha = beta = 0 and solves to 0, so every lane runs
-// the same unpredicated recurrences.  EA[row] = E[row - 1] (0 on row 0) and
-// EB[row] = E[row] are stored at row + row / C, so that lane c finds its
-// chunk's couplings at the fixed offsets c (C + 1) + t.
-template <int C, int MR>
-__global__ void __launch_bounds__(32 * kTileCW * MR, 4 / MR) tridiag_tile_kernel(const TriArgs<float> a) {
-  constexpr int NP = 32 * C;
-  constexpr int kTileWords = NP * kTileCW + 32;
-  constexpr int kEWords = NP + 32;
+// Tiled FP32 kernel (nr <= 64 C2, C2 <= 16): a CTA stages an nr x 8 column
+// tile of IP, the couplings E and the data of one right-hand side in shared
+// memory (cp.async, padded to 64 chunks of C2 rows with one word per chunk);
+// one column system per PAIR of warps, lane c of warp h owning rows
+// (32 h + c) C2 .. (32 h + c) C2 + C2 - 1, so a chunk, its alpha_t =
+// -E_{t-1} ip_t and beta_t = -E_t ip_t stay in registers after one pass over
+// the shared tile.  The affine carry maps of the chunks are composed with
+// shuffles inside each warp and through one shared word per pair between the
+// two warps.  Padding rows carry IP = E = 0 and solve to zero, so every lane
+// runs the same unpredicated recurrences.  For the tensor-core transform the
+// result is written in the BF16 split layout.
+template <int C2>
+__global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float> a) {
+  constexpr int NP = 64 * C2;
+  constexpr int kTileWords = NP * kTileCW + 64;
+  constexpr int kEWords = NP + 64;
   extern __shared__ __align__(16) float tsm[];
+  __shared__ float xfer[kTileCW][2];  // per column: forward total of warp 0, backward total of warp 1
   const int nr = a.nr, pitch = a.pitch;
-  float *ips = tsm;                  // [tile] IP
-  float *ea = ips + kTileWords;      // E[row - 1]
-  float *eb = ea + kEWords;          // E[row]
-  float *ds = eb + kEWords;          // [MR][tile] data
+  float *ips = tsm;
+  float *ea = ips + kTileWords;
+  float *eb = ea + kEWords;
+  float *ds = eb + kEWords;
   const int col0 = blockIdx.x * kTileCW;
-  const int m0 = blockIdx.y * MR;
-  const int mcount = min(MR, a.m - m0);
+  const int m = blockIdx.y;
   const int ncol = min(kTileCW, a.nz - col0);
-  // which of this CTA's right-hand sides are selected (uniform over the CTA)
-  bool sel[MR];
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < MR; ++j) {
-    sel[j] = j < mcount && rhs_selected(a.st, a.mask, m0 + j);
-    any = any || sel[j];
-  }
-  if (!any) return;
-  // ---- stage the tiles (coalesced: 8 consecutive threads read one row) ----
+  if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
+  // ---- stage the tiles (coalesced rows, cp.async) ----
   const int cw = threadIdx.x % kTileCW;
   {
     const bool colok = cw < ncol;
-    const int cc = colok ? cw : 0;  // a valid source address for the zero-filled lanes
-    const float *ipg = a.IP + (size_t)m0 * a.cstride + col0 + cc;
+    const int cc = colok ? cw : 0;
+    const float *ipg = a.IP + (size_t)m * a.cstride + col0 + cc;
+    const float *ing = a.in + (size_t)m * a.field + col0 + cc;
     for (int row = threadIdx.x / kTileCW; row < NP; row += blockDim.x / kTileCW) {
       const bool ok = colok && row < nr;
       const int rs = ok ? row : 0;
-      const int si = tidx(row, cw, C);
+      const int si = tidx(row, cw, C2);
       cp_async4(ips + si, ipg + (size_t)rs * pitch, ok);
-#pragma unroll
-      for (int j = 0; j < MR; ++j)
-        if (sel[j]) cp_async4(ds + j * kTileWords + si, a.in + (size_t)(m0 + j) * a.field + (size_t)rs * pitch + col0 + cc, ok);
+      cp_async4(ds + si, ing + (size_t)rs * pitch, ok);
     }
-    const float *eg = a.E + (size_t)m0 * a.estride;
+    const float *eg = a.E + (size_t)m * a.estride;
     for (int row = threadIdx.x; row < NP; row += blockDim.x) {
-      const int ei = row + row / C;
+      const int ei = row + row / C2;
       cp_async4(ea + ei, eg + (row > 0 && row - 1 < nr ? row - 1 : 0), row > 0 && row - 1 < nr);
       cp_async4(eb + ei, eg + (row < nr ? row : 0), row < nr);
     }
     cp_async_wait_all();
   }
   __syncthreads();
-  // ---- one system per warp ----
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = warp % kTileCW, j = warp / kTileCW;
-  if (sel[j] && w < ncol) {
-    // lane c: rows c C + t, tile offset c (8 C + 1) + w + 8 t
-    float *pd = ds + j * kTileWords + lane * (kTileCW * C + 1) + w;
-    const float *pip = ips + lane * (kTileCW * C + 1) + w;
-    const float *pea = ea + lane * (C + 1);
-    const float *peb = eb + lane * (C + 1);
-    // The chunk's values live in registers for C <= 16; 32-row chunks work in
-    // the shared tile itself (32 more registers would spill).
-    constexpr bool kRegs = C <= 16;
-    float v[kRegs ? C : 1];
-    if constexpr (kRegs) {
+  const int w = warp >> 1, h = warp & 1;  // column, half of the r-range
+  const int ci = h * 32 + lane;           // chunk index 0 .. 63
+  const bool active = w < ncol;
+  float *pd = ds + ci * (kTileCW * C2 + 1) + w;
+  const float *pip = ips + ci * (kTileCW * C2 + 1) + w;
+  const float *pea = ea + ci * (C2 + 1);
+  const float *peb = eb + ci * (C2 + 1);
+  float v[C2], al[C2], be[C2];
+  // forward, zero carry-in (one pass over the shared tile)
+  float g = 0.f, mu = 1.f;
 #pragma unroll
-      for (int t = 0; t < C; ++t) v[t] = pd[kTileCW * t];
-    }
-    auto rd = [&](int t) -> float {
-      if constexpr (kRegs) return v[t];
-      else return pd[kTileCW * t];
-    };
-    auto wr = [&](int t, float x) {
-      if constexpr (kRegs) v[t] = x;
-      else pd[kTileCW * t] = x;
-    };
-    // forward, zero carry-in: g_t = v_t ip_t + alpha_t g_{t-1}, alpha_t = -E_{t-1} ip_t
-    float g = 0.f, mu = 1.f;
+  for (int t = 0; t < C2; ++t) {
+    const float ip = pip[kTileCW * t];
+    al[t] = -pea[t] * ip;
+    be[t] = -peb[t] * ip;
+    g = fmaf(pd[kTileCW * t], ip, al[t] * g);
+    mu *= al[t];
+    v[t] = g;
+  }
+  // inclusive scan of the maps over the 32 chunks of this warp
+  float A = g, M = mu;
 #pragma unroll
-    for (int t = 0; t < C; ++t) {
-      // fences every 8 rows keep the unrolled loads near their use
-      if ((t & 7) == 0) asm volatile("" ::: "memory");
-      const float ip = pip[kTileCW * t];
-      const float al = -pea[t] * ip;
-      g = fmaf(rd(t), ip, al * g);
-      mu *= al;
-      wr(t, g);
-    }
-    float A = g, M = mu;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const float pa = __shfl_up_sync(0xffffffffu, A, off), pm = __shfl_up_sync(0xffffffffu, M, off);
-      if (lane >= off) {
-        A = fmaf(M, pa, A);
-        M *= pm;
-      }
-    }
-    float gin = __shfl_up_sync(0xffffffffu, A, 1);
-    if (lane == 0) gin = 0.f;
-    mu = 1.f;
-#pragma unroll
-    for (int t = 0; t < C; ++t) {
-      if ((t & 7) == 0) asm volatile("" ::: "memory");
-      mu *= -pea[t] * pip[kTileCW * t];
-      wr(t, fmaf(mu, gin, rd(t)));
-    }
-    // backward, zero carry-in: y_t = g_t + beta_t y_{t+1}, beta_t = -E_t ip_t
-    float y = 0.f;
-    mu = 1.f;
-#pragma unroll
-    for (int t = C - 1; t >= 0; --t) {
-      if ((t & 7) == 7) asm volatile("" ::: "memory");
-      const float be = -peb[t] * pip[kTileCW * t];
-      y = fmaf(be, y, rd(t));
-      mu *= be;
-      wr(t, y);
-    }
-    A = y;
-    M = mu;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const float pa = __shfl_down_sync(0xffffffffu, A, off), pm = __shfl_down_sync(0xffffffffu, M, off);
-      if (lane + off < 32) {
-        A = fmaf(M, pa, A);
-        M *= pm;
-      }
-    }
-    float yin = __shfl_down_sync(0xffffffffu, A, 1);
-    if (lane == 31) yin = 0.f;
-    mu = 1.f;
-#pragma unroll
-    for (int t = C - 1; t >= 0; --t) {
-      if ((t & 7) == 7) asm volatile("" ::: "memory");
-      mu *= -peb[t] * pip[kTileCW * t];
-      pd[kTileCW * t] = fmaf(mu, yin, rd(t));
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pa = __shfl_up_sync(0xffffffffu, A, off), pm = __shfl_up_sync(0xffffffffu, M, off);
+    if (lane >= off) {
+      A = fmaf(M, pa, A);
+      M *= pm;
     }
   }
+  float Ae = __shfl_up_sync(0xffffffffu, A, 1), Me = __shfl_up_sync(0xffffffffu, M, 1);
+  if (lane == 0) {
+    Ae = 0.f;
+    Me = 1.f;
+  }
+  if (h == 0 && lane == 31 && active) xfer[w][0] = A;  // carry out of rows 0 .. 32 C2 - 1
   __syncthreads();
-  // ---- write back (coalesced) ----
+  const float gin = (h == 0) ? Ae : fmaf(Me, active ? xfer[w][0] : 0.f, Ae);
+  mu = 1.f;
+#pragma unroll
+  for (int t = 0; t < C2; ++t) {
+    mu *= al[t];
+    v[t] = fmaf(mu, gin, v[t]);
+  }
+  // backward, zero carry-in
+  float y = 0.f;
+  mu = 1.f;
+#pragma unroll
+  for (int t = C2 - 1; t >= 0; --t) {
+    y = fmaf(be[t], y, v[t]);
+    mu *= be[t];
+    v[t] = y;
+  }
+  A = y;
+  M = mu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pa = __shfl_down_sync(0xffffffffu, A, off), pm = __shfl_down_sync(0xffffffffu, M, off);
+    if (lane + off < 32) {
+      A = fmaf(M, pa, A);
+      M *= pm;
+    }
+  }
+  Ae = __shfl_down_sync(0xffffffffu, A, 1);
+  Me = __shfl_down_sync(0xffffffffu, M, 1);
+  if (lane == 31) {
+    Ae = 0.f;
+    Me = 1.f;
+  }
+  if (h == 1 && lane == 0 && active) xfer[w][1] = A;  // carry into row 32 C2 - 1 from above
+  __syncthreads();
+  const float yin = (h == 1) ? Ae : fmaf(Me, active ? xfer[w][1] : 0.f, Ae);
+  mu = 1.f;
+#pragma unroll
+  for (int t = C2 - 1; t >= 0; --t) {
+    mu *= be[t];
+    v[t] = fmaf(mu, yin, v[t]);
+  }
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < C2; ++t) pd[kTileCW * t] = v[t];
+  }
+  __syncthreads();
+  // ---- write back (coalesced), as in the shared-memory kernel ----
   if (a.split != nullptr) {
-    // the 8 columns of a row (8 consecutive lanes) become, for the even and
-    // for the odd columns, 8 bytes of BF16 high parts and 8 of low parts:
-    // every lane splits its value, lanes 0, 1, 4, 5 pair theirs with lane + 2
-    // (the next column of the same parity) and store 4 bytes of each
     for (int base = 0; base < nr; base += blockDim.x / kTileCW) {
       const int row = base + threadIdx.x / kTileCW;
-#pragma unroll
-      for (int j = 0; j < MR; ++j) {
-        if (!sel[j]) continue;
-        const float v = (row < nr) ? ds[j * kTileWords + tidx(row, cw, C)] : 0.f;
-        const float hi = bf16_round(v), lo = v - hi;
-        const float hi2 = __shfl_down_sync(0xffffffffu, hi, 2), lo2 = __shfl_down_sync(0xffffffffu, lo, 2);
-        if ((cw & 2) == 0 && row < nr) {
-          unsigned char *t = a.split + split_byte(m0 + j, row, split_pos(col0 + cw, a.split_kbe), a.split_mtiles,
-                                                  a.split_ktiles);
-          *reinterpret_cast<unsigned *>(t) = bf16_pack2(hi, hi2);
-          *reinterpret_cast<unsigned *>(t + kSplitTileBytes / 2) = bf16_pack2(lo, lo2);
-        }
+      const float vv = (row < nr) ? ds[tidx(row, cw, C2)] : 0.f;
+      const float hi = bf16_round(vv), lo = vv - hi;
+      const float hi2 = __shfl_down_sync(0xffffffffu, hi, 2), lo2 = __shfl_down_sync(0xffffffffu, lo, 2);
+      if ((cw & 2) == 0 && row < nr) {
+        unsigned char *t = a.split + split_byte(m, row, split_pos(col0 + cw, a.split_kbe), a.split_mtiles,
+                                                a.split_ktiles);
+        *reinterpret_cast<unsigned *>(t) = bf16_pack2(hi, hi2);
+        *reinterpret_cast<unsigned *>(t + kSplitTileBytes / 2) = bf16_pack2(lo, lo2);
       }
     }
   } else if (cw < ncol) {
-    for (int row = threadIdx.x / kTileCW; row < nr; row += blockDim.x / kTileCW) {
-      const int si = tidx(row, cw, C);
-#pragma unroll
-      for (int j = 0; j < MR; ++j)
-        if (sel[j]) a.out[(size_t)(m0 + j) * a.field + (size_t)row * pitch + col0 + cw] = ds[j * kTileWords + si];
-    }
+    for (int row = threadIdx.x / kTileCW; row < nr; row += blockDim.x / kTileCW)
+      a.out[(size_t)m * a.field + (size_t)row * pitch + col0 + cw] = ds[tidx(row, cw, C2)];
   }
 }
 
@@ -400,29 +375,21 @@ void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
   tridiag_kernel<T, C><<<grid, W * P, smem, s>>>(a, W, P);
 }
 
-template <int C, int MR>
-void launch_tridiag_tile_cm(const TriArgs<float> &a, cudaStream_t s) {
-  // mirrors the kernel's layout: (1 + MR) padded tiles and the two E arrays
-  const size_t smem = sizeof(float) * ((1 + MR) * (32 * C * kTileCW + 32) + 2 * (32 * C + 32));
-  ensure_smem_attr((const void *)tridiag_tile_kernel<C, MR>, smem);
-  dim3 grid((a.nz + kTileCW - 1) / kTileCW, (a.m + MR - 1) / MR);
-  tridiag_tile_kernel<C, MR><<<grid, 32 * kTileCW * MR, smem, s>>>(a);
+template <int C2>
+void launch_tridiag_reg(const TriArgs<float> &a, cudaStream_t s) {
+  // mirrors the kernel's layout: the IP and data tiles and the two E arrays
+  const size_t smem = sizeof(float) * (2 * (64 * C2 * kTileCW + 64) + 2 * (64 * C2 + 64));
+  ensure_smem_attr((const void *)tridiag_reg_kernel<C2>, smem);
+  dim3 grid((a.nz + kTileCW - 1) / kTileCW, a.m);
+  tridiag_reg_kernel<C2><<<grid, 64 * kTileCW, smem, s>>>(a);
 }
 
-template <int C>
-void launch_tridiag_tile_c(const TriArgs<float> &a, cudaStream_t s) {
-  if (a.cstride == 0 && a.estride == 0) launch_tridiag_tile_cm<C, 2>(a, s);
-  else launch_tridiag_tile_cm<C, 1>(a, s);
-}
-
-// FP32 systems of up to 1024 rows use the tiled kernel (chunks of at most 32
-// rows per lane, held in registers); the CTA-chunk kernel takes the rest.
 bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
-  const int cneed = (a.nr + 31) / 32;
-  if (cneed <= 4) launch_tridiag_tile_c<4>(a, s);
-  else if (cneed <= 8) launch_tridiag_tile_c<8>(a, s);
-  else if (cneed <= 16) launch_tridiag_tile_c<16>(a, s);
-  else if (cneed <= 32) launch_tridiag_tile_c<32>(a, s);
+  // two warps per column system, chunks of up to 16 rows in registers
+  const int c2 = (a.nr + 63) / 64;
+  if (c2 <= 4) launch_tridiag_reg<4>(a, s);
+  else if (c2 <= 8) launch_tridiag_reg<8>(a, s);
+  else if (c2 <= 16) launch_tridiag_reg<16>(a, s);
   else return false;
   return true;
 }
