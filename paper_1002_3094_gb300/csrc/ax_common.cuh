@@ -56,6 +56,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 __device__ __forceinline__ bool rhs_selected(const RhsState *st, int mask, int m) {
+  if (mask == kDue) return st[m].state == kActive && st[m].due != 0;
   return mask < 0 || st[m].state == mask;
 }
 

@@ -99,13 +99,18 @@ struct RhsState {
   double tmp;
   double gate_phi; // (phi, B^-1 phi): preconditioned norm^2 of the zero-start residual
   double gate_res; // (r0, B^-1 r0) of the residual of a supplied initial guess
+  double rho_prev; // rho before the last direction update (residual replacement)
   int state;       // kActive / kCheck / kDone / kFailed
   int iters;
   int status;      // AX_* status
   int max_iter;
+  int due;         // mixed PCG: residual replacement due at the end of this iteration
+  int pad_;
 };
 
 enum { kActive = 0, kCheck = 1, kDone = 2, kFailed = 3, kIdle = 4 };
+// Selection mask of the replacement step: active right-hand sides marked due.
+constexpr int kDue = 8;
 
 // Launch geometry shared by producers and consumers of per-CTA partial sums.
 constexpr int kStencilRows = 16;     // rows per stencil CTA

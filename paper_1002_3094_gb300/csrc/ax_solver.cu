@@ -497,6 +497,7 @@ __global__ void sc_start(RhsState *st, const double *prr, int nbr, const double 
     s.beta = 0.0;
     s.cheb_a = 2.0;
     s.status = AX_OK;
+    s.due = 0;
     if (!isfinite(rr) || !isfinite(bb)) {
       s.state = kFailed;
       s.status = AX_ERR_BREAKDOWN;
@@ -536,6 +537,9 @@ __global__ void sc_alpha(RhsState *st, const double *p, int nb) {
 }
 
 // After x, r update: count the iteration and test the recursive residual.
+// on_converge == kDue: a right-hand side that passes its threshold stays
+// active for the rest of the iteration and is marked due for the replacement
+// step at its end (mixed PCG).
 __global__ void sc_after_update(RhsState *st, const double *p, int nb, int on_converge) {
   const int m = blockIdx.x;
   if (st[m].state != kActive) return;
@@ -548,7 +552,8 @@ __global__ void sc_after_update(RhsState *st, const double *p, int nb, int on_co
       s.state = kFailed;
       s.status = AX_ERR_BREAKDOWN;
     } else if (rr <= s.thresh2) {
-      s.state = on_converge;
+      if (on_converge == kDue) s.due = 1;
+      else s.state = on_converge;
     } else if (s.iters >= s.max_iter) {
       s.state = (on_converge == kDone) ? kDone : kFailed;
       if (on_converge != kDone) s.status = AX_ERR_NO_CONVERGENCE;
@@ -557,16 +562,20 @@ __global__ void sc_after_update(RhsState *st, const double *p, int nb, int on_co
   }
 }
 
-__global__ void sc_beta(RhsState *st, const double *p, int nb, int mask, int next_state) {
+// use_prev: the right-hand side already took this iteration's direction
+// update from its recursive residual; the new beta refers to the rho before
+// that update (mixed PCG residual replacement).
+__global__ void sc_beta(RhsState *st, const double *p, int nb, int mask, int next_state, int use_prev = 0) {
   const int m = blockIdx.x;
   if (st[m].state != mask) return;
   const double rz = reduce_part(p + (size_t)m * kPartialStride, nb);
   if (threadIdx.x == 0) {
-    const double rho = st[m].rho;
+    const double rho = use_prev ? st[m].rho_prev : st[m].rho;
     if (!isfinite(rz) || rho == 0.0) {
       st[m].state = kFailed;
       st[m].status = AX_ERR_BREAKDOWN;
     } else {
+      if (!use_prev) st[m].rho_prev = rho;
       st[m].beta = rz / rho;
       st[m].rho = rz;
       st[m].state = next_state;
@@ -653,11 +662,17 @@ __global__ void sc_mixed_start(RhsState *st, const double *prr, int nbr, const d
 // then recomputes z = B^-1 r and resumes with sc_beta).
 __global__ void sc_mixed_replace(RhsState *st, const double *prr, int nbr, double tol2, double delta2) {
   const int m = blockIdx.x;
-  if (st[m].state != kCheck) return;
+  if (!rhs_selected(st, kDue, m)) return;
   const double rr = reduce_part(prr + (size_t)m * kPartialStride, nbr);
   if (threadIdx.x == 0) {
     RhsState s = st[m];
+    // the iteration's z and rho came from the recursive residual: when the
+    // true one differs noticeably (||r||^2 by more than 1%: typically once the
+    // recursion has run below the FP32 accuracy of x), the right-hand side goes
+    // to kCheck for z = B^-1 r and beta from the new (r, z)
+    const bool consistent = fabs(rr - s.rr) <= 1e-2 * rr;
     s.rr = rr;
+    s.due = 0;
     s.tmp += 1.0;  // replacements
     if (!isfinite(rr)) {
       s.state = kFailed;
@@ -669,6 +684,7 @@ __global__ void sc_mixed_replace(RhsState *st, const double *prr, int nbr, doubl
       s.status = AX_ERR_NO_CONVERGENCE;
     } else {
       s.thresh2 = fmax(delta2 * rr, 0.25 * tol2 * s.bb);
+      if (!consistent) s.state = kCheck;
     }
     st[m] = s;
   }
@@ -1415,12 +1431,13 @@ int gate_guess(ax_operator *op, int m, RhsState *st, const T *phiT, const T *r0T
   return AX_OK;
 }
 
-// Mixed precision PCG with FP64 residual replacement.  The iteration runs in
-// FP32 (x32 holds the correction accumulated since the last replacement); when
-// a right-hand side's recursive residual passes its threshold it goes to
-// kCheck, x64 += x32, the FP64 true residual phi - A x64 replaces r (rounded
-// to FP32), and the iteration resumes with the same search direction (beta
-// from the new (r, z)).  It stops when the FP64 true residual meets tol.
+// Mixed precision PCG with residual replacement.  The iteration runs in FP32
+// (x32 holds the correction accumulated since the last replacement); the
+// iterate lives in double-float (xh + xl).  When a right-hand side's recursive
+// residual passes its threshold it finishes the iteration (z and beta from the
+// recursive residual), then x += x32 and the true residual phi - A x
+// (double-float) replaces r; the next iteration continues from it with the
+// same search direction.  It stops when the true residual meets tol.
 int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_iter, bool check_guess,
                    std::vector<int> &accepted, cudaStream_t s) {
   Workspace *w = op->ws;
@@ -1466,18 +1483,22 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   };
   note_launch();
   to_df<<<cblocks, 256, 0, s>>>(w->phi64, w->phh, w->phl, nall);
-  // Residual replacement of the right-hand sides in kCheck (every kernel
-  // returns at once for the others, so this runs after every iteration inside
-  // the captured graph and no right-hand side waits for the host).
+  // Residual replacement, inside the captured graph after every iteration: the
+  // right-hand sides marked due went through the whole iteration (z and beta
+  // from their recursive residual); x32 is folded into the double-float x and
+  // r is replaced by the true residual, which the next iteration's update
+  // continues from.  Where the true residual differs from the recursive one
+  // (kCheck), z and beta are recomputed from it.  Every kernel returns at once
+  // for the others; no right-hand side waits for the host.
   auto replace_step = [&](cudaStream_t ss) {
     note_launch();
-    fold_df<<<zg, 256, 0, ss>>>(w->xh, w->xl, w->x32, field, st, kCheck);
-    residual64(kCheck, ss);
+    fold_df<<<zg, 256, 0, ss>>>(w->xh, w->xl, w->x32, field, st, kDue);
+    residual64(kDue, ss);
     note_launch();
     sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbdf, tol * tol, delta * delta);
     precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss, v.q);
     note_launch();
-    sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive);
+    sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive, 1);
   };
   start();
   if (check_guess) {
@@ -1502,13 +1523,13 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     RhsState *h = w->h_st;
     if (w->profile) {
       if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
-      pcg_iteration<float>(op, m, v, st, w, kCheck, s, per_rhs * count_state(h, m, kActive));
+      pcg_iteration<float>(op, m, v, st, w, kDue, s, per_rhs * count_state(h, m, kActive));
       replace_step(s);
       AX_CHECK_LAUNCH();
     } else {
       rc = run_graph(w, w->g32, key, s, [&](cudaStream_t cs) {
         for (int k = 0; k < K; ++k) {
-          pcg_iteration<float>(op, m, v, st, w, kCheck, cs);
+          pcg_iteration<float>(op, m, v, st, w, kDue, cs);
           replace_step(cs);
         }
       });

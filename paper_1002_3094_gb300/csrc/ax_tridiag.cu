@@ -331,23 +331,26 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
     for (int t = 0; t < C2; ++t) pd[kTileCW * t] = v[t];
   }
   __syncthreads();
-  // ---- write back (coalesced), as in the shared-memory kernel ----
-  if (a.split != nullptr) {
-    for (int base = 0; base < nr; base += blockDim.x / kTileCW) {
-      const int row = base + threadIdx.x / kTileCW;
-      const float vv = (row < nr) ? ds[tidx(row, cw, C2)] : 0.f;
-      const float hi = bf16_round(vv), lo = vv - hi;
-      const float hi2 = __shfl_down_sync(0xffffffffu, hi, 2), lo2 = __shfl_down_sync(0xffffffffu, lo, 2);
-      if ((cw & 2) == 0 && row < nr) {
-        unsigned char *t = a.split + split_byte(m, row, split_pos(col0 + cw, a.split_kbe), a.split_mtiles,
-                                                a.split_ktiles);
-        *reinterpret_cast<unsigned *>(t) = bf16_pack2(hi, hi2);
-        *reinterpret_cast<unsigned *>(t + kSplitTileBytes / 2) = bf16_pack2(lo, lo2);
+  // ---- write back: one thread per row, its 8 columns at once ----
+  // (8 shared loads with a 4-way bank conflict, but every lane does useful
+  // work; rows go to 32-byte segments of the output, or to the even and odd
+  // halves of the split layout)
+  for (int row = threadIdx.x; row < nr; row += blockDim.x) {
+    float x[8];
+    const int r0 = row * kTileCW + row / C2;
+#pragma unroll
+    for (int c = 0; c < kTileCW; ++c) x[c] = ds[r0 + c];
+    if (a.split != nullptr) {
+      split_store8(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+    } else {
+      float *o = a.out + (size_t)m * a.field + (size_t)row * pitch + col0;
+      if (ncol == kTileCW) {
+        *reinterpret_cast<float4 *>(o) = make_float4(x[0], x[1], x[2], x[3]);
+        *reinterpret_cast<float4 *>(o + 4) = make_float4(x[4], x[5], x[6], x[7]);
+      } else {
+        for (int c = 0; c < ncol; ++c) o[c] = x[c];
       }
     }
-  } else if (cw < ncol) {
-    for (int row = threadIdx.x / kTileCW; row < nr; row += blockDim.x / kTileCW)
-      a.out[(size_t)m * a.field + (size_t)row * pitch + col0 + cw] = ds[tidx(row, cw, C2)];
   }
 }
 

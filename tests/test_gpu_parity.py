@@ -369,3 +369,21 @@ def test_guess_gate_rejects_bad_and_keeps_good_guesses(cuda, method):
     for j in range(2):
         assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-9
     pr.close()
+
+
+def test_mixed_iterations_track_fp64_on_fast_instances(cuda):
+    """Fast-converging instances of the uneven-size workload: the mixed
+    method's residual replacement (true residual swapped in at the end of an
+    iteration, z and beta recomputed only where it differs from the recursive
+    one) must not stall CG once the recursion runs below the FP32 accuracy of
+    the iterate: iterations within 1.5x + 8 of the FP64 method's."""
+    insts = batched_instances(16, sizes=(63, 127))
+    for nr, nz, med in insts:
+        pr = Pair(med, nr, nz, cuda)
+        f = sample_rhs(med, nr, nz)[:1]
+        st64, i64, _ = _solve(pr, f, P.AX_PCG_FP64, 1e-8)
+        st, imx, u = _solve(pr, f, P.AX_PCG_MIXED, 1e-8)
+        assert st == P.AX_OK and st64 == P.AX_OK
+        assert imx[0]["iters"] <= 1.5 * i64[0]["iters"] + 8, (nr, nz, imx[0], i64[0])
+        assert _oracle_rel_res(pr, f[0], u[0]) <= 1e-8
+        pr.close()
