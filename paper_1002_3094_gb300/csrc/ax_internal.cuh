@@ -280,6 +280,9 @@ struct TriArgs {
   // halves (layout of ax_common.cuh, tiles mtiles x ktiles) instead of to out
   unsigned char *split;
   int split_mtiles, split_ktiles, split_kbe;
+  // FP32 tile kernel only: if set, per-CTA partials of (in, out) into
+  // partial[m][blockIdx.x] (column groups of 8)
+  double *partial;
 };
 
 template <typename T>

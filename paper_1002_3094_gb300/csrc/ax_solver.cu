@@ -1075,8 +1075,11 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
 
 // Mode solves z -> split operand (the tile kernel writes it directly; otherwise
 // through the FP32 buffer tmp).
+// With `prz` (tile kernel only), the mode solves also form the partials of
+// (rhat, yhat), equal to (r, z) up to the rounding of the split input: S is
+// symmetric, so (r, S yhat) = (S r, yhat).
 void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, unsigned char *split,
-                   const RhsState *st, int mask, cudaStream_t s) {
+                   const RhsState *st, int mask, cudaStream_t s, double *prz = nullptr) {
   const SplitGeom g = split_geom(op, op->nr);
   TriArgs<float> t = tri_args<float>(op, m, z, tmp, st, mask);
   if (tridiag_split_ok(op->nr)) {
@@ -1084,6 +1087,7 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
     t.split_mtiles = g.mtiles;
     t.split_ktiles = g.ktiles;
     t.split_kbe = g.kbe;
+    t.partial = prz;
     launch_tridiag<float>(t, s);
   } else {
     launch_tridiag<float>(t, s);
@@ -1091,10 +1095,15 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
   }
 }
 
+// Where the (r, z) partials of the tensor-core path come from: the mode solves
+// (column groups of 8) when the tile kernel runs, else the inverse transform.
+bool tc_dot_in_modes(const ax_operator *op) { return tridiag_split_ok(op->nr); }
+
 // Number of (r, z) partial slots per RHS that precond_apply writes.
 template <typename T>
 int precond_partials(const ax_operator *op) {
-  if (use_tc<T>(op)) return dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
+  if (use_tc<T>(op))
+    return tc_dot_in_modes(op) ? (op->nz + 7) / 8 : dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
   return dst_blocks(op, op->nr, (int)sizeof(T));
 }
 
@@ -1107,10 +1116,11 @@ void precond_apply(const ax_operator *op, int m, const T *r, T *z, const RhsStat
   if constexpr (sizeof(T) == 4) {
     if (use_tc<T>(op) && tmp != nullptr) {
       unsigned char *sp = op->ws->split;
+      const bool dm = tc_dot_in_modes(op);
       tc_split(op, m, op->nr, r, sp, st, mask, s);
       tc_transform(op, m, op->nr, sp, z, st, mask, nullptr, nullptr, s);
-      tc_mode_solve(op, m, z, tmp, sp, st, mask, s);
-      tc_transform(op, m, op->nr, sp, z, st, mask, r, prz, s);
+      tc_mode_solve(op, m, z, tmp, sp, st, mask, s, dm ? prz : nullptr);
+      tc_transform(op, m, op->nr, sp, z, st, mask, dm ? nullptr : r, dm ? nullptr : prz, s);
       return;
     }
   }
@@ -1173,8 +1183,15 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
         note_launch();
         sc_after_update<<<m, 32, 0, s>>>(st, prr, kUpdateBlocks, on_converge);
       }
-      { ProfScope ps(w, kProfTridiag, units, s); tc_mode_solve(op, m, v.z, v.q, sp, st, kActive, s); }
-      { ProfScope ps(w, kProfDstInv, units, s); tc_transform(op, m, op->nr, sp, v.z, st, kActive, v.r, prz, s); }
+      const bool dm = tc_dot_in_modes(op);
+      {
+        ProfScope ps(w, kProfTridiag, units, s);
+        tc_mode_solve(op, m, v.z, v.q, sp, st, kActive, s, dm ? prz : nullptr);
+      }
+      {
+        ProfScope ps(w, kProfDstInv, units, s);
+        tc_transform(op, m, op->nr, sp, v.z, st, kActive, dm ? nullptr : v.r, dm ? nullptr : prz, s);
+      }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
         note_launch();

@@ -326,9 +326,24 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
     mu *= be[t];
     v[t] = fmaf(mu, yin, v[t]);
   }
+  float dot = 0.f;
   if (active) {
 #pragma unroll
-    for (int t = 0; t < C2; ++t) pd[kTileCW * t] = v[t];
+    for (int t = 0; t < C2; ++t) {
+      dot = fmaf(pd[kTileCW * t], v[t], dot);  // (input, solution) of this chunk
+      pd[kTileCW * t] = v[t];
+    }
+  }
+  if (a.partial != nullptr) {
+    __shared__ double red[16];
+    const double sw = warp_sum((double)dot);
+    if (lane == 0) red[warp] = sw;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+      a.partial[(size_t)m * kPartialStride + blockIdx.x] = tot;
+    }
   }
   __syncthreads();
   // ---- write back: one thread per row, its 8 columns at once ----
