@@ -18,6 +18,8 @@ from .axisym import (  # noqa: F401
     assemble,
     preconditioner_constants,
     dst1_matrix,
+    cosine_pair,
+    z_transforms,
     mode_eigenvalues,
     mode_tridiagonal,
     thomas,

@@ -10,10 +10,19 @@ y[a, b] the value at r-node i = a + 1 and z-node k = b + 1 (z fastest).  The
 flat unknown index is a * nz + b.
 
 Readings of the paper taken here (each also listed in the design doc):
-* z boundary: homogeneous Dirichlet at z = 0 and z = 1 on the vertex grid
-  z_k = k h_z, h_z = 1 / (nz + 1), k = 1..nz, faces zbar_k = (k + 1/2) h_z,
-  k = 0..nz.  (The paper's Section 2.1 uses Neumann in z with a DCT; the
-  Dirichlet variant uses the sine transform instead.)
+* z boundary, bc_z = 0: homogeneous Dirichlet at z = 0 and z = 1 on the
+  vertex grid z_k = k h_z, h_z = 1 / (nz + 1), k = 1..nz, faces
+  zbar_k = (k + 1/2) h_z, k = 0..nz; the sine transform diagonalises the
+  z-part of B.
+* z boundary, bc_z = 1 (the paper's own, Eq. main_eq): zero flux at z = 0 and
+  z = lz.  Cell-centred nodes z_k = (k - 1/2) h_z, h_z = lz / nz, faces
+  zbar_k = k h_z, k = 0..nz, so the two outer faces lie on the boundary and
+  carry no flux: the one-sided rows of Eq. scheme_op_r_z at k = 1 and
+  k = N_2.  The cosine pair of Eq. fft_phi diagonalises the z-part of B.
+  (Section 2.1 prints h_2 = l_2 / (N_2 - 1/2), which puts the last node on
+  z = l_2 and the zero-flux face half a cell outside the domain; the
+  one-sided rows and the cosine basis are the same for either spacing, and
+  h_z = lz / nz keeps the second order at z = lz.)
 * r grid as in Section 2.1: r_i = (i - 1/2) h_r, h_r = 1 / (nr + 1/2),
   i = 1..nr + 1, with y = 0 at r_{nr+1} = 1; faces rbar_i = i h_r, i = 0..nr.
 * Sign: the operator is the paper's Eq. poisson_diff_2 multiplied by -1, so
@@ -38,6 +47,7 @@ class Grid:
     nz: int
     lr: float = 1.0
     lz: float = 1.0
+    bc_z: int = 0  # 0: u = 0 at z = 0, lz; 1: zero flux there (Eq. main_eq)
 
     @property
     def hr(self) -> float:
@@ -45,7 +55,7 @@ class Grid:
 
     @property
     def hz(self) -> float:
-        return self.lz / (self.nz + 1.0)
+        return self.lz / (self.nz + 1.0) if self.bc_z == 0 else self.lz / self.nz
 
     @property
     def r(self) -> np.ndarray:
@@ -59,13 +69,15 @@ class Grid:
 
     @property
     def z(self) -> np.ndarray:
-        """Nodes z_k = k h_z, k = 1..nz."""
-        return np.arange(1, self.nz + 1) * self.hz
+        """Nodes z_k = k h_z (bc_z = 0) or (k - 1/2) h_z (bc_z = 1), k = 1..nz."""
+        k = np.arange(1, self.nz + 1)
+        return (k if self.bc_z == 0 else k - 0.5) * self.hz
 
     @property
     def zbar(self) -> np.ndarray:
-        """Faces zbar_k = z_k + h_z / 2, k = 0..nz."""
-        return (np.arange(0, self.nz + 1) + 0.5) * self.hz
+        """Faces zbar_k = z_k + h_z / 2, k = 0..nz (z_0 = 0, resp. -h_z / 2)."""
+        c = np.arange(0, self.nz + 1)
+        return (c + 0.5 if self.bc_z == 0 else c) * self.hz
 
 
 def sample_medium(medium, grid: Grid, rhs_index=None):
@@ -92,9 +104,15 @@ def scheme_coefficients(kappa_r, kappa_z, q, grid: Grid):
     """Eq. diff_approx1: a1 = rbar_i kappa(rbar_i, z_k), a2 = r_i kappa(r_i, zbar_k),
     w = r_i q(r_i, z_k).  Returns (KR (nr, nz), KZ (nr, nz+1), W (nr, nz)).
     The face rbar_0 = 0 on the axis carries no flux (axis condition of
-    Eq. main_eq), so it is not stored."""
+    Eq. main_eq), so it is not stored.  With the zero-flux z boundary
+    (bc_z = 1) the faces zbar_0 = 0 and zbar_nz = lz carry no flux either (the
+    one-sided rows of Eq. scheme_op_r_z at k = 1 and k = N_2): their KZ is 0."""
     KR = grid.rbar[1:, None] * kappa_r
     KZ = grid.r[:, None] * kappa_z
+    if grid.bc_z == 1:
+        KZ = KZ.copy()
+        KZ[:, 0] = 0.0
+        KZ[:, -1] = 0.0
     W = grid.r[:, None] * q
     return KR, KZ, W
 
@@ -116,7 +134,8 @@ def assemble(KR, KZ, W, grid: Grid) -> sp.csr_matrix:
                   + W_{i,k} y_{i,k}
 
     with KR_0 = 0 (one-sided axis row of Eq. scheme_op_r_z), y_{nr+1,k} = 0
-    (exact Dirichlet at r = l1, Section 2.1) and y_{i,0} = y_{i,nz+1} = 0."""
+    (exact Dirichlet at r = l1, Section 2.1) and y_{i,0} = y_{i,nz+1} = 0
+    (for bc_z = 1 the boundary faces have KZ = 0, so those values drop out)."""
     nr, nz = grid.nr, grid.nz
     hr2, hz2 = grid.hr ** 2, grid.hz ** 2
     n = nr * nz
@@ -160,7 +179,7 @@ def assemble_preconditioner(kappa_t: float, q_t: float, grid: Grid) -> sp.csr_ma
     nr, nz = grid.nr, grid.nz
     KR, KZ, W = scheme_coefficients(np.full((nr, nz), kappa_t), np.full((nr, nz + 1), kappa_t),
                                     np.full((nr, nz), q_t), grid)
-    return assemble(KR, KZ, W, grid)
+    return assemble(KR, KZ, W, grid)  # bc_z = 1: boundary faces zeroed there too
 
 
 def dst1_matrix(n: int) -> np.ndarray:
@@ -174,11 +193,30 @@ def dst1_matrix(n: int) -> np.ndarray:
     return math.sqrt(2.0 / (n + 1)) * np.sin(np.pi * kl / (n + 1))
 
 
-def mode_eigenvalues(nz: int, hz: float) -> np.ndarray:
-    """lambda_l = (4 / h_z^2) sin^2(pi l / (2 (nz + 1))), l = 1..nz: the
-    eigenvalues of (2 y_k - y_{k-1} - y_{k+1}) / h_z^2 with y_0 = y_{nz+1} = 0
-    (the Dirichlet counterpart of the shift in Eq. eq_trid)."""
+def cosine_pair(n: int):
+    """The two cosine sums of Eq. fft_phi for N_2 = n, as matrices acting on
+    the index k (rows of F and G are the modes l = 1..n):
+      forward  phi~(l) = sqrt(2/n) sum_k f_k cos(pi (k - 1/2)(l - 1) / n),
+               F[l-1, k-1] = sqrt(2/n) cos(pi (k - 1/2)(l - 1) / n);
+      inverse  y_k = sqrt(2/n) (y~(1) / 2 + sum_{l>=2} y~(l) cos(...)),
+               G[l-1, k-1] = w_l F[l-1, k-1], w_1 = 1/2, w_l = 1 otherwise."""
+    k = np.arange(1, n + 1) - 0.5
+    l = np.arange(0, n)
+    F = math.sqrt(2.0 / n) * np.cos(np.pi * np.outer(l, k) / n)
+    w = np.ones(n)
+    w[0] = 0.5
+    return F, w[:, None] * F
+
+
+def mode_eigenvalues(nz: int, hz: float, bc_z: int = 0) -> np.ndarray:
+    """bc_z = 0: lambda_l = (4 / h_z^2) sin^2(pi l / (2 (nz + 1))), l = 1..nz,
+    the eigenvalues of (2 y_k - y_{k-1} - y_{k+1}) / h_z^2 with
+    y_0 = y_{nz+1} = 0 (the Dirichlet counterpart of the shift in Eq. eq_trid).
+    bc_z = 1: lambda_l = (4 / h_z^2) sin^2(pi (l - 1) / (2 nz)), l = 1..nz, the
+    shift of Eq. eq_trid (the zero-flux second difference; lambda_1 = 0)."""
     l = np.arange(1, nz + 1)
+    if bc_z == 1:
+        return (4.0 / hz ** 2) * np.sin(np.pi * (l - 1) / (2.0 * nz)) ** 2
     return (4.0 / hz ** 2) * np.sin(np.pi * l / (2.0 * (nz + 1))) ** 2
 
 
@@ -231,18 +269,29 @@ def thomas(sub, diag, sup, b):
     return x
 
 
-def precond_solve(v, kappa_t: float, q_t: float, grid: Grid, S: Optional[np.ndarray] = None):
+def z_transforms(grid: Grid):
+    """(forward, inverse) matrices M with vt = v @ M along z: the sine matrix
+    (its own inverse) for bc_z = 0, the cosine pair of Eq. fft_phi for
+    bc_z = 1."""
+    if grid.bc_z == 1:
+        F, G = cosine_pair(grid.nz)
+        return F.T, G
+    S = dst1_matrix(grid.nz)
+    return S, S
+
+
+def precond_solve(v, kappa_t: float, q_t: float, grid: Grid, S=None):
     """y = B^{-1} v by separation of variables (Section 4.2, Eqs. fft_phi,
-    eq_trid): transform every r-row along z with the orthonormal sine matrix,
-    solve one tridiagonal system along r per z-mode l, transform back.
-    v has shape (nr, nz)."""
-    if S is None:
-        S = dst1_matrix(grid.nz)
-    vt = v @ S  # vt[:, l] = sum_k v[:, k] S[k, l]   (S symmetric)
-    lam = mode_eigenvalues(grid.nz, grid.hz)
+    eq_trid): transform every r-row along z (sine matrix for bc_z = 0, the
+    cosine sums of Eq. fft_phi for bc_z = 1), solve one tridiagonal system
+    along r per z-mode l, transform back.  v has shape (nr, nz); S, if given,
+    is the (forward, inverse) pair of z_transforms."""
+    fwd, inv = z_transforms(grid) if S is None else S
+    vt = v @ fwd  # vt[:, l] = sum_k v[:, k] fwd[k, l]
+    lam = mode_eigenvalues(grid.nz, grid.hz, grid.bc_z)
     sub, diag, sup = mode_tridiagonal(kappa_t, q_t, lam, grid)
     yt = thomas(sub, diag, sup, vt)  # one system per column l
-    return yt @ S
+    return yt @ inv
 
 
 # ---------------------------------------------------------------------------
@@ -366,7 +415,7 @@ class Operator:
         self.KR, self.KZ, self.W = scheme_coefficients(kappa_r, kappa_z, q, grid)
         self.A = assemble(self.KR, self.KZ, self.W, grid)
         self.kappa_t, self.q_t = preconditioner_constants(kappa_r, kappa_z, q)
-        self.S = dst1_matrix(grid.nz)
+        self.S = z_transforms(grid)
         self.gamma = chebyshev_bounds(kappa_r, kappa_z, q, self.kappa_t, self.q_t)
 
     @classmethod

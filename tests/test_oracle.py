@@ -11,7 +11,7 @@ import scipy.linalg
 import scipy.sparse.linalg as spl
 
 import oracle as O
-from workloads import bumps_medium, manufactured_medium, Medium
+from workloads import bumps_medium, manufactured_medium, manufactured_medium_neumann, Medium
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -227,3 +227,125 @@ def test_chebyshev_agrees_with_pcg():
     y2, i2 = op.solve(f[0], tol=1e-11, method="cheb")
     assert i1.converged and i2.converged
     assert np.linalg.norm(y1 - y2) <= 1e-8 * np.linalg.norm(y1)
+
+
+# ---------------------------------------------- zero-flux z boundary (bc_z = 1)
+def _op_n(nr, nz, seed=0, q_zero=False):
+    g = O.Grid(nr, nz, bc_z=1)
+    med = _random_medium(seed)
+    if q_zero:
+        med = Medium("rand0", med.kappa, lambda r, z: np.zeros(np.broadcast(r, z).shape), med.sources)
+    kr, kz, q, f = O.sample_medium(med, g)
+    return O.Operator(kr, kz, q, g), f
+
+
+@pytest.mark.parametrize("nr,nz", [(1, 1), (1, 4), (3, 1), (3, 5), (6, 4), (9, 7)])
+@pytest.mark.parametrize("q_zero", [False, True])
+def test_neumann_operator_symmetric_positive_definite(nr, nz, q_zero):
+    """With zero flux at z = 0, lz and q = 0 the only Dirichlet part is r = 1,
+    which still makes A definite (Eq. main_eq with Eq. elliptic_condition)."""
+    op, _ = _op_n(nr, nz, q_zero=q_zero)
+    A = op.A.toarray()
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+def test_neumann_row_sums_conservative():
+    """Every z-row is interior once the boundary faces carry no flux: (A 1) = W
+    on all rows but the last r-row (a non-zero boundary flux fails this)."""
+    nr, nz = 7, 9
+    op, _ = _op_n(nr, nz, seed=3)
+    s = op.apply_A(np.ones((nr, nz)))
+    np.testing.assert_allclose(s[:-1], op.W[:-1], rtol=1e-12, atol=1e-12)
+
+
+def test_neumann_grid_nodes_and_faces():
+    g = O.Grid(3, 4, lz=2.0, bc_z=1)
+    np.testing.assert_allclose(g.z, [0.25, 0.75, 1.25, 1.75], rtol=1e-15)
+    np.testing.assert_allclose(g.zbar, [0.0, 0.5, 1.0, 1.5, 2.0], rtol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 127])
+def test_cosine_pair_matches_scipy_and_inverts(n):
+    """Eq. fft_phi's sums are scipy's unnormalised DCT-II (forward) and DCT-III
+    (inverse) times sqrt(2/n) / 2; the pair inverts exactly."""
+    F, G = O.cosine_pair(n)
+    I = np.eye(n)
+    np.testing.assert_allclose(F, 0.5 * math.sqrt(2.0 / n) * scipy.fft.dct(I, type=2, axis=0), atol=1e-14)
+    np.testing.assert_allclose(G.T, 0.5 * math.sqrt(2.0 / n) * scipy.fft.dct(I, type=3, axis=0), atol=1e-14)
+    np.testing.assert_allclose(F.T @ G, I, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 33])
+def test_cosine_diagonalises_zero_flux_second_difference(n):
+    """Eq. eq_trid's shift: the rows of F are eigenvectors of the second
+    difference with one-sided end rows, eigenvalues 4/h^2 sin^2(pi(l-1)/(2n))."""
+    h = 1.0 / n
+    L = (2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1))
+    L[0, 0] -= 1.0  # no flux through the face z = 0
+    L[-1, -1] -= 1.0  # nor through z = lz
+    L /= h ** 2
+    F, _ = O.cosine_pair(n)
+    lam = O.mode_eigenvalues(n, h, bc_z=1)
+    assert lam[0] == 0.0
+    np.testing.assert_allclose(L @ F.T, F.T * lam[None, :], atol=1e-9 * n ** 2)
+
+
+@pytest.mark.parametrize("nr,nz", [(1, 1), (2, 3), (5, 2), (8, 8), (13, 6)])
+@pytest.mark.parametrize("qt", [0.35, 0.0])
+def test_neumann_precond_solve_matches_dense_solve_of_B(nr, nz, qt):
+    g = O.Grid(nr, nz, bc_z=1)
+    kt = 1.7
+    B = O.assemble_preconditioner(kt, qt, g).toarray()
+    v = np.random.default_rng(nr * 31 + nz).normal(size=(nr, nz))
+    ref = np.linalg.solve(B, v.ravel()).reshape(nr, nz)
+    np.testing.assert_allclose(O.precond_solve(v, kt, qt, g), ref, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("variable_kappa", [False, True])
+def test_neumann_manufactured_solution_second_order(variable_kappa):
+    """u* = cos(pi r/2) cos(pi z) has zero z-flux at z = 0, 1: the max-norm
+    nodal error must fall about 4x per halving of h (Section 2.1)."""
+    med, u = manufactured_medium_neumann(q0=1.0, variable_kappa=variable_kappa)
+    errs = []
+    for n in (16, 32, 64, 128):
+        g = O.Grid(n, n, bc_z=1)
+        kr, kz, q, f = O.sample_medium(med, g)
+        op = O.Operator(kr, kz, q, g)
+        y = spl.spsolve(op.A.tocsc(), op.phi(f[0]).ravel()).reshape(n, n)
+        errs.append(np.abs(y - u(g.r[:, None], g.z[None, :])).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.5 < x < 5.1 for x in ratios), ratios
+    assert errs[-1] < 1e-3
+
+
+@pytest.mark.parametrize("q0", [0.7, 0.0])
+def test_neumann_pcg_one_iteration_when_coefficients_constant(q0):
+    g = O.Grid(24, 20, bc_z=1)
+    med = Medium("const", lambda r, z: np.full(np.broadcast(r, z).shape, 2.3),
+                 lambda r, z: np.full(np.broadcast(r, z).shape, q0),
+                 [lambda r, z: np.exp(-((r - .3) ** 2 + (z - .6) ** 2) * 20)])
+    kr, kz, q, f = O.sample_medium(med, g)
+    op = O.Operator(kr, kz, q, g)
+    assert (abs(op.A - O.assemble_preconditioner(op.kappa_t, op.q_t, g)).max()) < 1e-10
+    y, info = op.solve(f[0], tol=1e-12)
+    assert info.iters == 1 and info.rel_res <= 1e-12
+
+
+@pytest.mark.parametrize("nr,nz", [(3, 4), (16, 9), (33, 20)])
+def test_neumann_pcg_and_chebyshev_match_direct_solve(nr, nz):
+    op, f = _op_n(nr, nz, seed=nr)
+    ref = spl.spsolve(op.A.tocsc(), op.phi(f[0]).ravel()).reshape(nr, nz)
+    for method in ("pcg", "cheb"):
+        y, info = op.solve(f[0], tol=1e-13, method=method)
+        assert info.converged
+        assert np.linalg.norm(y - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_neumann_chebyshev_bounds_contain_generalised_spectrum():
+    op, _ = _op_n(6, 5, seed=7)
+    A = op.A.toarray()
+    B = O.assemble_preconditioner(op.kappa_t, op.q_t, op.grid).toarray()
+    ev = scipy.linalg.eigh(A, B, eigvals_only=True)
+    g1, g2 = op.gamma
+    assert g1 <= ev.min() * (1 + 1e-12) and ev.max() <= g2 * (1 + 1e-12)

@@ -16,5 +16,6 @@ from .media import (  # noqa: F401
     grf_spec,
     large_medium,
     manufactured_medium,
+    manufactured_medium_neumann,
     WORKLOADS,
 )

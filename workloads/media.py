@@ -321,6 +321,43 @@ def manufactured_medium(q0: float = 1.0, variable_kappa: bool = True):
     return med, u
 
 
+def manufactured_medium_neumann(q0: float = 1.0, variable_kappa: bool = True):
+    """u*(r, z) = cos(pi r / 2) cos(pi z): u*_r = 0 at r = 0, u* = 0 at r = 1 and
+    u*_z = 0 at z = 0, 1 (the zero-flux z boundary of Eq. main_eq).  kappa and
+    f as in manufactured_medium.  Returns (Medium, u_exact)."""
+    pi = np.pi
+
+    def u(r, z):
+        return np.cos(0.5 * pi * r) * np.cos(pi * z)
+
+    def kappa(r, z):
+        if variable_kappa:
+            return 2.0 + r * r * np.cos(pi * z)
+        return np.ones(np.broadcast(r, z).shape)
+
+    def f(r, z):
+        r = np.asarray(r, dtype=np.float64)
+        z = np.asarray(z, dtype=np.float64)
+        s_r, c_r = np.sin(0.5 * pi * r), np.cos(0.5 * pi * r)
+        s_z, c_z = np.sin(pi * z), np.cos(pi * z)
+        u_r = -0.5 * pi * s_r * c_z
+        u_rr = -0.25 * pi * pi * c_r * c_z
+        u_zz = -pi * pi * c_r * c_z
+        u_z = -pi * c_r * s_z
+        u_r_over_r = -0.5 * pi * (s_r / r) * c_z
+        if variable_kappa:
+            k = 2.0 + r * r * c_z
+            k_r = 2.0 * r * c_z
+            k_z = -pi * r * r * s_z
+        else:
+            k, k_r, k_z = 1.0, 0.0, 0.0
+        return -(k * (u_rr + u_r_over_r + u_zz) + k_r * u_r + k_z * u_z) + q0 * c_r * c_z
+
+    med = Medium("manufactured_neumann", kappa, _const(q0), [f],
+                 "u* = cos(pi r/2) cos(pi z), kappa = 2 + r^2 cos(pi z)")
+    return med, u
+
+
 WORKLOADS = {
     "bumps_64": dict(nr=64, nz=64, build=lambda: bumps_medium(), tol=1e-10),
     "layered_1024_m64": dict(nr=1024, nz=1024, build=lambda: layered_inclusion_medium(64, 1024), tol=1e-8),
