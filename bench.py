@@ -99,6 +99,8 @@ def parse_args():
     ap.add_argument("--save", default="", help="guess_256: write the trained weights here")
     ap.add_argument("--h1", type=float, default=10.0, help="guess_256: weight of the loss's lattice-edge term")
     ap.add_argument("--no-pre", action="store_true", help="guess_256: raw f / s feature instead of B^-1 (r f)")
+    ap.add_argument("--bc-z", type=int, default=0, choices=[0, 1],
+                    help="z boundary: 0 = u = 0 (sine transform), 1 = the paper's zero flux (cosine pair)")
     ap.add_argument("--dst-tensor", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="FP32 path transform along z: -1 the library's choice, 0 FFT, 1 tensor-core GEMM "
                          "by S_hi + S_lo, 2 tensor-core GEMM by S_hi (option dst_tensor)")
@@ -166,18 +168,29 @@ class ClockSampler:
 # CPU baseline: the FP64 oracle, one right-hand side per process
 # ---------------------------------------------------------------------------
 def _oracle_one(args):
-    name, j = args
+    """Oracle PCG solves by one worker: right-hand sides (or, for single-source
+    workloads, seeded instances) j, j + stride, ... until min_s seconds have
+    passed (at least one)."""
+    name, j, stride, min_s, bc_z = args
     import oracle as O
     nr, nz, med = workload(name)
-    g = O.Grid(nr, nz)
-    kr, kz, q, f = O.sample_medium(med, g, rhs_index=[j])
+    single = med.n_rhs == 1
     t0 = time.perf_counter()
-    op = O.Operator(kr, kz, q, g)
-    t1 = time.perf_counter()
-    _, info = op.solve(f[0], TOL)
-    t2 = time.perf_counter()
-    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": info.iters, "unknowns": nr * nz,
-            "converged": bool(info.converged)}
+    unknowns, iters, solves, k = 0, [], 0, j
+    while True:
+        if single:
+            nr, nz, med = workload(name, instance=k)
+        g = O.Grid(nr, nz, bc_z=bc_z)
+        kr, kz, q, f = O.sample_medium(med, g, rhs_index=[0 if single else k % med.n_rhs])
+        op = O.Operator(kr, kz, q, g)
+        _, info = op.solve(f[0], TOL)
+        unknowns += nr * nz
+        iters.append(info.iters)
+        solves += 1
+        k += stride
+        if time.perf_counter() - t0 >= min_s:
+            break
+    return {"unknowns": unknowns, "iters": iters, "solves": solves}
 
 
 def oracle_pool(cores: int):
@@ -188,24 +201,27 @@ def oracle_pool(cores: int):
     return mp.get_context("spawn").Pool(cores)
 
 
-def cpu_baseline(name: str, cores: int, pool=None):
+def cpu_baseline(name: str, cores: int, pool=None, bc_z: int = 0):
     """Solves `cores` right-hand sides of the workload, one per core, with the
     oracle's PCG; returns unknowns solved per second of wall time."""
     own = pool is None
     pool = pool or oracle_pool(cores)
     try:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_one, [(name, j % 64) for j in range(cores)])
+        res = pool.map(_oracle_one, [(name, j, cores, 2.0, bc_z) for j in range(cores)])
         wall = time.perf_counter() - t0
     finally:
         if own:
             pool.close()
             pool.join()
     unknowns = sum(r["unknowns"] for r in res)
+    solves = sum(r["solves"] for r in res)
+    its = [i for r in res for i in r["iters"]]
     return {"value": unknowns / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cores} right-hand sides of {name}, one per host core, FP64 oracle PCG to {TOL:g} "
-                      f"(set-up included), wall {wall:.1f} s, iterations {[r['iters'] for r in res][:4]}...",
-            "wall_s": wall}
+            "sample": f"{solves} solves of {name} ({solves // cores}+ per host core, one process each), FP64 "
+                      f"oracle PCG to {TOL:g} (set-up included), wall {wall:.1f} s, iterations "
+                      f"{min(its)}..{max(its)}",
+            "wall_s": wall, "unknowns": unknowns}
 
 
 def run_reference(args):
@@ -217,21 +233,21 @@ def run_reference(args):
     try:
         # warm-up steps: a 64 x 64 solve per core (pool start-up, imports)
         for _ in range(args.warmup):
-            pool.map(_oracle_one, [("bumps_64", 0)] * cores)
+            pool.map(_oracle_one, [("bumps_64", 0, 1, 0.0, 0)] * cores)
         times, units = [], 0
         for _ in range(args.steps):
-            r = cpu_baseline(args.workload, cores, pool)
+            r = cpu_baseline(args.workload, cores, pool, args.bc_z)
             times.append(r["wall_s"])
-            units += cores * 1024 * 1024
+            units += r["unknowns"]
         total = sum(times)
         value = units / total
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "impl": "reference",
-                "config": {"workload": args.workload, "rhs_per_step": cores, "tol": TOL},
+                "config": {"workload": args.workload, "rhs_per_step": cores, "tol": TOL, "bc_z": args.bc_z},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                 "sample": f"each step: {cores} right-hand sides of {args.workload}, one per core"},
+                                 "sample": f"each step: {r['sample']}"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
     finally:
@@ -260,9 +276,9 @@ def run_batched(args):
     ops, fs, us, unknowns, nr_nz = [], [], [], 0, []
     for nr, nz, med in batched_instances(count):
         nr_nz.append((nr, nz))
-        kr, kz, q = sample_operator_inputs(med, nr, nz)
-        ops.append(P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz))
-        fs.append(torch.from_numpy(sample_rhs(med, nr, nz)[0]).to(dev))
+        kr, kz, q = sample_operator_inputs(med, nr, nz, bc_z=args.bc_z)
+        ops.append(P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz, bc_z=args.bc_z))
+        fs.append(torch.from_numpy(sample_rhs(med, nr, nz, bc_z=args.bc_z)[0]).to(dev))
         us.append(torch.zeros((nr, nz), dtype=torch.float64, device=dev))
         unknowns += nr * nz
     batch = P.ax_batch_create(ops)
@@ -306,6 +322,7 @@ def run_batched(args):
             "vs_baseline": None, "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64",
             "data": "synthetic",
             "config": {"workload": "batched_256", "instances": len(ops), "unknowns": unknowns, "groups": groups,
+                       "bc_z": args.bc_z,
                        "method": args.method, "tol": TOL},
             "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
                            "max": float(max(lats))},
@@ -423,11 +440,11 @@ def main():
 
     nr, nz, med = workload(args.workload, instance=rank, rhs=args.rhs)
     m = med.n_rhs
-    kr, kz, q = sample_operator_inputs(med, nr, nz)
-    op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz)
+    kr, kz, q = sample_operator_inputs(med, nr, nz, bc_z=args.bc_z)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz, bc_z=args.bc_z)
     if args.dst_tensor >= 0:
         P.ax_set_option(op, "dst_tensor", args.dst_tensor)
-    f_host = sample_rhs(med, nr, nz)
+    f_host = sample_rhs(med, nr, nz, bc_z=args.bc_z)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)
     method = P.METHODS[args.method]
@@ -558,7 +575,7 @@ def main():
     cpu = None
     if pool is not None:
         try:
-            cpu = cpu_baseline(args.workload, cores, pool)
+            cpu = cpu_baseline(args.workload, cores, pool, args.bc_z)
             cpu.pop("wall_s", None)
         finally:
             pool.close()
@@ -571,7 +588,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "nr": nr, "nz": nz, "rhs": m, "tol": TOL,
+            "config": {"workload": args.workload, "nr": nr, "nz": nz, "rhs": m, "tol": TOL, "bc_z": args.bc_z,
                        "method": args.method, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (f is %d MB, working set > 2 GB)" % (f_host.nbytes >> 20)},
             "iters": {"max": max(iters), "min": min(iters), "outer_max": max(outer)},

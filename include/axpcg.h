@@ -6,14 +6,17 @@
  *     (1/r) d_r(r kappa d_r u) + d_z(kappa d_z u) - q u = -f     on [0,lr] x [0,lz]
  *
  * (Section 2.1, Eq. main_eq), r kappa u_r = 0 on the axis r = 0, u = 0 on r = lr,
- * and u = 0 on z = 0 and z = lz (the sine-transform variant of the paper's
- * z-boundary; see the note on bc_z below).  Many right-hand sides share one
+ * and on z = 0 and z = lz either u = 0 (bc_z = 0, the sine-transform variant)
+ * or the paper's own zero-flux condition u_z = 0 (bc_z = 1, the cosine pair of
+ * Eq. fft_phi); see the note on bc_z below.  Many right-hand sides share one
  * operator (Section 1, Eq. main_problem).
  *
  * Discretisation (Section 2.1, Eqs. poisson_diff_2, scheme_op_r_z,
  * diff_approx1): r_i = (i - 1/2) h_r, h_r = lr / (nr + 1/2), i = 1..nr, with
- * u = 0 at r_{nr+1} = lr; faces rbar_i = i h_r.  z_k = k h_z, h_z = lz/(nz+1),
- * k = 1..nz; faces zbar_k = (k + 1/2) h_z, k = 0..nz.  The discrete operator is
+ * u = 0 at r_{nr+1} = lr; faces rbar_i = i h_r.  bc_z = 0: z_k = k h_z,
+ * h_z = lz/(nz+1), k = 1..nz; faces zbar_k = (k + 1/2) h_z, k = 0..nz.  bc_z = 1:
+ * z_k = (k - 1/2) h_z, h_z = lz/nz; faces zbar_k = k h_z, with KZ = 0 on the
+ * two boundary faces k = 0 and k = nz.  The discrete operator is
  * the r-weighted conservative 5-point scheme, sign-reversed so that it is
  * symmetric positive definite (Section 2.2, Eq. a-eq):
  *   (A y)_{i,k} = [KR_i (y_{i,k}-y_{i+1,k}) + KR_{i-1} (y_{i,k}-y_{i-1,k})] / h_r^2
@@ -58,7 +61,7 @@ enum {
   AX_ERR_TIMEOUT = 4,       /* a bounded device wait expired                                 */
   AX_ERR_OOM = 5,           /* device allocation failed                                      */
   AX_ERR_CUDA = 6,          /* any other CUDA runtime error                                  */
-  AX_ERR_UNSUPPORTED = 7    /* option not built (e.g. bc_z = 1)                              */
+  AX_ERR_UNSUPPORTED = 7    /* option not built (e.g. the tensor-core transform for bc_z = 1) */
 };
 
 /* ---- methods and flags -------------------------------------------------- */
@@ -91,9 +94,15 @@ enum { AX_PREC_FP64 = 0, AX_PREC_FP32 = 1, AX_PREC_FP32_TC = 2, AX_PREC_FP32_TC3
 typedef struct {
   int32_t nr, nz;   /* unknowns along r and z (>= 1)                                        */
   double lr, lz;    /* domain [0, lr] x [0, lz]                                             */
-  int32_t bc_z;     /* 0: u = 0 at z = 0, lz (sine transform).  1 (the paper's Neumann z
-                       condition with the cosine transform of Eq. fft_phi) is not built:
-                       AX_ERR_UNSUPPORTED                                                   */
+  int32_t bc_z;     /* 0: u = 0 at z = 0, lz; nodes z_k = k h_z, h_z = lz/(nz+1); sine
+                          transform (DST-I).
+                       1: the paper's zero-flux condition du/dz = 0 at z = 0, lz
+                          (Eq. main_eq); cell-centred nodes z_k = (k - 1/2) h_z,
+                          h_z = lz/nz, faces zbar_c = c h_z (c = 0..nz; kappa_z is still
+                          sampled there, but the two boundary faces carry no flux: the
+                          one-sided rows of Eq. scheme_op_r_z); the cosine pair of
+                          Eq. fft_phi.  The tensor-core transform is not built for it.
+                       Other values: AX_ERR_INVALID_ARG                                    */
 } ax_grid;
 
 typedef struct ax_operator ax_operator; /* opaque, library-owned */
@@ -144,8 +153,8 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
  *                    close to B^-1); 0: the FFT transform.  Default: 1 when
  *                    nz <= 2048 and the FFT length nz + 1 has a prime factor
- *                    above 7 (e.g. 1025 = 5^2 41), else 0.  nz <= 2048, else
- *                    AX_ERR_UNSUPPORTED
+ *                    above 7 (e.g. 1025 = 5^2 41), else 0.  nz <= 2048 and
+ *                    bc_z = 0, else AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */
@@ -246,11 +255,20 @@ int ax_guessnet_lift(const float *y, int32_t m, int32_t hw, const double *scale,
 int ax_apply_operator(ax_operator *op, const double *in, double *out, int32_t m,
                       int32_t precision, void *stream);
 
-/* out[row] = S in[row] for every one of `rows` rows of length nz, where
- * S[l][k] = sqrt(2/(nz+1)) sin(pi k l/(nz+1)) (orthonormal DST-I, the sine
- * counterpart of Eq. fft_phi; S = S^T = S^-1). */
+/* out[row] = S in[row] for every one of `rows` rows of length nz: the forward
+ * z-transform of the preconditioner.  bc_z = 0: S[l][k] = sqrt(2/(nz+1))
+ * sin(pi k l/(nz+1)) (orthonormal DST-I, the sine counterpart of Eq. fft_phi;
+ * S = S^T = S^-1).  bc_z = 1: S[l][k] = c_l sqrt(2/nz) cos(pi (k - 1/2) l / nz),
+ * l = 0..nz-1, c_0 = 1/sqrt 2, else 1 (orthonormal DCT-II: the forward sum of
+ * Eq. fft_phi with its first mode divided by sqrt 2). */
 int ax_apply_dst(ax_operator *op, const double *in, double *out, int32_t rows,
                  int32_t precision, void *stream);
+
+/* out[row] = S^T in[row]: the inverse z-transform (bc_z = 0: the same DST-I;
+ * bc_z = 1: the orthonormal DCT-III, the inverse sum of Eq. fft_phi with its
+ * first mode times sqrt 2).  precision AX_PREC_FP64 or AX_PREC_FP32 only. */
+int ax_apply_dst_inverse(ax_operator *op, const double *in, double *out, int32_t rows,
+                         int32_t precision, void *stream);
 
 /* For each right-hand side and each mode column l, solve T_l y[:, l] = in[:, l]
  * along r, T_l = Lr(kappa~) + diag(r_i (kappa~ lambda_l + q~)) (Eq. eq_trid). */

@@ -41,8 +41,8 @@ METHODS = {"pcg64": AX_PCG_FP64, "cheb64": AX_CHEB_FP64, "pcg_mixed": AX_PCG_MIX
            "cheb_mixed": AX_CHEB_MIXED}
 
 EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_set_option", "ax_solve",
-            "ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
-            "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read",
+            "ax_apply_operator", "ax_apply_dst", "ax_apply_dst_inverse", "ax_apply_mode_solve",
+            "ax_apply_preconditioner", "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read",
             "ax_apply_preconditioner_noalloc", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
             "ax_batch_destroy", "ax_solve_batched", "ax_last_error",
             "ax_guessnet_create", "ax_guessnet_destroy", "ax_guessnet_num_params", "ax_guessnet_get_params",
@@ -92,8 +92,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_operator_info.argtypes = [vp] + [ctypes.POINTER(dbl)] * 4
     lib.ax_set_option.argtypes = [vp, ctypes.c_char_p, dbl]
     lib.ax_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, i32, ctypes.POINTER(AxSolveInfo), vp]
-    for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_mode_solve", "ax_apply_preconditioner",
-                 "ax_apply_preconditioner_noalloc"):
+    for name in ("ax_apply_operator", "ax_apply_dst", "ax_apply_dst_inverse", "ax_apply_mode_solve",
+                 "ax_apply_preconditioner", "ax_apply_preconditioner_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, i32, i32, vp]
     lib.ax_last_error.argtypes = []
     lib.ax_status_string.argtypes = [ctypes.c_int]
@@ -221,6 +221,10 @@ def ax_apply_operator(op, x, y, m, precision=AX_PREC_FP64, stream=None):
 
 def ax_apply_dst(op, x, y, rows, precision=AX_PREC_FP64, stream=None):
     _apply("ax_apply_dst", op, x, y, rows, precision, stream)
+
+
+def ax_apply_dst_inverse(op, x, y, rows, precision=AX_PREC_FP64, stream=None):
+    _apply("ax_apply_dst_inverse", op, x, y, rows, precision, stream)
 
 
 def ax_apply_mode_solve(op, x, y, m, precision=AX_PREC_FP64, stream=None):

@@ -1,4 +1,4 @@
-// Sine transform, FP32 instantiation (see ax_dst_impl.cuh).
+// Sine and cosine transforms, FP32 instantiation (see ax_dst_impl.cuh).
 #include "ax_dst_impl.cuh"
 
 namespace ax {
@@ -6,8 +6,9 @@ namespace {
 template <typename T>
 void launch_dst_any(int mode, const DstArgs<T> &a_in, cudaStream_t s) {
   DstArgs<T> a = a_in;
-  a.rpb = dst_rows_per_block(a.plan.L, (int)sizeof(T));
-  size_t smem = dst_smem_bytes(a.plan.L, (int)sizeof(T));
+  const int LB = dst_buffer_len(a.plan.L, a.n);
+  a.rpb = dst_rows_per_block(LB, (int)sizeof(T));
+  size_t smem = dst_smem_bytes(LB, (int)sizeof(T));
   if (a.plan.rader) smem += 2ull * a.rpb * a.plan.tn_div[0].d * 2 * sizeof(T);
   dim3 grid(a.m, (a.rows + a.rpb - 1) / a.rpb);
   dim3 block(256);

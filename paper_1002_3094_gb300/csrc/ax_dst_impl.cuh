@@ -14,6 +14,20 @@
 // share the sums and differences of inputs r and R - r), eight output pairs
 // per thread.
 //
+// The zero-flux z boundary (the paper's own) uses the cosine pair of
+// Eq. fft_phi instead, in orthonormal form (the paper's forward sum with its
+// first mode divided by sqrt 2, and its inverse with the 1/2 weight times
+// sqrt 2: B^-1 = C^T T^-1 C is the same operator).  Both go through the same
+// complex FFT, now of length L = nz:
+//   forward (DCT-II): the even extension y (y_k = y_{2n-1-k} = in[k]) is
+//     packed as z_j = y_{2j} + i y_{2j+1}; with Z = FFT(z), E_l, O_l the
+//     transforms of the even / odd samples of y, Y_l = E_l + e^{-i 2 phi} O_l
+//     and out[l] = s_l Re(e^{-i phi} Y_l) / 2, phi = pi l / (2 n);
+//   inverse (DCT-III): the spectrum of that even extension,
+//     Y_l = 2 e^{i phi} X_l, is split back into E_l and O_l, packed as
+//     Z_l = E_l + i O_l, and z = IDFT(Z) = conj(FFT(conj Z)) / n holds
+//     out[2j] = Re z_j, out[2j+1] = Im z_j.
+//
 // One CTA transforms `rpb` rows of one right-hand side (blockIdx.x = RHS).
 // The fused variants update the CG iterate and residual while loading the
 // rows (forward) or form the (r, z) partial while storing (inverse).
@@ -465,11 +479,14 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   const int m = blockIdx.x;
   if (!rhs_selected(a.st, a.mask, m)) return;
   const int L = a.plan.L, n = a.n;
+  const int LB = dst_buffer_len(L, n);
+  const bool cosine = a.cosine != 0;
+  const bool inv = cosine && (a.inverse != 0 || MODE == kDstPcgInverse || MODE == kDstChebInverse);
   const int row0 = blockIdx.y * a.rpb;
   const int nrows = min(a.rpb, a.rows - row0);
   C *buf0 = reinterpret_cast<C *>(smem_raw);
-  C *buf1 = buf0 + ((a.rpb * L + 1) & ~1);  // 16-byte aligned (vector staging stores)
-  C *x0s = buf1 + a.rpb * L;                 // Rader: 2 values per first-stage butterfly
+  C *buf1 = buf0 + ((a.rpb * LB + 1) & ~1);  // 16-byte aligned (vector staging stores)
+  C *x0s = buf1 + a.rpb * LB;                 // Rader: 2 values per first-stage butterfly
   T *pk = reinterpret_cast<T *>(buf0);  // packed real view: pk[rr * 2L + idx] = x_idx
   const size_t base = (size_t)m * (size_t)a.field + (size_t)row0 * a.pitch;
   T alpha = T(0);
@@ -519,14 +536,36 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   for (int rr = 0; rr < nrows; ++rr) {
     T *px = pk + rr * 2 * L;
     const T *sr = stg + rr * spitch;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const T v = sr[k];
-      px[k + 1] = v;
-      px[2 * L - k - 1] = -v;
-    }
-    if (threadIdx.x == 0) {
-      px[0] = T(0);
-      px[L] = T(0);
+    if (!cosine) {  // odd extension of length 2L
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const T v = sr[k];
+        px[k + 1] = v;
+        px[2 * L - k - 1] = -v;
+      }
+      if (threadIdx.x == 0) {
+        px[0] = T(0);
+        px[L] = T(0);
+      }
+    } else if (!inv) {  // even extension of length 2n (L = n)
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const T v = sr[k];
+        px[k] = v;
+        px[2 * L - k - 1] = v;
+      }
+    } else {  // conj(Z_l), Z_l = E_l + i O_l from X_l and X_{n-l} (X_n = 0)
+      C *zr = buf0 + rr * L;
+      for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const T xl = sr[l], xm = l ? sr[n - l] : T(0);
+        const T c = __ldg(a.CW + 8 * l + 4), sn = __ldg(a.CW + 8 * l + 5);
+        const T c2 = __ldg(a.CW + 8 * l + 6), s2 = __ldg(a.CW + 8 * l + 7);
+        const T ex = fma(xl, c, xm * sn), ey = fma(xl, sn, -xm * c);
+        const T dx = fma(xl, c, -xm * sn), dy = fma(xl, sn, xm * c);
+        const T ox = fma(dx, c2, -dy * s2), oy = fma(dx, s2, dy * c2);
+        C zc;
+        zc.x = ex - oy;
+        zc.y = -(ey + ox);
+        zr[l] = zc;
+      }
     }
   }
 
@@ -580,13 +619,33 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
     cheb_a = (T)a.st[m].cheb_a;
     tau = (T)a.tau;
   }
-  for (int k = threadIdx.x + 1; k <= n; k += blockDim.x) {
-    const T c = __ldg(a.HW + 2 * k), sn = __ldg(a.HW + 2 * k + 1);
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    // per-column factors: sine (c, sn) = half-angle pair of k = o + 1; cosine
+    // forward: the four scaled factors of mode o
+    T c = T(0), sn = T(0), f2 = T(0), f3 = T(0);
+    if (!cosine) {
+      c = __ldg(a.HW + 2 * (o + 1));
+      sn = __ldg(a.HW + 2 * (o + 1) + 1);
+    } else if (!inv) {
+      c = __ldg(a.CW + 8 * o);
+      sn = __ldg(a.CW + 8 * o + 1);
+      f2 = __ldg(a.CW + 8 * o + 2);
+      f3 = __ldg(a.CW + 8 * o + 3);
+    }
     for (int rr = 0; rr < nrows; ++rr) {
       const C *Z = src + rr * L;
-      const C zk = Z[k], zm = Z[L - k];
-      const T v = ((zm.y - zk.y) + c * (zk.x - zm.x) + sn * (zk.y + zm.y)) * sc;
-      const size_t e = base + (size_t)rr * a.pitch + (k - 1);
+      T v;
+      if (!cosine) {
+        const C zk = Z[o + 1], zm = Z[L - o - 1];
+        v = ((zm.y - zk.y) + c * (zk.x - zm.x) + sn * (zk.y + zm.y)) * sc;
+      } else if (!inv) {
+        const C zl = Z[o], zm = Z[o ? n - o : 0];
+        v = (zl.x + zm.x) * c + (zl.y - zm.y) * sn + (zl.y + zm.y) * f2 - (zl.x - zm.x) * f3;
+      } else {
+        const C w = Z[o >> 1];
+        v = ((o & 1) ? -w.y : w.x) * sc;
+      }
+      const size_t e = base + (size_t)rr * a.pitch + o;
       if (MODE == kDstPlain || MODE == kDstPcgForward) {
         outg[e] = v;
       } else if (MODE == kDstPcgInverse) {

@@ -79,6 +79,9 @@ struct Coef {
   T *R = nullptr;    // [nr]          r_i
   T *TW = nullptr;   // [2 L]         (cos, sin)(2 pi j / L), j < L
   T *HW = nullptr;   // [2 L]         (cos, sin)(pi j / L),   j < L
+  T *CW = nullptr;   // [8 nz]        zero-flux z only: cosine-transform factors of mode l
+                     //               (forward: scaled cos/sin of phi_l, 3 phi_l; inverse:
+                     //               cos/sin of phi_l, 2 phi_l; phi_l = pi l / (2 nz))
   T *RK = nullptr;   // [2 P]         Rader: DFT of the permuted kernel W^(g^-m)
   T *RT = nullptr;   // [2 P]         Rader: (cos, sin)(2 pi j / P)
   // FP32 only: low parts of the FP64 stencil coefficients, CR64 = CR + CRl (CR the
@@ -138,6 +141,7 @@ enum { kProfStencil = 0, kProfDstFwd = 1, kProfTridiag = 2, kProfDstInv = 3, kPr
 
 struct ax_operator {
   int nr = 0, nz = 0, pitch = 0, pitchz = 0;
+  int bc_z = 0;  // 0: u = 0 at z = 0, lz (sine transform); 1: zero flux there (cosine pair)
   // A group operator stacks the coefficient tables of several operators of one
   // grid shape; right-hand side m then uses table m (strides in elements).
   long long cstride = 0, czstride = 0, estride = 0;
@@ -211,6 +215,9 @@ enum { kDstPlain = 0, kDstPcgForward = 1, kDstPcgInverse = 2, kDstChebInverse = 
 template <typename T>
 struct DstArgs {
   const T *TW, *HW;
+  const T *CW;             // cosine: per-mode factors (Coef::CW)
+  int cosine;              // 0: sine transform (DST-I, its own inverse); 1: cosine pair
+  int inverse;             // cosine, plain mode: 1 = inverse (DCT-III), 0 = forward (DCT-II)
   const T *RK, *RT;        // Rader tables (plan.rader)
   const int *RP;           // Rader permutations: g^p mod R (p < P), then g^-q mod R
   FftPlan plan;
@@ -223,7 +230,8 @@ struct DstArgs {
   T *pa, *pb;              // PcgForward: p is pb for an even iteration count, pa for odd
   T *y, *yprev;            // Cheb: y_{k+1} = a (y - tau res^) + (1 - a) y_{k-1}, written to yprev
   double tau;             // Cheb: constant step tau_0
-  double scale;           // 0.5 / sqrt(2 L): orthonormal scaling folded with the real-FFT split
+  double scale;           // sine: 0.5 / sqrt(2 L), the orthonormal scaling folded with the
+                          // real-FFT split; cosine inverse: 1 / sqrt(2 nz)
   int rpb;                // rows per CTA (set by the launcher)
   const RhsState *st;
   int mask;
@@ -240,6 +248,13 @@ int dst_rows_per_block(int L, int elem_bytes);
 int dst_prepare_device();  // constant tables of the unrolled prime radices (once per device)
 int dst_prepare_f64();
 size_t dst_smem_bytes(int L, int elem_bytes);
+// Row length (complex values) of the transform's shared buffers: the FFT
+// length L, or more when the staging copy of a row (n rounded up to 4 reals)
+// needs it (the cosine transform of n = 1, whose L is 1).
+__host__ __device__ inline int dst_buffer_len(int L, int n) {
+  const int need = ((n + 3) & ~3) / 2;
+  return L > need ? L : need;
+}
 
 // Tensor-core sine transform (input split into BF16 halves in the tile layout
 // of ax_common.cuh, BF16 DST matrix, FP32 accumulation).

@@ -94,6 +94,8 @@ int precond_noalloc(ax_operator *op, const double *in, double *out, int m, cudaS
   DstArgs<T> d{};
   d.TW = c.TW;
   d.HW = c.HW;
+  d.CW = c.CW;
+  d.cosine = op->bc_z == 1;
   d.RK = c.RK;
   d.RT = c.RT;
   d.RP = op->rader_perm;
@@ -103,7 +105,7 @@ int precond_noalloc(ax_operator *op, const double *in, double *out, int m, cudaS
   d.pitch = op->pitch;
   d.field = (long long)field;
   d.m = m;
-  d.scale = 0.5 / std::sqrt(2.0 * op->plan.L);
+  d.scale = op->bc_z == 1 ? 1.0 / std::sqrt(2.0 * op->nz) : 0.5 / std::sqrt(2.0 * op->plan.L);
   d.st = nullptr;
   d.mask = -1;
   d.in = a;
@@ -128,6 +130,7 @@ int precond_noalloc(ax_operator *op, const double *in, double *out, int m, cudaS
 
   d.in = b;
   d.out = b;
+  d.inverse = 1;
   launch_dst<T>(kDstPlain, d, s);
 
   note_launch();

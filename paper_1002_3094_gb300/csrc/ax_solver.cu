@@ -892,7 +892,7 @@ cudaError_t upload(T **dst, const std::vector<double> &src) {
 
 template <typename T>
 void free_coef(Coef<T> &c) {
-  dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW);
+  dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW); dfree(c.CW);
   dfree(c.RK); dfree(c.RT);
   dfree(c.CRl); dfree(c.CZl); dfree(c.Wl);
 }
@@ -914,6 +914,8 @@ DstArgs<T> dst_args(const ax_operator *op, int m, int rows, const RhsState *st, 
   const Coef<T> &c = coef<T>(op);
   a.TW = c.TW;
   a.HW = c.HW;
+  a.CW = c.CW;
+  a.cosine = op->bc_z == 1;
   a.RK = c.RK;
   a.RT = c.RT;
   a.RP = op->rader_perm;
@@ -923,7 +925,7 @@ DstArgs<T> dst_args(const ax_operator *op, int m, int rows, const RhsState *st, 
   a.pitch = op->pitch;
   a.field = (long long)rows * op->pitch;
   a.m = m;
-  a.scale = 0.5 / std::sqrt(2.0 * op->plan.L);
+  a.scale = op->bc_z == 1 ? 1.0 / std::sqrt(2.0 * op->nz) : 0.5 / std::sqrt(2.0 * op->plan.L);
   a.st = st;
   a.mask = mask;
   return a;
@@ -970,7 +972,7 @@ TriArgs<T> tri_args(const ax_operator *op, int m, const T *in, T *out, const Rhs
 }
 
 int dst_blocks(const ax_operator *op, int rows, int bytes) {
-  const int rpb = dst_rows_per_block(op->plan.L, bytes);
+  const int rpb = dst_rows_per_block(dst_buffer_len(op->plan.L, op->nz), bytes);
   return (rows + rpb - 1) / rpb;
 }
 
@@ -1655,7 +1657,7 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     w->replace_delta = value;
   } else if (!strcmp(name, "dst_tensor")) {
     if (value != 0.0 && value != 1.0 && value != 2.0) return AX_ERR_INVALID_ARG;
-    if (value != 0.0 && op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
+    if (value != 0.0 && (op->nz > kMaxTcN || op->bc_z != 0)) return AX_ERR_UNSUPPORTED;
     op->dst_tc = (int)value;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "max_outer")) {
@@ -1672,7 +1674,8 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   if (!out) return AX_ERR_INVALID_ARG;
   *out = nullptr;
   if (!kappa_r || !kappa_z || !q || !g) return AX_ERR_INVALID_ARG;
-  if (g->bc_z != 0) return g->bc_z == 1 ? AX_ERR_UNSUPPORTED : AX_ERR_INVALID_ARG;
+  if (g->bc_z != 0 && g->bc_z != 1) return AX_ERR_INVALID_ARG;
+  const int cosine = g->bc_z == 1;
   const int nr = g->nr, nz = g->nz;
   if (nr < 1 || nz < 1 || nr > kMaxNr || nz > kMaxNz) return AX_ERR_INVALID_ARG;
   if (!(g->lr > 0.0) || !(g->lz > 0.0) || !std::isfinite(g->lr) || !std::isfinite(g->lz)) return AX_ERR_INVALID_ARG;
@@ -1709,8 +1712,10 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   op->pitchz = (nz + 1 + 31) / 32 * 32;
   op->lr = g->lr;
   op->lz = g->lz;
+  op->bc_z = g->bc_z;
   op->hr = g->lr / (nr + 0.5);
-  op->hz = g->lz / (nz + 1.0);
+  // zero-flux z: cell-centred nodes, the boundary faces on z = 0 and z = lz
+  op->hz = cosine ? g->lz / nz : g->lz / (nz + 1.0);
   cudaGetDevice(&op->device);
   // Eq. coeff2 with the footnote of Eq. diff_approx2: mean of the extremes.
   op->kappa_t = 0.5 * (kmin + kmax);
@@ -1722,7 +1727,9 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
     op->gamma1 = std::min(op->gamma1, qmin / op->q_t);
     op->gamma2 = std::max(op->gamma2, qmax / op->q_t);
   }
-  const int L = nz + 1;
+  // FFT length: the sine transform packs its odd extension of length 2(nz+1),
+  // the cosine pair its even extension of length 2 nz
+  const int L = cosine ? nz : nz + 1;
   op->plan = make_plan(L);
   if (op->plan.nstages > kMaxStages) {
     ax_destroy_operator(op);
@@ -1732,7 +1739,7 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   // needs a prime radix above 8 (paired direct DFT or Rader stages, several
   // times the work of the small radices) and nz is within the GEMM's range.
   op->dst_tc = 0;
-  if (nz <= kMaxTcN)
+  if (nz <= kMaxTcN && !cosine)
     for (int i = 0; i < op->plan.nstages; ++i)
       if (op->plan.radix[i] > 8) op->dst_tc = 1;
 
@@ -1747,13 +1754,19 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
       W[(size_t)a * P + b] = ri[a] * qq[(size_t)a * nz + b];
     }
     for (int c = 0; c <= nz; ++c) CZ[(size_t)a * PZ + c] = ri[a] * kz[(size_t)a * (nz + 1) + c] / hz2;
+    if (cosine) {  // no flux through z = 0 and z = lz (one-sided rows of Eq. scheme_op_r_z)
+      CZ[(size_t)a * PZ] = 0.0;
+      CZ[(size_t)a * PZ + nz] = 0.0;
+    }
   }
   // Per-mode Thomas factors of T_l (Eq. eq_trid), computed in FP64.
   std::vector<double> E(nr, 0.0), IP((size_t)nr * P, 0.0);
   const double kt = op->kappa_t, qt = op->q_t;
   for (int a = 0; a + 1 < nr; ++a) E[a] = -kt * (a + 1) * hr / hr2;
   for (int l = 1; l <= nz; ++l) {
-    const double sn = std::sin(M_PI * l / (2.0 * (nz + 1)));
+    // mode eigenvalue of the z second difference: sine modes l = 1..nz, or the
+    // cosine modes of Eq. eq_trid, 4/h^2 sin^2(pi (l - 1) / (2 nz)) (0 for l = 1)
+    const double sn = cosine ? std::sin(M_PI * (l - 1) / (2.0 * nz)) : std::sin(M_PI * l / (2.0 * (nz + 1)));
     const double lam = 4.0 / hz2 * sn * sn;
     double delta = 0.0;
     for (int a = 0; a < nr; ++a) {
@@ -1770,7 +1783,31 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
     HW[2 * j] = std::cos(M_PI * j / L);
     HW[2 * j + 1] = std::sin(M_PI * j / L);
   }
+  // Cosine pair, per mode l = 0..nz-1 with phi = pi l / (2 nz): forward
+  // factors s_l / 4 * (cos phi, sin phi, cos 3 phi, sin 3 phi), s_l the
+  // orthonormal scale (sqrt(1/nz) for l = 0, sqrt(2/nz) otherwise); inverse
+  // factors (cos phi, sin phi) (times sqrt 2 for l = 0: X_0 = sqrt(nz) Xhat_0
+  // against sqrt(nz / 2) for the others, which the store scale holds) and
+  // (cos 2 phi, sin 2 phi).
+  std::vector<double> CWt;
+  if (cosine) {
+    CWt.assign(8 * (size_t)nz, 0.0);
+    for (int l = 0; l < nz; ++l) {
+      const double phi = M_PI * l / (2.0 * nz);
+      const double f = 0.25 * std::sqrt(2.0 / nz) * (l == 0 ? std::sqrt(0.5) : 1.0);
+      const double g0 = l == 0 ? std::sqrt(2.0) : 1.0;
+      double *t = &CWt[8 * (size_t)l];
+      t[0] = f * std::cos(phi); t[1] = f * std::sin(phi);
+      t[2] = f * std::cos(3 * phi); t[3] = f * std::sin(3 * phi);
+      t[4] = g0 * std::cos(phi); t[5] = g0 * std::sin(phi);
+      t[6] = std::cos(2 * phi); t[7] = std::sin(2 * phi);
+    }
+  }
   cudaError_t e = cudaSuccess;
+  if (cosine) {
+    e = upload<double>(&op->c64.CW, CWt);
+    if (e == cudaSuccess) e = upload<float>(&op->c32.CW, CWt);
+  }
 #define AX_UP(T, field, vec) \
   if (e == cudaSuccess) e = upload<T>(&op->field, vec);
   AX_UP(double, c64.CR, CR) AX_UP(double, c64.CZ, CZ) AX_UP(double, c64.W, W) AX_UP(double, c64.IP, IP)
@@ -1857,6 +1894,12 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
       d.out = b;
       launch_dst<T>(kDstPlain, d, s);
     }
+  } else if (which == 4) {  // inverse transform (the sine transform is its own)
+    DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
+    d.in = a;
+    d.out = b;
+    d.inverse = 1;
+    launch_dst<T>(kDstPlain, d, s);
   } else if (which == 2) {
     launch_tridiag<T>(tri_args<T>(op, m, a, b, nullptr, -1), s);
   } else if (tc) {
@@ -1876,6 +1919,7 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
     DstArgs<T> d2 = dst_args<T>(op, m, rows_per, nullptr, -1);
     d2.in = b;
     d2.out = b;
+    d2.inverse = 1;
     launch_dst<T>(kDstPlain, d2, s);
   }
   note_launch();
@@ -1904,7 +1948,7 @@ static int apply_dispatch(ax_operator *op, const double *in, double *out, int m,
   if ((long long)rows_per * m > 2147483647LL / 2) return AX_ERR_INVALID_ARG;
   if (tc) {
     if (which != 1 && which != 3) return AX_ERR_INVALID_ARG;
-    if (op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
+    if (op->nz > kMaxTcN || op->bc_z != 0) return AX_ERR_UNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
   return precision == AX_PREC_FP64 ? apply_step<double>(op, in, out, m, rows_per, which, s)
@@ -1920,6 +1964,12 @@ int ax_apply_operator(ax_operator *op, const double *in, double *out, int32_t m,
 int ax_apply_dst(ax_operator *op, const double *in, double *out, int32_t rows, int32_t precision, void *stream) {
   if (op && rows > 65535 * 16) return AX_ERR_INVALID_ARG;
   return apply_dispatch(op, in, out, 1, rows, precision, 1, stream);
+}
+int ax_apply_dst_inverse(ax_operator *op, const double *in, double *out, int32_t rows, int32_t precision,
+                         void *stream) {
+  if (op && rows > 65535 * 16) return AX_ERR_INVALID_ARG;
+  if (precision != AX_PREC_FP64 && precision != AX_PREC_FP32) return AX_ERR_INVALID_ARG;
+  return apply_dispatch(op, in, out, 1, rows, precision, 4, stream);
 }
 int ax_apply_mode_solve(ax_operator *op, const double *in, double *out, int32_t m, int32_t precision,
                         void *stream) {
@@ -2221,6 +2271,7 @@ cudaError_t build_group_coef(Coef<T> &g, const std::vector<const ax_operator *> 
   if (err == cudaSuccess) err = copy_table(&g.R, c0.R, (size_t)o->nr, s);
   if (err == cudaSuccess) err = copy_table(&g.TW, c0.TW, 2 * (size_t)o->plan.L, s);
   if (err == cudaSuccess) err = copy_table(&g.HW, c0.HW, 2 * (size_t)o->plan.L, s);
+  if (err == cudaSuccess && c0.CW != nullptr) err = copy_table(&g.CW, c0.CW, 8 * (size_t)o->nz, s);
   if (err == cudaSuccess && o->plan.rader) {
     const size_t P = (size_t)o->plan.radix[0] - 1;
     err = copy_table(&g.RK, c0.RK, 2 * P, s);
@@ -2270,7 +2321,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     b->nr.push_back(ops[i]->nr);
     b->nz.push_back(ops[i]->nz);
   }
-  // group by grid shape (and domain), in order of first appearance
+  // group by grid shape, domain and z boundary, in order of first appearance
   std::vector<int> key_of(n, -1);
   for (int i = 0; i < n; ++i) {
     if (key_of[i] >= 0) continue;
@@ -2278,7 +2329,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     for (int j = i; j < n; ++j) {
       if (key_of[j] >= 0) continue;
       const ax_operator *a = ops[i], *c = ops[j];
-      if (a->nr == c->nr && a->nz == c->nz && a->lr == c->lr && a->lz == c->lz) {
+      if (a->nr == c->nr && a->nz == c->nz && a->lr == c->lr && a->lz == c->lz && a->bc_z == c->bc_z) {
         key_of[j] = (int)b->groups.size();
         g.members.push_back(j);
       }
@@ -2292,7 +2343,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     const ax_operator *o = mops[0];
     ax_operator *gop = new ax_operator();
     gop->ws = new Workspace();
-    gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz;
+    gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz; gop->bc_z = o->bc_z;
     gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;
     gop->kappa_t = o->kappa_t; gop->q_t = o->q_t; gop->gamma1 = o->gamma1; gop->gamma2 = o->gamma2;
     gop->device = o->device;

@@ -261,8 +261,8 @@ def test_invalid_arguments(cuda):
     with pytest.raises(P.AxError):
         P.ax_setup_operator(good[0], nan_k, good[2], nr, nz)
     with pytest.raises(P.AxError) as e:
-        P.ax_setup_operator(*good, nr, nz, bc_z=1)
-    assert e.value.status == P.AX_ERR_UNSUPPORTED
+        P.ax_setup_operator(*good, nr, nz, bc_z=2)
+    assert e.value.status == P.AX_ERR_INVALID_ARG
     with pytest.raises(P.AxError):
         P.ax_setup_operator(*good, 0, nz)
     op = P.ax_setup_operator(*good, nr, nz)
