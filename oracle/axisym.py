@@ -200,9 +200,13 @@ def cosine_pair(n: int):
                F[l-1, k-1] = sqrt(2/n) cos(pi (k - 1/2)(l - 1) / n);
       inverse  y_k = sqrt(2/n) (y~(1) / 2 + sum_{l>=2} y~(l) cos(...)),
                G[l-1, k-1] = w_l F[l-1, k-1], w_1 = 1/2, w_l = 1 otherwise."""
-    k = np.arange(1, n + 1) - 0.5
+    k = np.arange(1, n + 1)
     l = np.arange(0, n)
-    F = math.sqrt(2.0 / n) * np.cos(np.pi * np.outer(l, k) / n)
+    # cos(pi (k - 1/2)(l - 1) / n) = cos(pi m / (2n)) with the integer
+    # m = (2k - 1)(l - 1), of period 4n: reduce it exactly before scaling, so
+    # large arguments lose no accuracy.
+    m = np.outer(l, 2 * k - 1) % (4 * n)
+    F = math.sqrt(2.0 / n) * np.cos(np.pi * m / (2.0 * n))
     w = np.ones(n)
     w[0] = 0.5
     return F, w[:, None] * F
