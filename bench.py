@@ -35,48 +35,73 @@ TOL = 1e-8
 # M = right-hand sides sharing the coefficient tables.
 #   stencil (p = z + beta p, q = A p): read z, p_old; write p, q  -> 16 B, + CR, CZ, W (12 B / M)
 #   FFT forward transform (x += a p, r -= a q, rhat = S r): read x, p, r, q; write x, r, rhat -> 28 B
-#   update pass (x += a p, r -= a q) ahead of the tensor-core transform: read x, p, r, q; write x, r -> 24 B
-#   tensor-core forward transform (rhat = S r): read r, write rhat -> 8 B
+#   update pass (x += a p, r -= a q) ahead of the tensor-core transform: read x, p, r, q; write x, r
+#     and r split into BF16 halves (the transform's operand) -> 28 B
+#   tensor-core forward transform (rhat = S r): read split r, write rhat -> 8 B
 #   mode solves: read rhat, write yhat -> 8 B, + IP (4 B / M)
-#   inverse transform (z = S yhat, (r, z)): read yhat, r; write z -> 12 B
+#   FFT inverse transform (z = S yhat, (r, z)): read yhat, r; write z -> 12 B
+#   tensor-core inverse transform (z = S yhat; (r, z) comes from the mode solves): read split
+#     yhat, write z -> 8 B
 #   true residual (r = phi - A x, x and phi as FP32 pairs): read x, phi (16 B); write r (4 B) -> 20 B,
 #     + coefficients and their low parts 24 B / M
 ALG_BYTES = {"stencil": (16.0, 12.0), "dst_forward": (28.0, 0.0), "mode_solve": (8.0, 4.0),
-             "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0), "pcg_update": (24.0, 0.0)}
-ALG_BYTES_TC = dict(ALG_BYTES, dst_forward=(8.0, 0.0))
+             "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0), "pcg_update": (28.0, 0.0)}
+ALG_BYTES_TC = dict(ALG_BYTES, dst_forward=(8.0, 0.0), dst_inverse=(8.0, 0.0))
 # Tensor-core transform: multiply-adds per row = products x n^2 / 2 (even / odd
 # halves), 2 flops each.
 TC_CLASSES = ("dst_forward", "dst_inverse")
 
 
-# Source files whose change invalidates an ncu traffic figure of a kernel class.
-KERNEL_SOURCES = {"stencil": ["ax_stencil.cu"],
-                  "dst_forward": ["ax_dst_impl.cuh", "ax_dst_f32.cu", "ax_dst_gemm.cu"],
-                  "dst_inverse": ["ax_dst_impl.cuh", "ax_dst_f32.cu", "ax_dst_gemm.cu"],
-                  "mode_solve": ["ax_tridiag.cu"], "outer_residual": ["ax_stencil.cu"],
-                  "pcg_update": ["ax_solver.cu"]}
+# Source of each kernel class whose change invalidates its ncu traffic figure:
+# (file, __global__ function or None for the whole file), plus the shared
+# device helpers.
+KERNEL_SOURCES = {"stencil": [("ax_stencil.cu", "stencil_kernel")],
+                  "dst_forward": [("ax_dst_impl.cuh", None), ("ax_dst_gemm.cu", None)],
+                  "dst_inverse": [("ax_dst_impl.cuh", None), ("ax_dst_gemm.cu", None)],
+                  "mode_solve": [("ax_tridiag.cu", "tridiag_reg_kernel")],
+                  "outer_residual": [("ax_stencil.cu", "residual_df_kernel")],
+                  "pcg_update": [("ax_solver.cu", "pcg_update")]}
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic_per_unknown.md")
+
+
+def _function_text(src: str, name: str) -> str:
+    """The text of the __global__ function `name`: from its declaration line
+    to the first line that closes it at column 0."""
+    lines = src.splitlines()
+    for i, line in enumerate(lines):
+        if "__global__" in line and (name + "(") in " ".join(lines[i:i + 2]):
+            for j in range(i, len(lines)):
+                if lines[j] == "}":
+                    return "\n".join(lines[i:j + 1])
+    return src
 
 
 def source_hash(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES.get(kernel, []):
-        with open(os.path.join(ROOT, "paper_1002_3094_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_1002_3094_gb300", "csrc")
+    for f, fn in KERNEL_SOURCES.get(kernel, []) + [("ax_common.cuh", None)]:
+        with open(os.path.join(csrc, f)) as fh:
+            text = fh.read()
+        h.update((text if fn is None else _function_text(text, fn)).encode())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel: str, units_per_launch: float):
     """DRAM bytes (read + write) per launch of `kernel`, scaled from the ncu
-    capture recorded in profiles/traffic.json (bytes per grid unknown of the
-    captured launch), or None when no capture matches the current source."""
+    capture recorded in profiles/traffic_per_unknown.md (bytes per grid
+    unknown of the captured launch), or None when no capture matches the
+    current source of the kernel."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
-    except (OSError, ValueError):
+        lines = open(TRAFFIC_TABLE).read().splitlines()
+    except OSError:
         return None
-    if not rec or rec.get("source_sha") != source_hash(kernel):
-        return None
-    return rec["dram_bytes_per_unknown"] * units_per_launch
+    want = source_hash(kernel)
+    for line in lines:
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == kernel and cells[2] == want:
+            return float(cells[1]) * units_per_launch
+    return None
 
 
 def parse_args():
@@ -167,14 +192,40 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle, one right-hand side per process
 # ---------------------------------------------------------------------------
+# Above this many unknowns per solve the oracle is timed on its parts and
+# extrapolated (a full 4096^2 solve takes many minutes on one core).
+ORACLE_FULL_MAX = 1 << 21
+# FP64 PCG iteration counts (max over right-hand sides) of the large workloads,
+# as measured by the library's FP64 PCG (the oracle's algorithm, same count to
+# +-1), for the extrapolation when no GPU count is at hand (reference arm).
+ORACLE_ITERS_HINT = {"large_4096_m16": 87}
+
+
 def _oracle_one(args):
     """Oracle PCG solves by one worker: right-hand sides (or, for single-source
     workloads, seeded instances) j, j + stride, ... until min_s seconds have
-    passed (at least one)."""
-    name, j, stride, min_s, bc_z = args
+    passed (at least one).  Large grids: one operator set-up, one A y and one
+    B^-1 v are timed, and the solve time is extrapolated to `iters_hint`
+    iterations (each one A p and one B^-1 r, plus the initial pair)."""
+    name, j, stride, min_s, bc_z, iters_hint = args
+    import numpy as np
     import oracle as O
     nr, nz, med = workload(name)
     single = med.n_rhs == 1
+    if nr * nz > ORACLE_FULL_MAX:
+        g = O.Grid(nr, nz, bc_z=bc_z)
+        kr, kz, q, f = O.sample_medium(med, g, rhs_index=[j % med.n_rhs])
+        t0 = time.perf_counter()
+        op = O.Operator(kr, kz, q, g)
+        t1 = time.perf_counter()
+        y = op.apply_A(f[0])
+        t2 = time.perf_counter()
+        z = op.apply_Binv(y)
+        t3 = time.perf_counter()
+        assert np.isfinite(z).all()
+        est = (t1 - t0) + (iters_hint + 1) * ((t2 - t1) + (t3 - t2))
+        return {"unknowns": nr * nz, "iters": [iters_hint], "solves": 1, "est_s": est,
+                "parts_s": [t1 - t0, t2 - t1, t3 - t2]}
     t0 = time.perf_counter()
     unknowns, iters, solves, k = 0, [], 0, j
     while True:
@@ -201,14 +252,14 @@ def oracle_pool(cores: int):
     return mp.get_context("spawn").Pool(cores)
 
 
-def cpu_baseline(name: str, cores: int, pool=None, bc_z: int = 0):
+def cpu_baseline(name: str, cores: int, pool=None, bc_z: int = 0, iters_hint: int = 0):
     """Solves `cores` right-hand sides of the workload, one per core, with the
     oracle's PCG; returns unknowns solved per second of wall time."""
     own = pool is None
     pool = pool or oracle_pool(cores)
     try:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_one, [(name, j, cores, 2.0, bc_z) for j in range(cores)])
+        res = pool.map(_oracle_one, [(name, j, cores, 2.0, bc_z, iters_hint) for j in range(cores)])
         wall = time.perf_counter() - t0
     finally:
         if own:
@@ -217,6 +268,15 @@ def cpu_baseline(name: str, cores: int, pool=None, bc_z: int = 0):
     unknowns = sum(r["unknowns"] for r in res)
     solves = sum(r["solves"] for r in res)
     its = [i for r in res for i in r["iters"]]
+    if "est_s" in res[0]:
+        est = max(r["est_s"] for r in res)
+        parts = res[0]["parts_s"]
+        return {"value": unknowns / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"extrapolated: {cores} right-hand sides of {name}, one per host core; each core timed "
+                          f"its operator set-up ({parts[0]:.1f} s), one A y ({parts[1]:.2f} s) and one B^-1 v "
+                          f"({parts[2]:.1f} s) and the solve was taken as set-up + {iters_hint + 1} x (A + B^-1), "
+                          f"{iters_hint} being the GPU FP64 PCG iteration count; sample wall {wall:.1f} s",
+                "wall_s": est, "unknowns": unknowns, "extrapolated": True}
     return {"value": unknowns / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{solves} solves of {name} ({solves // cores}+ per host core, one process each), FP64 "
                       f"oracle PCG to {TOL:g} (set-up included), wall {wall:.1f} s, iterations "
@@ -233,10 +293,10 @@ def run_reference(args):
     try:
         # warm-up steps: a 64 x 64 solve per core (pool start-up, imports)
         for _ in range(args.warmup):
-            pool.map(_oracle_one, [("bumps_64", 0, 1, 0.0, 0)] * cores)
+            pool.map(_oracle_one, [("bumps_64", 0, 1, 0.0, 0, 0)] * cores)
         times, units = [], 0
         for _ in range(args.steps):
-            r = cpu_baseline(args.workload, cores, pool, args.bc_z)
+            r = cpu_baseline(args.workload, cores, pool, args.bc_z, ORACLE_ITERS_HINT.get(args.workload, 0))
             times.append(r["wall_s"])
             units += r["unknowns"]
         total = sum(times)
@@ -575,8 +635,10 @@ def main():
     cpu = None
     if pool is not None:
         try:
-            cpu = cpu_baseline(args.workload, cores, pool, args.bc_z)
+            hint = plain["iters_max"] if plain else ORACLE_ITERS_HINT.get(args.workload, max(iters))
+            cpu = cpu_baseline(args.workload, cores, pool, args.bc_z, hint)
             cpu.pop("wall_s", None)
+            cpu.pop("unknowns", None)
         finally:
             pool.close()
             pool.join()

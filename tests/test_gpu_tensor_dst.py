@@ -59,7 +59,7 @@ def _split_reference(x, n, three):
 
 
 @pytest.mark.parametrize("rows,nz", [(300, 1024), (129, 200), (7, 31), (128, 256), (1, 1), (5, 2), (3, 9),
-                                     (130, 65), (64, 127), (260, 2048)])
+                                     (130, 65), (64, 127), (260, 2048), (40, 4096), (9, 3001)])
 @pytest.mark.parametrize("prec", [P.AX_PREC_FP32_TC, P.AX_PREC_FP32_TC3])
 def test_tensor_transform_matches_split_products(cuda, rows, nz, prec):
     op, _, _ = _op(max(rows, 2), nz, cuda)
@@ -128,7 +128,7 @@ def test_mixed_pcg_with_tensor_transform_meets_tolerance(cuda, form):
 
 
 def test_tensor_option_rejects_long_columns(cuda):
-    op, _, _ = _op(4, 2100, cuda)
+    op, _, _ = _op(4, 4100, cuda)
     with pytest.raises(P.AxError):
         P.ax_set_option(op, "dst_tensor", 1)
     P.ax_destroy_operator(op)
