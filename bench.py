@@ -56,9 +56,12 @@ TC_CLASSES = ("dst_forward", "dst_inverse")
 # (file, __global__ function or None for the whole file), plus the shared
 # device helpers.
 KERNEL_SOURCES = {"stencil": [("ax_stencil.cu", "stencil_kernel")],
-                  "dst_forward": [("ax_dst_impl.cuh", None), ("ax_dst_gemm.cu", None)],
-                  "dst_inverse": [("ax_dst_impl.cuh", None), ("ax_dst_gemm.cu", None)],
+                  "dst_forward": [("ax_dst_impl.cuh", None)],
+                  "dst_inverse": [("ax_dst_impl.cuh", None)],
+                  "dst_forward_tc": [("ax_dst_gemm.cu", None)],
+                  "dst_inverse_tc": [("ax_dst_gemm.cu", None)],
                   "mode_solve": [("ax_tridiag.cu", "tridiag_reg_kernel")],
+                  "mode_solve_tall": [("ax_tridiag.cu", "tridiag_kernel")],
                   "outer_residual": [("ax_stencil.cu", "residual_df_kernel")],
                   "pcg_update": [("ax_solver.cu", "pcg_update")]}
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic_per_unknown.md")
@@ -616,7 +619,10 @@ def main():
         bytes_per_launch = units_per_launch * per_u + (nr * nz) * per_m
         avg_s = p["ms"] / p["launches"] / 1000.0
         achieved = bytes_per_launch / avg_s / 1e9
-        traffic = measured_traffic(top, units_per_launch)
+        variant = top + ("_tc" if tc_path and top in TC_CLASSES else "")
+        if top == "mode_solve" and nr > 1024:
+            variant = "mode_solve_tall"  # the FP32 register kernel covers nr <= 1024
+        traffic = measured_traffic(variant, units_per_launch)
         roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",

@@ -152,7 +152,7 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    (two products; a fixed symmetric matrix within ~3e-3 of
  *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
  *                    close to B^-1); 0: the FFT transform.  Default: 1 when
- *                    nz <= 2048 and the FFT length nz + 1 has a prime factor
+ *                    nz <= 4096 and the FFT length nz + 1 has a prime factor
  *                    above 7 (e.g. 1025 = 5^2 41), else 0.  Accepted for
  *                    nz <= 4096 and bc_z = 0, else AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32

@@ -978,9 +978,6 @@ int dst_blocks(const ax_operator *op, int rows, int bytes) {
 
 // ---- tensor-core transform (FP32 path, nz <= kMaxTcN) ----------------------
 constexpr int kMaxTcN = 4096;
-// Longest column the tensor-core transform is chosen for by default (its cost
-// grows as nz^2 per row, the FFT's as nz log nz).
-constexpr int kAutoTcN = 2048;
 
 // BF16 DST-matrix tiles per (device, nz), built on first use and kept for the
 // life of the process (shared by every operator with that nz); and one device
@@ -1742,7 +1739,7 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   // needs a prime radix above 8 (paired direct DFT or Rader stages, several
   // times the work of the small radices) and nz is within the GEMM's range.
   op->dst_tc = 0;
-  if (nz <= kAutoTcN && !cosine)
+  if (nz <= kMaxTcN && !cosine)
     for (int i = 0; i < op->plan.nstages; ++i)
       if (op->plan.radix[i] > 8) op->dst_tc = 1;
 
