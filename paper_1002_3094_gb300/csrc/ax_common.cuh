@@ -112,4 +112,22 @@ __device__ __forceinline__ void split_store8(unsigned char *split, int m, int ro
   *reinterpret_cast<uint2 *>(to + kSplitTileBytes / 2) = make_uint2(bf16_pack2(lo[1], lo[3]), bf16_pack2(lo[5], lo[7]));
 }
 
+// Writes the 4 consecutive columns col .. col + 3 (col % 4 == 0) of one row:
+// the 2 even ones and the 2 odd ones each as 4 bytes of high and of low parts.
+__device__ __forceinline__ void split_store4(unsigned char *split, int m, int row, int col, int mtiles, int ktiles,
+                                             int kbe, const float (&x)[4]) {
+  float hi[4], lo[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    hi[e] = bf16_round(x[e]);
+    lo[e] = x[e] - hi[e];
+  }
+  unsigned char *te = split + split_byte(m, row, split_pos(col, kbe), mtiles, ktiles);
+  unsigned char *to = split + split_byte(m, row, split_pos(col + 1, kbe), mtiles, ktiles);
+  *reinterpret_cast<unsigned *>(te) = bf16_pack2(hi[0], hi[2]);
+  *reinterpret_cast<unsigned *>(te + kSplitTileBytes / 2) = bf16_pack2(lo[0], lo[2]);
+  *reinterpret_cast<unsigned *>(to) = bf16_pack2(hi[1], hi[3]);
+  *reinterpret_cast<unsigned *>(to + kSplitTileBytes / 2) = bf16_pack2(lo[1], lo[3]);
+}
+
 }  // namespace ax

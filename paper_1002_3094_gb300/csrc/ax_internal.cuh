@@ -304,5 +304,8 @@ template <typename T>
 void launch_tridiag(const TriArgs<T> &a, cudaStream_t s);
 // whether launch_tridiag<float> can write the split layout for these sizes
 bool tridiag_split_ok(int nr);
+// mode columns per CTA of the FP32 register kernel for nr rows (0: not used);
+// its (in, out) partials come in ceil(nz / cols) slots per right-hand side
+int tridiag_reg_cols(int nr);
 
 }  // namespace ax

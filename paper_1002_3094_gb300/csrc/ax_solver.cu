@@ -1098,14 +1098,16 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
 }
 
 // Where the (r, z) partials of the tensor-core path come from: the mode solves
-// (column groups of 8) when the tile kernel runs, else the inverse transform.
+// (one per column group of the register kernel) when it runs, else the inverse
+// transform.
 bool tc_dot_in_modes(const ax_operator *op) { return tridiag_split_ok(op->nr); }
 
 // Number of (r, z) partial slots per RHS that precond_apply writes.
 template <typename T>
 int precond_partials(const ax_operator *op) {
   if (use_tc<T>(op))
-    return tc_dot_in_modes(op) ? (op->nz + 7) / 8 : dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
+    return tc_dot_in_modes(op) ? (op->nz + tridiag_reg_cols(op->nr) - 1) / tridiag_reg_cols(op->nr)
+                               : dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
   return dst_blocks(op, op->nr, (int)sizeof(T));
 }
 

@@ -181,14 +181,11 @@ __global__ void __launch_bounds__(1024) tridiag_kernel(const TriArgs<T> a, int W
   }
 }
 
-// Tiles of the register kernel below: a CTA stages an nr x kTileCW column tile
-// in shared memory; idx(row, col) = row kTileCW + col + row / C is padded by
-// one word per chunk of C rows, so the lanes of a warp (rows c C + t of one
-// column, c = lane) fall in distinct banks: the bank is ((8 C + 1) c + 8 t +
-// col) mod 32 for kTileCW = 8, and 8 C + 1 is odd.
-constexpr int kTileCW = 8;   // columns per CTA (one 32-byte sector per row)
-
-__device__ __forceinline__ int tidx(int row, int col, int C) { return row * kTileCW + col + row / C; }
+// Tiles of the register kernel below: a CTA stages an nr x CW column tile in
+// shared memory; idx(row, col) = row CW + col + row / C2 is padded by one word
+// per chunk of C2 rows, so the lanes of a warp (rows c C2 + t of one column,
+// c = lane) fall in distinct banks: the bank is ((CW C2 + 1) c + CW t + col)
+// mod 32, and CW C2 + 1 is odd.
 
 // 4-byte asynchronous global -> shared copy (zero fill when !ok); the whole
 // tile is in flight at once instead of one row per round trip.
@@ -198,49 +195,56 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Tiled FP32 kernel (nr <= 64 C2, C2 <= 16): a CTA stages an nr x 8 column
+// Register kernel (FP32, nr <= 32 WPC C2): a CTA stages an nr x CW column
 // tile of IP, the couplings E and the data of one right-hand side in shared
-// memory (cp.async, padded to 64 chunks of C2 rows with one word per chunk);
-// one column system per PAIR of warps, lane c of warp h owning rows
-// (32 h + c) C2 .. (32 h + c) C2 + C2 - 1, so a chunk, its alpha_t =
+// memory (cp.async, padded to 32 WPC chunks of C2 rows with one word per
+// chunk); one column system per group of WPC warps, lane c of warp h owning
+// rows (32 h + c) C2 .. (32 h + c) C2 + C2 - 1, so a chunk, its alpha_t =
 // -E_{t-1} ip_t and beta_t = -E_t ip_t stay in registers after one pass over
 // the shared tile.  The affine carry maps of the chunks are composed with
-// shuffles inside each warp and through one shared word per pair between the
-// two warps.  Padding rows carry IP = E = 0 and solve to zero, so every lane
-// runs the same unpredicated recurrences.  For the tensor-core transform the
-// result is written in the BF16 split layout.
-template <int C2>
-__global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float> a) {
-  constexpr int NP = 64 * C2;
-  constexpr int kTileWords = NP * kTileCW + 64;
-  constexpr int kEWords = NP + 64;
+// shuffles inside each warp, and the WPC warp totals of a column through
+// shared memory.  Padding rows carry IP = E = 0 and solve to zero, so every
+// lane runs the same unpredicated recurrences.  For the tensor-core transform
+// the result is written in the BF16 split layout.
+// Shapes: <C2, 2, 8> for nr <= 64 C2 (C2 = 4, 8, 16), <16, 4, 8> for
+// nr <= 2048 and <16, 8, 4> for nr <= 4096 (1024 threads).
+template <int C2, int WPC, int CW>
+__global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
+    tridiag_reg_kernel(const TriArgs<float> a) {
+  constexpr int NT = 32 * WPC * CW;  // threads
+  constexpr int NCH = 32 * WPC;      // chunks per column
+  constexpr int NP = NCH * C2;       // padded rows
+  constexpr int kTileWords = NP * CW + NCH;
+  constexpr int kEWords = NP + NCH;
+  static_assert(NT <= 1024 && (CW == 4 || CW == 8), "tile shape");
   extern __shared__ __align__(16) float tsm[];
-  __shared__ float xfer[kTileCW][2];  // per column: forward total of warp 0, backward total of warp 1
+  // per column and warp: the warp's composed map (A, M), forward and backward
+  __shared__ float xfa[CW][WPC], xfm[CW][WPC], xba[CW][WPC], xbm[CW][WPC];
   const int nr = a.nr, pitch = a.pitch;
   float *ips = tsm;
   float *ea = ips + kTileWords;
   float *eb = ea + kEWords;
   float *ds = eb + kEWords;
-  const int col0 = blockIdx.x * kTileCW;
+  const int col0 = blockIdx.x * CW;
   const int m = blockIdx.y;
-  const int ncol = min(kTileCW, a.nz - col0);
+  const int ncol = min(CW, a.nz - col0);
   if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
   // ---- stage the tiles (coalesced rows, cp.async) ----
-  const int cw = threadIdx.x % kTileCW;
+  const int cw = threadIdx.x % CW;
   {
     const bool colok = cw < ncol;
     const int cc = colok ? cw : 0;
     const float *ipg = a.IP + (size_t)m * a.cstride + col0 + cc;
     const float *ing = a.in + (size_t)m * a.field + col0 + cc;
-    for (int row = threadIdx.x / kTileCW; row < NP; row += blockDim.x / kTileCW) {
+    for (int row = threadIdx.x / CW; row < NP; row += NT / CW) {
       const bool ok = colok && row < nr;
       const int rs = ok ? row : 0;
-      const int si = tidx(row, cw, C2);
+      const int si = row * CW + cw + row / C2;
       cp_async4(ips + si, ipg + (size_t)rs * pitch, ok);
       cp_async4(ds + si, ing + (size_t)rs * pitch, ok);
     }
     const float *eg = a.E + (size_t)m * a.estride;
-    for (int row = threadIdx.x; row < NP; row += blockDim.x) {
+    for (int row = threadIdx.x; row < NP; row += NT) {
       const int ei = row + row / C2;
       cp_async4(ea + ei, eg + (row > 0 && row - 1 < nr ? row - 1 : 0), row > 0 && row - 1 < nr);
       cp_async4(eb + ei, eg + (row < nr ? row : 0), row < nr);
@@ -249,11 +253,11 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = warp >> 1, h = warp & 1;  // column, half of the r-range
-  const int ci = h * 32 + lane;           // chunk index 0 .. 63
+  const int w = warp / WPC, h = warp % WPC;  // column, segment of the r-range
+  const int ci = h * 32 + lane;               // chunk index 0 .. NCH - 1
   const bool active = w < ncol;
-  float *pd = ds + ci * (kTileCW * C2 + 1) + w;
-  const float *pip = ips + ci * (kTileCW * C2 + 1) + w;
+  float *pd = ds + ci * (CW * C2 + 1) + w;
+  const float *pip = ips + ci * (CW * C2 + 1) + w;
   const float *pea = ea + ci * (C2 + 1);
   const float *peb = eb + ci * (C2 + 1);
   float v[C2], al[C2], be[C2];
@@ -261,10 +265,10 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
   float g = 0.f, mu = 1.f;
 #pragma unroll
   for (int t = 0; t < C2; ++t) {
-    const float ip = pip[kTileCW * t];
+    const float ip = pip[CW * t];
     al[t] = -pea[t] * ip;
     be[t] = -peb[t] * ip;
-    g = fmaf(pd[kTileCW * t], ip, al[t] * g);
+    g = fmaf(pd[CW * t], ip, al[t] * g);
     mu *= al[t];
     v[t] = g;
   }
@@ -283,9 +287,15 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
     Ae = 0.f;
     Me = 1.f;
   }
-  if (h == 0 && lane == 31 && active) xfer[w][0] = A;  // carry out of rows 0 .. 32 C2 - 1
+  if (lane == 31 && active) {  // map of all 32 chunks of this warp
+    xfa[w][h] = A;
+    xfm[w][h] = M;
+  }
   __syncthreads();
-  const float gin = (h == 0) ? Ae : fmaf(Me, active ? xfer[w][0] : 0.f, Ae);
+  float cin = 0.f;  // carry into this warp's first chunk: the maps of warps 0 .. h-1
+  if (active)
+    for (int j = 0; j < h; ++j) cin = fmaf(xfm[w][j], cin, xfa[w][j]);
+  const float gin = fmaf(Me, cin, Ae);
   mu = 1.f;
 #pragma unroll
   for (int t = 0; t < C2; ++t) {
@@ -317,9 +327,15 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
     Ae = 0.f;
     Me = 1.f;
   }
-  if (h == 1 && lane == 0 && active) xfer[w][1] = A;  // carry into row 32 C2 - 1 from above
+  if (lane == 0 && active) {  // map of all 32 chunks of this warp, from its last row up
+    xba[w][h] = A;
+    xbm[w][h] = M;
+  }
   __syncthreads();
-  const float yin = (h == 1) ? Ae : fmaf(Me, active ? xfer[w][1] : 0.f, Ae);
+  cin = 0.f;  // carry into this warp's last chunk: the maps of warps WPC-1 .. h+1
+  if (active)
+    for (int j = WPC - 1; j > h; --j) cin = fmaf(xbm[w][j], cin, xba[w][j]);
+  const float yin = fmaf(Me, cin, Ae);
   mu = 1.f;
 #pragma unroll
   for (int t = C2 - 1; t >= 0; --t) {
@@ -330,38 +346,39 @@ __global__ void __launch_bounds__(512, 2) tridiag_reg_kernel(const TriArgs<float
   if (active) {
 #pragma unroll
     for (int t = 0; t < C2; ++t) {
-      dot = fmaf(pd[kTileCW * t], v[t], dot);  // (input, solution) of this chunk
-      pd[kTileCW * t] = v[t];
+      dot = fmaf(pd[CW * t], v[t], dot);  // (input, solution) of this chunk
+      pd[CW * t] = v[t];
     }
   }
   if (a.partial != nullptr) {
-    __shared__ double red[16];
+    __shared__ double red[NT / 32];
     const double sw = warp_sum((double)dot);
     if (lane == 0) red[warp] = sw;
     __syncthreads();
     if (threadIdx.x == 0) {
       double tot = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+      for (int i = 0; i < NT / 32; ++i) tot += red[i];
       a.partial[(size_t)m * kPartialStride + blockIdx.x] = tot;
     }
   }
   __syncthreads();
-  // ---- write back: one thread per row, its 8 columns at once ----
-  // (8 shared loads with a 4-way bank conflict, but every lane does useful
-  // work; rows go to 32-byte segments of the output, or to the even and odd
-  // halves of the split layout)
-  for (int row = threadIdx.x; row < nr; row += blockDim.x) {
-    float x[8];
-    const int r0 = row * kTileCW + row / C2;
+  // ---- write back: one thread per row, its CW columns at once ----
+  // (CW shared loads with a 4-way bank conflict, but every lane does useful
+  // work; rows go to 16- or 32-byte segments of the output, or to the even
+  // and odd halves of the split layout)
+  for (int row = threadIdx.x; row < nr; row += NT) {
+    float x[CW];
+    const int r0 = row * CW + row / C2;
 #pragma unroll
-    for (int c = 0; c < kTileCW; ++c) x[c] = ds[r0 + c];
+    for (int c = 0; c < CW; ++c) x[c] = ds[r0 + c];
     if (a.split != nullptr) {
-      split_store8(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      if constexpr (CW == 8) split_store8(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      else split_store4(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
     } else {
       float *o = a.out + (size_t)m * a.field + (size_t)row * pitch + col0;
-      if (ncol == kTileCW) {
-        *reinterpret_cast<float4 *>(o) = make_float4(x[0], x[1], x[2], x[3]);
-        *reinterpret_cast<float4 *>(o + 4) = make_float4(x[4], x[5], x[6], x[7]);
+      if (ncol == CW) {
+#pragma unroll
+        for (int c = 0; c < CW; c += 4) *reinterpret_cast<float4 *>(o + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
       } else {
         for (int c = 0; c < ncol; ++c) o[c] = x[c];
       }
@@ -393,26 +410,32 @@ void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
   tridiag_kernel<T, C><<<grid, W * P, smem, s>>>(a, W, P);
 }
 
-template <int C2>
+template <int C2, int WPC, int CW>
 void launch_tridiag_reg(const TriArgs<float> &a, cudaStream_t s) {
   // mirrors the kernel's layout: the IP and data tiles and the two E arrays
-  const size_t smem = sizeof(float) * (2 * (64 * C2 * kTileCW + 64) + 2 * (64 * C2 + 64));
-  ensure_smem_attr((const void *)tridiag_reg_kernel<C2>, smem);
-  dim3 grid((a.nz + kTileCW - 1) / kTileCW, a.m);
-  tridiag_reg_kernel<C2><<<grid, 64 * kTileCW, smem, s>>>(a);
+  constexpr int NCH = 32 * WPC, NP = NCH * C2;
+  const size_t smem = sizeof(float) * (2 * (NP * CW + NCH) + 2 * (NP + NCH));
+  ensure_smem_attr((const void *)tridiag_reg_kernel<C2, WPC, CW>, smem);
+  dim3 grid((a.nz + CW - 1) / CW, a.m);
+  tridiag_reg_kernel<C2, WPC, CW><<<grid, 32 * WPC * CW, smem, s>>>(a);
 }
 
+// Columns per CTA of the register kernel for nr rows (0: not covered).
+int tridiag_reg_cols(int nr) { return nr <= 2048 ? 8 : (nr <= 4096 ? 4 : 0); }
+
 bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
-  // two warps per column system, chunks of up to 16 rows in registers
+  // chunks of up to 16 rows in registers; 2, 4 or 8 warps per column system
   const int c2 = (a.nr + 63) / 64;
-  if (c2 <= 4) launch_tridiag_reg<4>(a, s);
-  else if (c2 <= 8) launch_tridiag_reg<8>(a, s);
-  else if (c2 <= 16) launch_tridiag_reg<16>(a, s);
+  if (c2 <= 4) launch_tridiag_reg<4, 2, 8>(a, s);
+  else if (c2 <= 8) launch_tridiag_reg<8, 2, 8>(a, s);
+  else if (c2 <= 16) launch_tridiag_reg<16, 2, 8>(a, s);
+  else if (a.nr <= 2048) launch_tridiag_reg<16, 4, 8>(a, s);
+  else if (a.nr <= 4096) launch_tridiag_reg<16, 8, 4>(a, s);
   else return false;
   return true;
 }
 
-bool tridiag_split_ok(int nr) { return nr <= 32 * 32; }
+bool tridiag_split_ok(int nr) { return tridiag_reg_cols(nr) != 0; }
 
 template <typename T>
 void launch_tridiag(const TriArgs<T> &a, cudaStream_t s) {

@@ -98,9 +98,11 @@ def test_tensor_preconditioner_symmetric_and_close(cuda):
 
 
 @pytest.mark.parametrize("form", [1, 2])
-def test_mixed_pcg_with_tensor_transform_meets_tolerance(cuda, form):
-    nr, nz = 160, 144
-    med = layered_inclusion_medium(n_rhs=4, nominal_n=160)
+@pytest.mark.parametrize("nr,nz", [(160, 144), (1500, 130), (3000, 72)])
+def test_mixed_pcg_with_tensor_transform_meets_tolerance(cuda, form, nr, nz):
+    """Also for tall grids, whose mode solves run 4 or 8 warps per column
+    (nr > 1024) and still write the split operand and the (r, z) partials."""
+    med = layered_inclusion_medium(n_rhs=4, nominal_n=max(nr, nz))
     kr, kz, q = sample_operator_inputs(med, nr, nz)
     op = P.ax_setup_operator(*[torch.from_numpy(x).to(cuda) for x in (kr, kz, q)], nr, nz)
     g = O.Grid(nr, nz)
