@@ -47,6 +47,12 @@ TOL = 1e-8
 ALG_BYTES = {"stencil": (16.0, 12.0), "dst_forward": (28.0, 0.0), "mode_solve": (8.0, 4.0),
              "dst_inverse": (12.0, 0.0), "outer_residual": (20.0, 24.0), "pcg_update": (28.0, 0.0)}
 ALG_BYTES_TC = dict(ALG_BYTES, dst_forward=(8.0, 0.0), dst_inverse=(8.0, 0.0))
+# Fused tensor-core iteration of the mixed PCG (nr <= 4096): the inverse
+# transform's epilogue forms p = z + beta p and x += alpha p_old, so
+#   stencil (q = A p): read p, write q -> 8 B, + CR, CZ, W (12 B / M)
+#   update pass (r -= a q): read r, q; write r and its split -> 16 B
+#   inverse transform: read split yhat, p_old, x; write p_new, x -> 20 B
+ALG_BYTES_FUSED = dict(ALG_BYTES_TC, stencil=(8.0, 12.0), pcg_update=(16.0, 0.0), dst_inverse=(20.0, 0.0))
 # Tensor-core transform: multiply-adds per row = products x n^2 / 2 (even / odd
 # halves), 2 flops each.
 TC_CLASSES = ("dst_forward", "dst_inverse")
@@ -344,6 +350,9 @@ def run_batched(args):
         fs.append(torch.from_numpy(sample_rhs(med, nr, nz, bc_z=args.bc_z)[0]).to(dev))
         us.append(torch.zeros((nr, nz), dtype=torch.float64, device=dev))
         unknowns += nr * nz
+    if args.dst_tensor >= 0:
+        for op in ops:
+            P.ax_set_option(op, "dst_tensor", args.dst_tensor)
     batch = P.ax_batch_create(ops)
     method = P.METHODS[args.method]
     stream = torch.cuda.current_stream()
@@ -607,7 +616,8 @@ def main():
     tc_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     tc_path = prof.get("pcg_update", {}).get("launches", 0) > 0  # the tensor-core transform is in use
     products = 2 if args.dst_tensor == 2 else 3
-    alg = ALG_BYTES_TC if tc_path else ALG_BYTES
+    fused = tc_path and args.method == "pcg_mixed" and nr <= 4096
+    alg = ALG_BYTES_FUSED if fused else (ALG_BYTES_TC if tc_path else ALG_BYTES)
     roof = None
     cand = {k: v for k, v in prof.items() if k in alg and v["launches"] > 0}
     if cand:

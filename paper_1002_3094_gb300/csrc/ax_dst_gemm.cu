@@ -285,6 +285,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
     // warp w drains TMEM lane quarter w % 4, columns half (w - 4) / 4 of P and Q
     const int ew = warp - 4;
     const int q = warp & 3, half = ew >> 2;
+    // per epilogue warp a 32 x 32 FP32 transpose tile behind the stages
+    float *epi = reinterpret_cast<float *>(gsm + kStages * kStageBytes);
     const int n = a.n, ne = (n + 1) >> 1;
     int it = 0;  // tiles processed so far, as counted by the MMA issuer
     for (int t = blockIdx.x; t < ntile_all; t += gridDim.x) {
@@ -302,9 +304,28 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
       const int grow = mt * kBM + q * 32 + lane;
       float acc = 0.f;
       if (__all_sync(0xffffffffu, ok)) {
-        float *outr = a.out + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
-        const float *rr =
-            (a.r != nullptr) ? a.r + (size_t)m * (size_t)a.field + (size_t)grow * a.pitch : nullptr;
+        const size_t roff = (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
+        const bool pupd = a.pa != nullptr;
+        float *outr = pupd ? nullptr : a.out + roff;
+        const float *rr = (a.r != nullptr) ? a.r + roff : nullptr;
+        // direction update: p_new = out + beta p_old (and x += alpha p_old)
+        float *por = nullptr, *pnr = nullptr, *xr = nullptr;
+        const float *pog = nullptr;
+        float *png = nullptr, *xg = nullptr;
+        float beta = 0.f, alpha = 0.f;
+        if (pupd) {
+          const bool odd = a.st[m].iters & 1;
+          pog = odd ? a.pb : a.pa;
+          png = odd ? a.pa : a.pb;
+          por = const_cast<float *>(pog) + roff;
+          pnr = png + roff;
+          beta = (float)a.st[m].beta;
+          if (a.x != nullptr) {
+            xg = a.x;
+            xr = a.x + roff;
+            alpha = (float)a.st[m].alpha;
+          }
+        }
         const unsigned tP = tmem + ((unsigned)(q * 32) << 16) + (unsigned)b * kTileCols;
 #pragma unroll 1
         for (int c = half * 2; c < half * 2 + 2; ++c) {
@@ -317,6 +338,63 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
+          }
+          if (rr == nullptr) {
+            // Write-back transposed through this warp's 32 x 32 shared tile
+            // (XOR-swizzled: conflict-free in both directions), so that every
+            // global access of the warp is a run of 32 consecutive columns of
+            // one row: first the columns l0 + j (P + Q), then their mirrors
+            // n - 1 - l0 - j (P - Q).  The direction update loads all 32 rows
+            // of p_old (and x) before it uses them, so that the warp has its
+            // whole tile of loads in flight at once.
+            float *T = epi + ew * 1024;
+            const int row0 = mt * kBM + q * 32;
+            const size_t mbase = (size_t)m * (size_t)a.field;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              T[lane * 32 + (i ^ lane)] = P[i] + Q[i];
+              P[i] -= Q[i];  // P now holds the mirrored half
+            }
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+              if (pass == 1) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = P[i];
+              }
+              __syncwarp();
+              const int lc = l0 + lane;                 // column of the half range
+              const int col = pass ? n - 1 - lc : lc;   // output column
+              const bool colok = lc < ne && (pass == 0 || col != lc);  // middle column of odd n once
+              const size_t cbase = mbase + (size_t)row0 * a.pitch + col;
+              if (pupd) {
+#pragma unroll 1
+                for (int h = 0; h < 32; h += 16) {
+                  float po[16], xv[16];
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) {
+                    const int r = h + j;
+                    const bool ok = colok && row0 + r < a.nr;
+                    po[j] = ok ? __ldg(pog + cbase + (size_t)r * a.pitch) : 0.f;
+                    xv[j] = (ok && xg) ? xg[cbase + (size_t)r * a.pitch] : 0.f;
+                  }
+#pragma unroll
+                  for (int j = 0; j < 16; ++j) {
+                    const int r = h + j;
+                    if (colok && row0 + r < a.nr) {
+                      const size_t e = cbase + (size_t)r * a.pitch;
+                      png[e] = fmaf(beta, po[j], T[r * 32 + (lane ^ r)]);
+                      if (xg) xg[e] = fmaf(alpha, po[j], xv[j]);
+                    }
+                  }
+                }
+              } else {
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r)
+                  if (colok && row0 + r < a.nr) a.out[cbase + (size_t)r * a.pitch] = T[r * 32 + (lane ^ r)];
+              }
+              __syncwarp();
+            }
+            continue;
           }
           if (grow < a.nr) {
 #pragma unroll
@@ -332,8 +410,29 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
                 // n % 4 == 0: both runs are whole aligned float4 groups, and the
                 // mirrored one (columns n - 4 - l .. n - 1 - l) lies above ne
                 const int lm = n - 4 - l;
-                *reinterpret_cast<float4 *>(outr + l) = make_float4(s0[0], s0[1], s0[2], s0[3]);
-                *reinterpret_cast<float4 *>(outr + lm) = make_float4(d0[3], d0[2], d0[1], d0[0]);
+                if (pupd) {
+                  const float4 pa4 = *reinterpret_cast<const float4 *>(por + l);
+                  const float4 pb4 = *reinterpret_cast<const float4 *>(por + lm);
+                  *reinterpret_cast<float4 *>(pnr + l) =
+                      make_float4(fmaf(beta, pa4.x, s0[0]), fmaf(beta, pa4.y, s0[1]), fmaf(beta, pa4.z, s0[2]),
+                                  fmaf(beta, pa4.w, s0[3]));
+                  *reinterpret_cast<float4 *>(pnr + lm) =
+                      make_float4(fmaf(beta, pb4.x, d0[3]), fmaf(beta, pb4.y, d0[2]), fmaf(beta, pb4.z, d0[1]),
+                                  fmaf(beta, pb4.w, d0[0]));
+                  if (xr) {
+                    float4 xa = *reinterpret_cast<const float4 *>(xr + l);
+                    float4 xb = *reinterpret_cast<const float4 *>(xr + lm);
+                    xa.x = fmaf(alpha, pa4.x, xa.x); xa.y = fmaf(alpha, pa4.y, xa.y);
+                    xa.z = fmaf(alpha, pa4.z, xa.z); xa.w = fmaf(alpha, pa4.w, xa.w);
+                    xb.x = fmaf(alpha, pb4.x, xb.x); xb.y = fmaf(alpha, pb4.y, xb.y);
+                    xb.z = fmaf(alpha, pb4.z, xb.z); xb.w = fmaf(alpha, pb4.w, xb.w);
+                    *reinterpret_cast<float4 *>(xr + l) = xa;
+                    *reinterpret_cast<float4 *>(xr + lm) = xb;
+                  }
+                } else {
+                  *reinterpret_cast<float4 *>(outr + l) = make_float4(s0[0], s0[1], s0[2], s0[3]);
+                  *reinterpret_cast<float4 *>(outr + lm) = make_float4(d0[3], d0[2], d0[1], d0[0]);
+                }
                 if (rr) {
                   const float4 ra = *reinterpret_cast<const float4 *>(rr + l);
                   const float4 rb = *reinterpret_cast<const float4 *>(rr + lm);
@@ -347,10 +446,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
                 for (int e = 0; e < 4; ++e) {
                   const int le = l + e, lm = n - 1 - le;
                   if (le < ne) {
-                    outr[le] = s0[e];
+                    if (pupd) {
+                      const float po = por[le];
+                      pnr[le] = fmaf(beta, po, s0[e]);
+                      if (xr) xr[le] = fmaf(alpha, po, xr[le]);
+                    } else {
+                      outr[le] = s0[e];
+                    }
                     if (rr) acc = fmaf(rr[le], s0[e], acc);
                     if (lm != le) {  // the middle column of odd n is written once
-                      outr[lm] = d0[e];
+                      if (pupd) {
+                        const float po = por[lm];
+                        pnr[lm] = fmaf(beta, po, d0[e]);
+                        if (xr) xr[lm] = fmaf(alpha, po, xr[lm]);
+                      } else {
+                        outr[lm] = d0[e];
+                      }
                       if (rr) acc = fmaf(rr[lm], d0[e], acc);
                     }
                   }
@@ -395,8 +506,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
 }  // namespace
 
 size_t dst_gemm_smem_bytes(int three) {
-  return three ? (size_t)GemmStages<1>::stages * GemmStages<1>::stage_bytes + 1024
-               : (size_t)GemmStages<0>::stages * GemmStages<0>::stage_bytes + 1024;
+  constexpr size_t kEpiBytes = (size_t)kEpiWarps * 32 * 32 * sizeof(float);  // transpose tiles
+  return (three ? (size_t)GemmStages<1>::stages * GemmStages<1>::stage_bytes
+                : (size_t)GemmStages<0>::stages * GemmStages<0>::stage_bytes) +
+         kEpiBytes + 1024;
 }
 
 // K tiles of even and of odd input columns.  The writers of the split operand

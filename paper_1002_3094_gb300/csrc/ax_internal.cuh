@@ -165,7 +165,7 @@ namespace ax {
 // ---------------------------------------------------------------------------
 
 // Stencil modes
-enum { kStencilApply = 0, kStencilPcg = 1, kStencilResidual = 2, kStencilCheb = 3 };
+enum { kStencilApply = 0, kStencilPcg = 1, kStencilResidual = 2, kStencilCheb = 3, kStencilPcgP = 4 };
 
 template <typename T>
 struct StencilArgs {
@@ -174,9 +174,11 @@ struct StencilArgs {
   int nr, nz, pitch, pitchz;
   long long field;       // elements per RHS (nr * pitch)
   int m;
-  const T *in;           // Apply: y.  Pcg: z.  Residual: x.  Cheb: y
+  const T *in;           // Apply: y.  Pcg: z.  Residual: x.  Cheb: y.  PcgP: unused (p by parity)
   T *pa, *pb;            // Pcg: the two search-direction buffers; an RHS with an even
-                         // iteration count reads pa and writes pb, an odd one the reverse
+                         // iteration count reads pa and writes pb, an odd one the reverse.
+                         // PcgP: p is already formed (by the inverse transform); q = A p
+                         // from pb (even count) or pa (odd)
   T *out;                // Apply: A y.  Pcg: q = A p_new.  Cheb: res = A y - phi
   const T *phi;          // Residual, Cheb: phi
   float *out32;          // Residual: phi - A x rounded to FP32 (may be null)
@@ -271,6 +273,13 @@ struct GemmDstArgs {
   const RhsState *st;
   int mask;
   int *err;                // set to 1 when a bounded wait expired
+  // PCG direction update in the epilogue (out is then not written): with
+  // p_old / p_new the two direction buffers by the parity of st[m].iters
+  // (odd: pb -> pa, even: pa -> pb), p_new = out + beta p_old, and with x
+  // also x += alpha p_old (the iterate update of the step that produced
+  // p_old); alpha and beta from st[m]
+  float *pa, *pb;
+  float *x;
 };
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);

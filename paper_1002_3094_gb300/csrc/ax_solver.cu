@@ -406,7 +406,8 @@ __global__ void fold_df(float *__restrict__ xh, float *__restrict__ xl, float *_
 // partials of ||r||^2 and the new r written split into BF16 halves for the
 // tensor-core transform: the update that the FFT forward transform fuses into
 // its load phase.  p is pb for an even iteration count, pa for an odd one (as
-// in the stencil).
+// in the stencil).  x == nullptr: r only (the iterate update then happens in
+// the inverse transform's epilogue, with the next direction).
 constexpr int kUpdateBlocks = 64;  // CTAs per right-hand side
 __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *__restrict__ r,
                                                   const float *__restrict__ q, const float *__restrict__ pa,
@@ -426,23 +427,27 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
     int row, col;
     split_task(t, nch, row, col);  // row < nr, col < n, col + 8 <= n rounded up to 8 <= pitch
     const size_t e = (size_t)m * field + (size_t)row * pitch + col;
-    float xv[8], pv[8], rv[8], qv[8];
-    *reinterpret_cast<float4 *>(xv) = *reinterpret_cast<const float4 *>(x + e);
-    *reinterpret_cast<float4 *>(xv + 4) = *reinterpret_cast<const float4 *>(x + e + 4);
-    *reinterpret_cast<float4 *>(pv) = *reinterpret_cast<const float4 *>(p + e);
-    *reinterpret_cast<float4 *>(pv + 4) = *reinterpret_cast<const float4 *>(p + e + 4);
+    float rv[8], qv[8];
     *reinterpret_cast<float4 *>(rv) = *reinterpret_cast<const float4 *>(r + e);
     *reinterpret_cast<float4 *>(rv + 4) = *reinterpret_cast<const float4 *>(r + e + 4);
     *reinterpret_cast<float4 *>(qv) = *reinterpret_cast<const float4 *>(q + e);
     *reinterpret_cast<float4 *>(qv + 4) = *reinterpret_cast<const float4 *>(q + e + 4);
+    if (x != nullptr) {
+      float xv[8], pv[8];
+      *reinterpret_cast<float4 *>(xv) = *reinterpret_cast<const float4 *>(x + e);
+      *reinterpret_cast<float4 *>(xv + 4) = *reinterpret_cast<const float4 *>(x + e + 4);
+      *reinterpret_cast<float4 *>(pv) = *reinterpret_cast<const float4 *>(p + e);
+      *reinterpret_cast<float4 *>(pv + 4) = *reinterpret_cast<const float4 *>(p + e + 4);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) xv[i] = fmaf(alpha, pv[i], xv[i]);
+      *reinterpret_cast<float4 *>(x + e) = *reinterpret_cast<const float4 *>(xv);
+      *reinterpret_cast<float4 *>(x + e + 4) = *reinterpret_cast<const float4 *>(xv + 4);
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      xv[i] = fmaf(alpha, pv[i], xv[i]);
       rv[i] = fmaf(-alpha, qv[i], rv[i]);
       acc = fmaf(rv[i], rv[i], acc);
     }
-    *reinterpret_cast<float4 *>(x + e) = *reinterpret_cast<const float4 *>(xv);
-    *reinterpret_cast<float4 *>(x + e + 4) = *reinterpret_cast<const float4 *>(xv + 4);
     *reinterpret_cast<float4 *>(r + e) = *reinterpret_cast<const float4 *>(rv);
     *reinterpret_cast<float4 *>(r + e + 4) = *reinterpret_cast<const float4 *>(rv + 4);
     split_store8(split, m, row, col, mtiles, ktiles, kbe, rv);
@@ -581,6 +586,12 @@ __global__ void sc_beta(RhsState *st, const double *p, int nb, int mask, int nex
       st[m].state = next_state;
     }
   }
+}
+
+// Right-hand sides (of n) in state `from` move to `to`.
+__global__ void sc_promote(RhsState *st, int n, int from, int to) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n && st[m].state == from) st[m].state = to;
 }
 
 // True-residual test of right-hand sides in kCheck.
@@ -1041,10 +1052,16 @@ SplitGeom split_geom(const ax_operator *op, int rows) {
 
 // Tensor-core transform of `rows` rows per RHS: out = A S for the selected
 // right-hand sides (A in the split layout); with r, the (r, out) partials
-// into `partial`.
+// into `partial`.  With pa, pb the result is not stored but forms the next
+// search direction p_new = out + beta p_old (and, with x, x += alpha p_old);
+// see GemmDstArgs.
 void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, float *out, const RhsState *st,
-                  int mask, const float *r, double *partial, cudaStream_t s, int three = -1) {
+                  int mask, const float *r, double *partial, cudaStream_t s, int three = -1, float *pa = nullptr,
+                  float *pb = nullptr, float *x = nullptr) {
   GemmDstArgs g{};
+  g.pa = pa;
+  g.pb = pb;
+  g.x = x;
   g.A = A;
   g.out = out;
   g.SB = tc_table(op->device, op->nz);
@@ -1149,9 +1166,18 @@ struct PcgVecs {
   T *x, *r, *pa, *pb, *q, *z;
 };
 
+// Whether the mixed PCG loop runs the fused tensor-core iteration: the inverse
+// transform's epilogue forms the next direction p = z + beta p and updates x
+// (beta is known before it because the mode solves give the (r, z) partials),
+// so z is never stored, the stencil reads p alone and the update pass only r.
+bool tc_fused(const ax_operator *op) { return use_tc<float>(op) && tc_dot_in_modes(op); }
+
+// One PCG iteration for the right-hand sides in kActive.  fused (FP32
+// tensor-core path with tc_fused only): p was formed by the previous
+// iteration's inverse transform (or the start), see tc_fused.
 template <typename T>
 void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *st, Workspace *w,
-                   int on_converge, cudaStream_t s, double units = 0.0) {
+                   int on_converge, cudaStream_t s, double units = 0.0, bool fused = false) {
   const int V = VecT<T>::n;
   const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
   const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
@@ -1162,7 +1188,10 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
   sa.pb = v.pb;
   sa.out = v.q;
   sa.partial = pq;
-  { ProfScope ps(w, kProfStencil, units, s); launch_stencil<T>(kStencilPcg, sa, s); }
+  {
+    ProfScope ps(w, kProfStencil, units, s);
+    launch_stencil<T>(fused ? kStencilPcgP : kStencilPcg, sa, s);
+  }
   {
     ProfScope ps(w, kProfScalar, 0.0, s);
     note_launch();
@@ -1177,9 +1206,9 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       {
         ProfScope ps(w, kProfUpdate, units, s);
         note_launch();
-        pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(v.x, v.r, v.q, v.pa, v.pb, op->nr, op->nz, op->pitch,
-                                                          field_elems(op), g.mtiles, g.ktiles, g.kbe, sp,
-                                                          st, kActive, prr);
+        pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(fused ? nullptr : v.x, v.r, v.q, v.pa, v.pb, op->nr,
+                                                          op->nz, op->pitch, field_elems(op), g.mtiles, g.ktiles,
+                                                          g.kbe, sp, st, kActive, prr);
       }
       { ProfScope ps(w, kProfDstFwd, units, s); tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s); }
       {
@@ -1191,6 +1220,16 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       {
         ProfScope ps(w, kProfTridiag, units, s);
         tc_mode_solve(op, m, v.z, v.q, sp, st, kActive, s, dm ? prz : nullptr);
+      }
+      if (fused) {
+        {
+          ProfScope ps(w, kProfScalar, 0.0, s);
+          note_launch();
+          sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op), kActive, kActive);
+        }
+        ProfScope ps(w, kProfDstInv, units, s);
+        tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s, -1, v.pa, v.pb, v.x);
+        return;
       }
       {
         ProfScope ps(w, kProfDstInv, units, s);
@@ -1511,12 +1550,27 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   // continues from.  Where the true residual differs from the recursive one
   // (kCheck), z and beta are recomputed from it.  Every kernel returns at once
   // for the others; no right-hand side waits for the host.
+  const bool fused = tc_fused(op);
   auto replace_step = [&](cudaStream_t ss) {
     note_launch();
     fold_df<<<zg, 256, 0, ss>>>(w->xh, w->xl, w->x32, field, st, kDue);
     residual64(kDue, ss);
     note_launch();
     sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbdf, tol * tol, delta * delta);
+    if (fused) {
+      // z = B^-1 r and beta from the true residual, then the direction of this
+      // step again, p_new = z + beta p_old (x already holds alpha p_old)
+      unsigned char *sp = w->split;
+      tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss);
+      tc_transform(op, m, op->nr, sp, v.z, st, kCheck, nullptr, nullptr, ss);
+      tc_mode_solve(op, m, v.z, v.q, sp, st, kCheck, ss, part_ptr(w, kPartC));
+      note_launch();
+      sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kCheck, 1);
+      tc_transform(op, m, op->nr, sp, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr);
+      note_launch();
+      sc_promote<<<(m + 31) / 32, 32, 0, ss>>>(st, m, kCheck, kActive);
+      return;
+    }
     precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss, v.q);
     note_launch();
     sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kActive, 1);
@@ -1535,6 +1589,9 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   note_launch();
   sc_rho_init<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, kActive);
   AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(float) * field * m, s));
+  // fused iteration: the first direction p_0 = z_0, where an even iteration
+  // count finds it (pb)
+  if (fused) AX_TRY(cudaMemcpyAsync(v.pb, v.z, sizeof(float) * field * m, cudaMemcpyDeviceToDevice, s));
   AX_CHECK_LAUNCH();
   const int K = w->graph_iters;
   const int key = m * 4 + 3;
@@ -1544,13 +1601,13 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     RhsState *h = w->h_st;
     if (w->profile) {
       if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
-      pcg_iteration<float>(op, m, v, st, w, kDue, s, per_rhs * count_state(h, m, kActive));
+      pcg_iteration<float>(op, m, v, st, w, kDue, s, per_rhs * count_state(h, m, kActive), fused);
       replace_step(s);
       AX_CHECK_LAUNCH();
     } else {
       rc = run_graph(w, w->g32, key, s, [&](cudaStream_t cs) {
         for (int k = 0; k < K; ++k) {
-          pcg_iteration<float>(op, m, v, st, w, kDue, cs);
+          pcg_iteration<float>(op, m, v, st, w, kDue, cs, 0.0, fused);
           replace_step(cs);
         }
       });

@@ -25,9 +25,9 @@ namespace {
 template <typename T, int MODE>
 struct StencilValue {
   // Value of the grid function the operator is applied to, at element e.
-  __device__ __forceinline__ static T at(const StencilArgs<T> &a, const T *p_old, size_t e, T beta) {
-    if (MODE == kStencilPcg) return a.in[e] + beta * p_old[e];
-    return a.in[e];
+  __device__ __forceinline__ static T at(const T *in, const T *p_old, size_t e, T beta) {
+    if (MODE == kStencilPcg) return in[e] + beta * p_old[e];
+    return in[e];
   }
 };
 
@@ -52,11 +52,14 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   T beta = T(0);
   const T *p_old = nullptr;
   T *p_new = nullptr;
+  const T *src = a.in;  // the grid function (before the direction update in mode Pcg)
   if (MODE == kStencilPcg) {
     beta = (T)a.st[m].beta;
     const bool odd = a.st[m].iters & 1;
     p_old = odd ? a.pb : a.pa;
     p_new = odd ? a.pa : a.pb;
+  } else if (MODE == kStencilPcgP) {
+    src = (a.st[m].iters & 1) ? a.pa : a.pb;
   }
 
   auto load_row = [&](int i, T (&v)[V]) {
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     if (!col_ok) return;
     const size_t off = base + (size_t)i * a.pitch + k0;
     T t[V];
-    load_vec<T>(a.in + off, t);
+    load_vec<T>(src + off, t);
     if (MODE == kStencilPcg) {
       T po[V];
       load_vec<T>(p_old + off, po);
@@ -87,9 +90,9 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   auto load_halo = [&](int i, T &left, T &right, T &czlast) {
     const size_t rowoff = base + (size_t)i * a.pitch;
     left = right = czlast = T(0);
-    if (lane == 0 && col_ok && k0 > 0) left = StencilValue<T, MODE>::at(a, p_old, rowoff + k0 - 1, beta);
+    if (lane == 0 && col_ok && k0 > 0) left = StencilValue<T, MODE>::at(src, p_old, rowoff + k0 - 1, beta);
     if (lane == 31) {
-      if (k0 + V < nz) right = StencilValue<T, MODE>::at(a, p_old, rowoff + k0 + V, beta);
+      if (k0 + V < nz) right = StencilValue<T, MODE>::at(src, p_old, rowoff + k0 + V, beta);
       if (k0 + V <= nz) czlast = CZ[(size_t)i * a.pitchz + k0 + V];
     }
   };
@@ -164,8 +167,8 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     if (col_ok) {
       if (MODE == kStencilApply) {
         store_vec<T>(a.out + rowoff + k0, o);
-      } else if (MODE == kStencilPcg) {
-        store_vec<T>(p_new + rowoff + k0, pc);
+      } else if (MODE == kStencilPcg || MODE == kStencilPcgP) {
+        if (MODE == kStencilPcg) store_vec<T>(p_new + rowoff + k0, pc);
         store_vec<T>(a.out + rowoff + k0, o);
 #pragma unroll
         for (int e = 0; e < V; ++e) acc = fma(pc[e], o[e], acc);
@@ -352,6 +355,7 @@ void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
   switch (mode) {
     case kStencilApply: stencil_kernel<T, kStencilApply><<<grid, block, 0, s>>>(a); break;
     case kStencilPcg: stencil_kernel<T, kStencilPcg><<<grid, block, 0, s>>>(a); break;
+    case kStencilPcgP: stencil_kernel<T, kStencilPcgP><<<grid, block, 0, s>>>(a); break;
     case kStencilResidual: stencil_kernel<T, kStencilResidual><<<grid, block, 0, s>>>(a); break;
     default: stencil_kernel<T, kStencilCheb><<<grid, block, 0, s>>>(a); break;
   }
