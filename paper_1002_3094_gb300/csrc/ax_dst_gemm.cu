@@ -331,35 +331,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
         for (int c = half * 2; c < half * 2 + 2; ++c) {
           const int l0 = nt * kBN + c * 32;
           if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= ne) break;  // nothing left for this warp
-          float P[32], Q[32];
-          tmem_ld32(tP + (unsigned)(c * 32), P);
-          if (a.ktiles > a.kbe) {
-            tmem_ld32(tP + (unsigned)(kBN + c * 32), Q);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
-          }
           if (rr == nullptr) {
             // Write-back transposed through this warp's 32 x 32 shared tile
             // (XOR-swizzled: conflict-free in both directions), so that every
             // global access of the warp is a run of 32 consecutive columns of
             // one row: first the columns l0 + j (P + Q), then their mirrors
-            // n - 1 - l0 - j (P - Q).  The direction update loads all 32 rows
-            // of p_old (and x) before it uses them, so that the warp has its
-            // whole tile of loads in flight at once.
+            // n - 1 - l0 - j (P - Q; the accumulators are read from TMEM again
+            // so that neither pass holds them).  The direction update loads
+            // 16 rows of p_old and x before it uses them, so that the warp has
+            // 32 loads in flight at once.
             float *T = epi + ew * 1024;
             const int row0 = mt * kBM + q * 32;
             const size_t mbase = (size_t)m * (size_t)a.field;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              T[lane * 32 + (i ^ lane)] = P[i] + Q[i];
-              P[i] -= Q[i];  // P now holds the mirrored half
-            }
 #pragma unroll 1
             for (int pass = 0; pass < 2; ++pass) {
-              if (pass == 1) {
+              {
+                float P[32], Q[32];
+                tmem_ld32(tP + (unsigned)(c * 32), P);
+                if (a.ktiles > a.kbe) {
+                  tmem_ld32(tP + (unsigned)(kBN + c * 32), Q);
+                } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = P[i];
+                  for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = pass ? P[i] - Q[i] : P[i] + Q[i];
               }
               __syncwarp();
               const int lc = l0 + lane;                 // column of the half range
@@ -395,6 +391,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
               __syncwarp();
             }
             continue;
+          }
+          float P[32], Q[32];
+          tmem_ld32(tP + (unsigned)(c * 32), P);
+          if (a.ktiles > a.kbe) {
+            tmem_ld32(tP + (unsigned)(kBN + c * 32), Q);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
           }
           if (grow < a.nr) {
 #pragma unroll
