@@ -369,36 +369,54 @@ __device__ __forceinline__ void split_task(int t, int nch, int &row, int &col) {
 }
 
 // FP64 field -> double-float pair (hi = fl(x), lo = fl(x - hi)) and back.
+// n is a multiple of 32 (whole rows of pitch elements): pairs of elements.
 __global__ void to_df(const double *__restrict__ x, float *__restrict__ h, float *__restrict__ l, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float hv = (float)v;
-    h[i] = hv;
-    l[i] = (float)(v - (double)hv);
+  const double2 *x2 = reinterpret_cast<const double2 *>(x);
+  float2 *h2 = reinterpret_cast<float2 *>(h), *l2 = reinterpret_cast<float2 *>(l);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = x2[i];
+    const float hx = (float)v.x, hy = (float)v.y;
+    h2[i] = make_float2(hx, hy);
+    l2[i] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
   }
 }
 __global__ void from_df(const float *__restrict__ h, const float *__restrict__ l, double *__restrict__ x, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    x[i] = (double)h[i] + (double)l[i];
+  const float2 *h2 = reinterpret_cast<const float2 *>(h), *l2 = reinterpret_cast<const float2 *>(l);
+  double2 *x2 = reinterpret_cast<double2 *>(x);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 a = h2[i], b = l2[i];
+    x2[i] = make_double2((double)a.x + (double)b.x, (double)a.y + (double)b.y);
+  }
 }
 // Replacement of the selected right-hand sides in double-float: (xh, xl) +=
-// x32 (two-sum, then renormalised) and x32 = 0 in one pass.  Launched with a
-// few CTAs per right-hand side, since in most launches no right-hand side is
-// selected and every CTA returns at once.
+// x32 (two-sum, then renormalised) and x32 = 0 in one pass.  Launched with
+// many CTAs per right-hand side, since only the few that are due at a step
+// do work (the others return at once).
 __global__ void fold_df(float *__restrict__ xh, float *__restrict__ xl, float *__restrict__ d, size_t field,
                         const RhsState *st, int mask) {
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
-  const size_t b = (size_t)m * field;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < field; e += (size_t)gridDim.x * blockDim.x) {
-    const float a = xh[b + e], c = d[b + e];
+  // field is a multiple of 32 (rows of pitch elements): whole float4 groups
+  float4 *h4 = reinterpret_cast<float4 *>(xh + (size_t)m * field);
+  float4 *l4 = reinterpret_cast<float4 *>(xl + (size_t)m * field);
+  float4 *d4 = reinterpret_cast<float4 *>(d + (size_t)m * field);
+  const size_t n4 = field / 4;
+  auto fold = [](float a, float c, float lo, float &h, float &l) {
     const float s = a + c, bb = s - a;
-    float err = (a - (s - bb)) + (c - bb);
-    err += xl[b + e];
-    const float hs = s + err;
-    xh[b + e] = hs;
-    xl[b + e] = err - (hs - s);
-    d[b + e] = 0.f;
+    const float err = ((a - (s - bb)) + (c - bb)) + lo;
+    h = s + err;
+    l = err - (h - s);
+  };
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = h4[e], c = d4[e], lo = l4[e];
+    float4 h, l;
+    fold(a.x, c.x, lo.x, h.x, l.x);
+    fold(a.y, c.y, lo.y, h.y, l.y);
+    fold(a.z, c.z, lo.z, h.z, l.z);
+    fold(a.w, c.w, lo.w, h.w, l.w);
+    h4[e] = h;
+    l4[e] = l;
+    d4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -1509,9 +1527,10 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
   const size_t nall = field * m;
   const unsigned cblocks = (unsigned)std::min<size_t>((nall + 255) / 256, 65535);
-  // a few thousand CTAs in all for the replacement fold (see fold_df)
+  // up to ~8k CTAs in all for the replacement fold (see fold_df): many per
+  // right-hand side, since only the few that are due at a step do work
   const unsigned fold_x = (unsigned)std::max<size_t>(
-      1, std::min<size_t>((field / 4 + 255) / 256, (size_t)std::max(8, 4096 / std::max(1, m))));
+      1, std::min<size_t>((field / 4 + 255) / 256, (size_t)std::max(16, 8192 / std::max(1, m))));
   const dim3 zg(fold_x, m);
   // The true residual phi - A x in double-float (x and phi as FP32 pairs, the
   // FP64 coefficients as FP32 + low part): FP32 arithmetic throughout.

@@ -196,12 +196,16 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Register kernel (FP32, nr <= 32 WPC C2): a CTA stages an nr x CW column
-// tile of IP, the couplings E and the data of one right-hand side in shared
-// memory (cp.async, padded to 32 WPC chunks of C2 rows with one word per
-// chunk); one column system per group of WPC warps, lane c of warp h owning
-// rows (32 h + c) C2 .. (32 h + c) C2 + C2 - 1, so a chunk, its alpha_t =
-// -E_{t-1} ip_t and beta_t = -E_t ip_t stay in registers after one pass over
-// the shared tile.  The affine carry maps of the chunks are composed with
+// tile of IP and the data of one right-hand side in shared memory (cp.async,
+// padded to 32 WPC chunks of C2 rows with one word per chunk); one column
+// system per group of WPC warps, lane c of warp h owning rows (32 h + c) C2 ..
+// (32 h + c) C2 + C2 - 1, so a chunk, its alpha_t = -E_{t-1} ip_t and
+// beta_t = -E_t ip_t stay in registers after one pass over the shared tile.
+// The couplings are E_i = E_0 (i + 1) (faces rbar_{i+1} = (i + 1) h_r of
+// Eq. eq_trid), so they are formed from the row index instead of being
+// loaded; the last row's coupling to the Dirichlet row nr, 0 in the table,
+// only ever multiplies that row's value 0 (a zero padding row, or the zero
+// carry into the last chunk) and needs no special case.  The affine carry maps of the chunks are composed with
 // shuffles inside each warp, and the WPC warp totals of a column through
 // shared memory.  Padding rows carry IP = E = 0 and solve to zero, so every
 // lane runs the same unpredicated recurrences.  For the tensor-core transform
@@ -215,16 +219,13 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
   constexpr int NCH = 32 * WPC;      // chunks per column
   constexpr int NP = NCH * C2;       // padded rows
   constexpr int kTileWords = NP * CW + NCH;
-  constexpr int kEWords = NP + NCH;
   static_assert(NT <= 1024 && (CW == 4 || CW == 8), "tile shape");
   extern __shared__ __align__(16) float tsm[];
   // per column and warp: the warp's composed map (A, M), forward and backward
   __shared__ float xfa[CW][WPC], xfm[CW][WPC], xba[CW][WPC], xbm[CW][WPC];
   const int nr = a.nr, pitch = a.pitch;
   float *ips = tsm;
-  float *ea = ips + kTileWords;
-  float *eb = ea + kEWords;
-  float *ds = eb + kEWords;
+  float *ds = ips + kTileWords;
   const int col0 = blockIdx.x * CW;
   const int m = blockIdx.y;
   const int ncol = min(CW, a.nz - col0);
@@ -243,12 +244,6 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
       cp_async4(ips + si, ipg + (size_t)rs * pitch, ok);
       cp_async4(ds + si, ing + (size_t)rs * pitch, ok);
     }
-    const float *eg = a.E + (size_t)m * a.estride;
-    for (int row = threadIdx.x; row < NP; row += NT) {
-      const int ei = row + row / C2;
-      cp_async4(ea + ei, eg + (row > 0 && row - 1 < nr ? row - 1 : 0), row > 0 && row - 1 < nr);
-      cp_async4(eb + ei, eg + (row < nr ? row : 0), row < nr);
-    }
     cp_async_wait_all();
   }
   __syncthreads();
@@ -258,16 +253,19 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
   const bool active = w < ncol;
   float *pd = ds + ci * (CW * C2 + 1) + w;
   const float *pip = ips + ci * (CW * C2 + 1) + w;
-  const float *pea = ea + ci * (C2 + 1);
-  const float *peb = eb + ci * (C2 + 1);
+  const float e0 = nr > 1 ? a.E[(size_t)m * a.estride] : 0.f;  // E_0
+  const int rbase = ci * C2;                                   // first row of the chunk
   float v[C2], al[C2], be[C2];
   // forward, zero carry-in (one pass over the shared tile)
   float g = 0.f, mu = 1.f;
+  float rowf = (float)rbase;  // row index, exact in FP32
 #pragma unroll
   for (int t = 0; t < C2; ++t) {
     const float ip = pip[CW * t];
-    al[t] = -pea[t] * ip;
-    be[t] = -peb[t] * ip;
+    const float f = -e0 * ip;  // padding rows: ip = 0
+    al[t] = f * rowf;          // -E_{row-1} ip (0 on the axis row)
+    rowf += 1.f;
+    be[t] = f * rowf;          // -E_row ip (on the last row it multiplies y_nr = 0)
     g = fmaf(pd[CW * t], ip, al[t] * g);
     mu *= al[t];
     v[t] = g;
@@ -412,9 +410,9 @@ void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
 
 template <int C2, int WPC, int CW>
 void launch_tridiag_reg(const TriArgs<float> &a, cudaStream_t s) {
-  // mirrors the kernel's layout: the IP and data tiles and the two E arrays
+  // mirrors the kernel's layout: the IP and data tiles
   constexpr int NCH = 32 * WPC, NP = NCH * C2;
-  const size_t smem = sizeof(float) * (2 * (NP * CW + NCH) + 2 * (NP + NCH));
+  const size_t smem = sizeof(float) * 2 * (NP * CW + NCH);
   ensure_smem_attr((const void *)tridiag_reg_kernel<C2, WPC, CW>, smem);
   dim3 grid((a.nz + CW - 1) / CW, a.m);
   tridiag_reg_kernel<C2, WPC, CW><<<grid, 32 * WPC * CW, smem, s>>>(a);
