@@ -488,9 +488,8 @@ def main():
         run_batched(args)
         return
     # The oracle pool must start before the first CUDA call (spawned workers).
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1002_3094_gb300 import replicas as RP
+    world, rank, local_rank = RP.rank_env()
     cores = os.cpu_count() or 1
     pool = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -510,7 +509,7 @@ def main():
     P.build()
     P.load_library()
 
-    nr, nz, med = workload(args.workload, instance=rank, rhs=args.rhs)
+    nr, nz, med = workload(args.workload, instance=RP.replica_instance(rank), rhs=args.rhs)
     m = med.n_rhs
     kr, kz, q = sample_operator_inputs(med, nr, nz, bc_z=args.bc_z)
     op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz, bc_z=args.bc_z)
@@ -533,11 +532,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return RP.max_over_ranks(x, dist, dev)
 
     for _ in range(args.warmup):
         info = solve()
@@ -560,7 +555,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms)
     unknowns_step = nr * nz * m
-    value = world * unknowns_step * args.steps / (ms_max / 1000.0)
+    value = RP.aggregate_rate(unknowns_step * args.steps, ms_max / 1000.0, dist, dev)
     iters = [i["iters"] for i in info]
     outer = [i["outer"] for i in info]
     rel = max(i["rel_res"] for i in info)
@@ -578,7 +573,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         pms = max_over_ranks(e0.elapsed_time(e1)) / args.plain_steps
-        pval = world * unknowns_step / (pms / 1000.0)
+        pval = RP.aggregate_rate(unknowns_step, pms / 1000.0, dist, dev)
         diff = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
         plain = {"value": pval, "ms_per_step": pms, "iters_max": max(i["iters"] for i in pinfo),
                  "rel_diff_to_chosen": diff}
@@ -597,7 +592,8 @@ def main():
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0)
         nbytes = f_host.nbytes
-        e2e = {"value": world * unknowns_step * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": RP.aggregate_rate(unknowns_step * args.steps, el, dist, dev), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
     # ---- per-kernel times with CUDA events (one profiled solve) ----
