@@ -171,7 +171,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
              int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
 
 /* ---- many independent operators (uneven grids) in one batched solve ---------
- * Operators with the same (nr, nz, lr, lz) form a group whose coefficient
+ * Operators with the same (nr, nz, lr, lz, bc_z) form a group whose coefficient
  * tables are stacked, so each kernel launch serves the whole group with
  * per-instance convergence masks; groups run concurrently on their own
  * streams.  The paper has no batched form; it solves one series of right-hand
@@ -179,8 +179,9 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
  * ax_batch_create copies the tables of `ops` (the operators stay owned by the
  * caller and may be destroyed afterwards).  Synchronises `stream`.
  * ax_batch_solve: f[i], u[i] are device arrays [nr_i][nz_i] of instance i;
- * methods AX_PCG_FP64 and AX_PCG_MIXED (others: AX_ERR_UNSUPPORTED); info is a
- * host array [n] (may be NULL).  Blocks until all groups are done.
+ * every method of ax_solve (the Chebyshev methods with each instance's own
+ * gamma bounds, hence its own tau_0 and rho_0); info is a host array [n]
+ * (may be NULL).  Blocks until all groups are done.
  * ax_batch_latency: per-instance wall time (ms) from the start of the last
  * ax_batch_solve to the completion of the instance's group; *groups = count.
  * ax_solve_batched = create + solve + destroy. */

@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(256, DstOcc<T>::min_blocks) dst_kernel(const D
   T cheb_a = T(0), tau = T(0);
   if (MODE == kDstChebInverse) {
     cheb_a = (T)a.st[m].cheb_a;
-    tau = (T)a.tau;
+    tau = (T)a.chp[2 * m];
   }
   for (int o = threadIdx.x; o < n; o += blockDim.x) {
     // per-column factors: sine (c, sn) = half-angle pair of k = o + 1; cosine

@@ -147,6 +147,8 @@ struct ax_operator {
   long long cstride = 0, czstride = 0, estride = 0;
   double lr = 1, lz = 1, hr = 0, hz = 0;
   double kappa_t = 0, q_t = 0, gamma1 = 0, gamma2 = 0;
+  // group operator of a batch: the Chebyshev bounds of each member (by RHS)
+  std::vector<double> mgamma1, mgamma2;
   int device = 0;
   ax::FftPlan plan;
   int *rader_perm = nullptr;  // [2 P] device
@@ -231,7 +233,7 @@ struct DstArgs {
   T *x, *r;                // PcgForward: x += alpha p, r -= alpha q.  PcgInverse: r for (r,z)
   T *pa, *pb;              // PcgForward: p is pb for an even iteration count, pa for odd
   T *y, *yprev;            // Cheb: y_{k+1} = a (y - tau res^) + (1 - a) y_{k-1}, written to yprev
-  double tau;             // Cheb: constant step tau_0
+  const double *chp;      // Cheb: (tau_0, rho_0^2) per right-hand side
   double scale;           // sine: 0.5 / sqrt(2 L), the orthonormal scaling folded with the
                           // real-FFT split; cosine inverse: 1 / sqrt(2 nz)
   int rpb;                // rows per CTA (set by the launcher)

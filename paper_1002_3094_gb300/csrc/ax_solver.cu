@@ -57,6 +57,7 @@ struct Workspace {
         *y32prev = nullptr;
   // partial sums [4][m][kPartialStride]
   double *part = nullptr;
+  double *chp = nullptr;      // Chebyshev (tau, rho0^2) per right-hand side [m][2]
   RhsState *st = nullptr, *st_outer = nullptr;
   RhsState *h_st = nullptr;   // pinned host mirror [2 m]
   // dense FP64 staging for host buffers and single-step entry points
@@ -168,7 +169,7 @@ void free_vectors32(Workspace *w) {
   free_graph(w->gc32);
 }
 void free_base(Workspace *w) {
-  dfree(w->phi64); dfree(w->x64); dfree(w->part); dfree(w->st); dfree(w->st_outer);
+  dfree(w->phi64); dfree(w->x64); dfree(w->part); dfree(w->chp); dfree(w->st); dfree(w->st_outer);
   if (w->h_st) cudaFreeHost(w->h_st);
   w->h_st = nullptr;
   w->mbase = 0;
@@ -186,6 +187,7 @@ int ensure_base(ax_operator *op, int m) {
   AX_TRY(dalloc(&w->phi64, f));
   AX_TRY(dalloc(&w->x64, f));
   AX_TRY(dalloc(&w->part, (size_t)4 * m * kPartialStride));
+  AX_TRY(dalloc(&w->chp, (size_t)2 * m));
   AX_TRY(dalloc(&w->st, (size_t)m));
   AX_TRY(dalloc(&w->st_outer, (size_t)m));
   AX_TRY(cudaMallocHost((void **)&w->h_st, sizeof(RhsState) * 2 * m));
@@ -629,9 +631,10 @@ __global__ void sc_true_check(RhsState *st, const double *p, int nb) {
 
 // Chebyshev: rr = ||A y - phi||^2 of the current iterate; stop or continue and
 // advance alpha_{k+1} = 4 / (4 - rho0^2 alpha_k) (alpha for the first step is 1).
-__global__ void sc_cheb(RhsState *st, const double *p, int nb, double rho0sq, int on_converge) {
+__global__ void sc_cheb(RhsState *st, const double *p, int nb, const double *chp, int on_converge) {
   const int m = blockIdx.x;
   if (st[m].state != kActive) return;
+  const double rho0sq = chp[2 * m + 1];
   const double rr = reduce_part(p + (size_t)m * kPartialStride, nb);
   if (threadIdx.x == 0) {
     RhsState s = st[m];
@@ -1302,7 +1305,7 @@ __global__ void cheb_swap_dummy() {}
 
 template <typename T>
 void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, Workspace *w,
-                    double tau, double rho0sq, int on_converge, int parity, cudaStream_t s) {
+                    int on_converge, int parity, cudaStream_t s) {
   const int V = VecT<T>::n;
   const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
   double *prr = part_ptr(w, kPartB);
@@ -1315,7 +1318,7 @@ void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState
   sa.partial = prr;
   launch_stencil<T>(kStencilCheb, sa, s);
   note_launch();
-  sc_cheb<<<m, 32, 0, s>>>(st, prr, nbs, rho0sq, on_converge);
+  sc_cheb<<<m, 32, 0, s>>>(st, prr, nbs, w->chp, on_converge);
   DstArgs<T> f = dst_args<T>(op, m, op->nr, st, kActive);
   f.in = v.res;
   f.out = v.res;
@@ -1325,7 +1328,7 @@ void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState
   b.in = v.res;
   b.y = y;
   b.yprev = yprev;
-  b.tau = tau;
+  b.chp = w->chp;
   launch_dst<T>(kDstChebInverse, b, s);
 }
 
@@ -1442,14 +1445,25 @@ template <typename T>
 int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphCache &g, int on_conv, int *parity,
               cudaStream_t s) {
   Workspace *w = op->ws;
-  const double tau = 2.0 / (op->gamma1 + op->gamma2);
-  const double xi = op->gamma1 / op->gamma2;
-  const double rho0 = (1.0 - xi) / (1.0 + xi);
+  // tau_0 = 2 / (gamma1 + gamma2), rho_0 = (1 - xi) / (1 + xi), xi = gamma1 / gamma2,
+  // per right-hand side: the members of a batched group have their own bounds
+  {
+    std::vector<double> par(2 * (size_t)m);
+    for (int i = 0; i < m; ++i) {
+      const bool mem = (size_t)i < op->mgamma1.size();
+      const double g1 = mem ? op->mgamma1[i] : op->gamma1, g2 = mem ? op->mgamma2[i] : op->gamma2;
+      const double xi = g1 / g2, rho0 = (1.0 - xi) / (1.0 + xi);
+      par[2 * i] = 2.0 / (g1 + g2);
+      par[2 * i + 1] = rho0 * rho0;
+    }
+    AX_TRY(cudaMemcpyAsync(w->chp, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice, s));
+    AX_TRY(cudaStreamSynchronize(s));
+  }
   const int K = 2 * std::max(1, w->graph_iters / 2);  // even: the buffer roles repeat
   const int key = m * 4 + 2 + (on_conv == kDone ? 1 : 0) + (*parity << 20);
   for (int guard = 0; guard < 1000000; ++guard) {
     int rc = run_graph(w, g, key, s, [&](cudaStream_t cs) {
-      for (int k = 0; k < K; ++k) cheb_iteration<T>(op, m, v, st, w, tau, rho0 * rho0, on_conv, (*parity + k) & 1, cs);
+      for (int k = 0; k < K; ++k) cheb_iteration<T>(op, m, v, st, w, on_conv, (*parity + k) & 1, cs);
     });
     if (rc != AX_OK) return rc;
     RhsState *h = w->h_st;
@@ -2424,6 +2438,10 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz; gop->bc_z = o->bc_z;
     gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;
     gop->kappa_t = o->kappa_t; gop->q_t = o->q_t; gop->gamma1 = o->gamma1; gop->gamma2 = o->gamma2;
+    for (const ax_operator *mo : mops) {  // Chebyshev bounds of each member
+      gop->mgamma1.push_back(mo->gamma1);
+      gop->mgamma2.push_back(mo->gamma2);
+    }
     gop->device = o->device;
     gop->plan = o->plan;
     gop->dst_tc = o->dst_tc;
@@ -2458,7 +2476,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
 int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double tol, int32_t max_iter,
                    int32_t method, int32_t flags, ax_solve_info *info, void *stream) {
   if (!b || !f || !u) return AX_ERR_INVALID_ARG;
-  if (method != AX_PCG_FP64 && method != AX_PCG_MIXED) return AX_ERR_UNSUPPORTED;
+  if (method < AX_PCG_FP64 || method > AX_CHEB_MIXED) return AX_ERR_INVALID_ARG;
   if (flags & AX_FLAG_HOST_BUFFERS) return AX_ERR_UNSUPPORTED;
   for (int i = 0; i < b->n; ++i)
     if (!f[i] || !u[i]) return AX_ERR_INVALID_ARG;

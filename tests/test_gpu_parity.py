@@ -318,7 +318,7 @@ def test_mixed_replacement_keeps_fp64_iteration_count(cuda):
     pr.close()
 
 
-@pytest.mark.parametrize("method", [P.AX_PCG_FP64, P.AX_PCG_MIXED])
+@pytest.mark.parametrize("method", [P.AX_PCG_FP64, P.AX_PCG_MIXED, P.AX_CHEB_FP64, P.AX_CHEB_MIXED])
 def test_batched_uneven_instances_equal_single_solves(cuda, method):
     """Instances of the uneven-size workload (sizes reduced to keep the test
     short; shapes repeat so groups hold several instances): the batched solve
