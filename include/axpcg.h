@@ -61,7 +61,7 @@ enum {
   AX_ERR_TIMEOUT = 4,       /* a bounded device wait expired                                 */
   AX_ERR_OOM = 5,           /* device allocation failed                                      */
   AX_ERR_CUDA = 6,          /* any other CUDA runtime error                                  */
-  AX_ERR_UNSUPPORTED = 7    /* option not built (e.g. the tensor-core transform for bc_z = 1) */
+  AX_ERR_UNSUPPORTED = 7    /* option not built (e.g. the tensor-core transform for nz > 4096) */
 };
 
 /* ---- methods and flags -------------------------------------------------- */
@@ -101,7 +101,7 @@ typedef struct {
                           h_z = lz/nz, faces zbar_c = c h_z (c = 0..nz; kappa_z is still
                           sampled there, but the two boundary faces carry no flux: the
                           one-sided rows of Eq. scheme_op_r_z); the cosine pair of
-                          Eq. fft_phi.  The tensor-core transform is not built for it.
+                          Eq. fft_phi.
                        Other values: AX_ERR_INVALID_ARG                                    */
 } ax_grid;
 
@@ -153,8 +153,12 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
  *                    close to B^-1); 0: the FFT transform.  Default: 1 when
  *                    nz <= 4096 and the FFT length nz + 1 has a prime factor
- *                    above 7 (e.g. 1025 = 5^2 41), else 0.  Accepted for
- *                    nz <= 4096 and bc_z = 0, else AX_ERR_UNSUPPORTED
+ *                    above 7 (e.g. 1025 = 5^2 41), or bc_z = 1; else 0.
+ *                    For bc_z = 1 the tensor-core transform multiplies by the
+ *                    orthonormal cosine pair (the forward on folded input:
+ *                    r_k + r_{n-1-k} against the even modes, r_k - r_{n-1-k}
+ *                    against the odd ones).  Accepted for nz <= 4096, else
+ *                    AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */

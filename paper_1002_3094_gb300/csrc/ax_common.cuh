@@ -130,4 +130,38 @@ __device__ __forceinline__ void split_store4(unsigned char *split, int m, int ro
   *reinterpret_cast<unsigned *>(to + kSplitTileBytes / 2) = bf16_pack2(lo[1], lo[3]);
 }
 
+// Folded input of the tensor-core cosine forward transform for the 8
+// positions k0 .. k0 + 7 (k0 % 8 == 0) of one row, from x[e] = r_{k0+e} and
+// xm[e] = r_{n-1-k0-e}: u_k = r_k + r_{n-1-k} at position k of the first K
+// half, w_k = r_k - r_{n-1-k} at position kbe 64 + k of the second, for
+// k < ceil(n/2) (the middle entry of odd n: u = r, w = 0), zeros after.
+__device__ __forceinline__ void fold_store8(unsigned char *split, int m, int row, int k0, int n, int mtiles,
+                                            int ktiles, int kbe, const float (&x)[8], const float (&xm)[8]) {
+  const int ne = (n + 1) >> 1;
+  unsigned uh[4], ul[4], wh[4], wl[4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    float u2[2], w2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int k = k0 + e + j;
+      const bool mid = 2 * k + 1 == n;
+      u2[j] = k < ne ? (mid ? x[e + j] : x[e + j] + xm[e + j]) : 0.f;
+      w2[j] = (k < ne && !mid) ? x[e + j] - xm[e + j] : 0.f;
+    }
+    const float uh0 = bf16_round(u2[0]), uh1 = bf16_round(u2[1]);
+    const float wh0 = bf16_round(w2[0]), wh1 = bf16_round(w2[1]);
+    uh[e / 2] = bf16_pack2(uh0, uh1);
+    ul[e / 2] = bf16_pack2(u2[0] - uh0, u2[1] - uh1);
+    wh[e / 2] = bf16_pack2(wh0, wh1);
+    wl[e / 2] = bf16_pack2(w2[0] - wh0, w2[1] - wh1);
+  }
+  unsigned char *pu = split + split_byte(m, row, k0, mtiles, ktiles);
+  unsigned char *pw = split + split_byte(m, row, kbe * 64 + k0, mtiles, ktiles);
+  *reinterpret_cast<uint4 *>(pu) = make_uint4(uh[0], uh[1], uh[2], uh[3]);
+  *reinterpret_cast<uint4 *>(pu + kSplitTileBytes / 2) = make_uint4(ul[0], ul[1], ul[2], ul[3]);
+  *reinterpret_cast<uint4 *>(pw) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+  *reinterpret_cast<uint4 *>(pw + kSplitTileBytes / 2) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+}
+
 }  // namespace ax

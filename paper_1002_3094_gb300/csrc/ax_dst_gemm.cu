@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
             // global access of the warp is a run of 32 consecutive columns of
             // one row: first the columns l0 + j (P + Q), then their mirrors
             // n - 1 - l0 - j (P - Q; the accumulators are read from TMEM again
-            // so that neither pass holds them).  The direction update loads
+            // so that neither pass holds them).  The cosine forward writes
+            // P to the even columns 2 (l0 + j) and Q to the odd ones.  The direction update loads
             // 16 rows of p_old and x before it uses them, so that the warp has
             // 32 loads in flight at once.
             float *T = epi + ew * 1024;
@@ -354,13 +355,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
 #pragma unroll
                   for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
                 }
+                if (a.cosfwd) {  // even output columns from P, odd ones from Q
 #pragma unroll
-                for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = pass ? P[i] - Q[i] : P[i] + Q[i];
+                  for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = pass ? Q[i] : P[i];
+                } else {
+#pragma unroll
+                  for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = pass ? P[i] - Q[i] : P[i] + Q[i];
+                }
               }
               __syncwarp();
-              const int lc = l0 + lane;                 // column of the half range
-              const int col = pass ? n - 1 - lc : lc;   // output column
-              const bool colok = lc < ne && (pass == 0 || col != lc);  // middle column of odd n once
+              const int lc = l0 + lane;  // column of the half range
+              // output column: the mirrored pair l, n - 1 - l (the middle column of
+              // odd n once), or for the cosine forward 2 l and 2 l + 1
+              const int col = a.cosfwd ? 2 * lc + pass : (pass ? n - 1 - lc : lc);
+              const bool colok = a.cosfwd ? (lc < ne && col < n) : (lc < ne && (pass == 0 || col != lc));
               const size_t cbase = mbase + (size_t)row0 * a.pitch + col;
               if (pupd) {
 #pragma unroll 1
@@ -529,10 +537,9 @@ int dst_gemm_mtiles(int rows) { return (rows + kBM - 1) / kBM; }
 // ones after) a 32 KB tile of S_hi and one of S_lo, each in the shared-memory
 // layout above holding S[k][l] at (row l, column k).  Values in FP64, rounded
 // to BF16 (nearest, ties to even, by way of FP32).
-std::vector<uint16_t> dst_gemm_table(int n) {
+std::vector<uint16_t> dst_gemm_table(int n, int kind) {
   const int KB = dst_gemm_ktiles(n), KBE = dst_gemm_kbe(n), NT = dst_gemm_ntiles(n);
   const int L = n + 1, ne = (n + 1) / 2;
-  const double sc = std::sqrt(2.0 / L);
   auto to_bf16 = [](double x) -> uint16_t {
     const float v = (float)x;
     uint32_t u;
@@ -546,20 +553,41 @@ std::vector<uint16_t> dst_gemm_table(int n) {
     std::memcpy(&v, &u, 4);
     return v;
   };
+  // orthonormal cosine matrix C[l][k] = c_l sqrt(2/n) cos(pi (2k + 1) l / (2n)),
+  // c_0 = 1/sqrt 2, the integer (2k + 1) l reduced exactly mod 4n
+  auto cosm = [n](int l, int k) -> double {
+    const long long e = ((long long)(2 * k + 1) * l) % (4LL * n);
+    return std::sqrt(2.0 / n) * (l == 0 ? std::sqrt(0.5) : 1.0) * std::cos(M_PI * (double)e / (2.0 * n));
+  };
   const size_t tile = (size_t)kBN * kBK;  // elements of one 32 KB tile
   std::vector<uint16_t> t((size_t)NT * KB * 2 * tile, 0);
   for (int nt = 0; nt < NT; ++nt)
     for (int kb = 0; kb < KB; ++kb) {
       uint16_t *hi = t.data() + ((size_t)nt * KB + kb) * 2 * tile;
       uint16_t *lo = hi + tile;
+      const bool second = kb >= KBE;
       for (int nl = 0; nl < kBN; ++nl) {
-        const int l = nt * kBN + nl;
+        const int l = nt * kBN + nl;  // output column of the half range
         if (l >= ne) continue;
         for (int kl = 0; kl < kBK; ++kl) {
-          const int k = (kb < KBE) ? 2 * (kb * kBK + kl) : 2 * ((kb - KBE) * kBK + kl) + 1;
-          if (k >= n) continue;
-          const long long e = ((long long)(k + 1) * (l + 1)) % (2LL * L);  // sin(pi e / L), e reduced
-          const double v = sc * std::sin(M_PI * (double)e / L);
+          const int kk = (second ? kb - KBE : kb) * kBK + kl;  // position in the K half
+          double v;
+          if (kind == kTableCosForward) {
+            // first half: u_kk = r_kk + r_{n-1-kk} times C[2l][kk]; second half:
+            // w_kk = r_kk - r_{n-1-kk} times C[2l+1][kk] (kk < ceil(n/2))
+            const int lo_ = second ? 2 * l + 1 : 2 * l;
+            if (kk >= ne || lo_ >= n) continue;
+            v = cosm(lo_, kk);
+          } else {
+            const int k = second ? 2 * kk + 1 : 2 * kk;  // input index, even ones first
+            if (k >= n) continue;
+            if (kind == kTableCosInverse) {
+              v = cosm(k, l);  // out[l] = sum over modes k of C[k][l] in[k]
+            } else {
+              const long long e = ((long long)(k + 1) * (l + 1)) % (2LL * L);  // sin(pi e / L), e reduced
+              v = std::sqrt(2.0 / L) * std::sin(M_PI * (double)e / L);
+            }
+          }
           const uint16_t h = to_bf16(v);
           const int off = ((nl >> 3) * 1024 + (kl >> 3) * 128 + (nl & 7) * 16 + (kl & 7) * 2) / 2;
           hi[off] = h;

@@ -282,6 +282,10 @@ struct GemmDstArgs {
   // p_old); alpha and beta from st[m]
   float *pa, *pb;
   float *x;
+  // cosine forward (table kTableCosForward): the two accumulators hold the
+  // even and the odd output columns (out[2l] = P, out[2l+1] = Q) instead of
+  // the mirrored pair
+  int cosfwd;
 };
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);
@@ -289,7 +293,13 @@ int dst_gemm_ktiles(int n);
 int dst_gemm_kbe(int n);
 int dst_gemm_ntiles(int n);
 int dst_gemm_mtiles(int rows);
-std::vector<uint16_t> dst_gemm_table(int n);
+// B tables of the tensor-core transform: the sine matrix (its own inverse),
+// or the orthonormal cosine pair of the zero-flux z boundary: the forward
+// DCT-II on folded input (u = r_k + r_{n-1-k} first, w = r_k - r_{n-1-k}
+// second; output columns 2l and 2l + 1) and the inverse DCT-III (even modes
+// first, outputs l and n - 1 - l as for the sine matrix).
+enum { kTableSine = 0, kTableCosForward = 1, kTableCosInverse = 2 };
+std::vector<uint16_t> dst_gemm_table(int n, int kind);
 
 template <typename T>
 struct TriArgs {

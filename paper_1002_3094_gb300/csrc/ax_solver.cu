@@ -434,7 +434,8 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
                                                   const float *__restrict__ pb, int nr, int n, int pitch,
                                                   size_t field, int mtiles, int ktiles, int kbe,
                                                   unsigned char *__restrict__ split,
-                                                  const RhsState *st, int mask, double *__restrict__ partial) {
+                                                  const RhsState *st, int mask, double *__restrict__ partial,
+                                                  int cosine) {
   __shared__ double red[8];
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
@@ -470,17 +471,20 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
     }
     *reinterpret_cast<float4 *>(r + e) = *reinterpret_cast<const float4 *>(rv);
     *reinterpret_cast<float4 *>(r + e + 4) = *reinterpret_cast<const float4 *>(rv + 4);
-    split_store8(split, m, row, col, mtiles, ktiles, kbe, rv);
+    // the cosine transform folds mirrored columns, which other threads update:
+    // its split input is written by a separate pass (split_field)
+    if (!cosine) split_store8(split, m, row, col, mtiles, ktiles, kbe, rv);
   }
   const double sum = block_sum((double)acc, red);
   if (threadIdx.x == 0) partial[(size_t)m * kPartialStride + blockIdx.x] = sum;
 }
 
 // The rows of a field written split into BF16 halves (tensor-core transform input).
+// cosine: the folded input of the cosine forward transform instead (fold_store8).
 __global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int n, int pitch,
                                                    size_t field, int mtiles, int ktiles, int kbe,
                                                    unsigned char *__restrict__ split,
-                                                   const RhsState *st, int mask) {
+                                                   const RhsState *st, int mask, int cosine) {
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
   const int nch = (n + 7) >> 3;
@@ -492,7 +496,15 @@ __global__ void __launch_bounds__(256) split_field(const float *__restrict__ in,
     float v[8];
     *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(in + e);
     *reinterpret_cast<float4 *>(v + 4) = *reinterpret_cast<const float4 *>(in + e + 4);
-    split_store8(split, m, row, col, mtiles, ktiles, kbe, v);
+    if (!cosine) {
+      split_store8(split, m, row, col, mtiles, ktiles, kbe, v);
+    } else if (2 * col < n) {  // chunks of the first half: u and w of columns col .. col + 7
+      const float *rowp = in + (size_t)m * field + (size_t)row * pitch;
+      float vm[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) vm[i] = (col + i < n) ? rowp[n - 1 - col - i] : 0.f;
+      fold_store8(split, m, row, col, n, mtiles, ktiles, kbe, v, vm);
+    }
   }
 }
 
@@ -1023,13 +1035,13 @@ TcCache &tc_cache() {
   static TcCache c;
   return c;
 }
-const uint16_t *tc_table(int device, int n) {
+const uint16_t *tc_table(int device, int n, int kind = kTableSine) {
   TcCache &c = tc_cache();
   std::lock_guard<std::mutex> lock(c.mu);
-  const long long key = (long long)device << 32 | (unsigned)n;
+  const long long key = (long long)device << 32 | (unsigned)n | (long long)kind << 24;
   for (auto &e : c.tables)
     if (e.first == key) return e.second;
-  std::vector<uint16_t> t = dst_gemm_table(n);
+  std::vector<uint16_t> t = dst_gemm_table(n, kind);
   uint16_t *d = nullptr;
   std::lock_guard<std::recursive_mutex> lock2(g_alloc_capture_mutex);
   if (dalloc(&d, t.size()) != cudaSuccess) return nullptr;
@@ -1072,20 +1084,23 @@ SplitGeom split_geom(const ax_operator *op, int rows) {
 }
 
 // Tensor-core transform of `rows` rows per RHS: out = A S for the selected
-// right-hand sides (A in the split layout); with r, the (r, out) partials
-// into `partial`.  With pa, pb the result is not stored but forms the next
+// right-hand sides (A in the split layout; S the sine matrix, or for the
+// zero-flux z boundary the forward cosine matrix on folded input or its
+// inverse); with r, the (r, out) partials into `partial`.  With pa, pb the result is not stored but forms the next
 // search direction p_new = out + beta p_old (and, with x, x += alpha p_old);
 // see GemmDstArgs.
-void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, float *out, const RhsState *st,
-                  int mask, const float *r, double *partial, cudaStream_t s, int three = -1, float *pa = nullptr,
-                  float *pb = nullptr, float *x = nullptr) {
+void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, bool inverse, float *out,
+                  const RhsState *st, int mask, const float *r, double *partial, cudaStream_t s, int three = -1,
+                  float *pa = nullptr, float *pb = nullptr, float *x = nullptr) {
   GemmDstArgs g{};
   g.pa = pa;
   g.pb = pb;
   g.x = x;
+  const int kind = op->bc_z == 1 ? (inverse ? kTableCosInverse : kTableCosForward) : kTableSine;
+  g.cosfwd = kind == kTableCosForward;
   g.A = A;
   g.out = out;
-  g.SB = tc_table(op->device, op->nz);
+  g.SB = tc_table(op->device, op->nz, kind);
   g.n = op->nz;
   g.nr = rows;
   g.pitch = op->pitch;
@@ -1110,7 +1125,7 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
   const SplitGeom g = split_geom(op, rows);
   note_launch();
   split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->nz, op->pitch, (size_t)rows * op->pitch,
-                                                      g.mtiles, g.ktiles, g.kbe, split, st, mask);
+                                                      g.mtiles, g.ktiles, g.kbe, split, st, mask, op->bc_z == 1);
 }
 
 // Mode solves z -> split operand (the tile kernel writes it directly; otherwise
@@ -1160,9 +1175,9 @@ void precond_apply(const ax_operator *op, int m, const T *r, T *z, const RhsStat
       unsigned char *sp = op->ws->split;
       const bool dm = tc_dot_in_modes(op);
       tc_split(op, m, op->nr, r, sp, st, mask, s);
-      tc_transform(op, m, op->nr, sp, z, st, mask, nullptr, nullptr, s);
+      tc_transform(op, m, op->nr, sp, false, z, st, mask, nullptr, nullptr, s);
       tc_mode_solve(op, m, z, tmp, sp, st, mask, s, dm ? prz : nullptr);
-      tc_transform(op, m, op->nr, sp, z, st, mask, dm ? nullptr : r, dm ? nullptr : prz, s);
+      tc_transform(op, m, op->nr, sp, true, z, st, mask, dm ? nullptr : r, dm ? nullptr : prz, s);
       return;
     }
   }
@@ -1229,9 +1244,10 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
         note_launch();
         pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(fused ? nullptr : v.x, v.r, v.q, v.pa, v.pb, op->nr,
                                                           op->nz, op->pitch, field_elems(op), g.mtiles, g.ktiles,
-                                                          g.kbe, sp, st, kActive, prr);
+                                                          g.kbe, sp, st, kActive, prr, op->bc_z == 1);
+        if (op->bc_z == 1) tc_split(op, m, op->nr, v.r, sp, st, kActive, s);
       }
-      { ProfScope ps(w, kProfDstFwd, units, s); tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s); }
+      { ProfScope ps(w, kProfDstFwd, units, s); tc_transform(op, m, op->nr, sp, false, v.z, st, kActive, nullptr, nullptr, s); }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
         note_launch();
@@ -1249,12 +1265,12 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
           sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op), kActive, kActive);
         }
         ProfScope ps(w, kProfDstInv, units, s);
-        tc_transform(op, m, op->nr, sp, v.z, st, kActive, nullptr, nullptr, s, -1, v.pa, v.pb, v.x);
+        tc_transform(op, m, op->nr, sp, true, v.z, st, kActive, nullptr, nullptr, s, -1, v.pa, v.pb, v.x);
         return;
       }
       {
         ProfScope ps(w, kProfDstInv, units, s);
-        tc_transform(op, m, op->nr, sp, v.z, st, kActive, dm ? nullptr : v.r, dm ? nullptr : prz, s);
+        tc_transform(op, m, op->nr, sp, true, v.z, st, kActive, dm ? nullptr : v.r, dm ? nullptr : prz, s);
       }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
@@ -1595,11 +1611,11 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
       // step again, p_new = z + beta p_old (x already holds alpha p_old)
       unsigned char *sp = w->split;
       tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss);
-      tc_transform(op, m, op->nr, sp, v.z, st, kCheck, nullptr, nullptr, ss);
+      tc_transform(op, m, op->nr, sp, false, v.z, st, kCheck, nullptr, nullptr, ss);
       tc_mode_solve(op, m, v.z, v.q, sp, st, kCheck, ss, part_ptr(w, kPartC));
       note_launch();
       sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kCheck, 1);
-      tc_transform(op, m, op->nr, sp, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr);
+      tc_transform(op, m, op->nr, sp, true, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr);
       note_launch();
       sc_promote<<<(m + 31) / 32, 32, 0, ss>>>(st, m, kCheck, kActive);
       return;
@@ -1749,7 +1765,7 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     w->replace_delta = value;
   } else if (!strcmp(name, "dst_tensor")) {
     if (value != 0.0 && value != 1.0 && value != 2.0) return AX_ERR_INVALID_ARG;
-    if (value != 0.0 && (op->nz > kMaxTcN || op->bc_z != 0)) return AX_ERR_UNSUPPORTED;
+    if (value != 0.0 && op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
     op->dst_tc = (int)value;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "max_outer")) {
@@ -1827,13 +1843,18 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
     ax_destroy_operator(op);
     return AX_ERR_UNSUPPORTED;
   }
-  // Transform of the FP32 path: the tensor-core GEMM when the FFT of length L
-  // needs a prime radix above 8 (paired direct DFT or Rader stages, several
-  // times the work of the small radices) and nz is within the GEMM's range.
+  // Transform of the FP32 path: the tensor-core GEMM when nz is within its
+  // range and either the sine FFT of length L needs a prime radix above 8
+  // (paired direct DFT or Rader stages, several times the work of the small
+  // radices) or the transform is the cosine pair (its FFT form reads and
+  // writes each row twice around the packing; at nz = 1024 the GEMM pair
+  // solves in 2/3 of the time).
   op->dst_tc = 0;
-  if (nz <= kMaxTcN && !cosine)
+  if (nz <= kMaxTcN) {
+    if (cosine) op->dst_tc = 1;
     for (int i = 0; i < op->plan.nstages; ++i)
       if (op->plan.radix[i] > 8) op->dst_tc = 1;
+  }
 
   const double hr = op->hr, hz = op->hz, hr2 = hr * hr, hz2 = hz * hz;
   const int P = op->pitch, PZ = op->pitchz;
@@ -1977,7 +1998,7 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
       if (tc) {
         unsigned char *sp = w->split;
         tc_split(op, m, rows_per, a, sp, nullptr, -1, s);
-        tc_transform(op, m, rows_per, sp, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+        tc_transform(op, m, rows_per, sp, false, b, nullptr, -1, nullptr, nullptr, s, tc_three);
       }
     }
     if (!tc) {
@@ -1998,9 +2019,9 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
     if constexpr (sizeof(T) == 4) {
       unsigned char *sp = w->split;
       tc_split(op, m, rows_per, a, sp, nullptr, -1, s);
-      tc_transform(op, m, rows_per, sp, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+      tc_transform(op, m, rows_per, sp, false, b, nullptr, -1, nullptr, nullptr, s, tc_three);
       tc_mode_solve(op, m, b, a, sp, nullptr, -1, s);
-      tc_transform(op, m, rows_per, sp, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+      tc_transform(op, m, rows_per, sp, true, b, nullptr, -1, nullptr, nullptr, s, tc_three);
     }
   } else {
     DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
@@ -2040,7 +2061,7 @@ static int apply_dispatch(ax_operator *op, const double *in, double *out, int m,
   if ((long long)rows_per * m > 2147483647LL / 2) return AX_ERR_INVALID_ARG;
   if (tc) {
     if (which != 1 && which != 3) return AX_ERR_INVALID_ARG;
-    if (op->nz > kMaxTcN || op->bc_z != 0) return AX_ERR_UNSUPPORTED;
+    if (op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;
   return precision == AX_PREC_FP64 ? apply_step<double>(op, in, out, m, rows_per, which, s)
@@ -2203,7 +2224,10 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     if (op->dst_tc) {
       // buffers and tables before any graph capture
       if ((rc = ensure_split(op, (size_t)m * split_geom(op, nr).bytes_per_rhs)) != AX_OK) return rc;
-      if (!tc_table(op->device, nz) || !tc_flag(op->device)) return AX_ERR_OOM;
+      const bool cz = op->bc_z == 1;
+      if (!tc_table(op->device, nz, cz ? kTableCosForward : kTableSine) ||
+          !tc_table(op->device, nz, cz ? kTableCosInverse : kTableSine) || !tc_flag(op->device))
+        return AX_ERR_OOM;
     }
     if (!cheb && !w->mixed_restart) {
       // FP32 PCG with FP64 residual replacement

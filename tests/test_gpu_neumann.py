@@ -24,6 +24,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
+from oracle import guessnet as G  # noqa: E402
 import scipy.sparse.linalg as spl  # noqa: E402
 import paper_1002_3094_gb300 as P  # noqa: E402
 from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs  # noqa: E402
@@ -276,12 +277,95 @@ def test_batched_mixes_both_boundaries(cuda, method):
         P.ax_destroy_operator(op)
 
 
-def test_tensor_transform_not_built_for_zero_flux(cuda):
-    pr = Pair(_rand_medium(2), 8, 64, cuda)
+def _folded_reference(x, n, three):
+    """The tensor-core cosine forward on the same rounded values: x in FP32,
+    u = x_k + x_{n-1-k} and w = x_k - x_{n-1-k} in FP32 (the middle entry of
+    odd n: u = x, w = 0), each split into BF16 hi + lo, multiplied by
+    C_hi = bf16(C) (and hi by C_lo = bf16(C - C_hi) for three products):
+    out[2l] from u and the even modes, out[2l+1] from w and the odd ones."""
+    ne = (n + 1) // 2
+    x32 = x.astype(np.float32)
+    k = np.arange(ne)
+    xm = x32[:, n - 1 - k]
+    xk = x32[:, k]
+    u = (xk + xm).astype(np.float32)
+    w = (xk - xm).astype(np.float32)
+    if n % 2:
+        u[:, ne - 1] = xk[:, ne - 1]
+        w[:, ne - 1] = 0.0
+    C = _orthonormal_cosine(n)
+    Ch = G.round_bf16(C)
+    Cl = G.round_bf16(C - Ch)
+    out = np.zeros((x.shape[0], n))
+    for v, rows in ((u, np.arange(0, n, 2)), (w, np.arange(1, n, 2))):
+        hi = G.round_bf16(v)
+        lo = G.round_bf16((v.astype(np.float32) - hi.astype(np.float32)).astype(np.float32))
+        M = Ch[rows][:, :ne]
+        out[:, rows] = (hi + lo) @ M.T
+        if three:
+            out[:, rows] += hi @ Cl[rows][:, :ne].T
+    return out
+
+
+@pytest.mark.parametrize("rows,nz", [(7, 1), (5, 2), (9, 3), (130, 64), (33, 127), (260, 1024), (40, 1001)])
+@pytest.mark.parametrize("prec", [P.AX_PREC_FP32_TC, P.AX_PREC_FP32_TC3])
+def test_tensor_cosine_forward_matches_folded_products(cuda, rows, nz, prec):
+    pr = Pair(_rand_medium(4), max(rows, 2), nz, cuda)
+    x = np.random.default_rng(rows + nz).normal(size=(rows, nz))
+    y = torch.zeros((rows, nz), dtype=torch.float64, device=cuda)
+    P.ax_apply_dst(pr.op, pr.dev_array(x), y, rows, prec)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    three = prec == P.AX_PREC_FP32_TC3
+    ref = _folded_reference(x, nz, three)
+    err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 1e-5, err.max()
+    exact = x @ _orthonormal_cosine(nz).T
+    assert np.linalg.norm(got - exact) <= (1e-4 if three else 1e-2) * np.linalg.norm(exact)
+    pr.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(P.AX_PREC_FP32_TC, 2e-2), (P.AX_PREC_FP32_TC3, 1e-4)])
+def test_tensor_cosine_preconditioner_symmetric_and_close(cuda, prec, tol):
+    """B^-1 through the tensor-core cosine pair is C_hi^T T^-1 C_hi: symmetric
+    up to the splitting of its input, and close to the exact B^-1."""
+    nr, nz = 160, 300
+    pr = Pair(_rand_medium(6), nr, nz, cuda)
+    rng = np.random.default_rng(8)
+    u, v = rng.normal(size=(1, nr, nz)), rng.normal(size=(1, nr, nz))
+
+    def apply(x):
+        out = torch.zeros((1, nr, nz), dtype=torch.float64, device=cuda)
+        P.ax_apply_preconditioner(pr.op, pr.dev_array(x), out, 1, prec)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    bu, bv = apply(u), apply(v)
+    a, b = np.sum(u * bv), np.sum(bu * v)
+    assert abs(a - b) <= 1e-5 * np.sqrt(np.sum(u * bu) * np.sum(v * bv))
+    ex = pr.ora.apply_Binv(v[0])
+    assert _rel(bv[0], ex) <= tol
+    pr.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("nr,nz", [(96, 80), (1500, 64)])
+def test_mixed_pcg_tensor_cosine(cuda, form, nr, nz):
+    pr = Pair(_rand_medium(12), nr, nz, cuda)
+    f = pr.rhs()
+    _, i64, _ = _solve(pr, f, P.AX_PCG_FP64, 1e-8)
+    P.ax_set_option(pr.op, "dst_tensor", form)
+    st, imx, u = _solve(pr, f, P.AX_PCG_MIXED, 1e-8)
+    assert st == P.AX_OK
+    for j in range(f.shape[0]):
+        assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-8
+        assert imx[j]["iters"] <= 1.2 * i64[j]["iters"] + 4, (imx[j], i64[j])
+    pr.close()
+
+
+def test_tensor_cosine_rejects_long_columns(cuda):
+    pr = Pair(_rand_medium(2), 4, 4100, cuda)
     with pytest.raises(P.AxError) as e:
         P.ax_set_option(pr.op, "dst_tensor", 1)
     assert e.value.status == P.AX_ERR_UNSUPPORTED
-    x = torch.zeros((2, 64), dtype=torch.float64, device=cuda)
-    with pytest.raises(P.AxError):
-        P.ax_apply_dst(pr.op, x, x.clone(), 2, P.AX_PREC_FP32_TC)
     pr.close()
