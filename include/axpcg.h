@@ -161,6 +161,11 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
+ *   "tc_stall_test"  1: test of the failure path: the next tensor-core transform
+ *                    stops its copies before the first stage, one of its bounded
+ *                    waits (short limit) runs out, the kernel sets the device's
+ *                    error flag, frees its tensor memory and returns; the call
+ *                    returns AX_ERR_TIMEOUT and the context stays usable
  * Unknown names or out-of-range values: AX_ERR_INVALID_ARG. */
 int ax_set_option(ax_operator *op, const char *name, double value);
 

@@ -82,9 +82,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false when it expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  for (unsigned i = 0; i < kWaitPolls; ++i)
+// Bounded wait for the phase with the given parity (at most `polls` tries);
+// false when it expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned polls) {
+  for (unsigned i = 0; i < polls; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int KB = a.ktiles;
+  const unsigned polls = a.polls ? a.polls : kWaitPolls;
   const int ntile_all = a.m * a.mtiles * a.ntiles;
 
   if (threadIdx.x == 0) {
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
         if (!rhs_selected(a.st, a.mask, m)) continue;  // skipped alike by every role
         const int b = it & 1;
         // the epilogue must have drained this buffer (its previous tile)
-        if (it >= 2 && !mbar_wait(&tempty_bar[b], (unsigned)((it >> 1) - 1) & 1u)) {
+        if (it >= 2 && !mbar_wait(&tempty_bar[b], (unsigned)((it >> 1) - 1) & 1u, polls)) {
           ok = false;
           break;
         }
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
         const unsigned accP = tmem + (unsigned)b * kTileCols, accQ = accP + kBN;
         for (int kb = 0; kb < KB; ++kb, ++kk) {
           const int s = kk % kStages;
-          if (!mbar_wait(&full_bar[s], (unsigned)(kk / kStages) & 1u)) {
+          if (!mbar_wait(&full_bar[s], (unsigned)(kk / kStages) & 1u, polls)) {
             ok = false;
             break;
           }
@@ -258,11 +260,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
             reinterpret_cast<const unsigned char *>(a.SB) + (size_t)nt * KB * 2 * kBTileBytes;
         for (int kb = 0; kb < KB; ++kb, ++kk) {
           const int s = kk % kStages;
-          if (kk >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(kk / kStages - 1) & 1u)) {
+          if (kk >= kStages && !mbar_wait(&empty_bar[s], (unsigned)(kk / kStages - 1) & 1u, polls)) {
             ok = false;
             break;
           }
-          if (abort_flag) {
+          if (abort_flag || kk == a.stall_at) {  // stall_at: test of the expiry path, see GemmDstArgs
             ok = false;
             break;
           }
@@ -278,6 +280,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
       if (!ok) {
         atomicExch(&abort_flag, 1);
         if (a.err) atomicExch(a.err, 1);
+        // wait (bounded) for the copies this warp issued before it stopped:
+        // only the last kStages issues can still be in flight
+        for (int j = kk > kStages ? kk - kStages : 0; j < kk; ++j)
+          mbar_wait(&full_bar[j % kStages], (unsigned)(j / kStages) & 1u, polls);
       }
     }
   } else if (warp >= 4) {
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
       if (!rhs_selected(a.st, a.mask, m)) continue;
       const int b = it & 1;
       ++it;
-      const bool ok = !abort_flag && mbar_wait(&tfull_bar[b], (unsigned)((it - 1) >> 1) & 1u);
+      const bool ok = !abort_flag && mbar_wait(&tfull_bar[b], (unsigned)((it - 1) >> 1) & 1u, polls);
       if (!ok) {
         atomicExch(&abort_flag, 1);
         if (a.err) atomicExch(a.err, 1);
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
     // every MMA this CTA issued has completed once its tile's tfull fired; after
     // an expired wait, give the tensor core a bounded moment before freeing
     if (abort_flag) {
-      for (int b = 0; b < 2; ++b) mbar_wait(&tfull_bar[b], 0u);
+      for (int b = 0; b < 2; ++b) mbar_wait(&tfull_bar[b], 0u, polls);
     }
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");

@@ -286,6 +286,13 @@ struct GemmDstArgs {
   // even and the odd output columns (out[2l] = P, out[2l+1] = Q) instead of
   // the mirrored pair
   int cosfwd;
+  // Bounded waits: tries per mbarrier wait (0: the default, ~2^22).  Test of
+  // the expiry path: with stall_at >= 0 the copy warp stops before issuing
+  // stage stall_at, so that the MMA warp's wait for it runs out (the kernel
+  // then sets err, waits for its own copies in flight, frees TMEM and returns);
+  // -1 in normal use.
+  unsigned polls;
+  int stall_at;
 };
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);

@@ -75,6 +75,7 @@ struct Workspace {
   int graph_iters = 16;
   int max_outer = 30;
   int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
+  int tc_stall_test = 0;        // 1: the next tensor-core transform lets one bounded wait run out
   double replace_delta = 1e-2;  // residual reduction between FP64 replacements
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
@@ -1096,6 +1097,13 @@ void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A
   g.pa = pa;
   g.pb = pb;
   g.x = x;
+  g.polls = 0;
+  g.stall_at = -1;
+  if (op->ws->tc_stall_test) {  // test of the expiry path (option "tc_stall_test"), once
+    g.polls = 1u << 14;
+    g.stall_at = 0;
+    op->ws->tc_stall_test = 0;
+  }
   const int kind = op->bc_z == 1 ? (inverse ? kTableCosInverse : kTableCosForward) : kTableSine;
   g.cosfwd = kind == kTableCosForward;
   g.A = A;
@@ -1763,6 +1771,11 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
   } else if (!strcmp(name, "replace_delta")) {
     if (!(value > 0.0 && value < 1.0)) return AX_ERR_INVALID_ARG;
     w->replace_delta = value;
+  } else if (!strcmp(name, "tc_stall_test")) {
+    // The next tensor-core transform stops its copies before the first stage,
+    // so that the MMA warp's bounded wait runs out (short limit): the call
+    // returns AX_ERR_TIMEOUT and the context stays usable.  For tests.
+    w->tc_stall_test = value != 0.0;
   } else if (!strcmp(name, "dst_tensor")) {
     if (value != 0.0 && value != 1.0 && value != 2.0) return AX_ERR_INVALID_ARG;
     if (value != 0.0 && op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;

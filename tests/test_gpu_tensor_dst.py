@@ -134,3 +134,26 @@ def test_tensor_option_rejects_long_columns(cuda):
     with pytest.raises(P.AxError):
         P.ax_set_option(op, "dst_tensor", 1)
     P.ax_destroy_operator(op)
+
+
+def test_bounded_wait_expiry_returns_timeout_and_context_stays_usable(cuda):
+    """The failure path of the tensor-core transform without a fault: the
+    copy warp stops before its first stage, the MMA warp's bounded wait runs
+    out, the kernel flags the error, frees its tensor memory and returns; the
+    call reports AX_ERR_TIMEOUT, and the next call computes the transform."""
+    rows, nz = 64, 256
+    op, _, _ = _op(rows, nz, cuda)
+    x = np.random.default_rng(1).normal(size=(rows, nz))
+    xd = torch.from_numpy(x).to(cuda)
+    y = torch.zeros((rows, nz), dtype=torch.float64, device=cuda)
+    P.ax_set_option(op, "tc_stall_test", 1)
+    with pytest.raises(P.AxError) as e:
+        P.ax_apply_dst(op, xd, y, rows, P.AX_PREC_FP32_TC3)
+    assert e.value.status == P.AX_ERR_TIMEOUT
+    y.zero_()
+    P.ax_apply_dst(op, xd, y, rows, P.AX_PREC_FP32_TC3)
+    torch.cuda.synchronize()
+    ref = _split_reference(x, nz, True)
+    err = np.linalg.norm(y.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 1e-5
+    P.ax_destroy_operator(op)
