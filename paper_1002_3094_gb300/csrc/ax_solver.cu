@@ -1325,9 +1325,6 @@ struct ChebVecs {
 };
 
 template <typename T>
-__global__ void cheb_swap_dummy() {}
-
-template <typename T>
 void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, Workspace *w,
                     int on_converge, int parity, cudaStream_t s) {
   const int V = VecT<T>::n;
