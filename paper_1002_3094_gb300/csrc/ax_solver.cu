@@ -429,7 +429,14 @@ __global__ void fold_df(float *__restrict__ xh, float *__restrict__ xl, float *_
 // its load phase.  p is pb for an even iteration count, pa for an odd one (as
 // in the stencil).  x == nullptr: r only (the iterate update then happens in
 // the inverse transform's epilogue, with the next direction).
-constexpr int kUpdateBlocks = 64;  // CTAs per right-hand side
+// CTAs per right-hand side of the update and split passes: about four
+// 8-column tasks per thread (at least 64, at most 4096 CTAs), so that large
+// fields keep enough loads in flight.
+int update_blocks(int rows, int nz) {
+  const long long tasks = (long long)rows * ((nz + 7) / 8);
+  const long long b = (tasks + 4 * 256 - 1) / (4 * 256);
+  return (int)std::max(64LL, std::min(4096LL, b));
+}
 __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *__restrict__ r,
                                                   const float *__restrict__ q, const float *__restrict__ pa,
                                                   const float *__restrict__ pb, int nr, int n, int pitch,
@@ -1132,7 +1139,8 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
               int mask, cudaStream_t s) {
   const SplitGeom g = split_geom(op, rows);
   note_launch();
-  split_field<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(in, rows, op->nz, op->pitch, (size_t)rows * op->pitch,
+  split_field<<<dim3(update_blocks(rows, op->nz), m), 256, 0, s>>>(in, rows, op->nz, op->pitch,
+                                                                   (size_t)rows * op->pitch,
                                                       g.mtiles, g.ktiles, g.kbe, split, st, mask, op->bc_z == 1);
 }
 
@@ -1250,7 +1258,8 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       {
         ProfScope ps(w, kProfUpdate, units, s);
         note_launch();
-        pcg_update<<<dim3(kUpdateBlocks, m), 256, 0, s>>>(fused ? nullptr : v.x, v.r, v.q, v.pa, v.pb, op->nr,
+        pcg_update<<<dim3(update_blocks(op->nr, op->nz), m), 256, 0, s>>>(fused ? nullptr : v.x, v.r, v.q, v.pa,
+                                                                           v.pb, op->nr,
                                                           op->nz, op->pitch, field_elems(op), g.mtiles, g.ktiles,
                                                           g.kbe, sp, st, kActive, prr, op->bc_z == 1);
         if (op->bc_z == 1) tc_split(op, m, op->nr, v.r, sp, st, kActive, s);
@@ -1259,7 +1268,7 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
         note_launch();
-        sc_after_update<<<m, 32, 0, s>>>(st, prr, kUpdateBlocks, on_converge);
+        sc_after_update<<<m, 32, 0, s>>>(st, prr, update_blocks(op->nr, op->nz), on_converge);
       }
       const bool dm = tc_dot_in_modes(op);
       {
