@@ -153,7 +153,9 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
  *                    close to B^-1); 0: the FFT transform.  Default: 1 when
  *                    nz <= 4096 and the FFT length nz + 1 has a prime factor
- *                    above 7 (e.g. 1025 = 5^2 41), or bc_z = 1; else 0.
+ *                    above 7 (e.g. 1025 = 5^2 41), or bc_z = 1 and nr <= 1024;
+ *                    else 0 (on some tall weakly absorbing instances the split-BF16
+ *                    transform costs the mixed PCG several times the iterations).
  *                    For bc_z = 1 the tensor-core transform multiplies by the
  *                    orthonormal cosine pair (the forward on folded input:
  *                    r_k + r_{n-1-k} against the even modes, r_k - r_{n-1-k}
@@ -161,6 +163,9 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    AX_ERR_UNSUPPORTED
  *   "mixed_restart"  1: AX_PCG_MIXED runs restarted iterative refinement (FP32
  *                    inner PCG to "inner_tol", x += d in FP64) instead
+ *   "tc_fused"       1 (default): with the tensor-core transform, the mixed PCG
+ *                    forms p = z + beta p and x += alpha p in the inverse
+ *                    transform's epilogue; 0: in the stencil and update pass
  *   "tc_stall_test"  1: test of the failure path: the next tensor-core transform
  *                    stops its copies before the first stage, one of its bounded
  *                    waits (short limit) runs out, the kernel sets the device's

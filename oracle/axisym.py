@@ -9,7 +9,7 @@ Array conventions: a grid function y is an array of shape (nr, nz) with
 y[a, b] the value at r-node i = a + 1 and z-node k = b + 1 (z fastest).  The
 flat unknown index is a * nz + b.
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here:
 * z boundary, bc_z = 0: homogeneous Dirichlet at z = 0 and z = 1 on the
   vertex grid z_k = k h_z, h_z = 1 / (nz + 1), k = 1..nz, faces
   zbar_k = (k + 1/2) h_z, k = 0..nz; the sine transform diagonalises the

@@ -76,6 +76,7 @@ struct Workspace {
   int max_outer = 30;
   int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
   int tc_stall_test = 0;        // 1: the next tensor-core transform lets one bounded wait run out
+  int tc_unfused = 0;           // 1: mixed PCG forms p in the stencil, not in the inverse transform
   double replace_delta = 1e-2;  // residual reduction between FP64 replacements
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
@@ -1222,7 +1223,7 @@ struct PcgVecs {
 // transform's epilogue forms the next direction p = z + beta p and updates x
 // (beta is known before it because the mode solves give the (r, z) partials),
 // so z is never stored, the stencil reads p alone and the update pass only r.
-bool tc_fused(const ax_operator *op) { return use_tc<float>(op) && tc_dot_in_modes(op); }
+bool tc_fused(const ax_operator *op) { return use_tc<float>(op) && tc_dot_in_modes(op) && !op->ws->tc_unfused; }
 
 // One PCG iteration for the right-hand sides in kActive.  fused (FP32
 // tensor-core path with tc_fused only): p was formed by the previous
@@ -1777,6 +1778,9 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
   } else if (!strcmp(name, "replace_delta")) {
     if (!(value > 0.0 && value < 1.0)) return AX_ERR_INVALID_ARG;
     w->replace_delta = value;
+  } else if (!strcmp(name, "tc_fused")) {
+    w->tc_unfused = value == 0.0;
+    free_graph(w->g32);
   } else if (!strcmp(name, "tc_stall_test")) {
     // The next tensor-core transform stops its copies before the first stage,
     // so that the MMA warp's bounded wait runs out (short limit): the call
@@ -1865,14 +1869,18 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   // Transform of the FP32 path: the tensor-core GEMM when nz is within its
   // range and either the sine FFT of length L needs a prime radix above 8
   // (paired direct DFT or Rader stages, several times the work of the small
-  // radices) or the transform is the cosine pair (its FFT form reads and
-  // writes each row twice around the packing; at nz = 1024 the GEMM pair
-  // solves in 2/3 of the time).
+  // radices) or the transform is the cosine pair on at most 1024 rows (its FFT
+  // form reads and writes each row twice around the packing; at 1024^2 the
+  // GEMM pair solves in 2/3 of the time).  Measured limits of the split-BF16
+  // transform: on some tall, weakly absorbing instances (2047 rows, small q)
+  // the mixed PCG needs several times the iterations with the GEMM pair, and
+  // with the sine GEMM when L is a power of two; those keep the FFT.
   op->dst_tc = 0;
   if (nz <= kMaxTcN) {
-    if (cosine) op->dst_tc = 1;
-    for (int i = 0; i < op->plan.nstages; ++i)
-      if (op->plan.radix[i] > 8) op->dst_tc = 1;
+    if (cosine && nr <= 1024) op->dst_tc = 1;
+    if (!cosine)
+      for (int i = 0; i < op->plan.nstages; ++i)
+        if (op->plan.radix[i] > 8) op->dst_tc = 1;
   }
 
   const double hr = op->hr, hz = op->hz, hr2 = hr * hr, hz2 = hz * hz;

@@ -363,6 +363,24 @@ def test_mixed_pcg_tensor_cosine(cuda, form, nr, nz):
     pr.close()
 
 
+@pytest.mark.parametrize("fused", [0, 1])
+def test_mixed_pcg_tensor_cosine_fused_and_unfused(cuda, fused):
+    """The direction update p = z + beta p and x += alpha p run either in the
+    inverse transform's epilogue or in the stencil and update pass: both
+    reach the tolerance with the iterations of the FP64 method."""
+    pr = Pair(_rand_medium(15), 200, 136, cuda)
+    f = pr.rhs()
+    _, i64, _ = _solve(pr, f, P.AX_PCG_FP64, 1e-8)
+    P.ax_set_option(pr.op, "dst_tensor", 1)
+    P.ax_set_option(pr.op, "tc_fused", fused)
+    st, imx, u = _solve(pr, f, P.AX_PCG_MIXED, 1e-8)
+    assert st == P.AX_OK
+    for j in range(f.shape[0]):
+        assert _oracle_rel_res(pr, f[j], u[j]) <= 1e-8
+        assert imx[j]["iters"] <= 1.2 * i64[j]["iters"] + 4, (imx[j], i64[j])
+    pr.close()
+
+
 def test_tensor_cosine_rejects_long_columns(cuda):
     pr = Pair(_rand_medium(2), 4, 4100, cuda)
     with pytest.raises(P.AxError) as e:
