@@ -138,6 +138,8 @@ def parse_args():
     ap.add_argument("--dst-tensor", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="FP32 path transform along z: -1 the library's choice, 0 FFT, 1 tensor-core GEMM "
                          "by S_hi + S_lo, 2 tensor-core GEMM by S_hi (option dst_tensor)")
+    ap.add_argument("--replace-delta", type=float, default=0.0,
+                    help="mixed PCG: residual reduction between FP64 residual replacements (0: the library's)")
     return ap.parse_args()
 
 
@@ -350,9 +352,11 @@ def run_batched(args):
         fs.append(torch.from_numpy(sample_rhs(med, nr, nz, bc_z=args.bc_z)[0]).to(dev))
         us.append(torch.zeros((nr, nz), dtype=torch.float64, device=dev))
         unknowns += nr * nz
-    if args.dst_tensor >= 0:
-        for op in ops:
+    for op in ops:
+        if args.dst_tensor >= 0:
             P.ax_set_option(op, "dst_tensor", args.dst_tensor)
+        if args.replace_delta > 0:
+            P.ax_set_option(op, "replace_delta", args.replace_delta)
     batch = P.ax_batch_create(ops)
     method = P.METHODS[args.method]
     stream = torch.cuda.current_stream()
@@ -515,6 +519,8 @@ def main():
     op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz, bc_z=args.bc_z)
     if args.dst_tensor >= 0:
         P.ax_set_option(op, "dst_tensor", args.dst_tensor)
+    if args.replace_delta > 0:
+        P.ax_set_option(op, "replace_delta", args.replace_delta)
     f_host = sample_rhs(med, nr, nz, bc_z=args.bc_z)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)

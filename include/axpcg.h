@@ -145,7 +145,10 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *   "max_outer"      cap on FP64 refinement steps (default 30)
  *   "replace_delta"  AX_PCG_MIXED: recursive-residual reduction (relative to the
  *                    last FP64 true residual) that triggers the next FP64
- *                    residual replacement (0 < v < 1, default 1e-2)
+ *                    residual replacement (0 < v < 1, default 0.1; with 1e-2
+ *                    the FP32 recursion of the tensor-core path can drift for
+ *                    many iterations between replacements on ill-conditioned
+ *                    media)
  *   "dst_tensor"     AX_PCG_MIXED's FP32 kernels transform along z with the
  *                    tcgen05 tensor-core GEMM: 1 by S_hi + S_lo (three BF16
  *                    products, S to about 2^-16), 2 by S_hi = bf16(S) alone
@@ -153,9 +156,7 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *                    S, so the preconditioner S_hi T^-1 S_hi stays SPD and
  *                    close to B^-1); 0: the FFT transform.  Default: 1 when
  *                    nz <= 4096 and the FFT length nz + 1 has a prime factor
- *                    above 7 (e.g. 1025 = 5^2 41), or bc_z = 1 and nr <= 1024;
- *                    else 0 (on some tall weakly absorbing instances the split-BF16
- *                    transform costs the mixed PCG several times the iterations).
+ *                    above 7 (e.g. 1025 = 5^2 41), or bc_z = 1; else 0.
  *                    For bc_z = 1 the tensor-core transform multiplies by the
  *                    orthonormal cosine pair (the forward on folded input:
  *                    r_k + r_{n-1-k} against the even modes, r_k - r_{n-1-k}
@@ -191,7 +192,9 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
  * streams.  The paper has no batched form; it solves one series of right-hand
  * sides per operator (Eq. main_problem).
  * ax_batch_create copies the tables of `ops` (the operators stay owned by the
- * caller and may be destroyed afterwards).  Synchronises `stream`.
+ * caller and may be destroyed afterwards) and the solver options set with
+ * ax_set_option (instances of one shape share those of the first of them).
+ * Synchronises `stream`.
  * ax_batch_solve: f[i], u[i] are device arrays [nr_i][nz_i] of instance i;
  * every method of ax_solve (the Chebyshev methods with each instance's own
  * gamma bounds, hence its own tau_0 and rho_0); info is a host array [n]

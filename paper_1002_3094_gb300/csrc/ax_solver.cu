@@ -77,7 +77,7 @@ struct Workspace {
   int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
   int tc_stall_test = 0;        // 1: the next tensor-core transform lets one bounded wait run out
   int tc_unfused = 0;           // 1: mixed PCG forms p in the stencil, not in the inverse transform
-  double replace_delta = 1e-2;  // residual reduction between FP64 replacements
+  double replace_delta = 0.1;   // residual reduction between FP64 replacements
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
   std::vector<ProfEvent> prof_events;
@@ -1869,18 +1869,14 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   // Transform of the FP32 path: the tensor-core GEMM when nz is within its
   // range and either the sine FFT of length L needs a prime radix above 8
   // (paired direct DFT or Rader stages, several times the work of the small
-  // radices) or the transform is the cosine pair on at most 1024 rows (its FFT
-  // form reads and writes each row twice around the packing; at 1024^2 the
-  // GEMM pair solves in 2/3 of the time).  Measured limits of the split-BF16
-  // transform: on some tall, weakly absorbing instances (2047 rows, small q)
-  // the mixed PCG needs several times the iterations with the GEMM pair, and
-  // with the sine GEMM when L is a power of two; those keep the FFT.
+  // radices) or the transform is the cosine pair (its FFT form reads and
+  // writes each row twice around the packing; at 1024^2 the GEMM pair solves
+  // in 2/3 of the time).
   op->dst_tc = 0;
   if (nz <= kMaxTcN) {
-    if (cosine && nr <= 1024) op->dst_tc = 1;
-    if (!cosine)
-      for (int i = 0; i < op->plan.nstages; ++i)
-        if (op->plan.radix[i] > 8) op->dst_tc = 1;
+    if (cosine) op->dst_tc = 1;
+    for (int i = 0; i < op->plan.nstages; ++i)
+      if (op->plan.radix[i] > 8) op->dst_tc = 1;
   }
 
   const double hr = op->hr, hz = op->hz, hr2 = hr * hr, hz2 = hz * hz;
@@ -2486,6 +2482,17 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     const ax_operator *o = mops[0];
     ax_operator *gop = new ax_operator();
     gop->ws = new Workspace();
+    {  // solver options of the group: those of its first member
+      Workspace *gw = gop->ws;
+      const Workspace *ow = o->ws;
+      gw->inner_tol = ow->inner_tol;
+      gw->inner_max = ow->inner_max;
+      gw->graph_iters = ow->graph_iters;
+      gw->max_outer = ow->max_outer;
+      gw->mixed_restart = ow->mixed_restart;
+      gw->tc_unfused = ow->tc_unfused;
+      gw->replace_delta = ow->replace_delta;
+    }
     gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz; gop->bc_z = o->bc_z;
     gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;
     gop->kappa_t = o->kappa_t; gop->q_t = o->q_t; gop->gamma1 = o->gamma1; gop->gamma2 = o->gamma2;

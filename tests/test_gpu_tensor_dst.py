@@ -129,6 +129,37 @@ def test_mixed_pcg_with_tensor_transform_meets_tolerance(cuda, form, nr, nz):
     P.ax_destroy_operator(op)
 
 
+@pytest.mark.parametrize("j,nr,nz,bc", [(66, 2047, 255, 0), (66, 2047, 1024, 0), (3, 1024, 4096, 0),
+                                         (186, 2047, 1023, 1)])
+def test_mixed_pcg_tensor_transform_ill_conditioned_media(cuda, j, nr, nz, bc):
+    """Random-field media of the batched workload whose FP32 recursion, with
+    the split-BF16 transform, drifted for up to 50 times the iterations when
+    the FP64 residual replacement came only every 100-fold residual reduction:
+    with the default (every 10-fold reduction) the tensor-core path needs
+    about the FFT path's iterations, and both meet the tolerance in the
+    oracle's FP64 residual (bc = 1: the cosine pair of the zero-flux
+    boundary)."""
+    from workloads import batched_instances
+    _, _, med = batched_instances(256)[j]
+    kr, kz, q = sample_operator_inputs(med, nr, nz, bc_z=bc)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(cuda) for x in (kr, kz, q)], nr, nz, bc_z=bc)
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz, bc_z=bc))
+    f = sample_rhs(med, nr, nz, bc_z=bc)[:1]
+    fd = torch.from_numpy(f).to(cuda)
+    iters = {}
+    for form in (0, 1):
+        P.ax_set_option(op, "dst_tensor", form)
+        u = torch.zeros_like(fd)
+        st, info = P.ax_solve(op, fd, u, 1, 1e-8, 2000, P.AX_PCG_MIXED)
+        torch.cuda.synchronize()
+        assert st == P.AX_OK
+        phi = ora.phi(f[0])
+        assert np.linalg.norm(phi - ora.apply_A(u.cpu().numpy()[0])) <= 1e-8 * np.linalg.norm(phi)
+        iters[form] = info[0]["iters"]
+    assert iters[1] <= 1.3 * iters[0] + 4, iters
+    P.ax_destroy_operator(op)
+
+
 def test_tensor_option_rejects_long_columns(cuda):
     op, _, _ = _op(4, 4100, cuda)
     with pytest.raises(P.AxError):
