@@ -295,6 +295,57 @@ def test_full_size_layered_1024_m64_sampled(cuda):
     P.ax_destroy_operator(op)
 
 
+def test_full_size_large_4096_m16_sampled(cuda):
+    """The 4096 x 4096 workload with 16 right-hand sides in the benchmark's
+    launch configuration (mixed PCG, tensor-core transform of length 4097,
+    tol 1e-8): the oracle's FP64 true residual of two sampled right-hand
+    sides, and the (rhat, yhat)-based iteration count within a few of the
+    FP64 method's on the first one."""
+    from workloads import large_medium
+    nr = nz = 4096
+    med = large_medium(16, 4096)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    t = [torch.from_numpy(x).cuda() for x in (kr, kz, q)]
+    op = P.ax_setup_operator(*t, nr, nz)
+    fh = sample_rhs(med, nr, nz)
+    f = torch.from_numpy(fh).cuda()
+    u = torch.zeros_like(f)
+    st, info = P.ax_solve(op, f, u, 16, 1e-8, 5000, P.AX_PCG_MIXED)
+    assert st == P.AX_OK
+    uh = u.cpu().numpy()
+    del u
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
+    for j in (0, 11):
+        phi = ora.phi(fh[j])
+        assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1e-8 * np.linalg.norm(phi)
+    u64 = torch.zeros_like(f[:1])
+    _, i64 = P.ax_solve(op, f[:1], u64, 1, 1e-8, 5000, P.AX_PCG_FP64)
+    assert info[0]["iters"] <= 1.2 * i64[0]["iters"] + 4, (info[0], i64[0])
+    P.ax_destroy_operator(op)
+
+
+def test_full_size_layered_1024_m64_zero_flux_sampled(cuda):
+    """The benchmark's workload with the paper's zero-flux z boundary
+    (tensor-core cosine pair): the oracle's FP64 true residual of sampled
+    right-hand sides."""
+    nr = nz = 1024
+    med = layered_inclusion_medium(64, 1024)
+    kr, kz, q = sample_operator_inputs(med, nr, nz, bc_z=1)
+    t = [torch.from_numpy(x).cuda() for x in (kr, kz, q)]
+    op = P.ax_setup_operator(*t, nr, nz, bc_z=1)
+    fh = sample_rhs(med, nr, nz, bc_z=1)
+    f = torch.from_numpy(fh).cuda()
+    u = torch.zeros_like(f)
+    st, info = P.ax_solve(op, f, u, 64, 1e-8, 5000, P.AX_PCG_MIXED)
+    assert st == P.AX_OK
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz, bc_z=1))
+    uh = u.cpu().numpy()
+    for j in (0, 40, 63):
+        phi = ora.phi(fh[j])
+        assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1e-8 * np.linalg.norm(phi)
+    P.ax_destroy_operator(op)
+
+
 def test_mixed_replacement_keeps_fp64_iteration_count(cuda):
     """FP32 PCG with FP64 residual replacement keeps the search direction, so
     its iteration count stays close to the FP64 method's; the restarted
