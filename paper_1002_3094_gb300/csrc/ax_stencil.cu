@@ -31,9 +31,6 @@ struct StencilValue {
   }
 };
 
-// rows between the L2 prefetch of the grid function and its use
-constexpr int kStencilPrefetch = 4;
-
 // Hint: bring the line holding p into L2 (no register, no completion; p must
 // be a valid global address).
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -111,6 +108,15 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     if (k0 <= nz) load_vec<T>(CZ + (size_t)i * a.pitchz + k0, v);
   };
 
+  // every row of the DRAM stream(s) this CTA reads, into L2 at once: the
+  // register loads below then wait on L2 instead of DRAM
+  if (col_ok)
+    for (int i = max(i0 - 1, 0); i <= i1 && i < nr; ++i) {
+      const size_t off = base + (size_t)i * a.pitch + k0;
+      prefetch_l2(src + off);
+      if (MODE == kStencilPcg) prefetch_l2(p_old + off);
+      if ((MODE == kStencilResidual || MODE == kStencilCheb) && i >= i0 && i < i1) prefetch_l2(a.phi + off);
+    }
   T pm[V], pc[V], pn[V], crl[V], crh[V], czl[V], w[V];
   T left, right, czlast;
   if (i0 > 0) {
@@ -131,11 +137,6 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   T acc = T(0);
   for (int i = i0; i < i1; ++i) {
     T crn[V], czn[V], wn[V], leftn = T(0), rightn = T(0), czlastn = T(0);
-    if (i + kStencilPrefetch < nr && col_ok) {  // the DRAM stream, a few rows ahead, into L2
-      const size_t off = base + (size_t)(i + kStencilPrefetch) * a.pitch + k0;
-      prefetch_l2(src + off);
-      if (MODE == kStencilPcg) prefetch_l2(p_old + off);
-    }
     if (i + 1 < nr) {
       load_row(i + 1, pn);
     } else {
