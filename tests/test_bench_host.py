@@ -1,0 +1,51 @@
+"""Host logic of bench.py that needs no GPU: the JSON line of the reference
+arm (the FP64 oracle timed on the host cores), the source hashing that keeps a
+recorded ncu traffic figure tied to the kernel it was measured on, and the
+table lookup that scales it to a launch."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench as B  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "bumps_64", "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "unknowns/s"
+    assert d["metric"] == B.METRIC and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["config"]["workload"] == "bumps_64"
+
+
+def test_function_text_is_one_global_function():
+    src = open(os.path.join(ROOT, "paper_1002_3094_gb300", "csrc", "ax_stencil.cu")).read()
+    text = B._function_text(src, "residual_df_kernel")
+    assert text.splitlines()[0].startswith("__global__") and "residual_df_kernel(" in text.splitlines()[0]
+    assert text.rstrip().endswith("}") and "stencil_kernel(" not in text
+    assert len(B.source_hash("stencil")) == 16 and B.source_hash("stencil") != B.source_hash("outer_residual")
+
+
+def test_traffic_row_applies_only_to_the_source_it_was_measured_on(tmp_path, monkeypatch):
+    table = tmp_path / "traffic.md"
+    table.write_text("| class | DRAM bytes / unknown | source sha | kernel |\n|---|---:|---|---|\n"
+                     f"| stencil | 6.5 | `{B.source_hash('stencil')}` | `stencil_kernel` |\n"
+                     "| pcg_update | 12.0 | `0000000000000000` | `pcg_update` |\n")
+    monkeypatch.setattr(B, "TRAFFIC_TABLE", str(table))
+    assert B.measured_traffic("stencil", 1000.0) == pytest.approx(6500.0)
+    assert B.measured_traffic("pcg_update", 1000.0) is None  # recorded on other code
+    assert B.measured_traffic("mode_solve", 1000.0) is None  # never recorded
