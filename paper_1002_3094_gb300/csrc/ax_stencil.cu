@@ -261,7 +261,7 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
   return df_fast(p, e);
 }
 
-constexpr int kDfRows = 8;       // rows per CTA (short: few right-hand sides are due at a time)
+constexpr int kDfRows = 16;      // rows per CTA (short: few right-hand sides are due at a time)
 constexpr int kDfThreads = 256;  // 4 z-nodes per thread
 
 __global__ void __launch_bounds__(kDfThreads) residual_df_kernel(const DfResidualArgs a) {
