@@ -7,9 +7,11 @@ its Python binding never import it and share no code with it.
 Every function follows one passage of the paper (Terekhov, "High performance
 parallel algorithm for solving elliptic equations with non-separable
 variables", arXiv 1002.3094); the docstrings name the section and equation.
-All functions are pinned by ``tests/test_oracle.py`` against closed forms,
+All functions are pinned by ``tests/test_oracle.py`` (and the Laguerre chain of
+``laguerre.py`` by ``tests/test_oracle_laguerre.py``) against closed forms,
 library routines, brute force on tiny grids and a manufactured solution.
 """
+from . import laguerre  # noqa: F401
 from .axisym import (  # noqa: F401
     Grid,
     sample_medium,
