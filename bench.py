@@ -138,6 +138,7 @@ def parse_args():
     ap.add_argument("--dst-tensor", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="FP32 path transform along z: -1 the library's choice, 0 FFT, 1 tensor-core GEMM "
                          "by S_hi + S_lo, 2 tensor-core GEMM by S_hi (option dst_tensor)")
+    ap.add_argument("--harmonics", type=int, default=2000, help="laguerre_chain: number of harmonics")
     ap.add_argument("--replace-delta", type=float, default=0.0,
                     help="mixed PCG: residual reduction between FP64 residual replacements (0: the library's)")
     return ap.parse_args()
@@ -411,6 +412,72 @@ def run_batched(args):
         P.ax_destroy_operator(op)
 
 
+def run_laguerre(args):
+    """Workload laguerre_chain (Section 4.1): the harmonics Q_0 .. Q_{n-1} of the
+    Laguerre expansion in time (n = --harmonics, default 2000, alpha = 5,
+    h = 300 as in the paper) on a 1024 x 1024 grid of a 2048 m x 2048 m layered
+    medium with a fault, zero-flux z boundary, point source at the origin.  One
+    step = the whole sequential chain; value = n nr nz / time.  The source
+    coefficients are scaled by 1 / max |f_m| (the problem is linear)."""
+    import numpy as np
+    import torch
+    import paper_1002_3094_gb300 as P
+    from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs
+    from paper_1002_3094_gb300.laguerre import solve_chain
+    from workloads.laguerre import ALPHA, H_LAG, fault_medium, wavelet_coefficients
+    nr = nz = 1024
+    lr = lz = 2048.0
+    n = args.harmonics
+    dev = torch.device("cuda", 0)
+    P.build()
+    P.load_library()
+    med = fault_medium(lr, lz)
+    kr, kz, q = sample_operator_inputs(med, nr, nz, lr, lz, bc_z=1)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz, lr, lz, bc_z=1)
+    if args.replace_delta > 0:
+        P.ax_set_option(op, "replace_delta", args.replace_delta)
+    src = torch.from_numpy(sample_rhs(med, nr, nz, lr, lz, bc_z=1)[0]).to(dev)
+    c2 = torch.from_numpy(4.0 * q).to(dev)
+    fm = wavelet_coefficients(n, ALPHA, H_LAG)
+    fm = fm / np.abs(fm).max()
+    method = P.METHODS[args.method]
+    stream = torch.cuda.current_stream()
+    qf = torch.zeros((1, nr, nz), dtype=torch.float64, device=dev)
+    work = torch.zeros((3, nr, nz), dtype=torch.float64, device=dev)
+
+    def chain():
+        return solve_chain(op, c2, src, fm, ALPHA, TOL, qf, work, method=method, stream=stream)
+
+    for _ in range(args.warmup):
+        chain()
+    torch.cuda.synchronize()
+    launches0 = P.ax_kernel_launches()
+    clocks = ClockSampler(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        infos = chain()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    iters = [i["iters"] for i in infos]
+    line = {"metric": METRIC, "value": n * nr * nz * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64", "data": "synthetic",
+            "config": {"workload": "laguerre_chain", "nr": nr, "nz": nz, "lr_m": lr, "lz_m": lz, "harmonics": n,
+                       "alpha": ALPHA, "h": H_LAG, "bc_z": 1, "method": args.method, "tol": TOL,
+                       "warm_start": "previous harmonic (gated)"},
+            "ms_per_harmonic": ms / args.steps / n,
+            "iters": {"mean": float(np.mean(iters)), "max": max(iters), "min": min(iters),
+                      "preconditioner_applications": int(sum(iters))},
+            "max_rel_res": max(i["rel_res"] for i in infos),
+            "gpu_launches": P.ax_kernel_launches() - launches0, "clocks": clk}
+    print(json.dumps(line))
+    P.ax_destroy_operator(op)
+
+
 def run_guess(args):
     """Workload guess_256 (random-field media on 256 x 256): solve
     `--train` seeds with the batched solver, train the guess network on the
@@ -487,6 +554,12 @@ def main():
         return
     if args.workload == "guess_256":
         run_guess(args)
+        return
+    if args.workload == "laguerre_chain":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times layered_1024_m64 only"}))
+        else:
+            run_laguerre(args)
         return
     if args.workload == "batched_256":
         run_batched(args)

@@ -312,6 +312,26 @@ int ax_apply_preconditioner(ax_operator *op, const double *in, double *out, int3
 int ax_apply_preconditioner_noalloc(ax_operator *op, const double *in, double *out, int32_t m,
                                     int32_t precision, void *stream);
 
+/* ---- Laguerre-harmonic chain ---------------------------------------------
+ * Section 4.1, Eq. laguerre_h: harmonic m of the Laguerre transform in time
+ * solves the operator of ax_solve with kappa = V, q = h^2 / (4 rho^2) and the
+ * physical right-hand side
+ *   f_m src - c2 a_m S_m,   S_m = sum_{k<m} (m - k) w_k Q_k,
+ *   a_m = sqrt(m! / (m + alpha)!),  w_k = sqrt((k + alpha)! / k!),  c2 = h^2 / rho^2,
+ * where src approximates the point source delta(x - x_0) and f_m is the m-th
+ * Laguerre coefficient of the source wavelet.  After Q_m is solved,
+ * ax_laguerre_step advances the running fields
+ *   T <- T + w_m Q_m   (T = sum_{k<=m} w_k Q_k),   S <- S + T   (S = S_{m+1})
+ * and writes the right-hand side of harmonic m + 1:
+ *   f_out = f_next src - c2 a_next S,   (w_m, a_next, f_next: host scalars).
+ * T and S start at zero (harmonic 0 has f = f_0 src).  Q, T, S, c2, src and
+ * f_out are dense FP64 device arrays [nr][nz] of op's grid (caller-owned; f_out
+ * must not overlap the others).  Errors: AX_ERR_INVALID_ARG for a null
+ * pointer or a non-finite scalar; AX_ERR_CUDA if the launch fails. */
+int ax_laguerre_step(ax_operator *op, const double *Q, double *T, double *S, const double *c2,
+                     const double *src, double w_m, double a_next, double f_next, double *f_out,
+                     void *stream);
+
 /* ---- diagnostics ----------------------------------------------------------
  * Number of CUDA kernels this library has issued in this process (direct
  * launches plus the kernel nodes of replayed graphs). */

@@ -43,7 +43,7 @@ METHODS = {"pcg64": AX_PCG_FP64, "cheb64": AX_CHEB_FP64, "pcg_mixed": AX_PCG_MIX
 EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_set_option", "ax_solve",
             "ax_apply_operator", "ax_apply_dst", "ax_apply_dst_inverse", "ax_apply_mode_solve",
             "ax_apply_preconditioner", "ax_status_string", "ax_version", "ax_kernel_launches", "ax_profile_read",
-            "ax_apply_preconditioner_noalloc", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
+            "ax_apply_preconditioner_noalloc", "ax_laguerre_step", "ax_batch_create", "ax_batch_solve", "ax_batch_latency",
             "ax_batch_destroy", "ax_solve_batched", "ax_last_error",
             "ax_guessnet_create", "ax_guessnet_destroy", "ax_guessnet_num_params", "ax_guessnet_get_params",
             "ax_guessnet_set_params", "ax_guessnet_forward", "ax_guessnet_gradients", "ax_guessnet_train_step",
@@ -122,6 +122,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_guessnet_lift.argtypes = [vp, i32, i32, vp, i32, i32, vp, vp]
     lib.ax_guessnet_set_loss.argtypes = [vp, dbl]
     lib.ax_guessnet_features_pre.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp]
+    lib.ax_laguerre_step.argtypes = [vp, vp, vp, vp, vp, vp, dbl, dbl, dbl, vp, vp]
     lib.ax_kernel_launches.argtypes = []
     lib.ax_kernel_launches.restype = ctypes.c_int64
     lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
@@ -239,6 +240,13 @@ def ax_apply_preconditioner_noalloc(op, x, y, m, precision=AX_PREC_FP64, stream=
     """B^-1 without device allocation: stages through the library's fixed
     32 MiB array (see include/axpcg.h)."""
     _apply("ax_apply_preconditioner_noalloc", op, x, y, m, precision, stream)
+
+
+def ax_laguerre_step(op, Q, T, S, c2, src, w_m: float, a_next: float, f_next: float, f_out, stream=None) -> None:
+    """T += w_m Q, S += T, f_out = f_next src - c2 a_next S (dense FP64 device
+    arrays [nr][nz]; see include/axpcg.h)."""
+    _check(load_library().ax_laguerre_step(op, _ptr(Q), _ptr(T), _ptr(S), _ptr(c2), _ptr(src), w_m, a_next, f_next,
+                                           _ptr(f_out), _stream(stream)), "ax_laguerre_step")
 
 
 def ax_kernel_launches() -> int:

@@ -58,6 +58,7 @@ struct Workspace {
   // partial sums [4][m][kPartialStride]
   double *part = nullptr;
   double *chp = nullptr;      // Chebyshev (tau, rho0^2) per right-hand side [m][2]
+  double *rscale = nullptr;   // mixed methods: power-of-two scale of phi and x per right-hand side [m]
   RhsState *st = nullptr, *st_outer = nullptr;
   RhsState *h_st = nullptr;   // pinned host mirror [2 m]
   // dense FP64 staging for host buffers and single-step entry points
@@ -171,7 +172,8 @@ void free_vectors32(Workspace *w) {
   free_graph(w->gc32);
 }
 void free_base(Workspace *w) {
-  dfree(w->phi64); dfree(w->x64); dfree(w->part); dfree(w->chp); dfree(w->st); dfree(w->st_outer);
+  dfree(w->phi64); dfree(w->x64); dfree(w->part); dfree(w->chp); dfree(w->rscale); dfree(w->st);
+  dfree(w->st_outer);
   if (w->h_st) cudaFreeHost(w->h_st);
   w->h_st = nullptr;
   w->mbase = 0;
@@ -190,6 +192,7 @@ int ensure_base(ax_operator *op, int m) {
   AX_TRY(dalloc(&w->x64, f));
   AX_TRY(dalloc(&w->part, (size_t)4 * m * kPartialStride));
   AX_TRY(dalloc(&w->chp, (size_t)2 * m));
+  AX_TRY(dalloc(&w->rscale, (size_t)m));
   AX_TRY(dalloc(&w->st, (size_t)m));
   AX_TRY(dalloc(&w->st_outer, (size_t)m));
   AX_TRY(cudaMallocHost((void **)&w->h_st, sizeof(RhsState) * 2 * m));
@@ -324,6 +327,35 @@ __global__ void padded_to_dense(const T *__restrict__ src, double *__restrict__ 
                                 int pitch) {
   for (long long row = blockIdx.x; row < rows; row += gridDim.x)
     for (int k = threadIdx.x; k < nz; k += blockDim.x) dst[row * nz + k] = (double)src[row * pitch + k];
+}
+
+// Mixed methods: sigma_m = 2^-round(log2(rms(phi_m))) (1 for phi_m = 0), from
+// the ||phi||^2 partials, so that the FP32 inner iteration works on values of
+// order one whatever the units of f (FP32 squares of residuals near 1e-20
+// would underflow).  A power of two scales FP64 values exactly.
+__global__ void rhs_scale(double *scale, const double *part, int nb, int m, double count) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double ss = 0.0;
+  for (int b = 0; b < nb; ++b) ss += part[(size_t)j * kPartialStride + b];
+  double sc = 1.0;
+  if (ss > 0.0 && isfinite(ss)) sc = ldexp(1.0, -(int)lrint(0.5 * log2(ss / count)));
+  scale[j] = sc;
+}
+
+// phi *= sigma and x *= sigma (x may be null) with the ||phi||^2 partials *=
+// sigma^2 (inverse = false), or x /= sigma (inverse = true).  grid (., m).
+__global__ void apply_rhs_scale(double *phi, double *x, const double *scale, double *part, int nb, size_t field,
+                                bool inverse) {
+  const int m = blockIdx.y;
+  const double sc = inverse ? 1.0 / scale[m] : scale[m];
+  const size_t b = (size_t)m * field;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < field; e += (size_t)gridDim.x * blockDim.x) {
+    if (phi) phi[b + e] *= sc;
+    if (x) x[b + e] *= sc;
+  }
+  if (part && blockIdx.x == 0)
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) part[(size_t)m * kPartialStride + k] *= sc * sc;
 }
 
 // phi = r_i f (Eq. diff_approx1), FP64, plus per-CTA partials of ||phi||^2.
@@ -2195,6 +2227,17 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   } else {
     AX_TRY(cudaMemsetAsync(w->x64, 0, field * m * sizeof(double), s));
   }
+  // the mixed methods solve A (sigma u) = sigma phi (see rhs_scale)
+  const bool scaled = (method == AX_PCG_MIXED || method == AX_CHEB_MIXED);
+  const unsigned sblocks =
+      (unsigned)std::max<size_t>(1, std::min<size_t>((field + 1023) / 1024, (8192 + (size_t)m - 1) / (size_t)m));
+  if (scaled) {
+    note_launch();
+    rhs_scale<<<(m + 31) / 32, 32, 0, s>>>(w->rscale, part_ptr(w, kPartD), nbf, m, (double)nr * nz);
+    note_launch();
+    apply_rhs_scale<<<dim3(sblocks, m), 256, 0, s>>>(w->phi64, guess ? w->x64 : nullptr, w->rscale,
+                                                     part_ptr(w, kPartD), nbf, field, false);
+  }
   AX_CHECK_LAUNCH();
   const int nbs64 = stencil_blocks_per_rhs(nr, nz, 2);
   const bool cheb = (method == AX_CHEB_FP64 || method == AX_CHEB_MIXED);
@@ -2314,6 +2357,10 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     }
     rc = finish_info(op, m, so, info, 1, accepted, s);
     }
+  }
+  if (scaled) {
+    note_launch();
+    apply_rhs_scale<<<dim3(sblocks, m), 256, 0, s>>>(nullptr, w->x64, w->rscale, nullptr, 0, field, true);
   }
   note_launch();
   padded_to_dense<double><<<cblocks, 256, 0, s>>>(w->x64, ud, rows, nz, P);

@@ -346,6 +346,31 @@ def test_full_size_layered_1024_m64_zero_flux_sampled(cuda):
     P.ax_destroy_operator(op)
 
 
+@pytest.mark.parametrize("method", [P.AX_PCG_MIXED, P.AX_CHEB_MIXED])
+@pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e25])
+def test_mixed_methods_are_scale_invariant(cuda, method, scale):
+    """f scaled by 1e-30 .. 1e25: the mixed methods (FP32 inner iteration)
+    return scale times the unscaled solution to the tolerance, with the same
+    iteration count (their right-hand side is scaled by a power of two near
+    1 / rms(phi) inside the solve)."""
+    nr, nz = 96, 80
+    med = layered_inclusion_medium(2, 96)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).cuda() for x in (kr, kz, q)], nr, nz)
+    f = torch.from_numpy(sample_rhs(med, nr, nz)).cuda()
+    u1, u2 = torch.zeros_like(f), torch.zeros_like(f)
+    st1, i1 = P.ax_solve(op, f, u1, 2, 1e-8, 5000, method)
+    st2, i2 = P.ax_solve(op, f * scale, u2, 2, 1e-8, 5000, method)
+    assert st1 == P.AX_OK and st2 == P.AX_OK
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
+    fh, uh = f.cpu().numpy() * scale, u2.cpu().numpy()
+    for j in range(2):
+        phi = ora.phi(fh[j])
+        assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1e-8 * np.linalg.norm(phi)
+        assert abs(i1[j]["iters"] - i2[j]["iters"]) <= 2, (i1[j], i2[j])
+    P.ax_destroy_operator(op)
+
+
 def test_mixed_replacement_keeps_fp64_iteration_count(cuda):
     """FP32 PCG with FP64 residual replacement keeps the search direction, so
     its iteration count stays close to the FP64 method's; the restarted
