@@ -181,6 +181,9 @@ int ax_set_option(ax_operator *op, const char *name, double value);
  * u : [m][nr][nz] out: solution; in: guess if AX_FLAG_USE_GUESS
  * Each right-hand side stops when its FP64 true residual satisfies
  * ||phi - A u||_2 <= tol ||phi||_2, or fails after max_iter iterations.
+ * The mixed methods solve A (sigma u) = sigma phi with sigma the power of two
+ * nearest 1 / rms(phi) per right-hand side (exact in FP64), so their FP32 inner
+ * iteration does not depend on the units of f.
  * info : host array [m] (may be NULL).  Returns the worst per-RHS status. */
 int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
              int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
