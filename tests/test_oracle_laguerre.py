@@ -87,3 +87,24 @@ def test_chain_solves_each_harmonic_with_its_own_right_hand_side():
     for m in range(4):
         phi = op.phi(L.harmonic_rhs(m, Q[:m], c2, src, fm[m], 5))
         assert np.linalg.norm(op.apply_A(Q[m]) - phi) <= 1e-11 * np.linalg.norm(phi)
+
+
+def test_library_host_weights_are_the_factorial_ratios():
+    from paper_1002_3094_gb300.laguerre import laguerre_weights
+    for m in range(0, 30):
+        a, w = laguerre_weights(m, 5)
+        exact = Fraction(math.factorial(m), math.factorial(m + 5))
+        assert a * a == pytest.approx(float(exact), rel=1e-13) and w * w == pytest.approx(float(1 / exact), rel=1e-13)
+
+
+def test_wavelet_coefficients_match_quadrature():
+    """Input generator of the chain workload: the trapezoid-rule coefficients
+    of the Eq. functiont wavelet against adaptive quadrature with SciPy's
+    Laguerre polynomials (Eq. series_lag)."""
+    from workloads.laguerre import ALPHA, H_LAG, source_wavelet, wavelet_coefficients
+    got = wavelet_coefficients(12)
+    for m in (0, 3, 11):
+        c = math.sqrt(H_LAG * math.factorial(m) / math.factorial(m + ALPHA))
+        g = lambda t: source_wavelet(t) * c * np.exp(-H_LAG * t / 2) * special.eval_genlaguerre(m, ALPHA, H_LAG * t)
+        want = integrate.quad(g, 0.0, 0.5, limit=800, points=[0.2], epsabs=1e-30, epsrel=1e-11)[0]
+        assert got[m] == pytest.approx(want, rel=1e-6, abs=1e-12 * np.abs(got).max())
