@@ -296,9 +296,50 @@ def cpu_baseline(name: str, cores: int, pool=None, bc_z: int = 0, iters_hint: in
             "wall_s": wall, "unknowns": unknowns}
 
 
+def _reference_laguerre(args):
+    """Reference arm of laguerre_chain: the oracle's chain (direct sums, FP64
+    PCG to the same tolerance, warm start from the previous harmonic) over the
+    first 12 harmonics of the workload on one host core (the chain is
+    sequential); value = harmonics nr nz / wall time."""
+    import numpy as np
+    import oracle as O
+    from oracle import laguerre as OL
+    from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs
+    from workloads.laguerre import ALPHA, H_LAG, fault_medium, wavelet_coefficients
+    nr = nz = 1024
+    lr = lz = 2048.0
+    k = 12
+    med = fault_medium(lr, lz)
+    kr, kz, q = sample_operator_inputs(med, nr, nz, lr, lz, bc_z=1)
+    src = sample_rhs(med, nr, nz, lr, lz, bc_z=1)[0]
+    fm = wavelet_coefficients(args.harmonics, ALPHA, H_LAG)
+    fm = fm / np.abs(fm).max()
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ora = O.Operator(kr, kz, q, O.Grid(nr, nz, lr, lz, bc_z=1))
+        OL.chain(lambda rhs, prev: ora.solve(rhs, TOL, y0=prev)[0], 4.0 * q, src, fm[:k], ALPHA)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = k * nr * nz * args.steps / total
+    sample = f"harmonics 0..{k - 1} of laguerre_chain ({nr}^2), FP64 oracle PCG to {TOL:g}, set-up included"
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "impl": "reference", "config": {"workload": "laguerre_chain", "harmonics_per_step": k,
+                                                      "nr": nr, "nz": nz, "tol": TOL, "bc_z": 1},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": f"each step: {sample}"},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "laguerre_chain":
+        _reference_laguerre(args)
         return
     cores = os.cpu_count() or 1
     pool = oracle_pool(cores)
@@ -556,10 +597,7 @@ def main():
         run_guess(args)
         return
     if args.workload == "laguerre_chain":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times layered_1024_m64 only"}))
-        else:
-            run_laguerre(args)
+        run_laguerre(args)
         return
     if args.workload == "batched_256":
         run_batched(args)
