@@ -139,6 +139,8 @@ def parse_args():
                     help="FP32 path transform along z: -1 the library's choice, 0 FFT, 1 tensor-core GEMM "
                          "by S_hi + S_lo, 2 tensor-core GEMM by S_hi (option dst_tensor)")
     ap.add_argument("--harmonics", type=int, default=2000, help="laguerre_chain: number of harmonics")
+    ap.add_argument("--mode-kernel", type=int, default=0,
+                    help="FP32 mode-solve kernel variant (option mode_kernel; 0 the library's choice)")
     ap.add_argument("--replace-delta", type=float, default=0.0,
                     help="mixed PCG: residual reduction between FP64 residual replacements (0: the library's)")
     return ap.parse_args()
@@ -632,6 +634,8 @@ def main():
         P.ax_set_option(op, "dst_tensor", args.dst_tensor)
     if args.replace_delta > 0:
         P.ax_set_option(op, "replace_delta", args.replace_delta)
+    if args.mode_kernel > 0:
+        P.ax_set_option(op, "mode_kernel", args.mode_kernel)
     f_host = sample_rhs(med, nr, nz, bc_z=args.bc_z)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)

@@ -196,8 +196,11 @@ def ax_operator_info(op: int):
     return tuple(v.value for v in vals)
 
 
-def ax_set_option(op: int, name: str, value: float) -> None:
-    _check(load_library().ax_set_option(op, name.encode(), float(value)), f"ax_set_option({name})")
+def ax_set_option(op: int, name: str, value: float, raise_on_error: bool = True) -> int:
+    st = load_library().ax_set_option(op, name.encode(), float(value))
+    if raise_on_error:
+        _check(st, f"ax_set_option({name})")
+    return st
 
 
 def ax_solve(op: int, f, u, m: int, tol: float, max_iter: int = 10000, method: int = AX_PCG_FP64,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include "ax_internal.cuh"
 
 namespace ax {
@@ -83,51 +84,46 @@ __device__ __forceinline__ size_t split_byte(int m, int row, int pos, int mtiles
          ((row & 127) >> 3) * 1024 + ((pos & 63) >> 3) * 128 + (row & 7) * 16 + (pos & 7) * 2;
 }
 __device__ __forceinline__ unsigned bf16_pack2(float a, float b) {
-  // round-to-nearest-even BF16 of a (low half, lower address) and b
-  unsigned ua = __float_as_uint(a), ub = __float_as_uint(b);
-  ua += 0x7FFFu + ((ua >> 16) & 1u);
-  ub += 0x7FFFu + ((ub >> 16) & 1u);
-  return (ua >> 16) | (ub & 0xFFFF0000u);
+  // round-to-nearest-even BF16 of a (low half, lower address) and b, by the
+  // packed conversion instruction
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const unsigned *>(&h);
 }
-__device__ __forceinline__ float bf16_round(float a) {
-  unsigned u = __float_as_uint(a);
-  u += 0x7FFFu + ((u >> 16) & 1u);
-  return __uint_as_float(u & 0xFFFF0000u);
-}
+__device__ __forceinline__ float bf16_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+// The two BF16 halves of a packed pair as FP32 (exact).
+__device__ __forceinline__ float bf16_lo(unsigned p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned p) { return __uint_as_float(p & 0xFFFF0000u); }
 // Writes the 8 consecutive columns col .. col + 7 (col % 8 == 0) of one row:
 // the 4 even ones and the 4 odd ones each as 8 bytes of high and of low parts.
 __device__ __forceinline__ void split_store8(unsigned char *split, int m, int row, int col, int mtiles, int ktiles,
                                              int kbe, const float (&x)[8]) {
-  float hi[8], lo[8];
+  unsigned he[2], le[2], ho[2], lo[2];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    hi[e] = bf16_round(x[e]);
-    lo[e] = x[e] - hi[e];
+  for (int e = 0; e < 2; ++e) {
+    he[e] = bf16_pack2(x[4 * e], x[4 * e + 2]);
+    ho[e] = bf16_pack2(x[4 * e + 1], x[4 * e + 3]);
+    le[e] = bf16_pack2(x[4 * e] - bf16_lo(he[e]), x[4 * e + 2] - bf16_hi(he[e]));
+    lo[e] = bf16_pack2(x[4 * e + 1] - bf16_lo(ho[e]), x[4 * e + 3] - bf16_hi(ho[e]));
   }
   unsigned char *te = split + split_byte(m, row, split_pos(col, kbe), mtiles, ktiles);
   unsigned char *to = split + split_byte(m, row, split_pos(col + 1, kbe), mtiles, ktiles);
-  *reinterpret_cast<uint2 *>(te) = make_uint2(bf16_pack2(hi[0], hi[2]), bf16_pack2(hi[4], hi[6]));
-  *reinterpret_cast<uint2 *>(te + kSplitTileBytes / 2) = make_uint2(bf16_pack2(lo[0], lo[2]), bf16_pack2(lo[4], lo[6]));
-  *reinterpret_cast<uint2 *>(to) = make_uint2(bf16_pack2(hi[1], hi[3]), bf16_pack2(hi[5], hi[7]));
-  *reinterpret_cast<uint2 *>(to + kSplitTileBytes / 2) = make_uint2(bf16_pack2(lo[1], lo[3]), bf16_pack2(lo[5], lo[7]));
+  *reinterpret_cast<uint2 *>(te) = make_uint2(he[0], he[1]);
+  *reinterpret_cast<uint2 *>(te + kSplitTileBytes / 2) = make_uint2(le[0], le[1]);
+  *reinterpret_cast<uint2 *>(to) = make_uint2(ho[0], ho[1]);
+  *reinterpret_cast<uint2 *>(to + kSplitTileBytes / 2) = make_uint2(lo[0], lo[1]);
 }
 
 // Writes the 4 consecutive columns col .. col + 3 (col % 4 == 0) of one row:
 // the 2 even ones and the 2 odd ones each as 4 bytes of high and of low parts.
 __device__ __forceinline__ void split_store4(unsigned char *split, int m, int row, int col, int mtiles, int ktiles,
                                              int kbe, const float (&x)[4]) {
-  float hi[4], lo[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    hi[e] = bf16_round(x[e]);
-    lo[e] = x[e] - hi[e];
-  }
+  const unsigned he = bf16_pack2(x[0], x[2]), ho = bf16_pack2(x[1], x[3]);
   unsigned char *te = split + split_byte(m, row, split_pos(col, kbe), mtiles, ktiles);
   unsigned char *to = split + split_byte(m, row, split_pos(col + 1, kbe), mtiles, ktiles);
-  *reinterpret_cast<unsigned *>(te) = bf16_pack2(hi[0], hi[2]);
-  *reinterpret_cast<unsigned *>(te + kSplitTileBytes / 2) = bf16_pack2(lo[0], lo[2]);
-  *reinterpret_cast<unsigned *>(to) = bf16_pack2(hi[1], hi[3]);
-  *reinterpret_cast<unsigned *>(to + kSplitTileBytes / 2) = bf16_pack2(lo[1], lo[3]);
+  *reinterpret_cast<unsigned *>(te) = he;
+  *reinterpret_cast<unsigned *>(te + kSplitTileBytes / 2) = bf16_pack2(x[0] - bf16_lo(he), x[2] - bf16_hi(he));
+  *reinterpret_cast<unsigned *>(to) = ho;
+  *reinterpret_cast<unsigned *>(to + kSplitTileBytes / 2) = bf16_pack2(x[1] - bf16_lo(ho), x[3] - bf16_hi(ho));
 }
 
 // Folded input of the tensor-core cosine forward transform for the 8

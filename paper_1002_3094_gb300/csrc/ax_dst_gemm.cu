@@ -308,6 +308,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
       }
       tc_fence_after();
       const int grow = mt * kBM + q * 32 + lane;
+      // row scale of this lane's row (1 without rowscale)
+      const float rsc = (a.rowscale != nullptr && grow < a.nr) ? __ldg(a.rowscale + m * a.rsstride + grow) : 1.f;
       float acc = 0.f;
       if (__all_sync(0xffffffffu, ok)) {
         const size_t roff = (size_t)m * (size_t)a.field + (size_t)grow * a.pitch;
@@ -363,10 +365,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
                 }
                 if (a.cosfwd) {  // even output columns from P, odd ones from Q
 #pragma unroll
-                  for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = pass ? Q[i] : P[i];
+                  for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = rsc * (pass ? Q[i] : P[i]);
                 } else {
 #pragma unroll
-                  for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = pass ? P[i] - Q[i] : P[i] + Q[i];
+                  for (int i = 0; i < 32; ++i) T[lane * 32 + (i ^ lane)] = rsc * (pass ? P[i] - Q[i] : P[i] + Q[i]);
                 }
               }
               __syncwarp();
@@ -421,8 +423,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
               float s0[4], d0[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                s0[e] = P[i + e] + Q[i + e];  // out[l + e]
-                d0[e] = P[i + e] - Q[i + e];  // out[n - 1 - l - e]
+                s0[e] = rsc * (P[i + e] + Q[i + e]);  // out[l + e]
+                d0[e] = rsc * (P[i + e] - Q[i + e]);  // out[n - 1 - l - e]
               }
               if (l + 3 < ne && (n & 3) == 0) {
                 // n % 4 == 0: both runs are whole aligned float4 groups, and the

@@ -84,6 +84,10 @@ struct Coef {
                      //               cos/sin of phi_l, 2 phi_l; phi_l = pi l / (2 nz))
   T *RK = nullptr;   // [2 P]         Rader: DFT of the permuted kernel W^(g^-m)
   T *RT = nullptr;   // [2 P]         Rader: (cos, sin)(2 pi j / P)
+  // FP32 only: the mode systems scaled to unit couplings, T'_l = D T_l D with
+  // D = diag(RS), RS_i RS_{i+1} |E_i| = 1: IPS [nr][pitch] the inverse pivots
+  // 1 / delta'_i(l) of T'_l (column l), RS [nr]
+  T *IPS = nullptr, *RS = nullptr;
   // FP32 only: low parts of the FP64 stencil coefficients, CR64 = CR + CRl (CR the
   // FP32 rounding), for the double-float residual of the mixed method
   T *CRl = nullptr, *CZl = nullptr, *Wl = nullptr;
@@ -153,6 +157,7 @@ struct ax_operator {
   ax::FftPlan plan;
   int *rader_perm = nullptr;  // [2 P] device
   int dst_tc = 0;             // 1: the FP32 PCG path transforms with the tensor-core GEMM
+  int tri_variant = 0;        // FP32 mode-solve kernel (0: default for nr; option "mode_kernel")
   int *tc_err = nullptr;      // device flag: a bounded wait of the GEMM expired
   ax::Coef<double> c64;
   ax::Coef<float> c32;
@@ -293,6 +298,11 @@ struct GemmDstArgs {
   // -1 in normal use.
   unsigned polls;
   int stall_at;
+  // non-null: every output row (grid row i < nr of right-hand side m) is
+  // multiplied by rowscale[m rsstride + i] before it is stored or combined
+  // (the row scaling D of the pipelined mode solves)
+  const float *rowscale;
+  long long rsstride;
 };
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);
@@ -311,6 +321,9 @@ std::vector<uint16_t> dst_gemm_table(int n, int kind);
 template <typename T>
 struct TriArgs {
   const T *IP, *E;
+  // FP32 pipelined kernels: the factors of the row-scaled systems (Coef::IPS,
+  // Coef::RS), with the strides of IP and E; null: those kernels are not used
+  const T *IPS, *RS;
   long long cstride, estride;   // factor elements per RHS (0: one operator for all RHS)
   int nr, nz, pitch;
   long long field;
@@ -323,17 +336,34 @@ struct TriArgs {
   // halves (layout of ax_common.cuh, tiles mtiles x ktiles) instead of to out
   unsigned char *split;
   int split_mtiles, split_ktiles, split_kbe;
-  // FP32 tile kernel only: if set, per-CTA partials of (in, out) into
-  // partial[m][blockIdx.x] (column groups of 8)
+  // FP32 tile kernels only: if set, per-CTA partials of (in, out) into
+  // partial[m][g], one slot g per group of tridiag_reg_cols(nr, variant) columns
+  // (variant = tridiag_effective(...))
   double *partial;
+  // FP32 kernel choice (0: the tuned or default choice for nr; see
+  // tridiag_variants); set from the operator's "mode_kernel" option
+  int variant;
+  // 1: in and out hold the row-scaled systems of IPS / RS (b' = D b, y' =
+  // T'^-1 b'; the pipelined kernels); 0: the plain systems of IP / E.  Set
+  // exactly when tridiag_effective(...) >= 2.
+  int prescaled;
 };
 
 template <typename T>
 void launch_tridiag(const TriArgs<T> &a, cudaStream_t s);
 // whether launch_tridiag<float> can write the split layout for these sizes
 bool tridiag_split_ok(int nr);
-// mode columns per CTA of the FP32 register kernel for nr rows (0: not used);
-// its (in, out) partials come in ceil(nz / cols) slots per right-hand side
-int tridiag_reg_cols(int nr);
+// Mode columns per partial slot of the FP32 kernel `variant` for nr rows (0:
+// no FP32 tile kernel covers nr); its (in, out) partials come in
+// ceil(nz / cols) slots per right-hand side
+int tridiag_reg_cols(int nr, int variant = 0);
+// FP32 mode-solve kernels that cover nr rows: fills ids (at most 8) and
+// returns their number; ids[0] is the default.  1: the staged register
+// kernel; 2..: the pipelined column-tile kernels (see ax_tridiag.cu).
+int tridiag_variants(int nr, int *ids);
+// The FP32 kernel variant that runs for nr rows, option `variant`, m
+// right-hand sides, and whether the scaled tables exist (0: none covers nr).
+// The pipelined variants (>= 2) run on row-scaled data only.
+int tridiag_effective(int nr, int variant, int m, bool scaled_tables);
 
 }  // namespace ax

@@ -980,6 +980,7 @@ void free_coef(Coef<T> &c) {
   dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW); dfree(c.CW);
   dfree(c.RK); dfree(c.RT);
   dfree(c.CRl); dfree(c.CZl); dfree(c.Wl);
+  dfree(c.IPS); dfree(c.RS);
 }
 
 // ---------------------------------------------------------------------------
@@ -1042,6 +1043,8 @@ TriArgs<T> tri_args(const ax_operator *op, int m, const T *in, T *out, const Rhs
   const Coef<T> &c = coef<T>(op);
   a.IP = c.IP;
   a.E = c.E;
+  a.IPS = c.IPS;
+  a.RS = c.RS;
   a.cstride = op->cstride;
   a.estride = op->estride;
   a.nr = op->nr;
@@ -1053,6 +1056,7 @@ TriArgs<T> tri_args(const ax_operator *op, int m, const T *in, T *out, const Rhs
   a.out = out;
   a.st = st;
   a.mask = mask;
+  a.variant = op->tri_variant;
   return a;
 }
 
@@ -1130,10 +1134,25 @@ SplitGeom split_geom(const ax_operator *op, int rows) {
 // inverse); with r, the (r, out) partials into `partial`.  With pa, pb the result is not stored but forms the next
 // search direction p_new = out + beta p_old (and, with x, x += alpha p_old);
 // see GemmDstArgs.
+// FP32 mode-solve variant of the tensor-core path for m right-hand sides, and
+// whether it is a pipelined one, which works on the row-scaled systems: the
+// transforms around it then take the scaling D in their epilogues.
+int tc_mode_variant(const ax_operator *op, int m) {
+  return tridiag_effective(op->nr, op->tri_variant, m, op->c32.IPS != nullptr && op->c32.RS != nullptr);
+}
+bool tc_scaled(const ax_operator *op, int m) { return tc_mode_variant(op, m) >= 2; }
+
+// scaled: multiply every output row by D (the row scale of the pipelined mode
+// solves); set for the two transforms of a preconditioner application
+// exactly when tc_scaled(op, m).
 void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, bool inverse, float *out,
                   const RhsState *st, int mask, const float *r, double *partial, cudaStream_t s, int three = -1,
-                  float *pa = nullptr, float *pb = nullptr, float *x = nullptr) {
+                  float *pa = nullptr, float *pb = nullptr, float *x = nullptr, bool scaled = false) {
   GemmDstArgs g{};
+  if (scaled) {
+    g.rowscale = op->c32.RS;
+    g.rsstride = op->estride;
+  }
   g.pa = pa;
   g.pb = pb;
   g.x = x;
@@ -1186,6 +1205,8 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
                    const RhsState *st, int mask, cudaStream_t s, double *prz = nullptr) {
   const SplitGeom g = split_geom(op, op->nr);
   TriArgs<float> t = tri_args<float>(op, m, z, tmp, st, mask);
+  t.variant = tc_mode_variant(op, m);
+  t.prescaled = tc_scaled(op, m);
   if (tridiag_split_ok(op->nr)) {
     t.split = split;
     t.split_mtiles = g.mtiles;
@@ -1200,16 +1221,19 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
 }
 
 // Where the (r, z) partials of the tensor-core path come from: the mode solves
-// (one per column group of the register kernel) when it runs, else the inverse
-// transform.
+// (one per column group of the FP32 tile kernel) when it runs, else the
+// inverse transform.
 bool tc_dot_in_modes(const ax_operator *op) { return tridiag_split_ok(op->nr); }
 
-// Number of (r, z) partial slots per RHS that precond_apply writes.
+// Number of (r, z) partial slots per RHS that precond_apply writes for m
+// right-hand sides.
 template <typename T>
-int precond_partials(const ax_operator *op) {
-  if (use_tc<T>(op))
-    return tc_dot_in_modes(op) ? (op->nz + tridiag_reg_cols(op->nr) - 1) / tridiag_reg_cols(op->nr)
-                               : dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
+int precond_partials(const ax_operator *op, int m) {
+  if (use_tc<T>(op)) {
+    if (!tc_dot_in_modes(op)) return dst_gemm_mtiles(op->nr) * dst_gemm_ntiles(op->nz);
+    const int cols = tridiag_reg_cols(op->nr, tc_mode_variant(op, m));
+    return (op->nz + cols - 1) / cols;
+  }
   return dst_blocks(op, op->nr, (int)sizeof(T));
 }
 
@@ -1224,9 +1248,11 @@ void precond_apply(const ax_operator *op, int m, const T *r, T *z, const RhsStat
       unsigned char *sp = op->ws->split;
       const bool dm = tc_dot_in_modes(op);
       tc_split(op, m, op->nr, r, sp, st, mask, s);
-      tc_transform(op, m, op->nr, sp, false, z, st, mask, nullptr, nullptr, s);
+      const bool sc = tc_scaled(op, m);
+      tc_transform(op, m, op->nr, sp, false, z, st, mask, nullptr, nullptr, s, -1, nullptr, nullptr, nullptr, sc);
       tc_mode_solve(op, m, z, tmp, sp, st, mask, s, dm ? prz : nullptr);
-      tc_transform(op, m, op->nr, sp, true, z, st, mask, dm ? nullptr : r, dm ? nullptr : prz, s);
+      tc_transform(op, m, op->nr, sp, true, z, st, mask, dm ? nullptr : r, dm ? nullptr : prz, s, -1, nullptr, nullptr,
+                   nullptr, sc);
       return;
     }
   }
@@ -1297,7 +1323,11 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
                                                           g.kbe, sp, st, kActive, prr, op->bc_z == 1);
         if (op->bc_z == 1) tc_split(op, m, op->nr, v.r, sp, st, kActive, s);
       }
-      { ProfScope ps(w, kProfDstFwd, units, s); tc_transform(op, m, op->nr, sp, false, v.z, st, kActive, nullptr, nullptr, s); }
+      const bool sc = tc_scaled(op, m);
+      {
+        ProfScope ps(w, kProfDstFwd, units, s);
+        tc_transform(op, m, op->nr, sp, false, v.z, st, kActive, nullptr, nullptr, s, -1, nullptr, nullptr, nullptr, sc);
+      }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
         note_launch();
@@ -1312,20 +1342,21 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
         {
           ProfScope ps(w, kProfScalar, 0.0, s);
           note_launch();
-          sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op), kActive, kActive);
+          sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op, m), kActive, kActive);
         }
         ProfScope ps(w, kProfDstInv, units, s);
-        tc_transform(op, m, op->nr, sp, true, v.z, st, kActive, nullptr, nullptr, s, -1, v.pa, v.pb, v.x);
+        tc_transform(op, m, op->nr, sp, true, v.z, st, kActive, nullptr, nullptr, s, -1, v.pa, v.pb, v.x, sc);
         return;
       }
       {
         ProfScope ps(w, kProfDstInv, units, s);
-        tc_transform(op, m, op->nr, sp, true, v.z, st, kActive, dm ? nullptr : v.r, dm ? nullptr : prz, s);
+        tc_transform(op, m, op->nr, sp, true, v.z, st, kActive, dm ? nullptr : v.r, dm ? nullptr : prz, s, -1, nullptr,
+                     nullptr, nullptr, sc);
       }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
         note_launch();
-        sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op), kActive, kActive);
+        sc_beta<<<m, 32, 0, s>>>(st, prz, precond_partials<T>(op, m), kActive, kActive);
       }
       return;
     }
@@ -1452,7 +1483,7 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
   Workspace *w = op->ws;
   const int V = VecT<T>::n;
   const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
-  const int nbd = precond_partials<T>(op);
+  const int nbd = precond_partials<T>(op, m);
   // z = B^-1 r, rho = (r, z), p = 0 so that p_1 = z
   precond_apply<T>(op, m, v.r, v.z, st, kActive, part_ptr(w, kPartC), s, v.q);
   note_launch();
@@ -1560,7 +1591,7 @@ template <typename T, typename F>
 int gate_guess(ax_operator *op, int m, RhsState *st, const T *phiT, const T *r0T, T *zbuf, T *tmp,
                std::vector<int> &accepted, cudaStream_t s, F restart) {
   Workspace *w = op->ws;
-  const int nbd = precond_partials<T>(op);
+  const int nbd = precond_partials<T>(op, m);
   precond_apply<T>(op, m, phiT, zbuf, st, -1, part_ptr(w, kPartC), s, tmp);
   note_launch();
   sc_store_gate<<<m, 32, 0, s>>>(st, part_ptr(w, kPartC), nbd, 0);
@@ -1600,7 +1631,7 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   const size_t field = field_elems(op);
   const int nbdf = residual_df_blocks(op->nr, op->nz);
   const int nbf = (op->nr + 15) / 16;
-  const int nbd = precond_partials<float>(op);
+  const int nbd = precond_partials<float>(op, m);
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
   const size_t nall = field * m;
   const unsigned cblocks = (unsigned)std::min<size_t>((nall + 255) / 256, 65535);
@@ -1658,11 +1689,12 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
       // step again, p_new = z + beta p_old (x already holds alpha p_old)
       unsigned char *sp = w->split;
       tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss);
-      tc_transform(op, m, op->nr, sp, false, v.z, st, kCheck, nullptr, nullptr, ss);
+      const bool sc = tc_scaled(op, m);
+      tc_transform(op, m, op->nr, sp, false, v.z, st, kCheck, nullptr, nullptr, ss, -1, nullptr, nullptr, nullptr, sc);
       tc_mode_solve(op, m, v.z, v.q, sp, st, kCheck, ss, part_ptr(w, kPartC));
       note_launch();
       sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kCheck, 1);
-      tc_transform(op, m, op->nr, sp, true, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr);
+      tc_transform(op, m, op->nr, sp, true, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr, sc);
       note_launch();
       sc_promote<<<(m + 31) / 32, 32, 0, ss>>>(st, m, kCheck, kActive);
       return;
@@ -1823,6 +1855,21 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     if (value != 0.0 && op->nz > kMaxTcN) return AX_ERR_UNSUPPORTED;
     op->dst_tc = (int)value;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+  } else if (!strcmp(name, "mode_kernel")) {
+    // FP32 mode-solve kernel: 0 the default for nr, else a variant id of
+    // tridiag_variants (1 the staged register kernel, 2.. the pipelined
+    // column-tile kernels); ids that do not cover nr are refused
+    const int v = (int)value;
+    if ((double)v != value || v < 0) return AX_ERR_INVALID_ARG;
+    if (v != 0) {
+      int ids[16];
+      const int n = tridiag_variants(op->nr, ids);
+      bool ok = false;
+      for (int i = 0; i < n; ++i) ok = ok || ids[i] == v;
+      if (!ok) return AX_ERR_INVALID_ARG;
+    }
+    op->tri_variant = v;
+    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "max_outer")) {
     if (!(value >= 1)) return AX_ERR_INVALID_ARG;
     w->max_outer = (int)value;
@@ -1944,6 +1991,26 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
       IP[(size_t)a * P + (l - 1)] = 1.0 / delta;
     }
   }
+  // The same systems scaled to unit couplings for the FP32 pipelined mode
+  // solves: T' = D T D, D = diag(rs), rs_a rs_{a+1} |E_a| = 1 (rs_0 =
+  // |E_0|^-1/2, so the scale stays near |E_a|^-1/2); pivots of the scaled
+  // diagonal rs_a^2 d_a(l) with off-diagonal -1.
+  std::vector<double> RS(nr, 1.0), IPS((size_t)nr * P, 0.0);
+  if (nr > 1) {
+    RS[0] = 1.0 / std::sqrt(std::fabs(E[0]));
+    for (int a = 0; a + 1 < nr; ++a) RS[a + 1] = 1.0 / (std::fabs(E[a]) * RS[a]);
+  }
+  for (int l = 1; l <= nz; ++l) {
+    const double sn = cosine ? std::sin(M_PI * (l - 1) / (2.0 * nz)) : std::sin(M_PI * l / (2.0 * (nz + 1)));
+    const double lam = 4.0 / hz2 * sn * sn;
+    double delta = 0.0;
+    for (int a = 0; a < nr; ++a) {
+      const double rbar_hi = (a + 1) * hr, rbar_lo = a * hr;
+      const double d = (kt * (rbar_hi + rbar_lo) / hr2 + ri[a] * (kt * lam + qt)) * RS[a] * RS[a];
+      delta = (a == 0) ? d : d - 1.0 / delta;
+      IPS[(size_t)a * P + (l - 1)] = 1.0 / delta;
+    }
+  }
   std::vector<double> TW(2 * (size_t)L), HW(2 * (size_t)L);
   for (int j = 0; j < L; ++j) {
     TW[2 * j] = std::cos(2.0 * M_PI * j / L);
@@ -1982,6 +2049,7 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   AX_UP(double, c64.E, E) AX_UP(double, c64.R, ri) AX_UP(double, c64.TW, TW) AX_UP(double, c64.HW, HW)
   AX_UP(float, c32.CR, CR) AX_UP(float, c32.CZ, CZ) AX_UP(float, c32.W, W) AX_UP(float, c32.IP, IP)
   AX_UP(float, c32.E, E) AX_UP(float, c32.R, ri) AX_UP(float, c32.TW, TW) AX_UP(float, c32.HW, HW)
+  AX_UP(float, c32.IPS, IPS) AX_UP(float, c32.RS, RS)
 #undef AX_UP
   {
     // low parts for the double-float residual: v64 = (float)v64 + lo
@@ -2027,6 +2095,23 @@ __global__ void scale_rows_by_r(const double *__restrict__ f, double *__restrict
   }
 }
 
+// x[m][i][k] *= rs[m rsstride + i] for the rows i < rows of each right-hand
+// side (the row scaling D of the pipelined mode solves), in place.
+__global__ void scale_rows(float *__restrict__ x, const float *__restrict__ rs, long long rsstride, int rows,
+                           int pitch, size_t field) {
+  const int m = blockIdx.y;
+  const int per_row = pitch / 4;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)rows * per_row;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / per_row), c4 = (int)(t % per_row);
+    const float sv = rs[m * rsstride + row];
+    float4 *p = reinterpret_cast<float4 *>(x + m * field + (size_t)row * pitch) + c4;
+    float4 v = *p;
+    v.x *= sv; v.y *= sv; v.z *= sv; v.w *= sv;
+    *p = v;
+  }
+}
+
 // ---- single-step entry points --------------------------------------------
 template <typename T>
 static int apply_step(ax_operator *op, const double *in, double *out, int m, int rows_per, int which,
@@ -2069,14 +2154,35 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
     d.inverse = 1;
     launch_dst<T>(kDstPlain, d, s);
   } else if (which == 2) {
-    launch_tridiag<T>(tri_args<T>(op, m, a, b, nullptr, -1), s);
+    TriArgs<T> t = tri_args<T>(op, m, a, b, nullptr, -1);
+    if constexpr (sizeof(T) == 4) {
+      // the pipelined kernels solve the row-scaled systems: b' = D b, y = D y'
+      t.variant = tc_mode_variant(op, m);
+      t.prescaled = t.variant >= 2;
+      if (t.prescaled) {
+        note_launch();
+        scale_rows<<<dim3(update_blocks(rows_per, op->nz), m), 256, 0, s>>>(a, op->c32.RS, op->estride, rows_per,
+                                                                           op->pitch, field);
+      }
+      launch_tridiag<T>(t, s);
+      if (t.prescaled) {
+        note_launch();
+        scale_rows<<<dim3(update_blocks(rows_per, op->nz), m), 256, 0, s>>>(b, op->c32.RS, op->estride, rows_per,
+                                                                           op->pitch, field);
+      }
+    } else {
+      launch_tridiag<T>(t, s);
+    }
   } else if (tc) {
     if constexpr (sizeof(T) == 4) {
       unsigned char *sp = w->split;
       tc_split(op, m, rows_per, a, sp, nullptr, -1, s);
-      tc_transform(op, m, rows_per, sp, false, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+      const bool sc = tc_scaled(op, m);
+      tc_transform(op, m, rows_per, sp, false, b, nullptr, -1, nullptr, nullptr, s, tc_three, nullptr, nullptr, nullptr,
+                   sc);
       tc_mode_solve(op, m, b, a, sp, nullptr, -1, s);
-      tc_transform(op, m, rows_per, sp, true, b, nullptr, -1, nullptr, nullptr, s, tc_three);
+      tc_transform(op, m, rows_per, sp, true, b, nullptr, -1, nullptr, nullptr, s, tc_three, nullptr, nullptr, nullptr,
+                   sc);
     }
   } else {
     DstArgs<T> d = dst_args<T>(op, m, rows_per, nullptr, -1);
@@ -2443,6 +2549,15 @@ cudaError_t build_group_coef(Coef<T> &g, const std::vector<const ax_operator *> 
   if (err == cudaSuccess) err = stack_table(&g.W, f, w, s);
   if (err == cudaSuccess) err = stack_table(&g.IP, f, ip, s);
   if (err == cudaSuccess) err = stack_table(&g.E, (size_t)o->nr, e, s);
+  if (pick(o).IPS != nullptr) {
+    std::vector<const T *> ips, rs;
+    for (auto *op : ops) {
+      ips.push_back(pick(op).IPS);
+      rs.push_back(pick(op).RS);
+    }
+    if (err == cudaSuccess) err = stack_table(&g.IPS, f, ips, s);
+    if (err == cudaSuccess) err = stack_table(&g.RS, (size_t)o->nr, rs, s);
+  }
   if (pick(o).CRl != nullptr) {
     std::vector<const T *> crl, czl, wl;
     for (auto *op : ops) {
@@ -2550,6 +2665,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     gop->device = o->device;
     gop->plan = o->plan;
     gop->dst_tc = o->dst_tc;
+    gop->tri_variant = o->tri_variant;
     gop->cstride = (long long)o->nr * o->pitch;
     gop->czstride = (long long)o->nr * o->pitchz;
     gop->estride = o->nr;

@@ -24,6 +24,7 @@
 // sub-system boundaries follow from precomputable linear combinations), laid
 // out for one CTA instead of a multicomputer.  The data are read and written
 // once; IP is re-read from L1/L2.
+#include <algorithm>
 #include "ax_common.cuh"
 
 namespace ax {
@@ -55,6 +56,7 @@ __device__ __forceinline__ int launder_i(int x) {
   asm volatile("" : "+r"(x));
   return x;
 }
+
 
 template <typename T>
 __device__ __forceinline__ void scan_affine(T *sa, T *sm, int P, int W, int c, int w, T &a, T &mu,
@@ -384,6 +386,347 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined column-tile kernel (FP32, nr <= 16 NT / CW).
+//
+// Scaled systems.  With the row scaling D = diag(s_i), s_i s_{i+1} |E_i| = 1
+// (E_i the coupling of rows i and i + 1, the same for every mode), each mode
+// matrix becomes T'_l = D T_l D with off-diagonal -1, and
+//     T_l y = b   <=>   T'_l y' = b',  b' = D b,  y = D y'.
+// Its LU factors are the pivots delta'_i = d'_i - 1 / delta'_{i-1} of the
+// scaled diagonal d'_i = s_i^2 d_i(l); with ips = 1 / delta' (computed in FP64
+// at set-up) Thomas is
+//     g_i = ips_i (b'_i + g_{i-1})       (forward)
+//     y'_i = g_i + ips_i y'_{i+1}        (backward),
+// one or two operations per step and no per-row coupling.  T'_l is symmetric
+// positive definite like T_l, so the elimination needs no pivoting.  The
+// kernel solves T'_l y' = b' for data already scaled by D: D acts along r and
+// the sine / cosine transform along z, so D commutes with them and the
+// preconditioner B^-1 = S^T T^-1 S = D S^T T'^-1 S D takes the scaling in the
+// epilogues of the two transforms (GemmDstArgs::rowscale); the (rhat, yhat)
+// partials are unchanged, (b', y') = (b, y).
+//
+// Work.  Persistent CTAs walk groups of items; an item is (right-hand side,
+// tile of CW mode columns), a group R right-hand sides of one tile (the factors
+// ips are the same for all of them and are read once per group).  Lanes run
+// along l: thread (c, w) owns column w of the tile and the chunk of C = 16 rows
+// c C .. c C + 15, so every shared-memory row access of a warp is one
+// conflict-free wavefront and ips comes by coalesced row segments from global
+// memory (L2) into registers.  Groups go round-robin over the CTAs, tiles
+// fastest, so CTAs that run at the same time read neighbouring tiles of the
+// same rows (whole 128-byte lines).  The data tile of the next item is copied
+// to shared memory with 16-byte cp.async while the current one is solved
+// (two stages).
+//
+// Chunks.  Each chunk runs its forward (then backward) recurrence with zero
+// carry-in, yielding the affine map carry_out = A + M carry_in (M the product
+// of the chunk's ips); the maps of a column are composed by CW scan warps (one
+// column each, 32 chunks per shuffle round), and the true carry-ins are
+// applied in a second pass over the registers.  Rows past nr carry ips = 0
+// and data 0: they solve to zero and cut the carry chain (M = 0), so the
+// recurrences run unpredicated.
+//
+// Shared-memory tile: row `row`, column `col` at word (row + row / 16) CW +
+// col (one spare row per chunk), so the 32 / CW chunks held by one warp
+// (chunk c = 32 j / CW + i) hit distinct banks: the bank is
+// (CW (c + t) + col) mod 32.
+// Map buffers: column w, chunk c at word w (P + 1) + c.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// Writes columns col .. col + 15 (col % 16 == 0) of one row in the split
+// layout: the 8 even ones are one 16-byte row of a core matrix (high parts,
+// then low parts), the 8 odd ones another.
+__device__ __forceinline__ void split_store16(unsigned char *split, int m, int row, int col, int mtiles, int ktiles,
+                                              int kbe, const float (&x)[16]) {
+  unsigned he[4], le[4], ho[4], lo[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    he[e] = bf16_pack2(x[4 * e], x[4 * e + 2]);
+    ho[e] = bf16_pack2(x[4 * e + 1], x[4 * e + 3]);
+    le[e] = bf16_pack2(x[4 * e] - bf16_lo(he[e]), x[4 * e + 2] - bf16_hi(he[e]));
+    lo[e] = bf16_pack2(x[4 * e + 1] - bf16_lo(ho[e]), x[4 * e + 3] - bf16_hi(ho[e]));
+  }
+  unsigned char *te = split + split_byte(m, row, split_pos(col, kbe), mtiles, ktiles);
+  unsigned char *to = split + split_byte(m, row, split_pos(col + 1, kbe), mtiles, ktiles);
+  *reinterpret_cast<uint4 *>(te) = make_uint4(he[0], he[1], he[2], he[3]);
+  *reinterpret_cast<uint4 *>(te + kSplitTileBytes / 2) = make_uint4(le[0], le[1], le[2], le[3]);
+  *reinterpret_cast<uint4 *>(to) = make_uint4(ho[0], ho[1], ho[2], ho[3]);
+  *reinterpret_cast<uint4 *>(to + kSplitTileBytes / 2) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+template <int CW, int NT>
+struct PipeShape {
+  static constexpr int C = 16;                     // rows per chunk
+  static constexpr int P = NT / CW;                // chunks per column
+  static constexpr int kRows = P * C;              // rows covered
+  static constexpr int kStageWords = P * (C + 1) * CW;
+  static constexpr int kMapWords = CW * (P + 1);
+  static constexpr int kMaxList = 8192;            // right-hand sides in the item list
+  static constexpr size_t smem = sizeof(float) * (2 * kStageWords + 2 * kMapWords) + sizeof(int) * kMaxList;
+  static_assert(P >= 32 && P % 32 == 0 && CW <= 32 && 32 % CW == 0, "pipe shape");
+};
+
+// Exclusive scan of the affine maps of one column (warp-wide, called by one
+// warp per column): on entry ma/mm[k] hold chunk k's map (A, M); on return
+// ma[k] holds the carry into chunk k, in chunk order 0, 1, .. (reverse =
+// false) or P-1, P-2, .. (reverse = true).
+template <int P>
+__device__ __forceinline__ void column_scan(float *ma, const float *mm, int lane, bool reverse) {
+  float carry = 0.f;
+#pragma unroll
+  for (int j = 0; j < P / 32; ++j) {
+    const int k = reverse ? (P - 1 - (32 * j + lane)) : (32 * j + lane);
+    float A = ma[k], M = mm[k];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float pa = __shfl_up_sync(0xffffffffu, A, off), pm = __shfl_up_sync(0xffffffffu, M, off);
+      if (lane >= off) {
+        A = fmaf(M, pa, A);
+        M *= pm;
+      }
+    }
+    float Ae = __shfl_up_sync(0xffffffffu, A, 1), Me = __shfl_up_sync(0xffffffffu, M, 1);
+    if (lane == 0) {
+      Ae = 0.f;
+      Me = 1.f;
+    }
+    ma[k] = fmaf(Me, carry, Ae);
+    carry = __shfl_sync(0xffffffffu, fmaf(M, carry, A), 31);
+  }
+}
+
+template <int CW, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) tridiag_pipe_kernel(const TriArgs<float> a) {
+  using S = PipeShape<CW, NT>;
+  constexpr int C = S::C, P = S::P;
+  extern __shared__ __align__(16) float psm[];
+  float *mapA = psm + 2 * S::kStageWords;
+  float *mapM = mapA + S::kMapWords;
+  int *act = reinterpret_cast<int *>(mapM + S::kMapWords);
+  __shared__ double red[NT / 32];
+  __shared__ int nact_s;
+  const int nr = a.nr, nz = a.nz, pitch = a.pitch;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // right-hand sides selected by the mask, in order
+  if (warp == 0) {
+    int n = 0;
+    for (int b = 0; b < a.m; b += 32) {
+      const int mm = b + lane;
+      const bool sel = mm < a.m && rhs_selected(a.st, a.mask, mm);
+      const unsigned bal = __ballot_sync(0xffffffffu, sel);
+      if (sel) act[n + __popc(bal & ((1u << lane) - 1u))] = mm;
+      n += __popc(bal);
+    }
+    if (lane == 0) nact_s = n;
+  }
+  __syncthreads();
+  const int nact = nact_s;
+  if (nact == 0) return;
+  const int ntiles = (nz + CW - 1) / CW;
+  // R right-hand sides per group: the R <= 8 with the shortest longest CTA
+  // (groups per CTA times R items), the larger R on ties
+  int R = 1;
+  {
+    long long best = -1;
+    for (int r = 1; r <= 8 && r <= nact; ++r) {
+      const long long ng = (long long)((nact + r - 1) / r) * ntiles;
+      const long long span = (ng + gridDim.x - 1) / gridDim.x * r;
+      if (best < 0 || span <= best) {
+        best = span;
+        R = r;
+      }
+    }
+  }
+  const int nblk = (nact + R - 1) / R;
+  const int ngroups = nblk * ntiles;
+  if ((int)blockIdx.x >= ngroups) return;
+
+  const int w = threadIdx.x % CW, c = threadIdx.x / CW;
+  const int rbase = c * C;
+
+  // item (group g, index j) -> tile, right-hand side
+  auto item_of = [&](int g, int j, int &tile, int &mm) {
+    tile = g % ntiles;
+    mm = act[(g / ntiles) * R + j];
+  };
+  auto group_size = [&](int g) { return min(R, nact - (g / ntiles) * R); };
+  auto issue = [&](int g, int j, float *dst) {
+    int tile, mm;
+    item_of(g, j, tile, mm);
+    const float *src = a.in + (size_t)mm * a.field + (size_t)tile * CW;
+    constexpr int kParts = CW / 4;  // 16-byte pieces per tile row
+#pragma unroll
+    for (int i = 0; i < S::kRows * kParts / NT; ++i) {
+      const int q = threadIdx.x + i * NT;
+      const int row = q / kParts, part = q % kParts;
+      const bool ok = row < nr;
+      cp_async16(dst + (row + row / C) * CW + part * 4, src + (size_t)(ok ? row : 0) * pitch + part * 4, ok);
+    }
+    cp_async_commit();
+  };
+
+  int g = blockIdx.x, j = 0, buf = 0;
+  issue(g, 0, psm);
+  float ip[C];
+  int loaded = -1;  // group (stacked tables: item) whose factors are in ip
+  while (g < ngroups) {
+    int tile, mm;
+    item_of(g, j, tile, mm);
+    const int col = tile * CW + w;
+    const int gs = group_size(g);
+    // next item
+    int gn = g, jn = j + 1;
+    if (jn == gs) {
+      gn = g + gridDim.x;
+      jn = 0;
+    }
+    const int key = a.cstride != 0 ? g * R + j : g;
+    if (key != loaded) {
+      loaded = key;
+      const float *ipg = a.IP + (size_t)mm * a.cstride + (size_t)rbase * pitch + col;
+#pragma unroll
+      for (int t = 0; t < C; ++t) ip[t] = (rbase + t < nr && col < nz) ? __ldg(ipg + (size_t)t * pitch) : 0.f;
+    }
+    if (jn == 0 && gn < ngroups && a.cstride == 0) {  // last item of the group: next group's factors into L1
+      const int coln = (gn % ntiles) * CW + w;
+      if (coln < nz) {
+        const float *ipn = a.IP + (size_t)rbase * pitch + coln;
+#pragma unroll
+        for (int t = 0; t < C; ++t)
+          if (rbase + t < nr) prefetch_l1(ipn + (size_t)t * pitch);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();  // this item's tile is in place; the other stage is free
+    float *sbuf = psm + buf * S::kStageWords;
+    if (gn < ngroups) issue(gn, jn, psm + (buf ^ 1) * S::kStageWords);
+    float *sd = sbuf + (c * (C + 1)) * CW + w;  // row rbase + t at sd[t CW]
+    float v[C];
+#pragma unroll
+    for (int t = 0; t < C; ++t) v[t] = sd[t * CW];
+    // forward with zero carry-in
+    float gg = 0.f, mu = 1.f;
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      gg = ip[t] * (v[t] + gg);
+      mu *= ip[t];
+      v[t] = gg;
+    }
+    mapA[w * (P + 1) + c] = gg;
+    mapM[w * (P + 1) + c] = mu;
+    __syncthreads();
+    if (warp < CW) column_scan<P>(mapA + warp * (P + 1), mapM + warp * (P + 1), lane, false);
+    __syncthreads();
+    const float gin = mapA[w * (P + 1) + c];
+    // apply the carry, then the backward recurrence with zero carry-in
+    float pr = 1.f;
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      pr *= ip[t];
+      v[t] = fmaf(pr, gin, v[t]);
+    }
+    float y = 0.f;
+    mu = 1.f;
+#pragma unroll
+    for (int t = C - 1; t >= 0; --t) {
+      y = fmaf(ip[t], y, v[t]);
+      mu *= ip[t];
+      v[t] = y;
+    }
+    mapA[w * (P + 1) + c] = y;  // each thread rewrites only its own slot
+    mapM[w * (P + 1) + c] = mu;
+    __syncthreads();
+    if (warp < CW) column_scan<P>(mapA + warp * (P + 1), mapM + warp * (P + 1), lane, true);
+    __syncthreads();
+    const float yin = mapA[w * (P + 1) + c];
+    // apply the carry; (b', y') partial
+    pr = 1.f;
+    float dot = 0.f;
+#pragma unroll
+    for (int t = C - 1; t >= 0; --t) {
+      pr *= ip[t];
+      v[t] = fmaf(pr, yin, v[t]);
+      dot = fmaf(sd[t * CW], v[t], dot);
+    }
+    if (a.partial != nullptr) {
+      const double sw = warp_sum((double)dot);
+      if (lane == 0) red[warp] = sw;
+    }
+    if (a.split == nullptr) {
+      if (col < nz) {
+        float *o = a.out + (size_t)mm * a.field + (size_t)rbase * pitch + col;
+#pragma unroll
+        for (int t = 0; t < C; ++t)
+          if (rbase + t < nr) o[(size_t)t * pitch] = v[t];
+      }
+      if (a.partial != nullptr) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double tot = 0.0;
+          for (int i = 0; i < NT / 32; ++i) tot += red[i];
+          a.partial[(size_t)mm * kPartialStride + tile] = tot;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < C; ++t) sd[t * CW] = v[t];
+      __syncthreads();
+      if (a.partial != nullptr && threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < NT / 32; ++i) tot += red[i];
+        a.partial[(size_t)mm * kPartialStride + tile] = tot;
+      }
+      // write back in the split layout: one row segment of min(CW, 16)
+      // columns per thread and step
+      constexpr int kSeg = CW < 16 ? CW : 16;
+      constexpr int kSegs = CW / kSeg;
+      const int c0 = tile * CW;
+      for (int q = threadIdx.x; q < nr * kSegs; q += NT) {
+        const int row = q / kSegs, sg = q % kSegs;
+        const int cs = c0 + sg * kSeg;
+        if (cs >= nz) continue;
+        const float *src = sbuf + (row + row / C) * CW + sg * kSeg;
+        if constexpr (kSeg == 16) {
+          float x[16];
+#pragma unroll
+          for (int e = 0; e < 16; e += 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(src + e);
+            x[e] = f.x; x[e + 1] = f.y; x[e + 2] = f.z; x[e + 3] = f.w;
+          }
+          if (cs + 8 < nz) {
+            split_store16(a.split, mm, row, cs, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+          } else {  // only the first 8 columns are inside n8
+            float x8[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x8[e] = x[e];
+            split_store8(a.split, mm, row, cs, a.split_mtiles, a.split_ktiles, a.split_kbe, x8);
+          }
+        } else if constexpr (kSeg == 8) {
+          float x[8];
+          const float4 f0 = *reinterpret_cast<const float4 *>(src), f1 = *reinterpret_cast<const float4 *>(src + 4);
+          x[0] = f0.x; x[1] = f0.y; x[2] = f0.z; x[3] = f0.w; x[4] = f1.x; x[5] = f1.y; x[6] = f1.z; x[7] = f1.w;
+          split_store8(a.split, mm, row, cs, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+        } else {
+          float x[4];
+          const float4 f0 = *reinterpret_cast<const float4 *>(src);
+          x[0] = f0.x; x[1] = f0.y; x[2] = f0.z; x[3] = f0.w;
+          split_store4(a.split, mm, row, cs, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+        }
+      }
+    }
+    g = gn;
+    j = jn;
+    buf ^= 1;
+  }
+}
+
 }  // namespace
 
 // Chunk length C: short enough that the chunk stays in registers without
@@ -418,11 +761,95 @@ void launch_tridiag_reg(const TriArgs<float> &a, cudaStream_t s) {
   tridiag_reg_kernel<C2, WPC, CW><<<grid, 32 * WPC * CW, smem, s>>>(a);
 }
 
+// FP32 kernel variants: 1 the staged register kernel; 2.. the pipelined
+// column-tile kernels <CW columns, NT threads>.
+struct PipeVariant { int id, cw, nt; };
+constexpr PipeVariant kPipeVariants[] = {{2, 32, 1024}, {3, 16, 512}, {4, 16, 1024}, {5, 8, 512},
+                                         {6, 8, 1024}, {7, 4, 512}, {8, 4, 1024}};
+
+int pipe_max_rows(const PipeVariant &v) { return 16 * v.nt / v.cw; }
+
+int tridiag_variants(int nr, int *ids) {
+  // the register kernel first (the default: measured faster than the
+  // pipelined kernels at nr = 1024 and equal at 4096), then the pipelined
+  // kernels whose column covers nr with at most half of it idle
+  int n = 0;
+  if (nr <= 4096) ids[n++] = 1;
+  for (const PipeVariant &v : kPipeVariants)
+    if (nr <= pipe_max_rows(v) && 2 * nr > pipe_max_rows(v)) ids[n++] = v.id;
+  return n;
+}
+
+static const PipeVariant *find_pipe(int id) {
+  for (const PipeVariant &v : kPipeVariants)
+    if (v.id == id) return &v;
+  return nullptr;
+}
+
+// The variant that runs for nr rows: `variant` if it covers nr, else the
+// default (0 when no FP32 tile kernel covers nr).
+static int resolve_variant(int nr, int variant) {
+  int ids[16];
+  const int n = tridiag_variants(nr, ids);
+  if (n == 0) return 0;
+  for (int i = 0; i < n; ++i)
+    if (ids[i] == variant) return variant;
+  return ids[0];
+}
+
 // Columns per CTA of the register kernel for nr rows (0: not covered).
-int tridiag_reg_cols(int nr) { return nr <= 2048 ? 8 : (nr <= 4096 ? 4 : 0); }
+static int reg_cols(int nr) { return nr <= 2048 ? 8 : (nr <= 4096 ? 4 : 0); }
+
+int tridiag_reg_cols(int nr, int variant) {
+  const int v = resolve_variant(nr, variant);
+  if (v == 0) return 0;
+  if (v == 1) return reg_cols(nr);
+  return find_pipe(v)->cw;
+}
+
+template <int CW, int NT>
+void launch_tridiag_pipe(const TriArgs<float> &a, cudaStream_t s) {
+  using S = PipeShape<CW, NT>;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  ensure_smem_attr((const void *)tridiag_pipe_kernel<CW, NT>, S::smem);
+  const long long items = (long long)a.m * ((a.nz + CW - 1) / CW);
+  const int grid = (int)std::min<long long>(items, (long long)sms * (1024 / NT));
+  TriArgs<float> b = a;  // the kernel reads the scaled tables through IP and E
+  b.IP = a.IPS;
+  b.E = a.RS;
+  tridiag_pipe_kernel<CW, NT><<<grid, NT, S::smem, s>>>(b);
+}
+
+int tridiag_effective(int nr, int variant, int m, bool scaled_tables) {
+  const int v = resolve_variant(nr, variant);
+  if (v >= 2 && (m > PipeShape<16, 1024>::kMaxList || !scaled_tables)) return 1;
+  return v;
+}
 
 bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
-  // chunks of up to 16 rows in registers; 2, 4 or 8 warps per column system
+  int v = resolve_variant(a.nr, a.variant);
+  if (v == 0) return false;
+  // the pipelined kernels solve the row-scaled systems; plain data takes the
+  // register kernel
+  if (!a.prescaled) v = 1;
+  switch (v) {
+    case 2: launch_tridiag_pipe<32, 1024>(a, s); return true;
+    case 3: launch_tridiag_pipe<16, 512>(a, s); return true;
+    case 4: launch_tridiag_pipe<16, 1024>(a, s); return true;
+    case 5: launch_tridiag_pipe<8, 512>(a, s); return true;
+    case 6: launch_tridiag_pipe<8, 1024>(a, s); return true;
+    case 7: launch_tridiag_pipe<4, 512>(a, s); return true;
+    case 8: launch_tridiag_pipe<4, 1024>(a, s); return true;
+    default: break;
+  }
+  // the staged register kernel: chunks of up to 16 rows in registers; 2, 4 or
+  // 8 warps per column system
   const int c2 = (a.nr + 63) / 64;
   if (c2 <= 4) launch_tridiag_reg<4, 2, 8>(a, s);
   else if (c2 <= 8) launch_tridiag_reg<8, 2, 8>(a, s);
@@ -433,7 +860,7 @@ bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
   return true;
 }
 
-bool tridiag_split_ok(int nr) { return tridiag_reg_cols(nr) != 0; }
+bool tridiag_split_ok(int nr) { return reg_cols(nr) != 0; }
 
 template <typename T>
 void launch_tridiag(const TriArgs<T> &a, cudaStream_t s) {
