@@ -136,6 +136,14 @@ int ax_destroy_operator(ax_operator *op);
 int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
                      double *gamma1, double *gamma2);
 
+/* The Chebyshev bounds (gamma_1, gamma_2 of Eq. energy_rel) that a solve of m
+ * right-hand sides uses, per right-hand side (host arrays [m]): the Lanczos
+ * estimate of option "cheb_bounds" where it applies and has been formed (by
+ * an earlier Chebyshev solve of at least m right-hand sides), else the
+ * face-wise bounds.  *estimated = 1 if any right-hand side takes the
+ * estimate.  No device work. */
+int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double *gamma2, int32_t *estimated);
+
 /* Tuning options of an operator (host-side settings, no device work):
  *   "profile"        1: per-launch CUDA-event profiler on (see ax_profile_read)
  *   "inner_tol"      relative residual reduction of each FP32 inner solve of the
@@ -167,6 +175,27 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  *   "tc_fused"       1 (default): with the tensor-core transform, the mixed PCG
  *                    forms p = z + beta p and x += alpha p in the inverse
  *                    transform's epilogue; 0: in the stencil and update pass
+ *   "mode_kernel"    FP32 mode solves (the per-mode tridiagonal systems of
+ *                    Eq. eq_trid): 0 (default) the library's choice, 1 the
+ *                    staged register kernel, 2..8 the pipelined column-tile
+ *                    kernels on the row-scaled systems D T_l D (unit
+ *                    couplings; the transforms around them apply D); an id
+ *                    whose column does not fit nr is refused
+ *   "cheb_bounds"    Chebyshev bounds gamma_1, gamma_2 (Eq. energy_rel): 0 the
+ *                    face-wise bounds (min / max of kappa / kappa~ and q / q~),
+ *                    1 a Lanczos estimate from "cheb_steps" PCG steps (the
+ *                    extreme eigenvalues of the Lanczos tridiagonal of the PCG
+ *                    coefficients, widened by "cheb_widen"), -1 (default) the
+ *                    estimate only where the face-wise gamma_1 is 0 (q_min = 0 <
+ *                    q_max).  The estimate runs once per operator (FP32 kernels,
+ *                    all right-hand sides, cached); its steps count in
+ *                    info.iters of the solve that ran it
+ *   "cheb_steps"     PCG steps of that estimate (2..200, default 20)
+ *   "cheb_widen"     relative widening of the estimate (0 <= v < 1, default 0.05)
+ *   "cheb_check"     the Chebyshev methods form the residual norm (a reduction)
+ *                    every v-th step only (1..256, default 1; always on the last
+ *                    step of each graph replay); the steps between advance the
+ *                    three-term recurrence without any inner product
  *   "tc_stall_test"  1: test of the failure path: the next tensor-core transform
  *                    stops its copies before the first stage, one of its bounded
  *                    waits (short limit) runs out, the kernel sets the device's

@@ -29,6 +29,7 @@ from .axisym import (  # noqa: F401
     assemble_preconditioner,
     pcg,
     chebyshev_bounds,
+    lanczos_bounds,
     chebyshev,
     Operator,
 )

@@ -365,6 +365,49 @@ def chebyshev_bounds(kappa_r, kappa_z, q, kappa_t: float, q_t: float):
     return lo, hi
 
 
+def lanczos_bounds(apply_A: Callable, apply_Binv: Callable, phi, steps: int = 20, widen: float = 0.05):
+    """Estimates of gamma_1, gamma_2 (Eq. energy_rel) for the Chebyshev
+    iteration where the face-wise bounds are loose or degenerate (q_min = 0 <
+    q_max).  `steps` textbook PCG steps (the iteration of pcg() without its
+    stop test) on A y = phi from y = 0 give the coefficients alpha_j, beta_j;
+    they are the Lanczos process of B^-1 A in the B-inner product, whose
+    tridiagonal matrix T has (Saad, "Iterative methods for sparse linear
+    systems", 2nd ed., Section 6.7.3)
+      T[j, j] = 1 / alpha_j + beta_{j-1} / alpha_{j-1}   (beta_{-1} = 0),
+      T[j, j+1] = T[j+1, j] = sqrt(beta_j) / alpha_j.
+    Its extreme eigenvalues (Ritz values) approach lambda_min and lambda_max of
+    B^-1 A from inside; the estimates are widened: gamma_1 = (1 - widen)
+    theta_min, gamma_2 = (1 + widen) theta_max.  Stops early when the
+    residual vanishes.  Returns (gamma1, gamma2, alphas, betas)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    r = phi.copy()
+    z = apply_Binv(r)
+    p = z.copy()
+    rho = float(np.vdot(r, z))
+    alphas, betas = [], []
+    for _ in range(steps):
+        if rho == 0.0:
+            break
+        q = apply_A(p)
+        alpha = rho / float(np.vdot(p, q))
+        alphas.append(alpha)
+        r = r - alpha * q
+        z = apply_Binv(r)
+        rho_new = float(np.vdot(r, z))
+        beta = rho_new / rho
+        betas.append(beta)
+        rho = rho_new
+        p = z + beta * p
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    theta = np.linalg.eigvalsh(T)
+    return (1.0 - widen) * theta[0], (1.0 + widen) * theta[-1], alphas, betas
+
+
 def chebyshev(apply_A: Callable, apply_Binv: Callable, phi, gamma1: float, gamma2: float,
               tol: float, y0=None, max_iter: int = 100000):
     """Implicit three-layer Chebyshev iteration (Eq. main-scheme) with the

@@ -186,3 +186,88 @@ def h1_loss(out, target, lam):
 def mse_loss(out, target):
     d = out - target
     return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+# ---------------------------------------------------------------------------
+# Solver-side steps of the learned guess: lattice features, lift, optimiser.
+# The paper has no network; these are the plain definitions the library's
+# features / lift kernels and its Adam step are checked against.
+# ---------------------------------------------------------------------------
+def lattice_index(p, n, hw):
+    """Grid index range of lattice cell p along an axis of n grid points:
+    cell averages when n is a multiple of hw (indices p n/hw .. p n/hw +
+    n/hw - 1), else the single sample at index floor(p n / hw)."""
+    if n % hw == 0:
+        f = n // hw
+        return list(range(p * f, p * f + f))
+    return [(p * n) // hw]
+
+
+def features(kappa, q, f, hw, g=None):
+    """Network input of one right-hand side on an hw x hw lattice: channel 0
+    the mean of log kappa, channel 1 the mean of q, channel 2 the mean of
+    g / s over the grid samples of each lattice cell (lattice_index along r
+    and along z), s = max |g| (1 if g = 0).  g defaults to f (raw feature);
+    features_pre passes g = B^-1 (r f).  Returns (x (3, hw, hw), s)."""
+    kappa = np.asarray(kappa, dtype=np.float64)
+    g = np.asarray(f if g is None else g, dtype=np.float64)
+    nr, nz = kappa.shape
+    s = float(np.abs(g).max())
+    s = s if s > 0.0 else 1.0
+    x = np.zeros((3, hw, hw))
+    lk = np.log(kappa)
+    for py in range(hw):
+        ri = lattice_index(py, nr, hw)
+        for px in range(hw):
+            zi = lattice_index(px, nz, hw)
+            blk = np.ix_(ri, zi)
+            x[0, py, px] = lk[blk].mean()
+            x[1, py, px] = np.asarray(q)[blk].mean()
+            x[2, py, px] = g[blk].mean() / s
+    return x, s
+
+
+def features_pre(op, kappa, q, f, hw):
+    """features() with g = B^-1 (r f): the right-hand side after one
+    application of the operator's Laplace preconditioner (Section 4.2,
+    Eqs. fft_phi, eq_trid), op an oracle Operator."""
+    g = op.apply_Binv(op.phi(f))
+    return features(kappa, q, f, hw, g=g)
+
+
+def bilinear_lift(y, s, nr, nz):
+    """u[i, k] = s times the bilinear interpolation of the lattice values y
+    (hw x hw) at grid node (i, k), both placed by cell centres on the unit
+    square of index space: lattice value (py, px) at ((py + 1/2)/hw,
+    (px + 1/2)/hw), node (i, k) at ((i + 1/2)/nr, (k + 1/2)/nz).  Beyond the
+    outermost lattice centres the value is held constant (the coordinates
+    are clamped to the lattice)."""
+    y = np.asarray(y, dtype=np.float64)
+    hw = y.shape[0]
+    u = np.zeros((nr, nz))
+    for i in range(nr):
+        gy = (i + 0.5) * hw / nr - 0.5
+        y0 = min(max(int(np.floor(gy)), 0), hw - 1)
+        y1 = min(y0 + 1, hw - 1)
+        wy = min(max(gy - y0, 0.0), 1.0)
+        for k in range(nz):
+            gx = (k + 0.5) * hw / nz - 0.5
+            x0 = min(max(int(np.floor(gx)), 0), hw - 1)
+            x1 = min(x0 + 1, hw - 1)
+            wx = min(max(gx - x0, 0.0), 1.0)
+            u[i, k] = s * ((1 - wy) * ((1 - wx) * y[y0, x0] + wx * y[y0, x1])
+                           + wy * ((1 - wx) * y[y1, x0] + wx * y[y1, x1]))
+    return u
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One step of Adam (Kingma and Ba, "Adam: a method for stochastic
+    optimization", Algorithm 1): moments m <- b1 m + (1 - b1) g,
+    v <- b2 v + (1 - b2) g^2, bias corrections 1 - b1^t and 1 - b2^t, update
+    p <- p - lr mhat / (sqrt(vhat) + eps).  t counts steps from 1.  Returns
+    (p, m, v) as new arrays."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v

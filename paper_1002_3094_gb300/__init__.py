@@ -48,7 +48,7 @@ EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_
             "ax_guessnet_create", "ax_guessnet_destroy", "ax_guessnet_num_params", "ax_guessnet_get_params",
             "ax_guessnet_set_params", "ax_guessnet_forward", "ax_guessnet_gradients", "ax_guessnet_train_step",
             "ax_guessnet_save", "ax_guessnet_load", "ax_guessnet_features", "ax_guessnet_lift",
-            "ax_guessnet_set_loss", "ax_guessnet_features_pre")
+            "ax_guessnet_set_loss", "ax_guessnet_features_pre", "ax_chebyshev_bounds")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "pcg_update": 6, "other": 7}
@@ -126,6 +126,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_kernel_launches.argtypes = []
     lib.ax_kernel_launches.restype = ctypes.c_int64
     lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
+    lib.ax_chebyshev_bounds.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i32)]
     for name in EXPORTED:
         if name not in ("ax_status_string", "ax_version", "ax_kernel_launches", "ax_last_error",
                         "ax_guessnet_num_params"):
@@ -194,6 +195,18 @@ def ax_operator_info(op: int):
     vals = [ctypes.c_double() for _ in range(4)]
     _check(load_library().ax_operator_info(op, *[ctypes.byref(v) for v in vals]), "ax_operator_info")
     return tuple(v.value for v in vals)
+
+
+def ax_chebyshev_bounds(op: int, m: int):
+    """(gamma1 [m], gamma2 [m], estimated) of the next Chebyshev solve of m
+    right-hand sides (see include/axpcg.h)."""
+    import numpy as np
+    g1 = np.zeros(m)
+    g2 = np.zeros(m)
+    est = ctypes.c_int32()
+    _check(load_library().ax_chebyshev_bounds(op, m, g1.ctypes.data, g2.ctypes.data, ctypes.byref(est)),
+           "ax_chebyshev_bounds")
+    return g1, g2, bool(est.value)
 
 
 def ax_set_option(op: int, name: str, value: float, raise_on_error: bool = True) -> int:

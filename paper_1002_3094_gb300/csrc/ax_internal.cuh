@@ -153,6 +153,10 @@ struct ax_operator {
   double kappa_t = 0, q_t = 0, gamma1 = 0, gamma2 = 0;
   // group operator of a batch: the Chebyshev bounds of each member (by RHS)
   std::vector<double> mgamma1, mgamma2;
+  // Lanczos estimates of the Chebyshev bounds per right-hand side (option
+  // "cheb_bounds"), valid for lz_m right-hand sides (0: none)
+  std::vector<double> lz_g1, lz_g2;
+  int lz_m = 0;
   int device = 0;
   ax::FftPlan plan;
   int *rader_perm = nullptr;  // [2 P] device

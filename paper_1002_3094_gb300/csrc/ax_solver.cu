@@ -79,6 +79,11 @@ struct Workspace {
   int tc_stall_test = 0;        // 1: the next tensor-core transform lets one bounded wait run out
   int tc_unfused = 0;           // 1: mixed PCG forms p in the stencil, not in the inverse transform
   double replace_delta = 0.1;   // residual reduction between FP64 replacements
+  int cheb_bounds = -1;         // Chebyshev bounds: 0 face-wise, 1 Lanczos estimate, -1 Lanczos
+                                // where the face-wise gamma_1 degenerates (q_min = 0 < q_max)
+  int cheb_steps = 20;          // PCG steps of the Lanczos estimate
+  double cheb_widen = 0.05;     // relative widening of the estimated bounds
+  int cheb_check = 1;           // Chebyshev: residual norm (a reduction) every cheb_check-th step
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
   std::vector<ProfEvent> prof_events;
@@ -684,18 +689,20 @@ __global__ void sc_true_check(RhsState *st, const double *p, int nb) {
 
 // Chebyshev: rr = ||A y - phi||^2 of the current iterate; stop or continue and
 // advance alpha_{k+1} = 4 / (4 - rho0^2 alpha_k) (alpha for the first step is 1).
-__global__ void sc_cheb(RhsState *st, const double *p, int nb, const double *chp, int on_converge) {
+// check = 0: a step without the residual norm (no reduction): only the
+// recurrence advances.
+__global__ void sc_cheb(RhsState *st, const double *p, int nb, const double *chp, int on_converge, int check = 1) {
   const int m = blockIdx.x;
   if (st[m].state != kActive) return;
   const double rho0sq = chp[2 * m + 1];
-  const double rr = reduce_part(p + (size_t)m * kPartialStride, nb);
+  const double rr = check ? reduce_part(p + (size_t)m * kPartialStride, nb) : st[m].rr;
   if (threadIdx.x == 0) {
     RhsState s = st[m];
     s.rr = rr;
     if (!isfinite(rr)) {
       s.state = kFailed;
       s.status = AX_ERR_BREAKDOWN;
-    } else if (rr <= s.thresh2) {
+    } else if (check && rr <= s.thresh2) {
       s.state = on_converge;
     } else if (s.iters >= s.max_iter) {
       s.state = (on_converge == kDone) ? kDone : kFailed;
@@ -1399,7 +1406,7 @@ struct ChebVecs {
 
 template <typename T>
 void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, Workspace *w,
-                    int on_converge, int parity, cudaStream_t s) {
+                    int on_converge, int parity, cudaStream_t s, bool check = true) {
   const int V = VecT<T>::n;
   const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
   double *prr = part_ptr(w, kPartB);
@@ -1409,10 +1416,10 @@ void cheb_iteration(const ax_operator *op, int m, const ChebVecs<T> &v, RhsState
   sa.in = y;
   sa.out = v.res;
   sa.phi = v.phi;
-  sa.partial = prr;
+  sa.partial = check ? prr : nullptr;  // no reduction on the steps between checks
   launch_stencil<T>(kStencilCheb, sa, s);
   note_launch();
-  sc_cheb<<<m, 32, 0, s>>>(st, prr, nbs, w->chp, on_converge);
+  sc_cheb<<<m, 32, 0, s>>>(st, prr, nbs, w->chp, on_converge, check ? 1 : 0);
   DstArgs<T> f = dst_args<T>(op, m, op->nr, st, kActive);
   f.in = v.res;
   f.out = v.res;
@@ -1535,9 +1542,206 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
   return AX_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Lanczos estimate of the Chebyshev bounds (Eq. energy_rel).  The face-wise
+// bounds min / max of kappa / kappa~ and q / q~ are rigorous, but with
+// q_min = 0 < q_max the lower one is 0, which leaves the Chebyshev iteration
+// without a spectral interval.  There the bounds come from `cheb_steps` PCG
+// steps (FP32 kernels, every right-hand side at once, from zero): the
+// coefficients alpha_j, beta_j are the Lanczos process of B^-1 A in the
+// B-inner product, with the tridiagonal matrix (Saad, "Iterative methods for
+// sparse linear systems", 2nd ed., Section 6.7.3)
+//   T[j][j] = 1 / alpha_j + beta_{j-1} / alpha_{j-1},  T[j][j+1] = sqrt(beta_j) / alpha_j,
+// whose extreme eigenvalues (Ritz values) approach those of B^-1 A from
+// inside; they are widened by `cheb_widen` (gamma_1 = (1 - w) theta_min,
+// gamma_2 = (1 + w) theta_max).  Cached per operator and right-hand side.
+// ---------------------------------------------------------------------------
+bool cheb_uses_lanczos(const ax_operator *op, double face_gamma1) {
+  const int mode = op->ws->cheb_bounds;
+  return mode == 1 || (mode == -1 && !(face_gamma1 > 0.0));
+}
+
+// hist[m][2 k]: (alpha_j, beta_j) of step j of right-hand side m; an alpha of
+// 0 marks the end (the step did not run, or broke down).
+__global__ void sc_record_lanczos(const RhsState *st, double *hist, int m, int j, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const RhsState s = st[i];
+  double *h = hist + (size_t)i * 2 * k;
+  const bool ran = (s.state == kActive || s.state == kDone) && s.iters == j + 1 && isfinite(s.alpha);
+  h[2 * j] = ran ? s.alpha : 0.0;
+  h[2 * j + 1] = (ran && s.state == kActive && isfinite(s.beta)) ? s.beta : 0.0;
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal (d, e) (Sturm
+// count of the LDL^T pivots; Golub and Van Loan, Section 8.4).
+static int sturm_count(const std::vector<double> &d, const std::vector<double> &e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t j = 0; j < d.size(); ++j) {
+    const double e2 = j ? e[j - 1] * e[j - 1] : 0.0;
+    q = d[j] - x - (j ? e2 / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Smallest and largest eigenvalue of the symmetric tridiagonal (d, e) by
+// bisection on the Gershgorin interval.
+static void tridiag_extremes(const std::vector<double> &d, const std::vector<double> &e, double &lo, double &hi) {
+  const size_t n = d.size();
+  double a = d[0], b = d[0];
+  for (size_t j = 0; j < n; ++j) {
+    const double r = (j ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < n ? std::fabs(e[j]) : 0.0);
+    a = std::min(a, d[j] - r);
+    b = std::max(b, d[j] + r);
+  }
+  double x0 = a, x1 = b;  // smallest: count(x) >= 1
+  for (int it = 0; it < 200 && x1 - x0 > 1e-15 * std::max(std::fabs(x0), std::fabs(x1)); ++it) {
+    const double mid = 0.5 * (x0 + x1);
+    if (sturm_count(d, e, mid) >= 1) x1 = mid; else x0 = mid;
+  }
+  lo = 0.5 * (x0 + x1);
+  x0 = a, x1 = b;  // largest: count(x) >= n
+  for (int it = 0; it < 200 && x1 - x0 > 1e-15 * std::max(std::fabs(x0), std::fabs(x1)); ++it) {
+    const double mid = 0.5 * (x0 + x1);
+    if (sturm_count(d, e, mid) >= (int)n) x1 = mid; else x0 = mid;
+  }
+  hi = 0.5 * (x0 + x1);
+}
+
+// Runs the PCG steps of the estimate on phi64 (already formed) and caches the
+// bounds of every right-hand side in op->lz_g1 / lz_g2; `steps` (host
+// vector, may be null) receives the steps each right-hand side ran.  Uses
+// the FP32 vectors and the right-hand-side states (before the solve sets them).
+int cheb_estimate(ax_operator *op, int m, cudaStream_t s, std::vector<int> *steps) {
+  Workspace *w = op->ws;
+  const int k = w->cheb_steps;
+  const size_t field = field_elems(op);
+  int rc;
+  if ((rc = ensure_vec32(op, m, false)) != AX_OK) return rc;
+  if (op->dst_tc) {
+    if ((rc = ensure_split(op, (size_t)m * split_geom(op, op->nr).bytes_per_rhs)) != AX_OK) return rc;
+    const bool cz = op->bc_z == 1;
+    if (!tc_table(op->device, op->nz, cz ? kTableCosForward : kTableSine) ||
+        !tc_table(op->device, op->nz, cz ? kTableCosInverse : kTableSine) || !tc_flag(op->device))
+      return AX_ERR_OOM;
+  }
+  double *hist = nullptr;
+  AX_TRY(dalloc(&hist, (size_t)m * 2 * k));
+  struct Free { double *p; ~Free() { dfree(p); } } hold{hist};
+  AX_TRY(cudaMemsetAsync(hist, 0, sizeof(double) * m * 2 * k, s));
+  const size_t n = field * m;
+  const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 65535);
+  note_launch();
+  to_precision<float><<<blocks, 256, 0, s>>>(w->phi64, w->r32, n);
+  AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * n, s));
+  // states: every right-hand side active (threshold 0: nothing converges
+  // before the k steps unless its residual vanishes), max_iter = k
+  {
+    std::vector<RhsState> init(m);
+    for (int i = 0; i < m; ++i) {
+      std::memset(&init[i], 0, sizeof(RhsState));
+      init[i].state = kActive;
+      init[i].max_iter = k;
+      init[i].thresh2 = 0.0;
+      init[i].bb = 1.0;
+    }
+    AX_TRY(cudaMemcpyAsync(w->st, init.data(), sizeof(RhsState) * m, cudaMemcpyHostToDevice, s));
+  }
+  PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
+  const int nbd = precond_partials<float>(op, m);
+  precond_apply<float>(op, m, v.r, v.z, w->st, kActive, part_ptr(w, kPartC), s, v.q);
+  note_launch();
+  sc_rho_init<<<m, 32, 0, s>>>(w->st, part_ptr(w, kPartC), nbd, kActive);
+  AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(float) * n, s));
+  for (int j = 0; j < k; ++j) {
+    pcg_iteration<float>(op, m, v, w->st, w, kDone, s);
+    note_launch();
+    sc_record_lanczos<<<(m + 31) / 32, 32, 0, s>>>(w->st, hist, m, j, k);
+  }
+  AX_CHECK_LAUNCH();
+  std::vector<double> h((size_t)m * 2 * k);
+  AX_TRY(cudaMemcpyAsync(h.data(), hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  AX_TRY(cudaStreamSynchronize(s));
+  op->lz_g1.assign(m, 0.0);
+  op->lz_g2.assign(m, 0.0);
+  if (steps) steps->assign(m, 0);
+  const double wd = w->cheb_widen;
+  for (int i = 0; i < m; ++i) {
+    const double *hi = &h[(size_t)i * 2 * k];
+    int cnt = 0;
+    while (cnt < k && hi[2 * cnt] > 0.0) ++cnt;
+    // the last beta is only needed when a further step follows
+    std::vector<double> d(cnt), e(cnt > 0 ? cnt - 1 : 0);
+    bool ok = cnt > 0;
+    for (int j = 0; j < cnt && ok; ++j) {
+      d[j] = 1.0 / hi[2 * j] + (j ? hi[2 * j - 1] / hi[2 * j - 2] : 0.0);
+      if (j + 1 < cnt) {
+        ok = hi[2 * j + 1] > 0.0;
+        e[j] = std::sqrt(std::max(hi[2 * j + 1], 0.0)) / hi[2 * j];
+      }
+    }
+    const bool mem = (size_t)i < op->mgamma1.size();
+    double g1 = mem ? op->mgamma1[i] : op->gamma1, g2 = mem ? op->mgamma2[i] : op->gamma2;
+    if (ok) {
+      double lo, hi2;
+      tridiag_extremes(d, e, lo, hi2);
+      if (lo > 0.0 && std::isfinite(hi2) && hi2 >= lo) {
+        g1 = (1.0 - wd) * lo;
+        g2 = (1.0 + wd) * hi2;
+      }
+    }
+    if (!(g1 > 0.0)) g1 = 1e-3 * g2;  // no usable estimate: a wide interval
+    op->lz_g1[i] = g1;
+    op->lz_g2[i] = g2;
+    if (steps) (*steps)[i] = cnt;
+  }
+  if (op->mgamma1.empty()) {
+    // one operator: the spectrum is that of every right-hand side, so all of
+    // them take the widest interval found
+    const double g1 = *std::min_element(op->lz_g1.begin(), op->lz_g1.end());
+    const double g2 = *std::max_element(op->lz_g2.begin(), op->lz_g2.end());
+    op->lz_g1.assign(m, g1);
+    op->lz_g2.assign(m, g2);
+  }
+  op->lz_m = m;
+  return AX_OK;
+}
+
+// Inner Chebyshev solves of known length: right-hand side i runs exactly
+// n[i] steps (the residual test is off; the FP64 outer residual decides).
+__global__ void sc_cheb_fixed(RhsState *st, const int *n, int m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || st[i].state != kActive) return;
+  st[i].max_iter = n[i];
+  st[i].thresh2 = -1.0;
+}
+
+// Smallest n >= 1 with the Chebyshev bound 2 rho1^n / (1 + rho1^(2n)) <= eta
+// on the A-norm error (rho1 = (1 - sqrt xi) / (1 + sqrt xi), xi =
+// gamma1 / gamma2), at most cap.
+static int cheb_steps_for(double xi, double eta, int cap) {
+  const double sx = std::sqrt(std::max(xi, 0.0)), rho1 = (1.0 - sx) / (1.0 + sx);
+  double pn = 1.0;
+  for (int n = 1; n <= cap; ++n) {
+    pn *= rho1;
+    if (2.0 * pn / (1.0 + pn * pn) <= eta) return n;
+  }
+  return cap;
+}
+
+// apriori_eta > 0 (the inner solves of AX_CHEB_MIXED): every active
+// right-hand side runs the number of steps whose Chebyshev bound reaches
+// apriori_eta, with no residual test on the way (the residual norm is formed
+// on the last step of each graph replay only): no inner products at all.
+// The residual an FP32 iteration recomputes as A y - phi stops falling at its
+// rounding level (far above the inner tolerance for ill-conditioned A), so a
+// residual test there never passes.
 template <typename T>
 int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphCache &g, int on_conv, int *parity,
-              cudaStream_t s) {
+              cudaStream_t s, double apriori_eta = 0.0) {
   Workspace *w = op->ws;
   // tau_0 = 2 / (gamma1 + gamma2), rho_0 = (1 - xi) / (1 + xi), xi = gamma1 / gamma2,
   // per right-hand side: the members of a batched group have their own bounds
@@ -1545,19 +1749,38 @@ int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphC
     std::vector<double> par(2 * (size_t)m);
     for (int i = 0; i < m; ++i) {
       const bool mem = (size_t)i < op->mgamma1.size();
-      const double g1 = mem ? op->mgamma1[i] : op->gamma1, g2 = mem ? op->mgamma2[i] : op->gamma2;
+      double g1 = mem ? op->mgamma1[i] : op->gamma1, g2 = mem ? op->mgamma2[i] : op->gamma2;
+      if (op->lz_m >= m && cheb_uses_lanczos(op, g1)) {
+        g1 = op->lz_g1[i];
+        g2 = op->lz_g2[i];
+      }
       const double xi = g1 / g2, rho0 = (1.0 - xi) / (1.0 + xi);
       par[2 * i] = 2.0 / (g1 + g2);
       par[2 * i + 1] = rho0 * rho0;
     }
     AX_TRY(cudaMemcpyAsync(w->chp, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice, s));
+    if (apriori_eta > 0.0) {
+      std::vector<int> n(m);
+      for (int i = 0; i < m; ++i) {
+        const double rho0 = std::sqrt(par[2 * i + 1]), xi = (1.0 - rho0) / (1.0 + rho0);
+        n[i] = cheb_steps_for(xi, apriori_eta, w->inner_max);
+      }
+      int *dn = reinterpret_cast<int *>(part_ptr(w, kPartD));  // free at this point of the solve
+      AX_TRY(cudaMemcpyAsync(dn, n.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+      note_launch();
+      sc_cheb_fixed<<<(m + 31) / 32, 32, 0, s>>>(st, dn, m);
+    }
     AX_TRY(cudaStreamSynchronize(s));
   }
   const int K = 2 * std::max(1, w->graph_iters / 2);  // even: the buffer roles repeat
-  const int key = m * 4 + 2 + (on_conv == kDone ? 1 : 0) + (*parity << 20);
+  const int key = m * 4 + 2 + (on_conv == kDone ? 1 : 0) + (*parity << 20) + (apriori_eta > 0.0 ? 1 << 21 : 0);
   for (int guard = 0; guard < 1000000; ++guard) {
+    // the residual norm every cheb_check-th step, and on the last step of
+    // each replay (where the host reads the states)
+    const int ck = apriori_eta > 0.0 ? K : w->cheb_check;
     int rc = run_graph(w, g, key, s, [&](cudaStream_t cs) {
-      for (int k = 0; k < K; ++k) cheb_iteration<T>(op, m, v, st, w, on_conv, (*parity + k) & 1, cs);
+      for (int k = 0; k < K; ++k)
+        cheb_iteration<T>(op, m, v, st, w, on_conv, (*parity + k) & 1, cs, (k + 1) % ck == 0 || k == K - 1);
     });
     if (rc != AX_OK) return rc;
     RhsState *h = w->h_st;
@@ -1820,6 +2043,24 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t, double
   return AX_OK;
 }
 
+int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double *gamma2, int32_t *estimated) {
+  if (!op || m < 1 || !gamma1 || !gamma2) return AX_ERR_INVALID_ARG;
+  int any = 0;
+  for (int i = 0; i < m; ++i) {
+    const bool mem = (size_t)i < op->mgamma1.size();
+    double g1 = mem ? op->mgamma1[i] : op->gamma1, g2 = mem ? op->mgamma2[i] : op->gamma2;
+    if (op->lz_m >= m && cheb_uses_lanczos(op, g1)) {
+      g1 = op->lz_g1[i];
+      g2 = op->lz_g2[i];
+      any = 1;
+    }
+    gamma1[i] = g1;
+    gamma2[i] = g2;
+  }
+  if (estimated) *estimated = any;
+  return AX_OK;
+}
+
 int ax_set_option(ax_operator *op, const char *name, double value) {
   if (!op || !name) return AX_ERR_INVALID_ARG;
   Workspace *w = op->ws;
@@ -1870,6 +2111,22 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     }
     op->tri_variant = v;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+  } else if (!strcmp(name, "cheb_bounds")) {
+    if (value != -1.0 && value != 0.0 && value != 1.0) return AX_ERR_INVALID_ARG;
+    w->cheb_bounds = (int)value;
+    op->lz_m = 0;
+  } else if (!strcmp(name, "cheb_steps")) {
+    if (!(value >= 2 && value <= 200) || value != (int)value) return AX_ERR_INVALID_ARG;
+    w->cheb_steps = (int)value;
+    op->lz_m = 0;
+  } else if (!strcmp(name, "cheb_widen")) {
+    if (!(value >= 0.0 && value < 1.0)) return AX_ERR_INVALID_ARG;
+    w->cheb_widen = value;
+    op->lz_m = 0;
+  } else if (!strcmp(name, "cheb_check")) {
+    if (!(value >= 1 && value <= 256) || value != (int)value) return AX_ERR_INVALID_ARG;
+    w->cheb_check = (int)value;
+    free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "max_outer")) {
     if (!(value >= 1)) return AX_ERR_INVALID_ARG;
     w->max_outer = (int)value;
@@ -2348,6 +2605,15 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   const int nbs64 = stencil_blocks_per_rhs(nr, nz, 2);
   const bool cheb = (method == AX_CHEB_FP64 || method == AX_CHEB_MIXED);
   int outer_kind = 0;
+  // Chebyshev bounds from a Lanczos estimate where they are needed (see
+  // cheb_estimate); its PCG steps count as iterations of this solve
+  std::vector<int> lz_steps;
+  if (cheb && op->lz_m < m) {
+    bool need = false;
+    for (int i = 0; i < m && !need; ++i)
+      need = cheb_uses_lanczos(op, (size_t)i < op->mgamma1.size() ? op->mgamma1[i] : op->gamma1);
+    if (need && (rc = cheb_estimate(op, m, s, &lz_steps)) != AX_OK) return rc;
+  }
 
   if (method == AX_PCG_FP64 || method == AX_CHEB_FP64) {
     if ((rc = ensure_vec64(op, m, cheb)) != AX_OK) return rc;
@@ -2452,7 +2718,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
         AX_TRY(cudaMemsetAsync(w->y32prev, 0, field * m * sizeof(float), s));
         ChebVecs<float> v{w->x32, w->y32prev, w->z32, w->r32};
         int parity = 0;
-        if ((rc = cheb_loop<float>(op, m, v, si, w->gc32, kDone, &parity, s)) != AX_OK) return rc;
+        if ((rc = cheb_loop<float>(op, m, v, si, w->gc32, kDone, &parity, s, w->inner_tol)) != AX_OK) return rc;
         RhsState *hh = w->h_st + m;
         if ((rc = read_states(w, si, m, s, hh)) != AX_OK) return rc;
         for (int i = 0; i < m; ++i)
@@ -2464,6 +2730,8 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     rc = finish_info(op, m, so, info, 1, accepted, s);
     }
   }
+  if (info && !lz_steps.empty())
+    for (int i = 0; i < m; ++i) info[i].iters += lz_steps[i];
   if (scaled) {
     note_launch();
     apply_rhs_scale<<<dim3(sblocks, m), 256, 0, s>>>(nullptr, w->x64, w->rscale, nullptr, 0, field, true);
@@ -2654,6 +2922,10 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
       gw->mixed_restart = ow->mixed_restart;
       gw->tc_unfused = ow->tc_unfused;
       gw->replace_delta = ow->replace_delta;
+      gw->cheb_bounds = ow->cheb_bounds;
+      gw->cheb_steps = ow->cheb_steps;
+      gw->cheb_widen = ow->cheb_widen;
+      gw->cheb_check = ow->cheb_check;
     }
     gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz; gop->bc_z = o->bc_z;
     gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
     right = rightn;
     czlast = czlastn;
   }
-  if (MODE != kStencilApply) {
+  if (MODE != kStencilApply && a.partial != nullptr) {  // uniform over the CTA
     const double s = block_sum((double)acc, red);
     if (threadIdx.x == 0)
       a.partial[(size_t)m * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = s;

@@ -1,0 +1,150 @@
+"""Chebyshev iteration (Eq. main-scheme) with the bounds of Eq. energy_rel
+estimated by Lanczos where the face-wise bounds degenerate, and with
+reduction-free steps between residual checks, through the C ABI.
+
+  - q = 0 on part of the domain (q_min = 0 < q_max): the face-wise gamma_1 is
+    0; the library's estimate (20 FP32 PCG steps, widened 5%) is within 2% of
+    the oracle's FP64 estimate (lanczos_bounds, the same steps in FP64) and
+    encloses the generalised spectrum of (A, B) on a grid small enough for
+    scipy.linalg.eigh;
+  - every Chebyshev method then meets 1e-8 in the oracle's FP64 true residual,
+    in at most 1.5 times the FP64 PCG iterations plus the 20 estimation steps;
+  - option cheb_bounds = 1 on a medium whose face-wise bounds are fine gives
+    the same tolerance;
+  - cheb_check = 4 (residual norm every 4th step): same tolerance, at most 3
+    more iterations than checking every step.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+import paper_1002_3094_gb300 as P  # noqa: E402
+from paper_1002_3094_gb300.inputs import sample_operator_inputs, sample_rhs  # noqa: E402
+from workloads import Medium, layered_inclusion_medium  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    P.load_library()
+    return torch.device("cuda:0")
+
+
+def _qzero_medium(n_rhs=2):
+    base = layered_inclusion_medium(n_rhs=n_rhs, nominal_n=64, instance=2)
+
+    def q(r, z):
+        return np.where(z < 0.45, 0.0, 2.0) + 0.0 * r
+
+    return Medium("qzero", base.kappa, q, base.sources)
+
+
+def _setup(med, nr, nz, dev):
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(dev) for x in (kr, kz, q)], nr, nz)
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
+    f = sample_rhs(med, nr, nz)
+    return op, ora, f
+
+
+def _residuals(ora, f, u):
+    out = []
+    for j in range(f.shape[0]):
+        phi = ora.phi(f[j])
+        out.append(np.linalg.norm(phi - ora.apply_A(u[j])) / np.linalg.norm(phi))
+    return np.array(out)
+
+
+def test_estimate_matches_oracle_and_encloses_spectrum(cuda):
+    nr, nz = 24, 20
+    op, ora, f = _setup(_qzero_medium(), nr, nz, cuda)
+    kt, qt, g1_face, g2_face = P.ax_operator_info(op)
+    assert g1_face == 0.0  # degenerate face-wise bound
+    fd = torch.from_numpy(f).to(cuda)
+    u = torch.zeros_like(fd)
+    st, info = P.ax_solve(op, fd, u, 2, 1e-8, 5000, P.AX_CHEB_FP64)
+    assert st == P.AX_OK
+    g1, g2, est = P.ax_chebyshev_bounds(op, 2)
+    assert est
+    A = ora.A.toarray()
+    B = O.assemble_preconditioner(ora.kappa_t, ora.q_t, ora.grid).toarray()
+    ev = scipy.linalg.eigh(A, B, eigvals_only=True)
+    og1, og2 = np.inf, 0.0
+    for j in range(2):
+        a, b, _, _ = O.lanczos_bounds(ora.apply_A, ora.apply_Binv, ora.phi(f[j]), steps=20, widen=0.05)
+        og1, og2 = min(og1, a), max(og2, b)
+    for j in range(2):
+        assert abs(g1[j] - og1) <= 0.02 * og1 and abs(g2[j] - og2) <= 0.02 * og2, (g1, g2, og1, og2)
+        assert 0.0 < g1[j] <= ev.min() * 1.01 and ev.max() <= g2[j] * 1.01
+    assert (_residuals(ora, f, u.cpu().numpy()) <= 1e-8).all()
+    P.ax_destroy_operator(op)
+
+
+@pytest.mark.parametrize("method", [P.AX_CHEB_FP64, P.AX_CHEB_MIXED])
+@pytest.mark.parametrize("nr,nz", [(64, 64), (200, 96)])
+def test_degenerate_q_chebyshev_converges(cuda, method, nr, nz):
+    op, ora, f = _setup(_qzero_medium(), nr, nz, cuda)
+    fd = torch.from_numpy(f).to(cuda)
+    u64 = torch.zeros_like(fd)
+    st, ip = P.ax_solve(op, fd, u64, 2, 1e-8, 5000, P.AX_PCG_FP64)
+    assert st == P.AX_OK
+    u = torch.zeros_like(fd)
+    st, ic = P.ax_solve(op, fd, u, 2, 1e-8, 5000, method)
+    torch.cuda.synchronize()
+    assert st == P.AX_OK, ic
+    assert (_residuals(ora, f, u.cpu().numpy()) <= 1e-8).all()
+    if method == P.AX_CHEB_FP64:
+        for j in range(2):
+            assert ic[j]["iters"] <= 1.5 * ip[j]["iters"] + 20, (ic[j], ip[j])
+    # a second solve reuses the cached estimate: no estimation steps
+    u2 = torch.zeros_like(fd)
+    st, ic2 = P.ax_solve(op, fd, u2, 2, 1e-8, 5000, method)
+    assert st == P.AX_OK
+    if method == P.AX_CHEB_FP64:
+        assert ic2[0]["iters"] < ic[0]["iters"]
+    P.ax_destroy_operator(op)
+
+
+def test_forced_estimate_on_regular_medium(cuda):
+    med = layered_inclusion_medium(n_rhs=2, nominal_n=96, instance=4)
+    op, ora, f = _setup(med, 96, 80, cuda)
+    assert P.ax_operator_info(op)[2] > 0.0
+    P.ax_set_option(op, "cheb_bounds", 1)
+    fd = torch.from_numpy(f).to(cuda)
+    u = torch.zeros_like(fd)
+    st, _ = P.ax_solve(op, fd, u, 2, 1e-8, 5000, P.AX_CHEB_FP64)
+    assert st == P.AX_OK
+    assert P.ax_chebyshev_bounds(op, 2)[2]
+    assert (_residuals(ora, f, u.cpu().numpy()) <= 1e-8).all()
+    P.ax_set_option(op, "cheb_bounds", 0)
+    assert not P.ax_chebyshev_bounds(op, 2)[2]
+    assert P.ax_set_option(op, "cheb_bounds", 2, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+    P.ax_destroy_operator(op)
+
+
+@pytest.mark.parametrize("method", [P.AX_CHEB_FP64, P.AX_CHEB_MIXED])
+def test_reduction_free_steps(cuda, method):
+    med = layered_inclusion_medium(n_rhs=3, nominal_n=128, instance=6)
+    op, ora, f = _setup(med, 128, 100, cuda)
+    fd = torch.from_numpy(f).to(cuda)
+    u1 = torch.zeros_like(fd)
+    st, i1 = P.ax_solve(op, fd, u1, 3, 1e-8, 5000, method)
+    assert st == P.AX_OK
+    P.ax_set_option(op, "cheb_check", 4)
+    u4 = torch.zeros_like(fd)
+    st, i4 = P.ax_solve(op, fd, u4, 3, 1e-8, 5000, method)
+    torch.cuda.synchronize()
+    assert st == P.AX_OK
+    assert (_residuals(ora, f, u4.cpu().numpy()) <= 1e-8).all()
+    if method == P.AX_CHEB_FP64:
+        for a, b in zip(i1, i4):
+            assert a["iters"] <= b["iters"] <= a["iters"] + 3, (a, b)
+    assert P.ax_set_option(op, "cheb_check", 0, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+    P.ax_destroy_operator(op)

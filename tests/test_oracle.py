@@ -219,6 +219,49 @@ def test_chebyshev_error_bound_each_step():
         assert anorm(u - y) <= bound * e0 * (1 + 1e-9) + 1e-14
 
 
+def test_lanczos_ritz_values_interlace_and_converge():
+    """The Lanczos tridiagonal of the PCG coefficients: its Ritz values lie
+    inside the spectrum of B^-1 A (the generalised eigenvalues of (A, B),
+    scipy.linalg.eigh) and its extreme ones reach the extreme eigenvalues."""
+    op, f = _op(6, 5, seed=3)
+    A = op.A.toarray()
+    B = O.assemble_preconditioner(op.kappa_t, op.q_t, op.grid).toarray()
+    ev = scipy.linalg.eigh(A, B, eigvals_only=True)
+    phi = op.phi(f[0])
+    for steps in (3, 6, 12, 24):
+        g1, g2, al, be = O.lanczos_bounds(op.apply_A, op.apply_Binv, phi, steps=steps, widen=0.0)
+        assert len(al) == steps and len(be) == steps
+        assert g1 >= ev.min() * (1 - 1e-10) and g2 <= ev.max() * (1 + 1e-10), steps
+    assert g1 <= ev.min() * (1 + 1e-6) and g2 >= ev.max() * (1 - 1e-6)
+
+
+@pytest.mark.parametrize("q_zero", [False, True])
+def test_lanczos_bounds_contain_spectrum_and_drive_chebyshev(q_zero):
+    """20 PCG steps, widened 5%, enclose the spectrum of B^-1 A on a 16 x 14
+    grid (10 steps leave the smallest Ritz value 6% above lambda_min here);
+    with q = 0 on part of the domain (q_min = 0 < q_max) the face-wise
+    gamma_1 is 0 (degenerate) while the estimate is not, and the Chebyshev
+    iteration with the estimate converges in at most 1.5 times the PCG
+    iterations (plus 4)."""
+    g = O.Grid(16, 14)
+    med = _random_medium(5)
+    if q_zero:
+        med = Medium("qzero", med.kappa, lambda r, z: np.where(z < 0.5, 0.0, 0.8) + 0 * r, med.sources)
+    kr, kz, q, f = O.sample_medium(med, g)
+    op = O.Operator(kr, kz, q, g)
+    A = op.A.toarray()
+    B = O.assemble_preconditioner(op.kappa_t, op.q_t, g).toarray()
+    ev = scipy.linalg.eigh(A, B, eigvals_only=True)
+    phi = op.phi(f[0])
+    g1, g2, _, _ = O.lanczos_bounds(op.apply_A, op.apply_Binv, phi, steps=20, widen=0.05)
+    assert 0.0 < g1 <= ev.min() and ev.max() <= g2
+    if q_zero:
+        assert op.gamma[0] == 0.0
+    _, ipcg = op.solve(f[0], tol=1e-10)
+    _, icheb = O.chebyshev(op.apply_A, op.apply_Binv, phi, g1, g2, tol=1e-10)
+    assert icheb.converged and icheb.iters <= 1.5 * ipcg.iters + 4, (icheb.iters, ipcg.iters)
+
+
 def test_chebyshev_agrees_with_pcg():
     g = O.Grid(64, 64)
     kr, kz, q, f = O.sample_medium(bumps_medium(), g)

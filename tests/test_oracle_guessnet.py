@@ -132,3 +132,119 @@ def test_h1_loss_closed_forms_and_finite_differences():
         om[idx] -= eps
         fd = (G.h1_loss(op, t, lam)[0] - G.h1_loss(om, t, lam)[0]) / (2 * eps)
         assert abs(fd - g[idx]) <= 1e-7 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------------------
+# Solver-side steps: lattice features, lift, Adam
+# ---------------------------------------------------------------------------
+import os  # noqa: E402
+
+import oracle as O  # noqa: E402
+
+
+def _golden_features():
+    cases = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "guess_features.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            c = cases.setdefault(parts[0], {"x": np.zeros((3, 2, 2)), "s": None})
+            if parts[1] == "SCALE":
+                c["s"] = float(parts[2])
+            else:
+                ch, py, px = map(int, parts[1:4])
+                c["x"][ch, py, px] = float(parts[4])
+    return cases
+
+
+def test_features_hand_worked_cases():
+    g = _golden_features()
+    i, k = np.meshgrid(np.arange(5), np.arange(3), indexing="ij")
+    x, s = G.features(np.exp(i - k), i * k, (i - 2.0) * (k + 1), 2)
+    np.testing.assert_allclose(x, g["A"]["x"], rtol=0, atol=1e-15)
+    assert s == g["A"]["s"]
+    i, k = np.meshgrid(np.arange(4), np.arange(2), indexing="ij")
+    x, s = G.features(np.exp(i + k), i * 1.0, i * (k + 1.0) - 1.0, 2)
+    np.testing.assert_allclose(x, g["B"]["x"], rtol=0, atol=1e-15)
+    assert s == g["B"]["s"]
+
+
+def test_features_identity_lattice_and_separable_log_mean():
+    rng = np.random.default_rng(2)
+    kap = np.exp(rng.normal(size=(8, 8)))
+    q = rng.uniform(size=(8, 8))
+    f = rng.normal(size=(8, 8))
+    x, s = G.features(kap, q, f, 8)            # lattice = grid: the samples themselves
+    assert s == np.abs(f).max()
+    np.testing.assert_allclose(x[0], np.log(kap), rtol=1e-15)
+    np.testing.assert_allclose(x[2] * s, f, rtol=1e-15)
+    # kappa = a(r) b(z): the cell mean of log kappa is mean log a + mean log b
+    a, b = np.exp(rng.normal(size=12)), np.exp(rng.normal(size=9))
+    x, _ = G.features(np.outer(a, b), np.ones((12, 9)), np.ones((12, 9)), 3)
+    ref = np.log(a).reshape(3, 4).mean(1)[:, None] + np.log(b).reshape(3, 3).mean(1)[None, :]
+    np.testing.assert_allclose(x[0], ref, rtol=1e-13)
+    assert np.allclose(x[1], 1.0) and np.allclose(x[2], 1.0)
+    # a zero right-hand side keeps s = 1
+    _, s0 = G.features(kap, q, np.zeros((8, 8)), 4)
+    assert s0 == 1.0
+
+
+def test_features_pre_is_the_preconditioned_rhs():
+    """Channel 2 holds g / s, g = B^-1 (r f): B g = phi with the dense
+    assembly of B (tiny grid, lattice = grid)."""
+    nr, nz = 6, 5
+    grid = O.Grid(nr, nz)
+    rng = np.random.default_rng(7)
+    kr = 1 + rng.uniform(size=(nr, nz))
+    kz = 1 + rng.uniform(size=(nr, nz + 1))
+    q = rng.uniform(size=(nr, nz))
+    f = rng.normal(size=(nr, nz))
+    op = O.Operator(kr, kz, q, grid)
+    x, s = G.features_pre(op, kr, q, f, 1)     # 1 x 1 lattice: the means over the grid
+    B = O.assemble_preconditioner(op.kappa_t, op.q_t, grid).toarray()
+    g = np.linalg.solve(B, op.phi(f).ravel()).reshape(nr, nz)
+    assert np.isclose(s, np.abs(g).max(), rtol=1e-12)
+    assert np.isclose(x[2, 0, 0], g.mean() / s, rtol=1e-10)
+    assert np.isclose(x[0, 0, 0], np.log(kr).mean(), rtol=1e-14)
+
+
+def test_lift_reproduces_affine_and_matches_scipy():
+    from scipy.interpolate import RegularGridInterpolator
+    hw, nr, nz, s = 8, 37, 50, 2.5
+    c = (np.arange(hw) + 0.5) / hw
+    y = 0.3 + 1.7 * c[:, None] - 0.9 * c[None, :]
+    u = G.bilinear_lift(y, s, nr, nz)
+    ny, nx = (np.arange(nr) + 0.5) / nr, (np.arange(nz) + 0.5) / nz
+    inner_r = (ny >= c[0]) & (ny <= c[-1])
+    inner_z = (nx >= c[0]) & (nx <= c[-1])
+    exact = s * (0.3 + 1.7 * ny[:, None] - 0.9 * nx[None, :])
+    np.testing.assert_allclose(u[np.ix_(inner_r, inner_z)], exact[np.ix_(inner_r, inner_z)], rtol=1e-12, atol=1e-14)
+    # any lattice values, against scipy with the coordinates clamped to the lattice
+    yr = np.random.default_rng(3).normal(size=(hw, hw))
+    u = G.bilinear_lift(yr, s, nr, nz)
+    rgi = RegularGridInterpolator((c, c), yr, method="linear")
+    pts = np.stack(np.meshgrid(np.clip(ny, c[0], c[-1]), np.clip(nx, c[0], c[-1]), indexing="ij"), -1)
+    np.testing.assert_allclose(u, s * rgi(pts), rtol=1e-12, atol=1e-14)
+    # lattice = grid: the values themselves
+    np.testing.assert_allclose(G.bilinear_lift(yr, s, hw, hw), s * yr, rtol=1e-15)
+
+
+def test_adam_matches_torch_and_first_step_closed_form():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    p0 = rng.normal(size=20)
+    grads = [rng.normal(size=20) for _ in range(3)]
+    lr = 3e-3
+    # first step: mhat = g, vhat = g^2, so the update is lr g / (|g| + eps)
+    p1, _, _ = G.adam_step(p0, grads[0], np.zeros(20), np.zeros(20), 1, lr)
+    np.testing.assert_allclose(p1, p0 - lr * grads[0] / (np.abs(grads[0]) + 1e-8), rtol=1e-14)
+    t = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros(20), np.zeros(20)
+    for step, g in enumerate(grads, start=1):
+        opt.zero_grad()
+        t.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        p, m, v = G.adam_step(p, g, m, v, step, lr)
+        np.testing.assert_allclose(p, t.detach().numpy(), rtol=1e-13, atol=1e-15)
