@@ -139,6 +139,8 @@ def parse_args():
                     help="FP32 path transform along z: -1 the library's choice, 0 FFT, 1 tensor-core GEMM "
                          "by S_hi + S_lo, 2 tensor-core GEMM by S_hi (option dst_tensor)")
     ap.add_argument("--harmonics", type=int, default=2000, help="laguerre_chain: number of harmonics")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default transform and mode-solve kernel (no ax_autotune)")
     ap.add_argument("--mode-kernel", type=int, default=0,
                     help="FP32 mode-solve kernel variant (option mode_kernel; 0 the library's choice)")
     ap.add_argument("--replace-delta", type=float, default=0.0,
@@ -404,6 +406,11 @@ def run_batched(args):
     batch = P.ax_batch_create(ops)
     method = P.METHODS[args.method]
     stream = torch.cuda.current_stream()
+    tune_s = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        P.ax_batch_autotune(batch, 5, stream=stream)
+        tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         st, info = P.ax_batch_solve(batch, fs, us, TOL, 20000, method, stream=stream, raise_on_error=False)
         if st != P.AX_OK:
@@ -437,18 +444,44 @@ def run_batched(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     value = unknowns * args.steps / (ms / 1e3)
+    launches = P.ax_kernel_launches() - launches0
+    # the plain FP64 PCG on the same batch (the comparator of the metric)
+    plain = None
+    if args.plain_steps > 0 and method != P.AX_PCG_FP64:
+        u64 = [torch.zeros_like(u_) for u_ in us]
+        P.ax_batch_solve(batch, fs, u64, TOL, 20000, P.AX_PCG_FP64, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.plain_steps):
+            _, pinfo = P.ax_batch_solve(batch, fs, u64, TOL, 20000, P.AX_PCG_FP64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / args.plain_steps
+        plat, _ = P.ax_batch_latency(batch, len(ops))
+        diff = max(float(torch.linalg.vector_norm(a - b_) / torch.linalg.vector_norm(b_)) for a, b_ in zip(us, u64))
+        plain = {"value": unknowns / (pms / 1e3), "ms_per_step": pms,
+                 "iters_max": max(i["iters"] for i in pinfo),
+                 "latency_ms": {"p50": float(np.percentile(plat, 50)), "p99": float(np.percentile(plat, 99))},
+                 "max_rel_diff_to_chosen": diff}
+        del u64
+    tuned = [P.ax_batch_config(batch, g) for g in range(groups)]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64",
             "data": "synthetic",
             "config": {"workload": "batched_256", "instances": len(ops), "unknowns": unknowns, "groups": groups,
                        "bc_z": args.bc_z,
-                       "method": args.method, "tol": TOL},
+                       "method": args.method, "tol": TOL, "autotuned": not args.no_autotune},
             "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
-                           "max": float(max(lats))},
-            "iters": {"max": max(i["iters"] for i in info), "min": min(i["iters"] for i in info)},
+                           "max": float(max(lats)), "min": float(min(lats)),
+                           "meaning": "per instance: batch start to the graph replay in which it converged"},
+            "iters": {"max": max(i["iters"] for i in info), "min": min(i["iters"] for i in info),
+                      "mean": float(np.mean([i["iters"] for i in info]))},
             "max_rel_res": max(i["rel_res"] for i in info),
-            "gpu_launches": P.ax_kernel_launches() - launches0, "clocks": clk}
+            "plain_fp64": plain, "vs_plain_fp64": (value / plain["value"]) if plain else None,
+            "autotune_s": tune_s, "tuned_groups": tuned,
+            "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line))
     P.ax_batch_destroy(batch)
     for op in ops:
@@ -636,6 +669,12 @@ def main():
         P.ax_set_option(op, "replace_delta", args.replace_delta)
     if args.mode_kernel > 0:
         P.ax_set_option(op, "mode_kernel", args.mode_kernel)
+    tuned = None
+    if not args.no_autotune and args.dst_tensor < 0 and args.mode_kernel == 0 and "mixed" in args.method:
+        t0 = time.perf_counter()
+        P.ax_autotune(op, m, 5)
+        tuned = {"dst_tensor": int(P.ax_get_option(op, "dst_tensor")),
+                 "mode_kernel": int(P.ax_get_option(op, "mode_kernel")), "autotune_s": time.perf_counter() - t0}
     f_host = sample_rhs(med, nr, nz, bc_z=args.bc_z)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)
@@ -797,7 +836,7 @@ def main():
             "max_rel_res": rel,
             "plain_fp64": plain,
             "vs_plain_fp64": (value / plain["value"]) if plain else None,
-            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "autotuned": tuned,
             "kernel_ms_profiled_solve": kernel_ms, "cpu_baseline": cpu,
         }
         print(json.dumps(line))

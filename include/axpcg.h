@@ -136,6 +136,24 @@ int ax_destroy_operator(ax_operator *op);
 int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
                      double *gamma1, double *gamma2);
 
+/* Reads an option of ax_set_option (and the ones the autotuner sets:
+ * "dst_tensor", "mode_kernel"); unknown names: AX_ERR_INVALID_ARG. */
+int ax_get_option(const ax_operator *op, const char *name, double *value);
+
+/* Autotuner (the paper has no counterpart; its workloads ran one fixed code).
+ * Times `reps` FP32 PCG iterations (those of AX_PCG_MIXED) on m right-hand
+ * sides of the operator's own grid for every candidate: the FFT
+ * transform, or the tensor-core transform (nz <= 4096) with each FP32
+ * mode-solve kernel covering nr, and sets "dst_tensor" and "mode_kernel" to
+ * the fastest.  Choices are cached per process by (device name, nr, nz, bc_z,
+ * m rounded up to a power of two) and, when the environment variable
+ * AX_TUNE_CACHE names a file, in that file across processes.  Synchronises
+ * `stream`; uses the operator's workspace (not concurrently with a solve on
+ * it).  Errors: AX_ERR_INVALID_ARG (reps outside 1..1000), AX_ERR_OOM,
+ * AX_ERR_CUDA, AX_ERR_TIMEOUT (a bounded wait of the tensor-core transform
+ * expired; the previous configuration is kept). */
+int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream);
+
 /* The Chebyshev bounds (gamma_1, gamma_2 of Eq. energy_rel) that a solve of m
  * right-hand sides uses, per right-hand side (host arrays [m]): the Lanczos
  * estimate of option "cheb_bounds" where it applies and has been formed (by
@@ -231,14 +249,22 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
  * every method of ax_solve (the Chebyshev methods with each instance's own
  * gamma bounds, hence its own tau_0 and rho_0); info is a host array [n]
  * (may be NULL).  Blocks until all groups are done.
- * ax_batch_latency: per-instance wall time (ms) from the start of the last
- * ax_batch_solve to the completion of the instance's group; *groups = count.
+ * ax_batch_latency: per-instance time (ms) from the start of the last
+ * ax_batch_solve until the host saw that instance's solve finish (its group's
+ * states are read after every graph replay of iterations, so the resolution
+ * is one replay); *groups = count.
+ * ax_batch_autotune: ax_autotune on every group (m = its instances).
+ * ax_batch_config: grid, instance count and the transform / mode-solve kernel
+ * (ax_get_option names) that group `group` (0 .. groups-1) uses.
  * ax_solve_batched = create + solve + destroy. */
 typedef struct ax_batch ax_batch;
 int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch **out);
 int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double tol, int32_t max_iter,
                    int32_t method, int32_t flags, ax_solve_info *info, void *stream);
 int ax_batch_latency(const ax_batch *b, double *ms, int32_t *groups);
+int ax_batch_autotune(ax_batch *b, int32_t reps, void *stream);
+int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, int32_t *members, int32_t *dst_tensor,
+                    int32_t *mode_kernel);
 int ax_batch_destroy(ax_batch *b);
 int ax_solve_batched(ax_operator *const *ops, const double *const *f, double *const *u, int32_t n, double tol,
                      int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);

@@ -48,7 +48,8 @@ EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_
             "ax_guessnet_create", "ax_guessnet_destroy", "ax_guessnet_num_params", "ax_guessnet_get_params",
             "ax_guessnet_set_params", "ax_guessnet_forward", "ax_guessnet_gradients", "ax_guessnet_train_step",
             "ax_guessnet_save", "ax_guessnet_load", "ax_guessnet_features", "ax_guessnet_lift",
-            "ax_guessnet_set_loss", "ax_guessnet_features_pre", "ax_chebyshev_bounds")
+            "ax_guessnet_set_loss", "ax_guessnet_features_pre", "ax_chebyshev_bounds", "ax_get_option",
+            "ax_autotune", "ax_batch_autotune", "ax_batch_config")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "pcg_update": 6, "other": 7}
@@ -127,6 +128,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_kernel_launches.restype = ctypes.c_int64
     lib.ax_profile_read.argtypes = [vp, i32] + [ctypes.POINTER(dbl)] * 3
     lib.ax_chebyshev_bounds.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i32)]
+    lib.ax_get_option.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dbl)]
+    lib.ax_autotune.argtypes = [vp, i32, i32, vp]
+    lib.ax_batch_autotune.argtypes = [vp, i32, vp]
+    lib.ax_batch_config.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 5
     for name in EXPORTED:
         if name not in ("ax_status_string", "ax_version", "ax_kernel_launches", "ax_last_error",
                         "ax_guessnet_num_params"):
@@ -207,6 +212,26 @@ def ax_chebyshev_bounds(op: int, m: int):
     _check(load_library().ax_chebyshev_bounds(op, m, g1.ctypes.data, g2.ctypes.data, ctypes.byref(est)),
            "ax_chebyshev_bounds")
     return g1, g2, bool(est.value)
+
+
+def ax_get_option(op: int, name: str) -> float:
+    v = ctypes.c_double()
+    _check(load_library().ax_get_option(op, name.encode(), ctypes.byref(v)), f"ax_get_option({name})")
+    return v.value
+
+
+def ax_autotune(op: int, m: int, reps: int = 5, stream=None) -> None:
+    _check(load_library().ax_autotune(op, m, reps, _stream(stream)), "ax_autotune")
+
+
+def ax_batch_autotune(batch: int, reps: int = 5, stream=None) -> None:
+    _check(load_library().ax_batch_autotune(batch, reps, _stream(stream)), "ax_batch_autotune")
+
+
+def ax_batch_config(batch: int, group: int) -> dict:
+    vals = [ctypes.c_int32() for _ in range(5)]
+    _check(load_library().ax_batch_config(batch, group, *[ctypes.byref(v) for v in vals]), "ax_batch_config")
+    return dict(zip(("nr", "nz", "members", "dst_tensor", "mode_kernel"), (v.value for v in vals)))
 
 
 def ax_set_option(op: int, name: str, value: float, raise_on_error: bool = True) -> int:

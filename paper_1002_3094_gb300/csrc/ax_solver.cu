@@ -25,6 +25,9 @@
 #include <cstring>
 #include <algorithm>
 #include <mutex>
+#include <chrono>
+#include <map>
+#include <string>
 #include <vector>
 
 #include "ax_common.cuh"
@@ -84,6 +87,12 @@ struct Workspace {
   int cheb_steps = 20;          // PCG steps of the Lanczos estimate
   double cheb_widen = 0.05;     // relative widening of the estimated bounds
   int cheb_check = 1;           // Chebyshev: residual norm (a reduction) every cheb_check-th step
+  // per right-hand-side completion times (ms since lat_t0) of the current
+  // solve, taken when the host reads the states after each graph replay
+  // (resolution: one replay); set by the batched solve, -1 = not finished
+  bool lat_track = false;
+  std::chrono::steady_clock::time_point lat_t0;
+  std::vector<double> lat_ms;
   // per-launch profiler (off by default; graphs are not used while it is on)
   bool profile = false;
   std::vector<ProfEvent> prof_events;
@@ -1439,6 +1448,16 @@ int read_states(Workspace *w, const RhsState *dev, int m, cudaStream_t s, RhsSta
   return AX_OK;
 }
 
+// Completion times: right-hand sides whose top-level state (just read into h)
+// is final get the current time, once.
+void lat_mark(Workspace *w, const RhsState *h, int m) {
+  if (!w->lat_track) return;
+  if ((int)w->lat_ms.size() < m) w->lat_ms.resize(m, -1.0);
+  const double now = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w->lat_t0).count();
+  for (int i = 0; i < m; ++i)
+    if (w->lat_ms[i] < 0.0 && (h[i].state == kDone || h[i].state == kFailed)) w->lat_ms[i] = now;
+}
+
 // Runs `iters` captured iterations of `body` on stream s (graph cached by key).
 template <typename F>
 int run_graph(Workspace *w, GraphCache &g, int key, cudaStream_t s, F body) {
@@ -1537,6 +1556,7 @@ int pcg_loop(ax_operator *op, int m, const PcgVecs<T> &v, const T *phi, RhsState
     }
     if (rc != AX_OK) return rc;
     if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    if (true_check) lat_mark(w, h, m);
     if (!any_state(h, m, kActive) && !any_state(h, m, kCheck)) break;
   }
   return AX_OK;
@@ -1785,6 +1805,7 @@ int cheb_loop(ax_operator *op, int m, const ChebVecs<T> &v, RhsState *st, GraphC
     if (rc != AX_OK) return rc;
     RhsState *h = w->h_st;
     if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    if (apriori_eta == 0.0) lat_mark(w, h, m);  // the top-level Chebyshev (not an inner solve)
     if (!any_state(h, m, kActive)) break;
   }
   return AX_OK;
@@ -1965,6 +1986,7 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     }
     if (rc != AX_OK) return rc;
     if ((rc = read_states(w, st, m, s, h)) != AX_OK) return rc;
+    lat_mark(w, h, m);
     if (!any_state(h, m, kActive) && !any_state(h, m, kCheck)) break;
   }
   // the iterate back in FP64
@@ -2040,6 +2062,189 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t, double
   if (q_t) *q_t = op->q_t;
   if (gamma1) *gamma1 = op->gamma1;
   if (gamma2) *gamma2 = op->gamma2;
+  return AX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner.  For an operator's grid shape and a number of right-hand sides
+// it times FP32 PCG iterations (those of the mixed method: stencil, vector
+// updates, z-transforms, mode solves, scalars) for every candidate
+// configuration, on the operator's own tables, and keeps the fastest: the FFT transform (dst_tensor 0), or the tensor-core transform
+// (dst_tensor 1, nz <= 4096) with each FP32 mode-solve kernel that covers nr
+// (mode_kernel: the staged register kernel or a pipelined column-tile
+// kernel of its tile width and CTA size).  Choices are cached per process by
+// (device name, nr, nz, bc_z, right-hand sides rounded up to a power of two)
+// and, if the environment variable AX_TUNE_CACHE names a file, kept there
+// across processes (one line per entry: the key fields, the transform and the
+// kernel, the time in ms).
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneChoice { int dst = 0, variant = 0; double ms = 0.0; };
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const ax_operator *op, int m) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, op->device);
+  int mb = 1;
+  while (mb < m) mb <<= 1;
+  std::string name = prop.name;
+  for (char &c : name)
+    if (c == ' ' || c == '|') c = '_';
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d", name.c_str(), op->nr, op->nz, op->bc_z, mb);
+  return buf;
+}
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = std::getenv("AX_TUNE_CACHE");
+  if (!path) return;
+  FILE *fp = fopen(path, "r");
+  if (!fp) return;
+  char key[200];
+  TuneChoice c;
+  while (fscanf(fp, "%199s %d %d %lf", key, &c.dst, &c.variant, &c.ms) == 4) g_tune[key] = c;
+  fclose(fp);
+}
+
+void tune_save() {
+  const char *path = std::getenv("AX_TUNE_CACHE");
+  if (!path) return;
+  FILE *fp = fopen(path, "w");
+  if (!fp) return;
+  for (auto &e : g_tune) fprintf(fp, "%s %d %d %.6f\n", e.first.c_str(), e.second.dst, e.second.variant, e.second.ms);
+  fclose(fp);
+}
+
+void apply_choice(ax_operator *op, const TuneChoice &c) {
+  op->dst_tc = c.dst;
+  op->tri_variant = c.variant;
+  Workspace *w = op->ws;
+  free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+}
+}  // namespace
+
+extern "C" {
+
+int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
+  if (!op || m < 1 || reps < 1 || reps > 1000) return AX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = tune_key(op, m);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      apply_choice(op, it->second);
+      return AX_OK;
+    }
+  }
+  Workspace *w = op->ws;
+  int rc;
+  if ((rc = ensure_base(op, m)) != AX_OK) return rc;
+  if ((rc = ensure_vec32(op, m, false)) != AX_OK) return rc;
+  std::vector<TuneChoice> cand;
+  cand.push_back({0, 0});
+  if (op->nz <= kMaxTcN) {
+    int ids[16];
+    const int n = tridiag_variants(op->nr, ids);
+    if (n == 0) cand.push_back({1, 0});
+    for (int i = 0; i < n; ++i) cand.push_back({1, ids[i]});
+    if ((rc = ensure_split(op, (size_t)m * split_geom(op, op->nr).bytes_per_rhs)) != AX_OK) return rc;
+    const bool cz = op->bc_z == 1;
+    if (!tc_table(op->device, op->nz, cz ? kTableCosForward : kTableSine) ||
+        !tc_table(op->device, op->nz, cz ? kTableCosInverse : kTableSine) || !tc_flag(op->device))
+      return AX_ERR_OOM;
+  }
+  const TuneChoice saved{op->dst_tc, op->tri_variant, 0.0};
+  const size_t n = field_elems(op) * m;
+  cudaEvent_t e0, e1;
+  AX_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return AX_ERR_CUDA;
+  }
+  // Each candidate runs 2 + reps FP32 PCG iterations (the mixed method's
+  // iteration, fused as the solve would run it) on A x = r from x = 0 with
+  // r = 0.747 in every element; the last reps are timed.
+  PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
+  std::vector<RhsState> init(m);
+  for (int i = 0; i < m; ++i) {
+    std::memset(&init[i], 0, sizeof(RhsState));
+    init[i].state = kActive;
+    init[i].max_iter = 1 << 30;
+    init[i].thresh2 = -1.0;
+    init[i].bb = 1.0;
+  }
+  TuneChoice best;
+  best.ms = -1.0;
+  for (TuneChoice &c : cand) {
+    apply_choice(op, c);
+    const bool fused = tc_fused(op);
+    AX_TRY(cudaMemsetAsync(w->r32, 0x3f, sizeof(float) * n, s));  // 0x3f3f3f3f: 0.747
+    AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * n, s));
+    AX_TRY(cudaMemsetAsync(v.pa, 0, sizeof(float) * n, s));
+    AX_TRY(cudaMemcpyAsync(w->st, init.data(), sizeof(RhsState) * m, cudaMemcpyHostToDevice, s));
+    precond_apply<float>(op, m, v.r, v.z, w->st, kActive, part_ptr(w, kPartC), s, v.q);
+    note_launch();
+    sc_rho_init<<<m, 32, 0, s>>>(w->st, part_ptr(w, kPartC), precond_partials<float>(op, m), kActive);
+    if (fused) AX_TRY(cudaMemcpyAsync(v.pb, v.z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < 2; ++i) pcg_iteration<float>(op, m, v, w->st, w, kDone, s, 0.0, fused);
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i) pcg_iteration<float>(op, m, v, w->st, w, kDone, s, 0.0, fused);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c.ms = ms / reps;
+    if (best.ms < 0.0 || c.ms < best.ms) best = c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || best.ms < 0.0) {
+    apply_choice(op, saved);
+    return e != cudaSuccess ? status_from_cuda(e) : AX_ERR_CUDA;
+  }
+  int *flag = tc_flag(op->device), hf = 0;
+  if (flag) {  // a bounded wait of a tensor-core transform expired while timing
+    AX_TRY(cudaMemcpy(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hf) {
+      cudaMemset(flag, 0, sizeof(int));
+      apply_choice(op, saved);
+      return AX_ERR_TIMEOUT;
+    }
+  }
+  apply_choice(op, best);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  tune_save();
+  return AX_OK;
+}
+
+int ax_get_option(const ax_operator *op, const char *name, double *value) {
+  if (!op || !name || !value) return AX_ERR_INVALID_ARG;
+  const Workspace *w = op->ws;
+  if (!strcmp(name, "dst_tensor")) *value = op->dst_tc;
+  else if (!strcmp(name, "mode_kernel")) *value = op->tri_variant;
+  else if (!strcmp(name, "inner_tol")) *value = w->inner_tol;
+  else if (!strcmp(name, "inner_max_iter")) *value = w->inner_max;
+  else if (!strcmp(name, "graph_iters")) *value = w->graph_iters;
+  else if (!strcmp(name, "max_outer")) *value = w->max_outer;
+  else if (!strcmp(name, "replace_delta")) *value = w->replace_delta;
+  else if (!strcmp(name, "mixed_restart")) *value = w->mixed_restart;
+  else if (!strcmp(name, "tc_fused")) *value = w->tc_unfused ? 0 : 1;
+  else if (!strcmp(name, "cheb_bounds")) *value = w->cheb_bounds;
+  else if (!strcmp(name, "cheb_steps")) *value = w->cheb_steps;
+  else if (!strcmp(name, "cheb_widen")) *value = w->cheb_widen;
+  else if (!strcmp(name, "cheb_check")) *value = w->cheb_check;
+  else if (!strcmp(name, "profile")) *value = w->profile ? 1 : 0;
+  else return AX_ERR_INVALID_ARG;
   return AX_OK;
 }
 
@@ -2708,6 +2913,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
       AX_CHECK_LAUNCH();
       RhsState *h = w->h_st;
       if ((rc = read_states(w, so, m, s, h)) != AX_OK) return rc;
+      lat_mark(w, h, m);
       if (!any_state(h, m, kActive) || outer == w->max_outer) break;
       AX_TRY(cudaMemsetAsync(w->x32, 0, field * m * sizeof(float), s));
       if (!cheb) {
@@ -2997,14 +3203,22 @@ int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double
                         g.stream);
     }
     ginfo[gi].resize(m);
+    Workspace *gw = g.gop->ws;
+    gw->lat_track = true;
+    gw->lat_t0 = t0;
+    gw->lat_ms.assign(m, -1.0);
     status[gi] = ax_solve(g.gop, g.f_stack, g.u_stack, m, tol, max_iter, method, flags & ~AX_FLAG_SERIAL_GROUPS,
                           ginfo[gi].data(), g.stream);
+    gw->lat_track = false;
     for (int k = 0; k < m; ++k)
       cudaMemcpyAsync(u[g.members[k]], g.u_stack + k * per, per * sizeof(double), cudaMemcpyDeviceToDevice, g.stream);
     cudaEventRecord(g.done, g.stream);
     cudaStreamSynchronize(g.stream);
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    for (int k = 0; k < m; ++k) b->latency_ms[g.members[k]] = ms;
+    for (int k = 0; k < m; ++k) {
+      const double own = k < (int)gw->lat_ms.size() ? gw->lat_ms[k] : -1.0;
+      b->latency_ms[g.members[k]] = own >= 0.0 ? own : ms;
+    }
   };
   if (flags & AX_FLAG_SERIAL_GROUPS) {
     for (size_t gi = 0; gi < b->groups.size(); ++gi) run(gi);
@@ -3024,6 +3238,28 @@ int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double
   }
   if (cudaGetLastError() != cudaSuccess) return AX_ERR_CUDA;
   return worst;
+}
+
+int ax_batch_autotune(ax_batch *b, int32_t reps, void *stream) {
+  if (!b) return AX_ERR_INVALID_ARG;
+  for (auto &g : b->groups) {
+    const int rc = ax_autotune(g.gop, (int)g.members.size(), reps, stream);
+    if (rc != AX_OK) return rc;
+  }
+  return AX_OK;
+}
+
+int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, int32_t *members, int32_t *dst_tensor,
+                    int32_t *mode_kernel) {
+  if (!b || group < 0 || group >= (int)b->groups.size()) return AX_ERR_INVALID_ARG;
+  const ax::BatchGroup &g = b->groups[group];
+  if (nr) *nr = g.gop->nr;
+  if (nz) *nz = g.gop->nz;
+  if (members) *members = (int32_t)g.members.size();
+  if (dst_tensor) *dst_tensor = g.gop->dst_tc;
+  if (mode_kernel) *mode_kernel = ax::tridiag_effective(g.gop->nr, g.gop->tri_variant, (int)g.members.size(),
+                                                         g.gop->c32.IPS != nullptr);
+  return AX_OK;
 }
 
 int ax_batch_latency(const ax_batch *b, double *ms, int32_t *groups) {
