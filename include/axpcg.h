@@ -228,9 +228,10 @@ int ax_set_option(ax_operator *op, const char *name, double value);
  * u : [m][nr][nz] out: solution; in: guess if AX_FLAG_USE_GUESS
  * Each right-hand side stops when its FP64 true residual satisfies
  * ||phi - A u||_2 <= tol ||phi||_2, or fails after max_iter iterations.
- * The mixed methods solve A (sigma u) = sigma phi with sigma the power of two
- * nearest 1 / rms(phi) per right-hand side (exact in FP64), so their FP32 inner
- * iteration does not depend on the units of f.
+ * The mixed methods solve A (sigma u) = sigma phi with sigma = 2^-e per
+ * right-hand side, max |phi| = f 2^e with 1/2 <= f < 1 (exact in FP64, and no
+ * square of phi is formed before the scaling), so their FP32 inner iteration
+ * does not depend on the units of f anywhere in the FP64 range.
  * info : host array [m] (may be NULL).  Returns the worst per-RHS status. */
 int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
              int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);
@@ -382,10 +383,12 @@ int ax_apply_preconditioner_noalloc(ax_operator *op, const double *in, double *o
  *   T <- T + w_m Q_m   (T = sum_{k<=m} w_k Q_k),   S <- S + T   (S = S_{m+1})
  * and writes the right-hand side of harmonic m + 1:
  *   f_out = f_next src - c2 a_next S,   (w_m, a_next, f_next: host scalars).
- * T and S start at zero (harmonic 0 has f = f_0 src).  Q, T, S, c2, src and
- * f_out are dense FP64 device arrays [nr][nz] of op's grid (caller-owned; f_out
- * must not overlap the others).  Errors: AX_ERR_INVALID_ARG for a null
- * pointer or a non-finite scalar; AX_ERR_CUDA if the launch fails. */
+ * T and S start at zero (harmonic 0 has f = f_0 src: call with Q = NULL and
+ * w_m = 0).  Q, T, S, c2, src and f_out are dense FP64 device arrays [nr][nz]
+ * of op's grid (caller-owned; T, S and f_out are written and must not overlap
+ * each other or the inputs).  Errors: AX_ERR_INVALID_ARG for a null pointer
+ * (Q only with w_m = 0), Q equal to T, S or f_out, or a non-finite scalar;
+ * AX_ERR_CUDA if the launch fails. */
 int ax_laguerre_step(ax_operator *op, const double *Q, double *T, double *S, const double *c2,
                      const double *src, double w_m, double a_next, double f_next, double *f_out,
                      void *stream);

@@ -24,11 +24,13 @@
 namespace ax {
 namespace {
 
-__global__ void laguerre_step_kernel(const double *__restrict__ Q, double *__restrict__ T, double *__restrict__ S,
+// Q may be null (then w_m is 0 and Q is not read: harmonic 0 has no solved
+// field to add).
+__global__ void laguerre_step_kernel(const double *Q, double *__restrict__ T, double *__restrict__ S,
                                      const double *__restrict__ c2, const double *__restrict__ src, double w_m,
                                      double a_next, double f_next, double *__restrict__ f_out, size_t n) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const double t = fma(w_m, Q[e], T[e]);
+    const double t = Q ? fma(w_m, Q[e], T[e]) : T[e];
     const double s = S[e] + t;
     T[e] = t;
     S[e] = s;
@@ -42,8 +44,10 @@ __global__ void laguerre_step_kernel(const double *__restrict__ Q, double *__res
 extern "C" int ax_laguerre_step(ax_operator *op, const double *Q, double *T, double *S, const double *c2,
                                 const double *src, double w_m, double a_next, double f_next, double *f_out,
                                 void *stream) {
-  if (!op || !Q || !T || !S || !c2 || !src || !f_out) return AX_ERR_INVALID_ARG;
+  if (!op || !T || !S || !c2 || !src || !f_out) return AX_ERR_INVALID_ARG;
   if (!std::isfinite(w_m) || !std::isfinite(a_next) || !std::isfinite(f_next)) return AX_ERR_INVALID_ARG;
+  if (!Q && w_m != 0.0) return AX_ERR_INVALID_ARG;
+  if (Q && (Q == T || Q == S || Q == f_out)) return AX_ERR_INVALID_ARG;  // T, S, f_out are written
   const size_t n = (size_t)op->nr * op->nz;
   const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 8);
   ax::note_launch();

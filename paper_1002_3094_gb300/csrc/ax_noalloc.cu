@@ -18,8 +18,9 @@
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before any stream capture begins.  Later calls only queue kernels.
 //  * All calls share the one array, and it keeps the last call's contents.
-//    Nothing here reads the array before writing it (each call writes every
-//    element it later reads), so no clearing is needed.  Two calls whose work
+//    Each call writes every element it later reads (the packing pass also
+//    zeroes the padding columns of both halves), so no clearing is needed.
+//    Two calls whose work
 //    overlaps on the GPU (different streams, no ordering between them) race
 //    on the array and corrupt each other's results: order them.
 #include <cmath>
@@ -56,11 +57,18 @@ int noalloc_scratch(void **out) {
   return AX_OK;
 }
 
+// Packs the dense input rows into the padded layout of the first half and
+// zeroes the padding columns nz .. pitch-1 of both halves: the transforms'
+// vector loads cover those columns, and the array keeps the previous call's
+// contents.
 template <typename T>
-__global__ void noalloc_pack(const double *__restrict__ src, T *__restrict__ dst, long long rows, int nz,
-                             int pitch) {
+__global__ void noalloc_pack(const double *__restrict__ src, T *__restrict__ dst, T *__restrict__ dst2,
+                             long long rows, int nz, int pitch) {
   for (long long row = blockIdx.x; row < rows; row += gridDim.x)
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) dst[row * pitch + k] = (T)src[row * nz + k];
+    for (int k = threadIdx.x; k < pitch; k += blockDim.x) {
+      dst[row * pitch + k] = k < nz ? (T)src[row * nz + k] : T(0);
+      if (k >= nz) dst2[row * pitch + k] = T(0);
+    }
 }
 
 template <typename T>
@@ -89,7 +97,7 @@ int precond_noalloc(ax_operator *op, const double *in, double *out, int m, cudaS
   const int blocks = (int)(rows < 65535 ? rows : 65535);
 
   note_launch();
-  noalloc_pack<T><<<blocks, 256, 0, s>>>(in, a, rows, op->nz, op->pitch);
+  noalloc_pack<T><<<blocks, 256, 0, s>>>(in, a, b, rows, op->nz, op->pitch);
 
   DstArgs<T> d{};
   d.TW = c.TW;

@@ -347,14 +347,38 @@ __global__ void padded_to_dense(const T *__restrict__ src, double *__restrict__ 
 // the ||phi||^2 partials, so that the FP32 inner iteration works on values of
 // order one whatever the units of f (FP32 squares of residuals near 1e-20
 // would underflow).  A power of two scales FP64 values exactly.
-__global__ void rhs_scale(double *scale, const double *part, int nb, int m, double count) {
+// sigma = 2^-e with max |phi| = f 2^e, 1/2 <= f < 1 (frexp): the scaled
+// right-hand side has its largest magnitude in [1/2, 1) for any finite
+// nonzero phi of FP64 (no square is formed, so nothing overflows or
+// underflows on the way); 1 for phi = 0 or non-finite phi.  pmax holds the
+// per-CTA maxima of |phi| (nb per right-hand side).
+__global__ void rhs_scale(double *scale, const double *pmax, int nb, int m) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  double ss = 0.0;
-  for (int b = 0; b < nb; ++b) ss += part[(size_t)j * kPartialStride + b];
+  double mx = 0.0;
+  for (int b = 0; b < nb; ++b) mx = fmax(mx, pmax[(size_t)j * kPartialStride + b]);
   double sc = 1.0;
-  if (ss > 0.0 && isfinite(ss)) sc = ldexp(1.0, -(int)lrint(0.5 * log2(ss / count)));
+  if (mx > 0.0 && isfinite(mx)) {
+    int e = 0;
+    frexp(mx, &e);
+    sc = ldexp(1.0, -e);
+  }
   scale[j] = sc;
+}
+
+// Per-CTA partials of ||phi||^2 in the block structure of prep_rhs (grid
+// (m, ceil(nr / 16)), 256 threads), for the scaled right-hand side.
+__global__ void phi_norm2(const double *__restrict__ phi, int nr, int nz, int pitch, double *__restrict__ part) {
+  __shared__ double red[8];
+  const int m = blockIdx.x;
+  const int i0 = blockIdx.y * 16, i1 = min(i0 + 16, nr);
+  double acc = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double *pr = phi + ((size_t)m * nr + i) * pitch;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) acc = fma(pr[k], pr[k], acc);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[(size_t)m * kPartialStride + blockIdx.y] = s;
 }
 
 // phi *= sigma and x *= sigma (x may be null) with the ||phi||^2 partials *=
@@ -372,14 +396,15 @@ __global__ void apply_rhs_scale(double *phi, double *x, const double *scale, dou
     for (int k = threadIdx.x; k < nb; k += blockDim.x) part[(size_t)m * kPartialStride + k] *= sc * sc;
 }
 
-// phi = r_i f (Eq. diff_approx1), FP64, plus per-CTA partials of ||phi||^2.
-// grid (m, ceil(nr / 16)), 256 threads.
+// phi = r_i f (Eq. diff_approx1), FP64, plus per-CTA partials of ||phi||^2
+// (part) and of max |phi| (pmax).  grid (m, ceil(nr / 16)), 256 threads.
 __global__ void prep_rhs(const double *__restrict__ f, double *__restrict__ phi, const double *__restrict__ R,
-                         int nr, int nz, int pitch, double *__restrict__ part) {
+                         int nr, int nz, int pitch, double *__restrict__ part, double *__restrict__ pmax) {
   __shared__ double red[8];
+  __shared__ double redm[8];
   const int m = blockIdx.x;
   const int i0 = blockIdx.y * 16, i1 = min(i0 + 16, nr);
-  double acc = 0.0;
+  double acc = 0.0, mx = 0.0;
   for (int i = i0; i < i1; ++i) {
     const double ri = R[i];
     const double *fr = f + ((size_t)m * nr + i) * nz;
@@ -388,10 +413,21 @@ __global__ void prep_rhs(const double *__restrict__ f, double *__restrict__ phi,
       const double v = ri * fr[k];
       pr[k] = v;
       acc = fma(v, v, acc);
+      mx = fmax(mx, fabs(v));
     }
   }
   const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) part[(size_t)m * kPartialStride + blockIdx.y] = s;
+  // block maximum (fixed order as block_sum)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, redm[w]);
+    part[(size_t)m * kPartialStride + blockIdx.y] = s;
+    pmax[(size_t)m * kPartialStride + blockIdx.y] = b;
+  }
 }
 
 template <typename T>
@@ -2786,7 +2822,8 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   const int cblocks = (int)std::min<long long>(rows, 65535);
   // phi = r f (FP64) and ||phi||^2 partials
   note_launch();
-  prep_rhs<<<dim3(m, (nr + 15) / 16), 256, 0, s>>>(fd, w->phi64, op->c64.R, nr, nz, P, part_ptr(w, kPartD));
+  prep_rhs<<<dim3(m, (nr + 15) / 16), 256, 0, s>>>(fd, w->phi64, op->c64.R, nr, nz, P, part_ptr(w, kPartD),
+                                                   part_ptr(w, kPartC));
   const int nbf = (nr + 15) / 16;
   // x64: guess or zero
   if (guess) {
@@ -2801,10 +2838,14 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
       (unsigned)std::max<size_t>(1, std::min<size_t>((field + 1023) / 1024, (8192 + (size_t)m - 1) / (size_t)m));
   if (scaled) {
     note_launch();
-    rhs_scale<<<(m + 31) / 32, 32, 0, s>>>(w->rscale, part_ptr(w, kPartD), nbf, m, (double)nr * nz);
+    rhs_scale<<<(m + 31) / 32, 32, 0, s>>>(w->rscale, part_ptr(w, kPartC), nbf, m);
     note_launch();
-    apply_rhs_scale<<<dim3(sblocks, m), 256, 0, s>>>(w->phi64, guess ? w->x64 : nullptr, w->rscale,
-                                                     part_ptr(w, kPartD), nbf, field, false);
+    apply_rhs_scale<<<dim3(sblocks, m), 256, 0, s>>>(w->phi64, guess ? w->x64 : nullptr, w->rscale, nullptr, 0,
+                                                     field, false);
+    // ||phi||^2 of the scaled right-hand side, formed anew (the unscaled
+    // squares may have overflowed or underflowed)
+    note_launch();
+    phi_norm2<<<dim3(m, nbf), 256, 0, s>>>(w->phi64, nr, nz, P, part_ptr(w, kPartD));
   }
   AX_CHECK_LAUNCH();
   const int nbs64 = stencil_blocks_per_rhs(nr, nz, 2);

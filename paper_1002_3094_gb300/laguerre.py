@@ -31,8 +31,8 @@ def solve_chain(op, c2, src, fm: Sequence[float], alpha: int, tol: float, q_out,
     T, S, f = work[0], work[1], work[2]
     q_out.zero_()
     infos = []
-    # harmonic 0: T = S = 0, so the step writes f = f_0 src
-    ax_laguerre_step(op, T, T, S, c2, src, 0.0, laguerre_weights(0, alpha)[0], float(fm[0]), f, stream)
+    # harmonic 0: T = S = 0 and no solved field yet, so the step writes f = f_0 src
+    ax_laguerre_step(op, None, T, S, c2, src, 0.0, laguerre_weights(0, alpha)[0], float(fm[0]), f, stream)
     for m in range(len(fm)):
         flags = (AX_FLAG_USE_GUESS | AX_FLAG_CHECK_GUESS) if (warm and m > 0) else 0
         st, info = ax_solve(op, f.unsqueeze(0), q_out, 1, tol, max_iter, method, flags, stream=stream,

@@ -45,7 +45,7 @@ def test_step_matches_the_direct_sum(cuda, nr, nz):
     d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda)
     T, S, f = (torch.zeros((nr, nz), dtype=torch.float64, device=cuda) for _ in range(3))
     c2d, srcd = d(c2), d(src)
-    P.ax_laguerre_step(op, T, T, S, c2d, srcd, 0.0, L.weights(0, ALPHA)[0], fm[0], f)
+    P.ax_laguerre_step(op, None, T, S, c2d, srcd, 0.0, L.weights(0, ALPHA)[0], fm[0], f)
     assert np.array_equal(f.cpu().numpy(), fm[0] * src)
     for m in range(7):
         P.ax_laguerre_step(op, d(Q[m]), T, S, c2d, srcd, L.weights(m, ALPHA)[1], L.weights(m + 1, ALPHA)[0],
@@ -54,7 +54,11 @@ def test_step_matches_the_direct_sum(cuda, nr, nz):
         got = f.cpu().numpy()
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), m
     with pytest.raises(P.AxError):
-        P.ax_laguerre_step(op, T, T, S, c2d, srcd, float("nan"), 1.0, 1.0, f)
+        P.ax_laguerre_step(op, d(Q[0]), T, S, c2d, srcd, float("nan"), 1.0, 1.0, f)
+    with pytest.raises(P.AxError):  # no field to add, but a weight
+        P.ax_laguerre_step(op, None, T, S, c2d, srcd, 0.5, 1.0, 1.0, f)
+    with pytest.raises(P.AxError):  # Q is read while T is written
+        P.ax_laguerre_step(op, T, T, S, c2d, srcd, 0.5, 1.0, 1.0, f)
     P.ax_destroy_operator(op)
 
 

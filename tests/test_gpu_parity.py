@@ -347,12 +347,13 @@ def test_full_size_layered_1024_m64_zero_flux_sampled(cuda):
 
 
 @pytest.mark.parametrize("method", [P.AX_PCG_MIXED, P.AX_CHEB_MIXED])
-@pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e25])
+@pytest.mark.parametrize("scale", [1e-200, 1e-30, 1e-12, 1e25, 1e200])
 def test_mixed_methods_are_scale_invariant(cuda, method, scale):
-    """f scaled by 1e-30 .. 1e25: the mixed methods (FP32 inner iteration)
+    """f scaled by 1e-200 .. 1e200: the mixed methods (FP32 inner iteration)
     return scale times the unscaled solution to the tolerance, with the same
-    iteration count (their right-hand side is scaled by a power of two near
-    1 / rms(phi) inside the solve)."""
+    iteration count (their right-hand side is scaled by the power of two that
+    brings max |phi| into [1/2, 1) inside the solve).  The residual is
+    checked on u / scale against the unscaled phi (squares of 1e200 overflow)."""
     nr, nz = 96, 80
     med = layered_inclusion_medium(2, 96)
     kr, kz, q = sample_operator_inputs(med, nr, nz)
@@ -363,10 +364,11 @@ def test_mixed_methods_are_scale_invariant(cuda, method, scale):
     st2, i2 = P.ax_solve(op, f * scale, u2, 2, 1e-8, 5000, method)
     assert st1 == P.AX_OK and st2 == P.AX_OK
     ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
-    fh, uh = f.cpu().numpy() * scale, u2.cpu().numpy()
+    fh, uh = f.cpu().numpy(), u2.cpu().numpy() / scale
+    assert np.isfinite(uh).all()
     for j in range(2):
         phi = ora.phi(fh[j])
-        assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1e-8 * np.linalg.norm(phi)
+        assert np.linalg.norm(phi - ora.apply_A(uh[j])) <= 1.001e-8 * np.linalg.norm(phi)
         assert abs(i1[j]["iters"] - i2[j]["iters"]) <= 2, (i1[j], i2[j])
     P.ax_destroy_operator(op)
 
