@@ -195,9 +195,13 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    transform's epilogue; 0: in the stencil and update pass
  *   "mode_kernel"    FP32 mode solves (the per-mode tridiagonal systems of
  *                    Eq. eq_trid): 0 (default) the library's choice, 1 the
- *                    staged register kernel, 2..8 the pipelined column-tile
- *                    kernels on the row-scaled systems D T_l D (unit
- *                    couplings; the transforms around them apply D); an id
+ *                    staged register kernel, 9 the same on the row-scaled
+ *                    systems D T_l D (unit couplings; the transforms around
+ *                    the mode solves then apply D; 12 on 16-column tiles,
+ *                    nr <= 1024), 10 and 11 that kernel
+ *                    with the factors of a column tile kept in registers
+ *                    over 4 or 8 right-hand sides, 2..8 pipelined
+ *                    column-tile kernels on the row-scaled systems; an id
  *                    whose column does not fit nr is refused
  *   "cheb_bounds"    Chebyshev bounds gamma_1, gamma_2 (Eq. energy_rel): 0 the
  *                    face-wise bounds (min / max of kappa / kappa~ and q / q~),

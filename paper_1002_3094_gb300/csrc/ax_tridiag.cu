@@ -727,6 +727,404 @@ __global__ void __launch_bounds__(NT, 1024 / NT) tridiag_pipe_kernel(const TriAr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Staged register kernel on the row-scaled systems (FP32, variant 9).
+//
+// The layout of tridiag_reg_kernel (a CTA stages an nr x CW column tile of
+// one right-hand side and of the factors in shared memory; WPC warps per
+// column, lane c of warp h owning chunk (32 h + c) of C2 rows in registers;
+// chunk carries by warp shuffles, across the warps of a column through
+// shared memory), but on the systems T'_l = D T_l D with unit couplings (see
+// the pipelined kernels above: g = ips (b' + g), y' = g + ips y'), so a chunk
+// keeps only its values and factors in registers and each recurrence step is
+// one or two operations.  Tiles are staged with 8-byte cp.async (two columns
+// per copy); the column pair p = col / 2 of row `row` sits at pair
+// p ^ sw(row), sw(row) = (row / (32 / CW)) mod (CW / 2), so row `row`, column `col`
+// is at word row CW + 2 (p ^ sw(row)) + col % 2 + 2 (row / C2).  The two spare
+// words per chunk keep the pieces 8-byte aligned, and the chunks of a warp's
+// lanes (stride C2 CW + 2 words; sw is the same for all of them) fall into 16
+// distinct bank pairs (a two-way conflict at most); the XOR spreads the
+// write-back, where the lanes of a warp read consecutive rows, over distinct
+// bank pairs instead of every fourth row sharing one.
+// ---------------------------------------------------------------------------
+template <int CW>
+__device__ __forceinline__ int reg2_sw(int row) { return (row / (32 / CW)) & (CW / 2 - 1); }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+
+template <int C2, int WPC, int CW>
+__global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
+    tridiag_reg2_kernel(const TriArgs<float> a) {
+  constexpr int NT = 32 * WPC * CW;  // threads
+  constexpr int NCH = 32 * WPC;      // chunks per column
+  constexpr int NP = NCH * C2;       // padded rows
+  constexpr int kChunkWords = C2 * CW + 2;
+  constexpr int kTileWords = NCH * kChunkWords;
+  static_assert(NT <= 1024 && (CW == 4 || CW == 8 || CW == 16), "tile shape");
+  extern __shared__ __align__(16) float tsm2[];
+  __shared__ float xfa[CW][WPC], xfm[CW][WPC], xba[CW][WPC], xbm[CW][WPC];
+  __shared__ double red[NT / 32];
+  const int nr = a.nr, pitch = a.pitch;
+  float *ips = tsm2;
+  float *ds = ips + kTileWords;
+  const int col0 = blockIdx.x * CW;
+  const int m = blockIdx.y;
+  if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
+  // ---- stage the tiles: 8-byte pieces, rows of the tile in order ----
+  {
+    constexpr int kParts = CW / 2;
+    const int part = threadIdx.x % kParts;
+    const float *ipg = a.IP + (size_t)m * a.cstride + col0 + 2 * part;
+    const float *ing = a.in + (size_t)m * a.field + col0 + 2 * part;
+#pragma unroll 4
+    for (int row = threadIdx.x / kParts; row < NP; row += NT / kParts) {
+      const bool ok = row < nr;
+      const size_t go = (size_t)(ok ? row : 0) * pitch;
+      const int si = row * CW + 2 * (part ^ reg2_sw<CW>(row)) + 2 * (row / C2);
+      cp_async8(ips + si, ipg + go, ok);
+      cp_async8(ds + si, ing + go, ok);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = warp / WPC, h = warp % WPC;  // column, segment of the r-range
+  const int ci = h * 32 + lane;               // chunk index 0 .. NCH - 1
+  // column w of row ci C2 + t at word ci kChunkWords + CW t + wc(t)
+  float *pd = ds + ci * kChunkWords;
+  const float *pip = ips + ci * kChunkWords;
+  const int rbase = ci * C2;
+  auto wc = [&](int t) { return 2 * ((w >> 1) ^ reg2_sw<CW>(rbase + t)) + (w & 1); };
+  float v[C2], ip[C2];
+  // forward, zero carry-in
+  float g = 0.f, mu = 1.f;
+#pragma unroll
+  for (int t = 0; t < C2; ++t) {
+    ip[t] = pip[CW * t + wc(t)];
+    g = ip[t] * (pd[CW * t + wc(t)] + g);
+    mu *= ip[t];
+    v[t] = g;
+  }
+  float A = g, M = mu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pa = __shfl_up_sync(0xffffffffu, A, off), pm = __shfl_up_sync(0xffffffffu, M, off);
+    if (lane >= off) {
+      A = fmaf(M, pa, A);
+      M *= pm;
+    }
+  }
+  float Ae = __shfl_up_sync(0xffffffffu, A, 1), Me = __shfl_up_sync(0xffffffffu, M, 1);
+  if (lane == 0) {
+    Ae = 0.f;
+    Me = 1.f;
+  }
+  if (WPC > 1) {
+    if (lane == 31) {
+      xfa[w][h] = A;
+      xfm[w][h] = M;
+    }
+    __syncthreads();
+  }
+  float cin = 0.f;  // carry into this warp's first chunk: the maps of warps 0 .. h-1
+  for (int j = 0; j < h; ++j) cin = fmaf(xfm[w][j], cin, xfa[w][j]);
+  const float gin = fmaf(Me, cin, Ae);
+  float pr = 1.f;
+#pragma unroll
+  for (int t = 0; t < C2; ++t) {
+    pr *= ip[t];
+    v[t] = fmaf(pr, gin, v[t]);
+  }
+  // backward, zero carry-in
+  float y = 0.f;
+  mu = 1.f;
+#pragma unroll
+  for (int t = C2 - 1; t >= 0; --t) {
+    y = fmaf(ip[t], y, v[t]);
+    mu *= ip[t];
+    v[t] = y;
+  }
+  A = y;
+  M = mu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pa = __shfl_down_sync(0xffffffffu, A, off), pm = __shfl_down_sync(0xffffffffu, M, off);
+    if (lane + off < 32) {
+      A = fmaf(M, pa, A);
+      M *= pm;
+    }
+  }
+  Ae = __shfl_down_sync(0xffffffffu, A, 1);
+  Me = __shfl_down_sync(0xffffffffu, M, 1);
+  if (lane == 31) {
+    Ae = 0.f;
+    Me = 1.f;
+  }
+  if (WPC > 1) {
+    if (lane == 0) {
+      xba[w][h] = A;
+      xbm[w][h] = M;
+    }
+    __syncthreads();
+  }
+  cin = 0.f;  // carry into this warp's last chunk: the maps of warps WPC-1 .. h+1
+  for (int j = WPC - 1; j > h; --j) cin = fmaf(xbm[w][j], cin, xba[w][j]);
+  const float yin = fmaf(Me, cin, Ae);
+  pr = 1.f;
+  float dot = 0.f;
+#pragma unroll
+  for (int t = C2 - 1; t >= 0; --t) {
+    pr *= ip[t];
+    v[t] = fmaf(pr, yin, v[t]);
+    dot = fmaf(pd[CW * t + wc(t)], v[t], dot);  // (b', y') of this chunk: the (rhat, yhat) partial
+    pd[CW * t + wc(t)] = v[t];
+  }
+  if (a.partial != nullptr) {
+    const double sw = warp_sum((double)dot);
+    if (lane == 0) red[warp] = sw;
+  }
+  __syncthreads();
+  if (a.partial != nullptr && threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < NT / 32; ++i) tot += red[i];
+    a.partial[(size_t)m * kPartialStride + blockIdx.x] = tot;
+  }
+  // ---- write back: one thread per row, its CW columns ----
+  const int ncol = min(CW, a.nz - col0);
+  for (int row = threadIdx.x; row < nr; row += NT) {
+    float x[CW];
+    const float *src = ds + row * CW + 2 * (row / C2);
+    const int sw = reg2_sw<CW>(row);
+#pragma unroll
+    for (int c = 0; c < CW; c += 2) {
+      const float2 f2 = *reinterpret_cast<const float2 *>(src + 2 * ((c >> 1) ^ sw));
+      x[c] = f2.x;
+      x[c + 1] = f2.y;
+    }
+    if (a.split != nullptr) {
+      if constexpr (CW == 16) {
+        if (col0 + 8 < a.nz) {
+          split_store16(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+        } else {  // only the first 8 columns are inside n8
+          float x8[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x8[e] = x[e];
+          split_store8(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x8);
+        }
+      } else if constexpr (CW == 8) {
+        split_store8(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      } else {
+        split_store4(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      }
+    } else {
+      float *o = a.out + (size_t)m * a.field + (size_t)row * pitch + col0;
+      if (ncol == CW) {
+#pragma unroll
+        for (int c = 0; c < CW; c += 4) *reinterpret_cast<float4 *>(o + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
+      } else {
+        for (int c = 0; c < ncol; ++c) o[c] = x[c];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Variants 10 and 11: the kernel above with the factors kept across right-hand
+// sides.  A CTA owns one column tile and R consecutive right-hand sides
+// (R = 4 or 8): it stages the factors of the tile once and keeps each lane's
+// C2 of them in registers, then solves the selected right-hand sides in turn,
+// the data tile of the next one copied into the second of two shared-memory
+// stages while the current one is solved.  Same layout, arithmetic and
+// partials as tridiag_reg2_kernel.
+// ---------------------------------------------------------------------------
+template <int C2, int WPC, int CW>
+__global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
+    tridiag_reg3_kernel(const TriArgs<float> a, int R) {
+  constexpr int NT = 32 * WPC * CW;
+  constexpr int NCH = 32 * WPC;
+  constexpr int NP = NCH * C2;
+  constexpr int kChunkWords = C2 * CW + 2;
+  constexpr int kTileWords = NCH * kChunkWords;
+  constexpr int kParts = CW / 2;
+  static_assert(NT <= 1024 && (CW == 4 || CW == 8), "tile shape");
+  extern __shared__ __align__(16) float tsm3[];
+  __shared__ float xfa[CW][WPC], xfm[CW][WPC], xba[CW][WPC], xbm[CW][WPC];
+  __shared__ double red[NT / 32];
+  const int nr = a.nr, pitch = a.pitch;
+  float *ips = tsm3;
+  auto dbuf = [&](int b) { return tsm3 + (1 + b) * kTileWords; };
+  const int col0 = blockIdx.x * CW;
+  const int m0 = blockIdx.y * R, m1 = min(a.m, m0 + R);
+  auto next_sel = [&](int from) {  // first selected right-hand side >= from (m1 if none)
+    int mm = from;
+    while (mm < m1 && !rhs_selected(a.st, a.mask, mm)) ++mm;
+    return mm;
+  };
+  int mc = next_sel(m0);
+  if (mc >= m1) return;  // uniform over the CTA
+  const int part = threadIdx.x % kParts;
+  auto stage = [&](const float *g, float *dst) {
+#pragma unroll 4
+    for (int row = threadIdx.x / kParts; row < NP; row += NT / kParts) {
+      const bool ok = row < nr;
+      cp_async8(dst + row * CW + 2 * (part ^ reg2_sw<CW>(row)) + 2 * (row / C2),
+                g + (size_t)(ok ? row : 0) * pitch + 2 * part, ok);
+    }
+  };
+  // factors (one table for all right-hand sides of an operator; a stacked
+  // group has one per right-hand side and is not launched here)
+  stage(a.IP + col0, ips);
+  stage(a.in + (size_t)mc * a.field + col0, dbuf(0));
+  cp_async_commit();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = warp / WPC, h = warp % WPC;
+  const int ci = h * 32 + lane;
+  const int rbase = ci * C2;
+  auto wc = [&](int t) { return 2 * ((w >> 1) ^ reg2_sw<CW>(rbase + t)) + (w & 1); };
+  const int ncol = min(CW, a.nz - col0);
+  float ip[C2];
+  bool have_ip = false;
+  int buf = 0;
+  while (mc < m1) {
+    const int mn = next_sel(mc + 1);
+    if (mn < m1) {
+      stage(a.in + (size_t)mn * a.field + col0, dbuf(buf ^ 1));
+      cp_async_commit();
+      asm volatile("cp.async.wait_group 1;" ::: "memory");  // all but the newest group
+    } else {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    if (!have_ip) {
+      const float *pip = ips + ci * kChunkWords;
+#pragma unroll
+      for (int t = 0; t < C2; ++t) ip[t] = pip[CW * t + wc(t)];
+      have_ip = true;
+    }
+    float *pd = dbuf(buf) + ci * kChunkWords;
+    float v[C2];
+    float g = 0.f, mu = 1.f;
+#pragma unroll
+    for (int t = 0; t < C2; ++t) {
+      g = ip[t] * (pd[CW * t + wc(t)] + g);
+      mu *= ip[t];
+      v[t] = g;
+    }
+    float A = g, M = mu;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float pa = __shfl_up_sync(0xffffffffu, A, off), pm = __shfl_up_sync(0xffffffffu, M, off);
+      if (lane >= off) {
+        A = fmaf(M, pa, A);
+        M *= pm;
+      }
+    }
+    float Ae = __shfl_up_sync(0xffffffffu, A, 1), Me = __shfl_up_sync(0xffffffffu, M, 1);
+    if (lane == 0) {
+      Ae = 0.f;
+      Me = 1.f;
+    }
+    if (WPC > 1) {
+      if (lane == 31) {
+        xfa[w][h] = A;
+        xfm[w][h] = M;
+      }
+      __syncthreads();
+    }
+    float cin = 0.f;
+    for (int j = 0; j < h; ++j) cin = fmaf(xfm[w][j], cin, xfa[w][j]);
+    const float gin = fmaf(Me, cin, Ae);
+    float pr = 1.f;
+#pragma unroll
+    for (int t = 0; t < C2; ++t) {
+      pr *= ip[t];
+      v[t] = fmaf(pr, gin, v[t]);
+    }
+    float y = 0.f;
+    mu = 1.f;
+#pragma unroll
+    for (int t = C2 - 1; t >= 0; --t) {
+      y = fmaf(ip[t], y, v[t]);
+      mu *= ip[t];
+      v[t] = y;
+    }
+    A = y;
+    M = mu;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float pa = __shfl_down_sync(0xffffffffu, A, off), pm = __shfl_down_sync(0xffffffffu, M, off);
+      if (lane + off < 32) {
+        A = fmaf(M, pa, A);
+        M *= pm;
+      }
+    }
+    Ae = __shfl_down_sync(0xffffffffu, A, 1);
+    Me = __shfl_down_sync(0xffffffffu, M, 1);
+    if (lane == 31) {
+      Ae = 0.f;
+      Me = 1.f;
+    }
+    if (WPC > 1) {
+      if (lane == 0) {
+        xba[w][h] = A;
+        xbm[w][h] = M;
+      }
+      __syncthreads();
+    }
+    cin = 0.f;
+    for (int j = WPC - 1; j > h; --j) cin = fmaf(xbm[w][j], cin, xba[w][j]);
+    const float yin = fmaf(Me, cin, Ae);
+    pr = 1.f;
+    float dot = 0.f;
+#pragma unroll
+    for (int t = C2 - 1; t >= 0; --t) {
+      pr *= ip[t];
+      v[t] = fmaf(pr, yin, v[t]);
+      dot = fmaf(pd[CW * t + wc(t)], v[t], dot);
+      pd[CW * t + wc(t)] = v[t];
+    }
+    if (a.partial != nullptr) {
+      const double sw = warp_sum((double)dot);
+      if (lane == 0) red[warp] = sw;
+    }
+    __syncthreads();
+    if (a.partial != nullptr && threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < NT / 32; ++i) tot += red[i];
+      a.partial[(size_t)mc * kPartialStride + blockIdx.x] = tot;
+    }
+    for (int row = threadIdx.x; row < nr; row += NT) {
+      float x[CW];
+      const float *src = dbuf(buf) + row * CW + 2 * (row / C2);
+      const int sw = reg2_sw<CW>(row);
+#pragma unroll
+      for (int c = 0; c < CW; c += 2) {
+        const float2 f2 = *reinterpret_cast<const float2 *>(src + 2 * ((c >> 1) ^ sw));
+        x[c] = f2.x;
+        x[c + 1] = f2.y;
+      }
+      if (a.split != nullptr) {
+        if constexpr (CW == 8) split_store8(a.split, mc, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+        else split_store4(a.split, mc, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      } else {
+        float *o = a.out + (size_t)mc * a.field + (size_t)row * pitch + col0;
+        if (ncol == CW) {
+#pragma unroll
+          for (int c = 0; c < CW; c += 4)
+            *reinterpret_cast<float4 *>(o + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
+        } else {
+          for (int c = 0; c < ncol; ++c) o[c] = x[c];
+        }
+      }
+    }
+    __syncthreads();  // the stage is read; the next copy into it may start
+    mc = mn;
+    buf ^= 1;
+  }
+}
+
 }  // namespace
 
 // Chunk length C: short enough that the chunk stays in registers without
@@ -752,6 +1150,28 @@ void launch_tridiag_c(const TriArgs<T> &a, cudaStream_t s) {
 }
 
 template <int C2, int WPC, int CW>
+void launch_tridiag_reg2(const TriArgs<float> &a, cudaStream_t s) {
+  constexpr int NCH = 32 * WPC;
+  const size_t smem = sizeof(float) * 2 * NCH * (C2 * CW + 2);
+  ensure_smem_attr((const void *)tridiag_reg2_kernel<C2, WPC, CW>, smem);
+  dim3 grid((a.nz + CW - 1) / CW, a.m);
+  TriArgs<float> b = a;  // the scaled factors through IP
+  b.IP = a.IPS;
+  tridiag_reg2_kernel<C2, WPC, CW><<<grid, 32 * WPC * CW, smem, s>>>(b);
+}
+
+template <int C2, int WPC, int CW>
+void launch_tridiag_reg3(const TriArgs<float> &a, int R, cudaStream_t s) {
+  constexpr int NCH = 32 * WPC;
+  const size_t smem = sizeof(float) * 3 * NCH * (C2 * CW + 2);
+  ensure_smem_attr((const void *)tridiag_reg3_kernel<C2, WPC, CW>, smem);
+  dim3 grid((a.nz + CW - 1) / CW, (a.m + R - 1) / R);
+  TriArgs<float> b = a;
+  b.IP = a.IPS;
+  tridiag_reg3_kernel<C2, WPC, CW><<<grid, 32 * WPC * CW, smem, s>>>(b, R);
+}
+
+template <int C2, int WPC, int CW>
 void launch_tridiag_reg(const TriArgs<float> &a, cudaStream_t s) {
   // mirrors the kernel's layout: the IP and data tiles
   constexpr int NCH = 32 * WPC, NP = NCH * C2;
@@ -770,11 +1190,19 @@ constexpr PipeVariant kPipeVariants[] = {{2, 32, 1024}, {3, 16, 512}, {4, 16, 10
 int pipe_max_rows(const PipeVariant &v) { return 16 * v.nt / v.cw; }
 
 int tridiag_variants(int nr, int *ids) {
-  // the register kernel first (the default: measured faster than the
-  // pipelined kernels at nr = 1024 and equal at 4096), then the pipelined
-  // kernels whose column covers nr with at most half of it idle
+  // the default first: the staged register kernel on the row-scaled systems
+  // (9; measured 9.7 ms per 1024^2 x 64 solve against 10.4 for the plain
+  // register kernel 1, 11.3 to 12.5 for the pipelined kernels and for 10, 11,
+  // 12), then the others; paths that cannot scale the rows (the FFT
+  // transforms) take kernel 1 (tridiag_effective)
   int n = 0;
-  if (nr <= 4096) ids[n++] = 1;
+  if (nr <= 4096) {
+    ids[n++] = 9;
+    ids[n++] = 1;
+    ids[n++] = 10;
+    ids[n++] = 11;
+  }
+  if (nr <= 1024) ids[n++] = 12;
   for (const PipeVariant &v : kPipeVariants)
     if (nr <= pipe_max_rows(v) && 2 * nr > pipe_max_rows(v)) ids[n++] = v.id;
   return n;
@@ -803,7 +1231,8 @@ static int reg_cols(int nr) { return nr <= 2048 ? 8 : (nr <= 4096 ? 4 : 0); }
 int tridiag_reg_cols(int nr, int variant) {
   const int v = resolve_variant(nr, variant);
   if (v == 0) return 0;
-  if (v == 1) return reg_cols(nr);
+  if (v == 12) return 16;
+  if (v == 1 || v >= 9) return reg_cols(nr);
   return find_pipe(v)->cw;
 }
 
@@ -828,7 +1257,7 @@ void launch_tridiag_pipe(const TriArgs<float> &a, cudaStream_t s) {
 
 int tridiag_effective(int nr, int variant, int m, bool scaled_tables) {
   const int v = resolve_variant(nr, variant);
-  if (v >= 2 && (m > PipeShape<16, 1024>::kMaxList || !scaled_tables)) return 1;
+  if (v >= 2 && (!scaled_tables || (v < 9 && m > PipeShape<16, 1024>::kMaxList))) return 1;
   return v;
 }
 
@@ -838,6 +1267,36 @@ bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
   // the pipelined kernels solve the row-scaled systems; plain data takes the
   // register kernel
   if (!a.prescaled) v = 1;
+  if (v == 10 || v == 11) {
+    if (a.cstride != 0) {
+      v = 9;  // a stacked group: factors per right-hand side
+    } else {
+      const int R = v == 10 ? 4 : 8;
+      const int c2 = (a.nr + 63) / 64;
+      if (c2 <= 4) launch_tridiag_reg3<4, 2, 8>(a, R, s);
+      else if (c2 <= 8) launch_tridiag_reg3<8, 2, 8>(a, R, s);
+      else if (c2 <= 16) launch_tridiag_reg3<16, 2, 8>(a, R, s);
+      else if (a.nr <= 2048) launch_tridiag_reg3<16, 4, 8>(a, R, s);
+      else launch_tridiag_reg3<16, 8, 4>(a, R, s);
+      return true;
+    }
+  }
+  if (v == 12) {  // the same on 16-column tiles (one 1024-thread CTA per SM)
+    const int c2 = (a.nr + 63) / 64;
+    if (c2 <= 4) launch_tridiag_reg2<4, 2, 16>(a, s);
+    else if (c2 <= 8) launch_tridiag_reg2<8, 2, 16>(a, s);
+    else launch_tridiag_reg2<16, 2, 16>(a, s);
+    return true;
+  }
+  if (v == 9) {  // the staged register kernel on the row-scaled systems
+    const int c2 = (a.nr + 63) / 64;
+    if (c2 <= 4) launch_tridiag_reg2<4, 2, 8>(a, s);
+    else if (c2 <= 8) launch_tridiag_reg2<8, 2, 8>(a, s);
+    else if (c2 <= 16) launch_tridiag_reg2<16, 2, 8>(a, s);
+    else if (a.nr <= 2048) launch_tridiag_reg2<16, 4, 8>(a, s);
+    else launch_tridiag_reg2<16, 8, 4>(a, s);
+    return true;
+  }
   switch (v) {
     case 2: launch_tridiag_pipe<32, 1024>(a, s); return true;
     case 3: launch_tridiag_pipe<16, 512>(a, s); return true;
