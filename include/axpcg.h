@@ -214,6 +214,13 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    info.iters of the solve that ran it
  *   "cheb_steps"     PCG steps of that estimate (2..200, default 20)
  *   "cheb_widen"     relative widening of the estimate (0 <= v < 1, default 0.05)
+ *   "host_chunks"    AX_FLAG_HOST_BUFFERS solves of m >= 2 v right-hand sides
+ *                    run in v chunks (1..64, default 1: one copy in, one copy
+ *                    out): the copies of one chunk overlap the solve of another
+ *                    (a second stream; two chunks of device staging).  The
+ *                    results equal a device-buffer solve's bit for bit.  Pays
+ *                    where the copies outweigh the loss of solving fewer
+ *                    right-hand sides per launch
  *   "cheb_check"     the Chebyshev methods form the residual norm (a reduction)
  *                    every v-th step only (1..256, default 1; always on the last
  *                    step of each graph replay); the steps between advance the
