@@ -62,15 +62,19 @@ TC_CLASSES = ("dst_forward", "dst_inverse")
 # (file, __global__ function or None for the whole file), plus the shared
 # device helpers.
 KERNEL_SOURCES = {"stencil": [("ax_stencil.cu", "stencil_kernel")],
+                  "stencil_staged": [("ax_stencil.cu", "stencil_bulk_kernel")],
                   "dst_forward": [("ax_dst_impl.cuh", None)],
                   "dst_inverse": [("ax_dst_impl.cuh", None)],
                   "dst_forward_tc": [("ax_dst_gemm.cu", None)],
                   "dst_inverse_tc": [("ax_dst_gemm.cu", None)],
                   "mode_solve": [("ax_tridiag.cu", "tridiag_reg_kernel")],
+                  "mode_solve_scaled": [("ax_tridiag.cu", "tridiag_reg2_kernel")],
+                  "mode_solve_reuse": [("ax_tridiag.cu", "tridiag_reg3_kernel")],
+                  "mode_solve_pipe": [("ax_tridiag.cu", "tridiag_pipe_kernel")],
                   "mode_solve_tall": [("ax_tridiag.cu", "tridiag_kernel")],
                   "outer_residual": [("ax_stencil.cu", "residual_df_kernel")],
                   "pcg_update": [("ax_solver.cu", "pcg_update")]}
-TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic_per_unknown.md")
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic_per_unknown.json")
 
 
 def _function_text(src: str, name: str) -> str:
@@ -98,19 +102,37 @@ def source_hash(kernel: str) -> str:
 
 def measured_traffic(kernel: str, units_per_launch: float):
     """DRAM bytes (read + write) per launch of `kernel`, scaled from the ncu
-    capture recorded in profiles/traffic_per_unknown.md (bytes per grid
+    capture recorded in profiles/traffic_per_unknown.json (bytes per grid
     unknown of the captured launch), or None when no capture matches the
     current source of the kernel."""
     try:
-        lines = open(TRAFFIC_TABLE).read().splitlines()
-    except OSError:
+        with open(TRAFFIC_TABLE) as fh:
+            entries = json.load(fh)["entries"]
+    except (OSError, ValueError, KeyError):
         return None
     want = source_hash(kernel)
-    for line in lines:
-        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 3 and cells[0] == kernel and cells[2] == want:
-            return float(cells[1]) * units_per_launch
+    for e in entries:
+        if e.get("class") == kernel and e.get("source_sha") == want:
+            return float(e["dram_bytes_per_unknown"]) * units_per_launch
     return None
+
+
+MODE_CLASSES = {1: "mode_solve", 9: "mode_solve_scaled", 12: "mode_solve_scaled", 10: "mode_solve_reuse",
+                11: "mode_solve_reuse"}
+
+
+def kernel_class(top: str, tc_path: bool, fused: bool, mode_eff: int, stencil_v: int) -> str:
+    """The KERNEL_SOURCES class of profiled kernel group `top` as the solve
+    ran it (transform form, mode-solve kernel id, stencil variant)."""
+    if top in TC_CLASSES and tc_path:
+        return top + "_tc"
+    if top == "mode_solve":
+        if mode_eff == 0:
+            return "mode_solve_tall"
+        return MODE_CLASSES.get(mode_eff, "mode_solve_pipe")
+    if top == "stencil" and fused and stencil_v != 0:
+        return "stencil_staged"
+    return top
 
 
 def parse_args():
@@ -143,6 +165,8 @@ def parse_args():
                     help="keep the library's default transform and mode-solve kernel (no ax_autotune)")
     ap.add_argument("--mode-kernel", type=int, default=0,
                     help="FP32 mode-solve kernel variant (option mode_kernel; 0 the library's choice)")
+    ap.add_argument("--stencil-kernel", type=int, default=-1,
+                    help="stencil of the fused FP32 iteration (option stencil_kernel; -1 the library's choice)")
     ap.add_argument("--replace-delta", type=float, default=0.0,
                     help="mixed PCG: residual reduction between FP64 residual replacements (0: the library's)")
     return ap.parse_args()
@@ -714,12 +738,18 @@ def main():
         P.ax_set_option(op, "replace_delta", args.replace_delta)
     if args.mode_kernel > 0:
         P.ax_set_option(op, "mode_kernel", args.mode_kernel)
+    if args.stencil_kernel >= 0:
+        P.ax_set_option(op, "stencil_kernel", args.stencil_kernel)
     tuned = None
-    if not args.no_autotune and args.dst_tensor < 0 and args.mode_kernel == 0 and "mixed" in args.method:
+    if (not args.no_autotune and args.dst_tensor < 0 and args.mode_kernel == 0 and args.stencil_kernel < 0
+            and "mixed" in args.method):
         t0 = time.perf_counter()
         P.ax_autotune(op, m, 5)
         tuned = {"dst_tensor": int(P.ax_get_option(op, "dst_tensor")),
-                 "mode_kernel": int(P.ax_get_option(op, "mode_kernel")), "autotune_s": time.perf_counter() - t0}
+                 "mode_kernel": int(P.ax_get_option(op, "mode_kernel")),
+                 "stencil_kernel": int(P.ax_get_option(op, "stencil_kernel")), "autotune_s": time.perf_counter() - t0}
+    mode_eff = int(P.ax_get_option(op, "mode_kernel_effective"))
+    stencil_v = int(P.ax_get_option(op, "stencil_kernel"))
     f_host = sample_rhs(med, nr, nz, bc_z=args.bc_z)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)
@@ -833,9 +863,7 @@ def main():
         bytes_per_launch = units_per_launch * per_u + (nr * nz) * per_m
         avg_s = p["ms"] / p["launches"] / 1000.0
         achieved = bytes_per_launch / avg_s / 1e9
-        variant = top + ("_tc" if tc_path and top in TC_CLASSES else "")
-        if top == "mode_solve" and nr > 1024:
-            variant = "mode_solve_tall"  # the FP32 register kernel covers nr <= 1024
+        variant = kernel_class(top, tc_path, fused, mode_eff, stencil_v)
         traffic = measured_traffic(variant, units_per_launch)
         roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,

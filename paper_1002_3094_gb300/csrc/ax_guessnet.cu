@@ -33,7 +33,6 @@ using bf16 = __nv_bfloat16;
 __device__ __forceinline__ float ld_as_float(const float *p) { return *p; }
 __device__ __forceinline__ float ld_as_float(const bf16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void st_from_float(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st_from_float(bf16 *p, float v) { *p = __float2bfloat16(v); }
 
 constexpr int kTile = 32;   // output tile edge (pixels)
 constexpr int kCib = 8;     // input channels per smem stage

@@ -162,6 +162,7 @@ struct ax_operator {
   int *rader_perm = nullptr;  // [2 P] device
   int dst_tc = 0;             // 1: the FP32 PCG path transforms with the tensor-core GEMM
   int tri_variant = 0;        // FP32 mode-solve kernel (0: default for nr; option "mode_kernel")
+  int st_variant = 0;         // stencil of the fused FP32 iteration (option "stencil_kernel")
   int *tc_err = nullptr;      // device flag: a bounded wait of the GEMM expired
   ax::Coef<double> c64;
   ax::Coef<float> c32;
@@ -197,11 +198,19 @@ struct StencilArgs {
   const RhsState *st;    // per RHS state (Pcg reads beta)
   int mask;
   double *partial;       // [m][kPartialStride] per-CTA sums: Pcg (p,q); Residual, Cheb ||res||^2
+  int variant;           // PcgP, FP32: 0 register window; 1, 2 rows of p staged in shared
+                         // memory by bulk copies, 16 or 8 rows per CTA
+  int *err;              // variants 1, 2: set when a bounded wait expired
+  unsigned polls;        // variants 1, 2: wait limit (0: the default)
+  int stall;             // variants 1, 2, test of the expiry path: no copy is issued, so
+                         // every wait runs out (with a short `polls`)
 };
 
 template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s);
-int stencil_blocks_per_rhs(int nr, int nz, int vec);
+// CTAs (and partial sums) per right-hand side of a stencil launch
+int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant = 0);
+constexpr int kStencilVariants = 3;
 
 // Double-float true residual r = phi - A x of the mixed method: x, phi and the
 // coefficients as pairs of FP32 numbers (hi + lo), all arithmetic in FP32 with

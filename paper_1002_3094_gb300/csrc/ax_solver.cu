@@ -80,6 +80,8 @@ struct Workspace {
   int max_outer = 30;
   int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
   int tc_stall_test = 0;        // 1: the next tensor-core transform lets one bounded wait run out
+  int st_stall_test = 0;        // 1: the next staged stencil lets its bounded waits run out
+  int st_stall_used = 0;        // a captured graph holds that stalled launch (freed after the solve)
   int tc_unfused = 0;           // 1: mixed PCG forms p in the stencil, not in the inverse transform
   double replace_delta = 0.1;   // residual reduction between FP64 replacements
   int cheb_bounds = -1;         // Chebyshev bounds: 0 face-wise, 1 Lanczos estimate, -1 Lanczos
@@ -1166,6 +1168,17 @@ int *tc_flag(int device) {
   return d;
 }
 
+// Test of the staged stencil's expiry path (option "stencil_stall_test"), once:
+// the launch issues no copy and waits briefly, so every wait runs out.
+template <typename T>
+void stencil_stall(const ax_operator *op, StencilArgs<T> &sa) {
+  if (!op->ws->st_stall_test) return;
+  sa.stall = 1;
+  sa.polls = 1u << 12;
+  op->ws->st_stall_test = 0;
+  op->ws->st_stall_used = 1;
+}
+
 template <typename T>
 bool use_tc(const ax_operator *op) {
   return sizeof(T) == 4 && op->dst_tc != 0;
@@ -1347,7 +1360,8 @@ template <typename T>
 void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *st, Workspace *w,
                    int on_converge, cudaStream_t s, double units = 0.0, bool fused = false) {
   const int V = VecT<T>::n;
-  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
+  const int stv = fused && sizeof(T) == 4 ? op->st_variant : 0;
+  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V, stv);
   const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
   double *pq = part_ptr(w, kPartA), *prr = part_ptr(w, kPartB), *prz = part_ptr(w, kPartC);
   StencilArgs<T> sa = stencil_args<T>(op, m, st, kActive);
@@ -1356,6 +1370,11 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
   sa.pb = v.pb;
   sa.out = v.q;
   sa.partial = pq;
+  if (stv != 0) {
+    sa.variant = stv;
+    sa.err = tc_flag(op->device);
+    stencil_stall(op, sa);
+  }
   {
     ProfScope ps(w, kProfStencil, units, s);
     launch_stencil<T>(fused ? kStencilPcgP : kStencilPcg, sa, s);
@@ -2190,7 +2209,7 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t, double
 // kernel, the time in ms).
 // ---------------------------------------------------------------------------
 namespace {
-struct TuneChoice { int dst = 0, variant = 0; double ms = 0.0; };
+struct TuneChoice { int dst = 0, variant = 0; double ms = 0.0; int stencil = 0; };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune;
 bool g_tune_loaded = false;
@@ -2217,7 +2236,7 @@ void tune_load() {
   if (!fp) return;
   char key[200];
   TuneChoice c;
-  while (fscanf(fp, "%199s %d %d %lf", key, &c.dst, &c.variant, &c.ms) == 4) g_tune[key] = c;
+  while (fscanf(fp, "%199s %d %d %d %lf", key, &c.dst, &c.variant, &c.stencil, &c.ms) == 5) g_tune[key] = c;
   fclose(fp);
 }
 
@@ -2226,13 +2245,15 @@ void tune_save() {
   if (!path) return;
   FILE *fp = fopen(path, "w");
   if (!fp) return;
-  for (auto &e : g_tune) fprintf(fp, "%s %d %d %.6f\n", e.first.c_str(), e.second.dst, e.second.variant, e.second.ms);
+  for (auto &e : g_tune)
+    fprintf(fp, "%s %d %d %d %.6f\n", e.first.c_str(), e.second.dst, e.second.variant, e.second.stencil, e.second.ms);
   fclose(fp);
 }
 
 void apply_choice(ax_operator *op, const TuneChoice &c) {
   op->dst_tc = c.dst;
   op->tri_variant = c.variant;
+  op->st_variant = c.stencil;
   Workspace *w = op->ws;
   free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
 }
@@ -2270,7 +2291,7 @@ int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
         !tc_table(op->device, op->nz, cz ? kTableCosInverse : kTableSine) || !tc_flag(op->device))
       return AX_ERR_OOM;
   }
-  const TuneChoice saved{op->dst_tc, op->tri_variant, 0.0};
+  const TuneChoice saved{op->dst_tc, op->tri_variant, 0.0, op->st_variant};
   const size_t n = field_elems(op) * m;
   cudaEvent_t e0, e1;
   AX_TRY(cudaEventCreate(&e0));
@@ -2292,7 +2313,9 @@ int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
   }
   TuneChoice best;
   best.ms = -1.0;
-  for (TuneChoice &c : cand) {
+  const size_t nbase = cand.size();
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    TuneChoice &c = cand[ci];
     apply_choice(op, c);
     const bool fused = tc_fused(op);
     AX_TRY(cudaMemsetAsync(w->r32, 0x3f, sizeof(float) * n, s));  // 0x3f3f3f3f: 0.747
@@ -2312,6 +2335,13 @@ int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
     cudaEventElapsedTime(&ms, e0, e1);
     c.ms = ms / reps;
     if (best.ms < 0.0 || c.ms < best.ms) best = c;
+    // then the staged stencils with the fastest tensor-core choice (only the
+    // fused iteration runs them)
+    if (ci + 1 == nbase && best.dst != 0) {
+      apply_choice(op, best);
+      if (tc_fused(op))
+        for (int sv = 1; sv < kStencilVariants; ++sv) cand.push_back({best.dst, best.variant, 0.0, sv});
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2341,6 +2371,9 @@ int ax_get_option(const ax_operator *op, const char *name, double *value) {
   const Workspace *w = op->ws;
   if (!strcmp(name, "dst_tensor")) *value = op->dst_tc;
   else if (!strcmp(name, "mode_kernel")) *value = op->tri_variant;
+  else if (!strcmp(name, "stencil_kernel")) *value = op->st_variant;
+  else if (!strcmp(name, "mode_kernel_effective"))  // the FP32 mode-solve kernel a solve runs (0: none of the tile kernels)
+    *value = tridiag_effective(op->nr, op->tri_variant, 1, op->c32.IPS != nullptr && op->c32.RS != nullptr);
   else if (!strcmp(name, "inner_tol")) *value = w->inner_tol;
   else if (!strcmp(name, "inner_max_iter")) *value = w->inner_max;
   else if (!strcmp(name, "graph_iters")) *value = w->graph_iters;
@@ -2401,6 +2434,12 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
   } else if (!strcmp(name, "tc_fused")) {
     w->tc_unfused = value == 0.0;
     free_graph(w->g32);
+  } else if (!strcmp(name, "stencil_stall_test")) {
+    // The next staged stencil (option "stencil_kernel" 1 or 2) issues no copy
+    // and waits briefly, so its bounded waits run out: the call returns
+    // AX_ERR_TIMEOUT and the context stays usable.  For tests.
+    w->st_stall_test = value != 0.0;
+    free_graph(w->g32);
   } else if (!strcmp(name, "tc_stall_test")) {
     // The next tensor-core transform stops its copies before the first stage,
     // so that the MMA warp's bounded wait runs out (short limit): the call
@@ -2425,6 +2464,14 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
       if (!ok) return AX_ERR_INVALID_ARG;
     }
     op->tri_variant = v;
+    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+  } else if (!strcmp(name, "stencil_kernel")) {
+    // stencil of the fused FP32 iteration: 0 the register window, 1 and 2 the
+    // rows of p staged in shared memory by bulk copies (16 or 8 rows per CTA)
+    const int v = (int)value;
+    if ((double)v != value || v < 0 || v >= kStencilVariants) return AX_ERR_INVALID_ARG;
+    if (v != 0 && !tc_flag(op->device)) return AX_ERR_OOM;
+    op->st_variant = v;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "cheb_bounds")) {
     if (value != -1.0 && value != 0.0 && value != 1.0) return AX_ERR_INVALID_ARG;
@@ -2703,10 +2750,17 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
   const int blocks = (int)std::min<long long>(rows, 65535);
   note_launch();
   dense_to_padded<T><<<blocks, 256, 0, s>>>(in, a, rows, op->nz, op->pitch);
+  bool staged = false;  // the staged stencil runs bounded waits
   if (which == 0) {
     StencilArgs<T> sa = stencil_args<T>(op, m, nullptr, -1);
     sa.in = a;
     sa.out = b;
+    if (sizeof(T) == 4 && op->st_variant != 0) {
+      sa.variant = op->st_variant;
+      sa.err = tc_flag(op->device);
+      staged = sa.err != nullptr;
+      stencil_stall(op, sa);
+    }
     launch_stencil<T>(kStencilApply, sa, s);
   } else if (which == 1) {
     if constexpr (sizeof(T) == 4) {
@@ -2774,14 +2828,14 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
   note_launch();
   padded_to_dense<T><<<blocks, 256, 0, s>>>(b, out, rows, op->nz, op->pitch);
   AX_CHECK_LAUNCH();
-  if (tc) {
+  if (tc || staged) {
     int *flag = tc_flag(op->device), hf = 0;
     if (flag) {
       AX_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
       AX_TRY(cudaStreamSynchronize(s));
       if (hf) {
         AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
-        snprintf(g_last_error, sizeof(g_last_error), "tensor-core transform: a bounded wait expired");
+        snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of a tensor-core transform or a staged stencil expired");
         return AX_ERR_TIMEOUT;
       }
     }
@@ -2932,7 +2986,6 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   AX_CHECK_LAUNCH();
   const int nbs64 = stencil_blocks_per_rhs(nr, nz, 2);
   const bool cheb = (method == AX_CHEB_FP64 || method == AX_CHEB_MIXED);
-  int outer_kind = 0;
   // Chebyshev bounds from a Lanczos estimate where they are needed (see
   // cheb_estimate); its PCG steps count as iterations of this solve
   std::vector<int> lz_steps;
@@ -2985,7 +3038,6 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     rc = finish_info(op, m, w->st, info, 0, accepted, s);
   } else {
     // ---- mixed precision
-    outer_kind = 1;
     if ((rc = ensure_vec32(op, m, cheb)) != AX_OK) return rc;
     if (op->dst_tc) {
       // buffers and tables before any graph capture
@@ -3073,6 +3125,10 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     AX_TRY(cudaMemcpyAsync(u, ud, dense * sizeof(double), cudaMemcpyDeviceToHost, s));
     AX_TRY(cudaStreamSynchronize(s));
   }
+  if (w->st_stall_used) {  // the graphs hold the stalled stencil of a test
+    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
+    w->st_stall_used = 0;
+  }
   if (op->dst_tc) {
     // a bounded wait of the tensor-core transform expired: report and re-arm
     int *flag = tc_flag(op->device), hf = 0;
@@ -3081,7 +3137,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
       AX_TRY(cudaStreamSynchronize(s));
       if (hf) {
         AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
-        snprintf(g_last_error, sizeof(g_last_error), "tensor-core transform: a bounded wait expired");
+        snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of a tensor-core transform or a staged stencil expired");
         return AX_ERR_TIMEOUT;
       }
     }
@@ -3267,6 +3323,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     gop->plan = o->plan;
     gop->dst_tc = o->dst_tc;
     gop->tri_variant = o->tri_variant;
+    gop->st_variant = o->st_variant;
     gop->cstride = (long long)o->nr * o->pitch;
     gop->czstride = (long long)o->nr * o->pitchz;
     gop->estride = o->nr;
@@ -3373,7 +3430,7 @@ int ax_batch_autotune(ax_batch *b, int32_t reps, void *stream) {
 }
 
 int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, int32_t *members, int32_t *dst_tensor,
-                    int32_t *mode_kernel) {
+                    int32_t *mode_kernel, int32_t *stencil_kernel) {
   if (!b || group < 0 || group >= (int)b->groups.size()) return AX_ERR_INVALID_ARG;
   const ax::BatchGroup &g = b->groups[group];
   if (nr) *nr = g.gop->nr;
@@ -3382,6 +3439,7 @@ int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, 
   if (dst_tensor) *dst_tensor = g.gop->dst_tc;
   if (mode_kernel) *mode_kernel = ax::tridiag_effective(g.gop->nr, g.gop->tri_variant, (int)g.members.size(),
                                                          g.gop->c32.IPS != nullptr);
+  if (stencil_kernel) *stencil_kernel = g.gop->st_variant;
   return AX_OK;
 }
 

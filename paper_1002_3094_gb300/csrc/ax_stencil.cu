@@ -231,6 +231,176 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   }
 }
 
+// ---- q = A p with the rows of p staged by bulk copies (fused FP32 iteration;
+// also y -> A y) --------------------------------------------------------------
+// The register-window kernel keeps about one row of DRAM loads in flight per
+// thread, and ncu shows it waiting on them (long scoreboard).  Here one thread
+// issues, as the CTA starts, one bulk copy (cp.async.bulk) per row of the
+// CTA's strip of p, its R rows and the halo row on each side, each completing
+// on its own mbarrier: the CTA has R + 2 row strips of reads in flight at
+// once, moved by the copy engine without registers.  The threads then walk
+// down the rows with the same register window, taking each row of p from
+// shared memory once its barrier has completed; the coefficient rows
+// (L2-resident, shared by all right-hand sides of an operator) are still
+// loaded one row ahead.  Waits are bounded: on expiry a thread sets *err and
+// stops, and thread 0 waits (bounded) for every copy before the CTA exits.
+constexpr int kBulkBarBytes = 256;            // room for the mbarriers of up to 32 rows
+constexpr unsigned kBulkPolls = 1u << 22;
+
+__host__ __device__ constexpr int bulk_rows(int variant) { return variant == 2 ? 8 : 16; }
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(256) stencil_bulk_kernel(const StencilArgs<float> a) {
+  static_assert(MODE == kStencilPcgP || MODE == kStencilApply, "modes without a second input field");
+  static_assert((R + 2) * 8 <= kBulkBarBytes, "barrier area");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[8];
+  const int m = blockIdx.x;
+  if (!rhs_selected(a.st, a.mask, m)) return;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  float *rows = reinterpret_cast<float *>(smem + kBulkBarBytes);
+  const int W = blockDim.x * 4;  // strip width (floats)
+  const int lane = threadIdx.x & 31;
+  const int c = threadIdx.x * 4;
+  const int ks = blockIdx.z * W;
+  const int k0 = ks + c;
+  const int nr = a.nr, nz = a.nz;
+  const int i0 = blockIdx.y * R, i1 = min(i0 + R, nr);
+  const int ilo = max(i0 - 1, 0), ihi = min(i1, nr - 1);  // staged rows
+  const size_t base = (size_t)m * (size_t)a.field;
+  const float *src = MODE == kStencilApply ? a.in : ((a.st[m].iters & 1) ? a.pa : a.pb);
+  const float *__restrict__ CR = a.CR + (size_t)m * a.cstride;
+  const float *__restrict__ CZ = a.CZ + (size_t)m * a.czstride;
+  const float *__restrict__ Wc = a.W + (size_t)m * a.cstride;
+  const unsigned polls = a.polls ? a.polls : kBulkPolls;
+  // whole padded rows: pitch - ks is a multiple of 32 floats (128 bytes), the
+  // source and destination addresses are 16-byte aligned
+  const unsigned bytes = (unsigned)min(W, a.pitch - ks) * 4u;
+  if (threadIdx.x == 0) {
+    for (int j = 0; j <= ihi - ilo; ++j) mbar_init(&bar[j], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !a.stall)
+    for (int i = ilo; i <= ihi; ++i) {
+      mbar_arrive_tx(&bar[i - ilo], bytes);
+      bulk_g2s(rows + (size_t)(i - ilo) * W, src + base + (size_t)i * a.pitch + ks, bytes, &bar[i - ilo]);
+    }
+  const bool col_ok = k0 < nz;
+  bool ok = true;
+  // row i of p (zero outside the grid and beyond nz), once its copy has landed
+  auto get_row = [&](int i, float (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 0.f;
+    if (i < 0 || i >= nr || !col_ok || !ok) return;
+    if (!mbar_wait(&bar[i - ilo], 0u, polls)) {
+      ok = false;
+      atomicExch(a.err, 1);
+      return;
+    }
+    const float4 t = *reinterpret_cast<const float4 *>(rows + (size_t)(i - ilo) * W + c);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (k0 + e < nz) ? v[e] : 0.f;
+  };
+  auto load_coef = [&](const float *cf, int i, float (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 0.f;
+    if (col_ok) load_vec<float>(cf + (size_t)i * a.pitch + k0, v);
+  };
+  auto load_cz = [&](int i, float (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 0.f;
+    if (k0 <= nz) load_vec<float>(CZ + (size_t)i * a.pitchz + k0, v);
+  };
+  // upper face of the lane's last node (lane 31 only; the others shuffle it)
+  auto load_czlast = [&](int i) {
+    return (lane == 31 && k0 + 4 <= nz) ? CZ[(size_t)i * a.pitchz + k0 + 4] : 0.f;
+  };
+  float pm[4], pc[4], pn[4], crl[4], crh[4], czl[4], w[4];
+  if (i0 > 0) {
+    get_row(i0 - 1, pm);
+    load_coef(CR, i0 - 1, crl);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) pm[e] = crl[e] = 0.f;
+  }
+  get_row(i0, pc);
+  load_coef(CR, i0, crh);
+  load_cz(i0, czl);
+  load_coef(Wc, i0, w);
+  float czlast = load_czlast(i0);
+  float acc = 0.f;
+  for (int i = i0; i < i1; ++i) {
+    float crn[4], czn[4], wn[4], czlastn = 0.f;
+    if (i + 1 < i1) {
+      load_coef(CR, i + 1, crn);
+      load_cz(i + 1, czn);
+      load_coef(Wc, i + 1, wn);
+      czlastn = load_czlast(i + 1);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) crn[e] = czn[e] = wn[e] = 0.f;
+    }
+    get_row(i + 1, pn);
+    // z-neighbours: shuffles inside the warp; the warp-edge lanes read the
+    // neighbouring warp's column from shared memory, or the next strip's from
+    // global memory at the strip edges
+    float l = __shfl_up_sync(0xffffffffu, pc[3], 1);
+    float r = __shfl_down_sync(0xffffffffu, pc[0], 1);
+    float czh_last = __shfl_down_sync(0xffffffffu, czl[0], 1);
+    if (lane == 0) {
+      l = 0.f;
+      if (col_ok && ok && k0 > 0)
+        l = c > 0 ? rows[(size_t)(i - ilo) * W + c - 1] : src[base + (size_t)i * a.pitch + k0 - 1];
+    }
+    if (lane == 31) {
+      r = 0.f;
+      if (col_ok && ok && k0 + 4 < nz)
+        r = c + 4 < W ? rows[(size_t)(i - ilo) * W + c + 4] : src[base + (size_t)i * a.pitch + k0 + 4];
+      czh_last = czlast;
+    }
+    float o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float yl = (e == 0) ? l : pc[e - 1];
+      const float yr = (e == 3) ? r : pc[e + 1];
+      const float czh = (e == 3) ? czh_last : czl[e + 1];
+      const float y = pc[e];
+      float v = w[e] * y;
+      v = fmaf(crh[e], y - pn[e], v);
+      v = fmaf(crl[e], y - pm[e], v);
+      v = fmaf(czh, y - yr, v);
+      v = fmaf(czl[e], y - yl, v);
+      o[e] = (k0 + e < nz) ? v : 0.f;
+    }
+    if (col_ok) {
+      store_vec<float>(a.out + base + (size_t)i * a.pitch + k0, o);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc = fmaf(pc[e], o[e], acc);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      pm[e] = pc[e];
+      pc[e] = pn[e];
+      crl[e] = crh[e];
+      crh[e] = crn[e];
+      czl[e] = czn[e];
+      w[e] = wn[e];
+    }
+    czlast = czlastn;
+  }
+  // no copy may still be writing shared memory when the CTA exits
+  if (threadIdx.x == 0 && !a.stall)
+    for (int j = 0; j <= ihi - ilo; ++j)
+      if (!mbar_wait(&bar[j], 0u, polls)) atomicExch(a.err, 1);
+  if (MODE == kStencilPcgP && a.partial != nullptr) {
+    const double sm = block_sum((double)acc, red);
+    if (threadIdx.x == 0)
+      a.partial[(size_t)m * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = sm;
+  }
+}
+
 // ---- double-float residual -------------------------------------------------
 // Pairs (h, l) of FP32 numbers carry about 48 significant bits: sums by Knuth's
 // two-sum and Dekker's fast two-sum, products by the FMA two-product (the exact
@@ -351,16 +521,37 @@ int column_warps(int nz, int vec) {
 
 }  // namespace
 
-int stencil_blocks_per_rhs(int nr, int nz, int vec) {
+int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant) {
   const int wx = column_warps(nz, vec);
+  const int rows = variant == 0 ? kStencilRows : bulk_rows(variant);
   const int gz = (nz + 32 * vec * wx - 1) / (32 * vec * wx);
-  const int gy = (nr + kStencilRows - 1) / kStencilRows;
+  const int gy = (nr + rows - 1) / rows;
   return gy * gz;
+}
+
+template <int R, int MODE>
+void launch_stencil_bulk(const StencilArgs<float> &a, cudaStream_t s) {
+  const int wx = column_warps(a.nz, 4);
+  const int W = 128 * wx;
+  const size_t smem = kBulkBarBytes + (size_t)(R + 2) * W * sizeof(float);
+  ensure_smem_attr((const void *)stencil_bulk_kernel<R, MODE>, smem);
+  dim3 grid(a.m, (a.nr + R - 1) / R, (a.nz + W - 1) / W);
+  note_launch();
+  stencil_bulk_kernel<R, MODE><<<grid, 32 * wx, smem, s>>>(a);
 }
 
 template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
   constexpr int V = VecT<T>::n;
+  if constexpr (sizeof(T) == 4) {
+    if ((mode == kStencilPcgP || mode == kStencilApply) && a.variant != 0 && a.err != nullptr) {
+      if (mode == kStencilPcgP)
+        a.variant == 2 ? launch_stencil_bulk<8, kStencilPcgP>(a, s) : launch_stencil_bulk<16, kStencilPcgP>(a, s);
+      else
+        a.variant == 2 ? launch_stencil_bulk<8, kStencilApply>(a, s) : launch_stencil_bulk<16, kStencilApply>(a, s);
+      return;
+    }
+  }
   const int wx = column_warps(a.nz, V);
   dim3 grid(a.m, (a.nr + kStencilRows - 1) / kStencilRows, (a.nz + 32 * V * wx - 1) / (32 * V * wx));
   dim3 block(32 * wx);

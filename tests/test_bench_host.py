@@ -41,11 +41,27 @@ def test_function_text_is_one_global_function():
 
 
 def test_traffic_row_applies_only_to_the_source_it_was_measured_on(tmp_path, monkeypatch):
-    table = tmp_path / "traffic.md"
-    table.write_text("| class | DRAM bytes / unknown | source sha | kernel |\n|---|---:|---|---|\n"
-                     f"| stencil | 6.5 | `{B.source_hash('stencil')}` | `stencil_kernel` |\n"
-                     "| pcg_update | 12.0 | `0000000000000000` | `pcg_update` |\n")
+    table = tmp_path / "traffic.json"
+    table.write_text(json.dumps({"entries": [
+        {"class": "stencil", "dram_bytes_per_unknown": 6.5, "source_sha": B.source_hash("stencil")},
+        {"class": "pcg_update", "dram_bytes_per_unknown": 12.0, "source_sha": "0000000000000000"}]}))
     monkeypatch.setattr(B, "TRAFFIC_TABLE", str(table))
     assert B.measured_traffic("stencil", 1000.0) == pytest.approx(6500.0)
     assert B.measured_traffic("pcg_update", 1000.0) is None  # recorded on other code
     assert B.measured_traffic("mode_solve", 1000.0) is None  # never recorded
+    assert B.measured_traffic("stencil_staged", 1000.0) is None
+    table.write_text("not json")
+    assert B.measured_traffic("stencil", 1000.0) is None
+
+
+def test_kernel_class_follows_the_kernels_the_solve_ran():
+    assert B.kernel_class("dst_inverse", True, True, 9, 0) == "dst_inverse_tc"
+    assert B.kernel_class("dst_inverse", False, False, 9, 0) == "dst_inverse"
+    assert B.kernel_class("mode_solve", True, True, 9, 0) == "mode_solve_scaled"
+    assert B.kernel_class("mode_solve", True, True, 1, 0) == "mode_solve"
+    assert B.kernel_class("mode_solve", True, True, 0, 0) == "mode_solve_tall"
+    assert B.kernel_class("mode_solve", True, True, 5, 0) == "mode_solve_pipe"
+    assert B.kernel_class("stencil", True, True, 9, 1) == "stencil_staged"
+    assert B.kernel_class("stencil", True, False, 9, 1) == "stencil"
+    for c in ("stencil_staged", "mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe"):
+        assert len(B.source_hash(c)) == 16 and B.source_hash(c) != B.source_hash("stencil")
