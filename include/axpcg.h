@@ -211,7 +211,10 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    (default) a register window down the rows, 1 and 2 the
  *                    rows of p staged in shared memory by bulk copies, 16 or 8
  *                    rows per CTA (bounded waits: an expiry makes the solve
- *                    return AX_ERR_TIMEOUT)
+ *                    return AX_ERR_TIMEOUT), 3 the register window over two
+ *                    right-hand sides per thread (one coefficient load for
+ *                    both; operators with per-right-hand-side tables use 0).
+ *                    Also selects the kernel of ax_apply_operator (FP32)
  *   "cheb_bounds"    Chebyshev bounds gamma_1, gamma_2 (Eq. energy_rel): 0 the
  *                    face-wise bounds (min / max of kappa / kappa~ and q / q~),
  *                    1 a Lanczos estimate from "cheb_steps" PCG steps (the

@@ -401,6 +401,187 @@ __global__ void __launch_bounds__(256) stencil_bulk_kernel(const StencilArgs<flo
   }
 }
 
+// ---- q = A p for two right-hand sides per thread (FP32; the fused iteration's
+// q = A p and y -> A y) ---------------------------------------------------------
+// The coefficient rows (CR, CZ, W) are the same for every right-hand side of
+// one operator.  A thread that applies the stencil at the same nodes of two
+// right-hand sides loads each coefficient row once for both, and keeps two
+// independent rows of p in flight instead of one.  CTA tile, partial-sum
+// layout (one partial per right-hand side and tile) and the arithmetic per
+// node are those of the register-window kernel, so the results are the same
+// bit for bit.  Operators whose tables differ per right-hand side (stacked
+// batch groups) take the register-window kernel.
+template <int MODE>
+__global__ void __launch_bounds__(256, 3) stencil_pair_kernel(const StencilArgs<float> a) {
+  static_assert(MODE == kStencilPcgP || MODE == kStencilApply, "modes without a second input field");
+  __shared__ double red[8];
+  const int m0 = 2 * blockIdx.x;
+  const bool sel0 = rhs_selected(a.st, a.mask, m0);
+  const bool sel1 = m0 + 1 < a.m && rhs_selected(a.st, a.mask, m0 + 1);
+  if (!sel0 && !sel1) return;
+  const bool sel[2] = {sel0, sel1};
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int k0 = ((blockIdx.z * nwarps + warp) * 32 + lane) * 4;
+  const int nr = a.nr, nz = a.nz;
+  const int i0 = blockIdx.y * kStencilRows;
+  const int i1 = min(i0 + kStencilRows, nr);
+  const bool col_ok = k0 < nz;
+  const float *src[2];
+  size_t base[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    base[j] = (size_t)(m0 + j) * (size_t)a.field;
+    src[j] = a.in;
+    if (MODE == kStencilPcgP && sel[j]) src[j] = (a.st[m0 + j].iters & 1) ? a.pa : a.pb;
+  }
+  const float *__restrict__ CR = a.CR;
+  const float *__restrict__ CZ = a.CZ;
+  const float *__restrict__ Wc = a.W;
+
+  auto load_row = [&](int j, int i, float (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 0.f;
+    if (!col_ok || !sel[j]) return;
+    load_vec<float>(src[j] + base[j] + (size_t)i * a.pitch + k0, v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (k0 + e < nz) ? v[e] : 0.f;
+  };
+  auto load_coef = [&](const float *c, int i, float (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 0.f;
+    if (col_ok) load_vec<float>(c + (size_t)i * a.pitch + k0, v);
+  };
+  auto load_cz = [&](int i, float (&v)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = 0.f;
+    if (k0 <= nz) load_vec<float>(CZ + (size_t)i * a.pitchz + k0, v);
+  };
+  auto load_halo = [&](int i, float (&left)[2], float (&right)[2], float &czlast) {
+    left[0] = left[1] = right[0] = right[1] = czlast = 0.f;
+    if (lane == 0 && col_ok && k0 > 0) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (sel[j]) left[j] = src[j][base[j] + (size_t)i * a.pitch + k0 - 1];
+    }
+    if (lane == 31) {
+      if (k0 + 4 < nz) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          if (sel[j]) right[j] = src[j][base[j] + (size_t)i * a.pitch + k0 + 4];
+      }
+      if (k0 + 4 <= nz) czlast = CZ[(size_t)i * a.pitchz + k0 + 4];
+    }
+  };
+
+  if (col_ok)
+    for (int i = max(i0 - 1, 0); i <= i1 && i < nr; ++i) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (sel[j]) prefetch_l2(src[j] + base[j] + (size_t)i * a.pitch + k0);
+    }
+  float pm[2][4], pc[2][4], pn[2][4], crl[4], crh[4], czl[4], w[4];
+  float left[2], right[2], czlast;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (i0 > 0) {
+      load_row(j, i0 - 1, pm[j]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) pm[j][e] = 0.f;
+    }
+    load_row(j, i0, pc[j]);
+  }
+  if (i0 > 0) {
+    load_coef(CR, i0 - 1, crl);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) crl[e] = 0.f;
+  }
+  load_coef(CR, i0, crh);
+  load_cz(i0, czl);
+  load_coef(Wc, i0, w);
+  load_halo(i0, left, right, czlast);
+
+  float acc[2] = {0.f, 0.f};
+  for (int i = i0; i < i1; ++i) {
+    float crn[4], czn[4], wn[4], leftn[2] = {0.f, 0.f}, rightn[2] = {0.f, 0.f}, czlastn = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (i + 1 < nr) {
+        load_row(j, i + 1, pn[j]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pn[j][e] = 0.f;
+      }
+    }
+    if (i + 1 < i1) {
+      load_coef(CR, i + 1, crn);
+      load_cz(i + 1, czn);
+      load_coef(Wc, i + 1, wn);
+      load_halo(i + 1, leftn, rightn, czlastn);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) crn[e] = czn[e] = wn[e] = 0.f;
+    }
+    float czh_last = __shfl_down_sync(0xffffffffu, czl[0], 1);
+    if (lane == 31) czh_last = czlast;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float l = __shfl_up_sync(0xffffffffu, pc[j][3], 1);
+      float r = __shfl_down_sync(0xffffffffu, pc[j][0], 1);
+      if (lane == 0) l = left[j];
+      if (lane == 31) r = right[j];
+      float o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float yl = (e == 0) ? l : pc[j][e - 1];
+        const float yr = (e == 3) ? r : pc[j][e + 1];
+        const float czh = (e == 3) ? czh_last : czl[e + 1];
+        const float y = pc[j][e];
+        float v = w[e] * y;
+        v = fmaf(crh[e], y - pn[j][e], v);
+        v = fmaf(crl[e], y - pm[j][e], v);
+        v = fmaf(czh, y - yr, v);
+        v = fmaf(czl[e], y - yl, v);
+        o[e] = (k0 + e < nz) ? v : 0.f;
+      }
+      if (col_ok && sel[j]) {
+        store_vec<float>(a.out + base[j] + (size_t)i * a.pitch + k0, o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j] = fmaf(pc[j][e], o[e], acc[j]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        pm[j][e] = pc[j][e];
+        pc[j][e] = pn[j][e];
+      }
+      crl[e] = crh[e];
+      crh[e] = crn[e];
+      czl[e] = czn[e];
+      w[e] = wn[e];
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      left[j] = leftn[j];
+      right[j] = rightn[j];
+    }
+    czlast = czlastn;
+  }
+  if (MODE == kStencilPcgP && a.partial != nullptr) {  // uniform over the CTA
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double sm = block_sum((double)acc[j], red);
+      if (threadIdx.x == 0 && sel[j])
+        a.partial[(size_t)(m0 + j) * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = sm;
+    }
+  }
+}
+
 // ---- double-float residual -------------------------------------------------
 // Pairs (h, l) of FP32 numbers carry about 48 significant bits: sums by Knuth's
 // two-sum and Dekker's fast two-sum, products by the FMA two-product (the exact
@@ -523,7 +704,7 @@ int column_warps(int nz, int vec) {
 
 int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant) {
   const int wx = column_warps(nz, vec);
-  const int rows = variant == 0 ? kStencilRows : bulk_rows(variant);
+  const int rows = (variant == 1 || variant == 2) ? bulk_rows(variant) : kStencilRows;
   const int gz = (nz + 32 * vec * wx - 1) / (32 * vec * wx);
   const int gy = (nr + rows - 1) / rows;
   return gy * gz;
@@ -544,7 +725,17 @@ template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
   constexpr int V = VecT<T>::n;
   if constexpr (sizeof(T) == 4) {
-    if ((mode == kStencilPcgP || mode == kStencilApply) && a.variant != 0 && a.err != nullptr) {
+    if ((mode == kStencilPcgP || mode == kStencilApply) && a.variant == 3 && a.cstride == 0 && a.czstride == 0) {
+      const int wx = column_warps(a.nz, V);
+      dim3 grid((a.m + 1) / 2, (a.nr + kStencilRows - 1) / kStencilRows, (a.nz + 32 * V * wx - 1) / (32 * V * wx));
+      note_launch();
+      if (mode == kStencilPcgP)
+        stencil_pair_kernel<kStencilPcgP><<<grid, 32 * wx, 0, s>>>(a);
+      else
+        stencil_pair_kernel<kStencilApply><<<grid, 32 * wx, 0, s>>>(a);
+      return;
+    }
+    if ((mode == kStencilPcgP || mode == kStencilApply) && (a.variant == 1 || a.variant == 2) && a.err != nullptr) {
       if (mode == kStencilPcgP)
         a.variant == 2 ? launch_stencil_bulk<8, kStencilPcgP>(a, s) : launch_stencil_bulk<16, kStencilPcgP>(a, s);
       else

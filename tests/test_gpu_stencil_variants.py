@@ -2,12 +2,13 @@
 through the C ABI.
 
 The operator of Eq. scheme_op_r_z (Section 2.1) is applied by the register-
-window kernel (0) or by the kernels that stage the rows of their input in
-shared memory with bulk copies, 16 (1) or 8 (2) rows per CTA.  Each must give
+window kernel (0), by the kernels that stage the rows of their input in
+shared memory with bulk copies, 16 (1) or 8 (2) rows per CTA, or by the
+register window over two right-hand sides per thread (3).  Each must give
   - y -> A y in FP32 within 2e-6 of the oracle's FP64 A y, and bit for bit
     the register kernel's result (the same FMAs in the same order per node);
   - in the fused mixed PCG iteration (q = A p with the (p, q) partials), an
-    oracle FP64 true residual <= 1e-8, with variant 1 taking the same
+    oracle FP64 true residual <= 1e-8, with variants 1 and 3 taking the same
     iterations as variant 0 (same CTA partition, so identical partials);
   - on the expiry path (option "stencil_stall_test": no copy is issued, every
     bounded wait runs out) AX_ERR_TIMEOUT, and a correct result from the next
@@ -57,18 +58,18 @@ def _apply(op, y, dev):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("nr,nz", [(1, 7), (5, 3), (17, 130), (40, 1024), (33, 1030), (100, 2051), (250, 4096),
-                                   (1031, 96)])
-def test_apply_matches_oracle_and_register_kernel(cuda, nr, nz):
+@pytest.mark.parametrize("nr,nz,m", [(1, 7, 2), (5, 3, 3), (17, 130, 2), (40, 1024, 1), (33, 1030, 3), (100, 2051, 2),
+                                     (250, 4096, 2), (1031, 96, 3)])
+def test_apply_matches_oracle_and_register_kernel(cuda, nr, nz, m):
     op, ora, _ = _setup(nr, nz, cuda)
-    y = np.random.default_rng(nr * 7 + nz).normal(size=(2, nr, nz))
+    y = np.random.default_rng(nr * 7 + nz).normal(size=(m, nr, nz))
     ref = _apply(op, y, cuda)
-    for v in (1, 2):
+    for v in (1, 2, 3):
         P.ax_set_option(op, "stencil_kernel", v)
         assert int(P.ax_get_option(op, "stencil_kernel")) == v
         got = _apply(op, y, cuda)
         assert np.array_equal(got, ref), (v, np.abs(got - ref).max())
-        for j in range(2):
+        for j in range(m):
             assert _rel(got[j], ora.apply_A(y[j])) <= 2e-6
     P.ax_destroy_operator(op)
 
@@ -80,7 +81,7 @@ def test_fused_mixed_pcg(cuda, nr, nz):
     fd = torch.from_numpy(f).to(cuda)
     P.ax_set_option(op, "dst_tensor", 1)
     iters = {}
-    for v in (0, 1, 2):
+    for v in (0, 1, 2, 3):
         P.ax_set_option(op, "stencil_kernel", v)
         u = torch.zeros_like(fd)
         st, info = P.ax_solve(op, fd, u, 3, 1e-8, 5000, P.AX_PCG_MIXED)
@@ -91,14 +92,14 @@ def test_fused_mixed_pcg(cuda, nr, nz):
         for j in range(3):
             phi = ora.phi(f[j])
             assert np.linalg.norm(phi - ora.apply_A(un[j])) <= 1e-8 * np.linalg.norm(phi), (v, j)
-    assert iters[1] == iters[0], iters
+    assert iters[1] == iters[0] and iters[3] == iters[0], iters
     assert all(abs(a - b) <= 2 for a, b in zip(iters[2], iters[0])), iters
     P.ax_destroy_operator(op)
 
 
 def test_option_values(cuda):
     op, _, _ = _setup(64, 64, cuda)
-    assert P.ax_set_option(op, "stencil_kernel", 3, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+    assert P.ax_set_option(op, "stencil_kernel", 4, raise_on_error=False) == P.AX_ERR_INVALID_ARG
     assert P.ax_set_option(op, "stencil_kernel", 0.5, raise_on_error=False) == P.AX_ERR_INVALID_ARG
     assert int(P.ax_get_option(op, "stencil_kernel")) == 0
     P.ax_destroy_operator(op)
