@@ -62,7 +62,7 @@ TC_CLASSES = ("dst_forward", "dst_inverse")
 # (file, __global__ function or None for the whole file), plus the shared
 # device helpers.
 KERNEL_SOURCES = {"stencil": [("ax_stencil.cu", "stencil_kernel")],
-                  "stencil_staged": [("ax_stencil.cu", "stencil_bulk_kernel")],
+                  "stencil_ring": [("ax_stencil.cu", "stencil_ring_kernel")],
                   "dst_forward": [("ax_dst_impl.cuh", None)],
                   "dst_inverse": [("ax_dst_impl.cuh", None)],
                   "dst_forward_tc": [("ax_dst_gemm.cu", None)],
@@ -131,7 +131,7 @@ def kernel_class(top: str, tc_path: bool, fused: bool, mode_eff: int, stencil_v:
             return "mode_solve_tall"
         return MODE_CLASSES.get(mode_eff, "mode_solve_pipe")
     if top == "stencil" and fused and stencil_v != 0:
-        return "stencil_staged"
+        return "stencil_ring"
     return top
 
 

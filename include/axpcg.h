@@ -207,14 +207,12 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    column-tile kernels on the row-scaled systems; an id
  *                    whose column does not fit nr is refused
  *   "stencil_kernel" stencil (Eq. scheme_op_r_z) of the fused FP32 iteration
- *                    (AX_PCG_MIXED with the tensor-core transform): 0
- *                    (default) a register window down the rows, 1 and 2 the
- *                    rows of p staged in shared memory by bulk copies, 16 or 8
- *                    rows per CTA (bounded waits: an expiry makes the solve
- *                    return AX_ERR_TIMEOUT), 3 the register window over two
- *                    right-hand sides per thread (one coefficient load for
- *                    both; operators with per-right-hand-side tables use 0).
- *                    Also selects the kernel of ax_apply_operator (FP32)
+ *                    (AX_PCG_MIXED with the tensor-core transform) and of
+ *                    ax_apply_operator in FP32: 0 (default) a register window
+ *                    down the rows, 1 p and the coefficient rows streamed
+ *                    through a ring of shared-memory slots by bulk copies
+ *                    (bounded waits: an expiry makes the call return
+ *                    AX_ERR_TIMEOUT)
  *   "cheb_bounds"    Chebyshev bounds gamma_1, gamma_2 (Eq. energy_rel): 0 the
  *                    face-wise bounds (min / max of kappa / kappa~ and q / q~),
  *                    1 a Lanczos estimate from "cheb_steps" PCG steps (the

@@ -198,12 +198,11 @@ struct StencilArgs {
   const RhsState *st;    // per RHS state (Pcg reads beta)
   int mask;
   double *partial;       // [m][kPartialStride] per-CTA sums: Pcg (p,q); Residual, Cheb ||res||^2
-  int variant;           // PcgP and Apply, FP32: 0 register window; 1, 2 rows of p staged in
-                         // shared memory by bulk copies, 16 or 8 rows per CTA; 3 the
-                         // register window over two right-hand sides per thread
-  int *err;              // variants 1, 2: set when a bounded wait expired
-  unsigned polls;        // variants 1, 2: wait limit (0: the default)
-  int stall;             // variants 1, 2, test of the expiry path: no copy is issued, so
+  int variant;           // PcgP and Apply, FP32: 0 register window; 1 p and the coefficient
+                         // rows streamed through a ring of bulk copies (needs err)
+  int *err;              // variant 1: set when a bounded wait expired
+  unsigned polls;        // variant 1: wait limit (0: the default)
+  int stall;             // variant 1, test of the expiry path: no copy is issued, so
                          // every wait runs out (with a short `polls`)
 };
 
@@ -211,7 +210,7 @@ template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s);
 // CTAs (and partial sums) per right-hand side of a stencil launch
 int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant = 0);
-constexpr int kStencilVariants = 4;
+constexpr int kStencilVariants = 2;
 
 // Double-float true residual r = phi - A x of the mixed method: x, phi and the
 // coefficients as pairs of FP32 numbers (hi + lo), all arithmetic in FP32 with

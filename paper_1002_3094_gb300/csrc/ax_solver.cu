@@ -2466,9 +2466,9 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     op->tri_variant = v;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "stencil_kernel")) {
-    // stencil of the fused FP32 iteration: 0 the register window, 1 and 2 the
-    // rows of p staged in shared memory by bulk copies (16 or 8 rows per CTA),
-    // 3 the register window over two right-hand sides per thread
+    // stencil of the fused FP32 iteration (and of ax_apply_operator in FP32):
+    // 0 the register window, 1 p and the coefficient rows streamed through a
+    // ring of bulk copies
     const int v = (int)value;
     if ((double)v != value || v < 0 || v >= kStencilVariants) return AX_ERR_INVALID_ARG;
     if (v != 0 && !tc_flag(op->device)) return AX_ERR_OOM;

@@ -231,354 +231,204 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   }
 }
 
-// ---- q = A p with the rows of p staged by bulk copies (fused FP32 iteration;
-// also y -> A y) --------------------------------------------------------------
-// The register-window kernel keeps about one row of DRAM loads in flight per
-// thread, and ncu shows it waiting on them (long scoreboard).  Here one thread
-// issues, as the CTA starts, one bulk copy (cp.async.bulk) per row of the
-// CTA's strip of p, its R rows and the halo row on each side, each completing
-// on its own mbarrier: the CTA has R + 2 row strips of reads in flight at
-// once, moved by the copy engine without registers.  The threads then walk
-// down the rows with the same register window, taking each row of p from
-// shared memory once its barrier has completed; the coefficient rows
-// (L2-resident, shared by all right-hand sides of an operator) are still
-// loaded one row ahead.  Waits are bounded: on expiry a thread sets *err and
-// stops, and thread 0 waits (bounded) for every copy before the CTA exits.
-constexpr int kBulkBarBytes = 256;            // room for the mbarriers of up to 32 rows
-constexpr unsigned kBulkPolls = 1u << 22;
+// ---- q = A p through a ring of bulk-copied rows (FP32) -----------------------
+// The register-window kernel waits on its loads (long scoreboard in ncu): each
+// warp has one row of p and of the coefficients in flight and too little work
+// per row to cover an L2 or DRAM round trip.  Here a producer warp streams
+// every input row the CTA needs (p, CR, W and CZ of its column strip) into a
+// ring of S shared-memory slots with bulk copies (cp.async.bulk), with one
+// mbarrier per slot for "full" (the copy bytes have landed) and one for
+// "empty" (every consumer warp has read the slot into registers).  The
+// consumer warps walk down the rows with the same three-row register window
+// and the same arithmetic per node, reading each row from shared memory, so
+// up to S rows per CTA are in flight without holding registers.  Where nz is
+// a multiple of 128 every lane holds four nodes of the grid and the range
+// tests against nz are compiled out (FULL).  Every wait is bounded: on expiry
+// a warp sets *err and stops; the producer then waits (bounded) for the
+// copies it issued before the CTA exits.
+constexpr int kRingRows = 32;   // rows per CTA
+constexpr int kRingSlots = 6;   // ring depth (rows in flight)
+constexpr unsigned kRingPolls = 1u << 22;  // bound of every mbarrier wait
 
-__host__ __device__ constexpr int bulk_rows(int variant) { return variant == 2 ? 8 : 16; }
-
-template <int R, int MODE>
-__global__ void __launch_bounds__(256) stencil_bulk_kernel(const StencilArgs<float> a) {
+template <int MODE, bool FULL>
+__global__ void __launch_bounds__(288) stencil_ring_kernel(const StencilArgs<float> a) {
   static_assert(MODE == kStencilPcgP || MODE == kStencilApply, "modes without a second input field");
-  static_assert((R + 2) * 8 <= kBulkBarBytes, "barrier area");
+  constexpr int S = kRingSlots;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double red[8];
+  __shared__ double red[9];
   const int m = blockIdx.x;
   if (!rhs_selected(a.st, a.mask, m)) return;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-  float *rows = reinterpret_cast<float *>(smem + kBulkBarBytes);
-  const int W = blockDim.x * 4;  // strip width (floats)
-  const int lane = threadIdx.x & 31;
-  const int c = threadIdx.x * 4;
-  const int ks = blockIdx.z * W;
-  const int k0 = ks + c;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *empty = full + S;
+  float *ring = reinterpret_cast<float *>(smem + 128);
+  const int nwc = (blockDim.x >> 5) - 1;  // consumer warps; the last warp is the producer
+  const int W = nwc * 128;                // strip width (floats)
+  const int SW = 4 * W + 4;               // slot: p, CR, W (W floats each), CZ (W + 4 faces)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nr = a.nr, nz = a.nz;
-  const int i0 = blockIdx.y * R, i1 = min(i0 + R, nr);
+  const int i0 = blockIdx.y * kRingRows, i1 = min(i0 + kRingRows, nr);
   const int ilo = max(i0 - 1, 0), ihi = min(i1, nr - 1);  // staged rows
+  const int T = ihi - ilo + 1;
+  const int ks = blockIdx.z * W;
   const size_t base = (size_t)m * (size_t)a.field;
   const float *src = MODE == kStencilApply ? a.in : ((a.st[m].iters & 1) ? a.pa : a.pb);
-  const float *__restrict__ CR = a.CR + (size_t)m * a.cstride;
-  const float *__restrict__ CZ = a.CZ + (size_t)m * a.czstride;
-  const float *__restrict__ Wc = a.W + (size_t)m * a.cstride;
-  const unsigned polls = a.polls ? a.polls : kBulkPolls;
-  // whole padded rows: pitch - ks is a multiple of 32 floats (128 bytes), the
-  // source and destination addresses are 16-byte aligned
-  const unsigned bytes = (unsigned)min(W, a.pitch - ks) * 4u;
+  const float *CR = a.CR + (size_t)m * a.cstride;
+  const float *CZ = a.CZ + (size_t)m * a.czstride;
+  const float *Wc = a.W + (size_t)m * a.cstride;
+  const unsigned polls = a.polls ? a.polls : kRingPolls;
   if (threadIdx.x == 0) {
-    for (int j = 0; j <= ihi - ilo; ++j) mbar_init(&bar[j], 1);
+    for (int k = 0; k < S; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], nwc);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0 && !a.stall)
-    for (int i = ilo; i <= ihi; ++i) {
-      mbar_arrive_tx(&bar[i - ilo], bytes);
-      bulk_g2s(rows + (size_t)(i - ilo) * W, src + base + (size_t)i * a.pitch + ks, bytes, &bar[i - ilo]);
-    }
-  const bool col_ok = k0 < nz;
-  bool ok = true;
-  // row i of p (zero outside the grid and beyond nz), once its copy has landed
-  auto get_row = [&](int i, float (&v)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = 0.f;
-    if (i < 0 || i >= nr || !col_ok || !ok) return;
-    if (!mbar_wait(&bar[i - ilo], 0u, polls)) {
-      ok = false;
-      atomicExch(a.err, 1);
-      return;
-    }
-    const float4 t = *reinterpret_cast<const float4 *>(rows + (size_t)(i - ilo) * W + c);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = (k0 + e < nz) ? v[e] : 0.f;
-  };
-  auto load_coef = [&](const float *cf, int i, float (&v)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = 0.f;
-    if (col_ok) load_vec<float>(cf + (size_t)i * a.pitch + k0, v);
-  };
-  auto load_cz = [&](int i, float (&v)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = 0.f;
-    if (k0 <= nz) load_vec<float>(CZ + (size_t)i * a.pitchz + k0, v);
-  };
-  // upper face of the lane's last node (lane 31 only; the others shuffle it)
-  auto load_czlast = [&](int i) {
-    return (lane == 31 && k0 + 4 <= nz) ? CZ[(size_t)i * a.pitchz + k0 + 4] : 0.f;
-  };
-  float pm[4], pc[4], pn[4], crl[4], crh[4], czl[4], w[4];
-  if (i0 > 0) {
-    get_row(i0 - 1, pm);
-    load_coef(CR, i0 - 1, crl);
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) pm[e] = crl[e] = 0.f;
-  }
-  get_row(i0, pc);
-  load_coef(CR, i0, crh);
-  load_cz(i0, czl);
-  load_coef(Wc, i0, w);
-  float czlast = load_czlast(i0);
   float acc = 0.f;
-  for (int i = i0; i < i1; ++i) {
-    float crn[4], czn[4], wn[4], czlastn = 0.f;
-    if (i + 1 < i1) {
-      load_coef(CR, i + 1, crn);
-      load_cz(i + 1, czn);
-      load_coef(Wc, i + 1, wn);
-      czlastn = load_czlast(i + 1);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) crn[e] = czn[e] = wn[e] = 0.f;
+  if (warp == nwc) {
+    // ---- producer: rows ilo .. ihi into slots t % S
+    if (lane == 0 && !a.stall) {
+      // whole padded rows (pitch - ks and pitchz - ks are multiples of 32
+      // floats); the CZ row takes the 4 faces after the strip too, when the
+      // padded row has them (it always has face ks + W <= nz)
+      const unsigned bp = (unsigned)min(W, a.pitch - ks) * 4u;
+      const unsigned bz = (unsigned)min(W + 4, a.pitchz - ks) * 4u;
+      int t = 0;
+      for (; t < T; ++t) {
+        const int k = t % S;
+        if (t >= S && !mbar_wait(&empty[k], (unsigned)((t / S) - 1) & 1u, polls)) {
+          atomicExch(a.err, 1);
+          break;
+        }
+        const size_t i = (size_t)(ilo + t);
+        float *slot = ring + (size_t)k * SW;
+        mbar_arrive_tx(&full[k], 3u * bp + bz);
+        bulk_g2s(slot, src + base + i * a.pitch + ks, bp, &full[k]);
+        bulk_g2s(slot + W, CR + i * a.pitch + ks, bp, &full[k]);
+        bulk_g2s(slot + 2 * W, Wc + i * a.pitch + ks, bp, &full[k]);
+        bulk_g2s(slot + 3 * W, CZ + i * a.pitchz + ks, bz, &full[k]);
+      }
+      // every issued copy has landed before the CTA may exit
+      for (int u = max(t - S, 0); u < t; ++u)
+        if (!mbar_wait(&full[u % S], (unsigned)(u / S) & 1u, polls)) atomicExch(a.err, 1);
     }
-    get_row(i + 1, pn);
-    // z-neighbours: shuffles inside the warp; the warp-edge lanes read the
-    // neighbouring warp's column from shared memory, or the next strip's from
-    // global memory at the strip edges
-    float l = __shfl_up_sync(0xffffffffu, pc[3], 1);
-    float r = __shfl_down_sync(0xffffffffu, pc[0], 1);
-    float czh_last = __shfl_down_sync(0xffffffffu, czl[0], 1);
-    if (lane == 0) {
-      l = 0.f;
-      if (col_ok && ok && k0 > 0)
-        l = c > 0 ? rows[(size_t)(i - ilo) * W + c - 1] : src[base + (size_t)i * a.pitch + k0 - 1];
-    }
-    if (lane == 31) {
-      r = 0.f;
-      if (col_ok && ok && k0 + 4 < nz)
-        r = c + 4 < W ? rows[(size_t)(i - ilo) * W + c + 4] : src[base + (size_t)i * a.pitch + k0 + 4];
-      czh_last = czlast;
-    }
-    float o[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float yl = (e == 0) ? l : pc[e - 1];
-      const float yr = (e == 3) ? r : pc[e + 1];
-      const float czh = (e == 3) ? czh_last : czl[e + 1];
-      const float y = pc[e];
-      float v = w[e] * y;
-      v = fmaf(crh[e], y - pn[e], v);
-      v = fmaf(crl[e], y - pm[e], v);
+  } else {
+    // ---- consumers
+    const int c = warp * 128 + lane * 4;  // column within the strip
+    const int k0 = ks + c;
+    const bool col_ok = FULL || k0 < nz;
+    bool ok = true;
+    struct Row {
+      float4 p, cr, w, cz;
+      float left, right, czlast;
+    };
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    // staged row t into registers (zeros where the grid ends), then release
+    // its slot
+    auto fetch = [&](int t, Row &r) {
+      const int k = t % S;
+      // warp-uniform outcome (every lane of a consumer warp fetches the same rows)
+      const bool got = __all_sync(0xffffffffu, ok && (mbar_try(&full[k], (unsigned)(t / S) & 1u) ||
+                                                       mbar_wait(&full[k], (unsigned)(t / S) & 1u, polls)));
+      if (!got) {
+        if (ok && lane == 0) atomicExch(a.err, 1);
+        ok = false;
+        r.p = r.cr = r.w = r.cz = zero;
+        r.left = r.right = r.czlast = 0.f;
+        return;
+      }
+      const float *slot = ring + (size_t)k * SW;
+      const int i = ilo + t;
+      r.left = r.right = r.czlast = 0.f;
+      if (col_ok) {
+        r.p = *reinterpret_cast<const float4 *>(slot + c);
+        r.cr = *reinterpret_cast<const float4 *>(slot + W + c);
+        r.w = *reinterpret_cast<const float4 *>(slot + 2 * W + c);
+        r.cz = *reinterpret_cast<const float4 *>(slot + 3 * W + c);
+        if (!FULL) {
+          r.p.y = k0 + 1 < nz ? r.p.y : 0.f;
+          r.p.z = k0 + 2 < nz ? r.p.z : 0.f;
+          r.p.w = k0 + 3 < nz ? r.p.w : 0.f;
+        }
+        if (lane == 0 && k0 > 0)
+          r.left = c > 0 ? slot[c - 1] : src[base + (size_t)i * a.pitch + k0 - 1];
+        if (lane == 31) {
+          if (k0 + 4 < nz) r.right = c + 4 < W ? slot[c + 4] : src[base + (size_t)i * a.pitch + k0 + 4];
+          if (FULL || k0 + 4 <= nz) r.czlast = slot[3 * W + c + 4];
+        }
+      } else {
+        r.p = r.cr = r.w = r.cz = zero;
+        // the lane just past the last node: its first face is the upper face
+        // of node nz - 1, fetched by the shuffle
+        if (k0 <= nz) r.cz.x = slot[3 * W + c];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[k]);
+    };
+    auto node = [](float y, float yl, float yr, float pn, float pm, float wv, float crh, float crl, float czh,
+                   float czl) {
+      float v = wv * y;
+      v = fmaf(crh, y - pn, v);
+      v = fmaf(crl, y - pm, v);
       v = fmaf(czh, y - yr, v);
-      v = fmaf(czl[e], y - yl, v);
-      o[e] = (k0 + e < nz) ? v : 0.f;
+      v = fmaf(czl, y - yl, v);
+      return v;
+    };
+    Row rm, rc, rn;
+    if (i0 > 0) {
+      fetch(0, rm);  // row i0 - 1: p and CR
+    } else {
+      rm.p = rm.cr = zero;
     }
-    if (col_ok) {
-      store_vec<float>(a.out + base + (size_t)i * a.pitch + k0, o);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc = fmaf(pc[e], o[e], acc);
+    fetch(i0 - ilo, rc);
+    auto step = [&](int i) {
+      if (i + 1 <= ihi) {
+        fetch(i + 1 - ilo, rn);
+      } else {
+        rn.p = zero;
+      }
+      float l = __shfl_up_sync(0xffffffffu, rc.p.w, 1);
+      float r = __shfl_down_sync(0xffffffffu, rc.p.x, 1);
+      float czh3 = __shfl_down_sync(0xffffffffu, rc.cz.x, 1);
+      if (lane == 0) l = rc.left;
+      if (lane == 31) {
+        r = rc.right;
+        czh3 = rc.czlast;
+      }
+      float4 o;
+      o.x = node(rc.p.x, l, rc.p.y, rn.p.x, rm.p.x, rc.w.x, rc.cr.x, rm.cr.x, rc.cz.y, rc.cz.x);
+      o.y = node(rc.p.y, rc.p.x, rc.p.z, rn.p.y, rm.p.y, rc.w.y, rc.cr.y, rm.cr.y, rc.cz.z, rc.cz.y);
+      o.z = node(rc.p.z, rc.p.y, rc.p.w, rn.p.z, rm.p.z, rc.w.z, rc.cr.z, rm.cr.z, rc.cz.w, rc.cz.z);
+      o.w = node(rc.p.w, rc.p.z, r, rn.p.w, rm.p.w, rc.w.w, rc.cr.w, rm.cr.w, czh3, rc.cz.w);
+      if (!FULL) {
+        o.y = k0 + 1 < nz ? o.y : 0.f;
+        o.z = k0 + 2 < nz ? o.z : 0.f;
+        o.w = k0 + 3 < nz ? o.w : 0.f;
+      }
+      if (col_ok) {
+        *reinterpret_cast<float4 *>(a.out + base + (size_t)i * a.pitch + k0) = o;
+        if (MODE == kStencilPcgP) {
+          acc = fmaf(rc.p.x, o.x, acc);
+          acc = fmaf(rc.p.y, o.y, acc);
+          acc = fmaf(rc.p.z, o.z, acc);
+          acc = fmaf(rc.p.w, o.w, acc);
+        }
+      }
+      rm = rc;
+      rc = rn;
+    };
+    if (i1 - i0 == kRingRows) {
+#pragma unroll 2
+      for (int j = 0; j < kRingRows; ++j) step(i0 + j);
+    } else {
+#pragma unroll 1
+      for (int i = i0; i < i1; ++i) step(i);
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      pm[e] = pc[e];
-      pc[e] = pn[e];
-      crl[e] = crh[e];
-      crh[e] = crn[e];
-      czl[e] = czn[e];
-      w[e] = wn[e];
-    }
-    czlast = czlastn;
   }
-  // no copy may still be writing shared memory when the CTA exits
-  if (threadIdx.x == 0 && !a.stall)
-    for (int j = 0; j <= ihi - ilo; ++j)
-      if (!mbar_wait(&bar[j], 0u, polls)) atomicExch(a.err, 1);
   if (MODE == kStencilPcgP && a.partial != nullptr) {
     const double sm = block_sum((double)acc, red);
     if (threadIdx.x == 0)
       a.partial[(size_t)m * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = sm;
-  }
-}
-
-// ---- q = A p for two right-hand sides per thread (FP32; the fused iteration's
-// q = A p and y -> A y) ---------------------------------------------------------
-// The coefficient rows (CR, CZ, W) are the same for every right-hand side of
-// one operator.  A thread that applies the stencil at the same nodes of two
-// right-hand sides loads each coefficient row once for both, and keeps two
-// independent rows of p in flight instead of one.  CTA tile, partial-sum
-// layout (one partial per right-hand side and tile) and the arithmetic per
-// node are those of the register-window kernel, so the results are the same
-// bit for bit.  Operators whose tables differ per right-hand side (stacked
-// batch groups) take the register-window kernel.
-template <int MODE>
-__global__ void __launch_bounds__(256, 3) stencil_pair_kernel(const StencilArgs<float> a) {
-  static_assert(MODE == kStencilPcgP || MODE == kStencilApply, "modes without a second input field");
-  __shared__ double red[8];
-  const int m0 = 2 * blockIdx.x;
-  const bool sel0 = rhs_selected(a.st, a.mask, m0);
-  const bool sel1 = m0 + 1 < a.m && rhs_selected(a.st, a.mask, m0 + 1);
-  if (!sel0 && !sel1) return;
-  const bool sel[2] = {sel0, sel1};
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const int k0 = ((blockIdx.z * nwarps + warp) * 32 + lane) * 4;
-  const int nr = a.nr, nz = a.nz;
-  const int i0 = blockIdx.y * kStencilRows;
-  const int i1 = min(i0 + kStencilRows, nr);
-  const bool col_ok = k0 < nz;
-  const float *src[2];
-  size_t base[2];
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    base[j] = (size_t)(m0 + j) * (size_t)a.field;
-    src[j] = a.in;
-    if (MODE == kStencilPcgP && sel[j]) src[j] = (a.st[m0 + j].iters & 1) ? a.pa : a.pb;
-  }
-  const float *__restrict__ CR = a.CR;
-  const float *__restrict__ CZ = a.CZ;
-  const float *__restrict__ Wc = a.W;
-
-  auto load_row = [&](int j, int i, float (&v)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = 0.f;
-    if (!col_ok || !sel[j]) return;
-    load_vec<float>(src[j] + base[j] + (size_t)i * a.pitch + k0, v);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = (k0 + e < nz) ? v[e] : 0.f;
-  };
-  auto load_coef = [&](const float *c, int i, float (&v)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = 0.f;
-    if (col_ok) load_vec<float>(c + (size_t)i * a.pitch + k0, v);
-  };
-  auto load_cz = [&](int i, float (&v)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = 0.f;
-    if (k0 <= nz) load_vec<float>(CZ + (size_t)i * a.pitchz + k0, v);
-  };
-  auto load_halo = [&](int i, float (&left)[2], float (&right)[2], float &czlast) {
-    left[0] = left[1] = right[0] = right[1] = czlast = 0.f;
-    if (lane == 0 && col_ok && k0 > 0) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (sel[j]) left[j] = src[j][base[j] + (size_t)i * a.pitch + k0 - 1];
-    }
-    if (lane == 31) {
-      if (k0 + 4 < nz) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-          if (sel[j]) right[j] = src[j][base[j] + (size_t)i * a.pitch + k0 + 4];
-      }
-      if (k0 + 4 <= nz) czlast = CZ[(size_t)i * a.pitchz + k0 + 4];
-    }
-  };
-
-  if (col_ok)
-    for (int i = max(i0 - 1, 0); i <= i1 && i < nr; ++i) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (sel[j]) prefetch_l2(src[j] + base[j] + (size_t)i * a.pitch + k0);
-    }
-  float pm[2][4], pc[2][4], pn[2][4], crl[4], crh[4], czl[4], w[4];
-  float left[2], right[2], czlast;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    if (i0 > 0) {
-      load_row(j, i0 - 1, pm[j]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) pm[j][e] = 0.f;
-    }
-    load_row(j, i0, pc[j]);
-  }
-  if (i0 > 0) {
-    load_coef(CR, i0 - 1, crl);
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) crl[e] = 0.f;
-  }
-  load_coef(CR, i0, crh);
-  load_cz(i0, czl);
-  load_coef(Wc, i0, w);
-  load_halo(i0, left, right, czlast);
-
-  float acc[2] = {0.f, 0.f};
-  for (int i = i0; i < i1; ++i) {
-    float crn[4], czn[4], wn[4], leftn[2] = {0.f, 0.f}, rightn[2] = {0.f, 0.f}, czlastn = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (i + 1 < nr) {
-        load_row(j, i + 1, pn[j]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) pn[j][e] = 0.f;
-      }
-    }
-    if (i + 1 < i1) {
-      load_coef(CR, i + 1, crn);
-      load_cz(i + 1, czn);
-      load_coef(Wc, i + 1, wn);
-      load_halo(i + 1, leftn, rightn, czlastn);
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) crn[e] = czn[e] = wn[e] = 0.f;
-    }
-    float czh_last = __shfl_down_sync(0xffffffffu, czl[0], 1);
-    if (lane == 31) czh_last = czlast;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      float l = __shfl_up_sync(0xffffffffu, pc[j][3], 1);
-      float r = __shfl_down_sync(0xffffffffu, pc[j][0], 1);
-      if (lane == 0) l = left[j];
-      if (lane == 31) r = right[j];
-      float o[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float yl = (e == 0) ? l : pc[j][e - 1];
-        const float yr = (e == 3) ? r : pc[j][e + 1];
-        const float czh = (e == 3) ? czh_last : czl[e + 1];
-        const float y = pc[j][e];
-        float v = w[e] * y;
-        v = fmaf(crh[e], y - pn[j][e], v);
-        v = fmaf(crl[e], y - pm[j][e], v);
-        v = fmaf(czh, y - yr, v);
-        v = fmaf(czl[e], y - yl, v);
-        o[e] = (k0 + e < nz) ? v : 0.f;
-      }
-      if (col_ok && sel[j]) {
-        store_vec<float>(a.out + base[j] + (size_t)i * a.pitch + k0, o);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[j] = fmaf(pc[j][e], o[e], acc[j]);
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        pm[j][e] = pc[j][e];
-        pc[j][e] = pn[j][e];
-      }
-      crl[e] = crh[e];
-      crh[e] = crn[e];
-      czl[e] = czn[e];
-      w[e] = wn[e];
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      left[j] = leftn[j];
-      right[j] = rightn[j];
-    }
-    czlast = czlastn;
-  }
-  if (MODE == kStencilPcgP && a.partial != nullptr) {  // uniform over the CTA
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const double sm = block_sum((double)acc[j], red);
-      if (threadIdx.x == 0 && sel[j])
-        a.partial[(size_t)(m0 + j) * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = sm;
-    }
   }
 }
 
@@ -704,42 +554,40 @@ int column_warps(int nz, int vec) {
 
 int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant) {
   const int wx = column_warps(nz, vec);
-  const int rows = (variant == 1 || variant == 2) ? bulk_rows(variant) : kStencilRows;
+  const int rows = variant == 1 ? kRingRows : kStencilRows;
   const int gz = (nz + 32 * vec * wx - 1) / (32 * vec * wx);
   const int gy = (nr + rows - 1) / rows;
   return gy * gz;
-}
-
-template <int R, int MODE>
-void launch_stencil_bulk(const StencilArgs<float> &a, cudaStream_t s) {
-  const int wx = column_warps(a.nz, 4);
-  const int W = 128 * wx;
-  const size_t smem = kBulkBarBytes + (size_t)(R + 2) * W * sizeof(float);
-  ensure_smem_attr((const void *)stencil_bulk_kernel<R, MODE>, smem);
-  dim3 grid(a.m, (a.nr + R - 1) / R, (a.nz + W - 1) / W);
-  note_launch();
-  stencil_bulk_kernel<R, MODE><<<grid, 32 * wx, smem, s>>>(a);
 }
 
 template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
   constexpr int V = VecT<T>::n;
   if constexpr (sizeof(T) == 4) {
-    if ((mode == kStencilPcgP || mode == kStencilApply) && a.variant == 3 && a.cstride == 0 && a.czstride == 0) {
+    if ((mode == kStencilPcgP || mode == kStencilApply) && a.variant == 1 && a.err != nullptr) {
       const int wx = column_warps(a.nz, V);
-      dim3 grid((a.m + 1) / 2, (a.nr + kStencilRows - 1) / kStencilRows, (a.nz + 32 * V * wx - 1) / (32 * V * wx));
+      const int W = 128 * wx;
+      const size_t smem = 128 + (size_t)kRingSlots * (4 * W + 4) * sizeof(float);
+      dim3 grid(a.m, (a.nr + kRingRows - 1) / kRingRows, (a.nz + W - 1) / W);
       note_launch();
-      if (mode == kStencilPcgP)
-        stencil_pair_kernel<kStencilPcgP><<<grid, 32 * wx, 0, s>>>(a);
-      else
-        stencil_pair_kernel<kStencilApply><<<grid, 32 * wx, 0, s>>>(a);
-      return;
-    }
-    if ((mode == kStencilPcgP || mode == kStencilApply) && (a.variant == 1 || a.variant == 2) && a.err != nullptr) {
-      if (mode == kStencilPcgP)
-        a.variant == 2 ? launch_stencil_bulk<8, kStencilPcgP>(a, s) : launch_stencil_bulk<16, kStencilPcgP>(a, s);
-      else
-        a.variant == 2 ? launch_stencil_bulk<8, kStencilApply>(a, s) : launch_stencil_bulk<16, kStencilApply>(a, s);
+      const bool full = a.nz % 128 == 0;  // every lane of every strip holds 4 nodes of the grid
+      const void *fn = mode == kStencilPcgP
+                           ? (full ? (const void *)stencil_ring_kernel<kStencilPcgP, true>
+                                   : (const void *)stencil_ring_kernel<kStencilPcgP, false>)
+                           : (full ? (const void *)stencil_ring_kernel<kStencilApply, true>
+                                   : (const void *)stencil_ring_kernel<kStencilApply, false>);
+      ensure_smem_attr(fn, smem);
+      if (mode == kStencilPcgP) {
+        if (full)
+          stencil_ring_kernel<kStencilPcgP, true><<<grid, 32 * (wx + 1), smem, s>>>(a);
+        else
+          stencil_ring_kernel<kStencilPcgP, false><<<grid, 32 * (wx + 1), smem, s>>>(a);
+      } else {
+        if (full)
+          stencil_ring_kernel<kStencilApply, true><<<grid, 32 * (wx + 1), smem, s>>>(a);
+        else
+          stencil_ring_kernel<kStencilApply, false><<<grid, 32 * (wx + 1), smem, s>>>(a);
+      }
       return;
     }
   }

@@ -49,7 +49,7 @@ def test_traffic_row_applies_only_to_the_source_it_was_measured_on(tmp_path, mon
     assert B.measured_traffic("stencil", 1000.0) == pytest.approx(6500.0)
     assert B.measured_traffic("pcg_update", 1000.0) is None  # recorded on other code
     assert B.measured_traffic("mode_solve", 1000.0) is None  # never recorded
-    assert B.measured_traffic("stencil_staged", 1000.0) is None
+    assert B.measured_traffic("stencil_ring", 1000.0) is None
     table.write_text("not json")
     assert B.measured_traffic("stencil", 1000.0) is None
 
@@ -61,7 +61,7 @@ def test_kernel_class_follows_the_kernels_the_solve_ran():
     assert B.kernel_class("mode_solve", True, True, 1, 0) == "mode_solve"
     assert B.kernel_class("mode_solve", True, True, 0, 0) == "mode_solve_tall"
     assert B.kernel_class("mode_solve", True, True, 5, 0) == "mode_solve_pipe"
-    assert B.kernel_class("stencil", True, True, 9, 1) == "stencil_staged"
+    assert B.kernel_class("stencil", True, True, 9, 1) == "stencil_ring"
     assert B.kernel_class("stencil", True, False, 9, 1) == "stencil"
-    for c in ("stencil_staged", "mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe"):
+    for c in ("stencil_ring", "mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe"):
         assert len(B.source_hash(c)) == 16 and B.source_hash(c) != B.source_hash("stencil")

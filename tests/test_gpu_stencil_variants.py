@@ -1,21 +1,21 @@
-"""The staged stencil variants (option "stencil_kernel") against the oracle,
-through the C ABI.
+"""The stencil variants (option "stencil_kernel") against the oracle, through
+the C ABI.
 
 The operator of Eq. scheme_op_r_z (Section 2.1) is applied by the register-
-window kernel (0), by the kernels that stage the rows of their input in
-shared memory with bulk copies, 16 (1) or 8 (2) rows per CTA, or by the
-register window over two right-hand sides per thread (3).  Each must give
+window kernel (0) or by the kernel whose producer warp streams p and the
+coefficient rows through a ring of shared-memory slots with bulk copies (1).
+Each must give
   - y -> A y in FP32 within 2e-6 of the oracle's FP64 A y, and bit for bit
     the register kernel's result (the same FMAs in the same order per node);
-  - in the fused mixed PCG iteration (q = A p with the (p, q) partials), an
-    oracle FP64 true residual <= 1e-8, with variants 1 and 3 taking the same
-    iterations as variant 0 (same CTA partition, so identical partials);
+  - in the fused mixed PCG iteration (q = A p with the (p, q) partials, summed
+    over other CTA tiles by variant 1), an oracle FP64 true residual <= 1e-8
+    within 2 iterations of variant 0;
   - on the expiry path (option "stencil_stall_test": no copy is issued, every
     bounded wait runs out) AX_ERR_TIMEOUT, and a correct result from the next
     call on the same context.
 Shapes span one and several column strips of 1024 (nz > 1024, ragged last
-strip), nz not a multiple of 4, nr not a multiple of the rows per CTA, and a
-single row.
+strip), nz a multiple of 128 (the range tests compiled out) and not, nz not a
+multiple of 4, nr not a multiple of the rows per CTA, and a single row.
 """
 import numpy as np
 import pytest
@@ -59,29 +59,29 @@ def _apply(op, y, dev):
 
 
 @pytest.mark.parametrize("nr,nz,m", [(1, 7, 2), (5, 3, 3), (17, 130, 2), (40, 1024, 1), (33, 1030, 3), (100, 2051, 2),
-                                     (250, 4096, 2), (1031, 96, 3)])
+                                     (250, 4096, 2), (1031, 96, 3), (1, 128, 1), (19, 384, 2), (64, 2048, 1),
+                                     (65, 1000, 1)])
 def test_apply_matches_oracle_and_register_kernel(cuda, nr, nz, m):
     op, ora, _ = _setup(nr, nz, cuda)
     y = np.random.default_rng(nr * 7 + nz).normal(size=(m, nr, nz))
     ref = _apply(op, y, cuda)
-    for v in (1, 2, 3):
-        P.ax_set_option(op, "stencil_kernel", v)
-        assert int(P.ax_get_option(op, "stencil_kernel")) == v
-        got = _apply(op, y, cuda)
-        assert np.array_equal(got, ref), (v, np.abs(got - ref).max())
-        for j in range(m):
-            assert _rel(got[j], ora.apply_A(y[j])) <= 2e-6
+    P.ax_set_option(op, "stencil_kernel", 1)
+    assert int(P.ax_get_option(op, "stencil_kernel")) == 1
+    got = _apply(op, y, cuda)
+    assert np.array_equal(got, ref), np.abs(got - ref).max()
+    for j in range(m):
+        assert _rel(got[j], ora.apply_A(y[j])) <= 2e-6
     P.ax_destroy_operator(op)
 
 
-@pytest.mark.parametrize("nr,nz", [(600, 200), (1024, 96), (129, 1300)])
+@pytest.mark.parametrize("nr,nz", [(600, 200), (1024, 96), (129, 1300), (200, 1024), (301, 256)])
 def test_fused_mixed_pcg(cuda, nr, nz):
     op, ora, med = _setup(nr, nz, cuda)
     f = sample_rhs(med, nr, nz)
     fd = torch.from_numpy(f).to(cuda)
     P.ax_set_option(op, "dst_tensor", 1)
     iters = {}
-    for v in (0, 1, 2, 3):
+    for v in (0, 1):
         P.ax_set_option(op, "stencil_kernel", v)
         u = torch.zeros_like(fd)
         st, info = P.ax_solve(op, fd, u, 3, 1e-8, 5000, P.AX_PCG_MIXED)
@@ -92,27 +92,25 @@ def test_fused_mixed_pcg(cuda, nr, nz):
         for j in range(3):
             phi = ora.phi(f[j])
             assert np.linalg.norm(phi - ora.apply_A(un[j])) <= 1e-8 * np.linalg.norm(phi), (v, j)
-    assert iters[1] == iters[0] and iters[3] == iters[0], iters
-    assert all(abs(a - b) <= 2 for a, b in zip(iters[2], iters[0])), iters
+    assert all(abs(a - b) <= 2 for a, b in zip(iters[1], iters[0])), iters
     P.ax_destroy_operator(op)
 
 
 def test_option_values(cuda):
     op, _, _ = _setup(64, 64, cuda)
-    assert P.ax_set_option(op, "stencil_kernel", 4, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+    assert P.ax_set_option(op, "stencil_kernel", 2, raise_on_error=False) == P.AX_ERR_INVALID_ARG
     assert P.ax_set_option(op, "stencil_kernel", 0.5, raise_on_error=False) == P.AX_ERR_INVALID_ARG
     assert int(P.ax_get_option(op, "stencil_kernel")) == 0
     P.ax_destroy_operator(op)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
-def test_bounded_wait_expiry_returns_timeout(cuda, variant):
+def test_bounded_wait_expiry_returns_timeout(cuda):
     """No copy is issued, so every wait of the launch runs out: the kernel
     flags the error and returns, the call reports AX_ERR_TIMEOUT, and the
     next call on the same context computes A y."""
     nr, nz = 48, 300
     op, ora, med = _setup(nr, nz, cuda)
-    P.ax_set_option(op, "stencil_kernel", variant)
+    P.ax_set_option(op, "stencil_kernel", 1)
     y = np.random.default_rng(3).normal(size=(1, nr, nz))
     P.ax_set_option(op, "stencil_stall_test", 1)
     with pytest.raises(P.AxError) as e:
