@@ -155,6 +155,9 @@ def parse_args():
     ap.add_argument("--save", default="", help="guess_256: write the trained weights here")
     ap.add_argument("--h1", type=float, default=10.0, help="guess_256: weight of the loss's lattice-edge term")
     ap.add_argument("--no-pre", action="store_true", help="guess_256: raw f / s feature instead of B^-1 (r f)")
+    ap.add_argument("--train-media", type=int, default=24,
+                    help="large_4096_m16_guess: training media (16 right-hand sides each)")
+    ap.add_argument("--eval-media", type=int, default=2, help="large_4096_m16_guess: held-out media")
     ap.add_argument("--bc-z", type=int, default=0, choices=[0, 1],
                     help="z boundary: 0 = u = 0 (sine transform), 1 = the paper's zero flux (cosine pair)")
     ap.add_argument("--dst-tensor", type=int, default=-1, choices=[-1, 0, 1, 2],
@@ -692,6 +695,91 @@ def run_guess(args):
     P.ax_guessnet_destroy(net)
 
 
+def run_guess_large(args):
+    """Workload large_4096_m16_guess: mixed PCG at 4096^2 x 16 right-hand sides
+    with the learned guess, the network at 512^2 with bilinear lift.  Solves
+    `--train-media` media of the large layered kind (disjoint seed stream),
+    trains the network on the GPU on (features with B^-1 (r f), cell averages
+    of u / s), then solves `--eval-media` held-out media from zero and from
+    the network's guess (features, inference and lift inside the timed
+    region; residual gate on) to 1e-8."""
+    import numpy as np
+    import torch
+    import paper_1002_3094_gb300 as P
+    from paper_1002_3094_gb300 import guess as GS
+    from workloads import large_spec
+    dev = torch.device("cuda", 0)
+    P.build()
+    P.load_library()
+    n, hw, m = 4096, 512, 16
+    t0 = time.perf_counter()
+    train = GS.make_dataset_large([large_spec(i, m, n, split="train") for i in range(args.train_media)], n, n, hw,
+                                  TOL, dev)
+    t_data = time.perf_counter() - t0
+    net = P.ax_guessnet_create(hw, None, batch_capacity=max(args.batch, m), seed=1)
+    P.ax_guessnet_set_loss(net, args.h1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = GS.train(net, train, args.epochs, args.batch, args.lr, log=lambda s_: print(s_, file=sys.stderr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    n_train = int(train["x"].shape[0])
+    tscale = train["tscale"]
+    del train
+    ev = GS.make_dataset_large([large_spec(i, m, n, split="eval") for i in range(args.eval_media)], n, n, hw, TOL,
+                               dev, target_scale=tscale, keep_ops=True)
+    rows = []
+    for med in ev["media"]:
+        op, f = med["op"], med["f"]
+        u = torch.zeros_like(f)
+        P.ax_solve(op, f, u, m, TOL, 20000, P.AX_PCG_MIXED)  # warm the graphs
+        torch.cuda.synchronize()
+        u.zero_()
+        a0 = time.perf_counter()
+        _, i0 = P.ax_solve(op, f, u, m, TOL, 20000, P.AX_PCG_MIXED)
+        torch.cuda.synchronize()
+        a1 = time.perf_counter()
+        u0 = GS.guess_large(net, med, hw, n, n, tscale)
+        _, ig = P.ax_solve(op, f, u0, m, TOL, 20000, P.AX_PCG_MIXED, P.AX_FLAG_USE_GUESS | P.AX_FLAG_CHECK_GUESS)
+        torch.cuda.synchronize()
+        a2 = time.perf_counter()
+        g1 = GS.guess_large(net, med, hw, n, n, tscale)
+        ratios = [GS.energy_ratio(op, f[j:j + 1], g1[j:j + 1]) for j in range(m)]
+        eratios = [GS.energy_error_ratio(op, med["u"][j], g1[j]) for j in range(m)]
+        rows.append({"iters_zero": [i["iters"] for i in i0], "iters_guess": [i["iters"] for i in ig],
+                     "ms_zero": 1e3 * (a1 - a0), "ms_guess": 1e3 * (a2 - a1),
+                     "accepted": [i["guess_accepted"] for i in ig], "energy_ratio": ratios,
+                     "energy_error_ratio": eratios,
+                     "max_rel_res_guess": max(i["rel_res"] for i in ig)})
+        del u, u0, g1
+    for med in ev["media"]:
+        P.ax_destroy_operator(med["op"])
+    it0 = np.array([x for r in rows for x in r["iters_zero"]])
+    itg = np.array([x for r in rows for x in r["iters_guess"]])
+    er = np.array([x for r in rows for x in r["energy_ratio"]])
+    ee = np.array([x for r in rows for x in r["energy_error_ratio"]])
+    line = {"metric": "PCG iterations and wall time at rel. residual 1e-8, from the learned guess vs from zero",
+            "workload": "large_4096_m16_guess", "grid": [n, n], "rhs_per_solve": m, "network_lattice": hw,
+            "lift": "bilinear", "method": "pcg_mixed", "train_media": args.train_media, "train_samples": n_train,
+            "eval_media": args.eval_media, "eval_samples": int(it0.size), "epochs": args.epochs,
+            "batch": args.batch, "h1_weight": args.h1, "feature": "B^-1 (r f) / s",
+            "data_s": t_data, "train_s": t_train, "train_samples_per_s": n_train * args.epochs / t_train,
+            "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+            "iters_zero_mean": float(it0.mean()), "iters_guess_mean": float(itg.mean()),
+            "iters_zero_max": int(it0.max()), "iters_guess_max": int(itg.max()),
+            "iters_saved_frac": float(1 - itg.mean() / it0.mean()),
+            "ms_zero_per_solve": float(np.mean([r["ms_zero"] for r in rows])),
+            "ms_guess_per_solve": float(np.mean([r["ms_guess"] for r in rows])),
+            "accepted_frac": float(np.mean([a for r in rows for a in r["accepted"]])),
+            "energy_ratio_median": float(np.median(er)), "energy_ratio_min": float(er.min()),
+            "energy_error_ratio_median": float(np.median(ee)), "energy_error_ratio_min": float(ee.min()),
+            "energy_ratio_meaning": "sqrt((r0, B^-1 r0) / (phi, B^-1 phi)) of the guess (the gate's test)",
+            "energy_error_ratio_meaning": "||u0 - u||_A / ||u||_A against the converged solution",
+            "max_rel_res_guess": max(r["max_rel_res_guess"] for r in rows), "data": "synthetic"}
+    print(json.dumps(line))
+    P.ax_guessnet_destroy(net)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -699,6 +787,9 @@ def main():
         return
     if args.workload == "guess_256":
         run_guess(args)
+        return
+    if args.workload == "large_4096_m16_guess":
+        run_guess_large(args)
         return
     if args.workload == "laguerre_chain":
         run_laguerre(args)

@@ -58,6 +58,85 @@ def grf_fields(specs, nr: int, nz: int, device):
     return torch.stack(kr), torch.stack(kz), torch.stack(qq), torch.stack(ff)
 
 
+def large_fields(spec, nr: int, nz: int, device):
+    """kappa_r [nr][nz], kappa_z [nr][nz+1], q [nr][nz] and f [M][nr][nz]
+    (FP64 torch tensors on `device`) of a large layered medium given by its
+    spec (workloads.large_spec), evaluated at the grid's sample points in
+    bulk on the GPU: log kappa = log(layer value) + sum of the inclusions'
+    log-factors times their logistic indicators, rescaled by the spec's
+    extremes to [0, log contrast]; Gaussian sources."""
+    import torch
+    rn, rf, zn, zf = sample_points(nr, nz)
+    t = lambda a: torch.as_tensor(np.asarray(a), dtype=torch.float64, device=device)  # noqa: E731
+    rn, rf, zn, zf = t(rn), t(rf), t(zn), t(zf)
+    cuts, values = t(spec["cuts"]), t(spec["values"])
+
+    def kappa(r, z):
+        lk = torch.log(values[torch.searchsorted(cuts, z, right=True)])[None, :].expand(r.numel(), z.numel())
+        lk = lk.clone()
+        for rc, zc, a, b, width, lf in spec["incs"]:
+            rho = torch.sqrt(((r[:, None] - rc) / a) ** 2 + ((z[None, :] - zc) / b) ** 2)
+            lk += lf * 0.5 * (1.0 - torch.tanh(0.5 * (rho - 1.0) * min(a, b) / width))
+        tt = ((lk - spec["lmin"]) / (spec["lmax"] - spec["lmin"])).clamp(0.0, 1.0)
+        return torch.exp(np.log(spec["contrast"]) * tt)
+
+    sg = spec["sigma"]
+    f = torch.stack([torch.exp(-((rn[:, None] - rc) ** 2 + (zn[None, :] - zc) ** 2) / (2 * sg * sg))
+                     for rc, zc in spec["centres"]])
+    q = torch.full((nr, nz), spec["q"], dtype=torch.float64, device=device)
+    return kappa(rf, zn).contiguous(), kappa(rn, zf).contiguous(), q, f.contiguous()
+
+
+def make_dataset_large(specs, nr: int, nz: int, hw: int, tol: float = 1e-8, device=None, target_scale: float = 0.0,
+                       keep_ops: bool = False):
+    """Solves every large medium (all its right-hand sides at once, mixed
+    PCG) and returns the lattice features x [n][3][hw][hw], the targets u / s
+    averaged over hw x hw cells (FP32, scaled by tscale), the scales s and
+    the solves' iteration counts; with keep_ops, the operators and the fields
+    stay for evaluation (one medium at a time otherwise, to bound memory)."""
+    import torch
+    xs, ys, ss, iters, kept = [], [], [], [], []
+    for spec in specs:
+        kr, kz, q, f = large_fields(spec, nr, nz, device)
+        m = f.shape[0]
+        op = ax_setup_operator(kr, kz, q, nr, nz)
+        u = torch.zeros_like(f)
+        _, info = ax_solve(op, f, u, m, tol, 20000, AX_PCG_MIXED)
+        iters += [i["iters"] for i in info]
+        x = torch.zeros((m, 3, hw, hw), dtype=torch.float32, device=device)
+        s = torch.zeros(m, dtype=torch.float64, device=device)
+        ax_guessnet_features_pre(op, kr, q, f, m, hw, x, s)
+        y = torch.nn.functional.avg_pool2d((u / s[:, None, None]).float()[:, None], (nr // hw, nz // hw))[:, 0]
+        xs.append(x)
+        ys.append(y)
+        ss.append(s)
+        if keep_ops:
+            kept.append({"op": op, "kr": kr, "q": q, "f": f, "u": u, "iters": [i["iters"] for i in info]})
+        else:
+            ax_destroy_operator(op)
+            del kr, kz, q, f, u
+    x, y, s = torch.cat(xs), torch.cat(ys), torch.cat(ss)
+    tscale = target_scale if target_scale else float(1.0 / y.std().item())
+    return {"x": x, "y": (y * tscale).contiguous(), "s": s, "iters": iters, "tscale": tscale, "media": kept}
+
+
+def guess_large(net: int, medium, hw: int, nr: int, nz: int, tscale: float):
+    """u0 [M][nr][nz] for every right-hand side of a kept large medium:
+    features (with the preconditioned right-hand side) -> network (one batch)
+    -> bilinear lift -> scale."""
+    import torch
+    dev = medium["f"].device
+    m = medium["f"].shape[0]
+    x = torch.zeros((m, 3, hw, hw), dtype=torch.float32, device=dev)
+    s = torch.zeros(m, dtype=torch.float64, device=dev)
+    ax_guessnet_features_pre(medium["op"], medium["kr"], medium["q"], medium["f"], m, hw, x, s)
+    y = torch.zeros((m, hw, hw), dtype=torch.float32, device=dev)
+    ax_guessnet_forward(net, x, y, m)
+    u0 = torch.zeros_like(medium["f"])
+    ax_guessnet_lift(y, m, hw, s / tscale, nr, nz, u0)
+    return u0
+
+
 def _features(data, i, x, s):
     """Features of sample i into x [1][3][hw][hw] and its scale into s [1]."""
     hw = x.shape[-1]
@@ -150,6 +229,19 @@ def energy_ratio(op, f, u0):
     ax_apply_preconditioner(op, r0, br, 1, AX_PREC_FP64)
     ax_apply_preconditioner(op, phi, bp, 1, AX_PREC_FP64)
     return float(torch.sqrt((r0 * br).sum() / (phi * bp).sum()))
+
+
+def energy_error_ratio(op, u, u0):
+    """||u0 - u||_A / ||u||_A (A in FP64) for the converged solution u: the
+    initial error in the norm that bounds PCG's convergence (diagnostic)."""
+    import torch
+    nr, nz = u.shape[-2:]
+    e = (u0 - u).reshape(1, nr, nz).contiguous()
+    uu = u.reshape(1, nr, nz).contiguous()
+    ae, au = torch.zeros_like(e), torch.zeros_like(e)
+    ax_apply_operator(op, e, ae, 1, AX_PREC_FP64)
+    ax_apply_operator(op, uu, au, 1, AX_PREC_FP64)
+    return float(torch.sqrt((e * ae).sum() / (uu * au).sum()))
 
 
 def evaluate(net: int, data, hw: int, nr: int, nz: int, tol: float = 1e-8, method: int = AX_PCG_MIXED):

@@ -17,6 +17,7 @@ from .media import (  # noqa: F401
     grf_medium,
     grf_spec,
     large_medium,
+    large_spec,
     manufactured_medium,
     manufactured_medium_neumann,
     WORKLOADS,

@@ -248,33 +248,51 @@ def grf_medium(instance: int, split: str = "train") -> Medium:
 # ---------------------------------------------------------------------------
 # Workload 5: large layered medium with 4 inclusions, contrast 100.
 # ---------------------------------------------------------------------------
-def large_medium(n_rhs: int = 16, nominal_n: int = 4096, instance: int = 0,
-                 contrast: float = 100.0) -> Medium:
-    rng = _rng(5, instance)
+def large_spec(instance: int = 0, n_rhs: int = 16, nominal_n: int = 4096, contrast: float = 100.0,
+               split: str = "bench") -> dict:
+    """All random draws of one large layered medium: the 7 layer cuts in z and
+    8 layer values, 4 elliptical inclusions (centre, semi-axes, logistic edge
+    width 2/n, log-factor), the extremes (lmin, lmax) of log kappa before
+    rescaling on a fixed 512^2 reference lattice, and the Gaussian source
+    centres (sigma 2/n).  split 'bench' is the benchmark's seed stream;
+    'train' and 'eval' are disjoint streams for the learned guess.
+    large_medium builds its functions from this, and bulk evaluators can
+    reproduce the same medium from it."""
+    rng = _rng({"bench": 5, "train": 50, "eval": 51}[split], instance)
     cuts = np.sort(rng.uniform(0.0, 1.0, size=7))
     values = np.exp(rng.uniform(0.0, np.log(10.0), size=8))
     h = 1.0 / nominal_n
-    incs = [(_ellipse_indicator(*rng.uniform(0.15, 0.85, size=2), *rng.uniform(0.04, 0.15, size=2),
-                                width=2.0 * h), rng.uniform(-1.5, 1.5)) for _ in range(4)]
-    layer = _layers(cuts, values)
-
-    def log_raw(r, z):
-        out = np.log(layer(r, z))
-        for ind, lf in incs:
-            out = out + lf * ind(r, z)
-        return out
-
+    incs = []
+    for _ in range(4):
+        rc, zc = rng.uniform(0.15, 0.85, size=2)
+        a, b = rng.uniform(0.04, 0.15, size=2)
+        incs.append((float(rc), float(zc), float(a), float(b), 2.0 * h, float(rng.uniform(-1.5, 1.5))))
+    spec = {"cuts": cuts, "values": values, "incs": incs, "contrast": float(contrast), "q": 0.05, "sigma": 2.0 * h}
     rr, zz = _reference_lattice(512)
-    lv = log_raw(rr, zz)
-    lmin, lmax = float(lv.min()), float(lv.max())
+    lv = _large_log_raw(spec, rr, zz)
+    spec["lmin"], spec["lmax"] = float(lv.min()), float(lv.max())
+    spec["centres"] = rng.uniform(0.05, 0.95, size=(n_rhs, 2))
+    return spec
+
+
+def _large_log_raw(spec: dict, r, z):
+    out = np.log(_layers(spec["cuts"], spec["values"])(r, z))
+    for rc, zc, a, b, width, lf in spec["incs"]:
+        out = out + lf * _ellipse_indicator(rc, zc, a, b, width)(r, z)
+    return out
+
+
+def large_medium(n_rhs: int = 16, nominal_n: int = 4096, instance: int = 0,
+                 contrast: float = 100.0, split: str = "bench") -> Medium:
+    spec = large_spec(instance, n_rhs, nominal_n, contrast, split)
+    lmin, lmax = spec["lmin"], spec["lmax"]
 
     def kappa(r, z):
-        t = np.clip((log_raw(r, z) - lmin) / (lmax - lmin), 0.0, 1.0)
+        t = np.clip((_large_log_raw(spec, r, z) - lmin) / (lmax - lmin), 0.0, 1.0)
         return np.exp(np.log(contrast) * t)
 
-    centres = rng.uniform(0.05, 0.95, size=(n_rhs, 2))
-    return Medium("large_layered", kappa, _const(0.05),
-                  [_gaussian(c[0], c[1], 2.0 * h) for c in centres],
+    return Medium("large_layered", kappa, _const(spec["q"]),
+                  [_gaussian(c[0], c[1], spec["sigma"]) for c in spec["centres"]],
                   "8 layers + 4 inclusions, contrast 100; q = 0.05; Gaussian sources sigma = 2/n")
 
 
