@@ -168,6 +168,8 @@ def parse_args():
                     help="keep the library's default transform and mode-solve kernel (no ax_autotune)")
     ap.add_argument("--mode-kernel", type=int, default=0,
                     help="FP32 mode-solve kernel variant (option mode_kernel; 0 the library's choice)")
+    ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
+                    help="ax_set_option on the operator before the run (repeatable)")
     ap.add_argument("--stencil-kernel", type=int, default=-1,
                     help="stencil of the fused FP32 iteration (option stencil_kernel; -1 the library's choice)")
     ap.add_argument("--replace-delta", type=float, default=0.0,
@@ -752,6 +754,8 @@ def run_guess_large(args):
                      "energy_error_ratio": eratios,
                      "max_rel_res_guess": max(i["rel_res"] for i in ig)})
         del u, u0, g1
+    med0 = ev["media"][0]
+    bounds = GS.lattice_bounds(med0["op"], med0["f"], med0["u"], hw)
     for med in ev["media"]:
         P.ax_destroy_operator(med["op"])
     it0 = np.array([x for r in rows for x in r["iters_zero"]])
@@ -775,7 +779,13 @@ def run_guess_large(args):
             "energy_error_ratio_median": float(np.median(ee)), "energy_error_ratio_min": float(ee.min()),
             "energy_ratio_meaning": "sqrt((r0, B^-1 r0) / (phi, B^-1 phi)) of the guess (the gate's test)",
             "energy_error_ratio_meaning": "||u0 - u||_A / ||u||_A against the converged solution",
-            "max_rel_res_guess": max(r["max_rel_res_guess"] for r in rows), "data": "synthetic"}
+            "max_rel_res_guess": max(r["max_rel_res_guess"] for r in rows),
+            "lattice_bounds_median": {k: float(np.median(v)) for k, v in bounds.items()},
+            "lattice_bounds_meaning": "energy-norm error ratio of the first held-out medium's 16 right-hand "
+                                      "sides: lattice = lift of u's own 512^2 cell averages; one_step = a B^-1 (r f) "
+                                      "with the A-optimal a; one_step_plus_lattice = that plus the lift of the cell "
+                                      "averages of the remainder",
+            "data": "synthetic"}
     print(json.dumps(line))
     P.ax_guessnet_destroy(net)
 
@@ -831,6 +841,9 @@ def main():
         P.ax_set_option(op, "mode_kernel", args.mode_kernel)
     if args.stencil_kernel >= 0:
         P.ax_set_option(op, "stencil_kernel", args.stencil_kernel)
+    for kv in args.option:
+        name, value = kv.split("=", 1)
+        P.ax_set_option(op, name, float(value))
     tuned = None
     if (not args.no_autotune and args.dst_tensor < 0 and args.mode_kernel == 0 and args.stencil_kernel < 0
             and "mixed" in args.method):
@@ -1000,7 +1013,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "nr": nr, "nz": nz, "rhs": m, "tol": TOL, "bc_z": args.bc_z,
                        "method": args.method, "parallelism": f"replicas x{world}",
-                       "l2": l2_note},
+                       "l2": l2_note, "options": args.option},
             "iters": {"max": max(iters), "min": min(iters), "outer_max": max(outer)},
             "max_rel_res": rel,
             "plain_fp64": plain,

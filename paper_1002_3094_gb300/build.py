@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaxpcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ax_stencil.cu", "ax_dst_f32.cu", "ax_dst_f64.cu", "ax_tridiag.cu", "ax_solver.cu", "ax_noalloc.cu", "ax_guessnet.cu", "ax_dst_gemm.cu", "ax_laguerre.cu"]
+SOURCES = ["ax_stencil.cu", "ax_dst_f32.cu", "ax_dst_f64.cu", "ax_tridiag.cu", "ax_solver.cu", "ax_noalloc.cu", "ax_guessnet.cu",
+           "ax_dst_gemm.cu", "ax_laguerre.cu", "ax_small.cu"]
 
 
 def nvcc_path() -> str:

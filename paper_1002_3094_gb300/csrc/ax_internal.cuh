@@ -231,6 +231,30 @@ struct DfResidualArgs {
 void launch_residual_df(const DfResidualArgs &a, cudaStream_t s);
 int residual_df_blocks(int nr, int nz);
 
+// Persistent FP64 PCG of one right-hand side on a small grid (ax_small.cu):
+// the whole iteration in one cooperative launch, phases separated by bounded
+// grid barriers.  Inputs are the state after sc_start (r = phi - A x, rr, bb,
+// thresh2); on return x, r and the state hold the result.
+struct SmallPcgArgs {
+  const double *CR, *CZ, *W, *IP, *E;  // operator and Thomas tables (FP64)
+  const double *F, *Ft;                // dense forward transform F[l][k] and its transpose
+  const double *phi;                   // [nr][pitch]
+  double *x, *r, *r2, *z, *pa, *pb, *q, *t; // [nr][pitch]; r, r2 the double-buffered
+                                           // residual; t the transformed field
+  double *part;                        // [4][G] per-CTA partial sums
+  unsigned *bar;                       // [2] barrier count and generation (zero at launch)
+  RhsState *st;
+  int nr, nz, pitch, pitchz;
+  int nch;                             // output chunks per row of the dense transforms
+  int *err;                            // set when a bounded wait expired
+  unsigned polls;                      // wait limit (0: the default)
+  int stall;                           // test of the expiry path: CTA 0 skips its first barrier
+};
+constexpr int kSmallMaxNr = 512, kSmallMaxNz = 256, kSmallMaxN = 65536;
+// Grid size for a launch (0 if the device cannot hold enough co-resident CTAs).
+int small_pcg_grid(int nr, int nz, int *nch);
+cudaError_t launch_small_pcg(const SmallPcgArgs &a, int grid, cudaStream_t s);
+
 // Sine-transform modes
 enum { kDstPlain = 0, kDstPcgForward = 1, kDstPcgInverse = 2, kDstChebInverse = 3 };
 

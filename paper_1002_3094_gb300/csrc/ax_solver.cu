@@ -92,6 +92,10 @@ struct Workspace {
   int host_chunks = 1;          // host-buffer solves: right-hand-side chunks whose copies overlap the solve
                                 // (1: none; at 1024^2 x 64, 4 chunks of 16 took 73 ms against 63 ms for one
                                 // 64-RHS solve with its copies in series)
+  int small_path = 1;           // FP64 PCG of one right-hand side on a small grid: one persistent launch
+  int small_stall_test = 0;     // 1: the next persistent launch lets its barrier waits run out
+  double *small_buf = nullptr;  // its second residual buffer and transformed field [2][nr][pitch]
+  unsigned *small_bar = nullptr;  // its grid-barrier words [2]
   cudaStream_t copy = nullptr;  // copy stream of those chunks
   cudaEvent_t cev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // per right-hand-side completion times (ms since lat_t0) of the current
@@ -1168,6 +1172,118 @@ int *tc_flag(int device) {
   return d;
 }
 
+// Dense FP64 matrices of the z-transform for the persistent small-grid PCG,
+// per (device, nz, boundary condition), kept for the life of the process:
+// F[l][k] (forward) followed by F^T.  Sine (bc_z = 0): the orthonormal DST-I,
+// F[l][k] = sqrt(2 / (nz + 1)) sin(pi (l + 1)(k + 1) / (nz + 1)), symmetric.
+// Cosine (bc_z = 1): the orthonormal pair of the cell-centred grid,
+// F[l][k] = sqrt(2 / nz) w_l cos(pi l (k + 1/2) / nz), w_0 = 1 / sqrt 2, w_l = 1
+// otherwise (mode l + 1 of Eq. eq_trid).  The angles are reduced exactly in
+// integers before the sine / cosine.
+struct DenseCache {
+  std::mutex mu;
+  std::vector<std::pair<long long, double *>> tables;
+};
+const double *dense_table(int device, int n, int cosine) {
+  static DenseCache c;
+  std::lock_guard<std::mutex> lock(c.mu);
+  const long long key = (long long)device << 32 | (unsigned)n | (long long)cosine << 24;
+  for (auto &e : c.tables)
+    if (e.first == key) return e.second;
+  std::vector<double> t(2 * (size_t)n * n);
+  for (int l = 0; l < n; ++l)
+    for (int k = 0; k < n; ++k) {
+      double v;
+      if (!cosine) {
+        const long long j = (long long)(l + 1) * (k + 1) % (2LL * (n + 1));  // angle pi j / (n + 1)
+        v = std::sqrt(2.0 / (n + 1)) * std::sin(M_PI * (double)j / (n + 1));
+      } else {
+        const long long j = (long long)l * (2 * k + 1) % (4LL * n);  // angle pi j / (2 n)
+        v = std::sqrt(2.0 / n) * (l == 0 ? std::sqrt(0.5) : 1.0) * std::cos(M_PI * (double)j / (2.0 * n));
+      }
+      t[(size_t)l * n + k] = v;
+      t[(size_t)n * n + (size_t)k * n + l] = v;
+    }
+  double *d = nullptr;
+  std::lock_guard<std::recursive_mutex> lock2(g_alloc_capture_mutex);
+  if (dalloc(&d, t.size()) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  c.tables.push_back({key, d});
+  return d;
+}
+
+// The persistent FP64 PCG applies to one right-hand side on a grid whose
+// transform fits its dense tables and whose mode solves fit one warp per
+// column (16 rows per lane).
+bool small_applies(const ax_operator *op, int m) {
+  return op->ws->small_path && m == 1 && op->nr <= kSmallMaxNr && op->nz <= kSmallMaxNz &&
+         (long long)op->nr * op->nz <= kSmallMaxN && op->cstride == 0;
+}
+
+// Runs it from the state sc_start left (r = phi - A x in r64).
+int small_pcg_run(ax_operator *op, cudaStream_t s) {
+  Workspace *w = op->ws;
+  int nch = 1;
+  const int grid = small_pcg_grid(op->nr, op->nz, &nch);
+  if (grid < 1) return AX_ERR_UNSUPPORTED;
+  const double *F = dense_table(op->device, op->nz, op->bc_z);
+  int *flag = tc_flag(op->device);
+  if (!F || !flag) return AX_ERR_OOM;
+  const size_t f = field_elems(op);
+  {
+    std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
+    if (!w->small_buf) AX_TRY(dalloc(&w->small_buf, 2 * f));
+    if (!w->small_bar) AX_TRY(dalloc(&w->small_bar, 2));
+  }
+  AX_TRY(cudaMemsetAsync(w->small_bar, 0, 2 * sizeof(unsigned), s));
+  AX_TRY(cudaMemsetAsync(w->pa64, 0, f * sizeof(double), s));
+  SmallPcgArgs a{};
+  const Coef<double> &c = op->c64;
+  a.CR = c.CR;
+  a.CZ = c.CZ;
+  a.W = c.W;
+  a.IP = c.IP;
+  a.E = c.E;
+  a.F = F;
+  a.Ft = F + (size_t)op->nz * op->nz;
+  a.phi = w->phi64;
+  a.x = w->x64;
+  a.r = w->r64;
+  a.r2 = w->small_buf;
+  a.z = w->z64;
+  a.pa = w->pa64;
+  a.pb = w->pb64;
+  a.q = w->q64;
+  a.t = w->small_buf + f;
+  a.part = part_ptr(w, kPartA);
+  a.bar = w->small_bar;
+  a.st = w->st;
+  a.nr = op->nr;
+  a.nz = op->nz;
+  a.pitch = op->pitch;
+  a.pitchz = op->pitchz;
+  a.nch = nch;
+  a.err = flag;
+  if (w->small_stall_test) {  // test of the expiry path (option "small_stall_test"), once
+    a.stall = 1;
+    a.polls = 1u << 12;
+    w->small_stall_test = 0;
+  }
+  AX_TRY(launch_small_pcg(a, grid, s));
+  int hf = 0;
+  AX_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AX_TRY(cudaStreamSynchronize(s));
+  if (hf) {
+    AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    snprintf(g_last_error, sizeof(g_last_error), "a grid-barrier wait of the persistent small-grid solve expired");
+    return AX_ERR_TIMEOUT;
+  }
+  return AX_OK;
+}
+
 // Test of the staged stencil's expiry path (option "stencil_stall_test"), once:
 // the launch issues no copy and waits briefly, so every wait runs out.
 template <typename T>
@@ -2173,6 +2289,8 @@ int ax_destroy_operator(ax_operator *op) {
     dfree(w->stage_a);
     dfree(w->stage_b);
     dfree(w->split);
+    dfree(w->small_buf);
+    dfree(w->small_bar);
     if (w->scratch) cudaFree(w->scratch);
     if (w->cap) cudaStreamDestroy(w->cap);
     if (w->copy) cudaStreamDestroy(w->copy);
@@ -2372,6 +2490,7 @@ int ax_get_option(const ax_operator *op, const char *name, double *value) {
   if (!strcmp(name, "dst_tensor")) *value = op->dst_tc;
   else if (!strcmp(name, "mode_kernel")) *value = op->tri_variant;
   else if (!strcmp(name, "stencil_kernel")) *value = op->st_variant;
+  else if (!strcmp(name, "small_path")) *value = op->ws->small_path;
   else if (!strcmp(name, "mode_kernel_effective"))  // the FP32 mode-solve kernel a solve runs (0: none of the tile kernels)
     *value = tridiag_effective(op->nr, op->tri_variant, 1, op->c32.IPS != nullptr && op->c32.RS != nullptr);
   else if (!strcmp(name, "inner_tol")) *value = w->inner_tol;
@@ -2434,6 +2553,16 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
   } else if (!strcmp(name, "tc_fused")) {
     w->tc_unfused = value == 0.0;
     free_graph(w->g32);
+  } else if (!strcmp(name, "small_path")) {
+    // AX_PCG_FP64 of one right-hand side on a small grid as one persistent
+    // launch (1, default) or through the graph-replayed kernels (0)
+    if (value != 0.0 && value != 1.0) return AX_ERR_INVALID_ARG;
+    w->small_path = (int)value;
+  } else if (!strcmp(name, "small_stall_test")) {
+    // The next persistent small-grid solve has one CTA leave before its first
+    // grid barrier, so that the others' bounded waits run out: the call
+    // returns AX_ERR_TIMEOUT and the context stays usable.  For tests.
+    w->small_stall_test = value != 0.0;
   } else if (!strcmp(name, "stencil_stall_test")) {
     // The next staged stencil (option "stencil_kernel" 1 or 2) issues no copy
     // and waits briefly, so its bounded waits run out: the call returns
@@ -3016,7 +3145,9 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     if (check_guess &&
         (rc = gate_guess<double>(op, m, w->st, w->phi64, w->r64, w->z64, w->q64, accepted, s, start)) != AX_OK)
       return rc;
-    if (!cheb) {
+    if (!cheb && small_applies(op, m)) {
+      if ((rc = small_pcg_run(op, s)) != AX_OK) return rc;
+    } else if (!cheb) {
       PcgVecs<double> v{w->x64, w->r64, w->pa64, w->pb64, w->q64, w->z64};
       if ((rc = pcg_loop<double>(op, m, v, w->phi64, w->st, w->g64, true, s)) != AX_OK) return rc;
     } else {

@@ -244,6 +244,40 @@ def energy_error_ratio(op, u, u0):
     return float(torch.sqrt((e * ae).sum() / (uu * au).sum()))
 
 
+def lattice_bounds(op, f, u, hw: int):
+    """What any guess built on an hw x hw lattice can reach, per right-hand
+    side of f [M][nr][nz] with converged solutions u (diagnostic, FP64
+    operator): the energy-norm error ratio ||u0 - u||_A / ||u||_A of
+    (a) the bilinear lift of u's own cell averages, (b) one preconditioned
+    step from zero, u0 = a g with g = B^-1 (r f) and the A-optimal a, and
+    (c) that step plus the lift of the cell averages of its remainder u - a g."""
+    import torch
+    from .inputs import sample_points
+    m, nr, nz = f.shape
+    rn = torch.as_tensor(sample_points(nr, nz)[0], dtype=torch.float64, device=f.device)
+    out = {"lattice": [], "one_step": [], "one_step_plus_lattice": []}
+    ones = torch.ones(1, dtype=torch.float64, device=f.device)
+
+    def lift_avg(v):
+        y = torch.nn.functional.avg_pool2d(v.float()[None, None], (nr // hw, nz // hw))[0].contiguous()
+        w = torch.zeros((1, nr, nz), dtype=torch.float64, device=f.device)
+        ax_guessnet_lift(y, 1, hw, ones, nr, nz, w)
+        return w[0]
+
+    for j in range(m):
+        phi = (rn[:, None] * f[j]).reshape(1, nr, nz).contiguous()
+        g = torch.zeros_like(phi)
+        ax_apply_preconditioner(op, phi, g, 1, AX_PREC_FP64)
+        ag = torch.zeros_like(phi)
+        ax_apply_operator(op, g, ag, 1, AX_PREC_FP64)
+        a = float((g * phi).sum() / (g * ag).sum())
+        ug = a * g[0]
+        out["lattice"].append(energy_error_ratio(op, u[j], lift_avg(u[j])))
+        out["one_step"].append(energy_error_ratio(op, u[j], ug))
+        out["one_step_plus_lattice"].append(energy_error_ratio(op, u[j], ug + lift_avg(u[j] - ug)))
+    return out
+
+
 def evaluate(net: int, data, hw: int, nr: int, nz: int, tol: float = 1e-8, method: int = AX_PCG_MIXED):
     """Per held-out sample: iterations and wall time from zero and from the
     network's guess (guess time included), with the residual gate on, and
