@@ -246,6 +246,15 @@ struct SmallPcgArgs {
   RhsState *st;
   int nr, nz, pitch, pitchz;
   int nch;                             // output chunks per row of the dense transforms
+  int msm;                             // set by the launcher: transform rows in shared memory
+  // Whole solve in the launch (f non-null): phi = r f, x = 0, r = phi and the
+  // stop threshold tol2 ||phi||^2 are formed first (the state is initialised
+  // as sc_start does), and u = x is written at the end.
+  const double *f;                     // dense [nr][nz] right-hand side, or null
+  double *u;                           // dense [nr][nz] solution (with f)
+  const double *R;                     // r_i [nr]
+  double tol2;
+  int max_iter;
   int *err;                            // set when a bounded wait expired
   unsigned polls;                      // wait limit (0: the default)
   int stall;                           // test of the expiry path: CTA 0 skips its first barrier

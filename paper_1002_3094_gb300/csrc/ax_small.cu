@@ -40,60 +40,131 @@ namespace ax {
 namespace {
 
 constexpr int kSmallThreads = 256;
-constexpr unsigned kSmallPolls = 1u << 24;  // x ~32 ns: about half a second
+constexpr unsigned kSmallPolls = 1u << 24;  // spins of an L2 load each: a second or so
 constexpr int kPartPQ = 0, kPartRR = 1, kPartRZ = 2;
-
-__device__ __forceinline__ unsigned ld_volatile(const unsigned *p) {
-  return *reinterpret_cast<const volatile unsigned *>(p);
-}
+constexpr size_t kSmallSmem = 100 * 1024;  // bound of the shared-memory copy of the transform rows
 
 // Grid barrier with a bounded wait; false on every thread of the CTA when the
-// wait expired (or, with skip, when the CTA left without arriving).
+// wait expired (or, with skip, when the CTA left without arriving).  bar[0]
+// counts arrivals over the whole launch: a CTA adds 1 (a release reduction,
+// no round trip) and waits until the count reaches G times the number of
+// barriers it has passed (acquire loads; unsigned differences, so the count
+// may wrap).
 __device__ bool grid_sync(unsigned *bar, unsigned G, unsigned &gen, unsigned polls, int *err, bool skip) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g0 = gen;
+    const unsigned target = G * (gen + 1);
     if (skip) {
       ok = 0;
     } else {
-      __threadfence();
-      if (atomicAdd(&bar[0], 1u) == G - 1) {
-        atomicExch(&bar[0], 0u);
-        __threadfence();
-        atomicAdd(&bar[1], 1u);
-      } else {
-        unsigned i = 0;
-        while (ld_volatile(&bar[1]) == g0) {
-          if (++i >= polls) {
-            ok = 0;
-            break;
-          }
-          __nanosleep(32);
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+      unsigned i = 0;
+      for (;;) {
+        unsigned c;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(bar) : "memory");
+        if ((int)(c - target) >= 0) break;
+        if (++i >= polls) {
+          ok = 0;
+          break;
         }
       }
-      __threadfence();
     }
     if (!ok) atomicExch(err, 1);
-    gen = g0 + 1;
+    gen += 1;
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
 }
 
+// Thomas on mode column l of a.t (in place), one warp: lane L owns rows
+// L C .. L C + C - 1.  Forward g_i = b_i IP_i + al_i g_{i-1}, al_i =
+// -E_{i-1} IP_i, and backward y_i = g_i + be_i y_{i+1}, be_i = -E_i IP_i, each
+// run per chunk with zero carry-in; the chunks' affine carry maps
+// (out = A + M in) are composed over the lanes by shuffles and the true
+// carries applied.  C is a template parameter so that no FP64 operation is
+// issued for rows a lane does not own (GB300's FP64 pipe is narrow).
+template <int C>
+__device__ __forceinline__ void thomas_warp(const SmallPcgArgs &a, int l, int lane) {
+  const int nr = a.nr, P = a.pitch, i0 = lane * C;
+  double v[C], al[C], be[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int i = i0 + j;
+    v[j] = 0.0;
+    al[j] = 0.0;
+    be[j] = 0.0;
+    if (i < nr) {
+      const double ip = __ldg(a.IP + (size_t)i * P + l);
+      al[j] = i > 0 ? -__ldg(a.E + i - 1) * ip : 0.0;
+      be[j] = -__ldg(a.E + i) * ip;
+      v[j] = __ldcg(a.t + (size_t)i * P + l) * ip;
+    }
+  }
+  double g = 0.0, mu = 1.0;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    g = fma(al[j], g, v[j]);
+    mu *= al[j];
+    v[j] = g;
+  }
+  double A = g, M = mu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, off), Mp = __shfl_up_sync(0xffffffffu, M, off);
+    if (lane >= off) {
+      A = fma(M, Ap, A);
+      M *= Mp;
+    }
+  }
+  double d = __shfl_up_sync(0xffffffffu, A, 1);
+  if (lane == 0) d = 0.0;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    d *= al[j];
+    v[j] += d;
+  }
+  double y = 0.0, nu = 1.0;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    y = fma(be[j], y, v[j]);
+    nu *= be[j];
+    v[j] = y;
+  }
+  A = y;
+  M = nu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double An = __shfl_down_sync(0xffffffffu, A, off), Mn = __shfl_down_sync(0xffffffffu, M, off);
+    if (lane + off < 32) {
+      A = fma(M, An, A);
+      M *= Mn;
+    }
+  }
+  double e = __shfl_down_sync(0xffffffffu, A, 1);
+  if (lane == 31) e = 0.0;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    e *= be[j];
+    const int i = i0 + j;
+    if (i < nr) a.t[(size_t)i * P + l] = v[j] + e;
+  }
+}
+
 __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcgArgs a) {
   __shared__ double red[kSmallThreads / 32];
   __shared__ double row[kSmallMaxNz];
+  extern __shared__ double msm[];  // a.msm: this CTA's rows of F and F^T, row stride nz + 1
   __shared__ double bc;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nr = a.nr, nz = a.nz, P = a.pitch, PZ = a.pitchz;
   const unsigned polls = a.polls ? a.polls : kSmallPolls;
   unsigned gen = 0;
   bool stall = a.stall != 0 && b == 0;
-  RhsState s = *a.st;  // the same state in every thread
-  if (s.state != kActive) return;
+  RhsState s = *a.st;  // the same state in every thread (overwritten below with a.f)
+  if (a.f == nullptr && s.state != kActive) return;
 
   auto sync = [&]() {
     const bool ok = grid_sync(a.bar, (unsigned)G, gen, polls, a.err, stall);
@@ -109,14 +180,32 @@ __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcg
   auto total = [&](int kind) {
     __syncthreads();
     if (warp == 0) {
+      // G <= 256: up to 8 loads per lane, all issued before the sum
+      double t[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t[j] = lane + 32 * j < G ? __ldcg(a.part + kind * G + lane + 32 * j) : 0.0;
       double v = 0.0;
-      for (int j = lane; j < G; j += 32) v += __ldcg(a.part + kind * G + j);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v += t[j];
       v = warp_sum(v);
       if (lane == 0) bc = v;
     }
     __syncthreads();
     return bc;
   };
+
+  // Every CTA transforms one output chunk c (see small_pcg_grid): with a.msm
+  // its rows of F and F^T are read once into shared memory.
+  const int CHs = (nz + a.nch - 1) / a.nch, c_own = b % a.nch;
+  if (a.msm) {
+    const int o0 = c_own * CHs, rows_m = min(CHs, nz - o0);
+    for (int e = tid; e < rows_m * nz; e += kSmallThreads) {
+      const int o = e / nz, k = e % nz;
+      msm[o * (nz + 1) + k] = __ldg(a.F + (size_t)(o0 + o) * nz + k);
+      msm[(CHs + o) * (nz + 1) + k] = __ldg(a.Ft + (size_t)(o0 + o) * nz + k);
+    }
+    __syncthreads();
+  }
 
   // r is double-buffered: rbuf[rsel] is the current residual
   double *rbuf[2] = {a.r, a.r2};
@@ -159,8 +248,14 @@ __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcg
         const int o = ob + grp;
         const bool valid = o < o1;
         double v = 0.0;
-        if (valid)
-          for (int k = sub; k < nz; k += 8) v = fma(__ldg(M + (size_t)o * nz + k), row[k], v);
+        if (valid) {
+          if (a.msm) {
+            const double *mr = msm + (size_t)((mode == 2 ? CHs : 0) + (o - o0)) * (nz + 1);
+            for (int k = sub; k < nz; k += 8) v = fma(mr[k], row[k], v);
+          } else {
+            for (int k = sub; k < nz; k += 8) v = fma(__ldg(M + (size_t)o * nz + k), row[k], v);
+          }
+        }
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
@@ -176,81 +271,17 @@ __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcg
     }
   };
 
-  // ---- mode solves on t, one warp per mode column
+  // ---- mode solves on t, one warp per mode column (columns spread over the
+  // CTAs first: GB300's FP64 pipe is narrow, so one SM should not take many)
   auto mode_solves = [&]() {
-    const int C = (nr + 31) / 32;  // rows per lane (<= 16)
-    const int i0 = lane * C;
+    const int C = (nr + 31) / 32;
     const int nw = G * (kSmallThreads / 32);
-    for (int l = b * (kSmallThreads / 32) + warp; l < nz; l += nw) {
-      double v[16];
-      // forward, zero carry-in: g_i = b_i IP_i + al_i g_{i-1}, al_i = -E_{i-1} IP_i
-      double g = 0.0, mu = 1.0;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = i0 + j;
-        v[j] = 0.0;
-        if (j < C && i < nr) {
-          const double ip = __ldg(a.IP + (size_t)i * P + l);
-          const double al = i > 0 ? -__ldg(a.E + i - 1) * ip : 0.0;
-          g = fma(al, g, __ldcg(a.t + (size_t)i * P + l) * ip);
-          mu *= al;
-          v[j] = g;
-        }
-      }
-      // carry maps g_out = A + M g_in, composed over the lanes below
-      double A = g, M = mu;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const double Ap = __shfl_up_sync(0xffffffffu, A, off), Mp = __shfl_up_sync(0xffffffffu, M, off);
-        if (lane >= off) {
-          A = fma(M, Ap, A);
-          M *= Mp;
-        }
-      }
-      double d = __shfl_up_sync(0xffffffffu, A, 1);
-      if (lane == 0) d = 0.0;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = i0 + j;
-        if (j < C && i < nr) {
-          const double al = i > 0 ? -__ldg(a.E + i - 1) * __ldg(a.IP + (size_t)i * P + l) : 0.0;
-          d *= al;
-          v[j] += d;
-        }
-      }
-      // backward, zero carry-in from below: y_i = g_i + be_i y_{i+1}, be_i = -E_i IP_i
-      double y = 0.0, nu = 1.0;
-#pragma unroll
-      for (int j = 15; j >= 0; --j) {
-        const int i = i0 + j;
-        if (j < C && i < nr) {
-          const double be = -__ldg(a.E + i) * __ldg(a.IP + (size_t)i * P + l);
-          y = fma(be, y, v[j]);
-          nu *= be;
-          v[j] = y;
-        }
-      }
-      A = y;
-      M = nu;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const double An = __shfl_down_sync(0xffffffffu, A, off), Mn = __shfl_down_sync(0xffffffffu, M, off);
-        if (lane + off < 32) {
-          A = fma(M, An, A);
-          M *= Mn;
-        }
-      }
-      double e = __shfl_down_sync(0xffffffffu, A, 1);
-      if (lane == 31) e = 0.0;
-#pragma unroll
-      for (int j = 15; j >= 0; --j) {
-        const int i = i0 + j;
-        if (j < C && i < nr) {
-          const double be = -__ldg(a.E + i) * __ldg(a.IP + (size_t)i * P + l);
-          e *= be;
-          a.t[(size_t)i * P + l] = v[j] + e;
-        }
-      }
+    for (int l = warp * G + b; l < nz; l += nw) {
+      if (C <= 1) thomas_warp<1>(a, l, lane);
+      else if (C <= 2) thomas_warp<2>(a, l, lane);
+      else if (C <= 4) thomas_warp<4>(a, l, lane);
+      else if (C <= 8) thomas_warp<8>(a, l, lane);
+      else thomas_warp<16>(a, l, lane);
     }
   };
 
@@ -289,9 +320,38 @@ __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcg
 
   bool failed = false, done = false;
   int status = AX_OK;
+  if (a.f != nullptr) {
+    // phi = r f, r = phi, x = 0 (A x = 0), and the state of sc_start
+    double acc = 0.0;
+    for (int n = b * kSmallThreads + tid; n < N; n += gstride) {
+      const int i = n / nz, k = n % nz;
+      const size_t e = (size_t)i * P + k;
+      const double v = __ldg(a.R + i) * __ldg(a.f + n);
+      const_cast<double *>(a.phi)[e] = v;
+      a.r[e] = v;
+      a.x[e] = 0.0;
+      acc = fma(v, v, acc);
+    }
+    put(kPartRR, acc);
+    if (!sync()) return;
+    const double bb = total(kPartRR);
+    s.rr = bb;
+    s.bb = bb;
+    s.thresh2 = a.tol2 * bb;
+    s.iters = 0;
+    s.max_iter = a.max_iter;
+    s.beta = 0.0;
+    s.status = AX_OK;
+    if (!isfinite(bb)) {
+      failed = true;
+      status = AX_ERR_BREAKDOWN;
+    } else if (bb <= s.thresh2 || bb == 0.0) {
+      done = true;
+    }
+  }
   double rho = 0.0, beta = 0.0, alpha = 0.0, rr = s.rr;
   // z = B^-1 r, rho = (r, z)
-  {
+  if (!failed && !done) {
     double acc = 0.0;
     transform(1, 0.0, nullptr, acc);
     if (!sync()) return;
@@ -316,7 +376,7 @@ __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcg
       auto pv = [&](int i, int k) {
         if (i < 0 || i >= nr || k < 0 || k >= nz) return 0.0;
         const size_t e = (size_t)i * P + k;
-        return fma(beta, __ldcg(pold + e), __ldcg(a.z + e));
+        return beta == 0.0 ? __ldcg(a.z + e) : fma(beta, __ldcg(pold + e), __ldcg(a.z + e));  // p_1 = z
       };
       double acc = 0.0;
       for (int n = b * kSmallThreads + tid; n < N; n += gstride) {
@@ -394,6 +454,13 @@ __global__ void __launch_bounds__(kSmallThreads) pcg_small_kernel(const SmallPcg
     beta = rz / rho;
     rho = rz;
   }
+  if (a.u != nullptr) {
+    // u = x (x is final: its last update came before the last barrier)
+    for (int n = b * kSmallThreads + tid; n < N; n += gstride) {
+      const int i = n / nz, k = n % nz;
+      a.u[n] = __ldcg(a.x + (size_t)i * P + k);
+    }
+  }
   if (b == 0 && tid == 0) {
     s.iters = iters;
     s.rr = rr;
@@ -437,16 +504,27 @@ int small_pcg_grid(int nr, int nz, int *nch) {
   // at most one CTA per SM's worth of the co-resident limit
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  const int target = std::min(maxg, std::max(sms, 1));
+  const int target = std::min(std::min(maxg, std::max(sms, 1)), 256);  // the partial sums take <= 256
   int c = std::max(1, std::min(target / std::max(nr, 1), nz / 16));
   *nch = c;
   return std::min(nr * c, target);
 }
 
-cudaError_t launch_small_pcg(const SmallPcgArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_small_pcg(const SmallPcgArgs &a0, int grid, cudaStream_t s) {
+  SmallPcgArgs a = a0;
+  // Each CTA's items share one output chunk (nch = 1, or grid = nr nch by
+  // small_pcg_grid), so its transform rows go to shared memory where they fit.
+  const int CH = (a.nz + a.nch - 1) / a.nch;
+  const size_t smem = 2 * (size_t)CH * (a.nz + 1) * sizeof(double);
+  a.msm = (a.nch == 1 || grid == a.nr * a.nch) && smem <= kSmallSmem ? 1 : 0;
+  const size_t dyn = a.msm ? smem : 0;
+  if (dyn > 48 * 1024) {
+    cudaError_t e = ensure_smem_attr((const void *)pcg_small_kernel, dyn);
+    if (e != cudaSuccess) return e;
+  }
   note_launch();
-  void *args[] = {const_cast<SmallPcgArgs *>(&a)};
-  return cudaLaunchCooperativeKernel((const void *)pcg_small_kernel, dim3(grid), dim3(kSmallThreads), args, 0, s);
+  void *args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void *)pcg_small_kernel, dim3(grid), dim3(kSmallThreads), args, dyn, s);
 }
 
 }  // namespace ax

@@ -96,6 +96,7 @@ struct Workspace {
   int small_stall_test = 0;     // 1: the next persistent launch lets its barrier waits run out
   double *small_buf = nullptr;  // its second residual buffer and transformed field [2][nr][pitch]
   unsigned *small_bar = nullptr;  // its grid-barrier words [2]
+  int *h_flag = nullptr;          // pinned host copy of the expiry flag
   cudaStream_t copy = nullptr;  // copy stream of those chunks
   cudaEvent_t cev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // per right-hand-side completion times (ms since lat_t0) of the current
@@ -1223,8 +1224,11 @@ bool small_applies(const ax_operator *op, int m) {
          (long long)op->nr * op->nz <= kSmallMaxN && op->cstride == 0;
 }
 
-// Runs it from the state sc_start left (r = phi - A x in r64).
-int small_pcg_run(ax_operator *op, cudaStream_t s) {
+// Runs it from the state sc_start left (r = phi - A x in r64); or, with f
+// (dense, device), the whole solve: phi, r, x = 0 and the state are formed in
+// the launch, u (dense, device) is written at its end, and info is filled.
+int small_pcg_run(ax_operator *op, cudaStream_t s, const double *f = nullptr, double *u = nullptr,
+                  double tol = 0.0, int max_iter = 0, ax_solve_info *info = nullptr) {
   Workspace *w = op->ws;
   int nch = 1;
   const int grid = small_pcg_grid(op->nr, op->nz, &nch);
@@ -1232,15 +1236,20 @@ int small_pcg_run(ax_operator *op, cudaStream_t s) {
   const double *F = dense_table(op->device, op->nz, op->bc_z);
   int *flag = tc_flag(op->device);
   if (!F || !flag) return AX_ERR_OOM;
-  const size_t f = field_elems(op);
+  const size_t fe = field_elems(op);
   {
     std::lock_guard<std::recursive_mutex> lock(g_alloc_capture_mutex);
-    if (!w->small_buf) AX_TRY(dalloc(&w->small_buf, 2 * f));
+    if (!w->small_buf) AX_TRY(dalloc(&w->small_buf, 2 * fe));
     if (!w->small_bar) AX_TRY(dalloc(&w->small_bar, 2));
+    if (!w->h_flag) AX_TRY(cudaMallocHost(&w->h_flag, sizeof(int)));
   }
   AX_TRY(cudaMemsetAsync(w->small_bar, 0, 2 * sizeof(unsigned), s));
-  AX_TRY(cudaMemsetAsync(w->pa64, 0, f * sizeof(double), s));
   SmallPcgArgs a{};
+  a.f = f;
+  a.u = u;
+  a.R = op->c64.R;
+  a.tol2 = tol * tol;
+  a.max_iter = max_iter;
   const Coef<double> &c = op->c64;
   a.CR = c.CR;
   a.CZ = c.CZ;
@@ -1257,7 +1266,7 @@ int small_pcg_run(ax_operator *op, cudaStream_t s) {
   a.pa = w->pa64;
   a.pb = w->pb64;
   a.q = w->q64;
-  a.t = w->small_buf + f;
+  a.t = w->small_buf + fe;
   a.part = part_ptr(w, kPartA);
   a.bar = w->small_bar;
   a.st = w->st;
@@ -1273,15 +1282,27 @@ int small_pcg_run(ax_operator *op, cudaStream_t s) {
     w->small_stall_test = 0;
   }
   AX_TRY(launch_small_pcg(a, grid, s));
-  int hf = 0;
-  AX_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // one synchronisation for the expiry flag and (whole solve) the state
+  AX_TRY(cudaMemcpyAsync(w->h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (f) AX_TRY(cudaMemcpyAsync(w->h_st, w->st, sizeof(RhsState), cudaMemcpyDeviceToHost, s));
   AX_TRY(cudaStreamSynchronize(s));
-  if (hf) {
+  if (*w->h_flag) {
     AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
     snprintf(g_last_error, sizeof(g_last_error), "a grid-barrier wait of the persistent small-grid solve expired");
     return AX_ERR_TIMEOUT;
   }
-  return AX_OK;
+  if (!f) return AX_OK;
+  const RhsState &h = w->h_st[0];
+  int st = h.status;
+  if (st == AX_OK && h.state != kDone) st = AX_ERR_NO_CONVERGENCE;
+  if (info) {
+    info[0].iters = h.iters;
+    info[0].outer = 0;
+    info[0].rel_res = h.bb > 0.0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    info[0].guess_accepted = 0;
+    info[0].status = st;
+  }
+  return st;
 }
 
 // Test of the staged stencil's expiry path (option "stencil_stall_test"), once:
@@ -2291,6 +2312,7 @@ int ax_destroy_operator(ax_operator *op) {
     dfree(w->split);
     dfree(w->small_buf);
     dfree(w->small_bar);
+    if (w->h_flag) cudaFreeHost(w->h_flag);
     if (w->scratch) cudaFree(w->scratch);
     if (w->cap) cudaStreamDestroy(w->cap);
     if (w->copy) cudaStreamDestroy(w->copy);
@@ -3071,6 +3093,11 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
   const size_t field = field_elems(op), dense = (size_t)nr * nz * m;
   int rc;
   if ((rc = ensure_base(op, m)) != AX_OK) return rc;
+  if (method == AX_PCG_FP64 && !(flags & (AX_FLAG_HOST_BUFFERS | AX_FLAG_USE_GUESS)) && small_applies(op, m)) {
+    // the whole solve as one persistent launch
+    if ((rc = ensure_vec64(op, m, false)) != AX_OK) return rc;
+    return small_pcg_run(op, s, f, u, tol, max_iter, info);
+  }
   const bool host = (flags & AX_FLAG_HOST_BUFFERS) != 0;
   const bool guess = (flags & AX_FLAG_USE_GUESS) != 0;
   const bool check_guess = guess && (flags & AX_FLAG_CHECK_GUESS) != 0;

@@ -12,6 +12,8 @@ warp-cooperative chunked Thomas (Section 3's dichotomy observation).  It must
   - cover sine and cosine z-transforms, one-row and one-column grids, the
     largest sizes it takes, warm starts (AX_FLAG_USE_GUESS) including an
     exact guess (no iteration), and max_iter (AX_ERR_NO_CONVERGENCE);
+  - take host buffers (set-up on the host side, then the persistent launch)
+    and a zero right-hand side (converged at the start, u = 0);
   - on the expiry path (option small_stall_test: one CTA leaves before the
     first barrier, so the others' bounded waits run out) return
     AX_ERR_TIMEOUT, with the next solve on the same context correct.
@@ -116,6 +118,16 @@ def test_option_and_fallbacks(cuda):
     assert st == P.AX_OK
     for j in range(2):
         assert _true_res(ora, f[j], u.cpu().numpy()[j]) <= 1e-10
+    # host buffers: the set-up runs on the host side, then the persistent launch
+    fh = np.ascontiguousarray(f[:1])
+    uh = np.zeros_like(fh)
+    st, info = P.ax_solve(op, fh, uh, 1, 1e-10, 5000, P.AX_PCG_FP64, P.AX_FLAG_HOST_BUFFERS)
+    assert st == P.AX_OK and _true_res(ora, f[0], uh[0]) <= 1e-10
+    # a zero right-hand side: converged at the start, u = 0
+    z = torch.zeros((1, 64, 48), dtype=torch.float64, device=cuda)
+    uz = torch.ones_like(z)
+    st, info = P.ax_solve(op, z, uz, 1, 1e-10, 5000, P.AX_PCG_FP64)
+    assert st == P.AX_OK and info[0]["iters"] == 0 and float(uz.abs().max()) == 0.0
     P.ax_destroy_operator(op)
 
 
