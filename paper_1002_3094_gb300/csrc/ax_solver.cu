@@ -3470,6 +3470,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
       gw->cheb_steps = ow->cheb_steps;
       gw->cheb_widen = ow->cheb_widen;
       gw->cheb_check = ow->cheb_check;
+      gw->small_path = ow->small_path;
     }
     gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz; gop->bc_z = o->bc_z;
     gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;

@@ -254,6 +254,7 @@ def test_batched_mixes_both_boundaries(cuda, method):
         kr, kz, q = sample_operator_inputs(med, nr, nz, bc_z=bc)
         t = [torch.from_numpy(x).to(cuda) for x in (kr, kz, q)]
         op = P.ax_setup_operator(*t, nr, nz, bc_z=bc)
+        P.ax_set_option(op, "small_path", 0)  # the batch's kernels for the single solves too
         g = O.Grid(nr, nz, bc_z=bc)
         ora = O.Operator(kr, kz, q, g)
         f = sample_rhs(med, nr, nz, bc_z=bc)[0]

@@ -207,6 +207,9 @@ def test_batched_rhs_equal_single(cuda):
     to solving it alone."""
     med = layered_inclusion_medium(n_rhs=3, nominal_n=96)
     pr = Pair(med, 96, 80, cuda)
+    # single right-hand sides through the same graph-replayed kernels as the
+    # batch (the persistent small-grid path sums in another order)
+    P.ax_set_option(pr.op, "small_path", 0)
     f = sample_rhs(med, 96, 80)
     _, info_b, ub = _solve(pr, f, P.AX_PCG_FP64, 1e-9)
     for j in range(3):
@@ -406,6 +409,7 @@ def test_batched_uneven_instances_equal_single_solves(cuda, method):
     pairs, fs, us = [], [], []
     for nr, nz, med in insts:
         pr = Pair(med, nr, nz, cuda)
+        P.ax_set_option(pr.op, "small_path", 0)  # the batch's kernels for the single solves too
         pairs.append(pr)
         fs.append(pr.dev_array(sample_rhs(med, nr, nz)[0]))
         us.append(torch.zeros((nr, nz), dtype=torch.float64, device=cuda))
