@@ -203,7 +203,10 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    the mode solves then apply D; 12 on 16-column tiles,
  *                    nr <= 1024), 10 and 11 that kernel
  *                    with the factors of a column tile kept in registers
- *                    over 4 or 8 right-hand sides, 2..8 pipelined
+ *                    over 4 or 8 right-hand sides, 14 that kernel fed
+ *                    mode-major by the forward tensor-core transform (the
+ *                    factors in the same layout; no shared-memory staging of
+ *                    the input; row-major inputs take 9), 2..8 pipelined
  *                    column-tile kernels on the row-scaled systems; an id
  *                    whose column does not fit nr is refused
  *   "stencil_kernel" stencil (Eq. scheme_op_r_z) of the fused FP32 iteration

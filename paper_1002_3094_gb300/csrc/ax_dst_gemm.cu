@@ -301,6 +301,36 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
         for (int c = half * 2; c < half * 2 + 2; ++c) {
           const int l0 = nt * kBN + c * 32;
           if (!__any_sync(0xffffffffu, grow < a.nr) || l0 >= ne) break;  // nothing left for this warp
+          if (a.tout) {
+            // mode-major output: lane = row, so every store of the warp is a run
+            // of 32 consecutive rows of one column (no transpose needed)
+            float P[32], Q[32];
+            tmem_ld32(tP + (unsigned)(c * 32), P);
+            if (a.ktiles > a.kbe) {
+              tmem_ld32(tP + (unsigned)(kBN + c * 32), Q);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) Q[i] = 0.f;  // n = 1: no odd column
+            }
+            if (grow < a.nr) {
+              float *ob = a.out + (size_t)m * n * a.tpitch + grow;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                const int l = l0 + i;
+                if (l < ne) {
+                  if (a.cosfwd) {  // even output columns from P, odd ones from Q
+                    ob[(size_t)(2 * l) * a.tpitch] = rsc * P[i];
+                    if (2 * l + 1 < n) ob[(size_t)(2 * l + 1) * a.tpitch] = rsc * Q[i];
+                  } else {
+                    ob[(size_t)l * a.tpitch] = rsc * (P[i] + Q[i]);
+                    const int lm = n - 1 - l;
+                    if (lm != l) ob[(size_t)lm * a.tpitch] = rsc * (P[i] - Q[i]);
+                  }
+                }
+              }
+            }
+            continue;
+          }
           if (rr == nullptr) {
             // Write-back transposed through this warp's 32 x 32 shared tile
             // (XOR-swizzled: conflict-free in both directions), so that every

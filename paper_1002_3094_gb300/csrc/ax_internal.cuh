@@ -82,6 +82,7 @@ struct Coef {
   T *CW = nullptr;   // [8 nz]        zero-flux z only: cosine-transform factors of mode l
                      //               (forward: scaled cos/sin of phi_l, 3 phi_l; inverse:
                      //               cos/sin of phi_l, 2 phi_l; phi_l = pi l / (2 nz))
+  T *IPST = nullptr; // [nz][tpitch]  IPS mode-major (FP32 mode-solve kernel 14)
   T *RK = nullptr;   // [2 P]         Rader: DFT of the permuted kernel W^(g^-m)
   T *RT = nullptr;   // [2 P]         Rader: (cos, sin)(2 pi j / P)
   // FP32 only: the mode systems scaled to unit couplings, T'_l = D T_l D with
@@ -145,6 +146,7 @@ enum { kProfStencil = 0, kProfDstFwd = 1, kProfTridiag = 2, kProfDstInv = 3, kPr
 
 struct ax_operator {
   int nr = 0, nz = 0, pitch = 0, pitchz = 0;
+  int tpitch = 0;  // rows per mode column of the mode-major layout (nr rounded up to 32)
   int bc_z = 0;  // 0: u = 0 at z = 0, lz (sine transform); 1: zero flux there (cosine pair)
   // A group operator stacks the coefficient tables of several operators of one
   // grid shape; right-hand side m then uses table m (strides in elements).
@@ -349,6 +351,10 @@ struct GemmDstArgs {
   // (the row scaling D of the pipelined mode solves)
   const float *rowscale;
   long long rsstride;
+  // tout: the output is written mode-major, column l of right-hand side m as
+  // the run out[(m n + l) tpitch + i], i < nr (no p update, no partials); the
+  // input of the mode-solve kernel 14
+  int tout, tpitch;
 };
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);
@@ -393,6 +399,12 @@ struct TriArgs {
   // T'^-1 b'; the pipelined kernels); 0: the plain systems of IP / E.  Set
   // exactly when tridiag_effective(...) >= 2.
   int prescaled;
+  // kernel 14: `in` is mode-major (column l of right-hand side m at
+  // in[(m nz + l) tpitch + i]) and IPST the factors IPS in the same layout
+  // ([nz][tpitch], tcstride elements per right-hand side for stacked groups)
+  const T *IPST;
+  long long tcstride;
+  int tpitch;
 };
 
 template <typename T>

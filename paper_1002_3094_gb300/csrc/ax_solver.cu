@@ -1044,7 +1044,7 @@ void free_coef(Coef<T> &c) {
   dfree(c.CR); dfree(c.CZ); dfree(c.W); dfree(c.IP); dfree(c.E); dfree(c.R); dfree(c.TW); dfree(c.HW); dfree(c.CW);
   dfree(c.RK); dfree(c.RT);
   dfree(c.CRl); dfree(c.CZl); dfree(c.Wl);
-  dfree(c.IPS); dfree(c.RS);
+  dfree(c.IPS); dfree(c.RS); dfree(c.IPST);
 }
 
 // ---------------------------------------------------------------------------
@@ -1348,14 +1348,26 @@ int tc_mode_variant(const ax_operator *op, int m) {
   return tridiag_effective(op->nr, op->tri_variant, m, op->c32.IPS != nullptr && op->c32.RS != nullptr);
 }
 bool tc_scaled(const ax_operator *op, int m) { return tc_mode_variant(op, m) >= 2; }
+// The forward transform of a preconditioner application writes mode-major
+// for the mode-solve kernel 14, when that layout fits the buffer it writes
+// (m nr pitch floats: nz tpitch <= nr pitch) and its factor table exists.
+bool tc_tr_mode(const ax_operator *op, int m) {
+  return tc_mode_variant(op, m) == 14 && op->c32.IPST != nullptr && op->tpitch > 0 &&
+         (long long)op->nz * op->tpitch <= (long long)op->nr * op->pitch;
+}
 
 // scaled: multiply every output row by D (the row scale of the pipelined mode
 // solves); set for the two transforms of a preconditioner application
 // exactly when tc_scaled(op, m).
 void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, bool inverse, float *out,
                   const RhsState *st, int mask, const float *r, double *partial, cudaStream_t s, int three = -1,
-                  float *pa = nullptr, float *pb = nullptr, float *x = nullptr, bool scaled = false) {
+                  float *pa = nullptr, float *pb = nullptr, float *x = nullptr, bool scaled = false,
+                  bool tout = false) {
   GemmDstArgs g{};
+  if (tout) {  // mode-major output for the mode-solve kernel 14 (forward only)
+    g.tout = 1;
+    g.tpitch = op->tpitch;
+  }
   if (scaled) {
     g.rowscale = op->c32.RS;
     g.rsstride = op->estride;
@@ -1414,6 +1426,13 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
   TriArgs<float> t = tri_args<float>(op, m, z, tmp, st, mask);
   t.variant = tc_mode_variant(op, m);
   t.prescaled = tc_scaled(op, m);
+  if (tc_tr_mode(op, m)) {  // z is mode-major (the forward transform wrote it so)
+    t.IPST = op->c32.IPST;
+    t.tcstride = op->cstride != 0 ? (long long)op->nz * op->tpitch : 0;
+    t.tpitch = op->tpitch;
+  } else if (t.variant == 14) {
+    t.variant = 9;
+  }
   if (tridiag_split_ok(op->nr)) {
     t.split = split;
     t.split_mtiles = g.mtiles;
@@ -1456,7 +1475,8 @@ void precond_apply(const ax_operator *op, int m, const T *r, T *z, const RhsStat
       const bool dm = tc_dot_in_modes(op);
       tc_split(op, m, op->nr, r, sp, st, mask, s);
       const bool sc = tc_scaled(op, m);
-      tc_transform(op, m, op->nr, sp, false, z, st, mask, nullptr, nullptr, s, -1, nullptr, nullptr, nullptr, sc);
+      tc_transform(op, m, op->nr, sp, false, z, st, mask, nullptr, nullptr, s, -1, nullptr, nullptr, nullptr, sc,
+                   tc_tr_mode(op, m));
       tc_mode_solve(op, m, z, tmp, sp, st, mask, s, dm ? prz : nullptr);
       tc_transform(op, m, op->nr, sp, true, z, st, mask, dm ? nullptr : r, dm ? nullptr : prz, s, -1, nullptr, nullptr,
                    nullptr, sc);
@@ -1539,7 +1559,8 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
       const bool sc = tc_scaled(op, m);
       {
         ProfScope ps(w, kProfDstFwd, units, s);
-        tc_transform(op, m, op->nr, sp, false, v.z, st, kActive, nullptr, nullptr, s, -1, nullptr, nullptr, nullptr, sc);
+        tc_transform(op, m, op->nr, sp, false, v.z, st, kActive, nullptr, nullptr, s, -1, nullptr, nullptr, nullptr, sc,
+                     tc_tr_mode(op, m));
       }
       {
         ProfScope ps(w, kProfScalar, 0.0, s);
@@ -2131,7 +2152,8 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
       unsigned char *sp = w->split;
       tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss);
       const bool sc = tc_scaled(op, m);
-      tc_transform(op, m, op->nr, sp, false, v.z, st, kCheck, nullptr, nullptr, ss, -1, nullptr, nullptr, nullptr, sc);
+      tc_transform(op, m, op->nr, sp, false, v.z, st, kCheck, nullptr, nullptr, ss, -1, nullptr, nullptr, nullptr, sc,
+                   tc_tr_mode(op, m));
       tc_mode_solve(op, m, v.z, v.q, sp, st, kCheck, ss, part_ptr(w, kPartC));
       note_launch();
       sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kCheck, 1);
@@ -2603,8 +2625,9 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "mode_kernel")) {
     // FP32 mode-solve kernel: 0 the default for nr, else a variant id of
-    // tridiag_variants (1 the staged register kernel, 2.. the pipelined
-    // column-tile kernels); ids that do not cover nr are refused
+    // tridiag_variants (1 the staged register kernel, 2..8 the pipelined
+    // column-tile kernels, 9..12 and 14 the row-scaled staged kernels); ids
+    // that do not cover nr are refused
     const int v = (int)value;
     if ((double)v != value || v < 0) return AX_ERR_INVALID_ARG;
     if (v != 0) {
@@ -2826,6 +2849,15 @@ int ax_setup_operator(const double *kappa_r, const double *kappa_z, const double
   AX_UP(float, c32.IPS, IPS) AX_UP(float, c32.RS, RS)
 #undef AX_UP
   {
+    // IPS mode-major for the mode-solve kernel 14: column l is the run of its
+    // nr factors, padded to tpitch with zeros
+    op->tpitch = (nr + 31) / 32 * 32;
+    std::vector<double> ipst((size_t)nz * op->tpitch, 0.0);
+    for (int a2 = 0; a2 < nr; ++a2)
+      for (int l = 0; l < nz; ++l) ipst[(size_t)l * op->tpitch + a2] = IPS[(size_t)a2 * P + l];
+    if (e == cudaSuccess) e = upload<float>(&op->c32.IPST, ipst);
+  }
+  {
     // low parts for the double-float residual: v64 = (float)v64 + lo
     auto lo_of = [](const std::vector<double> &v) {
       std::vector<double> lo(v.size());
@@ -2960,7 +2992,7 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
       tc_split(op, m, rows_per, a, sp, nullptr, -1, s);
       const bool sc = tc_scaled(op, m);
       tc_transform(op, m, rows_per, sp, false, b, nullptr, -1, nullptr, nullptr, s, tc_three, nullptr, nullptr, nullptr,
-                   sc);
+                   sc, rows_per == op->nr && tc_tr_mode(op, m));
       tc_mode_solve(op, m, b, a, sp, nullptr, -1, s);
       tc_transform(op, m, rows_per, sp, true, b, nullptr, -1, nullptr, nullptr, s, tc_three, nullptr, nullptr, nullptr,
                    sc);
@@ -3370,6 +3402,11 @@ cudaError_t build_group_coef(Coef<T> &g, const std::vector<const ax_operator *> 
     if (err == cudaSuccess) err = stack_table(&g.IPS, f, ips, s);
     if (err == cudaSuccess) err = stack_table(&g.RS, (size_t)o->nr, rs, s);
   }
+  if (pick(o).IPST != nullptr) {
+    std::vector<const T *> ipst;
+    for (auto *op : ops) ipst.push_back(pick(op).IPST);
+    if (err == cudaSuccess) err = stack_table(&g.IPST, (size_t)o->nz * o->tpitch, ipst, s);
+  }
   if (pick(o).CRl != nullptr) {
     std::vector<const T *> crl, czl, wl;
     for (auto *op : ops) {
@@ -3473,6 +3510,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
       gw->small_path = ow->small_path;
     }
     gop->nr = o->nr; gop->nz = o->nz; gop->pitch = o->pitch; gop->pitchz = o->pitchz; gop->bc_z = o->bc_z;
+    gop->tpitch = o->tpitch;
     gop->lr = o->lr; gop->lz = o->lz; gop->hr = o->hr; gop->hz = o->hz;
     gop->kappa_t = o->kappa_t; gop->q_t = o->q_t; gop->gamma1 = o->gamma1; gop->gamma2 = o->gamma2;
     for (const ax_operator *mo : mops) {  // Chebyshev bounds of each member

@@ -931,6 +931,195 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
 }
 
 // ---------------------------------------------------------------------------
+// Variant 14: the kernel above fed mode-major (FP32, row-scaled systems).
+//
+// The forward tensor-core transform writes rhat mode-major (tout): column l of
+// right-hand side m is a contiguous run of rows, and the factors IPS have the
+// same layout (IPST).  A lane's chunk of C2 rows of one column is then C2
+// contiguous floats, and the lanes of a warp (consecutive chunks of the same
+// column) read one contiguous run: data and factors go straight from global
+// memory to registers with 16-byte loads, with no shared-memory staging (the
+// staged kernels are bound by the shared-memory pipe).  Recurrences, carries,
+// partials and the write-back of the result through the CTA's shared tile into
+// the split operand are those of tridiag_reg2_kernel, whose layout the tile
+// keeps.
+// ---------------------------------------------------------------------------
+template <int C2, int WPC, int CW>
+__global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
+    tridiag_tr_kernel(const TriArgs<float> a) {
+  constexpr int NT = 32 * WPC * CW;
+  constexpr int kChunkWords = C2 * CW + 2;
+  static_assert(NT <= 1024 && (CW == 4 || CW == 8) && C2 % 4 == 0, "tile shape");
+  extern __shared__ __align__(16) float tsm3[];
+  __shared__ float xfa[CW][WPC], xfm[CW][WPC], xba[CW][WPC], xbm[CW][WPC];
+  __shared__ double red[NT / 32];
+  const int nr = a.nr;
+  float *ds = tsm3;
+  const int col0 = blockIdx.x * CW;
+  const int m = blockIdx.y;
+  if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = warp / WPC, h = warp % WPC;  // column, segment of the r-range
+  const int ci = h * 32 + lane;               // chunk index 0 .. NCH - 1
+  const int rbase = ci * C2;
+  const int col = col0 + w;
+  const bool cok = col < a.nz;
+  // the chunk's data and factors: C2 contiguous floats each (zeros past nr
+  // and past nz)
+  float v[C2], ip[C2];
+  {
+    const int colc = cok ? col : a.nz - 1;
+    const float *pv = a.in + ((size_t)m * a.nz + colc) * a.tpitch + rbase;
+    const float *pi = a.IPST + (size_t)m * a.tcstride + (size_t)colc * a.tpitch + rbase;
+#pragma unroll
+    for (int t = 0; t < C2; t += 4) {
+      const bool ok = cok && rbase + t < nr;  // a group of 4 rows lies inside tpitch (a multiple of 32)
+      const float4 d4 = ok ? *reinterpret_cast<const float4 *>(pv + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 f4 = ok ? __ldg(reinterpret_cast<const float4 *>(pi + t)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[t] = d4.x; v[t + 1] = d4.y; v[t + 2] = d4.z; v[t + 3] = d4.w;
+      ip[t] = f4.x; ip[t + 1] = f4.y; ip[t + 2] = f4.z; ip[t + 3] = f4.w;
+    }
+#pragma unroll
+    for (int t = 0; t < C2; ++t)
+      if (rbase + t >= nr) v[t] = ip[t] = 0.f;  // padding rows solve to zero
+  }
+  float b[C2];
+#pragma unroll
+  for (int t = 0; t < C2; ++t) b[t] = v[t];
+  // forward, zero carry-in
+  float g = 0.f, mu = 1.f;
+#pragma unroll
+  for (int t = 0; t < C2; ++t) {
+    g = ip[t] * (v[t] + g);
+    mu *= ip[t];
+    v[t] = g;
+  }
+  float A = g, M = mu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pa = __shfl_up_sync(0xffffffffu, A, off), pm = __shfl_up_sync(0xffffffffu, M, off);
+    if (lane >= off) {
+      A = fmaf(M, pa, A);
+      M *= pm;
+    }
+  }
+  float Ae = __shfl_up_sync(0xffffffffu, A, 1), Me = __shfl_up_sync(0xffffffffu, M, 1);
+  if (lane == 0) {
+    Ae = 0.f;
+    Me = 1.f;
+  }
+  if (WPC > 1) {
+    if (lane == 31) {
+      xfa[w][h] = A;
+      xfm[w][h] = M;
+    }
+    __syncthreads();
+  }
+  float cin = 0.f;
+  for (int j = 0; j < h; ++j) cin = fmaf(xfm[w][j], cin, xfa[w][j]);
+  const float gin = fmaf(Me, cin, Ae);
+  float pr = 1.f;
+#pragma unroll
+  for (int t = 0; t < C2; ++t) {
+    pr *= ip[t];
+    v[t] = fmaf(pr, gin, v[t]);
+  }
+  // backward, zero carry-in
+  float y = 0.f;
+  mu = 1.f;
+#pragma unroll
+  for (int t = C2 - 1; t >= 0; --t) {
+    y = fmaf(ip[t], y, v[t]);
+    mu *= ip[t];
+    v[t] = y;
+  }
+  A = y;
+  M = mu;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float pa = __shfl_down_sync(0xffffffffu, A, off), pm = __shfl_down_sync(0xffffffffu, M, off);
+    if (lane + off < 32) {
+      A = fmaf(M, pa, A);
+      M *= pm;
+    }
+  }
+  Ae = __shfl_down_sync(0xffffffffu, A, 1);
+  Me = __shfl_down_sync(0xffffffffu, M, 1);
+  if (lane == 31) {
+    Ae = 0.f;
+    Me = 1.f;
+  }
+  if (WPC > 1) {
+    if (lane == 0) {
+      xba[w][h] = A;
+      xbm[w][h] = M;
+    }
+    __syncthreads();
+  }
+  cin = 0.f;
+  for (int j = WPC - 1; j > h; --j) cin = fmaf(xbm[w][j], cin, xba[w][j]);
+  const float yin = fmaf(Me, cin, Ae);
+  pr = 1.f;
+  float dot = 0.f;
+  float *pd = ds + ci * kChunkWords;
+  auto wc = [&](int t) { return 2 * ((w >> 1) ^ reg2_sw<CW>(rbase + t)) + (w & 1); };
+#pragma unroll
+  for (int t = C2 - 1; t >= 0; --t) {
+    pr *= ip[t];
+    v[t] = fmaf(pr, yin, v[t]);
+    dot = fmaf(b[t], v[t], dot);  // (b', y') of this chunk: the (rhat, yhat) partial
+    pd[CW * t + wc(t)] = v[t];
+  }
+  if (a.partial != nullptr) {
+    const double sw = warp_sum((double)dot);
+    if (lane == 0) red[warp] = sw;
+  }
+  __syncthreads();
+  if (a.partial != nullptr && threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < NT / 32; ++i) tot += red[i];
+    a.partial[(size_t)m * kPartialStride + blockIdx.x] = tot;
+  }
+  // ---- write back: one thread per row, its CW columns (as tridiag_reg2_kernel)
+  const int ncol = min(CW, a.nz - col0);
+  for (int row = threadIdx.x; row < nr; row += NT) {
+    float x[CW];
+    const float *src = ds + row * CW + 2 * (row / C2);
+    const int sw = reg2_sw<CW>(row);
+#pragma unroll
+    for (int c = 0; c < CW; c += 2) {
+      const float2 f2 = *reinterpret_cast<const float2 *>(src + 2 * ((c >> 1) ^ sw));
+      x[c] = f2.x;
+      x[c + 1] = f2.y;
+    }
+    if (a.split != nullptr) {
+      if constexpr (CW == 8) {
+        split_store8(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      } else {
+        split_store4(a.split, m, row, col0, a.split_mtiles, a.split_ktiles, a.split_kbe, x);
+      }
+    } else {
+      float *o = a.out + (size_t)m * a.field + (size_t)row * a.pitch + col0;
+      if (ncol == CW) {
+#pragma unroll
+        for (int c = 0; c < CW; c += 4) *reinterpret_cast<float4 *>(o + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
+      } else {
+        for (int c = 0; c < ncol; ++c) o[c] = x[c];
+      }
+    }
+  }
+}
+
+template <int C2, int WPC, int CW>
+void launch_tridiag_tr(const TriArgs<float> &a, cudaStream_t s) {
+  constexpr int NT = 32 * WPC * CW;
+  const size_t smem = (size_t)(32 * WPC) * (C2 * CW + 2) * sizeof(float);
+  ensure_smem_attr((const void *)tridiag_tr_kernel<C2, WPC, CW>, smem);
+  dim3 grid((a.nz + CW - 1) / CW, a.m);
+  tridiag_tr_kernel<C2, WPC, CW><<<grid, NT, smem, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
 // Variants 10 and 11: the kernel above with the factors kept across right-hand
 // sides.  A CTA owns one column tile and R consecutive right-hand sides
 // (R = 4 or 8): it stages the factors of the tile once and keeps each lane's
@@ -1203,6 +1392,7 @@ int tridiag_variants(int nr, int *ids) {
     ids[n++] = 11;
   }
   if (nr <= 1024) ids[n++] = 12;
+  if (nr <= 4096) ids[n++] = 14;
   for (const PipeVariant &v : kPipeVariants)
     if (nr <= pipe_max_rows(v) && 2 * nr > pipe_max_rows(v)) ids[n++] = v.id;
   return n;
@@ -1278,6 +1468,19 @@ bool launch_tridiag_tile(const TriArgs<float> &a, cudaStream_t s) {
       else if (c2 <= 16) launch_tridiag_reg3<16, 2, 8>(a, R, s);
       else if (a.nr <= 2048) launch_tridiag_reg3<16, 4, 8>(a, R, s);
       else launch_tridiag_reg3<16, 8, 4>(a, R, s);
+      return true;
+    }
+  }
+  if (v == 14) {  // mode-major input (the forward transform wrote it so)
+    if (a.IPST == nullptr || a.tpitch == 0) {
+      v = 9;
+    } else {
+      const int c2 = (a.nr + 63) / 64;
+      if (c2 <= 4) launch_tridiag_tr<4, 2, 8>(a, s);
+      else if (c2 <= 8) launch_tridiag_tr<8, 2, 8>(a, s);
+      else if (c2 <= 16) launch_tridiag_tr<16, 2, 8>(a, s);
+      else if (a.nr <= 2048) launch_tridiag_tr<16, 4, 8>(a, s);
+      else launch_tridiag_tr<16, 8, 4>(a, s);
       return true;
     }
   }

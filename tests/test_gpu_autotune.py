@@ -48,7 +48,7 @@ def _setup(nr, nz, dev, n_rhs=4, instance=3):
 
 
 def _candidates(op):
-    ids = [v for v in range(1, 13) if P.ax_set_option(op, "mode_kernel", v, raise_on_error=False) == P.AX_OK]
+    ids = [v for v in range(1, 15) if P.ax_set_option(op, "mode_kernel", v, raise_on_error=False) == P.AX_OK]
     P.ax_set_option(op, "mode_kernel", 0)
     return ids
 

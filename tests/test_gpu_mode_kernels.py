@@ -5,7 +5,9 @@ The per-mode systems T_l y = b (Section 4.2, Eq. eq_trid; one fixed matrix
 per mode, Section 3, Eq. main_eq3) are solved by whichever kernel the
 option selects: 1 the staged register kernel, 9 the same on the row-scaled
 systems (12 on 16-column tiles), 10 and 11 that one with the factors kept
-over 4 or 8 right-hand sides, 2..8 the pipelined column-tile kernels (persistent CTAs, lanes along
+over 4 or 8 right-hand sides, 14 the staged kernel fed mode-major by the
+forward tensor-core transform (through the preconditioner and the solves; a
+row-major input, as in ax_apply_mode_solve, takes 9), 2..8 the pipelined column-tile kernels (persistent CTAs, lanes along
 the mode index, chunk carries composed by a shared-memory scan).  Each variant that covers nr must give
   - the backward error ||T_l y - b|| <= 2e-6 ||T_l|| ||y|| of every column
     (FP32), and the forward error against the oracle's Thomas <= 1e-3;
@@ -30,7 +32,7 @@ from workloads import layered_inclusion_medium  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = range(1, 13)
+VARIANTS = range(1, 15)
 
 
 @pytest.fixture(scope="module")
@@ -68,12 +70,13 @@ SHAPES = [(300, 37), (511, 64), (513, 100), (700, 130), (1024, 96), (1300, 45), 
 def test_variant_lists(cuda):
     """Each nr is covered by the register kernel and by the pipelined kernels
     whose column fits it with at most half idle; unknown ids are refused."""
-    reg = {1, 9, 10, 11}
+    reg = {1, 9, 10, 11, 14}
     for nr, want in [(64, reg | {12}), (300, reg | {2, 3, 12}), (1024, reg | {4, 5, 12}), (2047, reg | {6, 7}),
                      (4096, reg | {8}), (5000, set())]:
         op, _, _ = _setup(nr, 8, cuda)
         assert set(_covering(op)) == want, nr
         assert P.ax_set_option(op, "mode_kernel", 13, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+        assert P.ax_set_option(op, "mode_kernel", 15, raise_on_error=False) == P.AX_ERR_INVALID_ARG
         assert P.ax_set_option(op, "mode_kernel", 1.5, raise_on_error=False) == P.AX_ERR_INVALID_ARG
         P.ax_destroy_operator(op)
 
