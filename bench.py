@@ -71,6 +71,7 @@ KERNEL_SOURCES = {"stencil": [("ax_stencil.cu", "stencil_kernel")],
                   "mode_solve_scaled": [("ax_tridiag.cu", "tridiag_reg2_kernel")],
                   "mode_solve_reuse": [("ax_tridiag.cu", "tridiag_reg3_kernel")],
                   "mode_solve_pipe": [("ax_tridiag.cu", "tridiag_pipe_kernel")],
+                  "mode_solve_modemajor": [("ax_tridiag.cu", "tridiag_tr_kernel")],
                   "mode_solve_tall": [("ax_tridiag.cu", "tridiag_kernel")],
                   "outer_residual": [("ax_stencil.cu", "residual_df_kernel")],
                   "pcg_update": [("ax_solver.cu", "pcg_update")]}
@@ -118,7 +119,7 @@ def measured_traffic(kernel: str, units_per_launch: float):
 
 
 MODE_CLASSES = {1: "mode_solve", 9: "mode_solve_scaled", 12: "mode_solve_scaled", 10: "mode_solve_reuse",
-                11: "mode_solve_reuse"}
+                11: "mode_solve_reuse", 14: "mode_solve_modemajor"}
 
 
 def kernel_class(top: str, tc_path: bool, fused: bool, mode_eff: int, stencil_v: int) -> str:

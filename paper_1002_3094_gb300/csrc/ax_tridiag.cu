@@ -1379,20 +1379,23 @@ constexpr PipeVariant kPipeVariants[] = {{2, 32, 1024}, {3, 16, 512}, {4, 16, 10
 int pipe_max_rows(const PipeVariant &v) { return 16 * v.nt / v.cw; }
 
 int tridiag_variants(int nr, int *ids) {
-  // the default first: the staged register kernel on the row-scaled systems
-  // (9; measured 9.7 ms per 1024^2 x 64 solve against 10.4 for the plain
-  // register kernel 1, 11.3 to 12.5 for the pipelined kernels and for 10, 11,
-  // 12), then the others; paths that cannot scale the rows (the FFT
-  // transforms) take kernel 1 (tridiag_effective)
+  // the default first: the staged kernel on the row-scaled systems fed
+  // mode-major by the forward transform (14; measured 8.25 ms per
+  // 1024^2 x 64 solve and 99.9 ms per 4096^2 x 16 solve, against 9.7 and
+  // 140.6 for the same kernel staging a row-major input, 9, which runs where
+  // the input is row-major), then the others (10.4 ms for the plain register
+  // kernel 1, 11.3 to 12.5 for the pipelined kernels and for 10, 11, 12);
+  // paths that cannot scale the rows (the FFT transforms) take kernel 1
+  // (tridiag_effective)
   int n = 0;
   if (nr <= 4096) {
+    ids[n++] = 14;
     ids[n++] = 9;
     ids[n++] = 1;
     ids[n++] = 10;
     ids[n++] = 11;
   }
   if (nr <= 1024) ids[n++] = 12;
-  if (nr <= 4096) ids[n++] = 14;
   for (const PipeVariant &v : kPipeVariants)
     if (nr <= pipe_max_rows(v) && 2 * nr > pipe_max_rows(v)) ids[n++] = v.id;
   return n;

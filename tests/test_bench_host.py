@@ -61,7 +61,8 @@ def test_kernel_class_follows_the_kernels_the_solve_ran():
     assert B.kernel_class("mode_solve", True, True, 1, 0) == "mode_solve"
     assert B.kernel_class("mode_solve", True, True, 0, 0) == "mode_solve_tall"
     assert B.kernel_class("mode_solve", True, True, 5, 0) == "mode_solve_pipe"
+    assert B.kernel_class("mode_solve", True, True, 14, 0) == "mode_solve_modemajor"
     assert B.kernel_class("stencil", True, True, 9, 1) == "stencil_ring"
     assert B.kernel_class("stencil", True, False, 9, 1) == "stencil"
-    for c in ("stencil_ring", "mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe"):
+    for c in ("stencil_ring", "mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe", "mode_solve_modemajor"):
         assert len(B.source_hash(c)) == 16 and B.source_hash(c) != B.source_hash("stencil")
