@@ -62,7 +62,6 @@ TC_CLASSES = ("dst_forward", "dst_inverse")
 # (file, __global__ function or None for the whole file), plus the shared
 # device helpers.
 KERNEL_SOURCES = {"stencil": [("ax_stencil.cu", "stencil_kernel")],
-                  "stencil_ring": [("ax_stencil.cu", "stencil_ring_kernel")],
                   "dst_forward": [("ax_dst_impl.cuh", None)],
                   "dst_inverse": [("ax_dst_impl.cuh", None)],
                   "dst_forward_tc": [("ax_dst_gemm.cu", None)],
@@ -122,17 +121,15 @@ MODE_CLASSES = {1: "mode_solve", 9: "mode_solve_scaled", 12: "mode_solve_scaled"
                 11: "mode_solve_reuse", 14: "mode_solve_modemajor"}
 
 
-def kernel_class(top: str, tc_path: bool, fused: bool, mode_eff: int, stencil_v: int) -> str:
+def kernel_class(top: str, tc_path: bool, mode_eff: int) -> str:
     """The KERNEL_SOURCES class of profiled kernel group `top` as the solve
-    ran it (transform form, mode-solve kernel id, stencil variant)."""
+    ran it (transform form, mode-solve kernel id)."""
     if top in TC_CLASSES and tc_path:
         return top + "_tc"
     if top == "mode_solve":
         if mode_eff == 0:
             return "mode_solve_tall"
         return MODE_CLASSES.get(mode_eff, "mode_solve_pipe")
-    if top == "stencil" and fused and stencil_v != 0:
-        return "stencil_ring"
     return top
 
 
@@ -171,8 +168,6 @@ def parse_args():
                     help="FP32 mode-solve kernel variant (option mode_kernel; 0 the library's choice)")
     ap.add_argument("--option", action="append", default=[], metavar="NAME=VALUE",
                     help="ax_set_option on the operator before the run (repeatable)")
-    ap.add_argument("--stencil-kernel", type=int, default=-1,
-                    help="stencil of the fused FP32 iteration (option stencil_kernel; -1 the library's choice)")
     ap.add_argument("--replace-delta", type=float, default=0.0,
                     help="mixed PCG: residual reduction between FP64 residual replacements (0: the library's)")
     return ap.parse_args()
@@ -840,21 +835,16 @@ def main():
         P.ax_set_option(op, "replace_delta", args.replace_delta)
     if args.mode_kernel > 0:
         P.ax_set_option(op, "mode_kernel", args.mode_kernel)
-    if args.stencil_kernel >= 0:
-        P.ax_set_option(op, "stencil_kernel", args.stencil_kernel)
     for kv in args.option:
         name, value = kv.split("=", 1)
         P.ax_set_option(op, name, float(value))
     tuned = None
-    if (not args.no_autotune and args.dst_tensor < 0 and args.mode_kernel == 0 and args.stencil_kernel < 0
-            and "mixed" in args.method):
+    if not args.no_autotune and args.dst_tensor < 0 and args.mode_kernel == 0 and "mixed" in args.method:
         t0 = time.perf_counter()
         P.ax_autotune(op, m, 5)
         tuned = {"dst_tensor": int(P.ax_get_option(op, "dst_tensor")),
-                 "mode_kernel": int(P.ax_get_option(op, "mode_kernel")),
-                 "stencil_kernel": int(P.ax_get_option(op, "stencil_kernel")), "autotune_s": time.perf_counter() - t0}
+                 "mode_kernel": int(P.ax_get_option(op, "mode_kernel")), "autotune_s": time.perf_counter() - t0}
     mode_eff = int(P.ax_get_option(op, "mode_kernel_effective"))
-    stencil_v = int(P.ax_get_option(op, "stencil_kernel"))
     f_host = sample_rhs(med, nr, nz, bc_z=args.bc_z)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)
@@ -968,7 +958,7 @@ def main():
         bytes_per_launch = units_per_launch * per_u + (nr * nz) * per_m
         avg_s = p["ms"] / p["launches"] / 1000.0
         achieved = bytes_per_launch / avg_s / 1e9
-        variant = kernel_class(top, tc_path, fused, mode_eff, stencil_v)
+        variant = kernel_class(top, tc_path, mode_eff)
         traffic = measured_traffic(variant, units_per_launch)
         roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,

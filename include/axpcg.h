@@ -137,7 +137,7 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
                      double *gamma1, double *gamma2);
 
 /* Reads an option of ax_set_option (and the ones the autotuner sets:
- * "dst_tensor", "mode_kernel", "stencil_kernel"), or the read-only
+ * "dst_tensor", "mode_kernel"), or the read-only
  * "mode_kernel_effective": the FP32 mode-solve kernel id that option
  * "mode_kernel" resolves to for this nr (0: nr above the tile kernels, the
  * register-chunk kernel runs); unknown names: AX_ERR_INVALID_ARG. */
@@ -209,13 +209,6 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    the input; row-major inputs take 9), 2..8 pipelined
  *                    column-tile kernels on the row-scaled systems; an id
  *                    whose column does not fit nr is refused
- *   "stencil_kernel" stencil (Eq. scheme_op_r_z) of the fused FP32 iteration
- *                    (AX_PCG_MIXED with the tensor-core transform) and of
- *                    ax_apply_operator in FP32: 0 (default) a register window
- *                    down the rows, 1 p and the coefficient rows streamed
- *                    through a ring of shared-memory slots by bulk copies
- *                    (bounded waits: an expiry makes the call return
- *                    AX_ERR_TIMEOUT)
  *   "cheb_bounds"    Chebyshev bounds gamma_1, gamma_2 (Eq. energy_rel): 0 the
  *                    face-wise bounds (min / max of kappa / kappa~ and q / q~),
  *                    1 a Lanczos estimate from "cheb_steps" PCG steps (the
@@ -279,9 +272,9 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
  * states are read after every graph replay of iterations, so the resolution
  * is one replay); *groups = count.
  * ax_batch_autotune: ax_autotune on every group (m = its instances).
- * ax_batch_config: grid, instance count and the transform / mode-solve /
- * stencil kernel (ax_get_option names) that group `group` (0 .. groups-1)
- * uses (any output pointer may be NULL).
+ * ax_batch_config: grid, instance count and the transform / mode-solve
+ * kernel (ax_get_option names) that group `group` (0 .. groups-1) uses (any
+ * output pointer may be NULL).
  * ax_solve_batched = create + solve + destroy. */
 typedef struct ax_batch ax_batch;
 int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch **out);
@@ -290,7 +283,7 @@ int ax_batch_solve(ax_batch *b, const double *const *f, double *const *u, double
 int ax_batch_latency(const ax_batch *b, double *ms, int32_t *groups);
 int ax_batch_autotune(ax_batch *b, int32_t reps, void *stream);
 int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, int32_t *members, int32_t *dst_tensor,
-                    int32_t *mode_kernel, int32_t *stencil_kernel);
+                    int32_t *mode_kernel);
 int ax_batch_destroy(ax_batch *b);
 int ax_solve_batched(ax_operator *const *ops, const double *const *f, double *const *u, int32_t n, double tol,
                      int32_t max_iter, int32_t method, int32_t flags, ax_solve_info *info, void *stream);

@@ -131,7 +131,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_get_option.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dbl)]
     lib.ax_autotune.argtypes = [vp, i32, i32, vp]
     lib.ax_batch_autotune.argtypes = [vp, i32, vp]
-    lib.ax_batch_config.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 6
+    lib.ax_batch_config.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 5
     for name in EXPORTED:
         if name not in ("ax_status_string", "ax_version", "ax_kernel_launches", "ax_last_error",
                         "ax_guessnet_num_params"):
@@ -229,9 +229,9 @@ def ax_batch_autotune(batch: int, reps: int = 5, stream=None) -> None:
 
 
 def ax_batch_config(batch: int, group: int) -> dict:
-    vals = [ctypes.c_int32() for _ in range(6)]
+    vals = [ctypes.c_int32() for _ in range(5)]
     _check(load_library().ax_batch_config(batch, group, *[ctypes.byref(v) for v in vals]), "ax_batch_config")
-    return dict(zip(("nr", "nz", "members", "dst_tensor", "mode_kernel", "stencil_kernel"), (v.value for v in vals)))
+    return dict(zip(("nr", "nz", "members", "dst_tensor", "mode_kernel"), (v.value for v in vals)))
 
 
 def ax_set_option(op: int, name: str, value: float, raise_on_error: bool = True) -> int:

@@ -164,7 +164,6 @@ struct ax_operator {
   int *rader_perm = nullptr;  // [2 P] device
   int dst_tc = 0;             // 1: the FP32 PCG path transforms with the tensor-core GEMM
   int tri_variant = 0;        // FP32 mode-solve kernel (0: default for nr; option "mode_kernel")
-  int st_variant = 0;         // stencil of the fused FP32 iteration (option "stencil_kernel")
   int *tc_err = nullptr;      // device flag: a bounded wait of the GEMM expired
   ax::Coef<double> c64;
   ax::Coef<float> c32;
@@ -200,19 +199,12 @@ struct StencilArgs {
   const RhsState *st;    // per RHS state (Pcg reads beta)
   int mask;
   double *partial;       // [m][kPartialStride] per-CTA sums: Pcg (p,q); Residual, Cheb ||res||^2
-  int variant;           // PcgP and Apply, FP32: 0 register window; 1 p and the coefficient
-                         // rows streamed through a ring of bulk copies (needs err)
-  int *err;              // variant 1: set when a bounded wait expired
-  unsigned polls;        // variant 1: wait limit (0: the default)
-  int stall;             // variant 1, test of the expiry path: no copy is issued, so
-                         // every wait runs out (with a short `polls`)
 };
 
 template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s);
 // CTAs (and partial sums) per right-hand side of a stencil launch
-int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant = 0);
-constexpr int kStencilVariants = 2;
+int stencil_blocks_per_rhs(int nr, int nz, int vec);
 
 // Double-float true residual r = phi - A x of the mixed method: x, phi and the
 // coefficients as pairs of FP32 numbers (hi + lo), all arithmetic in FP32 with

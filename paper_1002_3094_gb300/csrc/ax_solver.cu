@@ -80,8 +80,6 @@ struct Workspace {
   int max_outer = 30;
   int mixed_restart = 0;        // 1: AX_PCG_MIXED uses restarted refinement instead of replacement
   int tc_stall_test = 0;        // 1: the next tensor-core transform lets one bounded wait run out
-  int st_stall_test = 0;        // 1: the next staged stencil lets its bounded waits run out
-  int st_stall_used = 0;        // a captured graph holds that stalled launch (freed after the solve)
   int tc_unfused = 0;           // 1: mixed PCG forms p in the stencil, not in the inverse transform
   double replace_delta = 0.1;   // residual reduction between FP64 replacements
   int cheb_bounds = -1;         // Chebyshev bounds: 0 face-wise, 1 Lanczos estimate, -1 Lanczos
@@ -1305,17 +1303,6 @@ int small_pcg_run(ax_operator *op, cudaStream_t s, const double *f = nullptr, do
   return st;
 }
 
-// Test of the staged stencil's expiry path (option "stencil_stall_test"), once:
-// the launch issues no copy and waits briefly, so every wait runs out.
-template <typename T>
-void stencil_stall(const ax_operator *op, StencilArgs<T> &sa) {
-  if (!op->ws->st_stall_test) return;
-  sa.stall = 1;
-  sa.polls = 1u << 12;
-  op->ws->st_stall_test = 0;
-  op->ws->st_stall_used = 1;
-}
-
 template <typename T>
 bool use_tc(const ax_operator *op) {
   return sizeof(T) == 4 && op->dst_tc != 0;
@@ -1517,8 +1504,7 @@ template <typename T>
 void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *st, Workspace *w,
                    int on_converge, cudaStream_t s, double units = 0.0, bool fused = false) {
   const int V = VecT<T>::n;
-  const int stv = fused && sizeof(T) == 4 ? op->st_variant : 0;
-  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V, stv);
+  const int nbs = stencil_blocks_per_rhs(op->nr, op->nz, V);
   const int nbd = dst_blocks(op, op->nr, (int)sizeof(T));
   double *pq = part_ptr(w, kPartA), *prr = part_ptr(w, kPartB), *prz = part_ptr(w, kPartC);
   StencilArgs<T> sa = stencil_args<T>(op, m, st, kActive);
@@ -1527,11 +1513,6 @@ void pcg_iteration(const ax_operator *op, int m, const PcgVecs<T> &v, RhsState *
   sa.pb = v.pb;
   sa.out = v.q;
   sa.partial = pq;
-  if (stv != 0) {
-    sa.variant = stv;
-    sa.err = tc_flag(op->device);
-    stencil_stall(op, sa);
-  }
   {
     ProfScope ps(w, kProfStencil, units, s);
     launch_stencil<T>(fused ? kStencilPcgP : kStencilPcg, sa, s);
@@ -2371,7 +2352,7 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t, double
 // kernel, the time in ms).
 // ---------------------------------------------------------------------------
 namespace {
-struct TuneChoice { int dst = 0, variant = 0; double ms = 0.0; int stencil = 0; };
+struct TuneChoice { int dst = 0, variant = 0; double ms = 0.0; };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune;
 bool g_tune_loaded = false;
@@ -2398,7 +2379,7 @@ void tune_load() {
   if (!fp) return;
   char key[200];
   TuneChoice c;
-  while (fscanf(fp, "%199s %d %d %d %lf", key, &c.dst, &c.variant, &c.stencil, &c.ms) == 5) g_tune[key] = c;
+  while (fscanf(fp, "%199s %d %d %lf", key, &c.dst, &c.variant, &c.ms) == 4) g_tune[key] = c;
   fclose(fp);
 }
 
@@ -2407,15 +2388,13 @@ void tune_save() {
   if (!path) return;
   FILE *fp = fopen(path, "w");
   if (!fp) return;
-  for (auto &e : g_tune)
-    fprintf(fp, "%s %d %d %d %.6f\n", e.first.c_str(), e.second.dst, e.second.variant, e.second.stencil, e.second.ms);
+  for (auto &e : g_tune) fprintf(fp, "%s %d %d %.6f\n", e.first.c_str(), e.second.dst, e.second.variant, e.second.ms);
   fclose(fp);
 }
 
 void apply_choice(ax_operator *op, const TuneChoice &c) {
   op->dst_tc = c.dst;
   op->tri_variant = c.variant;
-  op->st_variant = c.stencil;
   Workspace *w = op->ws;
   free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
 }
@@ -2453,7 +2432,7 @@ int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
         !tc_table(op->device, op->nz, cz ? kTableCosInverse : kTableSine) || !tc_flag(op->device))
       return AX_ERR_OOM;
   }
-  const TuneChoice saved{op->dst_tc, op->tri_variant, 0.0, op->st_variant};
+  const TuneChoice saved{op->dst_tc, op->tri_variant, 0.0};
   const size_t n = field_elems(op) * m;
   cudaEvent_t e0, e1;
   AX_TRY(cudaEventCreate(&e0));
@@ -2475,9 +2454,7 @@ int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
   }
   TuneChoice best;
   best.ms = -1.0;
-  const size_t nbase = cand.size();
-  for (size_t ci = 0; ci < cand.size(); ++ci) {
-    TuneChoice &c = cand[ci];
+  for (TuneChoice &c : cand) {
     apply_choice(op, c);
     const bool fused = tc_fused(op);
     AX_TRY(cudaMemsetAsync(w->r32, 0x3f, sizeof(float) * n, s));  // 0x3f3f3f3f: 0.747
@@ -2497,13 +2474,6 @@ int ax_autotune(ax_operator *op, int32_t m, int32_t reps, void *stream) {
     cudaEventElapsedTime(&ms, e0, e1);
     c.ms = ms / reps;
     if (best.ms < 0.0 || c.ms < best.ms) best = c;
-    // then the staged stencils with the fastest tensor-core choice (only the
-    // fused iteration runs them)
-    if (ci + 1 == nbase && best.dst != 0) {
-      apply_choice(op, best);
-      if (tc_fused(op))
-        for (int sv = 1; sv < kStencilVariants; ++sv) cand.push_back({best.dst, best.variant, 0.0, sv});
-    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -2533,7 +2503,6 @@ int ax_get_option(const ax_operator *op, const char *name, double *value) {
   const Workspace *w = op->ws;
   if (!strcmp(name, "dst_tensor")) *value = op->dst_tc;
   else if (!strcmp(name, "mode_kernel")) *value = op->tri_variant;
-  else if (!strcmp(name, "stencil_kernel")) *value = op->st_variant;
   else if (!strcmp(name, "small_path")) *value = op->ws->small_path;
   else if (!strcmp(name, "mode_kernel_effective"))  // the FP32 mode-solve kernel a solve runs (0: none of the tile kernels)
     *value = tridiag_effective(op->nr, op->tri_variant, 1, op->c32.IPS != nullptr && op->c32.RS != nullptr);
@@ -2607,12 +2576,6 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     // grid barrier, so that the others' bounded waits run out: the call
     // returns AX_ERR_TIMEOUT and the context stays usable.  For tests.
     w->small_stall_test = value != 0.0;
-  } else if (!strcmp(name, "stencil_stall_test")) {
-    // The next staged stencil (option "stencil_kernel" 1 or 2) issues no copy
-    // and waits briefly, so its bounded waits run out: the call returns
-    // AX_ERR_TIMEOUT and the context stays usable.  For tests.
-    w->st_stall_test = value != 0.0;
-    free_graph(w->g32);
   } else if (!strcmp(name, "tc_stall_test")) {
     // The next tensor-core transform stops its copies before the first stage,
     // so that the MMA warp's bounded wait runs out (short limit): the call
@@ -2638,15 +2601,6 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
       if (!ok) return AX_ERR_INVALID_ARG;
     }
     op->tri_variant = v;
-    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
-  } else if (!strcmp(name, "stencil_kernel")) {
-    // stencil of the fused FP32 iteration (and of ax_apply_operator in FP32):
-    // 0 the register window, 1 p and the coefficient rows streamed through a
-    // ring of bulk copies
-    const int v = (int)value;
-    if ((double)v != value || v < 0 || v >= kStencilVariants) return AX_ERR_INVALID_ARG;
-    if (v != 0 && !tc_flag(op->device)) return AX_ERR_OOM;
-    op->st_variant = v;
     free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
   } else if (!strcmp(name, "cheb_bounds")) {
     if (value != -1.0 && value != 0.0 && value != 1.0) return AX_ERR_INVALID_ARG;
@@ -2934,17 +2888,10 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
   const int blocks = (int)std::min<long long>(rows, 65535);
   note_launch();
   dense_to_padded<T><<<blocks, 256, 0, s>>>(in, a, rows, op->nz, op->pitch);
-  bool staged = false;  // the staged stencil runs bounded waits
   if (which == 0) {
     StencilArgs<T> sa = stencil_args<T>(op, m, nullptr, -1);
     sa.in = a;
     sa.out = b;
-    if (sizeof(T) == 4 && op->st_variant != 0) {
-      sa.variant = op->st_variant;
-      sa.err = tc_flag(op->device);
-      staged = sa.err != nullptr;
-      stencil_stall(op, sa);
-    }
     launch_stencil<T>(kStencilApply, sa, s);
   } else if (which == 1) {
     if constexpr (sizeof(T) == 4) {
@@ -3012,14 +2959,14 @@ static int apply_step(ax_operator *op, const double *in, double *out, int m, int
   note_launch();
   padded_to_dense<T><<<blocks, 256, 0, s>>>(b, out, rows, op->nz, op->pitch);
   AX_CHECK_LAUNCH();
-  if (tc || staged) {
+  if (tc) {
     int *flag = tc_flag(op->device), hf = 0;
     if (flag) {
       AX_TRY(cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
       AX_TRY(cudaStreamSynchronize(s));
       if (hf) {
         AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
-        snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of a tensor-core transform or a staged stencil expired");
+        snprintf(g_last_error, sizeof(g_last_error), "tensor-core transform: a bounded wait expired");
         return AX_ERR_TIMEOUT;
       }
     }
@@ -3316,10 +3263,6 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
     AX_TRY(cudaMemcpyAsync(u, ud, dense * sizeof(double), cudaMemcpyDeviceToHost, s));
     AX_TRY(cudaStreamSynchronize(s));
   }
-  if (w->st_stall_used) {  // the graphs hold the stalled stencil of a test
-    free_graph(w->g64); free_graph(w->g32); free_graph(w->gc64); free_graph(w->gc32);
-    w->st_stall_used = 0;
-  }
   if (op->dst_tc) {
     // a bounded wait of the tensor-core transform expired: report and re-arm
     int *flag = tc_flag(op->device), hf = 0;
@@ -3328,7 +3271,7 @@ int ax_solve(ax_operator *op, const double *f, double *u, int32_t m, double tol,
       AX_TRY(cudaStreamSynchronize(s));
       if (hf) {
         AX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
-        snprintf(g_last_error, sizeof(g_last_error), "a bounded wait of a tensor-core transform or a staged stencil expired");
+        snprintf(g_last_error, sizeof(g_last_error), "tensor-core transform: a bounded wait expired");
         return AX_ERR_TIMEOUT;
       }
     }
@@ -3521,7 +3464,6 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
     gop->plan = o->plan;
     gop->dst_tc = o->dst_tc;
     gop->tri_variant = o->tri_variant;
-    gop->st_variant = o->st_variant;
     gop->cstride = (long long)o->nr * o->pitch;
     gop->czstride = (long long)o->nr * o->pitchz;
     gop->estride = o->nr;
@@ -3628,7 +3570,7 @@ int ax_batch_autotune(ax_batch *b, int32_t reps, void *stream) {
 }
 
 int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, int32_t *members, int32_t *dst_tensor,
-                    int32_t *mode_kernel, int32_t *stencil_kernel) {
+                    int32_t *mode_kernel) {
   if (!b || group < 0 || group >= (int)b->groups.size()) return AX_ERR_INVALID_ARG;
   const ax::BatchGroup &g = b->groups[group];
   if (nr) *nr = g.gop->nr;
@@ -3637,7 +3579,6 @@ int ax_batch_config(const ax_batch *b, int32_t group, int32_t *nr, int32_t *nz, 
   if (dst_tensor) *dst_tensor = g.gop->dst_tc;
   if (mode_kernel) *mode_kernel = ax::tridiag_effective(g.gop->nr, g.gop->tri_variant, (int)g.members.size(),
                                                          g.gop->c32.IPS != nullptr);
-  if (stencil_kernel) *stencil_kernel = g.gop->st_variant;
   return AX_OK;
 }
 

@@ -231,207 +231,6 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
   }
 }
 
-// ---- q = A p through a ring of bulk-copied rows (FP32) -----------------------
-// The register-window kernel waits on its loads (long scoreboard in ncu): each
-// warp has one row of p and of the coefficients in flight and too little work
-// per row to cover an L2 or DRAM round trip.  Here a producer warp streams
-// every input row the CTA needs (p, CR, W and CZ of its column strip) into a
-// ring of S shared-memory slots with bulk copies (cp.async.bulk), with one
-// mbarrier per slot for "full" (the copy bytes have landed) and one for
-// "empty" (every consumer warp has read the slot into registers).  The
-// consumer warps walk down the rows with the same three-row register window
-// and the same arithmetic per node, reading each row from shared memory, so
-// up to S rows per CTA are in flight without holding registers.  Where nz is
-// a multiple of 128 every lane holds four nodes of the grid and the range
-// tests against nz are compiled out (FULL).  Every wait is bounded: on expiry
-// a warp sets *err and stops; the producer then waits (bounded) for the
-// copies it issued before the CTA exits.
-constexpr int kRingRows = 32;   // rows per CTA
-constexpr int kRingSlots = 6;   // ring depth (rows in flight)
-constexpr unsigned kRingPolls = 1u << 22;  // bound of every mbarrier wait
-
-template <int MODE, bool FULL>
-__global__ void __launch_bounds__(288) stencil_ring_kernel(const StencilArgs<float> a) {
-  static_assert(MODE == kStencilPcgP || MODE == kStencilApply, "modes without a second input field");
-  constexpr int S = kRingSlots;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double red[9];
-  const int m = blockIdx.x;
-  if (!rhs_selected(a.st, a.mask, m)) return;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
-  uint64_t *empty = full + S;
-  float *ring = reinterpret_cast<float *>(smem + 128);
-  const int nwc = (blockDim.x >> 5) - 1;  // consumer warps; the last warp is the producer
-  const int W = nwc * 128;                // strip width (floats)
-  const int SW = 4 * W + 4;               // slot: p, CR, W (W floats each), CZ (W + 4 faces)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nr = a.nr, nz = a.nz;
-  const int i0 = blockIdx.y * kRingRows, i1 = min(i0 + kRingRows, nr);
-  const int ilo = max(i0 - 1, 0), ihi = min(i1, nr - 1);  // staged rows
-  const int T = ihi - ilo + 1;
-  const int ks = blockIdx.z * W;
-  const size_t base = (size_t)m * (size_t)a.field;
-  const float *src = MODE == kStencilApply ? a.in : ((a.st[m].iters & 1) ? a.pa : a.pb);
-  const float *CR = a.CR + (size_t)m * a.cstride;
-  const float *CZ = a.CZ + (size_t)m * a.czstride;
-  const float *Wc = a.W + (size_t)m * a.cstride;
-  const unsigned polls = a.polls ? a.polls : kRingPolls;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < S; ++k) {
-      mbar_init(&full[k], 1);
-      mbar_init(&empty[k], nwc);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  float acc = 0.f;
-  if (warp == nwc) {
-    // ---- producer: rows ilo .. ihi into slots t % S
-    if (lane == 0 && !a.stall) {
-      // whole padded rows (pitch - ks and pitchz - ks are multiples of 32
-      // floats); the CZ row takes the 4 faces after the strip too, when the
-      // padded row has them (it always has face ks + W <= nz)
-      const unsigned bp = (unsigned)min(W, a.pitch - ks) * 4u;
-      const unsigned bz = (unsigned)min(W + 4, a.pitchz - ks) * 4u;
-      int t = 0;
-      for (; t < T; ++t) {
-        const int k = t % S;
-        if (t >= S && !mbar_wait(&empty[k], (unsigned)((t / S) - 1) & 1u, polls)) {
-          atomicExch(a.err, 1);
-          break;
-        }
-        const size_t i = (size_t)(ilo + t);
-        float *slot = ring + (size_t)k * SW;
-        mbar_arrive_tx(&full[k], 3u * bp + bz);
-        bulk_g2s(slot, src + base + i * a.pitch + ks, bp, &full[k]);
-        bulk_g2s(slot + W, CR + i * a.pitch + ks, bp, &full[k]);
-        bulk_g2s(slot + 2 * W, Wc + i * a.pitch + ks, bp, &full[k]);
-        bulk_g2s(slot + 3 * W, CZ + i * a.pitchz + ks, bz, &full[k]);
-      }
-      // every issued copy has landed before the CTA may exit
-      for (int u = max(t - S, 0); u < t; ++u)
-        if (!mbar_wait(&full[u % S], (unsigned)(u / S) & 1u, polls)) atomicExch(a.err, 1);
-    }
-  } else {
-    // ---- consumers
-    const int c = warp * 128 + lane * 4;  // column within the strip
-    const int k0 = ks + c;
-    const bool col_ok = FULL || k0 < nz;
-    bool ok = true;
-    struct Row {
-      float4 p, cr, w, cz;
-      float left, right, czlast;
-    };
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    // staged row t into registers (zeros where the grid ends), then release
-    // its slot
-    auto fetch = [&](int t, Row &r) {
-      const int k = t % S;
-      // warp-uniform outcome (every lane of a consumer warp fetches the same rows)
-      const bool got = __all_sync(0xffffffffu, ok && (mbar_try(&full[k], (unsigned)(t / S) & 1u) ||
-                                                       mbar_wait(&full[k], (unsigned)(t / S) & 1u, polls)));
-      if (!got) {
-        if (ok && lane == 0) atomicExch(a.err, 1);
-        ok = false;
-        r.p = r.cr = r.w = r.cz = zero;
-        r.left = r.right = r.czlast = 0.f;
-        return;
-      }
-      const float *slot = ring + (size_t)k * SW;
-      const int i = ilo + t;
-      r.left = r.right = r.czlast = 0.f;
-      if (col_ok) {
-        r.p = *reinterpret_cast<const float4 *>(slot + c);
-        r.cr = *reinterpret_cast<const float4 *>(slot + W + c);
-        r.w = *reinterpret_cast<const float4 *>(slot + 2 * W + c);
-        r.cz = *reinterpret_cast<const float4 *>(slot + 3 * W + c);
-        if (!FULL) {
-          r.p.y = k0 + 1 < nz ? r.p.y : 0.f;
-          r.p.z = k0 + 2 < nz ? r.p.z : 0.f;
-          r.p.w = k0 + 3 < nz ? r.p.w : 0.f;
-        }
-        if (lane == 0 && k0 > 0)
-          r.left = c > 0 ? slot[c - 1] : src[base + (size_t)i * a.pitch + k0 - 1];
-        if (lane == 31) {
-          if (k0 + 4 < nz) r.right = c + 4 < W ? slot[c + 4] : src[base + (size_t)i * a.pitch + k0 + 4];
-          if (FULL || k0 + 4 <= nz) r.czlast = slot[3 * W + c + 4];
-        }
-      } else {
-        r.p = r.cr = r.w = r.cz = zero;
-        // the lane just past the last node: its first face is the upper face
-        // of node nz - 1, fetched by the shuffle
-        if (k0 <= nz) r.cz.x = slot[3 * W + c];
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[k]);
-    };
-    auto node = [](float y, float yl, float yr, float pn, float pm, float wv, float crh, float crl, float czh,
-                   float czl) {
-      float v = wv * y;
-      v = fmaf(crh, y - pn, v);
-      v = fmaf(crl, y - pm, v);
-      v = fmaf(czh, y - yr, v);
-      v = fmaf(czl, y - yl, v);
-      return v;
-    };
-    Row rm, rc, rn;
-    if (i0 > 0) {
-      fetch(0, rm);  // row i0 - 1: p and CR
-    } else {
-      rm.p = rm.cr = zero;
-    }
-    fetch(i0 - ilo, rc);
-    auto step = [&](int i) {
-      if (i + 1 <= ihi) {
-        fetch(i + 1 - ilo, rn);
-      } else {
-        rn.p = zero;
-      }
-      float l = __shfl_up_sync(0xffffffffu, rc.p.w, 1);
-      float r = __shfl_down_sync(0xffffffffu, rc.p.x, 1);
-      float czh3 = __shfl_down_sync(0xffffffffu, rc.cz.x, 1);
-      if (lane == 0) l = rc.left;
-      if (lane == 31) {
-        r = rc.right;
-        czh3 = rc.czlast;
-      }
-      float4 o;
-      o.x = node(rc.p.x, l, rc.p.y, rn.p.x, rm.p.x, rc.w.x, rc.cr.x, rm.cr.x, rc.cz.y, rc.cz.x);
-      o.y = node(rc.p.y, rc.p.x, rc.p.z, rn.p.y, rm.p.y, rc.w.y, rc.cr.y, rm.cr.y, rc.cz.z, rc.cz.y);
-      o.z = node(rc.p.z, rc.p.y, rc.p.w, rn.p.z, rm.p.z, rc.w.z, rc.cr.z, rm.cr.z, rc.cz.w, rc.cz.z);
-      o.w = node(rc.p.w, rc.p.z, r, rn.p.w, rm.p.w, rc.w.w, rc.cr.w, rm.cr.w, czh3, rc.cz.w);
-      if (!FULL) {
-        o.y = k0 + 1 < nz ? o.y : 0.f;
-        o.z = k0 + 2 < nz ? o.z : 0.f;
-        o.w = k0 + 3 < nz ? o.w : 0.f;
-      }
-      if (col_ok) {
-        *reinterpret_cast<float4 *>(a.out + base + (size_t)i * a.pitch + k0) = o;
-        if (MODE == kStencilPcgP) {
-          acc = fmaf(rc.p.x, o.x, acc);
-          acc = fmaf(rc.p.y, o.y, acc);
-          acc = fmaf(rc.p.z, o.z, acc);
-          acc = fmaf(rc.p.w, o.w, acc);
-        }
-      }
-      rm = rc;
-      rc = rn;
-    };
-    if (i1 - i0 == kRingRows) {
-#pragma unroll 2
-      for (int j = 0; j < kRingRows; ++j) step(i0 + j);
-    } else {
-#pragma unroll 1
-      for (int i = i0; i < i1; ++i) step(i);
-    }
-  }
-  if (MODE == kStencilPcgP && a.partial != nullptr) {
-    const double sm = block_sum((double)acc, red);
-    if (threadIdx.x == 0)
-      a.partial[(size_t)m * kPartialStride + blockIdx.y * gridDim.z + blockIdx.z] = sm;
-  }
-}
-
 // ---- double-float residual -------------------------------------------------
 // Pairs (h, l) of FP32 numbers carry about 48 significant bits: sums by Knuth's
 // two-sum and Dekker's fast two-sum, products by the FMA two-product (the exact
@@ -552,45 +351,16 @@ int column_warps(int nz, int vec) {
 
 }  // namespace
 
-int stencil_blocks_per_rhs(int nr, int nz, int vec, int variant) {
+int stencil_blocks_per_rhs(int nr, int nz, int vec) {
   const int wx = column_warps(nz, vec);
-  const int rows = variant == 1 ? kRingRows : kStencilRows;
   const int gz = (nz + 32 * vec * wx - 1) / (32 * vec * wx);
-  const int gy = (nr + rows - 1) / rows;
+  const int gy = (nr + kStencilRows - 1) / kStencilRows;
   return gy * gz;
 }
 
 template <typename T>
 void launch_stencil(int mode, const StencilArgs<T> &a, cudaStream_t s) {
   constexpr int V = VecT<T>::n;
-  if constexpr (sizeof(T) == 4) {
-    if ((mode == kStencilPcgP || mode == kStencilApply) && a.variant == 1 && a.err != nullptr) {
-      const int wx = column_warps(a.nz, V);
-      const int W = 128 * wx;
-      const size_t smem = 128 + (size_t)kRingSlots * (4 * W + 4) * sizeof(float);
-      dim3 grid(a.m, (a.nr + kRingRows - 1) / kRingRows, (a.nz + W - 1) / W);
-      note_launch();
-      const bool full = a.nz % 128 == 0;  // every lane of every strip holds 4 nodes of the grid
-      const void *fn = mode == kStencilPcgP
-                           ? (full ? (const void *)stencil_ring_kernel<kStencilPcgP, true>
-                                   : (const void *)stencil_ring_kernel<kStencilPcgP, false>)
-                           : (full ? (const void *)stencil_ring_kernel<kStencilApply, true>
-                                   : (const void *)stencil_ring_kernel<kStencilApply, false>);
-      ensure_smem_attr(fn, smem);
-      if (mode == kStencilPcgP) {
-        if (full)
-          stencil_ring_kernel<kStencilPcgP, true><<<grid, 32 * (wx + 1), smem, s>>>(a);
-        else
-          stencil_ring_kernel<kStencilPcgP, false><<<grid, 32 * (wx + 1), smem, s>>>(a);
-      } else {
-        if (full)
-          stencil_ring_kernel<kStencilApply, true><<<grid, 32 * (wx + 1), smem, s>>>(a);
-        else
-          stencil_ring_kernel<kStencilApply, false><<<grid, 32 * (wx + 1), smem, s>>>(a);
-      }
-      return;
-    }
-  }
   const int wx = column_warps(a.nz, V);
   dim3 grid(a.m, (a.nr + kStencilRows - 1) / kStencilRows, (a.nz + 32 * V * wx - 1) / (32 * V * wx));
   dim3 block(32 * wx);

@@ -49,20 +49,18 @@ def test_traffic_row_applies_only_to_the_source_it_was_measured_on(tmp_path, mon
     assert B.measured_traffic("stencil", 1000.0) == pytest.approx(6500.0)
     assert B.measured_traffic("pcg_update", 1000.0) is None  # recorded on other code
     assert B.measured_traffic("mode_solve", 1000.0) is None  # never recorded
-    assert B.measured_traffic("stencil_ring", 1000.0) is None
     table.write_text("not json")
     assert B.measured_traffic("stencil", 1000.0) is None
 
 
 def test_kernel_class_follows_the_kernels_the_solve_ran():
-    assert B.kernel_class("dst_inverse", True, True, 9, 0) == "dst_inverse_tc"
-    assert B.kernel_class("dst_inverse", False, False, 9, 0) == "dst_inverse"
-    assert B.kernel_class("mode_solve", True, True, 9, 0) == "mode_solve_scaled"
-    assert B.kernel_class("mode_solve", True, True, 1, 0) == "mode_solve"
-    assert B.kernel_class("mode_solve", True, True, 0, 0) == "mode_solve_tall"
-    assert B.kernel_class("mode_solve", True, True, 5, 0) == "mode_solve_pipe"
-    assert B.kernel_class("mode_solve", True, True, 14, 0) == "mode_solve_modemajor"
-    assert B.kernel_class("stencil", True, True, 9, 1) == "stencil_ring"
-    assert B.kernel_class("stencil", True, False, 9, 1) == "stencil"
-    for c in ("stencil_ring", "mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe", "mode_solve_modemajor"):
+    assert B.kernel_class("dst_inverse", True, 14) == "dst_inverse_tc"
+    assert B.kernel_class("dst_inverse", False, 9) == "dst_inverse"
+    assert B.kernel_class("mode_solve", True, 9) == "mode_solve_scaled"
+    assert B.kernel_class("mode_solve", True, 14) == "mode_solve_modemajor"
+    assert B.kernel_class("mode_solve", True, 1) == "mode_solve"
+    assert B.kernel_class("mode_solve", True, 0) == "mode_solve_tall"
+    assert B.kernel_class("mode_solve", True, 5) == "mode_solve_pipe"
+    assert B.kernel_class("stencil", True, 14) == "stencil"
+    for c in ("mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe", "mode_solve_modemajor"):
         assert len(B.source_hash(c)) == 16 and B.source_hash(c) != B.source_hash("stencil")
