@@ -18,6 +18,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -89,14 +90,27 @@ def _function_text(src: str, name: str) -> str:
     return src
 
 
-def source_hash(kernel: str) -> str:
+def _code_only(text: str) -> str:
+    """`text` without its comments and blank lines: what decides the compiled
+    kernel (a comment edit keeps a traffic figure valid)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
+def source_hash(kernel: str, read=None) -> str:
+    """Hash of the code (comments dropped) of the sources of kernel class
+    `kernel`; read(name) returns a file's text (default: the csrc file)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1002_3094_gb300", "csrc")
+    if read is None:
+        def read(name):
+            with open(os.path.join(csrc, name)) as fh:
+                return fh.read()
     for f, fn in KERNEL_SOURCES.get(kernel, []) + [("ax_common.cuh", None)]:
-        with open(os.path.join(csrc, f)) as fh:
-            text = fh.read()
-        h.update((text if fn is None else _function_text(text, fn)).encode())
+        text = read(f)
+        h.update(_code_only(text if fn is None else _function_text(text, fn)).encode())
     return h.hexdigest()[:16]
 
 

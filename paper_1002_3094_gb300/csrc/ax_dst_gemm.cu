@@ -22,12 +22,14 @@
 // to about 2^-16.  Either way the FP64 residual replacement keeps the
 // solution accuracy.
 //
-// Tiles: 128 rows x 256 columns l of both P and Q per CTA (512 TMEM columns),
-// K in blocks of 64 (the even blocks feed P, the odd ones Q) through a ring of
-// shared-memory stages (3 of 64 KB, or 2 of 96 KB with S_lo), each filled by
-// bulk copies (cp.async.bulk) of one 32 KB input tile and one or two 32 KB
-// tiles of S (stored in the same layout: row l, column k).  Warp roles: warp
-// 0 lane 0 issues tcgen05.mma (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32);
+// Tiles: 128 rows x 128 columns l of both P and Q per CTA (256 TMEM columns;
+// persistent CTAs keep two tiles in flight, 512 columns, so that the epilogue
+// of one overlaps the MMAs of the next), K in blocks of 64 (the even blocks
+// feed P, the odd ones Q) through a ring of shared-memory stages (4 of 48 KB,
+// or 3 of 64 KB with S_lo), each filled by bulk copies (cp.async.bulk) of one
+// 32 KB input tile (hi and lo halves) and one or two 16 KB tiles of S (stored
+// in the same layout: row l, column k).  Warp roles: warp
+// 0 lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16, BF16 x BF16 -> FP32);
 // warp 1 lane 0 issues the copies; warps 4..7 run the epilogue (tcgen05.ld,
 // the even / odd combination, global stores, optional (r, out) partial).
 // Every mbarrier wait is bounded; on expiry the CTA records the failure in
@@ -532,9 +534,9 @@ int dst_gemm_ktiles(int n) { return 2 * dst_gemm_kbe(n); }
 int dst_gemm_ntiles(int n) { return ((n + 1) / 2 + kBN - 1) / kBN; }
 int dst_gemm_mtiles(int rows) { return (rows + kBM - 1) / kBM; }
 
-// S tiles: for every N tile (256 output columns l < ceil(n/2)) and K block (64
+// S tiles: for every N tile (128 output columns l < ceil(n/2)) and K block (64
 // input columns: the even columns 0, 2, ... in the first kbe blocks, the odd
-// ones after) a 32 KB tile of S_hi and one of S_lo, each in the shared-memory
+// ones after) a 16 KB tile of S_hi and one of S_lo, each in the shared-memory
 // layout above holding S[k][l] at (row l, column k).  Values in FP64, rounded
 // to BF16 (nearest, ties to even, by way of FP32).
 std::vector<uint16_t> dst_gemm_table(int n, int kind) {

@@ -40,6 +40,23 @@ def test_function_text_is_one_global_function():
     assert len(B.source_hash("stencil")) == 16 and B.source_hash("stencil") != B.source_hash("outer_residual")
 
 
+def test_source_hash_ignores_comments_but_not_code():
+    src = {"ax_stencil.cu": open(os.path.join(ROOT, "paper_1002_3094_gb300", "csrc", "ax_stencil.cu")).read(),
+           "ax_common.cuh": open(os.path.join(ROOT, "paper_1002_3094_gb300", "csrc", "ax_common.cuh")).read()}
+    base = B.source_hash("stencil", src.__getitem__)
+    assert base == B.source_hash("stencil")
+    decl = "__global__"
+    commented = dict(src)
+    i = src["ax_stencil.cu"].index(decl, src["ax_stencil.cu"].index("stencil_kernel(") - 400)
+    body = src["ax_stencil.cu"]
+    j = body.index("{", body.index("stencil_kernel(", i)) + 1
+    commented["ax_stencil.cu"] = body[:j] + "\n  // a new comment\n  /* and a block\n  comment */\n" + body[j:]
+    assert B.source_hash("stencil", commented.__getitem__) == base
+    changed = dict(src)
+    changed["ax_stencil.cu"] = body[:j] + "\n  int unused_probe = 0;\n" + body[j:]
+    assert B.source_hash("stencil", changed.__getitem__) != base
+
+
 def test_traffic_row_applies_only_to_the_source_it_was_measured_on(tmp_path, monkeypatch):
     table = tmp_path / "traffic.json"
     table.write_text(json.dumps({"entries": [
