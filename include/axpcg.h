@@ -140,7 +140,10 @@ int ax_operator_info(const ax_operator *op, double *kappa_t, double *q_t,
  * "dst_tensor", "mode_kernel"), or the read-only
  * "mode_kernel_effective": the FP32 mode-solve kernel id that option
  * "mode_kernel" resolves to for this nr (0: nr above the tile kernels, the
- * register-chunk kernel runs); unknown names: AX_ERR_INVALID_ARG. */
+ * register-chunk kernel runs), and the read-only "replace_checks": how many
+ * times the last AX_PCG_MIXED solve recomputed z after a residual replacement
+ * (synchronises the device; AX_ERR_CUDA if that read fails); unknown names:
+ * AX_ERR_INVALID_ARG. */
 int ax_get_option(const ax_operator *op, const char *name, double *value);
 
 /* Autotuner (the paper has no counterpart; its workloads ran one fixed code).
@@ -196,6 +199,13 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *   "tc_fused"       1 (default): with the tensor-core transform, the mixed PCG
  *                    forms p = z + beta p and x += alpha p in the inverse
  *                    transform's epilogue; 0: in the stencil and update pass
+ *   "replace_gate"   1 (default): with the fused tensor-core iteration, the
+ *                    split and transform launches that recompute z for the
+ *                    right-hand sides whose true residual departed from the
+ *                    recursive one (residual replacement) return at once when
+ *                    there are none (a device count kept by the scalar
+ *                    kernels); 0: they walk their grids.  Results are the
+ *                    same bit for bit
  *   "mode_kernel"    FP32 mode solves (the per-mode tridiagonal systems of
  *                    Eq. eq_trid): 0 (default) the library's choice, 1 the
  *                    staged register kernel, 9 the same on the row-scaled

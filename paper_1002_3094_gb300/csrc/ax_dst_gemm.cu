@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) dst_gemm_kernel(const GemmDst
   const int KB = a.ktiles;
   const unsigned polls = a.polls ? a.polls : kWaitPolls;
   const int ntile_all = a.m * a.mtiles * a.ntiles;
+  if (a.gate != nullptr && *a.gate == 0) return;  // nothing selected: before any set-up
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {

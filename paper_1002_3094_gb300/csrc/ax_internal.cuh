@@ -347,6 +347,10 @@ struct GemmDstArgs {
   // the run out[(m n + l) tpitch + i], i < nr (no p update, no partials); the
   // input of the mode-solve kernel 14
   int tout, tpitch;
+  // non-null: the launch returns at once while *gate == 0 (a count, kept by
+  // the scalar kernels, of the right-hand sides its mask can select; for the
+  // masked launches of the residual-replacement step)
+  const int *gate;
 };
 void launch_dst_gemm(const GemmDstArgs &a, cudaStream_t s);
 size_t dst_gemm_smem_bytes(int three);

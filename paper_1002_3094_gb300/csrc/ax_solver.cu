@@ -63,6 +63,11 @@ struct Workspace {
   double *chp = nullptr;      // Chebyshev (tau, rho0^2) per right-hand side [m][2]
   double *rscale = nullptr;   // mixed methods: power-of-two scale of phi and x per right-hand side [m]
   RhsState *st = nullptr, *st_outer = nullptr;
+  // [0] right-hand sides the residual-replacement step has put in kCheck (the
+  // gate of its masked launches; reset at the end of the step), [1] the same
+  // counted over the current solve (option "replace_checks")
+  int *chk = nullptr;
+  int replace_gate = 1;         // 0: the replacement step's launches are not gated
   RhsState *h_st = nullptr;   // pinned host mirror [2 m]
   // dense FP64 staging for host buffers and single-step entry points
   double *stage_a = nullptr, *stage_b = nullptr;
@@ -197,7 +202,7 @@ void free_vectors32(Workspace *w) {
 }
 void free_base(Workspace *w) {
   dfree(w->phi64); dfree(w->x64); dfree(w->part); dfree(w->chp); dfree(w->rscale); dfree(w->st);
-  dfree(w->st_outer);
+  dfree(w->st_outer); dfree(w->chk);
   if (w->h_st) cudaFreeHost(w->h_st);
   w->h_st = nullptr;
   w->mbase = 0;
@@ -219,6 +224,8 @@ int ensure_base(ax_operator *op, int m) {
   AX_TRY(dalloc(&w->rscale, (size_t)m));
   AX_TRY(dalloc(&w->st, (size_t)m));
   AX_TRY(dalloc(&w->st_outer, (size_t)m));
+  AX_TRY(dalloc(&w->chk, 2));
+  AX_TRY(cudaMemset(w->chk, 0, 2 * sizeof(int)));
   AX_TRY(cudaMallocHost((void **)&w->h_st, sizeof(RhsState) * 2 * m));
   w->mbase = m;
   return AX_OK;
@@ -585,7 +592,9 @@ __global__ void __launch_bounds__(256) pcg_update(float *__restrict__ x, float *
 __global__ void __launch_bounds__(256) split_field(const float *__restrict__ in, int nr, int n, int pitch,
                                                    size_t field, int mtiles, int ktiles, int kbe,
                                                    unsigned char *__restrict__ split,
-                                                   const RhsState *st, int mask, int cosine) {
+                                                   const RhsState *st, int mask, int cosine,
+                                                   const int *gate) {
+  if (gate != nullptr && *gate == 0) return;  // nothing selected (see GemmDstArgs::gate)
   const int m = blockIdx.y;
   if (!rhs_selected(st, mask, m)) return;
   const int nch = (n + 7) >> 3;
@@ -722,9 +731,10 @@ __global__ void sc_beta(RhsState *st, const double *p, int nb, int mask, int nex
 }
 
 // Right-hand sides (of n) in state `from` move to `to`.
-__global__ void sc_promote(RhsState *st, int n, int from, int to) {
+__global__ void sc_promote(RhsState *st, int n, int from, int to, int *reset) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < n && st[m].state == from) st[m].state = to;
+  if (reset != nullptr && m == 0) *reset = 0;
 }
 
 // True-residual test of right-hand sides in kCheck.
@@ -807,7 +817,7 @@ __global__ void sc_mixed_start(RhsState *st, const double *prr, int nbr, const d
 // Residual replacement: rr = ||phi - A x64||^2 just computed in FP64 for the
 // right-hand sides in kCheck.  Done, failed, or a new threshold (the caller
 // then recomputes z = B^-1 r and resumes with sc_beta).
-__global__ void sc_mixed_replace(RhsState *st, const double *prr, int nbr, double tol2, double delta2) {
+__global__ void sc_mixed_replace(RhsState *st, const double *prr, int nbr, double tol2, double delta2, int *chk) {
   const int m = blockIdx.x;
   if (!rhs_selected(st, kDue, m)) return;
   const double rr = reduce_part(prr + (size_t)m * kPartialStride, nbr);
@@ -831,7 +841,11 @@ __global__ void sc_mixed_replace(RhsState *st, const double *prr, int nbr, doubl
       s.status = AX_ERR_NO_CONVERGENCE;
     } else {
       s.thresh2 = fmax(delta2 * rr, 0.25 * tol2 * s.bb);
-      if (!consistent) s.state = kCheck;
+      if (!consistent) {
+        s.state = kCheck;
+        atomicAdd(chk, 1);  // opens the gate of the step's masked launches
+        atomicAdd(chk + 1, 1);
+      }
     }
     st[m] = s;
   }
@@ -1349,8 +1363,9 @@ bool tc_tr_mode(const ax_operator *op, int m) {
 void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A, bool inverse, float *out,
                   const RhsState *st, int mask, const float *r, double *partial, cudaStream_t s, int three = -1,
                   float *pa = nullptr, float *pb = nullptr, float *x = nullptr, bool scaled = false,
-                  bool tout = false) {
+                  bool tout = false, const int *gate = nullptr) {
   GemmDstArgs g{};
+  g.gate = gate;
   if (tout) {  // mode-major output for the mode-solve kernel 14 (forward only)
     g.tout = 1;
     g.tpitch = op->tpitch;
@@ -1394,12 +1409,17 @@ void tc_transform(const ax_operator *op, int m, int rows, const unsigned char *A
 
 // FP32 field -> split operand (rows per RHS `rows`).
 void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned char *split, const RhsState *st,
-              int mask, cudaStream_t s) {
+              int mask, cudaStream_t s, const int *gate = nullptr) {
   const SplitGeom g = split_geom(op, rows);
+  // kCheck (the replacement step's recomputation of z) selects a right-hand
+  // side rarely: fewer CTAs per right-hand side, so that the usual launch in
+  // which none is selected ends soon (the CTAs loop over the rows)
+  const int bx = mask == kCheck ? std::min(update_blocks(rows, op->nz), 8) : update_blocks(rows, op->nz);
   note_launch();
-  split_field<<<dim3(update_blocks(rows, op->nz), m), 256, 0, s>>>(in, rows, op->nz, op->pitch,
+  split_field<<<dim3(bx, m), 256, 0, s>>>(in, rows, op->nz, op->pitch,
                                                                    (size_t)rows * op->pitch,
-                                                      g.mtiles, g.ktiles, g.kbe, split, st, mask, op->bc_z == 1);
+                                                      g.mtiles, g.ktiles, g.kbe, split, st, mask, op->bc_z == 1,
+                                                      gate);
 }
 
 // Mode solves z -> split operand (the tile kernel writes it directly; otherwise
@@ -1408,7 +1428,7 @@ void tc_split(const ax_operator *op, int m, int rows, const float *in, unsigned 
 // (rhat, yhat), equal to (r, z) up to the rounding of the split input: S is
 // symmetric, so (r, S yhat) = (S r, yhat).
 void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, unsigned char *split,
-                   const RhsState *st, int mask, cudaStream_t s, double *prz = nullptr) {
+                   const RhsState *st, int mask, cudaStream_t s, double *prz = nullptr, const int *gate = nullptr) {
   const SplitGeom g = split_geom(op, op->nr);
   TriArgs<float> t = tri_args<float>(op, m, z, tmp, st, mask);
   t.variant = tc_mode_variant(op, m);
@@ -1429,7 +1449,7 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
     launch_tridiag<float>(t, s);
   } else {
     launch_tridiag<float>(t, s);
-    tc_split(op, m, op->nr, tmp, split, st, mask, s);
+    tc_split(op, m, op->nr, tmp, split, st, mask, s, gate);
   }
 }
 
@@ -2113,6 +2133,7 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
   };
   note_launch();
   to_df<<<cblocks, 256, 0, s>>>(w->phi64, w->phh, w->phl, nall);
+  AX_TRY(cudaMemsetAsync(w->chk, 0, 2 * sizeof(int), s));
   // Residual replacement, inside the captured graph after every iteration: the
   // right-hand sides marked due went through the whole iteration (z and beta
   // from their recursive residual); x32 is folded into the double-float x and
@@ -2126,21 +2147,28 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     fold_df<<<zg, 256, 0, ss>>>(w->xh, w->xl, w->x32, field, st, kDue);
     residual64(kDue, ss);
     note_launch();
-    sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbdf, tol * tol, delta * delta);
+    sc_mixed_replace<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartB), nbdf, tol * tol, delta * delta, w->chk);
     if (fused) {
       // z = B^-1 r and beta from the true residual, then the direction of this
-      // step again, p_new = z + beta p_old (x already holds alpha p_old)
+      // step again, p_new = z + beta p_old (x already holds alpha p_old).  The
+      // split and the two transforms are gated by the count of right-hand
+      // sides in kCheck, which is usually 0: they then return at once, where
+      // the transforms would otherwise walk their persistent tile lists
+      // (sc_promote resets the count).  The mode solves' CTAs each test their
+      // own right-hand side, as cheap as the gate
       unsigned char *sp = w->split;
-      tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss);
+      const int *gate = w->replace_gate ? w->chk : nullptr;
+      tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss, gate);
       const bool sc = tc_scaled(op, m);
       tc_transform(op, m, op->nr, sp, false, v.z, st, kCheck, nullptr, nullptr, ss, -1, nullptr, nullptr, nullptr, sc,
-                   tc_tr_mode(op, m));
-      tc_mode_solve(op, m, v.z, v.q, sp, st, kCheck, ss, part_ptr(w, kPartC));
+                   tc_tr_mode(op, m), gate);
+      tc_mode_solve(op, m, v.z, v.q, sp, st, kCheck, ss, part_ptr(w, kPartC), gate);
       note_launch();
       sc_beta<<<m, 32, 0, ss>>>(st, part_ptr(w, kPartC), nbd, kCheck, kCheck, 1);
-      tc_transform(op, m, op->nr, sp, true, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr, sc);
+      tc_transform(op, m, op->nr, sp, true, v.z, st, kCheck, nullptr, nullptr, ss, -1, v.pa, v.pb, nullptr, sc, false,
+                   gate);
       note_launch();
-      sc_promote<<<(m + 31) / 32, 32, 0, ss>>>(st, m, kCheck, kActive);
+      sc_promote<<<(m + 31) / 32, 32, 0, ss>>>(st, m, kCheck, kActive, w->chk);
       return;
     }
     precond_apply<float>(op, m, v.r, v.z, st, kCheck, part_ptr(w, kPartC), ss, v.q);
@@ -2513,6 +2541,13 @@ int ax_get_option(const ax_operator *op, const char *name, double *value) {
   else if (!strcmp(name, "replace_delta")) *value = w->replace_delta;
   else if (!strcmp(name, "mixed_restart")) *value = w->mixed_restart;
   else if (!strcmp(name, "tc_fused")) *value = w->tc_unfused ? 0 : 1;
+  else if (!strcmp(name, "replace_gate")) *value = w->replace_gate;
+  else if (!strcmp(name, "replace_checks")) {  // read-only: synchronises the device
+    int h = 0;
+    if (w->chk != nullptr && cudaMemcpy(&h, w->chk + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return AX_ERR_CUDA;
+    *value = h;
+  }
   else if (!strcmp(name, "cheb_bounds")) *value = w->cheb_bounds;
   else if (!strcmp(name, "cheb_steps")) *value = w->cheb_steps;
   else if (!strcmp(name, "cheb_widen")) *value = w->cheb_widen;
@@ -2565,6 +2600,13 @@ int ax_set_option(ax_operator *op, const char *name, double value) {
     w->replace_delta = value;
   } else if (!strcmp(name, "tc_fused")) {
     w->tc_unfused = value == 0.0;
+    free_graph(w->g32);
+  } else if (!strcmp(name, "replace_gate")) {
+    // 1 (default): the z recomputation of the residual-replacement step
+    // (tensor-core path) returns at once when no right-hand side needs it; 0:
+    // its launches walk their grids regardless.  Results are the same
+    if (value != 0.0 && value != 1.0) return AX_ERR_INVALID_ARG;
+    w->replace_gate = (int)value;
     free_graph(w->g32);
   } else if (!strcmp(name, "small_path")) {
     // AX_PCG_FP64 of one right-hand side on a small grid as one persistent
@@ -3445,6 +3487,7 @@ int ax_batch_create(ax_operator *const *ops, int32_t n, void *stream, ax_batch *
       gw->max_outer = ow->max_outer;
       gw->mixed_restart = ow->mixed_restart;
       gw->tc_unfused = ow->tc_unfused;
+      gw->replace_gate = ow->replace_gate;
       gw->replace_delta = ow->replace_delta;
       gw->cheb_bounds = ow->cheb_bounds;
       gw->cheb_steps = ow->cheb_steps;

@@ -188,3 +188,39 @@ def test_bounded_wait_expiry_returns_timeout_and_context_stays_usable(cuda):
     err = np.linalg.norm(y.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert err.max() <= 1e-5
     P.ax_destroy_operator(op)
+
+
+@pytest.mark.parametrize("j,nr,nz,m,tol,checks", [(66, 2047, 255, 1, 1e-8, True), (None, 600, 700, 3, 1e-11, False)])
+def test_replacement_gate_keeps_results(cuda, j, nr, nz, m, tol, checks):
+    """The split and transform launches that recompute z after a residual
+    replacement are gated by a device count of the right-hand sides that need
+    it (option replace_gate): with and without the gate the solve is the same
+    bit for bit, on a case where the recomputation does happen
+    (replace_checks > 0: an ill-conditioned random-field medium) and on one
+    where it does not (the gate stays closed)."""
+    from workloads import batched_instances
+    med = batched_instances(256)[j][2] if j is not None else layered_inclusion_medium(n_rhs=m, nominal_n=nr,
+                                                                                       instance=9)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    op = P.ax_setup_operator(*[torch.from_numpy(x).to(cuda) for x in (kr, kz, q)], nr, nz)
+    P.ax_set_option(op, "dst_tensor", 1)  # the fused tensor-core iteration, whose replacement step is gated
+    assert int(P.ax_get_option(op, "replace_gate")) == 1
+    assert P.ax_set_option(op, "replace_gate", 2, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+    f = sample_rhs(med, nr, nz)[:m]
+    fd = torch.from_numpy(f).to(cuda)
+    out = {}
+    for gate in (1, 0):
+        P.ax_set_option(op, "replace_gate", gate)
+        u = torch.zeros_like(fd)
+        st, info = P.ax_solve(op, fd, u, m, tol, 5000, P.AX_PCG_MIXED)
+        torch.cuda.synchronize()
+        assert st == P.AX_OK
+        out[gate] = ([i["iters"] for i in info], u.cpu().numpy(), int(P.ax_get_option(op, "replace_checks")))
+    assert (out[1][2] > 0) == checks and out[1][2] == out[0][2], (out[1][2], out[0][2])
+    assert out[1][0] == out[0][0]
+    assert np.array_equal(out[1][1], out[0][1])
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
+    for k in range(m):
+        phi = ora.phi(f[k])
+        assert np.linalg.norm(phi - ora.apply_A(out[1][1][k])) <= tol * np.linalg.norm(phi)
+    P.ax_destroy_operator(op)
