@@ -200,12 +200,11 @@ int ax_chebyshev_bounds(const ax_operator *op, int32_t m, double *gamma1, double
  *                    forms p = z + beta p and x += alpha p in the inverse
  *                    transform's epilogue; 0: in the stencil and update pass
  *   "replace_gate"   1 (default): with the fused tensor-core iteration, the
- *                    split and transform launches that recompute z for the
- *                    right-hand sides whose true residual departed from the
- *                    recursive one (residual replacement) return at once when
- *                    there are none (a device count kept by the scalar
- *                    kernels); 0: they walk their grids.  Results are the
- *                    same bit for bit
+ *                    launches that recompute z for the right-hand sides whose
+ *                    true residual departed from the recursive one (residual
+ *                    replacement) return at once when there are none (a device
+ *                    count kept by the scalar kernels); 0: they walk their
+ *                    grids.  Results are the same bit for bit
  *   "mode_kernel"    FP32 mode solves (the per-mode tridiagonal systems of
  *                    Eq. eq_trid): 0 (default) the library's choice, 1 the
  *                    staged register kernel, 9 the same on the row-scaled

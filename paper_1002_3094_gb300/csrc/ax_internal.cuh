@@ -401,6 +401,12 @@ struct TriArgs {
   const T *IPST;
   long long tcstride;
   int tpitch;
+  // kernel 14, for a mask that rarely selects a right-hand side: short_grid =
+  // 1 runs a few CTAs per SM that loop over the tiles (instead of one CTA per
+  // tile), returning at once while *gate == 0 if gate is set (see
+  // GemmDstArgs::gate)
+  int short_grid;
+  const int *gate;
 };
 
 template <typename T>

@@ -1437,6 +1437,10 @@ void tc_mode_solve(const ax_operator *op, int m, const float *z, float *tmp, uns
     t.IPST = op->c32.IPST;
     t.tcstride = op->cstride != 0 ? (long long)op->nz * op->tpitch : 0;
     t.tpitch = op->tpitch;
+    if (mask == kCheck) {  // rarely selected: a short grid, gated where the caller keeps the count
+      t.short_grid = 1;
+      t.gate = gate;
+    }
   } else if (t.variant == 14) {
     t.variant = 9;
   }
@@ -2151,11 +2155,10 @@ int pcg_mixed_loop(ax_operator *op, int m, double tol, double delta, int max_ite
     if (fused) {
       // z = B^-1 r and beta from the true residual, then the direction of this
       // step again, p_new = z + beta p_old (x already holds alpha p_old).  The
-      // split and the two transforms are gated by the count of right-hand
-      // sides in kCheck, which is usually 0: they then return at once, where
-      // the transforms would otherwise walk their persistent tile lists
-      // (sc_promote resets the count).  The mode solves' CTAs each test their
-      // own right-hand side, as cheap as the gate
+      // launches are gated by the count of right-hand sides in kCheck, which
+      // is usually 0: they then return at once, where they would otherwise
+      // walk their tile lists or grids (sc_promote resets the count); the mode
+      // solves run on a short grid of CTAs looping over the tiles
       unsigned char *sp = w->split;
       const int *gate = w->replace_gate ? w->chk : nullptr;
       tc_split(op, m, op->nr, v.r, sp, st, kCheck, ss, gate);

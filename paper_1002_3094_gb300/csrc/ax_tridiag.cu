@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
 // the split operand are those of tridiag_reg2_kernel, whose layout the tile
 // keeps.
 // ---------------------------------------------------------------------------
-template <int C2, int WPC, int CW>
+template <int C2, int WPC, int CW, bool LOOP>
 __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
     tridiag_tr_kernel(const TriArgs<float> a) {
   constexpr int NT = 32 * WPC * CW;
@@ -953,10 +953,11 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
   extern __shared__ __align__(16) float tsm3[];
   __shared__ float xfa[CW][WPC], xfm[CW][WPC], xba[CW][WPC], xbm[CW][WPC];
   __shared__ double red[NT / 32];
+  // one tile: column group cg (columns cg CW ..) of right-hand side m
+  auto tile = [&](const int cg, const int m) {
   const int nr = a.nr;
   float *ds = tsm3;
-  const int col0 = blockIdx.x * CW;
-  const int m = blockIdx.y;
+  const int col0 = cg * CW;
   if (!rhs_selected(a.st, a.mask, m)) return;  // uniform over the CTA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int w = warp / WPC, h = warp % WPC;  // column, segment of the r-range
@@ -1078,7 +1079,7 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
   if (a.partial != nullptr && threadIdx.x == 0) {
     double tot = 0.0;
     for (int i = 0; i < NT / 32; ++i) tot += red[i];
-    a.partial[(size_t)m * kPartialStride + blockIdx.x] = tot;
+    a.partial[(size_t)m * kPartialStride + cg] = tot;
   }
   // ---- write back: one thread per row, its CW columns (as tridiag_reg2_kernel)
   const int ncol = min(CW, a.nz - col0);
@@ -1108,15 +1109,43 @@ __global__ void __launch_bounds__(32 * WPC * CW, (32 * WPC * CW <= 512) ? 2 : 1)
       }
     }
   }
+  };
+  if constexpr (LOOP) {
+    // a launch that rarely selects a right-hand side (TriArgs::short_grid):
+    // a few CTAs per SM loop over the tiles t = (right-hand side t / ncg,
+    // column group t % ncg), after the gate (TriArgs::gate) if there is one
+    if (a.gate != nullptr && *a.gate == 0) return;  // nothing selected
+    const int ncg = (a.nz + CW - 1) / CW, ntiles = ncg * a.m;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      tile(t % ncg, t / ncg);
+      __syncthreads();  // the tile's shared arrays are read before the next tile writes them
+    }
+  } else {
+    tile(blockIdx.x, blockIdx.y);  // one CTA per tile
+  }
 }
 
 template <int C2, int WPC, int CW>
 void launch_tridiag_tr(const TriArgs<float> &a, cudaStream_t s) {
   constexpr int NT = 32 * WPC * CW;
   const size_t smem = (size_t)(32 * WPC) * (C2 * CW + 2) * sizeof(float);
-  ensure_smem_attr((const void *)tridiag_tr_kernel<C2, WPC, CW>, smem);
+  if (a.short_grid) {
+    ensure_smem_attr((const void *)tridiag_tr_kernel<C2, WPC, CW, true>, smem);
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 148;
+    }
+    const long long tiles = (long long)((a.nz + CW - 1) / CW) * a.m;
+    const int grid = (int)std::min<long long>(tiles, (long long)sms * (NT <= 512 ? 2 : 1));
+    tridiag_tr_kernel<C2, WPC, CW, true><<<grid, NT, smem, s>>>(a);
+    return;
+  }
+  ensure_smem_attr((const void *)tridiag_tr_kernel<C2, WPC, CW, false>, smem);
   dim3 grid((a.nz + CW - 1) / CW, a.m);
-  tridiag_tr_kernel<C2, WPC, CW><<<grid, NT, smem, s>>>(a);
+  tridiag_tr_kernel<C2, WPC, CW, false><<<grid, NT, smem, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
