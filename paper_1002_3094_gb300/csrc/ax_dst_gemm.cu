@@ -115,8 +115,13 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
 
 // Tile t (persistent CTAs take t = blockIdx.x, + gridDim.x, ...): N tile
 // fastest, so the CTAs working on one M tile at a time share its input tiles
-// in L2.
+// in L2.  The tiles run from the last right-hand side to the first: the
+// kernels that write this transform's input (the update pass, the mode
+// solves) and read its output (the mode solves) go from the first to the
+// last, so the input written last, still in L2, is read first, and the output
+// written last is read first by the next kernel.
 __device__ __forceinline__ void gemm_tile(const GemmDstArgs &a, int t, int &m, int &mt, int &nt) {
+  t = a.m * a.mtiles * a.ntiles - 1 - t;
   nt = t % a.ntiles;
   const int mm = t / a.ntiles;
   m = mm / a.mtiles;
