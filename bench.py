@@ -485,6 +485,9 @@ def run_batched(args):
             P.ax_set_option(op, "dst_tensor", args.dst_tensor)
         if args.replace_delta > 0:
             P.ax_set_option(op, "replace_delta", args.replace_delta)
+        for kv in args.option:  # every instance (a shape group takes its first member's solver options)
+            name, value = kv.split("=", 1)
+            P.ax_set_option(op, name, float(value))
     batch = P.ax_batch_create(ops)
     method = P.METHODS[args.method]
     stream = torch.cuda.current_stream()
@@ -554,12 +557,16 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": "batched_256", "instances": len(ops), "unknowns": unknowns, "groups": groups,
                        "bc_z": args.bc_z,
-                       "method": args.method, "tol": TOL, "autotuned": not args.no_autotune},
+                       "method": args.method, "tol": TOL, "autotuned": not args.no_autotune,
+                       "options": list(args.option)},
             "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
                            "max": float(max(lats)), "min": float(min(lats)),
                            "meaning": "per instance: batch start to the graph replay in which it converged"},
             "iters": {"max": max(i["iters"] for i in info), "min": min(i["iters"] for i in info),
-                      "mean": float(np.mean([i["iters"] for i in info]))},
+                      "mean": float(np.mean([i["iters"] for i in info])),
+                      "p90": float(np.percentile([i["iters"] for i in info], 90)),
+                      "slowest": sorted(([i["iters"], j, list(nr_nz[j])] for j, i in enumerate(info)),
+                                        reverse=True)[:3]},
             "max_rel_res": max(i["rel_res"] for i in info),
             "plain_fp64": plain, "vs_plain_fp64": (value / plain["value"]) if plain else None,
             "autotune_s": tune_s, "tuned_groups": tuned,

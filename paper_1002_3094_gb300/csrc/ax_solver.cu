@@ -1804,6 +1804,18 @@ bool cheb_uses_lanczos(const ax_operator *op, double face_gamma1) {
   return mode == 1 || (mode == -1 && !(face_gamma1 > 0.0));
 }
 
+// The estimate's steps of a right-hand side stop once its residual has fallen
+// to 1e-6 of ||phi|| (thresh2 = rel2 ||phi||^2; pbb: the ||phi||^2 partials):
+// the FP32 steps reach their rounding floor near 1e-7, the coefficients of
+// later steps come from rounding noise, and their Ritz values need not lie in
+// the spectrum of B^-1 A (with 40 steps one batched instance that PCG solves
+// in 9 iterations got bounds on which Chebyshev diverged).
+__global__ void sc_lanczos_stop(RhsState *st, const double *pbb, int nbb, double rel2) {
+  const int m = blockIdx.x;
+  const double bb = reduce_part(pbb + (size_t)m * kPartialStride, nbb);
+  if (threadIdx.x == 0) st[m].thresh2 = rel2 * bb;
+}
+
 // hist[m][2 k]: (alpha_j, beta_j) of step j of right-hand side m; an alpha of
 // 0 marks the end (the step did not run, or broke down).
 __global__ void sc_record_lanczos(const RhsState *st, double *hist, int m, int j, int k) {
@@ -1880,8 +1892,8 @@ int cheb_estimate(ax_operator *op, int m, cudaStream_t s, std::vector<int> *step
   note_launch();
   to_precision<float><<<blocks, 256, 0, s>>>(w->phi64, w->r32, n);
   AX_TRY(cudaMemsetAsync(w->x32, 0, sizeof(float) * n, s));
-  // states: every right-hand side active (threshold 0: nothing converges
-  // before the k steps unless its residual vanishes), max_iter = k
+  // states: every right-hand side active, max_iter = k, the threshold set
+  // below (sc_lanczos_stop)
   {
     std::vector<RhsState> init(m);
     for (int i = 0; i < m; ++i) {
@@ -1893,6 +1905,9 @@ int cheb_estimate(ax_operator *op, int m, cudaStream_t s, std::vector<int> *step
     }
     AX_TRY(cudaMemcpyAsync(w->st, init.data(), sizeof(RhsState) * m, cudaMemcpyHostToDevice, s));
   }
+  // ||phi||^2 partials of ax_solve (prep_rhs / phi_norm2; r starts as phi)
+  note_launch();
+  sc_lanczos_stop<<<m, 32, 0, s>>>(w->st, part_ptr(w, kPartD), (op->nr + 15) / 16, 1e-12);
   PcgVecs<float> v{w->x32, w->r32, w->pa32, w->pb32, w->q32, w->z32};
   const int nbd = precond_partials<float>(op, m);
   precond_apply<float>(op, m, v.r, v.z, w->st, kActive, part_ptr(w, kPartC), s, v.q);
