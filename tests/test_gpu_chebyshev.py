@@ -12,7 +12,10 @@ reduction-free steps between residual checks, through the C ABI.
   - option cheb_bounds = 1 on a medium whose face-wise bounds are fine gives
     the same tolerance;
   - cheb_check = 4 (residual norm every 4th step): same tolerance, at most 3
-    more iterations than checking every step.
+    more iterations than checking every step;
+  - on an instance that PCG solves in a few iterations, 20 or 40 estimation
+    steps (past the FP32 rounding floor, where the estimate stops) still give
+    bounds on which Chebyshev meets the tolerance.
 """
 import numpy as np
 import pytest
@@ -147,4 +150,33 @@ def test_reduction_free_steps(cuda, method):
         for a, b in zip(i1, i4):
             assert a["iters"] <= b["iters"] <= a["iters"] + 3, (a, b)
     assert P.ax_set_option(op, "cheb_check", 0, raise_on_error=False) == P.AX_ERR_INVALID_ARG
+    P.ax_destroy_operator(op)
+
+
+@pytest.mark.parametrize("steps", [20, 40])
+def test_estimate_stops_at_the_fp32_floor(cuda, steps):
+    """An instance of the batched workload that PCG solves in a few
+    iterations (127 x 511): more estimation steps than it needs run into the
+    FP32 rounding floor, whose coefficients are noise.  The estimate stops
+    there (residual below 1e-6 of ||phi||), so Chebyshev with the estimated
+    bounds still meets 1e-8 in the oracle's FP64 residual, in at most twice
+    the FP64 PCG iterations plus the estimation steps (with 40 steps and no
+    stop it diverged)."""
+    from workloads import batched_instances
+    nr, nz, med = batched_instances(256)[105]
+    assert (nr, nz) == (127, 511)
+    op, ora, f = _setup(med, nr, nz, cuda)
+    f = f[:1]
+    fd = torch.from_numpy(f).to(cuda)
+    u64 = torch.zeros_like(fd)
+    st, i64 = P.ax_solve(op, fd, u64, 1, 1e-8, 5000, P.AX_PCG_FP64)
+    assert st == P.AX_OK
+    P.ax_set_option(op, "cheb_bounds", 1)
+    P.ax_set_option(op, "cheb_steps", steps)
+    for method in (P.AX_CHEB_MIXED, P.AX_CHEB_FP64):
+        u = torch.zeros_like(fd)
+        st, info = P.ax_solve(op, fd, u, 1, 1e-8, 5000, method, raise_on_error=False)
+        assert st == P.AX_OK, info
+        assert (_residuals(ora, f, u.cpu().numpy()) <= 1e-8).all()
+        assert info[0]["iters"] <= 2 * i64[0]["iters"] + steps + 10, (info, i64)
     P.ax_destroy_operator(op)
