@@ -350,6 +350,21 @@ int ax_guessnet_features_pre(ax_operator *op, const double *kappa, const double 
 int ax_guessnet_lift(const float *y, int32_t m, int32_t hw, const double *scale, int32_t nr, int32_t nz,
                      double *u, void *stream);
 
+/* Solve from the network's guess, the learned-guess path in one call (the
+ * pieces above, composed): the features of (kappa, q, f) on the network's
+ * lattice (features_pre when pre != 0, else features; kappa, q [nr][nz] as
+ * there), the forward pass (in batches of the network's capacity), the lift
+ * u0 = (s / target_scale) * bilinear(y) (target_scale > 0: the factor the
+ * training targets u / s were multiplied by, 1 if none) into u, then ax_solve
+ * with AX_FLAG_USE_GUESS | AX_FLAG_CHECK_GUESS added to flags: a right-hand
+ * side keeps its guess only if the gate accepts it (info.guess_accepted) and
+ * always iterates to tol.  f, u: [m][nr][nz] device FP64 (host buffers:
+ * AX_ERR_UNSUPPORTED).  Allocates and frees its scratch (features, outputs,
+ * scales: (4 hw^2 + 2) m words) and, like ax_solve, returns after the solve. */
+int ax_solve_learned(ax_operator *op, void *net, const double *kappa, const double *q, const double *f, double *u,
+                     int32_t m, double tol, int32_t max_iter, int32_t method, int32_t flags, int32_t pre,
+                     double target_scale, ax_solve_info *info, void *stream);
+
 /* ---- single steps of the hot path, for testing each kernel -----------------
  * All take FP64 device arrays [m][nr][nz]; precision selects the kernel
  * (AX_PREC_FP64 or AX_PREC_FP32 — the FP32 kernels round the input to FP32

@@ -49,7 +49,7 @@ EXPORTED = ("ax_setup_operator", "ax_destroy_operator", "ax_operator_info", "ax_
             "ax_guessnet_set_params", "ax_guessnet_forward", "ax_guessnet_gradients", "ax_guessnet_train_step",
             "ax_guessnet_save", "ax_guessnet_load", "ax_guessnet_features", "ax_guessnet_lift",
             "ax_guessnet_set_loss", "ax_guessnet_features_pre", "ax_chebyshev_bounds", "ax_get_option",
-            "ax_autotune", "ax_batch_autotune", "ax_batch_config")
+            "ax_autotune", "ax_batch_autotune", "ax_batch_config", "ax_solve_learned")
 
 PROFILE_KINDS = {"stencil": 0, "dst_forward": 1, "mode_solve": 2, "dst_inverse": 3, "scalar": 4,
                  "outer_residual": 5, "pcg_update": 6, "other": 7}
@@ -132,6 +132,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.ax_autotune.argtypes = [vp, i32, i32, vp]
     lib.ax_batch_autotune.argtypes = [vp, i32, vp]
     lib.ax_batch_config.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 5
+    lib.ax_solve_learned.argtypes = [vp, vp, vp, vp, vp, vp, i32, dbl, i32, i32, i32, i32, dbl,
+                                     ctypes.POINTER(AxSolveInfo), vp]
     for name in EXPORTED:
         if name not in ("ax_status_string", "ax_version", "ax_kernel_launches", "ax_last_error",
                         "ax_guessnet_num_params"):
@@ -250,6 +252,19 @@ def ax_solve(op: int, f, u, m: int, tol: float, max_iter: int = 10000, method: i
                                  _stream(None))
     if raise_on_error and st not in (AX_OK, AX_ERR_NO_CONVERGENCE):
         raise AxError(st, "ax_solve")
+    return st, [i.as_dict() for i in infos]
+
+
+def ax_solve_learned(op: int, net: int, kappa, q, f, u, m: int, tol: float, max_iter: int = 10000,
+                     method: int = AX_PCG_MIXED, flags: int = 0, pre: bool = True, target_scale: float = 1.0,
+                     stream=None, raise_on_error: bool = True):
+    """Solve from the network's guess (features, forward, lift, gated solve in
+    one library call); returns (status, [info dicts])."""
+    infos = (AxSolveInfo * m)()
+    st = load_library().ax_solve_learned(op, net, _ptr(kappa), _ptr(q), _ptr(f), _ptr(u), m, tol, max_iter, method,
+                                         flags, 1 if pre else 0, target_scale, infos, _stream(stream))
+    if raise_on_error and st not in (AX_OK, AX_ERR_NO_CONVERGENCE):
+        raise AxError(st, "ax_solve_learned")
     return st, [i.as_dict() for i in infos]
 
 

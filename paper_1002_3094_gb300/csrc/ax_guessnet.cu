@@ -17,6 +17,7 @@
 // activation of the same level after their ReLU.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -517,6 +518,12 @@ __global__ void features_kernel(const double *__restrict__ kappa, const double *
 
 // u[m][i][k] = s[m] * bilinear(y[m], at the lattice position of grid node (i, k)),
 // lattice values sitting at cell centres ((p + 1/2) / hw).
+// s[i] /= t for i < m (the feature scale of a lift whose training targets were
+// u / s times t)
+__global__ void div_scale_kernel(double *s, int m, double t) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) s[i] /= t;
+}
+
 __global__ void lift_kernel(const float *__restrict__ y, const double *__restrict__ s, int hw, int nr, int nz,
                             double *__restrict__ u) {
   const int m = blockIdx.y;
@@ -1060,6 +1067,50 @@ int ax_guessnet_lift(const float *y, int32_t m, int32_t hw, const double *scale,
   note_launch();
   lift_kernel<<<dim3(grid1d((size_t)nr * nz), m), 256, 0, s>>>(y, scale, hw, nr, nz, u);
   return cudaGetLastError() == cudaSuccess ? AX_OK : AX_ERR_CUDA;
+}
+
+int ax_solve_learned(ax_operator *op, void *net, const double *kappa, const double *q, const double *f, double *u,
+                     int32_t m, double tol, int32_t max_iter, int32_t method, int32_t flags, int32_t pre,
+                     double target_scale, ax_solve_info *info, void *stream) {
+  GuessNet *n = (GuessNet *)net;
+  if (!op || !n || !kappa || !q || !f || !u || m < 1 || !(target_scale > 0.0) || !std::isfinite(target_scale))
+    return AX_ERR_INVALID_ARG;
+  if (flags & AX_FLAG_HOST_BUFFERS) return AX_ERR_UNSUPPORTED;
+  const int32_t nr = op->nr, nz = op->nz;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int hw = n->hw;
+  float *x = nullptr, *y = nullptr;
+  double *sc = nullptr;
+  struct Free {
+    float *x, *y;
+    double *sc;
+    ~Free() {
+      if (x) cudaFree(x);
+      if (y) cudaFree(y);
+      if (sc) cudaFree(sc);
+    }
+  } hold{nullptr, nullptr, nullptr};
+  if (cudaMalloc(&x, (size_t)m * 3 * hw * hw * sizeof(float)) != cudaSuccess) return AX_ERR_OOM;
+  hold.x = x;
+  if (cudaMalloc(&y, (size_t)m * hw * hw * sizeof(float)) != cudaSuccess) return AX_ERR_OOM;
+  hold.y = y;
+  if (cudaMalloc(&sc, (size_t)m * sizeof(double)) != cudaSuccess) return AX_ERR_OOM;
+  hold.sc = sc;
+  int rc = pre ? ax_guessnet_features_pre(op, kappa, q, f, m, hw, x, sc, stream)
+               : ax_guessnet_features(kappa, q, f, m, nr, nz, hw, x, sc, stream);
+  if (rc != AX_OK) return rc;
+  for (int c = 0; c < m; c += n->cap) {  // the network's batches
+    const int b = std::min(n->cap, m - c);
+    if ((rc = ax_guessnet_forward(net, x + (size_t)c * 3 * hw * hw, y + (size_t)c * hw * hw, b, stream)) != AX_OK)
+      return rc;
+  }
+  if (target_scale != 1.0) {
+    note_launch();
+    div_scale_kernel<<<(m + 255) / 256, 256, 0, s>>>(sc, m, target_scale);
+  }
+  if ((rc = ax_guessnet_lift(y, m, hw, sc, nr, nz, u, stream)) != AX_OK) return rc;
+  return ax_solve(op, f, u, m, tol, max_iter, method, flags | AX_FLAG_USE_GUESS | AX_FLAG_CHECK_GUESS, info,
+                  stream);
 }
 
 }  // extern "C"

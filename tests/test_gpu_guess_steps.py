@@ -204,3 +204,52 @@ def test_guess_started_solves_meet_tolerance(cuda, method):
     assert res <= 1e-8
     P.ax_guessnet_destroy(net)
     P.ax_destroy_operator(op)
+
+
+@pytest.mark.parametrize("pre,target_scale", [(True, 1.0), (False, 40.0)])
+def test_solve_learned_equals_its_composition(cuda, pre, target_scale):
+    """ax_solve_learned (features, forward in batches of the network's
+    capacity, lift with s / target_scale, gated solve) gives the same guesses,
+    gate decisions, iterations and solutions, bit for bit, as the same steps
+    called one by one, and meets the tolerance in the oracle's FP64 residual.
+    Three right-hand sides on a network of capacity 2: two forward batches."""
+    nr = nz = 64
+    hw = 32
+    med = layered_inclusion_medium(n_rhs=3, nominal_n=64, instance=12)
+    kr, kz, q = sample_operator_inputs(med, nr, nz)
+    f = sample_rhs(med, nr, nz)[:3]
+    m = f.shape[0]
+    op = P.ax_setup_operator(_t(kr, cuda), _t(kz, cuda), _t(q, cuda), nr, nz)
+    ora = O.Operator(kr, kz, q, O.Grid(nr, nz))
+    net = P.ax_guessnet_create(hw, batch_capacity=2, seed=7)
+    kd, qd, fd = _t(kr, cuda), _t(q, cuda), _t(f, cuda)
+    # the steps one by one
+    x = torch.zeros((m, 3, hw, hw), dtype=torch.float32, device=cuda)
+    s = torch.zeros(m, dtype=torch.float64, device=cuda)
+    if pre:
+        P.ax_guessnet_features_pre(op, kd, qd, fd, m, hw, x, s)
+    else:
+        P.ax_guessnet_features(kd, qd, fd, m, nr, nz, hw, x, s)
+    y = torch.zeros((m, hw, hw), dtype=torch.float32, device=cuda)
+    for c in range(0, m, 2):
+        b = min(2, m - c)
+        P.ax_guessnet_forward(net, x[c:c + b], y[c:c + b], b)
+    u1 = torch.zeros_like(fd)
+    P.ax_guessnet_lift(y, m, hw, s / target_scale, nr, nz, u1)
+    st1, i1 = P.ax_solve(op, fd, u1, m, 1e-8, 5000, P.AX_PCG_MIXED, P.AX_FLAG_USE_GUESS | P.AX_FLAG_CHECK_GUESS)
+    # in one call
+    u2 = torch.full_like(fd, float("nan"))  # overwritten by the lift
+    st2, i2 = P.ax_solve_learned(op, net, kd, qd, fd, u2, m, 1e-8, 5000, P.AX_PCG_MIXED, pre=pre,
+                                 target_scale=target_scale)
+    torch.cuda.synchronize()
+    assert st1 == st2 == P.AX_OK
+    assert [(a["iters"], a["guess_accepted"]) for a in i1] == [(b["iters"], b["guess_accepted"]) for b in i2]
+    assert torch.equal(u1, u2)
+    un = u2.cpu().numpy()
+    for j in range(m):
+        phi = ora.phi(f[j])
+        assert np.linalg.norm(phi - ora.apply_A(un[j])) <= 1e-8 * np.linalg.norm(phi)
+    assert P.ax_solve_learned(op, net, kd, qd, fd, u2, m, 1e-8, 5000, P.AX_PCG_MIXED, target_scale=0.0,
+                              raise_on_error=False)[0] == P.AX_ERR_INVALID_ARG
+    P.ax_guessnet_destroy(net)
+    P.ax_destroy_operator(op)
