@@ -233,32 +233,16 @@ __global__ void __launch_bounds__(256) stencil_kernel(const StencilArgs<T> a) {
 
 // ---- double-float residual -------------------------------------------------
 // Pairs (h, l) of FP32 numbers carry about 48 significant bits: sums by Knuth's
-// two-sum and Dekker's fast two-sum, products by the FMA two-product (the exact
-// error of a*b is fma(a, b, -a*b)).  GB300 runs FP32 about 58 times faster
-// than FP64, so the true residual of the mixed method costs a few FP32
-// operations per flop instead of FP64 ones.
+// two-sum, products by the FMA two-product (the exact error of a*b is
+// fma(a, b, -a*b)).  GB300 runs FP32 about 58 times faster than FP64, so the
+// true residual of the mixed method costs a few FP32 operations per flop
+// instead of FP64 ones.
 struct DF {
   float h, l;
 };
 __device__ __forceinline__ DF df_two_sum(float a, float b) {
   const float s = a + b, bb = s - a;
   return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const DF s = df_two_sum(a.h, b.h);
-  return df_fast(s.h, s.l + (a.l + b.l));
-}
-__device__ __forceinline__ DF df_neg(DF a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  return df_fast(p, e);
 }
 
 constexpr int kDfRows = 16;      // rows per CTA (short: few right-hand sides are due at a time)
@@ -321,15 +305,39 @@ __global__ void __launch_bounds__(kDfThreads) residual_df_kernel(const DfResidua
       const DF yr = (e == 3) ? yright : DF{ych[e + 1], ycl[e + 1]};
       const DF czlo = {zh[e], zl[e]};
       const DF czhi = (e == 3) ? z4 : DF{zh[e + 1], zl[e + 1]};
-      // A y = W y + CR_i (y - y_{i+1}) + CR_{i-1} (y - y_{i-1})
-      //           + CZ_{k+1} (y - y_{k+1}) + CZ_k (y - y_{k-1})
-      DF v = df_mul({w4h[e], w4l[e]}, y);
-      v = df_add(v, df_mul({cch[e], ccl[e]}, df_add(y, df_neg({ynh[e], ynl[e]}))));
-      v = df_add(v, df_mul({cph[e], cpl[e]}, df_add(y, df_neg({ymh[e], yml[e]}))));
-      v = df_add(v, df_mul(czhi, df_add(y, df_neg(yr))));
-      v = df_add(v, df_mul(czlo, df_add(y, df_neg(yl))));
-      const DF r = df_add({fh[e], fl[e]}, df_neg(v));
-      res[e] = (k0 + e < nz) ? r.h + r.l : 0.f;
+      // r = phi - A y, A y = W y + CR_i (y - y_{i+1}) + CR_{i-1} (y - y_{i-1})
+      //                     + CZ_{k+1} (y - y_{k+1}) + CZ_k (y - y_{k-1}),
+      // as a compensated sum (Ogita, Rump and Oishi's Dot2: each product's
+      // high part exact by the FMA two-product, each addition's error by
+      // two-sum, the small terms gathered in one FP32 word): the accuracy of
+      // double-float arithmetic without renormalising after every operation
+      float sh = fh[e], se = fl[e];
+      auto sub_prod = [&](float ch, float cl, float dh, float dl) {  // s -= (ch + cl)(dh + dl)
+        const float p = ch * dh;
+        const float pe = fmaf(ch, dh, -p);
+        const float lo = fmaf(ch, dl, fmaf(cl, dh, pe));
+        const float t = sh - p, bb = t - sh;
+        se += ((sh - (t - bb)) - (p + bb)) - lo;
+        sh = t;
+      };
+      // y - y_n as an unnormalised pair: the high parts by two-sum, the low
+      // parts' difference added to its error
+      auto diff = [](DF u, DF w, float &dh, float &dl) {
+        const DF s2 = df_two_sum(u.h, -w.h);
+        dh = s2.h;
+        dl = s2.l + (u.l - w.l);
+      };
+      float dh, dl;
+      sub_prod(w4h[e], w4l[e], y.h, y.l);
+      diff(y, DF{ynh[e], ynl[e]}, dh, dl);
+      sub_prod(cch[e], ccl[e], dh, dl);
+      diff(y, DF{ymh[e], yml[e]}, dh, dl);
+      sub_prod(cph[e], cpl[e], dh, dl);
+      diff(y, yr, dh, dl);
+      sub_prod(czhi.h, czhi.l, dh, dl);
+      diff(y, yl, dh, dl);
+      sub_prod(czlo.h, czlo.l, dh, dl);
+      res[e] = (k0 + e < nz) ? sh + se : 0.f;
       acc = fmaf(res[e], res[e], acc);
     }
     if (col_ok) *reinterpret_cast<float4 *>(a.r32 + base + ro) = make_float4(res[0], res[1], res[2], res[3]);
