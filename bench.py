@@ -420,6 +420,20 @@ def _reference_laguerre(args):
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def arm_config(args, nr: int, nz: int, m: int, world: int) -> dict:
+    """The config of a single-operator workload's line (the same on both arms)."""
+    # working set of the mixed solve: f and u (FP64), the double-float x and
+    # phi, six FP32 vectors and the split operand, about 64 B per unknown
+    unknowns = nr * nz * m
+    ws_mb = (unknowns * 64) >> 20
+    l2_note = ("inputs larger than L2 (f is %d MB, solver working set ~%d MB)" % ((unknowns * 8) >> 20, ws_mb)
+               if ws_mb > 129 else
+               "working set ~%d MB fits in L2, no flush between steps (a solve this small is launch-bound)"
+               % max(ws_mb, 1))
+    return {"workload": args.workload, "nr": nr, "nz": nz, "rhs": m, "tol": TOL, "bc_z": args.bc_z,
+            "method": args.method, "parallelism": f"replicas x{world}", "l2": l2_note, "options": args.option}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -440,11 +454,18 @@ def run_reference(args):
             units += r["unknowns"]
         total = sum(times)
         value = units / total
+        # the GPU arm's config of this workload (each step here solves a
+        # bounded sample of it: cpu_baseline.sample says which)
+        if args.workload in ("layered_1024_m64", "large_4096_m16", "bumps_64"):
+            nr, nz, med = workload(args.workload, rhs=args.rhs)
+            config = arm_config(args, nr, nz, med.n_rhs, args.gpus)
+        else:
+            config = {"workload": args.workload, "tol": TOL, "bc_z": args.bc_z}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "impl": "reference",
-                "config": {"workload": args.workload, "rhs_per_step": cores, "tol": TOL, "bc_z": args.bc_z},
+                "config": config,
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                  "sample": f"each step: {r['sample']}"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -1010,22 +1031,13 @@ def main():
             pool.join()
 
     if rank == 0:
-        # working set of the mixed solve: f and u (FP64), the double-float x and
-        # phi, six FP32 vectors and the split operand, about 64 B per unknown
-        ws_mb = (unknowns_step * 64) >> 20
-        l2_note = ("inputs larger than L2 (f is %d MB, solver working set ~%d MB)" % (f_host.nbytes >> 20, ws_mb)
-                   if ws_mb > 129 else
-                   "working set ~%d MB fits in L2, no flush between steps (a solve this small is launch-bound)"
-                   % max(ws_mb, 1))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 inner / f64 refinement" if "mixed" in args.method else "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "nr": nr, "nz": nz, "rhs": m, "tol": TOL, "bc_z": args.bc_z,
-                       "method": args.method, "parallelism": f"replicas x{world}",
-                       "l2": l2_note, "options": args.option},
+            "config": arm_config(args, nr, nz, m, world),
             "iters": {"max": max(iters), "min": min(iters), "outer_max": max(outer)},
             "max_rel_res": rel,
             "plain_fp64": plain,
