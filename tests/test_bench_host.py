@@ -81,3 +81,17 @@ def test_kernel_class_follows_the_kernels_the_solve_ran():
     assert B.kernel_class("stencil", True, 14) == "stencil"
     for c in ("mode_solve_scaled", "mode_solve_reuse", "mode_solve_pipe", "mode_solve_modemajor"):
         assert len(B.source_hash(c)) == 16 and B.source_hash(c) != B.source_hash("stencil")
+
+
+def test_both_arms_describe_the_same_workload():
+    """The reference arm's line carries the GPU arm's config (arm_config) for
+    the single-operator workloads, sizes and right-hand-side count included."""
+    import argparse
+    for name, shape in (("layered_1024_m64", (1024, 1024, 64)), ("large_4096_m16", (4096, 4096, 16)),
+                        ("bumps_64", (64, 64, 1))):
+        args = argparse.Namespace(workload=name, bc_z=0, method="pcg_mixed", option=[], rhs=0, gpus=1)
+        nr, nz, med = B.workload(name, rhs=0)
+        cfg = B.arm_config(args, nr, nz, med.n_rhs, 1)
+        assert (cfg["nr"], cfg["nz"], cfg["rhs"]) == shape
+        assert cfg["workload"] == name and cfg["tol"] == B.TOL and cfg["parallelism"] == "replicas x1"
+        assert ("larger than L2" in cfg["l2"]) == (name != "bumps_64")
